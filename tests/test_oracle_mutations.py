@@ -1,0 +1,116 @@
+"""Plant plausible mistakes in a copy of the oracle (CPU only) and check that
+the oracle's pins catch every one: a dropped term, a wrong sign, index or
+exponent anywhere in Eq. 1-5, Eq. 4, Eq. 9-12 or the resampling must fail at
+least one pin.  Each planted variant runs in its own process, so a variant
+that crashes (an index run past the end) counts as caught too."""
+import concurrent.futures as cf
+import functools
+import json
+import os
+import subprocess
+import sys
+
+import oracle
+from tests import test_oracle_pf as P
+from tests import test_oracle_scheme as S
+
+PINS = [
+    S.test_dt_matches_section_4_1_numbers,
+    S.test_dt_floor_cap_fixed_and_event_clipping,
+    S.test_two_cell_hand_steps,
+    functools.partial(S.test_manning_normal_flow_is_fixed_point_of_eq2, dt=0.3),
+    S.test_seiche_period_is_2L_over_sqrt_gH,
+    S.test_lake_at_rest_over_bumpy_bed,
+    S.test_uniform_rain_on_flat_closed_box,
+    S.test_volume_balance_exact_to_1e12,
+    S.test_transposition_symmetry,
+    S.test_no_flow_over_a_dry_wall_eq3,
+    S.test_shallow_sheet_below_h_eps_does_not_move,
+    S.test_free_outflow_passes_outward_only,
+    S.test_positivity_with_limiter_on_urban_dem,
+    functools.partial(P.test_weights_match_scipy_gaussian_density, seed=0),
+    P.test_relative_sigma_variant,
+    P.test_equal_likelihood_keeps_prior_weights_and_neff_bounds,
+    functools.partial(P.test_systematic_resampling_brute_force, M=5),
+    P.test_one_hot_weights_select_one_particle,
+    P.test_slot_assignment_keeps_survivors_in_place,
+]
+
+# (name, original text, planted mistake)
+MUTATIONS = [
+    ("friction exponent 4/3", "pow(hflow, 7.0 / 3.0)", "pow(hflow, 4.0 / 3.0)"),
+    ("friction n instead of n^2", "p->g * nl * nl * fabs(q)", "p->g * nl * fabs(q)"),
+    ("friction without dt", "fabs(q) * dt / pow", "fabs(q) / pow"),
+    ("slope sign flipped", "(eta2 - eta1) / p->dx", "(eta1 - eta2) / p->dx"),
+    ("gravity term without g", "q - p->g * hflow * dt * S", "q - hflow * dt * S"),
+    ("Eq 3 as max depth", "fmax(eta1, eta2) - fmax(z1, z2)", "fmax(h1, h2)"),
+    ("Eq 3 with min bed", "fmax(eta1, eta2) - fmax(z1, z2)", "fmax(eta1, eta2) - fmin(z1, z2)"),
+    ("limiter on downstream depth", "(qn > 0.0 ? h1 : h2)", "(qn > 0.0 ? h2 : h1)"),
+    ("Eq 5 drops the south link", "+ qy_new[IQY(r, c)] * dx - qy_new[IQY(r + 1, c)] * dx",
+     "+ qy_new[IQY(r, c)] * dx"),
+    ("Eq 5 x/y index swap", "qx_new[IQX(r, c)] * dx - qx_new[IQX(r, c + 1)] * dx",
+     "qx_new[IQX(r, c)] * dx - qx_new[IQX(r, c)] * dx"),
+    ("Eq 1 divides by dx only", "dt * dV / (dx * dx)", "dt * dV / dx"),
+    ("rain without dt", "+ dt * rain;", "+ rain;"),
+    ("x-link roughness not averaged", "scale * 0.5 * (n[IX(r, c - 1)] + n[IX(r, c)])",
+     "scale * n[IX(r, c)]"),
+    ("roughness scale dropped on y links", "double nl = scale * 0.5 * (n[IX(r - 1, c)]",
+     "double nl = 0.5 * (n[IX(r - 1, c)]"),
+    ("ghost cell dry", "orc_link_flux(p, h, z, h, z - p->edge_slope", "orc_link_flux(p, h, z, 0.0, z - p->edge_slope"),
+    ("ghost cell above the edge", "z - p->edge_slope * p->dx", "z + p->edge_slope * p->dx"),
+    ("Eq 4 without g", "sqrt(p->g * hm)", "sqrt(hm)"),
+    ("Eq 4 ignores the cap", "if (dt > p->dt_cap) dt = p->dt_cap;", ""),
+    ("no landing on the block edge", "if (t + dt >= stop) {", "if (0) {"),
+    ("likelihood without the 1/2", "lw[i] = log(w_prior[i]) - 0.5 * chi2;",
+     "lw[i] = log(w_prior[i]) - chi2;"),
+    ("prior weight ignored", "lw[i] = log(w_prior[i]) - 0.5 * chi2;", "lw[i] = -0.5 * chi2;"),
+    ("N_eff as 1/sum w", "s2 += w_post[i] * w_post[i];", "s2 += w_post[i];"),
+    ("sigma not squared", "double e = (y[(size_t)i * G + g] - d[g]) / s;\n            chi2 += e * e;",
+     "double e = (y[(size_t)i * G + g] - d[g]) / s;\n            chi2 += e * e * s;"),
+    ("systematic offsets u + j/M", "double uj = (u + (double)j) / (double)M;",
+     "double uj = u + (double)j / (double)M;"),
+    ("resampling picks zero-weight ties", "c[i] <= uj) ++i;", "c[i] < uj) ++i;"),
+    ("survivor slots not kept", "if (k[s] >= 1) {", "if (k[s] >= 2) {"),
+]
+
+
+
+
+def run_pins(lib_path):
+    """Run every pin against the oracle library at lib_path; return the names
+    of the pins that failed."""
+    oracle._lib = oracle.load(lib_path)
+    failed = []
+    for pin in PINS:
+        try:
+            pin()
+        except (AssertionError, ValueError, IndexError, FloatingPointError):
+            failed.append(getattr(pin, "__name__", getattr(pin, "func", pin).__name__))
+    return failed
+
+
+def test_pins_catch_every_planted_mistake(tmp_path):
+    src = oracle.source()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    jobs = []
+    for k, (name, orig, bad) in enumerate(MUTATIONS):
+        assert src.count(orig) == 1, f"mutation anchor for {name!r} not unique"
+        path = oracle.compile_variant(src.replace(orig, bad), str(tmp_path / f"libmut{k}.so"))
+        jobs.append((name, path))
+
+    def run(job):
+        name, path = job
+        code = ("import json, sys; from tests import test_oracle_mutations as T; "
+                f"print(json.dumps(T.run_pins({path!r})))")
+        r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True,
+                           text=True, timeout=600)
+        if r.returncode != 0:
+            return name, ["<crashed>"]
+        return name, json.loads(r.stdout.strip().splitlines()[-1])
+
+    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        results = dict(ex.map(run, jobs))
+    missed = [name for name, failed in results.items() if not failed]
+    assert not missed, f"pins missed planted mistakes: {missed}"
+    # the unmodified oracle passes every pin
+    assert run_pins(oracle.build()) == []
