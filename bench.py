@@ -1,0 +1,413 @@
+"""Benchmark: ensemble local-inertial flood model + particle filter on GB300.
+
+Workload: 2000 x 2000 cells of 3 m (4.0 M cells), 96 members, triangular
+60 mm/h storm peaking at 20 min, per-member rain multiplier LN(0, 0.3) and
+Manning scale U[0.6, 1.4], six depth gauges observing a hidden truth member
+with N(0, 0.05 m) noise.  One benchmark step = one 300 s assimilation window:
+every member advances 300 s with its own CFL time step (fused flux +
+continuity kernel, one launch per step for all members), then the gauges are
+sampled and the particle filter weights, resamples and replaces members on
+the device.  Twelve steps cover the 1 h storm.
+
+Metric: member-cell-steps/s (members x cells x steps actually taken, per
+second), plus the step kernel's HBM roofline fraction.
+
+`--impl reference` times the FP64 CPU oracle (the reference for this
+workload) on the host cores, each step a bounded sample of the same work.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NY = NX = 2000
+M = 96
+G = 6
+WINDOW = 300.0
+SEED = 1
+BYTES_STATE = 24.0          # read + write h, qx, qy (FP32) per member-cell-step
+BYTES_STATIC = 8.0          # z, n (FP32) per cell per tile pass
+MEMBERS_PER_TILE = 4        # members sharing one static-field tile pass
+ALGO_BYTES = BYTES_STATE + BYTES_STATIC / MEMBERS_PER_TILE
+KERNEL_SOURCES = ["paper_2302_08341_gb300/csrc/step_kernel.cu",
+                  "paper_2302_08341_gb300/csrc/flood_internal.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=12)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ny", type=int, default=2000, help="rows (smaller cases for profiling)")
+    ap.add_argument("--nx", type=int, default=2000)
+    ap.add_argument("--members", type=int, default=96)
+    args = ap.parse_args()
+    global NY, NX, M
+    NY, NX, M = args.ny, args.nx, args.members
+    return args
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_unit():
+    """DRAM bytes per member-cell-step of the step kernel from the committed
+    ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_2000x2000x96.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_sha") != kernel_hash():
+        return None
+    return d.get("dram_bytes_per_member_cell_step")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.f:
+            return None
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r)
+                          if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def make_inputs():
+    from paper_2302_08341_gb300 import synth
+    terr = synth.make_terrain(NY, NX, seed=SEED)
+    hy = synth.hyetograph_triangular(60.0, 1200.0, 3600.0)
+    rm, sc = synth.ensemble_prior(SEED, M)
+    cells = synth.gauge_cells(terr, G, seed=SEED)
+    return terr, hy, rm, sc, cells
+
+
+def truth_observations(capi, terr, hy, cells, n_windows):
+    """Hidden truth member (own prior draw) run on the GPU; noisy depths at
+    the gauges at every window end (inputs of the benchmark, not timed)."""
+    from paper_2302_08341_gb300 import synth
+    trm, tsc = synth.ensemble_prior(SEED + 1000, 1)
+    obs = []
+    with capi.Grid(terr.z, terr.n) as g:
+        g.ensemble_init(1, trm, tsc, hy)
+        for w in range(1, n_windows + 1):
+            g.advance_to(WINDOW * w)
+            y = g.gauge_sample(cells)
+            obs.append(synth.observe(y[0], seed=SEED, window=w))
+    return obs
+
+
+def cpu_baseline(terr, hy, rm, sc, target_s=15.0):
+    """The FP64 oracle on the host, single thread, on a bounded sample: one
+    member of the 2000 x 2000 grid from a 5 cm wet start, as many steps as
+    fit in ~target_s."""
+    import oracle
+    p = oracle.Params(ny=NY, nx=NX)
+    z = terr.z.astype(np.float64); n = terr.n.astype(np.float64)
+    m = oracle.Member.dry(NY, NX, np.full((NY, NX), 0.05))
+    hy64 = hy.astype(np.float64)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < target_s:
+        oracle.advance(p, z, n, float(sc[0]), float(rm[0]), hy64, m, max_steps=2)
+        steps += 2
+    el = time.perf_counter() - t0
+    return {"value": steps * NY * NX / el, "unit": "member-cell-steps/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"1 member x {NY}x{NX} cells x {steps} steps from a 5 cm wet start, "
+                      f"FP64, 1 thread, {el:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, local = dist_setup(args)
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    terr, hy, rm, sc, cells = make_inputs()
+    p = oracle.Params(ny=NY, nx=NX)
+    z = terr.z.astype(np.float64); n = terr.n.astype(np.float64)
+    hy64 = hy.astype(np.float64)
+    steps_per_sample = 2
+    m = oracle.Member.dry(NY, NX, np.full((NY, NX), 0.05))
+    for _ in range(args.warmup):
+        oracle.advance(p, z, n, float(sc[0]), float(rm[0]), hy64, m, max_steps=steps_per_sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.advance(p, z, n, float(sc[0]), float(rm[0]), hy64, m, max_steps=steps_per_sample)
+    el = time.perf_counter() - t0
+    units = args.steps * steps_per_sample * NY * NX
+    v = units / el
+    sample = (f"each step: 1 member x {NY}x{NX} cells x {steps_per_sample} FP64 oracle steps "
+              f"from a 5 cm wet start, 1 thread")
+    print(json.dumps({
+        "impl": "reference", "metric": "member-cell-steps/s", "value": v,
+        "unit": "member-cell-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"ensemble flood {NY}x{NX} cells x {M} members, 300 s windows "
+                               "(oracle sample)", "cells": NY * NX, "members": M},
+        "cpu_baseline": {"value": v, "unit": "member-cell-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "member-cell-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
+def run_gb300(args):
+    import torch
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    barrier(world)
+    from paper_2302_08341_gb300 import capi, synth
+    capi.lib()
+
+    terr, hy, rm, sc, cells = make_inputs()
+    n_win = args.warmup + args.steps
+    obs = truth_observations(capi, terr, hy, cells, max(n_win, args.steps))
+    stream = torch.cuda.current_stream(device)
+    ncell = NY * NX
+
+    g = capi.Grid(terr.z, terr.n)
+
+    def window(gr, w, d_dev, beta_dev, u, outs):
+        gr.advance_to(WINDOW * w, stream=stream)
+        gr.gauge_sample(cells, out=outs["y"], stream=stream)
+        gr.pf_assimilate(d_dev, 0.05, u, beta_dev, stream=stream, outputs=outs)
+
+    # device-resident per-window inputs (observations, perturbations)
+    d_all = [torch.tensor(o, dtype=torch.float64, device=device) for o in obs]
+    draws = [synth.pf_draws(SEED, w, M) for w in range(1, max(n_win, args.steps) + 1)]
+    beta_all = [torch.tensor(b, device=device) for _, b in draws]
+    outs = dict(weights=torch.zeros(M, dtype=torch.float64, device=device),
+                idx=torch.zeros(M, dtype=torch.int32, device=device),
+                neff=torch.zeros(1, dtype=torch.float64, device=device),
+                resampled=torch.zeros(1, dtype=torch.int32, device=device),
+                y=torch.zeros((M, G), dtype=torch.float32, device=device))
+
+    # warm-up windows
+    g.ensemble_init(M, rm, sc, hy, stream=stream)
+    for w in range(1, args.warmup + 1):
+        window(g, w, d_all[w - 1], beta_all[w - 1], draws[w - 1][0], outs)
+    torch.cuda.synchronize(device)
+
+    # timed windows from a fresh ensemble (the 1 h storm from t = 0)
+    g.ensemble_init(M, rm, sc, hy, stream=stream)
+    steps0 = g.members()["steps"].sum()
+    launches0 = g.launch_count
+    g.profile(True)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize(device)
+        start.record(stream)
+        for w in range(1, args.steps + 1):
+            window(g, w, d_all[w - 1], beta_all[w - 1], draws[w - 1][0], outs)
+        stop.record(stream)
+        torch.cuda.synchronize(device)
+        barrier(world)
+    ms = start.elapsed_time(stop)
+    kernel_ms, kernel_launches = g.profile(False)
+    gpu_launches = g.launch_count - launches0
+    units = float(g.members()["steps"].sum() - steps0) * ncell
+    member_steps = units / ncell
+    ms_max = max_over_ranks(ms, world, device)
+    units_all = sum_over_ranks(units, world, device)
+    value = units_all / (ms_max * 1e-3)
+
+    # roofline of the step kernel: algorithmic bytes / measured kernel time
+    hbm_peak, peak_kind = peaks()
+    achieved = member_steps * ncell * ALGO_BYTES / (kernel_ms * 1e-3) / 1e9
+    tpu = traffic_per_unit()
+    traffic = None if tpu is None else tpu * (member_steps / max(kernel_launches, 1)) * ncell
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": traffic,
+                "kernel": "step_kernel", "peak_kind": peak_kind,
+                "algorithmic_bytes_per_member_cell_step": ALGO_BYTES,
+                "kernel_ms_total": kernel_ms, "kernel_launches": kernel_launches,
+                "kernel_share_of_step": kernel_ms / ms if ms > 0 else None}
+
+    # end to end through the public API with host buffers (pinned), copies
+    # inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        h_d = [torch.tensor(o, dtype=torch.float64).pin_memory() for o in obs]
+        h_beta = [torch.tensor(b).pin_memory() for _, b in draws]
+        h_outs = dict(weights=torch.zeros(M, dtype=torch.float64).pin_memory(),
+                      idx=torch.zeros(M, dtype=torch.int32).pin_memory(),
+                      neff=torch.zeros(1, dtype=torch.float64).pin_memory(),
+                      resampled=torch.zeros(1, dtype=torch.int32).pin_memory(),
+                      y=torch.zeros((M, G), dtype=torch.float32).pin_memory())
+        g.ensemble_init(M, rm, sc, hy, stream=stream)
+        s0 = g.members()["steps"].sum()
+        barrier(world)
+        torch.cuda.synchronize(device)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for w in range(1, args.steps + 1):
+            window(g, w, h_d[w - 1], h_beta[w - 1], draws[w - 1][0], h_outs)
+            stream.synchronize()   # the host reads the window's result
+            _ = float(h_outs["neff"][0])
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        barrier(world)
+        e_ms = max_over_ranks(e0.elapsed_time(e1), world, device)
+        e_units = sum_over_ranks(float(g.members()["steps"].sum() - s0) * ncell, world, device)
+        e2e = {"value": e_units / (e_ms * 1e-3), "unit": "member-cell-steps/s",
+               "h2d_bytes_per_step": G * 8 + M * 4,
+               "d2h_bytes_per_step": M * 8 + M * 4 + 8 + 4 + M * G * 4}
+    g.close()
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(terr, hy, rm, sc)
+    line = {
+        "metric": "member-cell-steps/s", "value": value, "unit": "member-cell-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"ensemble flood + particle filter: {NY}x{NX} cells (3 m), "
+                               f"{M} members, 300 s assimilation windows, 1 h triangular storm",
+                   "cells": ncell, "members": M, "gauges": G, "window_s": WINDOW,
+                   "member_steps": member_steps, "parallelism": f"replicas{world}",
+                   "l2": "state 9.2 GB >> 129 MB L2 (no flush needed)"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * flood.h -- C ABI of libflood.so, the GB300 (sm_103a) ensemble
+ * local-inertial flood model with an on-device particle filter.
+ *
+ * Method: Wei et al., "Enable high-resolution, real-time ensemble simulation
+ * and data assimilation of flood inundation using distributed GPU
+ * parallelization" (arXiv 2302.08341).
+ *
+ * Conventions shared by every entry point
+ *  - Return value: FLOOD_OK (0) or a negative FLOOD_ERR_* code.  After an
+ *    error, flood_last_error(grid) returns a message (a static message for
+ *    errors raised before a grid exists: flood_last_error(NULL)).
+ *  - Grid: ny rows x nx columns of square cells of side dx.  Row-major
+ *    arrays [ny][nx]; flat cell index = r * nx + c.  x runs along columns,
+ *    y along rows.
+ *  - Links (the paper's Lx / Ly, Section 3.1): qx[r][c] is the flow per unit
+ *    width (m^2/s) on the link east of cell (r,c), positive toward +c;
+ *    qy[r][c] is the link south of cell (r,c), positive toward +r.  The west
+ *    and north edges are closed walls; qx[r][nx-1] / qy[ny-1][c] are the
+ *    east / south edge links (zero unless that edge is a free outflow).
+ *  - Pointers may be host or device memory (unified addressing decides);
+ *    inputs are copied during the call, so the caller keeps ownership.
+ *    Host outputs are complete when the call returns only for calls that
+ *    are documented as synchronous; otherwise they are valid once `stream`
+ *    has been synchronised.  Use page-locked host memory for overlap.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work of one
+ *    grid must be issued to one stream at a time.
+ *  - Precision: state (h, qx, qy) and fields are FP32; time, time step,
+ *    volume bookkeeping and particle weights are FP64.
+ *  - The library owns every device buffer it allocates; flood_destroy frees
+ *    them.
+ */
+#ifndef FLOOD_H
+#define FLOOD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    FLOOD_OK = 0,
+    FLOOD_ERR_ARG = -1,      /* invalid argument (size, pointer, range)        */
+    FLOOD_ERR_CUDA = -2,     /* a CUDA runtime call failed                     */
+    FLOOD_ERR_OOM = -3,      /* device allocation failed                       */
+    FLOOD_ERR_TIMEOUT = -4,  /* a bounded device wait gave up                  */
+    FLOOD_ERR_NAN = -5,      /* a kernel produced a non-finite depth           */
+    FLOOD_ERR_STATE = -6     /* call out of order (e.g. step before init)      */
+};
+
+typedef struct flood_grid flood_grid;
+
+/* Scheme constants (Section 2.1, Section 4.1). */
+typedef struct {
+    double dx;          /* cell size, dx = dy (m); the paper's case uses 3 m         */
+    double g;           /* gravitational acceleration, 9.81 m s^-2                   */
+    double alpha;       /* Courant coefficient k of Eq. 4 (0.2..0.7; default 0.7)    */
+    double dt_cap;      /* upper bound on the time step (s), default 1.0             */
+    double dt_fixed;    /* > 0: fixed time step (the paper ran 0.25 s), else Eq. 4   */
+    double h_eps;       /* links whose flow depth (Eq. 3) is <= h_eps carry no flow;
+                           default 0: Eq. 2-3 as printed (no flow only at zero
+                           flow depth).  A positive threshold makes FP32 and
+                           FP64 runs part where depths cross it               */
+    double h_floor;     /* floor on h_max inside Eq. 4 (m), default 1e-6             */
+    double rain_block;  /* rain is piecewise constant over blocks of this length (s),
+                           step (I) of Section 3.1: 300 s                          */
+    double edge_slope;  /* bed slope continued past a free-outflow edge             */
+    int32_t limiter;    /* 1: each link moves at most a quarter of the upstream
+                           cell's volume per step (keeps depths non-negative)       */
+    int32_t east_outflow;   /* 1: the east edge (c = nx-1) is a free outflow       */
+    int32_t south_outflow;  /* 1: the south edge (r = ny-1) is a free outflow      */
+    int32_t reserved;       /* must be 0                                           */
+} flood_params;
+
+/* Fill p with the defaults listed above (dx = 3, east free outflow). */
+void flood_default_params(flood_params* p);
+
+/* Message of the last error on grid g (or of the last error raised before a
+ * grid existed, when g is NULL).  The string is owned by the library. */
+const char* flood_last_error(const flood_grid* g);
+
+/*
+ * flood_create_grid -- the definitive (shared) data of the model: bed
+ * elevation z and base Manning n, both [ny][nx] FP32 (Section 3.2: stored
+ * once and shared by every member).  z should be referenced near 0 (its FP32
+ * spacing bounds depth resolution).  Synchronous.
+ * Errors: FLOOD_ERR_ARG for ny/nx < 1, NULL arrays, non-positive dx, g,
+ * dt_cap or rain_block; FLOOD_ERR_OOM; FLOOD_ERR_CUDA.
+ */
+int flood_create_grid(flood_grid** out, int ny, int nx, const float* z, const float* n_base,
+                      const flood_params* p);
+
+/* Release every device buffer of g.  Safe on NULL.  Synchronous. */
+int flood_destroy(flood_grid* g);
+
+/*
+ * flood_ensemble_init -- the initial ensemble (Eq. 6-7): N = n_members
+ * particles with equal weights 1/N, each with its own state, rainfall
+ * multiplier and Manning scale (the uncertain inputs, Section 4.1).
+ *   h0            NULL (dry start), [ny][nx] shared by all members
+ *                 (h0_per_member = 0) or [N][ny][nx] (h0_per_member = 1)
+ *   rain_mult     [N] multiplier on the hyetograph
+ *   manning_scale [N] multiplier on the base Manning field
+ *   hyetograph    [n_blocks] rain rate (m/s) of each block of rain_block s
+ *   t0            start time (s) of every member
+ * Link fluxes start at zero.  (Re)allocates the ensemble buffers.
+ * Synchronous.  Errors: FLOOD_ERR_ARG, FLOOD_ERR_OOM, FLOOD_ERR_CUDA.
+ */
+int flood_ensemble_init(flood_grid* g, int n_members, const float* h0, int h0_per_member,
+                        const float* rain_mult, const float* manning_scale,
+                        const float* hyetograph, int n_blocks, double t0, void* stream);
+
+/*
+ * flood_step -- evolve every member, x_{i,t+dt} = f(x_i, u_i, p_i) (Eq. 6),
+ * with the local-inertial scheme of Section 2.1: link fluxes from Eq. 2-3,
+ * then the continuity update of Eq. 5 and Eq. 1 with the block's rain, each
+ * member with its own time step from Eq. 4 (CFL on the member's own maximum
+ * depth), landing exactly on every rain-block edge and on t_end.
+ *   t_end < 0   issue exactly n_steps steps (asynchronous).
+ *   t_end >= 0  advance every member to t_end (members already there stay
+ *               put).  n_steps <= 0: no limit on steps, > 0: at most n_steps
+ *               steps.  Synchronises `stream` to follow the members' clocks.
+ * Errors: FLOOD_ERR_STATE before flood_ensemble_init, FLOOD_ERR_NAN if a
+ * depth became non-finite (detected at the synchronisation points),
+ * FLOOD_ERR_CUDA.
+ */
+int flood_step(flood_grid* g, int n_steps, double t_end, void* stream);
+
+/*
+ * flood_gauge_sample -- DA step (I) of Section 3.3: model output of every
+ * member at the gauges, y[i][k] = depth of member i at flat cell
+ * cell_idx[k].  y_out: [N][n_gauges] FP32 (host or device, may be NULL).
+ * The sample is also kept on the device as the default input of
+ * pf_assimilate.  Asynchronous.  Errors: FLOOD_ERR_ARG for a cell index out
+ * of range or n_gauges < 1.
+ */
+int flood_gauge_sample(flood_grid* g, int n_gauges, const int32_t* cell_idx, float* y_out,
+                       void* stream);
+
+/*
+ * pf_assimilate -- DA steps (II)-(V) of Section 3.3 on the device:
+ *   weights   w_i+ proportional to p(d|x_i) w_i- (Eq. 9-11) with the diagonal
+ *             Gaussian likelihood of Eq. 9 (sigma[k] absolute, or
+ *             sigma_rel * d[k] when sigma_rel > 0 as in Section 4.4), formed
+ *             in FP64 log-sum-exp;
+ *   N_eff     = 1 / sum w_i^2 (Eq. 12);
+ *   resample  if N_eff < n_thr_frac * N (Section 3.3 uses 0.8) or
+ *             force_resample: systematic resampling (Arulampalam et al. 2002)
+ *             with offsets (u + j)/N, u in [0,1) supplied by the caller;
+ *             survivors keep their slot, the extra copies of each particle
+ *             (in particle order) overwrite the dropped particles' slots (in
+ *             slot order); every member's rain multiplier is then multiplied
+ *             by beta[i] (Section 4.4: beta ~ N(1, 0.05^2), drawn by the
+ *             caller) and the weights reset to 1/N.
+ *   y            [N][n_gauges] FP32 model outputs or NULL = last gauge sample
+ *   d, sigma     [n_gauges] FP64 observations and their standard deviations
+ *   beta         [N] FP32 (only read when resampling)
+ *   weights_out  [N] FP64 posterior weights before any reset (or NULL)
+ *   idx_out      [N] int32 resampled particle indices, non-decreasing; the
+ *                identity 0..N-1 when no resampling happened (or NULL)
+ *   neff_out     N_eff, or 0 when every posterior weight underflowed to zero
+ *                (the ensemble is then left unchanged) (or NULL)
+ *   resampled_out 1 if the ensemble was resampled, else 0 (or NULL)
+ * Asynchronous (outputs valid after the stream is synchronised).
+ * Errors: FLOOD_ERR_ARG (sizes, u outside [0,1)), FLOOD_ERR_STATE.
+ */
+int pf_assimilate(flood_grid* g, int n_gauges, const float* y, const double* d,
+                  const double* sigma, double sigma_rel, double n_thr_frac, int force_resample,
+                  double u, const float* beta, double* weights_out, int32_t* idx_out,
+                  double* neff_out, int32_t* resampled_out, void* stream);
+
+/*
+ * pf_resample_systematic -- DA step (IV) alone: idx[j] = the particle whose
+ * cumulative-weight interval [c_{i-1}, c_i) holds (u + j)/n, with the
+ * cumulative sum taken in index order in FP64 and c_{n-1} set to 1.
+ * w: [n] FP64, idx: [n] int32 (host or device).  Asynchronous.
+ */
+int pf_resample_systematic(int n, const double* w, double u, int32_t* idx, void* stream);
+
+/* Copy member m's state out / in: h, qx, qy as [ny][nx] FP32 in the link
+ * convention above (any may be NULL).  Asynchronous. */
+int flood_get_state(flood_grid* g, int member, float* h, float* qx, float* qy, void* stream);
+int flood_set_state(flood_grid* g, int member, const float* h, const float* qx,
+                    const float* qy, void* stream);
+
+/* Per-member scalars, each [N] (any may be NULL): time (s), steps taken,
+ * rain multiplier, Manning scale, particle weight, maximum depth.
+ * Synchronous. */
+int flood_get_members(flood_grid* g, double* t, int64_t* steps, float* rain_mult,
+                      float* manning_scale, double* weights, float* hmax);
+
+/* Set per-member rain multipliers, Manning scales or weights (NULL = keep).
+ * Synchronous. */
+int flood_set_members(flood_grid* g, const float* rain_mult, const float* manning_scale,
+                      const double* weights);
+
+/*
+ * flood_volume_report -- FP64 volume bookkeeping per member (m^3), each [N]
+ * (any may be NULL): current storage sum(h) dx^2, rain added, volume that
+ * left through free-outflow edges, and volume added by clamping negative
+ * depths to zero.  Conservation: storage(t) - storage(t0) = rain - outflow
+ * + clamp up to FP32 rounding of the state.  Synchronous.
+ */
+int flood_volume_report(flood_grid* g, double* storage, double* rain, double* outflow,
+                        double* clamp);
+
+/* Number of kernels this grid has launched so far (for launch accounting). */
+int64_t flood_launch_count(const flood_grid* g);
+
+/* Per-launch timing of the step kernel with CUDA events recorded on the
+ * launching stream around every step launch.  Synchronises the device, writes
+ * the step-kernel time (ms) and launch count accumulated since the previous
+ * call (either pointer may be NULL), resets them, and turns timing on
+ * (enable = 1) or off (enable = 0). */
+int flood_profile(flood_grid* g, int enable, double* step_kernel_ms, int64_t* step_launches);
+
+/* Wait for `stream`, then report device-side faults of the method: returns
+ * FLOOD_ERR_NAN if any step produced a non-finite depth. */
+int flood_sync(flood_grid* g, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLOOD_H */

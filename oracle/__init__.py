@@ -128,8 +128,9 @@ def _i32(a):
 @dataclasses.dataclass
 class Params:
     """Scheme constants.  Defaults: g = 9.81, Courant k = 0.7 (Eq. 4),
-    step cap 1 s, wet/dry threshold 1 mm, rain blocks of 300 s (Section 3.1),
-    limiter on, free outflow through the east edge only."""
+    step cap 1 s, no flow only where the flow depth is zero (h_eps = 0),
+    rain blocks of 300 s (Section 3.1), limiter on, free outflow through the
+    east edge only."""
     ny: int
     nx: int
     dx: float = 3.0
@@ -137,7 +138,7 @@ class Params:
     alpha: float = 0.7
     dt_cap: float = 1.0
     dt_fixed: float = 0.0
-    h_eps: float = 1e-3
+    h_eps: float = 0.0
     h_floor: float = 1e-6
     rain_block: float = 300.0
     edge_slope: float = 0.005

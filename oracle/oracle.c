@@ -21,8 +21,9 @@
  * Readings of points the paper leaves open (each is listed in the design
  * notes): x runs along columns and y along rows; Eq. 1 is read as
  * dh = dt * dV / (dx dy) with dV the net volume flux of Eq. 5; the surface
- * slope in Eq. 2 is (eta_2 - eta_1)/dx along +axis; links whose flow depth is
- * <= h_eps carry no flow; each link is limited to a quarter of the upstream
+ * slope in Eq. 2 is (eta_2 - eta_1)/dx along +axis; a link carries no flow
+ * when its flow depth (Eq. 3) is zero (or below an optional threshold h_eps,
+ * default 0); each link is limited to a quarter of the upstream
  * cell's volume per step; free-outflow edges use a ghost cell one edge slope
  * lower with the edge cell's depth (normal-depth boundary) and pass outward
  * flow only; the west and north edges are walls.
@@ -46,7 +47,9 @@ typedef struct {
     double alpha;         /* Courant coefficient k of Eq. 4                  */
     double dt_cap;        /* upper bound on the time step (s)                */
     double dt_fixed;      /* > 0: use this fixed step instead of Eq. 4       */
-    double h_eps;         /* links with flow depth <= h_eps carry no flow (m)*/
+    double h_eps;         /* links with flow depth <= h_eps carry no flow (m);
+                             0 = Eq. 2-3 as printed: no flow only when the
+                             flow depth is zero                              */
     double h_floor;       /* floor on h_max inside Eq. 4 (m)                 */
     double rain_block;    /* length of one piecewise-constant rain block (s) */
     double edge_slope;    /* bed slope that places the outflow ghost cell    */
@@ -112,7 +115,9 @@ double orc_link_flux(const orc_params* p, double h1, double z1, double h2, doubl
     if (hflow <= p->h_eps) return 0.0;
     double S = (eta2 - eta1) / p->dx;                  /* water-surface slope */
     double num = q - p->g * hflow * dt * S;
-    double den = 1.0 + p->g * nl * nl * fabs(q) * dt / pow(hflow, 7.0 / 3.0);
+    /* friction term g n^2 |q_t| dt / h_flow^(7/3); exactly 0 when q_t = 0 */
+    double fric = q == 0.0 ? 0.0 : p->g * nl * nl * fabs(q) * dt / pow(hflow, 7.0 / 3.0);
+    double den = 1.0 + fric;
     double qn = num / den;                                          /* Eq. 2 */
     if (p->limiter) {
         double lim = (qn > 0.0 ? h1 : h2) * p->dx / (4.0 * dt);

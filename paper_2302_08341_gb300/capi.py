@@ -1,0 +1,301 @@
+"""ctypes binding of libflood.so (C ABI in include/flood.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Arrays may be numpy arrays (host memory) or torch tensors
+(host or device); streams may be a torch.cuda.Stream, a raw cudaStream_t
+integer, or None for torch's current stream.  There is no CPU fallback: if
+the library has not been built, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libflood.so")
+
+FLOOD_OK = 0
+ERRORS = {-1: "FLOOD_ERR_ARG", -2: "FLOOD_ERR_CUDA", -3: "FLOOD_ERR_OOM",
+          -4: "FLOOD_ERR_TIMEOUT", -5: "FLOOD_ERR_NAN", -6: "FLOOD_ERR_STATE"}
+
+EXPORTED = ["flood_default_params", "flood_last_error", "flood_create_grid", "flood_destroy",
+            "flood_ensemble_init", "flood_step", "flood_gauge_sample", "pf_assimilate",
+            "pf_resample_systematic", "flood_get_state", "flood_set_state", "flood_get_members",
+            "flood_set_members", "flood_volume_report", "flood_launch_count", "flood_sync",
+            "flood_profile"]
+
+
+class FloodError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    """flood_params (include/flood.h)."""
+    _fields_ = [("dx", C.c_double), ("g", C.c_double), ("alpha", C.c_double),
+                ("dt_cap", C.c_double), ("dt_fixed", C.c_double), ("h_eps", C.c_double),
+                ("h_floor", C.c_double), ("rain_block", C.c_double), ("edge_slope", C.c_double),
+                ("limiter", C.c_int32), ("east_outflow", C.c_int32), ("south_outflow", C.c_int32),
+                ("reserved", C.c_int32)]
+
+    @staticmethod
+    def default(**kw):
+        p = Params()
+        lib().flood_default_params(C.byref(p))
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise AttributeError(k)
+            setattr(p, k, v)
+        return p
+
+
+_lib = None
+_VP = C.c_void_p
+
+
+def lib(path: str = LIB_PATH):
+    """Load libflood.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libflood.so not found at {path}: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = C.CDLL(path)
+    L.flood_default_params.argtypes = [C.POINTER(Params)]
+    L.flood_default_params.restype = None
+    L.flood_last_error.argtypes = [_VP]
+    L.flood_last_error.restype = C.c_char_p
+    L.flood_create_grid.argtypes = [C.POINTER(_VP), C.c_int, C.c_int, _VP, _VP, C.POINTER(Params)]
+    L.flood_destroy.argtypes = [_VP]
+    L.flood_ensemble_init.argtypes = [_VP, C.c_int, _VP, C.c_int, _VP, _VP, _VP, C.c_int,
+                                      C.c_double, _VP]
+    L.flood_step.argtypes = [_VP, C.c_int, C.c_double, _VP]
+    L.flood_gauge_sample.argtypes = [_VP, C.c_int, _VP, _VP, _VP]
+    L.pf_assimilate.argtypes = [_VP, C.c_int, _VP, _VP, _VP, C.c_double, C.c_double, C.c_int,
+                                C.c_double, _VP, _VP, _VP, _VP, _VP, _VP]
+    L.pf_resample_systematic.argtypes = [C.c_int, _VP, C.c_double, _VP, _VP]
+    L.flood_get_state.argtypes = [_VP, C.c_int, _VP, _VP, _VP, _VP]
+    L.flood_set_state.argtypes = [_VP, C.c_int, _VP, _VP, _VP, _VP]
+    L.flood_get_members.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _VP]
+    L.flood_set_members.argtypes = [_VP, _VP, _VP, _VP]
+    L.flood_volume_report.argtypes = [_VP, _VP, _VP, _VP, _VP]
+    L.flood_launch_count.argtypes = [_VP]
+    L.flood_launch_count.restype = C.c_int64
+    L.flood_sync.argtypes = [_VP, _VP]
+    L.flood_profile.argtypes = [_VP, C.c_int, _VP, _VP]
+    for name in EXPORTED:
+        if name not in ("flood_default_params", "flood_last_error", "flood_launch_count"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def ptr(a):
+    """Raw pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _f32(a, shape=None):
+    if hasattr(a, "data_ptr"):
+        return a
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None and a.shape != tuple(shape):
+        a = a.reshape(shape)
+    return a
+
+
+def _check(rc, handle=None):
+    if rc != FLOOD_OK:
+        msg = lib().flood_last_error(handle)
+        raise FloodError(rc, msg.decode() if msg else "")
+
+
+def resample_systematic(w, u, stream=None):
+    """DA step (IV) on the device for given weights (FP64) and offset u."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    idx = np.zeros(len(w), dtype=np.int32)
+    s = stream_handle(stream)
+    _check(lib().pf_resample_systematic(len(w), ptr(w), float(u), ptr(idx), s))
+    _sync_stream(s)
+    return idx
+
+
+def _sync_stream(s):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            if s is None:
+                torch.cuda.synchronize()
+            else:
+                torch.cuda.ExternalStream(s).synchronize()
+    except ImportError:
+        pass
+
+
+class Grid:
+    """One terrain (bed z and base Manning n, shared by all members) and its
+    ensemble on the GPU."""
+
+    def __init__(self, z, n, params: Params | None = None):
+        L = lib()
+        self.params = params if params is not None else Params.default()
+        zz = _f32(z); nn = _f32(n)
+        ny, nx = (int(zz.shape[0]), int(zz.shape[1]))
+        self.ny, self.nx = ny, nx
+        h = _VP()
+        _check(L.flood_create_grid(C.byref(h), ny, nx, ptr(zz), ptr(nn), C.byref(self.params)))
+        self.h = h
+        self.M = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().flood_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- ensemble -------------------------------------------------------
+    def ensemble_init(self, M, rain_mult, scale, hyetograph, h0=None, t0=0.0, stream=None):
+        rm = _f32(rain_mult); sc = _f32(scale); hy = _f32(hyetograph)
+        per = 0
+        h0a = None
+        if h0 is not None:
+            h0a = _f32(h0)
+            per = 1 if len(h0a.shape) == 3 else 0
+        _check(lib().flood_ensemble_init(self.h, int(M), ptr(h0a), per, ptr(rm), ptr(sc), ptr(hy),
+                                         int(hy.shape[0]) if len(hy.shape) else 0, float(t0),
+                                         stream_handle(stream)), self.h)
+        self.M = int(M)
+
+    def step(self, n_steps=0, t_end=-1.0, stream=None):
+        _check(lib().flood_step(self.h, int(n_steps), float(t_end), stream_handle(stream)), self.h)
+
+    def advance_to(self, t_end, stream=None):
+        self.step(0, t_end, stream)
+
+    def sync(self, stream=None):
+        _check(lib().flood_sync(self.h, stream_handle(stream)), self.h)
+
+    def gauge_sample(self, cells, out=None, stream=None):
+        cells = np.ascontiguousarray(cells, dtype=np.int32)
+        y = out if out is not None else np.zeros((self.M, len(cells)), dtype=np.float32)
+        s = stream_handle(stream)
+        _check(lib().flood_gauge_sample(self.h, len(cells), ptr(cells), ptr(y), s), self.h)
+        if out is None:
+            _sync_stream(s)
+        return y
+
+    def pf_assimilate(self, d, sigma, u, beta, y=None, sigma_rel=0.0, n_thr_frac=0.8,
+                      force=False, stream=None, outputs=None):
+        """DA steps (II)-(V).  Returns a dict with weights, idx, neff,
+        resampled (host copies; the call synchronises the stream) unless
+        `outputs` supplies the destination buffers."""
+        G = int(d.shape[0]) if hasattr(d, "shape") else len(d)
+        if not hasattr(d, "data_ptr"):
+            d = np.ascontiguousarray(d, dtype=np.float64)
+        if sigma is None or hasattr(sigma, "data_ptr"):
+            sg = sigma
+        else:
+            sg = np.ascontiguousarray(np.broadcast_to(sigma, (G,)), dtype=np.float64)
+        beta = _f32(beta)
+        ya = None if y is None else _f32(y)
+        if outputs is None:
+            out = dict(weights=np.zeros(self.M), idx=np.zeros(self.M, dtype=np.int32),
+                       neff=np.zeros(1), resampled=np.zeros(1, dtype=np.int32))
+        else:
+            out = outputs
+        s = stream_handle(stream)
+        _check(lib().pf_assimilate(self.h, G, ptr(ya), ptr(d), ptr(sg), float(sigma_rel),
+                                   float(n_thr_frac), int(bool(force)), float(u), ptr(beta),
+                                   ptr(out["weights"]), ptr(out["idx"]), ptr(out["neff"]),
+                                   ptr(out["resampled"]), s), self.h)
+        if outputs is None:
+            _sync_stream(s)
+            return dict(weights=out["weights"], idx=out["idx"], neff=float(out["neff"][0]),
+                        resampled=bool(out["resampled"][0]))
+        return out
+
+    # ---- state access -----------------------------------------------------
+    def get_state(self, member, stream=None):
+        h = np.zeros((self.ny, self.nx), np.float32)
+        qx = np.zeros_like(h); qy = np.zeros_like(h)
+        s = stream_handle(stream)
+        _check(lib().flood_get_state(self.h, int(member), ptr(h), ptr(qx), ptr(qy), s), self.h)
+        _sync_stream(s)
+        return h, qx, qy
+
+    def set_state(self, member, h=None, qx=None, qy=None, stream=None):
+        a = [None if v is None else _f32(v, (self.ny, self.nx)) for v in (h, qx, qy)]
+        _check(lib().flood_set_state(self.h, int(member), ptr(a[0]), ptr(a[1]), ptr(a[2]),
+                                     stream_handle(stream)), self.h)
+
+    def members(self):
+        M = self.M
+        out = dict(t=np.zeros(M), steps=np.zeros(M, np.int64), rain_mult=np.zeros(M, np.float32),
+                   scale=np.zeros(M, np.float32), weights=np.zeros(M), hmax=np.zeros(M, np.float32))
+        _check(lib().flood_get_members(self.h, ptr(out["t"]), ptr(out["steps"]),
+                                       ptr(out["rain_mult"]), ptr(out["scale"]),
+                                       ptr(out["weights"]), ptr(out["hmax"])), self.h)
+        return out
+
+    def set_members(self, rain_mult=None, scale=None, weights=None):
+        rm = None if rain_mult is None else _f32(rain_mult)
+        sc = None if scale is None else _f32(scale)
+        w = None if weights is None else np.ascontiguousarray(weights, np.float64)
+        _check(lib().flood_set_members(self.h, ptr(rm), ptr(sc), ptr(w)), self.h)
+
+    def volumes(self):
+        M = self.M
+        out = dict(storage=np.zeros(M), rain=np.zeros(M), outflow=np.zeros(M), clamp=np.zeros(M))
+        _check(lib().flood_volume_report(self.h, ptr(out["storage"]), ptr(out["rain"]),
+                                         ptr(out["outflow"]), ptr(out["clamp"])), self.h)
+        return out
+
+    def profile(self, enable=True):
+        """Turn per-launch step-kernel timing on/off; returns (ms, launches)
+        accumulated since the previous call."""
+        ms = C.c_double(); n = C.c_int64()
+        _check(lib().flood_profile(self.h, int(bool(enable)), C.byref(ms), C.byref(n)), self.h)
+        return ms.value, n.value
+
+    @property
+    def launch_count(self):
+        return int(lib().flood_launch_count(self.h))

@@ -1,0 +1,667 @@
+// Host side of the C ABI declared in include/flood.h: argument checks,
+// device buffers, the step driver (per-member clocks, landing on t_end) and
+// the particle-filter sequence.  Every step of the method runs in the
+// kernels of step_kernel.cu and pf_kernels.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "flood_internal.cuh"
+#include "pf_kernels.cuh"
+
+using flood::MemberClock;
+
+struct flood_grid {
+    int ny = 0, nx = 0, ld = 0;
+    size_t plane = 0;
+    flood_params p{};
+    float* z = nullptr;
+    float* n = nullptr;
+    int n_sm = 0;
+    // ensemble
+    int M = 0, nb = 0;
+    float* state = nullptr;       // [2][M][3][plane]
+    float* rain_mult = nullptr;   // [M]
+    float* scale = nullptr;       // [M]
+    float* hyeto = nullptr;       // [nb]
+    double* w = nullptr;          // [M]
+    double* w_post = nullptr;     // [M]
+    MemberClock* ms = nullptr;    // [3][M]
+    double* vacc = nullptr;       // [M][nslot][2]
+    int nslot = 0;
+    double* rain_acc = nullptr;   // [M]
+    int* err = nullptr;           // device error word
+    int rows_per_strip = 64;
+    // particle filter
+    int G = 0, G_cap = 0;
+    int32_t* cells = nullptr;     // [G_cap]
+    float* y = nullptr;           // [M][G_cap] last gauge sample
+    float* y_in = nullptr;        // [M][G_cap] caller-supplied outputs
+    double* d = nullptr;          // [G_cap]
+    double* sigma = nullptr;      // [G_cap]
+    float* beta = nullptr;        // [M]
+    int32_t* pfi = nullptr;       // idx, src, cnt, copy_dst, copy_src: 5 x [M]
+    int32_t* pf_small = nullptr;  // n_copy, resampled, status
+    double* neff = nullptr;       // [1]
+    double* part = nullptr;       // storage partials
+    int part_cap = 0;
+    double* storage = nullptr;    // [M]
+    int64_t k = 0;                // step launches so far (member-slot rotation)
+    int64_t launches = 0;         // all kernel launches
+    // optional per-launch timing of the step kernel (CUDA events on the
+    // launching stream)
+    bool profile = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free;
+    double prof_ms = 0.0;
+    int64_t prof_launches = 0;
+    std::string msg;
+};
+
+namespace {
+
+thread_local std::string g_static_msg;
+
+int fail(flood_grid* g, int code, const std::string& m)
+{
+    if (g) g->msg = m; else g_static_msg = m;
+    return code;
+}
+
+#define CK(g, call)                                                                          \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail((g), e_ == cudaErrorMemoryAllocation ? FLOOD_ERR_OOM : FLOOD_ERR_CUDA, \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+    } while (0)
+
+template <class T>
+int dalloc(flood_grid* g, T** p, size_t count)
+{
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    if (count == 0) count = 1;
+    CK(g, cudaMalloc((void**)p, sizeof(T) * count));
+    return FLOOD_OK;
+}
+
+void dfree(void* p)
+{
+    if (p) cudaFree(p);
+}
+
+void free_ensemble(flood_grid* g)
+{
+    dfree(g->state); dfree(g->rain_mult); dfree(g->scale); dfree(g->hyeto); dfree(g->w);
+    dfree(g->w_post); dfree(g->ms); dfree(g->vacc); dfree(g->rain_acc); dfree(g->y);
+    dfree(g->y_in); dfree(g->beta); dfree(g->pfi); dfree(g->pf_small); dfree(g->neff);
+    dfree(g->part); dfree(g->storage); dfree(g->cells); dfree(g->d); dfree(g->sigma);
+    g->state = nullptr; g->rain_mult = nullptr; g->scale = nullptr; g->hyeto = nullptr;
+    g->w = nullptr; g->w_post = nullptr; g->ms = nullptr; g->vacc = nullptr;
+    g->rain_acc = nullptr; g->y = nullptr; g->y_in = nullptr; g->beta = nullptr;
+    g->pfi = nullptr; g->pf_small = nullptr; g->neff = nullptr; g->part = nullptr;
+    g->storage = nullptr; g->cells = nullptr; g->d = nullptr; g->sigma = nullptr;
+    g->M = 0; g->G = 0; g->G_cap = 0;
+}
+
+cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+flood::StepArgs step_args(const flood_grid* g, double t_end)
+{
+    flood::StepArgs a{};
+    a.state = g->state;
+    a.z = g->z;
+    a.n = g->n;
+    a.rain_mult = g->rain_mult;
+    a.scale = g->scale;
+    a.hyeto = g->hyeto;
+    const int64_t k = g->k;
+    a.ms_in = g->ms + (k % 3) * g->M;
+    a.ms_out = g->ms + ((k + 1) % 3) * g->M;
+    a.ms_clr = g->ms + ((k + 2) % 3) * g->M;
+    a.vacc = g->vacc;
+    a.rain_acc = g->rain_acc;
+    a.dt_log = nullptr;
+    a.err = g->err;
+    a.plane = g->plane;
+    a.ny = g->ny; a.nx = g->nx; a.ld = g->ld; a.M = g->M; a.nb = g->nb;
+    a.rows_per_strip = g->rows_per_strip;
+    a.nslot = g->nslot;
+    a.dt_log_cap = 0;
+    a.t_end = t_end;
+    a.alpha_dx = g->p.alpha * g->p.dx;
+    a.g = g->p.g;
+    a.dt_cap = g->p.dt_cap;
+    a.dt_fixed = g->p.dt_fixed;
+    a.h_floor = g->p.h_floor;
+    a.rain_block = g->p.rain_block;
+    a.dxd = g->p.dx;
+    a.cell_area = g->p.dx * g->p.dx;
+    a.ncell = (double)g->ny * (double)g->nx;
+    a.dx = (float)g->p.dx;
+    a.h_eps = (float)g->p.h_eps;
+    a.edge_drop = (float)(g->p.edge_slope * g->p.dx);
+    a.limiter = g->p.limiter;
+    a.east_out = g->p.east_outflow;
+    a.south_out = g->p.south_outflow;
+    return a;
+}
+
+// Fold finished timing pairs into the totals (after a synchronisation).
+void collect_profile(flood_grid* g)
+{
+    for (auto& p : g->ev_pending) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) {
+            g->prof_ms += ms;
+            g->prof_launches++;
+        }
+        g->ev_free.push_back(p);
+    }
+    g->ev_pending.clear();
+}
+
+int launch_steps(flood_grid* g, int64_t count, double t_end, cudaStream_t s)
+{
+    for (int64_t i = 0; i < count; ++i) {
+        flood::StepArgs a = step_args(g, t_end);
+        std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+        if (g->profile) {
+            if (g->ev_free.empty()) {
+                CK(g, cudaEventCreate(&ev.first));
+                CK(g, cudaEventCreate(&ev.second));
+            } else {
+                ev = g->ev_free.back();
+                g->ev_free.pop_back();
+            }
+            CK(g, cudaEventRecord(ev.first, s));
+        }
+        flood::launch_step(a, g->M >= 4 ? 0 : 1, s);
+        if (g->profile) {
+            CK(g, cudaEventRecord(ev.second, s));
+            g->ev_pending.push_back(ev);
+        }
+        g->k++;
+        g->launches++;
+    }
+    CK(g, cudaGetLastError());
+    return FLOOD_OK;
+}
+
+int read_clocks(flood_grid* g, std::vector<MemberClock>& out, cudaStream_t s)
+{
+    out.resize(g->M);
+    CK(g, cudaMemcpyAsync(out.data(), g->ms + (g->k % 3) * g->M, sizeof(MemberClock) * g->M,
+                          cudaMemcpyDeviceToHost, s));
+    CK(g, cudaStreamSynchronize(s));
+    collect_profile(g);
+    int err = 0;
+    CK(g, cudaMemcpy(&err, g->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) return fail(g, FLOOD_ERR_NAN, "a kernel produced a non-finite depth");
+    return FLOOD_OK;
+}
+
+int choose_rows_per_strip(int ny, int nx, int M, int n_sm)
+{
+    const int spans = (nx + 127) / 128;
+    int rh = 64;
+    while (rh > 4 && (int64_t)M * spans * ((ny + rh - 1) / rh) < (int64_t)n_sm * 32) rh /= 2;
+    return rh;
+}
+
+}  // namespace
+
+extern "C" {
+
+void flood_default_params(flood_params* p)
+{
+    if (!p) return;
+    p->dx = 3.0;
+    p->g = 9.81;
+    p->alpha = 0.7;
+    p->dt_cap = 1.0;
+    p->dt_fixed = 0.0;
+    p->h_eps = 0.0;
+    p->h_floor = 1e-6;
+    p->rain_block = 300.0;
+    p->edge_slope = 0.005;
+    p->limiter = 1;
+    p->east_outflow = 1;
+    p->south_outflow = 0;
+    p->reserved = 0;
+}
+
+const char* flood_last_error(const flood_grid* g)
+{
+    return g ? g->msg.c_str() : g_static_msg.c_str();
+}
+
+int flood_create_grid(flood_grid** out, int ny, int nx, const float* z, const float* n_base,
+                      const flood_params* p)
+{
+    if (!out) return fail(nullptr, FLOOD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (ny < 1 || nx < 1) return fail(nullptr, FLOOD_ERR_ARG, "ny and nx must be >= 1");
+    if ((int64_t)ny * nx > (int64_t)1 << 31) return fail(nullptr, FLOOD_ERR_ARG, "grid too large");
+    if (!z || !n_base || !p) return fail(nullptr, FLOOD_ERR_ARG, "z, n_base and p are required");
+    if (!(p->dx > 0) || !(p->g > 0) || !(p->dt_cap > 0) || !(p->rain_block > 0) ||
+        !(p->alpha > 0) || p->dt_fixed < 0 || p->h_eps < 0 || p->reserved != 0)
+        return fail(nullptr, FLOOD_ERR_ARG, "invalid flood_params");
+    flood_grid* g = new flood_grid();
+    g->ny = ny;
+    g->nx = nx;
+    g->ld = (nx + 31) / 32 * 32;
+    g->plane = (size_t)ny * g->ld;
+    g->p = *p;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g->n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (g->n_sm <= 0) g->n_sm = 1;
+    int rc;
+    if ((rc = dalloc(g, &g->z, g->plane)) || (rc = dalloc(g, &g->n, g->plane)) ||
+        (rc = dalloc(g, &g->err, 1))) {
+        g_static_msg = g->msg;
+        flood_destroy(g);
+        return rc;
+    }
+    cudaError_t e = cudaMemset(g->z, 0, sizeof(float) * g->plane);
+    if (e == cudaSuccess) e = cudaMemset(g->n, 0, sizeof(float) * g->plane);
+    if (e == cudaSuccess) e = cudaMemset(g->err, 0, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemcpy2D(g->z, sizeof(float) * g->ld, z, sizeof(float) * nx, sizeof(float) * nx, ny,
+                         cudaMemcpyDefault);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2D(g->n, sizeof(float) * g->ld, n_base, sizeof(float) * nx,
+                         sizeof(float) * nx, ny, cudaMemcpyDefault);
+    if (e != cudaSuccess) {
+        fail(nullptr, FLOOD_ERR_CUDA, std::string("flood_create_grid: ") + cudaGetErrorString(e));
+        flood_destroy(g);
+        return FLOOD_ERR_CUDA;
+    }
+    *out = g;
+    return FLOOD_OK;
+}
+
+int flood_destroy(flood_grid* g)
+{
+    if (!g) return FLOOD_OK;
+    cudaDeviceSynchronize();
+    collect_profile(g);
+    for (auto& p : g->ev_free) {
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+    }
+    free_ensemble(g);
+    dfree(g->z);
+    dfree(g->n);
+    dfree(g->err);
+    delete g;
+    return FLOOD_OK;
+}
+
+int flood_ensemble_init(flood_grid* g, int M, const float* h0, int h0_per_member,
+                        const float* rain_mult, const float* manning_scale,
+                        const float* hyetograph, int n_blocks, double t0, void* stream)
+{
+    if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    if (M < 1) return fail(g, FLOOD_ERR_ARG, "n_members must be >= 1");
+    if (!rain_mult || !manning_scale) return fail(g, FLOOD_ERR_ARG, "rain_mult and manning_scale are required");
+    if (n_blocks < 0 || (n_blocks > 0 && !hyetograph)) return fail(g, FLOOD_ERR_ARG, "bad hyetograph");
+    if (!(t0 >= 0.0)) return fail(g, FLOOD_ERR_ARG, "t0 must be >= 0");
+    cudaStream_t s = S(stream);
+    CK(g, cudaStreamSynchronize(s));
+    free_ensemble(g);
+    g->M = M;
+    g->nb = n_blocks;
+    g->rows_per_strip = choose_rows_per_strip(g->ny, g->nx, M, g->n_sm);
+    g->nslot = flood::step_nslot(g->ny, g->nx, g->rows_per_strip);
+    g->part_cap = (g->ny + 15) / 16;
+    int rc;
+    if ((rc = dalloc(g, &g->state, (size_t)2 * M * 3 * g->plane)) ||
+        (rc = dalloc(g, &g->rain_mult, M)) || (rc = dalloc(g, &g->scale, M)) ||
+        (rc = dalloc(g, &g->hyeto, n_blocks)) || (rc = dalloc(g, &g->w, M)) ||
+        (rc = dalloc(g, &g->w_post, M)) || (rc = dalloc(g, &g->ms, (size_t)3 * M)) ||
+        (rc = dalloc(g, &g->vacc, (size_t)M * g->nslot * 2)) || (rc = dalloc(g, &g->rain_acc, M)) ||
+        (rc = dalloc(g, &g->beta, M)) || (rc = dalloc(g, &g->pfi, (size_t)5 * M)) ||
+        (rc = dalloc(g, &g->pf_small, 4)) || (rc = dalloc(g, &g->neff, 1)) ||
+        (rc = dalloc(g, &g->part, (size_t)M * g->part_cap)) || (rc = dalloc(g, &g->storage, M))) {
+        free_ensemble(g);
+        return rc;
+    }
+    CK(g, cudaMemsetAsync(g->state, 0, sizeof(float) * 2 * (size_t)M * 3 * g->plane, s));
+    if (h0) {
+        for (int m = 0; m < M; ++m) {
+            const float* src = h0 + (h0_per_member ? (size_t)m * g->ny * g->nx : 0);
+            CK(g, cudaMemcpy2DAsync(g->state + (size_t)m * 3 * g->plane, sizeof(float) * g->ld, src,
+                                    sizeof(float) * g->nx, sizeof(float) * g->nx, g->ny,
+                                    cudaMemcpyDefault, s));
+        }
+    }
+    CK(g, cudaMemcpyAsync(g->rain_mult, rain_mult, sizeof(float) * M, cudaMemcpyDefault, s));
+    CK(g, cudaMemcpyAsync(g->scale, manning_scale, sizeof(float) * M, cudaMemcpyDefault, s));
+    if (n_blocks > 0)
+        CK(g, cudaMemcpyAsync(g->hyeto, hyetograph, sizeof(float) * n_blocks, cudaMemcpyDefault, s));
+    std::vector<double> w(M, 1.0 / M);
+    CK(g, cudaMemcpyAsync(g->w, w.data(), sizeof(double) * M, cudaMemcpyHostToDevice, s));
+    std::vector<MemberClock> ms((size_t)3 * M);
+    for (auto& c : ms) { c.t = t0; c.steps = 0; c.hmax_bits = 0; c.cur = 0; }
+    CK(g, cudaMemcpyAsync(g->ms, ms.data(), sizeof(MemberClock) * 3 * M, cudaMemcpyHostToDevice, s));
+    CK(g, cudaMemsetAsync(g->vacc, 0, sizeof(double) * M * g->nslot * 2, s));
+    CK(g, cudaMemsetAsync(g->rain_acc, 0, sizeof(double) * M, s));
+    CK(g, cudaMemsetAsync(g->err, 0, sizeof(int), s));
+    g->k = 0;
+    flood::launch_hmax(g->state, g->ms, M, g->ny, g->nx, g->ld, g->plane, g->n_sm, s);
+    g->launches++;
+    CK(g, cudaGetLastError());
+    CK(g, cudaStreamSynchronize(s));
+    return FLOOD_OK;
+}
+
+int flood_step(flood_grid* g, int n_steps, double t_end, void* stream)
+{
+    if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    if (g->M == 0) return fail(g, FLOOD_ERR_STATE, "flood_ensemble_init has not been called");
+    cudaStream_t s = S(stream);
+    if (t_end < 0.0) {
+        if (n_steps < 0) return fail(g, FLOOD_ERR_ARG, "n_steps must be >= 0");
+        return launch_steps(g, n_steps, -1.0, s);
+    }
+    int64_t done = 0;
+    std::vector<MemberClock> c;
+    double last_tmin = -1.0;
+    for (int rounds = 0;; ++rounds) {
+        int rc = read_clocks(g, c, s);
+        if (rc) return rc;
+        double tmin = t_end;
+        for (int m = 0; m < g->M; ++m) tmin = std::min(tmin, c[m].t);
+        if (rounds > 0 && tmin < t_end && !(tmin > last_tmin))
+            return fail(g, FLOOD_ERR_STATE, "members stopped advancing toward t_end");
+        last_tmin = tmin;
+        int64_t need = 0;
+        for (int m = 0; m < g->M; ++m) {
+            if (c[m].t >= t_end) continue;
+            double dt;
+            if (g->p.dt_fixed > 0) {
+                dt = g->p.dt_fixed;
+            } else {
+                float hf;
+                std::memcpy(&hf, &c[m].hmax_bits, sizeof(hf));
+                double hm = std::max((double)hf, g->p.h_floor);
+                dt = std::min(g->p.alpha * g->p.dx / std::sqrt(g->p.g * hm), g->p.dt_cap);
+            }
+            const double rb = g->p.rain_block;
+            const int64_t edges = (int64_t)std::floor(t_end / rb) - (int64_t)std::floor(c[m].t / rb) + 1;
+            need = std::max(need, (int64_t)std::ceil((t_end - c[m].t) / dt) + edges);
+        }
+        if (need == 0) break;
+        if (n_steps > 0) need = std::min<int64_t>(need, n_steps - done);
+        if (need <= 0) break;
+        if ((rc = launch_steps(g, need, t_end, s))) return rc;
+        done += need;
+    }
+    return FLOOD_OK;
+}
+
+int flood_gauge_sample(flood_grid* g, int G, const int32_t* cell_idx, float* y_out, void* stream)
+{
+    if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    if (g->M == 0) return fail(g, FLOOD_ERR_STATE, "flood_ensemble_init has not been called");
+    if (G < 1 || !cell_idx) return fail(g, FLOOD_ERR_ARG, "need n_gauges >= 1 and cell_idx");
+    cudaStream_t s = S(stream);
+    std::vector<int32_t> cells(G);
+    CK(g, cudaMemcpy(cells.data(), cell_idx, sizeof(int32_t) * G, cudaMemcpyDefault));
+    for (int k = 0; k < G; ++k)
+        if (cells[k] < 0 || (int64_t)cells[k] >= (int64_t)g->ny * g->nx)
+            return fail(g, FLOOD_ERR_ARG, "gauge cell index out of range");
+    if (G > g->G_cap) {
+        int rc;
+        if ((rc = dalloc(g, &g->cells, G)) || (rc = dalloc(g, &g->y, (size_t)g->M * G)) ||
+            (rc = dalloc(g, &g->y_in, (size_t)g->M * G)) || (rc = dalloc(g, &g->d, G)) ||
+            (rc = dalloc(g, &g->sigma, G)))
+            return rc;
+        g->G_cap = G;
+    }
+    g->G = G;
+    CK(g, cudaMemcpyAsync(g->cells, cells.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, s));
+    flood::launch_gauge(g->state, g->ms + (g->k % 3) * g->M, g->cells, G, g->M, g->ld, g->nx,
+                        g->plane, g->y, s);
+    g->launches++;
+    CK(g, cudaGetLastError());
+    if (y_out)
+        CK(g, cudaMemcpyAsync(y_out, g->y, sizeof(float) * g->M * G, cudaMemcpyDefault, s));
+    return FLOOD_OK;
+}
+
+int pf_assimilate(flood_grid* g, int G, const float* y, const double* d, const double* sigma,
+                  double sigma_rel, double n_thr_frac, int force_resample, double u,
+                  const float* beta, double* weights_out, int32_t* idx_out, double* neff_out,
+                  int32_t* resampled_out, void* stream)
+{
+    if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    if (g->M == 0) return fail(g, FLOOD_ERR_STATE, "flood_ensemble_init has not been called");
+    if (G < 1 || !d || (!sigma && !(sigma_rel > 0)) || !beta)
+        return fail(g, FLOOD_ERR_ARG, "need n_gauges >= 1, d, sigma (or sigma_rel) and beta");
+    if (!(u >= 0.0 && u < 1.0)) return fail(g, FLOOD_ERR_ARG, "u must lie in [0, 1)");
+    cudaStream_t s = S(stream);
+    if (!y && G != g->G)
+        return fail(g, FLOOD_ERR_STATE, "y is NULL but no gauge sample of this size exists");
+    if (G > g->G_cap) {
+        int rc;
+        if ((rc = dalloc(g, &g->y, (size_t)g->M * G)) ||
+            (rc = dalloc(g, &g->y_in, (size_t)g->M * G)) || (rc = dalloc(g, &g->d, G)) ||
+            (rc = dalloc(g, &g->sigma, G)) || (rc = dalloc(g, &g->cells, G)))
+            return rc;
+        g->G_cap = G;
+        g->G = 0;
+    }
+    const float* ydev = g->y;
+    if (y) {
+        CK(g, cudaMemcpyAsync(g->y_in, y, sizeof(float) * g->M * G, cudaMemcpyDefault, s));
+        ydev = g->y_in;
+    }
+    CK(g, cudaMemcpyAsync(g->d, d, sizeof(double) * G, cudaMemcpyDefault, s));
+    if (sigma) CK(g, cudaMemcpyAsync(g->sigma, sigma, sizeof(double) * G, cudaMemcpyDefault, s));
+    CK(g, cudaMemcpyAsync(g->beta, beta, sizeof(float) * g->M, cudaMemcpyDefault, s));
+    const int M = g->M;
+    flood::PfArgs a{};
+    a.y = ydev;
+    a.d = g->d;
+    a.sigma = g->sigma;
+    a.sigma_rel = sigma_rel;
+    a.n_thr_frac = n_thr_frac;
+    a.force = force_resample;
+    a.u = u;
+    a.beta = g->beta;
+    a.w = g->w;
+    a.w_post = g->w_post;
+    a.neff = g->neff;
+    a.n_copy = g->pf_small;
+    a.resampled = g->pf_small + 1;
+    a.status = g->pf_small + 2;
+    a.idx = g->pfi;
+    a.src = g->pfi + M;
+    a.cnt = g->pfi + 2 * M;
+    a.copy_dst = g->pfi + 3 * M;
+    a.copy_src = g->pfi + 4 * M;
+    a.rain_mult = g->rain_mult;
+    a.scale = g->scale;
+    a.ms = g->ms + (g->k % 3) * M;
+    a.M = M;
+    a.G = G;
+    flood::launch_pf(a, s);
+    flood::launch_copy(g->state, a.ms, a.n_copy, a.copy_dst, a.copy_src, M, g->plane, g->n_sm, s);
+    g->launches += 2;
+    CK(g, cudaGetLastError());
+    if (weights_out) CK(g, cudaMemcpyAsync(weights_out, g->w_post, sizeof(double) * M, cudaMemcpyDefault, s));
+    if (idx_out) CK(g, cudaMemcpyAsync(idx_out, a.idx, sizeof(int32_t) * M, cudaMemcpyDefault, s));
+    if (neff_out) CK(g, cudaMemcpyAsync(neff_out, g->neff, sizeof(double), cudaMemcpyDefault, s));
+    if (resampled_out)
+        CK(g, cudaMemcpyAsync(resampled_out, a.resampled, sizeof(int32_t), cudaMemcpyDefault, s));
+    return FLOOD_OK;
+}
+
+int pf_resample_systematic(int n, const double* w, double u, int32_t* idx, void* stream)
+{
+    if (n < 1 || !w || !idx) return fail(nullptr, FLOOD_ERR_ARG, "need n >= 1, w and idx");
+    if (!(u >= 0.0 && u < 1.0)) return fail(nullptr, FLOOD_ERR_ARG, "u must lie in [0, 1)");
+    cudaStream_t s = S(stream);
+    double* dw = nullptr;
+    int32_t* di = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&dw, sizeof(double) * n, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&di, sizeof(int32_t) * n, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dw, w, sizeof(double) * n, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) {
+        flood::launch_resample(n, dw, u, di, s);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(idx, di, sizeof(int32_t) * n, cudaMemcpyDefault, s);
+    if (dw) cudaFreeAsync(dw, s);
+    if (di) cudaFreeAsync(di, s);
+    if (e != cudaSuccess)
+        return fail(nullptr, FLOOD_ERR_CUDA, std::string("pf_resample_systematic: ") + cudaGetErrorString(e));
+    return FLOOD_OK;
+}
+
+int flood_get_state(flood_grid* g, int member, float* h, float* qx, float* qy, void* stream)
+{
+    if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    if (g->M == 0) return fail(g, FLOOD_ERR_STATE, "flood_ensemble_init has not been called");
+    if (member < 0 || member >= g->M) return fail(g, FLOOD_ERR_ARG, "member out of range");
+    cudaStream_t s = S(stream);
+    MemberClock c;
+    CK(g, cudaMemcpyAsync(&c, g->ms + (g->k % 3) * g->M + member, sizeof(c), cudaMemcpyDeviceToHost, s));
+    CK(g, cudaStreamSynchronize(s));
+    const float* base = g->state + (size_t)(c.cur * g->M + member) * 3 * g->plane;
+    float* outs[3] = {h, qx, qy};
+    for (int k = 0; k < 3; ++k)
+        if (outs[k])
+            CK(g, cudaMemcpy2DAsync(outs[k], sizeof(float) * g->nx, base + k * g->plane,
+                                    sizeof(float) * g->ld, sizeof(float) * g->nx, g->ny,
+                                    cudaMemcpyDefault, s));
+    return FLOOD_OK;
+}
+
+int flood_set_state(flood_grid* g, int member, const float* h, const float* qx, const float* qy,
+                    void* stream)
+{
+    if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    if (g->M == 0) return fail(g, FLOOD_ERR_STATE, "flood_ensemble_init has not been called");
+    if (member < 0 || member >= g->M) return fail(g, FLOOD_ERR_ARG, "member out of range");
+    cudaStream_t s = S(stream);
+    MemberClock* slot = g->ms + (g->k % 3) * g->M + member;
+    MemberClock c;
+    CK(g, cudaMemcpyAsync(&c, slot, sizeof(c), cudaMemcpyDeviceToHost, s));
+    CK(g, cudaStreamSynchronize(s));
+    float* base = g->state + (size_t)(c.cur * g->M + member) * 3 * g->plane;
+    const float* ins[3] = {h, qx, qy};
+    for (int k = 0; k < 3; ++k)
+        if (ins[k])
+            CK(g, cudaMemcpy2DAsync(base + k * g->plane, sizeof(float) * g->ld, ins[k],
+                                    sizeof(float) * g->nx, sizeof(float) * g->nx, g->ny,
+                                    cudaMemcpyDefault, s));
+    if (h) {  // refresh the member's maximum depth (input of Eq. 4)
+        CK(g, cudaMemsetAsync(&slot->hmax_bits, 0, sizeof(uint32_t), s));
+        flood::launch_hmax(g->state, g->ms + (g->k % 3) * g->M, g->M, g->ny, g->nx, g->ld, g->plane,
+                           g->n_sm, s);
+        g->launches++;
+    }
+    CK(g, cudaGetLastError());
+    CK(g, cudaStreamSynchronize(s));
+    return FLOOD_OK;
+}
+
+int flood_get_members(flood_grid* g, double* t, int64_t* steps, float* rain_mult,
+                      float* manning_scale, double* weights, float* hmax)
+{
+    if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    if (g->M == 0) return fail(g, FLOOD_ERR_STATE, "flood_ensemble_init has not been called");
+    const int M = g->M;
+    CK(g, cudaDeviceSynchronize());
+    std::vector<MemberClock> c(M);
+    CK(g, cudaMemcpy(c.data(), g->ms + (g->k % 3) * M, sizeof(MemberClock) * M, cudaMemcpyDeviceToHost));
+    for (int m = 0; m < M; ++m) {
+        if (t) t[m] = c[m].t;
+        if (steps) steps[m] = c[m].steps;
+        if (hmax) std::memcpy(&hmax[m], &c[m].hmax_bits, sizeof(float));
+    }
+    if (rain_mult) CK(g, cudaMemcpy(rain_mult, g->rain_mult, sizeof(float) * M, cudaMemcpyDefault));
+    if (manning_scale) CK(g, cudaMemcpy(manning_scale, g->scale, sizeof(float) * M, cudaMemcpyDefault));
+    if (weights) CK(g, cudaMemcpy(weights, g->w, sizeof(double) * M, cudaMemcpyDefault));
+    return FLOOD_OK;
+}
+
+int flood_set_members(flood_grid* g, const float* rain_mult, const float* manning_scale,
+                      const double* weights)
+{
+    if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    if (g->M == 0) return fail(g, FLOOD_ERR_STATE, "flood_ensemble_init has not been called");
+    const int M = g->M;
+    CK(g, cudaDeviceSynchronize());
+    if (rain_mult) CK(g, cudaMemcpy(g->rain_mult, rain_mult, sizeof(float) * M, cudaMemcpyDefault));
+    if (manning_scale) CK(g, cudaMemcpy(g->scale, manning_scale, sizeof(float) * M, cudaMemcpyDefault));
+    if (weights) CK(g, cudaMemcpy(g->w, weights, sizeof(double) * M, cudaMemcpyDefault));
+    return FLOOD_OK;
+}
+
+int flood_volume_report(flood_grid* g, double* storage, double* rain, double* outflow,
+                        double* clamp)
+{
+    if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    if (g->M == 0) return fail(g, FLOOD_ERR_STATE, "flood_ensemble_init has not been called");
+    const int M = g->M;
+    CK(g, cudaDeviceSynchronize());
+    if (storage) {
+        if (flood::launch_storage(g->state, g->ms + (g->k % 3) * M, M, g->ny, g->nx, g->ld, g->plane,
+                                  g->p.dx * g->p.dx, g->part, g->part_cap, g->storage, 0))
+            return fail(g, FLOOD_ERR_STATE, "storage partial buffer too small");
+        g->launches += 2;
+        CK(g, cudaGetLastError());
+        CK(g, cudaMemcpy(storage, g->storage, sizeof(double) * M, cudaMemcpyDefault));
+    }
+    if (rain) CK(g, cudaMemcpy(rain, g->rain_acc, sizeof(double) * M, cudaMemcpyDefault));
+    if (outflow || clamp) {
+        std::vector<double> v((size_t)M * g->nslot * 2);
+        CK(g, cudaMemcpy(v.data(), g->vacc, sizeof(double) * v.size(), cudaMemcpyDeviceToHost));
+        for (int m = 0; m < M; ++m) {
+            double o = 0.0, c = 0.0;
+            for (int k = 0; k < g->nslot; ++k) {
+                o += v[((size_t)m * g->nslot + k) * 2];
+                c += v[((size_t)m * g->nslot + k) * 2 + 1];
+            }
+            if (outflow) outflow[m] = o;
+            if (clamp) clamp[m] = c;
+        }
+    }
+    return FLOOD_OK;
+}
+
+int64_t flood_launch_count(const flood_grid* g) { return g ? g->launches : 0; }
+
+int flood_profile(flood_grid* g, int enable, double* step_kernel_ms, int64_t* step_launches)
+{
+    if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    CK(g, cudaDeviceSynchronize());
+    collect_profile(g);
+    if (step_kernel_ms) *step_kernel_ms = g->prof_ms;
+    if (step_launches) *step_launches = g->prof_launches;
+    g->prof_ms = 0.0;
+    g->prof_launches = 0;
+    g->profile = enable != 0;
+    return FLOOD_OK;
+}
+
+int flood_sync(flood_grid* g, void* stream)
+{
+    if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    CK(g, cudaStreamSynchronize(S(stream)));
+    int err = 0;
+    CK(g, cudaMemcpy(&err, g->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) return fail(g, FLOOD_ERR_NAN, "a kernel produced a non-finite depth");
+    return FLOOD_OK;
+}
+
+}  // extern "C"

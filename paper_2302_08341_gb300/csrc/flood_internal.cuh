@@ -1,0 +1,152 @@
+// Internal definitions shared by the CUDA translation units of libflood.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/flood.h"
+
+namespace flood {
+
+// Per-member scalars.  Kept in three rotating slots so that a step kernel can
+// read its inputs from one slot, build the next slot (the new clock, the new
+// maximum depth by atomicMax) and clear the slot after that, without any
+// grid-wide synchronisation: step k reads slot k%3, writes slot (k+1)%3 and
+// clears the maximum of slot (k+2)%3.
+struct MemberClock {
+    double t;           // simulated time (s)
+    int64_t steps;      // steps taken by this member
+    uint32_t hmax_bits; // max depth of the current state (non-negative float bits)
+    int32_t cur;        // which of the two state buffers holds the current state
+};
+
+// Everything a step launch needs, passed by value.
+struct StepArgs {
+    float* state;               // [2][M][3][plane]: h, qx, qy planes, two buffers
+    const float* z;             // [ny][ld]
+    const float* n;             // [ny][ld]
+    const float* rain_mult;     // [M]
+    const float* scale;         // [M]
+    const float* hyeto;         // [nb] rain rate per block (m/s)
+    const MemberClock* ms_in;   // slot k%3
+    MemberClock* ms_out;        // slot (k+1)%3
+    MemberClock* ms_clr;        // slot (k+2)%3
+    double* vacc;               // [M][nslot][2] outflow and clamp partial volumes
+    double* rain_acc;           // [M] rain volume added
+    double* dt_log;             // [M][dt_log_cap] step lengths (or null)
+    int* err;                   // device error word (bit 0: non-finite depth)
+    size_t plane;               // ny * ld
+    int ny, nx, ld, M, nb;
+    int rows_per_strip;
+    int nslot;                  // slots per member in vacc
+    int dt_log_cap;
+    double t_end;               // < 0: no end
+    double alpha_dx;            // k * dx of Eq. 4
+    double g;
+    double dt_cap, dt_fixed, h_floor, rain_block;
+    double dxd;                 // dx (FP64)
+    double cell_area;           // dx * dx
+    double ncell;               // ny * nx
+    float dx, h_eps, edge_drop; // edge_drop = edge_slope * dx
+    int limiter, east_out, south_out;
+};
+
+// Step length of one member (Eq. 4 with floor, cap and landing on the next
+// stop).  Every CTA of a member evaluates this identically in FP64.
+struct StepPlan {
+    double dt, t_next;
+    float dr;          // rain depth added to every cell this step (m)
+    bool active;
+};
+
+__device__ __forceinline__ StepPlan plan_step(const StepArgs& a, const MemberClock& in, int m)
+{
+    StepPlan s;
+    s.active = !(a.t_end >= 0.0 && in.t >= a.t_end);
+    double dt;
+    if (a.dt_fixed > 0.0) {
+        dt = a.dt_fixed;
+    } else {
+        double hm = (double)__uint_as_float(in.hmax_bits);
+        hm = hm > a.h_floor ? hm : a.h_floor;
+        dt = __ddiv_rn(a.alpha_dx, __dsqrt_rn(__dmul_rn(a.g, hm)));
+        dt = dt > a.dt_cap ? a.dt_cap : dt;
+    }
+    double blk = floor(__ddiv_rn(in.t, a.rain_block));
+    double stop = __dmul_rn(blk + 1.0, a.rain_block);
+    if (a.t_end >= 0.0 && a.t_end < stop) stop = a.t_end;
+    if (__dadd_rn(in.t, dt) >= stop) {
+        dt = __dsub_rn(stop, in.t);
+        s.t_next = stop;
+    } else {
+        s.t_next = __dadd_rn(in.t, dt);
+    }
+    s.dt = dt;
+    int b = (int)blk;
+    double rate = (blk >= 0.0 && b < a.nb) ? (double)a.hyeto[b] : 0.0;
+    s.dr = (float)__dmul_rn(__dmul_rn(dt, rate), (double)a.rain_mult[m]);
+    return s;
+}
+
+// Per-step constants of one member (FP32).
+struct FaceK {
+    float gdt_dx;   // g dt / dx
+    float gdt;      // g dt
+    float dx_4dt;   // dx / (4 dt): limiter factor
+    float h_eps;
+    float edge_drop;     // bed drop over one cell past a free-outflow edge
+    int limiter;
+};
+
+// Eq. 3 then Eq. 2 on one interior link (cell 1 on the low-index side, cell
+// 2 on the high-index side; positive flow from 1 to 2), then the
+// quarter-volume limiter.  No flow where the flow depth is not above h_eps
+// (0 by default: Eq. 2-3 as printed).  The friction term is exactly zero for
+// q = 0, and an underflowed h^(7/3) with q != 0 gives q' = 0, never NaN.  Every operation is an explicitly rounded
+// intrinsic, so a link computed twice (by the tile that owns it and, as a
+// halo, by its neighbour) gives bit-identical values and the update stays
+// exactly conservative.
+__device__ __forceinline__ float link_q(float h1, float z1, float h2, float z2, float q,
+                                        float n_link, const FaceK& k)
+{
+    float zm = fmaxf(z1, z2);
+    // h_flow = max(eta1, eta2) - max(z1, z2), formed from bed differences so
+    // the large bed elevation cancels exactly
+    float hf = fmaxf(__fadd_rn(h1, __fsub_rn(z1, zm)), __fadd_rn(h2, __fsub_rn(z2, zm)));
+    if (!(hf > k.h_eps)) return 0.0f;
+    // dx * S_surf = (z2 - z1) + (h2 - h1)
+    float dS = __fadd_rn(__fsub_rn(z2, z1), __fsub_rn(h2, h1));
+    float num = __fsub_rn(q, __fmul_rn(__fmul_rn(k.gdt_dx, hf), dS));
+    float h73 = __fmul_rn(__fmul_rn(hf, hf), cbrtf(hf));
+    float fr = (q == 0.0f) ? 0.0f
+                           : __fdiv_rn(__fmul_rn(__fmul_rn(k.gdt, __fmul_rn(n_link, n_link)), fabsf(q)), h73);
+    float qn = __fdiv_rn(num, __fadd_rn(1.0f, fr));
+    if (k.limiter) {
+        float lim = __fmul_rn(qn > 0.0f ? h1 : h2, k.dx_4dt);
+        qn = fminf(fmaxf(qn, -lim), lim);
+    }
+    return qn;
+}
+
+// Free-outflow edge link: a ghost cell continuing the bed at the edge slope
+// with the edge cell's depth, so h_flow = h and dx * S = -edge_slope * dx;
+// only outward flow passes.
+__device__ __forceinline__ float outflow_q(float h, float q, float n_cell, const FaceK& k)
+{
+    if (!(h > k.h_eps)) return 0.0f;
+    float num = __fadd_rn(q, __fmul_rn(__fmul_rn(k.gdt_dx, h), k.edge_drop));
+    float h73 = __fmul_rn(__fmul_rn(h, h), cbrtf(h));
+    float fr = (q == 0.0f) ? 0.0f
+                           : __fdiv_rn(__fmul_rn(__fmul_rn(k.gdt, __fmul_rn(n_cell, n_cell)), fabsf(q)), h73);
+    float qn = __fdiv_rn(num, __fadd_rn(1.0f, fr));
+    if (k.limiter) qn = fminf(qn, __fmul_rn(h, k.dx_4dt));
+    return fmaxf(qn, 0.0f);
+}
+
+__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+
+// Host-side helpers (flood_capi.cu).
+void launch_step(const StepArgs& a, int launch_mode, cudaStream_t s);
+int step_nslot(int ny, int nx, int rows_per_strip);
+
+}  // namespace flood

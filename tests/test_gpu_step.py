@@ -1,0 +1,216 @@
+"""GPU parity of the fused local-inertial step (Eq. 1-5, Eq. 4) against the
+FP64 oracle, through the C ABI.  Tolerances: depth 1e-3 m and relative
+volume 1e-5 at the end of a run (the bar the FP32 path is held to; the paper
+saw at most 0.3 cm between single and double precision, Section 4.2); one
+step from an identical state agrees to FP32 rounding."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2302_08341_gb300 import synth
+from tests.gpu_util import compare, oracle_member_from_gpu, oracle_params, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    return require_gpu()
+
+
+def _run_pair(capi, z, n, hy, rm, sc, t_end, params=None, h0=None, M=None):
+    """Run the GPU ensemble and the oracle members to t_end; return both."""
+    ny, nx = z.shape
+    p = params or capi.Params.default()
+    M = M or len(rm)
+    op = oracle_params(p, ny, nx)
+    with capi.Grid(z, n, p) as g:
+        g.ensemble_init(M, rm, sc, hy, h0=h0)
+        g.advance_to(t_end)
+        g.sync()
+        gs = [g.get_state(m) for m in range(M)]
+        mem = g.members()
+        vol = g.volumes()
+    outs = []
+    for m in range(M):
+        h0m = None if h0 is None else (h0[m] if np.ndim(h0) == 3 else h0)
+        mo = oracle.Member.dry(ny, nx, h0m)
+        oracle.advance(op, z, n, float(sc[m]), float(rm[m]), hy, mo, t_end=t_end)
+        outs.append(mo)
+    return gs, mem, vol, outs
+
+
+def test_single_member_256_square_600s_matches_oracle(capi):
+    """Single member, 256 x 256, 3 m cells, 50 mm/h for 600 s, Courant 0.7,
+    closed walls with free outflow on the lowest (east) edge."""
+    terr = synth.make_terrain(256, 256, seed=0)
+    hy = synth.hyetograph_constant(50.0, 600.0)
+    gs, mem, vol, outs = _run_pair(capi, terr.z, terr.n, hy, np.ones(1, np.float32),
+                                   np.ones(1, np.float32), 600.0)
+    h, qx, qy = gs[0]
+    mo = outs[0]
+    assert mem["t"][0] == 600.0 and mo.t == 600.0
+    assert mem["steps"][0] == mo.steps
+    err = compare(h, mo.h, 1e-3)
+    V_gpu, V_or = vol["storage"][0], oracle.storage(mo.h, 3.0)
+    assert abs(V_gpu - V_or) <= 1e-5 * V_or
+    assert abs(vol["rain"][0] - mo.rain) <= 1e-6 * mo.rain
+    assert abs(vol["outflow"][0] - mo.outflow) <= 1e-3 * mo.rain
+    print(f"256^2 600 s: max|dh| {err:.2e} m, steps {mo.steps}")
+
+
+def test_fixed_step_control_run(capi):
+    """The paper's fixed 0.25 s step (Section 4.1) as a control: identical
+    time grids on both sides."""
+    terr = synth.make_terrain(128, 160, seed=3)
+    hy = synth.hyetograph_constant(80.0, 300.0)
+    p = capi.Params.default(dt_fixed=0.25)
+    gs, mem, vol, outs = _run_pair(capi, terr.z, terr.n, hy, np.array([1.3], np.float32),
+                                   np.array([0.8], np.float32), 300.0, params=p)
+    assert mem["steps"][0] == 1200 == outs[0].steps
+    compare(gs[0][0], outs[0].h, 1e-3)
+
+
+@pytest.mark.parametrize("ny,nx", [(1, 1), (1, 2), (2, 1), (3, 3), (5, 7), (1, 131), (130, 1),
+                                   (37, 129), (70, 300), (9, 257)])
+def test_ragged_and_tiny_grids_one_step_from_random_state(capi, ny, nx):
+    """One step from the same random wet state (FP32 values on both sides):
+    every link and depth agrees to FP32 rounding, across warp spans (128
+    columns), row strips, ragged edges and degenerate 1-cell grids."""
+    rng = np.random.default_rng(ny * 1000 + nx)
+    z = rng.uniform(0.0, 1.5, (ny, nx)).astype(np.float32)
+    n = rng.uniform(0.02, 0.08, (ny, nx)).astype(np.float32)
+    h = rng.uniform(0.0, 0.8, (ny, nx)).astype(np.float32)
+    h[rng.random((ny, nx)) < 0.15] = 0.0
+    qx = rng.normal(0.0, 0.05, (ny, nx)).astype(np.float32)
+    qy = rng.normal(0.0, 0.05, (ny, nx)).astype(np.float32)
+    qx[:, -1] = np.abs(qx[:, -1])   # the east edge is an outflow: outward only
+    qy[-1, :] = 0.0                 # the south edge is a wall
+    p = capi.Params.default(dt_fixed=0.2)
+    hy = np.array([30.0 / 3.6e6], np.float32)
+    with capi.Grid(z, n, p) as g:
+        g.ensemble_init(1, np.array([1.1], np.float32), np.array([0.9], np.float32), hy)
+        g.set_state(0, h, qx, qy)
+        g.step(1)
+        h1, qx1, qy1 = g.get_state(0)
+    mo = oracle_member_from_gpu(h, qx, qy)
+    op = oracle_params(p, ny, nx)
+    oracle.step(op, z, n, 0.9, float(hy[0]) * 1.1, 0.2, mo)
+    compare(qx1, mo.qx[:, 1:], 2e-5 + 0.0)
+    compare(qy1, mo.qy[1:, :], 2e-5)
+    compare(h1, mo.h, 5e-6)
+    assert np.all(mo.qx[:, 0] == 0) and np.all(mo.qy[0, :] == 0)
+
+
+def test_south_outflow_and_limiter_off_variants(capi):
+    rng = np.random.default_rng(5)
+    ny, nx = 41, 67
+    z = (0.01 * np.arange(ny)[:, None] + rng.uniform(0, 0.2, (ny, nx))).astype(np.float32)
+    n = np.full((ny, nx), 0.04, np.float32)
+    h0 = rng.uniform(0.0, 0.4, (ny, nx)).astype(np.float32)
+    for lim in (0, 1):
+        p = capi.Params.default(east_outflow=0, south_outflow=1, limiter=lim, dt_cap=0.3)
+        gs, mem, vol, outs = _run_pair(capi, z, n, np.zeros(1, np.float32),
+                                       np.ones(1, np.float32), np.ones(1, np.float32), 60.0,
+                                       params=p, h0=h0)
+        compare(gs[0][0], outs[0].h, 1e-3)
+        assert vol["outflow"][0] > 0
+        assert abs(vol["outflow"][0] - outs[0].outflow) <= 1e-3 * max(outs[0].outflow, 1.0)
+
+
+def test_lake_at_rest_exact_on_gpu(capi):
+    rng = np.random.default_rng(7)
+    ny, nx = 45, 150
+    z = (rng.integers(0, 2600, (ny, nx)) * 2.0 ** -10).astype(np.float32)
+    h = np.maximum(2.0 - z, 0.0).astype(np.float32)
+    p = capi.Params.default(east_outflow=0)
+    with capi.Grid(z, np.full((ny, nx), 0.05, np.float32), p) as g:
+        g.ensemble_init(2, np.zeros(2, np.float32), np.ones(2, np.float32),
+                        np.zeros(1, np.float32), h0=h)
+        g.step(100)
+        for m in range(2):
+            h1, qx1, qy1 = g.get_state(m)
+            assert np.array_equal(h1, h)
+            assert not qx1.any() and not qy1.any()
+
+
+def test_transposition_symmetry_is_bitwise_on_gpu(capi):
+    terr = synth.make_terrain(72, 140, seed=9)
+    hy = synth.hyetograph_constant(100.0, 300.0)
+    pa = capi.Params.default(east_outflow=1, south_outflow=0)
+    pb = capi.Params.default(east_outflow=0, south_outflow=1)
+    with capi.Grid(terr.z, terr.n, pa) as a, capi.Grid(terr.z.T.copy(), terr.n.T.copy(), pb) as b:
+        for g in (a, b):
+            g.ensemble_init(1, np.ones(1, np.float32), np.ones(1, np.float32), hy)
+            g.advance_to(240.0)
+        ha, qxa, qya = a.get_state(0)
+        hb, qxb, qyb = b.get_state(0)
+    assert np.array_equal(ha, hb.T)
+    assert np.array_equal(qxa, qyb.T) and np.array_equal(qya, qxb.T)
+
+
+def test_two_runs_are_bitwise_identical(capi):
+    terr = synth.make_terrain(96, 200, seed=4)
+    hy = synth.hyetograph_constant(150.0, 600.0)
+    rm, sc = synth.ensemble_prior(4, 6)
+    res = []
+    for _ in range(2):
+        with capi.Grid(terr.z, terr.n) as g:
+            g.ensemble_init(6, rm, sc, hy)
+            g.advance_to(420.0)
+            res.append([g.get_state(m) for m in range(6)] + [g.volumes()])
+    for m in range(6):
+        for k in range(3):
+            assert np.array_equal(res[0][m][k], res[1][m][k])
+    for key in ("storage", "rain", "outflow", "clamp"):
+        assert np.array_equal(res[0][6][key], res[1][6][key])
+
+
+def test_ensemble_members_each_match_oracle_and_conserve_volume(capi):
+    """Per-member rain multiplier and Manning scale (Section 4.1's uncertain
+    inputs) with per-member adaptive steps."""
+    terr = synth.make_terrain(80, 150, seed=12)
+    hy = synth.hyetograph_triangular(60.0, 1200.0, 3600.0)
+    M = 9
+    rm, sc = synth.ensemble_prior(12, M)
+    rm = (rm * 3.0).astype(np.float32)   # heavier storm: deeper water, CFL-limited steps
+    gs, mem, vol, outs = _run_pair(capi, terr.z, terr.n, hy, rm, sc, 1500.0)
+    for m in range(M):
+        compare(gs[m][0], outs[m].h, 1e-3)
+        assert mem["t"][m] == 1500.0
+        V = vol["storage"][m]
+        Vo = oracle.storage(outs[m].h, 3.0)
+        assert abs(V - Vo) <= 1e-5 * Vo
+        bal = V - (vol["rain"][m] - vol["outflow"][m] + vol["clamp"][m])
+        assert abs(bal) <= 1e-5 * vol["rain"][m]
+        assert gs[m][0].min() >= 0.0
+    assert len(set(mem["steps"].tolist())) > 1 or mem["steps"][0] == outs[0].steps
+
+
+def test_nan_input_is_reported_at_sync(capi):
+    """Host-side fault injection: a non-finite depth fed in through the ABI is
+    flagged by the kernel and returned as FLOOD_ERR_NAN."""
+    z = np.zeros((8, 8), np.float32)
+    with capi.Grid(z, np.full((8, 8), 0.03, np.float32)) as g:
+        g.ensemble_init(1, np.ones(1, np.float32), np.ones(1, np.float32), np.zeros(1, np.float32))
+        h = np.full((8, 8), 0.1, np.float32)
+        h[3, 4] = np.nan
+        g.set_state(0, h)
+        g.step(2)
+        with pytest.raises(capi.FloodError) as e:
+            g.sync()
+        assert e.value.code == -5
+
+
+def test_bad_arguments_raise(capi):
+    z = np.zeros((4, 4), np.float32)
+    with capi.Grid(z, z + 0.03) as g:
+        with pytest.raises(capi.FloodError):
+            g.step(1)                                     # before ensemble_init
+        g.ensemble_init(2, np.ones(2, np.float32), np.ones(2, np.float32), np.zeros(1, np.float32))
+        with pytest.raises(capi.FloodError):
+            g.gauge_sample(np.array([16], np.int32))      # cell out of range
+        with pytest.raises(capi.FloodError):
+            g.pf_assimilate(np.zeros(1), 0.05, 1.5, np.ones(2, np.float32))  # u outside [0,1)
+        with pytest.raises(capi.FloodError):
+            g.get_state(2)

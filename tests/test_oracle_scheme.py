@@ -203,8 +203,10 @@ def test_no_flow_over_a_dry_wall_eq3():
 
 
 def test_shallow_sheet_below_h_eps_does_not_move():
+    """The optional wet/dry threshold: links with flow depth <= h_eps carry
+    nothing."""
     ny, nx = 4, 10
-    p = oracle.Params(ny=ny, nx=nx)
+    p = oracle.Params(ny=ny, nx=nx, h_eps=1e-3)
     z = np.broadcast_to(0.05 * (nx - 1 - np.arange(nx)), (ny, nx)).copy()
     m = oracle.Member.dry(ny, nx, np.full((ny, nx), 0.9e-3))
     oracle.advance(p, z, np.full((ny, nx), 0.03), 1.0, 1.0, np.zeros(1), m, max_steps=50)
