@@ -216,6 +216,14 @@ int64_t flood_launch_count(const flood_grid* g);
  * (enable = 1) or off (enable = 0). */
 int flood_profile(flood_grid* g, int enable, double* step_kernel_ms, int64_t* step_launches);
 
+/* Launch shape of the step kernel (for tuning): each warp marches down
+ * rows_per_strip rows of a 128-column span of one member; a CTA holds
+ * members_per_cta members (1, 2, 4 or 8) of the same span(s).  (0, 0) restores
+ * the automatic choice.  Applies to the following steps; results do not depend
+ * on it (bitwise).  Errors: FLOOD_ERR_ARG. */
+int flood_set_launch(flood_grid* g, int rows_per_strip, int members_per_cta);
+int flood_get_launch(const flood_grid* g, int* rows_per_strip, int* members_per_cta);
+
 /* Wait for `stream`, then report device-side faults of the method: returns
  * FLOOD_ERR_NAN if any step produced a non-finite depth. */
 int flood_sync(flood_grid* g, void* stream);

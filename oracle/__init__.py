@@ -89,6 +89,13 @@ def load(path: str):
         L.orc_resample_systematic.argtypes = [C.c_int, _D, C.c_double, _I32]
         L.orc_assign_slots.restype = None
         L.orc_assign_slots.argtypes = [C.c_int, _I32, _I32]
+        L.orc_step_adjoint.restype = None
+        L.orc_step_adjoint.argtypes = [C.POINTER(OrcParams), _D, _D, C.c_double, C.c_double,
+                                       C.c_double, C.c_double, _D, _D, _D, _D, _D, _D, _D, _D, _D]
+        L.orc_loss_and_grad.restype = C.c_double
+        L.orc_loss_and_grad.argtypes = [C.POINTER(OrcParams), _D, _D, C.c_double, C.c_double, _D,
+                                        C.c_int, _D, C.c_double, C.c_int, C.c_int, _I32, _D, _D,
+                                        _D, _D, _D, C.POINTER(C.c_long)]
     return L
 
 
@@ -318,3 +325,37 @@ def pf_assimilate(ens: Ensemble, y, d, sigma, rain_mult, scale, u, beta, n_thr_f
     scale = scale[src]
     ens.w = np.full(ens.M, 1.0 / ens.M)
     return w, neff, idx, rain_mult, scale
+
+
+def step_adjoint(p: Params, z, n, scale, rate, rain_mult, dt_, m: Member, lh, lqx, lqy):
+    """Reverse of one iteration at state m (the step's input).  lh, lqx, lqy
+    (oracle layout) are the loss's sensitivities to the step's outputs; they
+    are overwritten with those to its inputs.  Returns (grad_n, grad_rain,
+    grad_scale) contributions of this step."""
+    z = np.ascontiguousarray(z, np.float64); n = np.ascontiguousarray(n, np.float64)
+    gn = np.zeros(z.shape)
+    gr = C.c_double(0.0); gs = C.c_double(0.0)
+    lib().orc_step_adjoint(C.byref(p.c()), _d(z), _d(n), float(scale), float(rate),
+                           float(rain_mult), float(dt_), _d(m.h), _d(m.qx), _d(m.qy), _d(lh),
+                           _d(lqx), _d(lqy), _d(gn), C.byref(gr), C.byref(gs))
+    return gn, gr.value, gs.value
+
+
+def loss_and_grad(p: Params, z, n, scale, rain_mult, hyeto, h0, sample_dt, d, cells):
+    """Gauge-misfit loss sum_s sum_g (h(t_s)[cell_g] - d[s][g])^2 at
+    t_s = s * sample_dt and its gradients with respect to the base Manning
+    field, the initial depth, the rain multiplier and the Manning scale."""
+    z = np.ascontiguousarray(z, np.float64); n = np.ascontiguousarray(n, np.float64)
+    hy = np.ascontiguousarray(hyeto, np.float64)
+    h0 = np.ascontiguousarray(np.broadcast_to(h0, z.shape), np.float64)
+    d = np.ascontiguousarray(d, np.float64)
+    cells = np.ascontiguousarray(cells, np.int32)
+    ns, G = d.shape
+    gn = np.zeros(z.shape); gh = np.zeros(z.shape)
+    gr = C.c_double(); gs = C.c_double(); nst = C.c_long()
+    loss = lib().orc_loss_and_grad(C.byref(p.c()), _d(z), _d(n), float(scale), float(rain_mult),
+                                   _d(hy), len(hy), _d(h0), float(sample_dt), ns, G, _i32(cells),
+                                   _d(d), _d(gn), _d(gh), C.byref(gr), C.byref(gs),
+                                   C.byref(nst))
+    return dict(loss=loss, grad_n=gn, grad_h0=gh, grad_rain=gr.value, grad_scale=gs.value,
+                steps=nst.value)

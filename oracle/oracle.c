@@ -367,3 +367,258 @@ void orc_assign_slots(int M, const int32_t* idx, int32_t* src)
     }
     free(k);
 }
+
+/* ==== Adjoint (reverse mode) of one iteration ================================
+ * Extension beyond the paper: gradients of a gauge-misfit loss with respect
+ * to the Manning field, the member's rain multiplier and the initial depth.
+ * The step lengths are held fixed (the recorded schedule); at the kinks of
+ * Eq. 3 (max), the limiter, the wet/dry test, the outflow clip and the
+ * negative-depth clamp the derivative of the branch actually taken is used,
+ * ties in Eq. 3's max going to the first argument. */
+
+/* Forward link flux with the partial derivatives of q' with respect to h1,
+ * h2, the old flux q and the link roughness nl. */
+static double link_flux_d(const orc_params* p, double h1, double z1, double h2, double z2,
+                          double q, double nl, double dt, double* d_h1, double* d_h2,
+                          double* d_q, double* d_nl)
+{
+    *d_h1 = *d_h2 = *d_q = *d_nl = 0.0;
+    double eta1 = h1 + z1, eta2 = h2 + z2;
+    double hflow = fmax(eta1, eta2) - fmax(z1, z2);                 /* Eq. 3 */
+    if (hflow <= p->h_eps) return 0.0;
+    int first = eta1 >= eta2;            /* which argument of max(eta1, eta2) */
+    double S = (eta2 - eta1) / p->dx;
+    double num = q - p->g * hflow * dt * S;
+    double fric = q == 0.0 ? 0.0 : p->g * nl * nl * fabs(q) * dt / pow(hflow, 7.0 / 3.0);
+    double den = 1.0 + fric;
+    double qn = num / den;                                          /* Eq. 2 */
+    if (p->limiter) {
+        double lim = (qn > 0.0 ? h1 : h2) * p->dx / (4.0 * dt);
+        if (qn > lim) {
+            *d_h1 = p->dx / (4.0 * dt);
+            return lim;
+        }
+        if (qn < -lim) {
+            *d_h2 = -p->dx / (4.0 * dt);
+            return -lim;
+        }
+    }
+    /* q' = num / den */
+    double dq_dnum = 1.0 / den, dq_dfric = -qn / den;
+    double dnum_dhf = -p->g * dt * S, dnum_dS = -p->g * hflow * dt;
+    double dfric_dq = q == 0.0 ? 0.0 : fric / q;
+    double dfric_dhf = -(7.0 / 3.0) * fric / hflow;
+    double dfric_dnl = nl == 0.0 ? 0.0 : 2.0 * fric / nl;
+    double dq_dhf = dq_dnum * dnum_dhf + dq_dfric * dfric_dhf;
+    double dq_dS = dq_dnum * dnum_dS;
+    *d_h1 = (first ? dq_dhf : 0.0) - dq_dS / p->dx;
+    *d_h2 = (first ? 0.0 : dq_dhf) + dq_dS / p->dx;
+    *d_q = dq_dnum + dq_dfric * dfric_dq;
+    *d_nl = dq_dfric * dfric_dnl;
+    return qn;
+}
+
+/* Reverse of orc_step.  State (h, qx, qy) is the input of the forward step;
+ * (lh, lqx, lqy) hold the loss's sensitivities to the step's outputs on entry
+ * and to its inputs on exit.  grad_n (per cell) accumulates dL/dn_base,
+ * *grad_rain dL/d(rain multiplier) given the block rate, *grad_scale
+ * dL/d(Manning scale). */
+void orc_step_adjoint(const orc_params* p, const double* z, const double* n, double scale,
+                      double rate, double rain_mult, double dt, const double* h, const double* qx,
+                      const double* qy, double* lh, double* lqx, double* lqy, double* grad_n,
+                      double* grad_rain, double* grad_scale)
+{
+    const int ny = p->ny, nx = p->nx;
+    const double dx = p->dx, T = dt / dx;
+    const size_t nqx = (size_t)ny * (size_t)(nx + 1), nqy = (size_t)(ny + 1) * (size_t)nx;
+    double* qxn = (double*)calloc(nqx, sizeof(double));
+    double* qyn = (double*)calloc(nqy, sizeof(double));
+    double* dx1 = (double*)calloc(nqx * 4, sizeof(double));   /* d/dh1, d/dh2, d/dq, d/dnl */
+    double* dy1 = (double*)calloc(nqy * 4, sizeof(double));
+    double* lt = (double*)calloc((size_t)ny * nx, sizeof(double));
+    /* recompute the forward links with their derivatives */
+    for (int r = 0; r < ny; ++r)
+        for (int c = 1; c <= nx; ++c) {
+            double* dd = dx1 + IQX(r, c) * 4;
+            if (c == nx) {
+                if (!p->east_outflow) continue;
+                double hh = h[IX(r, nx - 1)], zz = z[IX(r, nx - 1)];
+                double nl = scale * n[IX(r, nx - 1)];
+                double a, b;
+                double qn = link_flux_d(p, hh, zz, hh, zz - p->edge_slope * dx, qx[IQX(r, nx)], nl,
+                                        dt, &a, &b, &dd[2], &dd[3]);
+                if (qn > 0.0) {
+                    dd[0] = a + b;   /* the ghost carries the edge depth */
+                    qxn[IQX(r, c)] = qn;
+                } else {
+                    dd[2] = dd[3] = 0.0;
+                }
+                continue;
+            }
+            double nl = scale * 0.5 * (n[IX(r, c - 1)] + n[IX(r, c)]);
+            qxn[IQX(r, c)] = link_flux_d(p, h[IX(r, c - 1)], z[IX(r, c - 1)], h[IX(r, c)],
+                                         z[IX(r, c)], qx[IQX(r, c)], nl, dt, &dd[0], &dd[1], &dd[2],
+                                         &dd[3]);
+        }
+    for (int r = 1; r <= ny; ++r)
+        for (int c = 0; c < nx; ++c) {
+            double* dd = dy1 + IQY(r, c) * 4;
+            if (r == ny) {
+                if (!p->south_outflow) continue;
+                double hh = h[IX(ny - 1, c)], zz = z[IX(ny - 1, c)];
+                double nl = scale * n[IX(ny - 1, c)];
+                double a, b;
+                double qn = link_flux_d(p, hh, zz, hh, zz - p->edge_slope * dx, qy[IQY(ny, c)], nl,
+                                        dt, &a, &b, &dd[2], &dd[3]);
+                if (qn > 0.0) {
+                    dd[0] = a + b;
+                    qyn[IQY(r, c)] = qn;
+                } else {
+                    dd[2] = dd[3] = 0.0;
+                }
+                continue;
+            }
+            double nl = scale * 0.5 * (n[IX(r - 1, c)] + n[IX(r, c)]);
+            qyn[IQY(r, c)] = link_flux_d(p, h[IX(r - 1, c)], z[IX(r - 1, c)], h[IX(r, c)],
+                                         z[IX(r, c)], qy[IQY(r, c)], nl, dt, &dd[0], &dd[1], &dd[2],
+                                         &dd[3]);
+        }
+    /* continuity: the clamp passes no sensitivity */
+    double gr = 0.0;
+    for (int r = 0; r < ny; ++r)
+        for (int c = 0; c < nx; ++c) {
+            double hpre = h[IX(r, c)] + T * (qxn[IQX(r, c)] - qxn[IQX(r, c + 1)] + qyn[IQY(r, c)] -
+                                             qyn[IQY(r + 1, c)]) + dt * rate * rain_mult;
+            lt[IX(r, c)] = hpre < 0.0 ? 0.0 : lh[IX(r, c)];
+            gr += lt[IX(r, c)] * dt * rate;
+        }
+    *grad_rain += gr;
+    /* sensitivity to each new link flux, then back through Eq. 2-3 */
+    double* lh_new = (double*)calloc((size_t)ny * nx, sizeof(double));
+    for (size_t i = 0; i < (size_t)ny * nx; ++i) lh_new[i] = lt[i];
+    for (int r = 0; r < ny; ++r)
+        for (int c = 1; c <= nx; ++c) {
+            const double* dd = dx1 + IQX(r, c) * 4;
+            double mu = lqx[IQX(r, c)] - T * lt[IX(r, c - 1)] + (c < nx ? T * lt[IX(r, c)] : 0.0);
+            lh_new[IX(r, c - 1)] += mu * dd[0];
+            if (c < nx) lh_new[IX(r, c)] += mu * dd[1];
+            lqx[IQX(r, c)] = mu * dd[2];
+            if (c < nx) {
+                grad_n[IX(r, c - 1)] += mu * dd[3] * scale * 0.5;
+                grad_n[IX(r, c)] += mu * dd[3] * scale * 0.5;
+                *grad_scale += mu * dd[3] * 0.5 * (n[IX(r, c - 1)] + n[IX(r, c)]);
+            } else {
+                grad_n[IX(r, c - 1)] += mu * dd[3] * scale;
+                *grad_scale += mu * dd[3] * n[IX(r, c - 1)];
+            }
+        }
+    for (int r = 0; r < ny; ++r) lqx[IQX(r, 0)] = 0.0;
+    for (int r = 1; r <= ny; ++r)
+        for (int c = 0; c < nx; ++c) {
+            const double* dd = dy1 + IQY(r, c) * 4;
+            double mu = lqy[IQY(r, c)] - T * lt[IX(r - 1, c)] + (r < ny ? T * lt[IX(r, c)] : 0.0);
+            lh_new[IX(r - 1, c)] += mu * dd[0];
+            if (r < ny) lh_new[IX(r, c)] += mu * dd[1];
+            lqy[IQY(r, c)] = mu * dd[2];
+            if (r < ny) {
+                grad_n[IX(r - 1, c)] += mu * dd[3] * scale * 0.5;
+                grad_n[IX(r, c)] += mu * dd[3] * scale * 0.5;
+                *grad_scale += mu * dd[3] * 0.5 * (n[IX(r - 1, c)] + n[IX(r, c)]);
+            } else {
+                grad_n[IX(r - 1, c)] += mu * dd[3] * scale;
+                *grad_scale += mu * dd[3] * n[IX(r - 1, c)];
+            }
+        }
+    for (int c = 0; c < nx; ++c) lqy[IQY(0, c)] = 0.0;
+    memcpy(lh, lh_new, sizeof(double) * (size_t)ny * nx);
+    free(lh_new);
+    free(qxn);
+    free(qyn);
+    free(dx1);
+    free(dy1);
+    free(lt);
+}
+
+/* Loss L = sum over sample times t_s = s * sample_dt (s = 1..ns) and gauges
+ * g of (h(t_s)[cells[g]] - d[s-1][g])^2 for one member started from h0 (links
+ * at rest) at t = 0, and its gradients: grad_n [ny*nx] (base Manning field),
+ * grad_h0 [ny*nx], *grad_rain (rain multiplier), *grad_scale (Manning scale).
+ * Stores the whole trajectory (small grids only).  Returns the loss. */
+double orc_loss_and_grad(const orc_params* p, const double* z, const double* n, double scale,
+                         double rain_mult, const double* hyeto, int n_blocks, const double* h0,
+                         double sample_dt, int ns, int G, const int32_t* cells, const double* d,
+                         double* grad_n, double* grad_h0, double* grad_rain, double* grad_scale,
+                         long* n_steps_out)
+{
+    const int ny = p->ny, nx = p->nx;
+    const size_t nc = (size_t)ny * nx, nqx = (size_t)ny * (nx + 1), nqy = (size_t)(ny + 1) * nx;
+    const size_t per = nc + nqx + nqy;
+    long cap = 1024, nst = 0;
+    double* traj = (double*)malloc(sizeof(double) * per * (size_t)(cap + 1));
+    double* dts = (double*)malloc(sizeof(double) * (size_t)cap);
+    double* rates = (double*)malloc(sizeof(double) * (size_t)cap);
+    int* sample_after = (int*)malloc(sizeof(int) * (size_t)cap);   /* sample index or -1 */
+    double* h = (double*)malloc(sizeof(double) * nc);
+    double* qx = (double*)calloc(nqx, sizeof(double));
+    double* qy = (double*)calloc(nqy, sizeof(double));
+    double* qxs = (double*)malloc(sizeof(double) * nqx);
+    double* qys = (double*)malloc(sizeof(double) * nqy);
+    memcpy(h, h0, sizeof(double) * nc);
+    orc_volumes vol = {0, 0, 0};
+    double t = 0.0, loss = 0.0;
+    for (int s = 1; s <= ns; ++s) {
+        double t_end = s * sample_dt;
+        while (t < t_end) {
+            if (nst == cap) {
+                cap *= 2;
+                traj = (double*)realloc(traj, sizeof(double) * per * (size_t)(cap + 1));
+                dts = (double*)realloc(dts, sizeof(double) * (size_t)cap);
+                rates = (double*)realloc(rates, sizeof(double) * (size_t)cap);
+                sample_after = (int*)realloc(sample_after, sizeof(int) * (size_t)cap);
+            }
+            double* st = traj + per * (size_t)nst;
+            memcpy(st, h, sizeof(double) * nc);
+            memcpy(st + nc, qx, sizeof(double) * nqx);
+            memcpy(st + nc + nqx, qy, sizeof(double) * nqy);
+            double t_next;
+            double dt = orc_dt(p, orc_hmax(ny, nx, h), t, t_end, &t_next);
+            double rate = orc_rain_rate(p, hyeto, n_blocks, t);
+            orc_step(p, z, n, scale, rate * rain_mult, dt, h, qx, qy, qxs, qys, &vol);
+            dts[nst] = dt;
+            rates[nst] = rate;
+            sample_after[nst] = -1;
+            t = t_next;
+            ++nst;
+        }
+        sample_after[nst - 1] = s - 1;
+        for (int g = 0; g < G; ++g) {
+            double e = h[cells[g]] - d[(size_t)(s - 1) * G + g];
+            loss += e * e;
+        }
+    }
+    /* reverse sweep */
+    double* lh = (double*)calloc(nc, sizeof(double));
+    double* lqx = (double*)calloc(nqx, sizeof(double));
+    double* lqy = (double*)calloc(nqy, sizeof(double));
+    for (size_t i = 0; i < nc; ++i) grad_n[i] = 0.0;
+    *grad_rain = 0.0;
+    *grad_scale = 0.0;
+    for (long k = nst - 1; k >= 0; --k) {
+        if (sample_after[k] >= 0) {
+            /* the state after step k is observed: h_{k+1} is the next stored
+               state, or the final state for the last step */
+            const double* hk1 = (k + 1 < nst) ? traj + per * (size_t)(k + 1) : h;
+            int s = sample_after[k];
+            for (int g = 0; g < G; ++g)
+                lh[cells[g]] += 2.0 * (hk1[cells[g]] - d[(size_t)s * G + g]);
+        }
+        const double* st = traj + per * (size_t)k;
+        orc_step_adjoint(p, z, n, scale, rates[k], rain_mult, dts[k], st, st + nc, st + nc + nqx,
+                         lh, lqx, lqy, grad_n, grad_rain, grad_scale);
+    }
+    memcpy(grad_h0, lh, sizeof(double) * nc);
+    if (n_steps_out) *n_steps_out = nst;
+    free(lh); free(lqx); free(lqy); free(traj); free(dts); free(rates); free(sample_after);
+    free(h); free(qx); free(qy); free(qxs); free(qys);
+    return loss;
+}

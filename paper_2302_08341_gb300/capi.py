@@ -24,7 +24,7 @@ EXPORTED = ["flood_default_params", "flood_last_error", "flood_create_grid", "fl
             "flood_ensemble_init", "flood_step", "flood_gauge_sample", "pf_assimilate",
             "pf_resample_systematic", "flood_get_state", "flood_set_state", "flood_get_members",
             "flood_set_members", "flood_volume_report", "flood_launch_count", "flood_sync",
-            "flood_profile"]
+            "flood_profile", "flood_set_launch", "flood_get_launch"]
 
 
 class FloodError(RuntimeError):
@@ -87,6 +87,8 @@ def lib(path: str = LIB_PATH):
     L.flood_launch_count.restype = C.c_int64
     L.flood_sync.argtypes = [_VP, _VP]
     L.flood_profile.argtypes = [_VP, C.c_int, _VP, _VP]
+    L.flood_set_launch.argtypes = [_VP, C.c_int, C.c_int]
+    L.flood_get_launch.argtypes = [_VP, _VP, _VP]
     for name in EXPORTED:
         if name not in ("flood_default_params", "flood_last_error", "flood_launch_count"):
             getattr(L, name).restype = C.c_int
@@ -288,6 +290,15 @@ class Grid:
         _check(lib().flood_volume_report(self.h, ptr(out["storage"]), ptr(out["rain"]),
                                          ptr(out["outflow"]), ptr(out["clamp"])), self.h)
         return out
+
+    def set_launch(self, rows_per_strip=0, members_per_cta=0):
+        """Step-kernel launch shape; (0, 0) = automatic."""
+        _check(lib().flood_set_launch(self.h, int(rows_per_strip), int(members_per_cta)), self.h)
+
+    def get_launch(self):
+        r = C.c_int(); m = C.c_int()
+        _check(lib().flood_get_launch(self.h, C.byref(r), C.byref(m)), self.h)
+        return r.value, m.value
 
     def profile(self, enable=True):
         """Turn per-launch step-kernel timing on/off; returns (ms, launches)

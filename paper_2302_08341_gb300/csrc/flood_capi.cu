@@ -35,6 +35,8 @@ struct flood_grid {
     double* rain_acc = nullptr;   // [M]
     int* err = nullptr;           // device error word
     int rows_per_strip = 64;
+    int members_per_cta = 4;
+    bool launch_fixed = false;    // set by flood_set_launch
     // particle filter
     int G = 0, G_cap = 0;
     int32_t* cells = nullptr;     // [G_cap]
@@ -180,7 +182,7 @@ int launch_steps(flood_grid* g, int64_t count, double t_end, cudaStream_t s)
             }
             CK(g, cudaEventRecord(ev.first, s));
         }
-        flood::launch_step(a, g->M >= 4 ? 0 : 1, s);
+        flood::launch_step(a, g->members_per_cta, s);
         if (g->profile) {
             CK(g, cudaEventRecord(ev.second, s));
             g->ev_pending.push_back(ev);
@@ -202,6 +204,26 @@ int read_clocks(flood_grid* g, std::vector<MemberClock>& out, cudaStream_t s)
     int err = 0;
     CK(g, cudaMemcpy(&err, g->err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) return fail(g, FLOOD_ERR_NAN, "a kernel produced a non-finite depth");
+    return FLOOD_OK;
+}
+
+// Grow the per-warp volume slots when a launch shape with more warp tasks
+// per member is chosen; the sums accumulated so far move to slot 0.
+int ensure_vacc(flood_grid* g, int need)
+{
+    if (!g->M || need <= g->nslot) return FLOOD_OK;
+    const int M = g->M;
+    std::vector<double> old((size_t)M * g->nslot * 2), nw((size_t)M * need * 2, 0.0);
+    CK(g, cudaDeviceSynchronize());
+    CK(g, cudaMemcpy(old.data(), g->vacc, sizeof(double) * old.size(), cudaMemcpyDeviceToHost));
+    for (int m = 0; m < M; ++m)
+        for (int k = 0; k < g->nslot; ++k)
+            for (int j = 0; j < 2; ++j)
+                nw[(size_t)m * need * 2 + j] += old[((size_t)m * g->nslot + k) * 2 + j];
+    int rc = dalloc(g, &g->vacc, nw.size());
+    if (rc) return rc;
+    CK(g, cudaMemcpy(g->vacc, nw.data(), sizeof(double) * nw.size(), cudaMemcpyHostToDevice));
+    g->nslot = need;
     return FLOOD_OK;
 }
 
@@ -317,7 +339,10 @@ int flood_ensemble_init(flood_grid* g, int M, const float* h0, int h0_per_member
     free_ensemble(g);
     g->M = M;
     g->nb = n_blocks;
-    g->rows_per_strip = choose_rows_per_strip(g->ny, g->nx, M, g->n_sm);
+    if (!g->launch_fixed) {
+        g->rows_per_strip = choose_rows_per_strip(g->ny, g->nx, M, g->n_sm);
+        g->members_per_cta = M >= 4 ? 4 : 1;
+    }
     g->nslot = flood::step_nslot(g->ny, g->nx, g->rows_per_strip);
     g->part_cap = (g->ny + 15) / 16;
     int rc;
@@ -651,6 +676,40 @@ int flood_profile(flood_grid* g, int enable, double* step_kernel_ms, int64_t* st
     g->prof_ms = 0.0;
     g->prof_launches = 0;
     g->profile = enable != 0;
+    return FLOOD_OK;
+}
+
+int flood_set_launch(flood_grid* g, int rows_per_strip, int members_per_cta)
+{
+    if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    if (rows_per_strip == 0 && members_per_cta == 0) {
+        g->launch_fixed = false;
+        if (g->M) {
+            const int rh = choose_rows_per_strip(g->ny, g->nx, g->M, g->n_sm);
+            int rc = ensure_vacc(g, flood::step_nslot(g->ny, g->nx, rh));
+            if (rc) return rc;
+            g->rows_per_strip = rh;
+            g->members_per_cta = g->M >= 4 ? 4 : 1;
+        }
+        return FLOOD_OK;
+    }
+    if (rows_per_strip < 1 || rows_per_strip > 4096)
+        return fail(g, FLOOD_ERR_ARG, "rows_per_strip must lie in [1, 4096]");
+    if (members_per_cta != 1 && members_per_cta != 2 && members_per_cta != 4 && members_per_cta != 8)
+        return fail(g, FLOOD_ERR_ARG, "members_per_cta must be 1, 2, 4 or 8");
+    int rc = ensure_vacc(g, flood::step_nslot(g->ny, g->nx, rows_per_strip));
+    if (rc) return rc;
+    g->rows_per_strip = rows_per_strip;
+    g->members_per_cta = members_per_cta;
+    g->launch_fixed = true;
+    return FLOOD_OK;
+}
+
+int flood_get_launch(const flood_grid* g, int* rows_per_strip, int* members_per_cta)
+{
+    if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    if (rows_per_strip) *rows_per_strip = g->rows_per_strip;
+    if (members_per_cta) *members_per_cta = g->members_per_cta;
     return FLOOD_OK;
 }
 

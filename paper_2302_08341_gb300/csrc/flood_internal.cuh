@@ -90,42 +90,54 @@ __device__ __forceinline__ StepPlan plan_step(const StepArgs& a, const MemberClo
 
 // Per-step constants of one member (FP32).
 struct FaceK {
-    float gdt_dx;   // g dt / dx
-    float gdt;      // g dt
-    float dx_4dt;   // dx / (4 dt): limiter factor
-    float h_eps;
-    float edge_drop;     // bed drop over one cell past a free-outflow edge
+    float gdt_dx;     // g dt / dx
+    float gdt;        // g dt
+    float dx_4dt;     // dx / (4 dt): limiter factor
+    float h_eps;      // no flow unless the flow depth exceeds this (0: Eq. 2-3 as printed)
+    float edge_drop;  // bed drop over one cell past a free-outflow edge
     int limiter;
 };
 
+// h^(-7/3) from the hardware base-2 logarithm and exponential
+// (h^(-7/3) = 2^(-7/3 log2 h)); capped so that h -> 0 gives a finite, huge
+// friction factor (q' -> 0) and q = 0 still gives exactly zero friction.
+__device__ __forceinline__ float inv_h73(float h)
+{
+    return fminf(exp2f(__fmul_rn(-2.33333333f, __log2f(h))), 1.0e30f);
+}
+
+// Eq. 2 given the flow depth hf, dx * S_surf (dS), the old flux q and the
+// link roughness: q' = (q - g hf dt S) / (1 + g n^2 |q| dt / hf^(7/3)).
+__device__ __forceinline__ float eq2(float hf, float dS, float q, float n_link, const FaceK& k)
+{
+    const float num = __fmaf_rn(-__fmul_rn(k.gdt_dx, hf), dS, q);
+    const float c = __fmul_rn(__fmul_rn(k.gdt, __fmul_rn(n_link, n_link)), fabsf(q));
+    const float fr = __fmul_rn(c, inv_h73(hf));
+    return __fdividef(num, __fadd_rn(1.0f, fr));
+}
+
 // Eq. 3 then Eq. 2 on one interior link (cell 1 on the low-index side, cell
 // 2 on the high-index side; positive flow from 1 to 2), then the
-// quarter-volume limiter.  No flow where the flow depth is not above h_eps
-// (0 by default: Eq. 2-3 as printed).  The friction term is exactly zero for
-// q = 0, and an underflowed h^(7/3) with q != 0 gives q' = 0, never NaN.  Every operation is an explicitly rounded
-// intrinsic, so a link computed twice (by the tile that owns it and, as a
+// quarter-volume limiter.  No flow unless the flow depth exceeds h_eps (0 by
+// default: Eq. 2-3 as printed).  Straight-line code of explicitly rounded
+// intrinsics, so a link computed twice (by the tile that owns it and, as a
 // halo, by its neighbour) gives bit-identical values and the update stays
 // exactly conservative.
 __device__ __forceinline__ float link_q(float h1, float z1, float h2, float z2, float q,
                                         float n_link, const FaceK& k)
 {
-    float zm = fmaxf(z1, z2);
+    const float zm = fmaxf(z1, z2);
     // h_flow = max(eta1, eta2) - max(z1, z2), formed from bed differences so
     // the large bed elevation cancels exactly
-    float hf = fmaxf(__fadd_rn(h1, __fsub_rn(z1, zm)), __fadd_rn(h2, __fsub_rn(z2, zm)));
-    if (!(hf > k.h_eps)) return 0.0f;
+    const float hf = fmaxf(__fadd_rn(h1, __fsub_rn(z1, zm)), __fadd_rn(h2, __fsub_rn(z2, zm)));
     // dx * S_surf = (z2 - z1) + (h2 - h1)
-    float dS = __fadd_rn(__fsub_rn(z2, z1), __fsub_rn(h2, h1));
-    float num = __fsub_rn(q, __fmul_rn(__fmul_rn(k.gdt_dx, hf), dS));
-    float h73 = __fmul_rn(__fmul_rn(hf, hf), cbrtf(hf));
-    float fr = (q == 0.0f) ? 0.0f
-                           : __fdiv_rn(__fmul_rn(__fmul_rn(k.gdt, __fmul_rn(n_link, n_link)), fabsf(q)), h73);
-    float qn = __fdiv_rn(num, __fadd_rn(1.0f, fr));
+    const float dS = __fadd_rn(__fsub_rn(z2, z1), __fsub_rn(h2, h1));
+    float qn = eq2(hf, dS, q, n_link, k);
     if (k.limiter) {
-        float lim = __fmul_rn(qn > 0.0f ? h1 : h2, k.dx_4dt);
+        const float lim = __fmul_rn(qn > 0.0f ? h1 : h2, k.dx_4dt);
         qn = fminf(fmaxf(qn, -lim), lim);
     }
-    return qn;
+    return hf > k.h_eps ? qn : 0.0f;
 }
 
 // Free-outflow edge link: a ghost cell continuing the bed at the edge slope
@@ -133,14 +145,9 @@ __device__ __forceinline__ float link_q(float h1, float z1, float h2, float z2, 
 // only outward flow passes.
 __device__ __forceinline__ float outflow_q(float h, float q, float n_cell, const FaceK& k)
 {
-    if (!(h > k.h_eps)) return 0.0f;
-    float num = __fadd_rn(q, __fmul_rn(__fmul_rn(k.gdt_dx, h), k.edge_drop));
-    float h73 = __fmul_rn(__fmul_rn(h, h), cbrtf(h));
-    float fr = (q == 0.0f) ? 0.0f
-                           : __fdiv_rn(__fmul_rn(__fmul_rn(k.gdt, __fmul_rn(n_cell, n_cell)), fabsf(q)), h73);
-    float qn = __fdiv_rn(num, __fadd_rn(1.0f, fr));
+    float qn = eq2(h, -k.edge_drop, q, n_cell, k);
     if (k.limiter) qn = fminf(qn, __fmul_rn(h, k.dx_4dt));
-    return fmaxf(qn, 0.0f);
+    return h > k.h_eps ? fmaxf(qn, 0.0f) : 0.0f;
 }
 
 __device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }

@@ -38,7 +38,10 @@ __device__ __forceinline__ void store4(float* p, const float (&v)[4])
 }
 
 template <int WM, int WC>
-__global__ void __launch_bounds__(32 * WM * WC) step_kernel(const StepArgs a)
+#ifndef FLOOD_STEP_MIN_BLOCKS
+#define FLOOD_STEP_MIN_BLOCKS 8
+#endif
+__global__ void __launch_bounds__(32 * WM * WC, FLOOD_STEP_MIN_BLOCKS) step_kernel(const StepArgs a)
 {
     const int lane = threadIdx.x;
     const int wm = threadIdx.y % WM;
@@ -258,18 +261,34 @@ int step_nslot(int ny, int nx, int rows_per_strip)
     return ((ny + rows_per_strip - 1) / rows_per_strip) * ((nx + kSpan - 1) / kSpan);
 }
 
-// launch_mode 0: WM=4 members x 1 span per CTA (ensembles); 1: 1 member x 4
-// spans (single members).
-void launch_step(const StepArgs& a, int launch_mode, cudaStream_t s)
+// members_per_cta: warps of one CTA hold this many members of the same span
+// (1: one member over 4 spans, for single members; 2: 2 members x 2 spans;
+// 4 or 8: 4 or 8 members of one span).
+void launch_step(const StepArgs& a, int members_per_cta, cudaStream_t s)
 {
     const int spans = (a.nx + kSpan - 1) / kSpan;
     const int strips = (a.ny + a.rows_per_strip - 1) / a.rows_per_strip;
-    if (launch_mode == 0) {
+    switch (members_per_cta) {
+    case 8: {
+        dim3 grid((a.M + 7) / 8, spans, strips), block(32, 8);
+        step_kernel<8, 1><<<grid, block, 0, s>>>(a);
+        break;
+    }
+    case 4: {
         dim3 grid((a.M + 3) / 4, spans, strips), block(32, 4);
         step_kernel<4, 1><<<grid, block, 0, s>>>(a);
-    } else {
+        break;
+    }
+    case 2: {
+        dim3 grid((a.M + 1) / 2, (spans + 1) / 2, strips), block(32, 4);
+        step_kernel<2, 2><<<grid, block, 0, s>>>(a);
+        break;
+    }
+    default: {
         dim3 grid(a.M, (spans + 3) / 4, strips), block(32, 4);
         step_kernel<1, 4><<<grid, block, 0, s>>>(a);
+        break;
+    }
     }
 }
 

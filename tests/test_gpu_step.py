@@ -214,3 +214,27 @@ def test_bad_arguments_raise(capi):
             g.pf_assimilate(np.zeros(1), 0.05, 1.5, np.ones(2, np.float32))  # u outside [0,1)
         with pytest.raises(capi.FloodError):
             g.get_state(2)
+
+
+def test_launch_shapes_give_bitwise_identical_results(capi):
+    """The step kernel's launch shape (rows per strip, members per CTA) moves
+    halo recomputation around but never changes a value."""
+    terr = synth.make_terrain(70, 300, seed=14)
+    hy = synth.hyetograph_constant(120.0, 300.0)
+    rm, sc = synth.ensemble_prior(14, 5)
+    res = []
+    for shape in [(0, 0), (1, 1), (3, 2), (16, 4), (64, 8), (128, 1)]:
+        with capi.Grid(terr.z, terr.n) as g:
+            g.ensemble_init(5, rm, sc, hy)
+            g.set_launch(*shape)
+            g.advance_to(90.0)
+            g.set_launch(0, 0)
+            g.advance_to(180.0)
+            res.append(([g.get_state(m) for m in range(5)], g.volumes()))
+    for states, vol in res[1:]:
+        for m in range(5):
+            for k in range(3):
+                assert np.array_equal(states[m][k], res[0][0][m][k])
+        for key in ("storage", "rain"):
+            assert np.array_equal(vol[key], res[0][1][key])
+        assert np.allclose(vol["outflow"], res[0][1]["outflow"], rtol=1e-12, atol=0)

@@ -11,6 +11,7 @@ import subprocess
 import sys
 
 import oracle
+from tests import test_oracle_adjoint as A
 from tests import test_oracle_pf as P
 from tests import test_oracle_scheme as S
 
@@ -34,6 +35,12 @@ PINS = [
     functools.partial(P.test_systematic_resampling_brute_force, M=5),
     P.test_one_hot_weights_select_one_particle,
     P.test_slot_assignment_keeps_survivors_in_place,
+    A.test_gradients_match_central_differences_fully_wet,
+    functools.partial(A.test_dot_product_identity_per_step, regime="wet"),
+    functools.partial(A.test_dot_product_identity_per_step, regime="limited"),
+    functools.partial(A.test_dot_product_identity_per_step, regime="drying"),
+    functools.partial(A.test_dot_product_identity_per_step, regime="outflow"),
+    A.test_closed_form_uniform_rain_on_flat_box,
 ]
 
 # (name, original text, planted mistake)
@@ -71,6 +78,23 @@ MUTATIONS = [
      "double uj = u + (double)j / (double)M;"),
     ("resampling picks zero-weight ties", "c[i] <= uj) ++i;", "c[i] < uj) ++i;"),
     ("survivor slots not kept", "if (k[s] >= 1) {", "if (k[s] >= 2) {"),
+    ("adjoint friction exponent", "-(7.0 / 3.0) * fric / hflow", "-(4.0 / 3.0) * fric / hflow"),
+    ("adjoint slope sign", "*d_h1 = (first ? dq_dhf : 0.0) - dq_dS / p->dx;",
+     "*d_h1 = (first ? dq_dhf : 0.0) + dq_dS / p->dx;"),
+    ("adjoint clamp passes sensitivity", "lt[IX(r, c)] = hpre < 0.0 ? 0.0 : lh[IX(r, c)];",
+     "lt[IX(r, c)] = lh[IX(r, c)];"),
+    ("adjoint limiter on the wrong cell", "*d_h1 = p->dx / (4.0 * dt);\n            return lim;",
+     "*d_h2 = p->dx / (4.0 * dt);\n            return lim;"),
+    ("adjoint continuity without dt/dx", "double mu = lqx[IQX(r, c)] - T * lt[IX(r, c - 1)]",
+     "double mu = lqx[IQX(r, c)] - lt[IX(r, c - 1)]"),
+    ("adjoint Manning gradient without scale",
+     "grad_n[IX(r, c - 1)] += mu * dd[3] * scale * 0.5;\n                grad_n[IX(r, c)] += mu * dd[3] * scale * 0.5;",
+     "grad_n[IX(r, c - 1)] += mu * dd[3] * 0.5;\n                grad_n[IX(r, c)] += mu * dd[3] * 0.5;"),
+    ("adjoint ghost depth ignored", "dd[0] = a + b;   /* the ghost carries the edge depth */",
+     "dd[0] = a;"),
+    ("adjoint loss without the 2", "lh[cells[g]] += 2.0 * (hk1[cells[g]]",
+     "lh[cells[g]] += (hk1[cells[g]]"),
+    ("adjoint rain without dt", "gr += lt[IX(r, c)] * dt * rate;", "gr += lt[IX(r, c)] * rate;"),
 ]
 
 
@@ -94,8 +118,10 @@ def test_pins_catch_every_planted_mistake(tmp_path):
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     jobs = []
     for k, (name, orig, bad) in enumerate(MUTATIONS):
-        assert src.count(orig) == 1, f"mutation anchor for {name!r} not unique"
-        path = oracle.compile_variant(src.replace(orig, bad), str(tmp_path / f"libmut{k}.so"))
+        # the first occurrence is planted (the forward link flux comes before
+        # its differentiated copy in the adjoint section)
+        assert src.count(orig) >= 1, f"mutation anchor for {name!r} not found"
+        path = oracle.compile_variant(src.replace(orig, bad, 1), str(tmp_path / f"libmut{k}.so"))
         jobs.append((name, path))
 
     def run(job):
