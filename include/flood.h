@@ -45,7 +45,7 @@ enum {
     FLOOD_ERR_ARG = -1,      /* invalid argument (size, pointer, range)        */
     FLOOD_ERR_CUDA = -2,     /* a CUDA runtime call failed                     */
     FLOOD_ERR_OOM = -3,      /* device allocation failed                       */
-    FLOOD_ERR_TIMEOUT = -4,  /* a bounded device wait gave up                  */
+    FLOOD_ERR_TIMEOUT = -4,  /* a bounded device wait (staged tiles) gave up    */
     FLOOD_ERR_NAN = -5,      /* a kernel produced a non-finite depth           */
     FLOOD_ERR_STATE = -6     /* call out of order (e.g. step before init)      */
 };
@@ -179,6 +179,42 @@ int pf_assimilate(flood_grid* g, int n_gauges, const float* y, const double* d,
  */
 int pf_resample_systematic(int n, const double* w, double u, int32_t* idx, void* stream);
 
+/* Observations of a gauge-misfit loss (adjoint, extension beyond the paper). */
+typedef struct {
+    int32_t n_samples;     /* observation times t0 + s * sample_dt, s = 1..n_samples      */
+    int32_t n_gauges;
+    double sample_dt;      /* seconds between observations (> 0)                         */
+    const int32_t* cells;  /* [n_gauges] flat cell indices r * nx + c (host or device)    */
+    const double* d;       /* [n_samples][n_gauges] observed depths (host or device)      */
+} flood_loss_spec;
+
+/*
+ * flood_adjoint -- gradients by reverse mode (extension: the paper has no
+ * adjoint).  All members must be at the same time t0.  The ensemble advances
+ * through [t0, t0 + n_samples * sample_dt] exactly as flood_step would (it is
+ * at the window's end afterwards), and for every member i the loss
+ *     L_i = sum_s sum_k (h_i(t_s)[cells[k]] - d[s][k])^2
+ * is differentiated with the step lengths held at the recorded schedule and
+ * the derivative of the branch taken at every kink (Eq. 3's max, limiter,
+ * wet/dry test, outflow clip, negative-depth clamp).  Memory: a checkpoint
+ * every ckpt_every steps (0: about sqrt(steps)) plus ckpt_every + 1 replayed
+ * states, each 12 bytes per cell per member.
+ *   grad_n      [ny][nx] FP32  sum_i dL_i/dn_base (or NULL)
+ *   grad_rain   [N] FP64       dL_i/d(rain multiplier of i) (or NULL)
+ *   grad_scale  [N] FP64       dL_i/d(Manning scale of i) (or NULL)
+ *   grad_h0     [N][ny][nx] FP32 dL_i/dh_i(t0) (or NULL)
+ *   loss_out    [N] FP64       L_i (or NULL)
+ * Synchronous.  Errors: FLOOD_ERR_ARG, FLOOD_ERR_STATE (members at different
+ * times), FLOOD_ERR_OOM, FLOOD_ERR_NAN, FLOOD_ERR_TIMEOUT.
+ */
+int flood_adjoint(flood_grid* g, const flood_loss_spec* loss, int ckpt_every, float* grad_n,
+                  double* grad_rain, double* grad_scale, float* grad_h0, double* loss_out,
+                  void* stream);
+
+/* Device time (ms, CUDA events) of the last flood_adjoint's forward pass
+ * (with checkpointing) and of its reverse pass (replay included). */
+int flood_adjoint_timing(const flood_grid* g, double* forward_ms, double* reverse_ms);
+
 /* Copy member m's state out / in: h, qx, qy as [ny][nx] FP32 in the link
  * convention above (any may be NULL).  Asynchronous. */
 int flood_get_state(flood_grid* g, int member, float* h, float* qx, float* qy, void* stream);
@@ -223,6 +259,11 @@ int flood_profile(flood_grid* g, int enable, double* step_kernel_ms, int64_t* st
  * on it (bitwise).  Errors: FLOOD_ERR_ARG. */
 int flood_set_launch(flood_grid* g, int rows_per_strip, int members_per_cta);
 int flood_get_launch(const flood_grid* g, int* rows_per_strip, int* members_per_cta);
+
+/* Step-kernel engine: 0 = direct float4 loads, 1 = rows staged through shared
+ * memory by the tensor memory accelerator (default where available).  Both
+ * give identical results.  Errors: FLOOD_ERR_ARG. */
+int flood_set_engine(flood_grid* g, int engine);
 
 /* Wait for `stream`, then report device-side faults of the method: returns
  * FLOOD_ERR_NAN if any step produced a non-finite depth. */

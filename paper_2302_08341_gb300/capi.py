@@ -24,13 +24,20 @@ EXPORTED = ["flood_default_params", "flood_last_error", "flood_create_grid", "fl
             "flood_ensemble_init", "flood_step", "flood_gauge_sample", "pf_assimilate",
             "pf_resample_systematic", "flood_get_state", "flood_set_state", "flood_get_members",
             "flood_set_members", "flood_volume_report", "flood_launch_count", "flood_sync",
-            "flood_profile", "flood_set_launch", "flood_get_launch"]
+            "flood_profile", "flood_set_launch", "flood_get_launch", "flood_set_engine",
+            "flood_adjoint", "flood_adjoint_timing"]
 
 
 class FloodError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
         self.code = code
+
+
+class LossSpec(C.Structure):
+    """flood_loss_spec (include/flood.h)."""
+    _fields_ = [("n_samples", C.c_int32), ("n_gauges", C.c_int32), ("sample_dt", C.c_double),
+                ("cells", C.c_void_p), ("d", C.c_void_p)]
 
 
 class Params(C.Structure):
@@ -89,6 +96,9 @@ def lib(path: str = LIB_PATH):
     L.flood_profile.argtypes = [_VP, C.c_int, _VP, _VP]
     L.flood_set_launch.argtypes = [_VP, C.c_int, C.c_int]
     L.flood_get_launch.argtypes = [_VP, _VP, _VP]
+    L.flood_set_engine.argtypes = [_VP, C.c_int]
+    L.flood_adjoint.argtypes = [_VP, C.POINTER(LossSpec), C.c_int, _VP, _VP, _VP, _VP, _VP, _VP]
+    L.flood_adjoint_timing.argtypes = [_VP, _VP, _VP]
     for name in EXPORTED:
         if name not in ("flood_default_params", "flood_last_error", "flood_launch_count"):
             getattr(L, name).restype = C.c_int
@@ -295,6 +305,10 @@ class Grid:
         """Step-kernel launch shape; (0, 0) = automatic."""
         _check(lib().flood_set_launch(self.h, int(rows_per_strip), int(members_per_cta)), self.h)
 
+    def set_engine(self, engine):
+        """0: direct loads, 1: TMA-staged tiles (identical results)."""
+        _check(lib().flood_set_engine(self.h, int(engine)), self.h)
+
     def get_launch(self):
         r = C.c_int(); m = C.c_int()
         _check(lib().flood_get_launch(self.h, C.byref(r), C.byref(m)), self.h)
@@ -306,6 +320,27 @@ class Grid:
         ms = C.c_double(); n = C.c_int64()
         _check(lib().flood_profile(self.h, int(bool(enable)), C.byref(ms), C.byref(n)), self.h)
         return ms.value, n.value
+
+    def adjoint(self, cells, d, sample_dt, ckpt_every=0, grad_n=True, grad_h0=True, stream=None):
+        """Gauge-misfit loss per member over the observation window and its
+        gradients (flood_adjoint).  d: [n_samples][n_gauges] observed depths
+        at t0 + s * sample_dt.  Returns a dict of host arrays."""
+        cells = np.ascontiguousarray(cells, dtype=np.int32)
+        d = np.ascontiguousarray(d, dtype=np.float64)
+        ns, G = d.shape
+        spec = LossSpec(ns, G, float(sample_dt), cells.ctypes.data, d.ctypes.data)
+        M = self.M
+        out = dict(loss=np.zeros(M), grad_rain=np.zeros(M), grad_scale=np.zeros(M),
+                   grad_n=np.zeros((self.ny, self.nx), np.float32) if grad_n else None,
+                   grad_h0=np.zeros((M, self.ny, self.nx), np.float32) if grad_h0 else None)
+        _check(lib().flood_adjoint(self.h, C.byref(spec), int(ckpt_every), ptr(out["grad_n"]),
+                                   ptr(out["grad_rain"]), ptr(out["grad_scale"]),
+                                   ptr(out["grad_h0"]), ptr(out["loss"]), stream_handle(stream)),
+               self.h)
+        f = C.c_double(); r = C.c_double()
+        _check(lib().flood_adjoint_timing(self.h, C.byref(f), C.byref(r)), self.h)
+        out["forward_ms"], out["reverse_ms"] = f.value, r.value
+        return out
 
     @property
     def launch_count(self):

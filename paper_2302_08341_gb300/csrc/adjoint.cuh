@@ -1,0 +1,36 @@
+// Reverse-mode kernels of the step (adjoint_kernel.cu).
+#pragma once
+
+#include "flood_internal.cuh"
+
+namespace flood {
+
+struct AdjArgs {
+    const float* seg;        // [slots][M][3][plane] forward states of the segment
+    float* lam;              // [2][M][3][plane] sensitivities (h, qx, qy)
+    int lam_in;              // buffer holding the sensitivities to the step's outputs
+    float* gn;               // [M][plane] per-member dL/dn_base (or null)
+    double* gpart;           // [M][nslot][2] per-warp partials of dL/d(rain mult), dL/d(scale)
+    const float* z;
+    const float* n;
+    const float* scale;      // [M]
+    const double* dt_log;    // [M][dt_log_cap]
+    const double* rdt_log;   // [M][dt_log_cap] dt x block rain rate
+    const int* seg_end;      // [M] first step index past this segment, per member
+    int dt_log_cap;
+    int seg_first;           // step index whose input state sits in slot 0
+    int rev_i;               // this launch handles step seg_end[m] - 1 - rev_i of member m
+    size_t plane;
+    int ny, nx, ld, M, rows_per_strip, nslot;
+    double g, dxd;
+    float h_eps, edge_drop;
+    int limiter, east_out, south_out;
+};
+
+void launch_adjoint(const AdjArgs& a, int members_per_cta, cudaStream_t s);
+void launch_seed(const AdjArgs& a, const int32_t* sample_step, const float* y, const double* d,
+                 const int32_t* cells, int ns, int G, cudaStream_t s);
+void launch_reduce_members(const float* gm, int M, int ny, int nx, int ld, size_t plane, float* out,
+                           cudaStream_t s);
+
+}  // namespace flood

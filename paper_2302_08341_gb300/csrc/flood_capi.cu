@@ -9,69 +9,41 @@
 #include <string>
 #include <vector>
 
-#include "flood_internal.cuh"
+#include "grid.cuh"
 #include "pf_kernels.cuh"
+#include "tma.cuh"
 
 using flood::MemberClock;
 
-struct flood_grid {
-    int ny = 0, nx = 0, ld = 0;
-    size_t plane = 0;
-    flood_params p{};
-    float* z = nullptr;
-    float* n = nullptr;
-    int n_sm = 0;
-    // ensemble
-    int M = 0, nb = 0;
-    float* state = nullptr;       // [2][M][3][plane]
-    float* rain_mult = nullptr;   // [M]
-    float* scale = nullptr;       // [M]
-    float* hyeto = nullptr;       // [nb]
-    double* w = nullptr;          // [M]
-    double* w_post = nullptr;     // [M]
-    MemberClock* ms = nullptr;    // [3][M]
-    double* vacc = nullptr;       // [M][nslot][2]
-    int nslot = 0;
-    double* rain_acc = nullptr;   // [M]
-    int* err = nullptr;           // device error word
-    int rows_per_strip = 64;
-    int members_per_cta = 4;
-    bool launch_fixed = false;    // set by flood_set_launch
-    // particle filter
-    int G = 0, G_cap = 0;
-    int32_t* cells = nullptr;     // [G_cap]
-    float* y = nullptr;           // [M][G_cap] last gauge sample
-    float* y_in = nullptr;        // [M][G_cap] caller-supplied outputs
-    double* d = nullptr;          // [G_cap]
-    double* sigma = nullptr;      // [G_cap]
-    float* beta = nullptr;        // [M]
-    int32_t* pfi = nullptr;       // idx, src, cnt, copy_dst, copy_src: 5 x [M]
-    int32_t* pf_small = nullptr;  // n_copy, resampled, status
-    double* neff = nullptr;       // [1]
-    double* part = nullptr;       // storage partials
-    int part_cap = 0;
-    double* storage = nullptr;    // [M]
-    int64_t k = 0;                // step launches so far (member-slot rotation)
-    int64_t launches = 0;         // all kernel launches
-    // optional per-launch timing of the step kernel (CUDA events on the
-    // launching stream)
-    bool profile = false;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free;
-    double prof_ms = 0.0;
-    int64_t prof_launches = 0;
-    std::string msg;
-};
-
 namespace {
-
 thread_local std::string g_static_msg;
+}  // namespace
+
+namespace flood {
 
 int fail(flood_grid* g, int code, const std::string& m)
 {
     if (g) g->msg = m; else g_static_msg = m;
     return code;
 }
+
+int dalloc_bytes(flood_grid* g, void** p, size_t bytes)
+{
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess)
+        return fail(g, e == cudaErrorMemoryAllocation ? FLOOD_ERR_OOM : FLOOD_ERR_CUDA,
+                    std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return FLOOD_OK;
+}
+
+}  // namespace flood
+
+using flood::fail;
+using flood::dalloc;
+
+namespace {
 
 #define CK(g, call)                                                                          \
     do {                                                                                     \
@@ -80,16 +52,6 @@ int fail(flood_grid* g, int code, const std::string& m)
             return fail((g), e_ == cudaErrorMemoryAllocation ? FLOOD_ERR_OOM : FLOOD_ERR_CUDA, \
                         std::string(#call) + ": " + cudaGetErrorString(e_));                 \
     } while (0)
-
-template <class T>
-int dalloc(flood_grid* g, T** p, size_t count)
-{
-    if (*p) cudaFree(*p);
-    *p = nullptr;
-    if (count == 0) count = 1;
-    CK(g, cudaMalloc((void**)p, sizeof(T) * count));
-    return FLOOD_OK;
-}
 
 void dfree(void* p)
 {
@@ -102,6 +64,14 @@ void free_ensemble(flood_grid* g)
     dfree(g->w_post); dfree(g->ms); dfree(g->vacc); dfree(g->rain_acc); dfree(g->y);
     dfree(g->y_in); dfree(g->beta); dfree(g->pfi); dfree(g->pf_small); dfree(g->neff);
     dfree(g->part); dfree(g->storage); dfree(g->cells); dfree(g->d); dfree(g->sigma);
+    dfree(g->dt_log); dfree(g->rdt_log); dfree(g->ckpt); dfree(g->seg); dfree(g->lam);
+    dfree(g->gnm); dfree(g->gn_out); dfree(g->gpart); dfree(g->seg_end); dfree(g->samp_step);
+    dfree(g->samp_y); dfree(g->samp_d); dfree(g->samp_cells);
+    g->dt_log = nullptr; g->rdt_log = nullptr; g->ckpt = nullptr; g->seg = nullptr;
+    g->lam = nullptr; g->gnm = nullptr; g->gn_out = nullptr; g->gpart = nullptr;
+    g->seg_end = nullptr; g->samp_step = nullptr; g->samp_y = nullptr; g->samp_d = nullptr;
+    g->samp_cells = nullptr; g->log_cap = 0; g->ckpt_floats = 0; g->seg_floats = 0;
+    g->logging = false;
     g->state = nullptr; g->rain_mult = nullptr; g->scale = nullptr; g->hyeto = nullptr;
     g->w = nullptr; g->w_post = nullptr; g->ms = nullptr; g->vacc = nullptr;
     g->rain_acc = nullptr; g->y = nullptr; g->y_in = nullptr; g->beta = nullptr;
@@ -112,7 +82,11 @@ void free_ensemble(flood_grid* g)
 
 cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-flood::StepArgs step_args(const flood_grid* g, double t_end)
+}  // namespace
+
+namespace flood {
+
+StepArgs step_args(const flood_grid* g, double t_end)
 {
     flood::StepArgs a{};
     a.state = g->state;
@@ -127,13 +101,16 @@ flood::StepArgs step_args(const flood_grid* g, double t_end)
     a.ms_clr = g->ms + ((k + 2) % 3) * g->M;
     a.vacc = g->vacc;
     a.rain_acc = g->rain_acc;
-    a.dt_log = nullptr;
+    a.dt_log = g->logging ? g->dt_log : nullptr;
+    a.rdt_log = g->logging ? g->rdt_log : nullptr;
+    a.dt_log_cap = g->log_cap;
+    a.ckpt = g->logging ? g->ckpt : nullptr;
+    a.ckpt_every = g->ckpt_every > 0 ? g->ckpt_every : 1;
     a.err = g->err;
     a.plane = g->plane;
     a.ny = g->ny; a.nx = g->nx; a.ld = g->ld; a.M = g->M; a.nb = g->nb;
     a.rows_per_strip = g->rows_per_strip;
     a.nslot = g->nslot;
-    a.dt_log_cap = 0;
     a.t_end = t_end;
     a.alpha_dx = g->p.alpha * g->p.dx;
     a.g = g->p.g;
@@ -182,7 +159,15 @@ int launch_steps(flood_grid* g, int64_t count, double t_end, cudaStream_t s)
             }
             CK(g, cudaEventRecord(ev.first, s));
         }
-        flood::launch_step(a, g->members_per_cta, s);
+        if (g->engine == 1 && g->maps_ok) {
+            flood::TmaArgs t;
+            t.state_map = g->state_map;
+            t.static_map = g->static_map;
+            t.a = a;
+            flood::launch_step_tma(t, g->members_per_cta, s);
+        } else {
+            flood::launch_step(a, g->members_per_cta, s);
+        }
         if (g->profile) {
             CK(g, cudaEventRecord(ev.second, s));
             g->ev_pending.push_back(ev);
@@ -194,6 +179,15 @@ int launch_steps(flood_grid* g, int64_t count, double t_end, cudaStream_t s)
     return FLOOD_OK;
 }
 
+int check_err(flood_grid* g)
+{
+    int err = 0;
+    CK(g, cudaMemcpy(&err, g->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err & 2) return fail(g, FLOOD_ERR_TIMEOUT, "a bounded wait for staged tiles gave up");
+    if (err) return fail(g, FLOOD_ERR_NAN, "a kernel produced a non-finite depth");
+    return FLOOD_OK;
+}
+
 int read_clocks(flood_grid* g, std::vector<MemberClock>& out, cudaStream_t s)
 {
     out.resize(g->M);
@@ -201,10 +195,7 @@ int read_clocks(flood_grid* g, std::vector<MemberClock>& out, cudaStream_t s)
                           cudaMemcpyDeviceToHost, s));
     CK(g, cudaStreamSynchronize(s));
     collect_profile(g);
-    int err = 0;
-    CK(g, cudaMemcpy(&err, g->err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (err) return fail(g, FLOOD_ERR_NAN, "a kernel produced a non-finite depth");
-    return FLOOD_OK;
+    return check_err(g);
 }
 
 // Grow the per-warp volume slots when a launch shape with more warp tasks
@@ -226,6 +217,15 @@ int ensure_vacc(flood_grid* g, int need)
     g->nslot = need;
     return FLOOD_OK;
 }
+
+}  // namespace flood
+
+using flood::launch_steps;
+using flood::read_clocks;
+using flood::collect_profile;
+using flood::ensure_vacc;
+
+namespace {
 
 int choose_rows_per_strip(int ny, int nx, int M, int n_sm)
 {
@@ -284,14 +284,14 @@ int flood_create_grid(flood_grid** out, int ny, int nx, const float* z, const fl
     cudaDeviceGetAttribute(&g->n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (g->n_sm <= 0) g->n_sm = 1;
     int rc;
-    if ((rc = dalloc(g, &g->z, g->plane)) || (rc = dalloc(g, &g->n, g->plane)) ||
-        (rc = dalloc(g, &g->err, 1))) {
+    if ((rc = dalloc(g, &g->zn, 2 * g->plane)) || (rc = dalloc(g, &g->err, 1))) {
         g_static_msg = g->msg;
         flood_destroy(g);
         return rc;
     }
-    cudaError_t e = cudaMemset(g->z, 0, sizeof(float) * g->plane);
-    if (e == cudaSuccess) e = cudaMemset(g->n, 0, sizeof(float) * g->plane);
+    g->z = g->zn;
+    g->n = g->zn + g->plane;
+    cudaError_t e = cudaMemset(g->zn, 0, sizeof(float) * 2 * g->plane);
     if (e == cudaSuccess) e = cudaMemset(g->err, 0, sizeof(int));
     if (e == cudaSuccess)
         e = cudaMemcpy2D(g->z, sizeof(float) * g->ld, z, sizeof(float) * nx, sizeof(float) * nx, ny,
@@ -304,6 +304,9 @@ int flood_create_grid(flood_grid** out, int ny, int nx, const float* z, const fl
         flood_destroy(g);
         return FLOOD_ERR_CUDA;
     }
+    if (flood::encode_map_3d(&g->static_map, g->zn, g->ld, g->ny, 2, sizeof(float) * g->ld,
+                             sizeof(float) * g->plane, flood::tma_box_cols(), 1, 2) != 0)
+        g->engine = 0;  // no tensor-map encoder: direct loads only
     *out = g;
     return FLOOD_OK;
 }
@@ -318,8 +321,7 @@ int flood_destroy(flood_grid* g)
         cudaEventDestroy(p.second);
     }
     free_ensemble(g);
-    dfree(g->z);
-    dfree(g->n);
+    dfree(g->zn);
     dfree(g->err);
     delete g;
     return FLOOD_OK;
@@ -358,6 +360,9 @@ int flood_ensemble_init(flood_grid* g, int M, const float* h0, int h0_per_member
         return rc;
     }
     CK(g, cudaMemsetAsync(g->state, 0, sizeof(float) * 2 * (size_t)M * 3 * g->plane, s));
+    g->maps_ok = flood::encode_map_3d(&g->state_map, g->state, g->ld, g->ny, (uint64_t)2 * M * 3,
+                                      sizeof(float) * g->ld, sizeof(float) * g->plane,
+                                      flood::tma_box_cols(), 1, 3) == 0;
     if (h0) {
         for (int m = 0; m < M; ++m) {
             const float* src = h0 + (h0_per_member ? (size_t)m * g->ny * g->nx : 0);
@@ -423,6 +428,8 @@ int flood_step(flood_grid* g, int n_steps, double t_end, void* stream)
             need = std::max(need, (int64_t)std::ceil((t_end - c[m].t) / dt) + edges);
         }
         if (need == 0) break;
+        if (need > (int64_t)1 << 26)
+            return fail(g, FLOOD_ERR_STATE, "reaching t_end would take more than 2^26 steps");
         if (n_steps > 0) need = std::min<int64_t>(need, n_steps - done);
         if (need <= 0) break;
         if ((rc = launch_steps(g, need, t_end, s))) return rc;
@@ -705,6 +712,14 @@ int flood_set_launch(flood_grid* g, int rows_per_strip, int members_per_cta)
     return FLOOD_OK;
 }
 
+int flood_set_engine(flood_grid* g, int engine)
+{
+    if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    if (engine != 0 && engine != 1) return fail(g, FLOOD_ERR_ARG, "engine must be 0 or 1");
+    g->engine = engine;
+    return FLOOD_OK;
+}
+
 int flood_get_launch(const flood_grid* g, int* rows_per_strip, int* members_per_cta)
 {
     if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
@@ -717,10 +732,7 @@ int flood_sync(flood_grid* g, void* stream)
 {
     if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
     CK(g, cudaStreamSynchronize(S(stream)));
-    int err = 0;
-    CK(g, cudaMemcpy(&err, g->err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (err) return fail(g, FLOOD_ERR_NAN, "a kernel produced a non-finite depth");
-    return FLOOD_OK;
+    return flood::check_err(g);
 }
 
 }  // extern "C"

@@ -1,6 +1,7 @@
 // Internal definitions shared by the CUDA translation units of libflood.so.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,6 +35,16 @@ struct StepArgs {
     double* vacc;               // [M][nslot][2] outflow and clamp partial volumes
     double* rain_acc;           // [M] rain volume added
     double* dt_log;             // [M][dt_log_cap] step lengths (or null)
+    double* rdt_log;            // [M][dt_log_cap] dt x block rain rate of each step (or null)
+    float* ckpt;                // [n_ckpt][M][3][plane] checkpoint states (or null)
+    int ckpt_every;             // a checkpoint after every ckpt_every steps of a member
+    // replay of a checkpointed segment (adjoint recomputation): slot i of
+    // seg holds the state after step seg_first + i; this launch recomputes
+    // step seg_first + replay_i of every member with seg_first + replay_i <
+    // seg_end[m], with the recorded step length and rain
+    float* seg;                 // [slots][M][3][plane]
+    const int* seg_end;         // [M]
+    int seg_first, replay_i;
     int* err;                   // device error word (bit 0: non-finite depth)
     size_t plane;               // ny * ld
     int ny, nx, ld, M, nb;
@@ -51,10 +62,20 @@ struct StepArgs {
     int limiter, east_out, south_out;
 };
 
+// Arguments of the TMA-staged step kernel: tensor maps of the two state
+// buffers ([2 M 3] planes of [ny][ld]) and of the static fields ([z, n]
+// planes), 3-D tiles of 136 columns x 1 row x (3 or 2) planes.
+struct TmaArgs {
+    CUtensorMap state_map;
+    CUtensorMap static_map;
+    StepArgs a;
+};
+
 // Step length of one member (Eq. 4 with floor, cap and landing on the next
 // stop).  Every CTA of a member evaluates this identically in FP64.
 struct StepPlan {
     double dt, t_next;
+    double rdt;        // dt x rain rate of the block (m), before the member's multiplier
     float dr;          // rain depth added to every cell this step (m)
     bool active;
 };
@@ -84,7 +105,8 @@ __device__ __forceinline__ StepPlan plan_step(const StepArgs& a, const MemberClo
     s.dt = dt;
     int b = (int)blk;
     double rate = (blk >= 0.0 && b < a.nb) ? (double)a.hyeto[b] : 0.0;
-    s.dr = (float)__dmul_rn(__dmul_rn(dt, rate), (double)a.rain_mult[m]);
+    s.rdt = __dmul_rn(dt, rate);
+    s.dr = (float)__dmul_rn(s.rdt, (double)a.rain_mult[m]);
     return s;
 }
 
@@ -153,7 +175,10 @@ __device__ __forceinline__ float outflow_q(float h, float q, float n_cell, const
 __device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
 
 // Host-side helpers (flood_capi.cu).
-void launch_step(const StepArgs& a, int launch_mode, cudaStream_t s);
+void launch_step(const StepArgs& a, int members_per_cta, cudaStream_t s);
+void launch_replay(const StepArgs& a, int members_per_cta, cudaStream_t s);
+int launch_step_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s);
+int tma_box_cols();
 int step_nslot(int ny, int nx, int rows_per_strip);
 
 }  // namespace flood

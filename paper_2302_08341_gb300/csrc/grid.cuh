@@ -1,0 +1,109 @@
+// Internal: the grid handle behind the C ABI and host helpers shared by
+// flood_capi.cu and adjoint_capi.cu.
+#pragma once
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "flood_internal.cuh"
+
+struct flood_grid {
+    int ny = 0, nx = 0, ld = 0;
+    size_t plane = 0;
+    flood_params p{};
+    float* zn = nullptr;          // [2][ny][ld]: z plane then n plane
+    float* z = nullptr;           // = zn
+    float* n = nullptr;           // = zn + plane
+    int n_sm = 0;
+    int engine = 1;               // 0: direct loads, 1: TMA-staged tiles
+    CUtensorMap static_map{};
+    CUtensorMap state_map{};
+    bool maps_ok = false;
+    // ensemble
+    int M = 0, nb = 0;
+    float* state = nullptr;       // [2][M][3][plane]
+    float* rain_mult = nullptr;   // [M]
+    float* scale = nullptr;       // [M]
+    float* hyeto = nullptr;       // [nb]
+    double* w = nullptr;          // [M]
+    double* w_post = nullptr;     // [M]
+    flood::MemberClock* ms = nullptr;  // [3][M]
+    double* vacc = nullptr;       // [M][nslot][2]
+    int nslot = 0;
+    double* rain_acc = nullptr;   // [M]
+    int* err = nullptr;           // device error word
+    int rows_per_strip = 64;
+    int members_per_cta = 4;
+    bool launch_fixed = false;    // set by flood_set_launch
+    // particle filter
+    int G = 0, G_cap = 0;
+    int32_t* cells = nullptr;     // [G_cap]
+    float* y = nullptr;           // [M][G_cap] last gauge sample
+    float* y_in = nullptr;        // [M][G_cap] caller-supplied outputs
+    double* d = nullptr;          // [G_cap]
+    double* sigma = nullptr;      // [G_cap]
+    float* beta = nullptr;        // [M]
+    int32_t* pfi = nullptr;       // idx, src, cnt, copy_dst, copy_src: 5 x [M]
+    int32_t* pf_small = nullptr;  // n_copy, resampled, status
+    double* neff = nullptr;       // [1]
+    double* part = nullptr;       // storage partials
+    int part_cap = 0;
+    double* storage = nullptr;    // [M]
+    int64_t k = 0;                // step launches so far (member-slot rotation)
+    int64_t launches = 0;         // all kernel launches
+    // optional per-launch timing of the step kernel (CUDA events on the
+    // launching stream)
+    bool profile = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free;
+    double prof_ms = 0.0;
+    int64_t prof_launches = 0;
+    // adjoint (flood_adjoint): step log, checkpoints, segment replay buffers
+    double* dt_log = nullptr;     // [M][log_cap]
+    double* rdt_log = nullptr;    // [M][log_cap]
+    int log_cap = 0;
+    bool logging = false;         // step kernels record dt and checkpoints
+    float* ckpt = nullptr;        // [n_ckpt][M][3][plane]
+    size_t ckpt_floats = 0;
+    int ckpt_every = 0;
+    float* seg = nullptr;         // [slots][M][3][plane]
+    size_t seg_floats = 0;
+    float* lam = nullptr;         // [2][M][3][plane]
+    float* gnm = nullptr;         // [M][plane] per-member Manning gradients
+    float* gn_out = nullptr;      // [ny][nx]
+    double* gpart = nullptr;      // [M][nslot][2]
+    int* seg_end = nullptr;       // [M]
+    int32_t* samp_step = nullptr; // [ns][M]
+    float* samp_y = nullptr;      // [ns][M][G]
+    double* samp_d = nullptr;     // [ns][G]
+    int32_t* samp_cells = nullptr;
+    double adj_fwd_ms = 0.0, adj_rev_ms = 0.0;
+    std::string msg;
+};
+
+
+namespace flood {
+
+int fail(flood_grid* g, int code, const std::string& m);
+int dalloc_bytes(flood_grid* g, void** p, size_t bytes);
+template <class T>
+int dalloc(flood_grid* g, T** p, size_t count)
+{
+    return dalloc_bytes(g, reinterpret_cast<void**>(p), sizeof(T) * (count ? count : 1));
+}
+StepArgs step_args(const flood_grid* g, double t_end);
+int launch_steps(flood_grid* g, int64_t count, double t_end, cudaStream_t s);
+int read_clocks(flood_grid* g, std::vector<MemberClock>& out, cudaStream_t s);
+int check_err(flood_grid* g);
+void collect_profile(flood_grid* g);
+
+}  // namespace flood
+
+#define FLOOD_CK(g, call)                                                                    \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return flood::fail((g), e_ == cudaErrorMemoryAllocation ? FLOOD_ERR_OOM : FLOOD_ERR_CUDA, \
+                               std::string(#call) + ": " + cudaGetErrorString(e_));          \
+    } while (0)

@@ -216,7 +216,7 @@ __global__ void hmax_kernel(const float* __restrict__ state, MemberClock* __rest
     for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
          t += (size_t)gridDim.x * blockDim.x) {
         const size_t r = t / nx, c = t % nx;
-        best = max(best, __float_as_uint(fmaxf(h[r * ld + c], 0.0f)));
+        best = max(best, __float_as_uint(fmaxf(h[r * ld + c], 0.0f)) & 0x7fffffffu);
     }
     best = __reduce_max_sync(0xffffffffu, best);
     if ((threadIdx.x & 31) == 0) atomicMax(&ms[m].hmax_bits, best);

@@ -37,11 +37,15 @@ __device__ __forceinline__ void store4(float* p, const float (&v)[4])
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
-template <int WM, int WC>
 #ifndef FLOOD_STEP_MIN_BLOCKS
-#define FLOOD_STEP_MIN_BLOCKS 8
+#define FLOOD_STEP_MIN_BLOCKS 6
 #endif
-__global__ void __launch_bounds__(32 * WM * WC, FLOOD_STEP_MIN_BLOCKS) step_kernel(const StepArgs a)
+
+// REPLAY = false: an ordinary step (per-member clock, Eq. 4 step length,
+// reductions, optional logging and checkpoints).  REPLAY = true: recompute
+// a recorded step of a checkpointed segment, bit for bit, for the adjoint.
+template <int WM, int WC, bool REPLAY>
+__global__ void __launch_bounds__(32 * WM * WC, FLOOD_STEP_MIN_BLOCKS * 4 / (WM * WC)) step_kernel(const StepArgs a)
 {
     const int lane = threadIdx.x;
     const int wm = threadIdx.y % WM;
@@ -52,28 +56,46 @@ __global__ void __launch_bounds__(32 * WM * WC, FLOOD_STEP_MIN_BLOCKS) step_kern
     if (m >= a.M || c0 >= a.nx) return;  // whole warps only: no block barriers below
 
     const int nx = a.nx, ny = a.ny, ld = a.ld;
+    const size_t plane = a.plane;
+    const size_t mstride = 3 * plane;
     const bool designated = (blockIdx.y == 0 && blockIdx.z == 0 && wc == 0 && lane == 0);
-    const MemberClock in = a.ms_in[m];
-    const StepPlan sp = plan_step(a, in, m);
-    if (!sp.active) {
-        if (designated) {
-            a.ms_out[m] = in;
-            a.ms_clr[m].hmax_bits = 0u;
+    StepPlan sp;
+    const float* src;
+    float* dst;
+    float* ck = nullptr;
+    if (REPLAY) {
+        const int j = a.seg_first + a.replay_i;
+        if (j >= a.seg_end[m]) return;
+        sp.dt = a.dt_log[(size_t)m * a.dt_log_cap + j];
+        sp.rdt = a.rdt_log[(size_t)m * a.dt_log_cap + j];
+        sp.dr = (float)__dmul_rn(sp.rdt, (double)a.rain_mult[m]);
+        dst = a.seg + ((size_t)(a.replay_i + 1) * a.M + m) * mstride;
+        src = dst - (size_t)a.M * mstride;
+    } else {
+        const MemberClock in = a.ms_in[m];
+        sp = plan_step(a, in, m);
+        if (!sp.active) {
+            if (designated) {
+                a.ms_out[m] = in;
+                a.ms_clr[m].hmax_bits = 0u;
+            }
+            return;
         }
-        return;
-    }
-    if (designated) {
-        MemberClock o;
-        o.t = sp.t_next;
-        o.steps = in.steps + 1;
-        o.hmax_bits = 0u;  // filled by atomicMax below (slot was cleared)
-        o.cur = 1 - in.cur;
-        a.ms_out[m].t = o.t;
-        a.ms_out[m].steps = o.steps;
-        a.ms_out[m].cur = o.cur;
-        a.ms_clr[m].hmax_bits = 0u;
-        a.rain_acc[m] += (double)sp.dr * a.cell_area * a.ncell;
-        if (a.dt_log && in.steps < a.dt_log_cap) a.dt_log[(size_t)m * a.dt_log_cap + in.steps] = sp.dt;
+        if (designated) {
+            a.ms_out[m].t = sp.t_next;
+            a.ms_out[m].steps = in.steps + 1;
+            a.ms_out[m].cur = 1 - in.cur;  // hmax_bits: filled by atomicMax (slot was cleared)
+            a.ms_clr[m].hmax_bits = 0u;
+            a.rain_acc[m] += (double)sp.dr * a.cell_area * a.ncell;
+            if (a.dt_log && in.steps < a.dt_log_cap) {
+                a.dt_log[(size_t)m * a.dt_log_cap + in.steps] = sp.dt;
+                a.rdt_log[(size_t)m * a.dt_log_cap + in.steps] = sp.rdt;
+            }
+        }
+        src = a.state + (size_t)(in.cur * a.M + m) * mstride;
+        dst = a.state + (size_t)((1 - in.cur) * a.M + m) * mstride;
+        if (a.ckpt && (in.steps + 1) % a.ckpt_every == 0 && in.steps + 1 <= a.dt_log_cap)
+            ck = a.ckpt + ((size_t)((in.steps + 1) / a.ckpt_every) * a.M + m) * mstride;
     }
 
     FaceK k;
@@ -88,9 +110,6 @@ __global__ void __launch_bounds__(32 * WM * WC, FLOOD_STEP_MIN_BLOCKS) step_kern
     const float s_half = 0.5f * s;
     const float dr = sp.dr;
 
-    const size_t plane = a.plane;
-    const float* __restrict__ src = a.state + (size_t)(in.cur * a.M + m) * 3 * plane;
-    float* __restrict__ dst = a.state + (size_t)((1 - in.cur) * a.M + m) * 3 * plane;
     const float* __restrict__ sh = src;
     const float* __restrict__ sqx = src + plane;
     const float* __restrict__ sqy = src + 2 * plane;
@@ -210,8 +229,10 @@ __global__ void __launch_bounds__(32 * WM * WC, FLOOD_STEP_MIN_BLOCKS) step_kern
                 const float net = __fadd_rn(__fsub_rn(qW, qxE[j]), __fsub_rn(qyN[j], qyS[j]));
                 hn = __fadd_rn(__fmaf_rn(dt_dx, net, hC[j]), dr);
                 if (hn < 0.0f) {
+                    // clamped cells keep a negative zero: the adjoint reads
+                    // the sign bit to know this branch was taken
                     clamp_acc -= (double)hn;
-                    hn = 0.0f;
+                    hn = -0.0f;
                 }
                 bad |= !(hn <= 3.0e38f);  // NaN or overflow
                 hmax = fmaxf(hmax, hn);
@@ -224,6 +245,11 @@ __global__ void __launch_bounds__(32 * WM * WC, FLOOD_STEP_MIN_BLOCKS) step_kern
             store4(dh + o, hN);
             store4(dqx + o, qxE);
             store4(dqy + o, qyS);
+            if (ck) {
+                store4(ck + o, hN);
+                store4(ck + plane + o, qxE);
+                store4(ck + 2 * plane + o, qyS);
+            }
         }
         // march: this row's south links are the next row's north links
 #pragma unroll
@@ -237,7 +263,8 @@ __global__ void __launch_bounds__(32 * WM * WC, FLOOD_STEP_MIN_BLOCKS) step_kern
 
     // warp reductions: max depth (order-free), FP64 volumes in a fixed order
     if (bad) atomicOr(a.err, 1);
-    const unsigned hb = __reduce_max_sync(0xffffffffu, __float_as_uint(hmax));
+    if (REPLAY) return;
+    const unsigned hb = __reduce_max_sync(0xffffffffu, __float_as_uint(hmax) & 0x7fffffffu);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         out_acc += __shfl_xor_sync(0xffffffffu, out_acc, off);
@@ -271,24 +298,37 @@ void launch_step(const StepArgs& a, int members_per_cta, cudaStream_t s)
     switch (members_per_cta) {
     case 8: {
         dim3 grid((a.M + 7) / 8, spans, strips), block(32, 8);
-        step_kernel<8, 1><<<grid, block, 0, s>>>(a);
+        step_kernel<8, 1, false><<<grid, block, 0, s>>>(a);
         break;
     }
     case 4: {
         dim3 grid((a.M + 3) / 4, spans, strips), block(32, 4);
-        step_kernel<4, 1><<<grid, block, 0, s>>>(a);
+        step_kernel<4, 1, false><<<grid, block, 0, s>>>(a);
         break;
     }
     case 2: {
         dim3 grid((a.M + 1) / 2, (spans + 1) / 2, strips), block(32, 4);
-        step_kernel<2, 2><<<grid, block, 0, s>>>(a);
+        step_kernel<2, 2, false><<<grid, block, 0, s>>>(a);
         break;
     }
     default: {
         dim3 grid(a.M, (spans + 3) / 4, strips), block(32, 4);
-        step_kernel<1, 4><<<grid, block, 0, s>>>(a);
+        step_kernel<1, 4, false><<<grid, block, 0, s>>>(a);
         break;
     }
+    }
+}
+
+void launch_replay(const StepArgs& a, int members_per_cta, cudaStream_t s)
+{
+    const int spans = (a.nx + kSpan - 1) / kSpan;
+    const int strips = (a.ny + a.rows_per_strip - 1) / a.rows_per_strip;
+    if (members_per_cta >= 4) {
+        dim3 grid((a.M + 3) / 4, spans, strips), block(32, 4);
+        step_kernel<4, 1, true><<<grid, block, 0, s>>>(a);
+    } else {
+        dim3 grid(a.M, (spans + 3) / 4, strips), block(32, 4);
+        step_kernel<1, 4, true><<<grid, block, 0, s>>>(a);
     }
 }
 

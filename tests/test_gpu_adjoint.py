@@ -1,0 +1,151 @@
+"""GPU adjoint (flood_adjoint, extension beyond the paper) against the FP64
+oracle adjoint and against central finite differences, plus the
+torch.autograd.Function wrapper and checkpoint-interval invariance."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2302_08341_gb300 import synth
+from tests.gpu_util import oracle_params, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    return require_gpu()
+
+
+def _wet_case(ny=40, nx=56, M=2, seed=31, depth=0.15):
+    terr = synth.make_terrain(ny, nx, seed=seed, building_frac=0.0)
+    zmax = float(terr.z.max())
+    h0 = np.maximum(depth + 0.4 * (zmax - terr.z) / max(zmax, 1e-6), depth).astype(np.float32)
+    rng = np.random.default_rng(seed)
+    rm = rng.uniform(0.8, 1.3, M).astype(np.float32)
+    sc = rng.uniform(0.8, 1.2, M).astype(np.float32)
+    hy = synth.hyetograph_triangular(60.0, 1200.0, 3600.0)
+    cells = rng.choice(ny * nx, 5, replace=False).astype(np.int32)
+    ns, sdt = 8, 30.0
+    d = (h0.ravel()[cells][None, :] + rng.normal(0, 0.02, (ns, 5))).astype(np.float64)
+    return terr, h0, rm, sc, hy, cells, d, ns, sdt
+
+
+def _gpu_adjoint(capi, terr, h0, rm, sc, hy, cells, d, sdt, params=None, ckpt=0):
+    with capi.Grid(terr.z, terr.n, params) as g:
+        g.ensemble_init(len(rm), rm, sc, hy, h0=h0)
+        return g.adjoint(cells, d, sdt, ckpt_every=ckpt)
+
+
+def test_adjoint_matches_fp64_oracle_adjoint(capi):
+    terr, h0, rm, sc, hy, cells, d, ns, sdt = _wet_case()
+    p = capi.Params.default()
+    out = _gpu_adjoint(capi, terr, h0, rm, sc, hy, cells, d, sdt, p)
+    op = oracle_params(p, *terr.z.shape)
+    gn_sum = np.zeros(terr.z.shape)
+    for m in range(len(rm)):
+        r = oracle.loss_and_grad(op, terr.z, terr.n, float(sc[m]), float(rm[m]), hy, h0, sdt, d,
+                                 cells)
+        assert abs(out["loss"][m] - r["loss"]) <= 1e-4 * r["loss"]
+        assert abs(out["grad_rain"][m] - r["grad_rain"]) <= 2e-3 * abs(r["grad_rain"])
+        assert abs(out["grad_scale"][m] - r["grad_scale"]) <= 2e-3 * abs(r["grad_scale"])
+        gh = out["grad_h0"][m]
+        assert np.max(np.abs(gh - r["grad_h0"])) <= 2e-3 * np.max(np.abs(r["grad_h0"]))
+        gn_sum += r["grad_n"]
+    assert np.max(np.abs(out["grad_n"] - gn_sum)) <= 2e-3 * np.max(np.abs(gn_sum))
+
+
+def test_adjoint_agrees_with_central_differences(capi):
+    """Fully wet, fixed steps (the schedule the adjoint freezes).  Central
+    differences (eps = 1e-3 relative) of the FP64 forward model give the
+    reference: the GPU adjoint's rain-multiplier and Manning-scale gradients
+    within 1e-3, the per-cell Manning gradient on 32 random wet cells within
+    1e-3 (median) and 1e-2 (worst).  Central differences of the GPU's own FP32
+    forward agree within 1e-2 (FP32 rounding of the two runs bounds them)."""
+    terr, h0, rm, sc, hy, cells, d, ns, sdt = _wet_case(M=1, seed=33)
+    hy = synth.hyetograph_constant(100.0, 600.0)
+    p = capi.Params.default(dt_fixed=0.5)
+    out = _gpu_adjoint(capi, terr, h0, rm, sc, hy, cells, d, sdt, p)
+    op = oracle_params(p, *terr.z.shape)
+    n64 = terr.n.astype(np.float64)
+
+    def loss64(rm_, sc_, n_=n64):
+        return oracle.loss_and_grad(op, terr.z, n_, sc_, rm_, hy, h0, sdt, d, cells)["loss"]
+
+    def loss32(rm_, sc_):
+        return _gpu_adjoint(capi, terr, h0, np.array([rm_], np.float32),
+                            np.array([sc_], np.float32), hy, cells, d, sdt, p)["loss"][0]
+
+    r0, s0 = float(rm[0]), float(sc[0])
+    for key, f64, f32, x0 in (("grad_rain", lambda e: (loss64(r0 + e, s0), loss64(r0 - e, s0)),
+                               lambda e: (loss32(r0 + e, s0), loss32(r0 - e, s0)), r0),
+                              ("grad_scale", lambda e: (loss64(r0, s0 + e), loss64(r0, s0 - e)),
+                               lambda e: (loss32(r0, s0 + e), loss32(r0, s0 - e)), s0)):
+        e = 1e-3 * x0
+        a, b = f64(e)
+        fd = (a - b) / (2 * e)
+        assert abs(fd - out[key][0]) <= 1e-3 * abs(fd), (key, fd, out[key][0])
+        a, b = f32(e)
+        fd32 = (a - b) / (2 * e)
+        assert abs(fd32 - out[key][0]) <= 1e-2 * abs(fd), (key, fd32, out[key][0])
+
+    g = out["grad_n"].astype(np.float64)
+    rng = np.random.default_rng(7)
+    cand = np.nonzero((np.abs(g).ravel() > 1e-2 * np.abs(g).max()) & (h0.ravel() > 0.05))[0]
+    pick = rng.choice(cand, 32, replace=False)
+    errs = []
+    for i in pick:
+        e = 1e-3 * n64.flat[i]
+        a = n64.copy(); a.flat[i] += e
+        b = n64.copy(); b.flat[i] -= e
+        fd = (loss64(r0, s0, a) - loss64(r0, s0, b)) / (2 * e)
+        errs.append(abs(fd - g.flat[i]) / abs(fd))
+    assert np.median(errs) <= 1e-3 and max(errs) <= 1e-2, (np.median(errs), max(errs))
+
+
+def test_checkpoint_interval_does_not_change_gradients(capi):
+    terr, h0, rm, sc, hy, cells, d, ns, sdt = _wet_case(M=3, seed=35)
+    res = [_gpu_adjoint(capi, terr, h0, rm, sc, hy, cells, d, sdt, ckpt=k) for k in (1, 7, 64, 0)]
+    for r in res[1:]:
+        for key in ("loss", "grad_rain", "grad_scale"):
+            assert np.array_equal(r[key], res[0][key])
+        assert np.array_equal(r["grad_n"], res[0]["grad_n"])
+        assert np.array_equal(r["grad_h0"], res[0]["grad_h0"])
+
+
+def test_members_with_different_step_counts(capi):
+    """Deep water makes Eq. 4 bind, so members take different numbers of
+    steps; each member's gradients still follow the oracle."""
+    terr, h0, rm, sc, hy, cells, d, ns, sdt = _wet_case(M=3, seed=37, depth=1.2)
+    rm = np.array([0.5, 1.0, 3.0], np.float32)
+    p = capi.Params.default()
+    with capi.Grid(terr.z, terr.n, p) as g:
+        g.ensemble_init(3, rm, sc, hy, h0=h0)
+        out = g.adjoint(cells, d, sdt)
+        steps = g.members()["steps"]
+    op = oracle_params(p, *terr.z.shape)
+    for m in range(3):
+        r = oracle.loss_and_grad(op, terr.z, terr.n, float(sc[m]), float(rm[m]), hy, h0, sdt, d,
+                                 cells)
+        assert abs(out["loss"][m] - r["loss"]) <= 1e-4 * r["loss"]
+        assert abs(out["grad_rain"][m] - r["grad_rain"]) <= 2e-3 * abs(r["grad_rain"])
+        assert np.max(np.abs(out["grad_h0"][m] - r["grad_h0"])) <= 2e-3 * np.max(np.abs(r["grad_h0"]))
+    assert len(set(steps.tolist())) > 1
+
+
+def test_autograd_function_returns_the_adjoint_gradients(capi):
+    torch = pytest.importorskip("torch")
+    from paper_2302_08341_gb300.autograd import gauge_misfit
+    terr, h0, rm, sc, hy, cells, d, ns, sdt = _wet_case(M=2, seed=39)
+    dev = torch.device("cuda")
+    n_t = torch.tensor(terr.n, device=dev, requires_grad=True)
+    rm_t = torch.tensor(rm, device=dev, requires_grad=True)
+    h0_t = torch.tensor(h0, device=dev, requires_grad=True)
+    loss = gauge_misfit(n_t, rm_t, h0_t, torch.tensor(terr.z, device=dev),
+                        torch.tensor(sc, device=dev), torch.tensor(hy, device=dev), cells, d, sdt)
+    loss.backward()
+    ref = _gpu_adjoint(capi, terr, np.broadcast_to(h0, (2,) + h0.shape).copy(), rm, sc, hy, cells,
+                       d, sdt)
+    assert abs(float(loss) - ref["loss"].sum()) <= 1e-12 * ref["loss"].sum()
+    assert np.array_equal(n_t.grad.cpu().numpy(), ref["grad_n"])
+    assert np.allclose(rm_t.grad.cpu().numpy(), ref["grad_rain"], rtol=1e-6)
+    assert np.allclose(h0_t.grad.cpu().numpy(), ref["grad_h0"].sum(axis=0), rtol=1e-5, atol=1e-9)
