@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--ny", type=int, default=2000, help="rows (smaller cases for profiling)")
     ap.add_argument("--nx", type=int, default=2000)
     ap.add_argument("--members", type=int, default=96)
+    ap.add_argument("--no-extensions", action="store_true",
+                    help="skip the adjoint and uneven-batch measurements")
     args = ap.parse_args()
     global NY, NX, M
     NY, NX, M = args.ny, args.nx, args.members
@@ -226,6 +228,69 @@ def cpu_baseline(terr, hy, rm, sc, target_s=15.0):
                       f"FP64, 1 thread, {el:.1f} s"}
 
 
+def adjoint_measure(capi):
+    """Adjoint cost: 1024 x 1024 single member, 8 gauges sampled every 60 s over
+    1800 s, checkpoint every 64 steps; reverse (replay included) / forward."""
+    from paper_2302_08341_gb300 import synth
+    terr = synth.make_terrain(1024, 1024, seed=3)
+    hy = synth.hyetograph_triangular(60.0, 1200.0, 3600.0)
+    rm, sc = synth.ensemble_prior(3, 1)
+    cells = synth.gauge_cells(terr, 8, seed=3)
+    trm, tsc = synth.ensemble_prior(1003, 1)
+    obs = []
+    with capi.Grid(terr.z, terr.n) as g:
+        g.ensemble_init(1, trm, tsc, hy)
+        for s in range(1, 31):
+            g.advance_to(60.0 * s)
+            obs.append(synth.observe(g.gauge_sample(cells)[0], seed=3, window=s))
+    d = np.array(obs)
+    res = None
+    with capi.Grid(terr.z, terr.n) as g:
+        for _ in range(2):  # the first call sizes the buffers
+            g.ensemble_init(1, rm, sc, hy)
+            res = g.adjoint(cells, d, 60.0, ckpt_every=64)
+    return {"config": "1024x1024 cells, 1 member, 8 gauges every 60 s over 1800 s, "
+                      "checkpoint every 64 steps",
+            "forward_ms": res["forward_ms"], "reverse_ms": res["reverse_ms"],
+            "adj_over_fwd": res["reverse_ms"] / res["forward_ms"]}
+
+
+def batch_measure(capi):
+    """Uneven batch: 64 scenarios, square sides U{512..2048}, own DEM seeds,
+    rain U[20, 100] mm/h, durations U[900, 3600] s, advanced in 300 s windows
+    by graph-replayed batched launches; member-cell-steps/s over the batch."""
+    import torch
+    from paper_2302_08341_gb300 import synth
+    scen = synth.uneven_batch(64)
+    terrs = [synth.make_terrain(s.ny, s.nx, seed=s.seed) for s in scen]
+    hys = [synth.hyetograph_constant(s.rain_mm_h, s.duration_s) for s in scen]
+    dur = np.array([s.duration_s for s in scen])
+    ones = np.ones(len(scen), np.float32)
+    cells = np.array([s.ny * s.nx for s in scen], np.float64)
+    with capi.Batch([t.z for t in terrs], [t.n for t in terrs]) as b:
+        b.init(hys, ones, ones, dur)
+        b.step(300.0)                      # warm-up window (graph capture)
+        b.init(hys, ones, ones, dur)
+        stream = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        l0 = b.launch_count
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for w in range(1, 13):
+            b.step(300.0 * w, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        mem = b.members()
+        launches = b.launch_count - l0
+    units = float((mem["steps"] * cells).sum())
+    return {"config": "64 scenarios, sides U{512..2048}, rain U[20,100] mm/h, durations "
+                      "U[900,3600] s, 300 s windows, CUDA-graph replayed batched step",
+            "value": units / (ms * 1e-3), "unit": "member-cell-steps/s", "ms": ms,
+            "total_cells": float(cells.sum()), "member_cell_steps": units,
+            "all_finished": bool(np.all(mem["t"] == dur)), "gpu_launches": launches}
+
+
 def run_reference(args):
     world, rank, local = dist_setup(args)
     if rank != 0:
@@ -300,11 +365,15 @@ def run_gb300(args):
                 resampled=torch.zeros(1, dtype=torch.int32, device=device),
                 y=torch.zeros((M, G), dtype=torch.float32, device=device))
 
-    # warm-up windows
+    # warm-up windows, then the autotuner picks the step kernel's launch
+    # configuration on the wet ensemble (and leaves it untouched)
     g.ensemble_init(M, rm, sc, hy, stream=stream)
     for w in range(1, args.warmup + 1):
         window(g, w, d_all[w - 1], beta_all[w - 1], draws[w - 1][0], outs)
     torch.cuda.synchronize(device)
+    rows_t, mpc_t, eng_t, ms_t = g.autotune(steps_per_trial=6, stream=stream)
+    tuned = {"rows_per_strip": rows_t, "members_per_cta": mpc_t, "engine": eng_t,
+             "ms_per_step": ms_t}
 
     # timed windows from a fresh ensemble (the 1 h storm from t = 0)
     g.ensemble_init(M, rm, sc, hy, stream=stream)
@@ -373,6 +442,11 @@ def run_gb300(args):
                "h2d_bytes_per_step": G * 8 + M * 4,
                "d2h_bytes_per_step": M * 8 + M * 4 + 8 + 4 + M * G * 4}
     g.close()
+    extensions = {}
+    if not args.no_extensions and world == 1:
+        extensions["adjoint"] = adjoint_measure(capi)
+        extensions["batched"] = batch_measure(capi)
+        extensions["autotune"] = tuned
 
     if rank != 0:
         if world > 1:
@@ -395,6 +469,7 @@ def run_gb300(args):
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
         "clocks": clk.summary(),
     }
+    line.update(extensions)
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -265,9 +265,62 @@ int flood_get_launch(const flood_grid* g, int* rows_per_strip, int* members_per_
  * give identical results.  Errors: FLOOD_ERR_ARG. */
 int flood_set_engine(flood_grid* g, int engine);
 
+/* Autotuner: time every step-kernel configuration (engine x rows per strip
+ * {32, 64, 128} x members per CTA {4, 1}) for steps_per_trial steps on the
+ * live ensemble, keep the fastest, and restore the ensemble (state, clocks,
+ * volume counters) to where it was.  Writes the choice and its time per step
+ * (ms); any output may be NULL.  Synchronous. */
+int flood_autotune(flood_grid* g, int steps_per_trial, int* best_rows, int* best_mpc,
+                   int* best_engine, double* best_ms, void* stream);
+
 /* Wait for `stream`, then report device-side faults of the method: returns
  * FLOOD_ERR_NAN if any step produced a non-finite depth. */
 int flood_sync(flood_grid* g, void* stream);
+
+/* ==== Uneven batches (extension beyond the paper) =========================
+ * Many independent scenarios, each with its own grid size, bed, roughness,
+ * storm, Manning scale and duration, advanced together: one launch per step
+ * covers every scenario's tiles, each scenario with its own step length from
+ * Eq. 4 on its own maximum depth; the launches are replayed from a CUDA graph
+ * of a fixed number of steps.  Same scheme, arithmetic and results as a
+ * single-member flood_grid of that scenario. */
+typedef struct flood_batch flood_batch;
+
+/* n scenarios: scenario i has ny[i] x nx[i] cells with bed z[i] and base
+ * Manning n_base[i] ([ny[i]][nx[i]] FP32, host or device; copied).  One
+ * flood_params for all.  Synchronous.  Errors: FLOOD_ERR_ARG, _OOM, _CUDA. */
+int flood_batch_create(flood_batch** out, int n, const int32_t* ny, const int32_t* nx,
+                       const float* const* z, const float* const* n_base, const flood_params* p);
+int flood_batch_destroy(flood_batch* b);
+const char* flood_batch_last_error(const flood_batch* b);
+
+/* Start every scenario dry at t = 0: scenario i with hyetographs[i]
+ * ([n_blocks[i]] rain rates per rain block, m/s), rain multiplier, Manning
+ * scale, and its own end time t_end[i] (s).  Synchronous. */
+int flood_batch_init(flood_batch* b, const float* const* hyetographs, const int32_t* n_blocks,
+                     const float* rain_mult, const float* manning_scale, const double* t_end,
+                     void* stream);
+
+/* Advance every scenario to min(t_stop, t_end[i]) (a window end), each with
+ * its own steps.  Synchronises `stream` between graph replays to follow the
+ * scenarios' clocks.  Errors: FLOOD_ERR_STATE (before init, or no progress),
+ * FLOOD_ERR_NAN. */
+int flood_batch_step(flood_batch* b, double t_stop, void* stream);
+
+/* Launch shape: rows per warp strip (1..4096) and warps per CTA (4 or 8);
+ * results do not depend on it.  Synchronous. */
+int flood_batch_set_launch(flood_batch* b, int rows_per_strip, int warps_per_cta);
+
+/* Scenario i's state as [ny[i]][nx[i]] FP32 arrays (any may be NULL). */
+int flood_batch_get_state(flood_batch* b, int i, float* h, float* qx, float* qy, void* stream);
+
+/* Per-scenario clocks and FP64 volumes, each [n] (any may be NULL).
+ * Synchronous. */
+int flood_batch_members(flood_batch* b, double* t, int64_t* steps, double* storage, double* rain,
+                        double* outflow, double* clamp);
+
+/* Step kernels launched so far (graph replays count every launch). */
+int64_t flood_batch_launch_count(const flood_batch* b);
 
 #ifdef __cplusplus
 }

@@ -25,7 +25,10 @@ EXPORTED = ["flood_default_params", "flood_last_error", "flood_create_grid", "fl
             "pf_resample_systematic", "flood_get_state", "flood_set_state", "flood_get_members",
             "flood_set_members", "flood_volume_report", "flood_launch_count", "flood_sync",
             "flood_profile", "flood_set_launch", "flood_get_launch", "flood_set_engine",
-            "flood_adjoint", "flood_adjoint_timing"]
+            "flood_adjoint", "flood_adjoint_timing", "flood_batch_create", "flood_batch_destroy",
+            "flood_batch_last_error", "flood_batch_init", "flood_batch_step",
+            "flood_batch_set_launch", "flood_batch_get_state", "flood_batch_members",
+            "flood_batch_launch_count", "flood_autotune"]
 
 
 class FloodError(RuntimeError):
@@ -99,8 +102,22 @@ def lib(path: str = LIB_PATH):
     L.flood_set_engine.argtypes = [_VP, C.c_int]
     L.flood_adjoint.argtypes = [_VP, C.POINTER(LossSpec), C.c_int, _VP, _VP, _VP, _VP, _VP, _VP]
     L.flood_adjoint_timing.argtypes = [_VP, _VP, _VP]
+    L.flood_autotune.argtypes = [_VP, C.c_int, _VP, _VP, _VP, _VP, _VP]
+    L.flood_batch_create.argtypes = [C.POINTER(_VP), C.c_int, _VP, _VP, _VP, _VP,
+                                     C.POINTER(Params)]
+    L.flood_batch_destroy.argtypes = [_VP]
+    L.flood_batch_last_error.argtypes = [_VP]
+    L.flood_batch_last_error.restype = C.c_char_p
+    L.flood_batch_init.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _VP]
+    L.flood_batch_step.argtypes = [_VP, C.c_double, _VP]
+    L.flood_batch_set_launch.argtypes = [_VP, C.c_int, C.c_int]
+    L.flood_batch_get_state.argtypes = [_VP, C.c_int, _VP, _VP, _VP, _VP]
+    L.flood_batch_members.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _VP]
+    L.flood_batch_launch_count.argtypes = [_VP]
+    L.flood_batch_launch_count.restype = C.c_int64
     for name in EXPORTED:
-        if name not in ("flood_default_params", "flood_last_error", "flood_launch_count"):
+        if name not in ("flood_default_params", "flood_last_error", "flood_launch_count",
+                        "flood_batch_last_error", "flood_batch_launch_count"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -314,6 +331,14 @@ class Grid:
         _check(lib().flood_get_launch(self.h, C.byref(r), C.byref(m)), self.h)
         return r.value, m.value
 
+    def autotune(self, steps_per_trial=6, stream=None):
+        """Pick the fastest step-kernel configuration on the live ensemble
+        (which is left unchanged); returns (rows, members_per_cta, engine, ms)."""
+        r = C.c_int(); mp = C.c_int(); e = C.c_int(); t = C.c_double()
+        _check(lib().flood_autotune(self.h, int(steps_per_trial), C.byref(r), C.byref(mp),
+                                    C.byref(e), C.byref(t), stream_handle(stream)), self.h)
+        return r.value, mp.value, e.value, t.value
+
     def profile(self, enable=True):
         """Turn per-launch step-kernel timing on/off; returns (ms, launches)
         accumulated since the previous call."""
@@ -345,3 +370,84 @@ class Grid:
     @property
     def launch_count(self):
         return int(lib().flood_launch_count(self.h))
+
+
+def _bcheck(rc, handle=None):
+    if rc != FLOOD_OK:
+        msg = lib().flood_batch_last_error(handle)
+        raise FloodError(rc, msg.decode() if msg else "")
+
+
+class Batch:
+    """Uneven batch of independent scenarios (flood_batch_*): each with its
+    own grid, bed, roughness, storm, Manning scale and duration."""
+
+    def __init__(self, zs, ns, params: Params | None = None):
+        L = lib()
+        self.params = params if params is not None else Params.default()
+        self._z = [np.ascontiguousarray(z, np.float32) for z in zs]
+        self._n = [np.ascontiguousarray(n, np.float32) for n in ns]
+        self.S = len(self._z)
+        self.shapes = [z.shape for z in self._z]
+        ny = np.array([s[0] for s in self.shapes], np.int32)
+        nx = np.array([s[1] for s in self.shapes], np.int32)
+        zp = (C.c_void_p * self.S)(*[z.ctypes.data for z in self._z])
+        np_ = (C.c_void_p * self.S)(*[n.ctypes.data for n in self._n])
+        h = _VP()
+        _bcheck(L.flood_batch_create(C.byref(h), self.S, ny.ctypes.data, nx.ctypes.data, zp, np_,
+                                     C.byref(self.params)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().flood_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def init(self, hyetographs, rain_mult, scale, t_end, stream=None):
+        self._hy = [np.ascontiguousarray(h, np.float32) for h in hyetographs]
+        hp = (C.c_void_p * self.S)(*[h.ctypes.data for h in self._hy])
+        nb = np.array([len(h) for h in self._hy], np.int32)
+        rm = np.ascontiguousarray(rain_mult, np.float32)
+        sc = np.ascontiguousarray(scale, np.float32)
+        te = np.ascontiguousarray(t_end, np.float64)
+        _bcheck(lib().flood_batch_init(self.h, hp, nb.ctypes.data, rm.ctypes.data, sc.ctypes.data,
+                                       te.ctypes.data, stream_handle(stream)), self.h)
+
+    def step(self, t_stop, stream=None):
+        _bcheck(lib().flood_batch_step(self.h, float(t_stop), stream_handle(stream)), self.h)
+
+    def set_launch(self, rows_per_strip, warps_per_cta=4):
+        _bcheck(lib().flood_batch_set_launch(self.h, int(rows_per_strip), int(warps_per_cta)),
+                self.h)
+
+    def get_state(self, i, stream=None):
+        ny, nx = self.shapes[i]
+        h = np.zeros((ny, nx), np.float32); qx = np.zeros_like(h); qy = np.zeros_like(h)
+        _bcheck(lib().flood_batch_get_state(self.h, int(i), h.ctypes.data, qx.ctypes.data,
+                                            qy.ctypes.data, stream_handle(stream)), self.h)
+        return h, qx, qy
+
+    def members(self):
+        S = self.S
+        out = dict(t=np.zeros(S), steps=np.zeros(S, np.int64), storage=np.zeros(S),
+                   rain=np.zeros(S), outflow=np.zeros(S), clamp=np.zeros(S))
+        _bcheck(lib().flood_batch_members(self.h, *(out[k].ctypes.data for k in
+                                                     ("t", "steps", "storage", "rain", "outflow",
+                                                      "clamp"))), self.h)
+        return out
+
+    @property
+    def launch_count(self):
+        return int(lib().flood_batch_launch_count(self.h))

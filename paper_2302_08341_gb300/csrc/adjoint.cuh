@@ -14,8 +14,7 @@ struct AdjArgs {
     const float* z;
     const float* n;
     const float* scale;      // [M]
-    const double* dt_log;    // [M][dt_log_cap]
-    const double* rdt_log;   // [M][dt_log_cap] dt x block rain rate
+    const MemberPlan* log;   // [M][dt_log_cap] plans of the recorded steps
     const int* seg_end;      // [M] first step index past this segment, per member
     int dt_log_cap;
     int seg_first;           // step index whose input state sits in slot 0

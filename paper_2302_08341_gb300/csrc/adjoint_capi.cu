@@ -107,9 +107,7 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
         K = ckpt_every > 0 ? ckpt_every : std::max(1, (int)std::lround(std::sqrt((double)cap)));
         const size_t n_ckpt = (size_t)cap / K + 1;
         have_log = 0;
-        if ((rc = grow(g, &g->dt_log, have_log, (size_t)M * cap))) return rc;
-        have_log = 0;
-        if ((rc = grow(g, &g->rdt_log, have_log, (size_t)M * cap))) return rc;
+        if ((rc = grow(g, &g->log, have_log, (size_t)M * cap))) return rc;
         if (n_ckpt * M * ms > g->ckpt_floats) {
             have_ckpt = 0;
             if ((rc = grow(g, &g->ckpt, have_ckpt, n_ckpt * M * ms))) return rc;
@@ -226,8 +224,7 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
         CK(g, cudaMemcpyAsync(g->seg, g->ckpt + (size_t)cs * M * ms, sizeof(float) * M * ms,
                               cudaMemcpyDeviceToDevice, s));
         flood::StepArgs a = flood::step_args(g, -1.0);
-        a.dt_log = g->dt_log;
-        a.rdt_log = g->rdt_log;
+        a.log = g->log;
         a.dt_log_cap = g->log_cap;
         a.ckpt = nullptr;
         a.seg = g->seg;
@@ -246,8 +243,7 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
         b.z = g->z;
         b.n = g->n;
         b.scale = g->scale;
-        b.dt_log = g->dt_log;
-        b.rdt_log = g->rdt_log;
+        b.log = g->log;
         b.seg_end = g->seg_end;
         b.dt_log_cap = g->log_cap;
         b.seg_first = first;

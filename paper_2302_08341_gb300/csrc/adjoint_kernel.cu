@@ -132,17 +132,16 @@ __global__ void __launch_bounds__(32 * WM * WC, 4) adjoint_kernel(const AdjArgs 
                 }
         return;
     }
-    const double dt = a.dt_log[(size_t)m * a.dt_log_cap + j];
-    const double rdt = a.rdt_log[(size_t)m * a.dt_log_cap + j];
+    const MemberPlan pl = a.log[(size_t)m * a.dt_log_cap + j];
     FaceK k;
-    k.gdt_dx = (float)(a.g * dt / a.dxd);
-    k.gdt = (float)(a.g * dt);
-    k.dx_4dt = (float)(a.dxd / (4.0 * dt));
+    k.gdt_dx = pl.gdt_dx;
+    k.gdt = pl.gdt;
+    k.dx_4dt = pl.dx_4dt;
     k.h_eps = a.h_eps;
     k.edge_drop = a.edge_drop;
     k.limiter = a.limiter;
     const float L = k.dx_4dt;
-    const float T = (float)(dt / a.dxd);
+    const float T = pl.dt_dx;
     const float s = a.scale[m];
     const float s_half = 0.5f * s;
 
@@ -177,12 +176,14 @@ __global__ void __launch_bounds__(32 * WM * WC, 4) adjoint_kernel(const AdjArgs 
                                        __fmul_rn(s_half, __fadd_rn(nU[q], nC[q])), k, L);
                 const float mu = lqU[q] + T * (lC[q] - masked(haU[q], lhU[q]));
                 carH[q] = mu * d.dh2;
-                carN[q] = mu * d.dnl;
+                carN[q] = mu * d.dnl * s_half;
             }
         }
     }
 
-    double g_rain = 0.0, g_scale = 0.0;
+    // FP32 compensated partials (sum of lambda~ for the rain gradient, of
+    // mu * dq'/dn * n for the scale gradient), widened to FP64 once per warp
+    float gr_s = 0.0f, gr_c = 0.0f, gs_s = 0.0f, gs_c = 0.0f;
     for (int r = r0; r < r1; ++r) {
         const size_t o = (size_t)r * ld + c;
         const bool has_s = (r + 1 < ny);
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(32 * WM * WC, 4) adjoint_kernel(const AdjArgs 
                 dEn[q] = 0.0f;
             }
             muE[q] = mu; dEh1[q] = d.dh1; dEh2[q] = d.dh2; dEq[q] = d.dq;
-            g_scale += (double)(mu * d.dnl * nl_w);
+            kahan_add(gs_s, gs_c, mu * d.dnl * nl_w);
         }
         // west link of the lane's first cell
         float muW = __shfl_up_sync(0xffffffffu, muE[3], 1);
@@ -271,8 +272,8 @@ __global__ void __launch_bounds__(32 * WM * WC, 4) adjoint_kernel(const AdjArgs 
                     dn = d.dnl * s;
                     nl_w = nC[q];
                 }
-                g_scale += (double)(mu * d.dnl * nl_w);
-                g_rain += (double)lC[q] * rdt;
+                kahan_add(gs_s, gs_c, mu * d.dnl * nl_w);
+                kahan_add(gr_s, gr_c, lC[q]);
             }
             const float muw = (q == 0) ? muW : muE[q - 1];
             const float dwh = (q == 0) ? dWh2 : dEh2[q - 1];
@@ -300,6 +301,8 @@ __global__ void __launch_bounds__(32 * WM * WC, 4) adjoint_kernel(const AdjArgs 
             hC[q] = hS[q]; zC[q] = zS[q]; nC[q] = nS[q]; lC[q] = lS[q];
         }
     }
+    double g_rain = ((double)gr_s - (double)gr_c) * pl.rdt;
+    double g_scale = (double)gs_s - (double)gs_c;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         g_rain += __shfl_xor_sync(0xffffffffu, g_rain, off);

@@ -1,0 +1,49 @@
+// Uneven batches: many independent scenarios, each with its own grid, bed,
+// roughness, rain and duration, stepped by one launch per step (extension
+// beyond the paper).
+#pragma once
+
+#include "flood_internal.cuh"
+
+namespace flood {
+
+struct ScenDesc {
+    float* state;          // [2][3][plane] (two buffers of h, qx, qy)
+    const float* z;        // [ny][ld]
+    const float* n;        // [ny][ld]
+    const float* hyeto;    // [nb] rain rate per block (m/s)
+    size_t plane;
+    int ny, nx, ld, nb;
+    float rain_mult, scale;
+    double t_end;          // the scenario's own end time
+    double ncell;
+};
+
+// One warp's work: a 128-column span of rows [r0, r1) of one scenario.
+struct WarpTask {
+    int scen, c0, r0, r1;
+    int slot;              // this task's FP64 volume slot
+    int first;             // 1 for the task that owns the scenario's clock
+};
+
+struct BatchArgs {
+    const ScenDesc* scen;
+    const WarpTask* tasks;
+    int ntasks;
+    const MemberClock* ms_in;  // [S] slot k%3
+    MemberClock* ms_out;       // slot (k+1)%3
+    MemberClock* ms_clr;       // slot (k+2)%3
+    const double* t_stop;      // window end (device scalar, so captured graphs are reusable)
+    MemberPlan* plan;          // [S] this step's plans
+    double* vacc;              // [nslot_total][2]
+    double* rain_acc;          // [S]
+    int* err;
+    double alpha_dx, g, dt_cap, dt_fixed, h_floor, rain_block, dxd, cell_area;
+    float h_eps, edge_drop;
+    int limiter, east_out, south_out;
+};
+
+void launch_batch_plan(const BatchArgs& a, int n_scen, cudaStream_t s);
+void launch_batch_step(const BatchArgs& a, int warps_per_cta, cudaStream_t s);
+
+}  // namespace flood

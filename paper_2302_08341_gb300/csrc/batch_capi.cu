@@ -1,0 +1,459 @@
+// Host side of the uneven-batch API (flood_batch_*): per-scenario buffers,
+// the flat warp-task table, and the step driver that replays a CUDA graph of
+// kGraphSteps step launches until every scenario has reached the window end.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/flood.h"
+#include "batch.cuh"
+#include "pf_kernels.cuh"
+
+using flood::MemberClock;
+
+namespace {
+
+constexpr int kGraphSteps = 96;  // a multiple of 3: clock slots line up across replays
+constexpr int kSpan = 128;
+
+thread_local std::string g_batch_msg;
+
+}  // namespace
+
+struct flood_batch {
+    int S = 0;
+    flood_params p{};
+    std::vector<int> ny, nx, ld;
+    std::vector<float*> zn, state, hyeto;
+    std::vector<flood::ScenDesc> desc;
+    flood::ScenDesc* d_desc = nullptr;
+    std::vector<flood::WarpTask> tasks;
+    flood::WarpTask* d_tasks = nullptr;
+    std::vector<int> slot0;           // first volume slot of each scenario
+    int nslot = 0;
+    MemberClock* ms = nullptr;        // [3][S]
+    double* vacc = nullptr;           // [nslot][2]
+    double* rain_acc = nullptr;       // [S]
+    double* storage = nullptr;        // [S]
+    double* part = nullptr;           // storage partials
+    int part_cap = 0;
+    int* err = nullptr;
+    double* t_stop = nullptr;         // device scalar
+    flood::MemberPlan* plan = nullptr; // [S]
+    int rows_per_strip = 64, warps_per_cta = 4;
+    bool initialised = false;
+    int64_t k = 0, launches = 0;
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    std::string msg;
+};
+
+namespace {
+
+int bfail(flood_batch* b, int code, const std::string& m)
+{
+    if (b) b->msg = m; else g_batch_msg = m;
+    return code;
+}
+
+#define BCK(b, call)                                                                          \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return bfail((b), e_ == cudaErrorMemoryAllocation ? FLOOD_ERR_OOM : FLOOD_ERR_CUDA, \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+    } while (0)
+
+cudaStream_t S_(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+void drop_graph(flood_batch* b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+}
+
+// Task table: for each scenario, strips of rows_per_strip rows x 128-column
+// spans, in row-major order so neighbouring warps share halo rows in L2.
+int build_tasks(flood_batch* b)
+{
+    b->tasks.clear();
+    b->slot0.assign(b->S, 0);
+    int slot = 0;
+    for (int i = 0; i < b->S; ++i) {
+        b->slot0[i] = slot;
+        const int spans = (b->nx[i] + kSpan - 1) / kSpan;
+        for (int r0 = 0; r0 < b->ny[i]; r0 += b->rows_per_strip)
+            for (int sp = 0; sp < spans; ++sp) {
+                flood::WarpTask t;
+                t.scen = i;
+                t.c0 = sp * kSpan;
+                t.r0 = r0;
+                t.r1 = std::min(r0 + b->rows_per_strip, b->ny[i]);
+                t.slot = slot++;
+                t.first = (r0 == 0 && sp == 0) ? 1 : 0;
+                b->tasks.push_back(t);
+            }
+    }
+    if (b->d_tasks) cudaFree(b->d_tasks);
+    b->d_tasks = nullptr;
+    BCK(b, cudaMalloc(&b->d_tasks, sizeof(flood::WarpTask) * b->tasks.size()));
+    BCK(b, cudaMemcpy(b->d_tasks, b->tasks.data(), sizeof(flood::WarpTask) * b->tasks.size(),
+                      cudaMemcpyHostToDevice));
+    // one FP64 volume slot per task (flood_batch_set_launch carries sums over)
+    std::vector<double> nw((size_t)slot * 2, 0.0);
+    if (b->vacc) cudaFree(b->vacc);
+    b->vacc = nullptr;
+    BCK(b, cudaMalloc(&b->vacc, sizeof(double) * nw.size()));
+    BCK(b, cudaMemcpy(b->vacc, nw.data(), sizeof(double) * nw.size(), cudaMemcpyHostToDevice));
+    b->nslot = slot;
+    drop_graph(b);
+    return FLOOD_OK;
+}
+
+flood::BatchArgs batch_args(const flood_batch* b, int64_t k)
+{
+    flood::BatchArgs a{};
+    a.scen = b->d_desc;
+    a.tasks = b->d_tasks;
+    a.ntasks = (int)b->tasks.size();
+    a.ms_in = b->ms + (k % 3) * b->S;
+    a.ms_out = b->ms + ((k + 1) % 3) * b->S;
+    a.ms_clr = b->ms + ((k + 2) % 3) * b->S;
+    a.t_stop = b->t_stop;
+    a.plan = b->plan;
+    a.vacc = b->vacc;
+    a.rain_acc = b->rain_acc;
+    a.err = b->err;
+    a.alpha_dx = b->p.alpha * b->p.dx;
+    a.g = b->p.g;
+    a.dt_cap = b->p.dt_cap;
+    a.dt_fixed = b->p.dt_fixed;
+    a.h_floor = b->p.h_floor;
+    a.rain_block = b->p.rain_block;
+    a.dxd = b->p.dx;
+    a.cell_area = b->p.dx * b->p.dx;
+    a.h_eps = (float)b->p.h_eps;
+    a.edge_drop = (float)(b->p.edge_slope * b->p.dx);
+    a.limiter = b->p.limiter;
+    a.east_out = b->p.east_outflow;
+    a.south_out = b->p.south_outflow;
+    return a;
+}
+
+int ensure_graph(flood_batch* b)
+{
+    if (b->graph) return FLOOD_OK;
+    if (!b->cap_stream) BCK(b, cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t gr;
+    BCK(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < kGraphSteps; ++i) {
+        const flood::BatchArgs a = batch_args(b, i);
+        flood::launch_batch_plan(a, b->S, b->cap_stream);
+        flood::launch_batch_step(a, b->warps_per_cta, b->cap_stream);
+    }
+    BCK(b, cudaStreamEndCapture(b->cap_stream, &gr));
+    cudaError_t e = cudaGraphInstantiate(&b->graph, gr, 0);
+    cudaGraphDestroy(gr);
+    BCK(b, e);
+    return FLOOD_OK;
+}
+
+int read_batch_clocks(flood_batch* b, std::vector<MemberClock>& c, cudaStream_t s)
+{
+    c.resize(b->S);
+    BCK(b, cudaMemcpyAsync(c.data(), b->ms + (b->k % 3) * b->S, sizeof(MemberClock) * b->S,
+                           cudaMemcpyDeviceToHost, s));
+    BCK(b, cudaStreamSynchronize(s));
+    int err = 0;
+    BCK(b, cudaMemcpy(&err, b->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) return bfail(b, FLOOD_ERR_NAN, "a kernel produced a non-finite depth");
+    return FLOOD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* flood_batch_last_error(const flood_batch* b)
+{
+    return b ? b->msg.c_str() : g_batch_msg.c_str();
+}
+
+int flood_batch_create(flood_batch** out, int n, const int32_t* ny, const int32_t* nx,
+                       const float* const* z, const float* const* n_base, const flood_params* p)
+{
+    if (!out) return bfail(nullptr, FLOOD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || !ny || !nx || !z || !n_base || !p)
+        return bfail(nullptr, FLOOD_ERR_ARG, "need n >= 1 and every array");
+    if (!(p->dx > 0) || !(p->g > 0) || !(p->dt_cap > 0) || !(p->rain_block > 0) || !(p->alpha > 0) ||
+        p->dt_fixed < 0 || p->h_eps < 0 || p->reserved != 0)
+        return bfail(nullptr, FLOOD_ERR_ARG, "invalid flood_params");
+    for (int i = 0; i < n; ++i)
+        if (ny[i] < 1 || nx[i] < 1 || !z[i] || !n_base[i])
+            return bfail(nullptr, FLOOD_ERR_ARG, "scenario with an empty grid or missing field");
+    flood_batch* b = new flood_batch();
+    b->S = n;
+    b->p = *p;
+    b->ny.assign(ny, ny + n);
+    b->nx.assign(nx, nx + n);
+    b->ld.resize(n);
+    b->zn.assign(n, nullptr);
+    b->state.assign(n, nullptr);
+    b->hyeto.assign(n, nullptr);
+    b->desc.resize(n);
+    auto bad = [&](cudaError_t e) {
+        g_batch_msg = std::string("flood_batch_create: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? FLOOD_ERR_OOM : FLOOD_ERR_CUDA;
+    };
+    for (int i = 0; i < n; ++i) {
+        b->ld[i] = (nx[i] + 31) / 32 * 32;
+        const size_t plane = (size_t)ny[i] * b->ld[i];
+        cudaError_t e = cudaMalloc(&b->zn[i], sizeof(float) * 2 * plane);
+        if (e == cudaSuccess) e = cudaMalloc(&b->state[i], sizeof(float) * 6 * plane);
+        if (e == cudaSuccess) e = cudaMemset(b->zn[i], 0, sizeof(float) * 2 * plane);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2D(b->zn[i], sizeof(float) * b->ld[i], z[i], sizeof(float) * nx[i],
+                             sizeof(float) * nx[i], ny[i], cudaMemcpyDefault);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2D(b->zn[i] + plane, sizeof(float) * b->ld[i], n_base[i], sizeof(float) * nx[i],
+                             sizeof(float) * nx[i], ny[i], cudaMemcpyDefault);
+        if (e != cudaSuccess) {
+            int rc = bad(e);
+            flood_batch_destroy(b);
+            return rc;
+        }
+        flood::ScenDesc& d = b->desc[i];
+        d.state = b->state[i];
+        d.z = b->zn[i];
+        d.n = b->zn[i] + plane;
+        d.hyeto = nullptr;
+        d.plane = plane;
+        d.ny = ny[i];
+        d.nx = nx[i];
+        d.ld = b->ld[i];
+        d.nb = 0;
+        d.rain_mult = 1.0f;
+        d.scale = 1.0f;
+        d.t_end = 0.0;
+        d.ncell = (double)ny[i] * nx[i];
+    }
+    cudaError_t e = cudaMalloc(&b->ms, sizeof(MemberClock) * 3 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->rain_acc, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->storage, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->t_stop, sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&b->plan, sizeof(flood::MemberPlan) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_desc, sizeof(flood::ScenDesc) * n);
+    int maxny = *std::max_element(b->ny.begin(), b->ny.end());
+    b->part_cap = (maxny + 15) / 16;
+    if (e == cudaSuccess) e = cudaMalloc(&b->part, sizeof(double) * b->part_cap);
+    if (e != cudaSuccess) {
+        int rc = bad(e);
+        flood_batch_destroy(b);
+        return rc;
+    }
+    int rc = build_tasks(b);
+    if (rc) {
+        g_batch_msg = b->msg;
+        flood_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return FLOOD_OK;
+}
+
+int flood_batch_destroy(flood_batch* b)
+{
+    if (!b) return FLOOD_OK;
+    cudaDeviceSynchronize();
+    drop_graph(b);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (float* p : b->zn) if (p) cudaFree(p);
+    for (float* p : b->state) if (p) cudaFree(p);
+    for (float* p : b->hyeto) if (p) cudaFree(p);
+    void* bufs[] = {b->d_desc, b->d_tasks, b->ms, b->vacc, b->rain_acc, b->storage, b->part,
+                    b->err, b->t_stop, b->plan};
+    for (void* p : bufs) if (p) cudaFree(p);
+    delete b;
+    return FLOOD_OK;
+}
+
+int flood_batch_init(flood_batch* b, const float* const* hyetographs, const int32_t* n_blocks,
+                     const float* rain_mult, const float* manning_scale, const double* t_end,
+                     void* stream)
+{
+    if (!b) return bfail(nullptr, FLOOD_ERR_ARG, "batch is NULL");
+    if (!hyetographs || !n_blocks || !rain_mult || !manning_scale || !t_end)
+        return bfail(b, FLOOD_ERR_ARG, "every array is required");
+    cudaStream_t s = S_(stream);
+    BCK(b, cudaStreamSynchronize(s));
+    for (int i = 0; i < b->S; ++i) {
+        if (n_blocks[i] < 0 || (n_blocks[i] > 0 && !hyetographs[i]) || !(t_end[i] >= 0.0))
+            return bfail(b, FLOOD_ERR_ARG, "bad hyetograph or end time");
+        if (b->hyeto[i]) cudaFree(b->hyeto[i]);
+        b->hyeto[i] = nullptr;
+        BCK(b, cudaMalloc(&b->hyeto[i], sizeof(float) * std::max(1, n_blocks[i])));
+        if (n_blocks[i] > 0)
+            BCK(b, cudaMemcpy(b->hyeto[i], hyetographs[i], sizeof(float) * n_blocks[i], cudaMemcpyDefault));
+        flood::ScenDesc& d = b->desc[i];
+        d.hyeto = b->hyeto[i];
+        d.nb = n_blocks[i];
+        d.rain_mult = rain_mult[i];
+        d.scale = manning_scale[i];
+        d.t_end = t_end[i];
+        BCK(b, cudaMemsetAsync(b->state[i], 0, sizeof(float) * 6 * d.plane, s));
+    }
+    BCK(b, cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(flood::ScenDesc) * b->S,
+                           cudaMemcpyHostToDevice, s));
+    std::vector<MemberClock> ms((size_t)3 * b->S);
+    for (auto& c : ms) { c.t = 0.0; c.steps = 0; c.hmax_bits = 0; c.cur = 0; }
+    BCK(b, cudaMemcpyAsync(b->ms, ms.data(), sizeof(MemberClock) * 3 * b->S, cudaMemcpyHostToDevice, s));
+    BCK(b, cudaMemsetAsync(b->rain_acc, 0, sizeof(double) * b->S, s));
+    BCK(b, cudaMemsetAsync(b->vacc, 0, sizeof(double) * b->nslot * 2, s));
+    BCK(b, cudaMemsetAsync(b->err, 0, sizeof(int), s));
+    BCK(b, cudaStreamSynchronize(s));
+    b->k = 0;
+    b->initialised = true;
+    return FLOOD_OK;
+}
+
+int flood_batch_set_launch(flood_batch* b, int rows_per_strip, int warps_per_cta)
+{
+    if (!b) return bfail(nullptr, FLOOD_ERR_ARG, "batch is NULL");
+    if (rows_per_strip < 1 || rows_per_strip > 4096 || (warps_per_cta != 4 && warps_per_cta != 8))
+        return bfail(b, FLOOD_ERR_ARG, "rows_per_strip in [1, 4096], warps_per_cta 4 or 8");
+    BCK(b, cudaDeviceSynchronize());
+    // fold the volume slots of each scenario before the table changes
+    std::vector<double> per((size_t)b->S * 2, 0.0);
+    if (b->vacc && b->nslot) {
+        std::vector<double> v((size_t)b->nslot * 2);
+        BCK(b, cudaMemcpy(v.data(), b->vacc, sizeof(double) * v.size(), cudaMemcpyDeviceToHost));
+        for (const auto& t : b->tasks) {
+            per[(size_t)t.scen * 2] += v[(size_t)t.slot * 2];
+            per[(size_t)t.scen * 2 + 1] += v[(size_t)t.slot * 2 + 1];
+        }
+    }
+    b->rows_per_strip = rows_per_strip;
+    b->warps_per_cta = warps_per_cta;
+    int rc = build_tasks(b);
+    if (rc) return rc;
+    std::vector<double> v((size_t)b->nslot * 2, 0.0);
+    for (int i = 0; i < b->S; ++i) {
+        v[(size_t)b->slot0[i] * 2] = per[(size_t)i * 2];
+        v[(size_t)b->slot0[i] * 2 + 1] = per[(size_t)i * 2 + 1];
+    }
+    BCK(b, cudaMemcpy(b->vacc, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice));
+    return FLOOD_OK;
+}
+
+int flood_batch_step(flood_batch* b, double t_stop, void* stream)
+{
+    if (!b) return bfail(nullptr, FLOOD_ERR_ARG, "batch is NULL");
+    if (!b->initialised) return bfail(b, FLOOD_ERR_STATE, "flood_batch_init has not been called");
+    if (!(t_stop >= 0.0)) return bfail(b, FLOOD_ERR_ARG, "t_stop must be >= 0");
+    cudaStream_t s = S_(stream);
+    int rc = ensure_graph(b);
+    if (rc) return rc;
+    BCK(b, cudaMemcpyAsync(b->t_stop, &t_stop, sizeof(double), cudaMemcpyHostToDevice, s));
+    std::vector<MemberClock> c;
+    double last = -1.0;
+    for (int rounds = 0;; ++rounds) {
+        if ((rc = read_batch_clocks(b, c, s))) return rc;
+        int64_t need = 0;
+        double tmin = 1e300;
+        for (int i = 0; i < b->S; ++i) {
+            const double te = std::min(t_stop, b->desc[i].t_end);
+            if (c[i].t >= te) continue;
+            tmin = std::min(tmin, c[i].t);
+            double dt;
+            if (b->p.dt_fixed > 0) {
+                dt = b->p.dt_fixed;
+            } else {
+                float hf;
+                std::memcpy(&hf, &c[i].hmax_bits, sizeof(hf));
+                const double hm = std::max((double)hf, b->p.h_floor);
+                dt = std::min(b->p.alpha * b->p.dx / std::sqrt(b->p.g * hm), b->p.dt_cap);
+            }
+            const double rb = b->p.rain_block;
+            const int64_t edges = (int64_t)std::floor(te / rb) - (int64_t)std::floor(c[i].t / rb) + 1;
+            need = std::max(need, (int64_t)std::ceil((te - c[i].t) / dt) + edges);
+        }
+        if (need == 0) break;
+        if (rounds > 0 && !(tmin > last))
+            return bfail(b, FLOOD_ERR_STATE, "scenarios stopped advancing toward t_stop");
+        if (need > (int64_t)1 << 26) return bfail(b, FLOOD_ERR_STATE, "too many steps to t_stop");
+        last = tmin;
+        const int64_t reps = (need + kGraphSteps - 1) / kGraphSteps;
+        for (int64_t r = 0; r < reps; ++r) BCK(b, cudaGraphLaunch(b->graph, s));
+        b->k += reps * kGraphSteps;
+        b->launches += reps * kGraphSteps * 2;
+    }
+    return FLOOD_OK;
+}
+
+int flood_batch_get_state(flood_batch* b, int i, float* h, float* qx, float* qy, void* stream)
+{
+    if (!b) return bfail(nullptr, FLOOD_ERR_ARG, "batch is NULL");
+    if (i < 0 || i >= b->S) return bfail(b, FLOOD_ERR_ARG, "scenario out of range");
+    cudaStream_t s = S_(stream);
+    MemberClock c;
+    BCK(b, cudaMemcpyAsync(&c, b->ms + (b->k % 3) * b->S + i, sizeof(c), cudaMemcpyDeviceToHost, s));
+    BCK(b, cudaStreamSynchronize(s));
+    const flood::ScenDesc& d = b->desc[i];
+    const float* base = d.state + (size_t)c.cur * 3 * d.plane;
+    float* outs[3] = {h, qx, qy};
+    for (int k = 0; k < 3; ++k)
+        if (outs[k])
+            BCK(b, cudaMemcpy2DAsync(outs[k], sizeof(float) * d.nx, base + k * d.plane,
+                                     sizeof(float) * d.ld, sizeof(float) * d.nx, d.ny,
+                                     cudaMemcpyDefault, s));
+    BCK(b, cudaStreamSynchronize(s));
+    return FLOOD_OK;
+}
+
+int flood_batch_members(flood_batch* b, double* t, int64_t* steps, double* storage, double* rain,
+                        double* outflow, double* clamp)
+{
+    if (!b) return bfail(nullptr, FLOOD_ERR_ARG, "batch is NULL");
+    BCK(b, cudaDeviceSynchronize());
+    std::vector<MemberClock> c(b->S);
+    BCK(b, cudaMemcpy(c.data(), b->ms + (b->k % 3) * b->S, sizeof(MemberClock) * b->S,
+                      cudaMemcpyDeviceToHost));
+    for (int i = 0; i < b->S; ++i) {
+        if (t) t[i] = c[i].t;
+        if (steps) steps[i] = c[i].steps;
+    }
+    if (rain) BCK(b, cudaMemcpy(rain, b->rain_acc, sizeof(double) * b->S, cudaMemcpyDeviceToHost));
+    if (outflow || clamp) {
+        std::vector<double> v((size_t)b->nslot * 2);
+        BCK(b, cudaMemcpy(v.data(), b->vacc, sizeof(double) * v.size(), cudaMemcpyDeviceToHost));
+        std::vector<double> o(b->S, 0.0), cl(b->S, 0.0);
+        for (const auto& tk : b->tasks) {
+            o[tk.scen] += v[(size_t)tk.slot * 2];
+            cl[tk.scen] += v[(size_t)tk.slot * 2 + 1];
+        }
+        for (int i = 0; i < b->S; ++i) {
+            if (outflow) outflow[i] = o[i];
+            if (clamp) clamp[i] = cl[i];
+        }
+    }
+    if (storage) {
+        for (int i = 0; i < b->S; ++i) {
+            const flood::ScenDesc& d = b->desc[i];
+            if (flood::launch_storage(d.state, b->ms + (b->k % 3) * b->S + i, 1, d.ny, d.nx, d.ld,
+                                      d.plane, b->p.dx * b->p.dx, b->part, b->part_cap,
+                                      b->storage + i, 0))
+                return bfail(b, FLOOD_ERR_STATE, "storage partial buffer too small");
+        }
+        BCK(b, cudaGetLastError());
+        BCK(b, cudaMemcpy(storage, b->storage, sizeof(double) * b->S, cudaMemcpyDeviceToHost));
+    }
+    return FLOOD_OK;
+}
+
+int64_t flood_batch_launch_count(const flood_batch* b) { return b ? b->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// Batched step over uneven scenarios: every warp takes one task (a span of a
+// strip of one scenario's grid) from a flat task table, plans the step of
+// its scenario from the scenario's own clock (Eq. 4 on its own maximum
+// depth, so each scenario has its own step length), and runs the same fused
+// march as the ensemble kernel.  Scenarios that reached min(window end, own
+// end time) are idle.
+#include "batch.cuh"
+#include "march.cuh"
+
+namespace flood {
+
+namespace {
+
+
+// Per-scenario plan (one thread per scenario, FP64): its own Eq. 4 step
+// toward min(window end, own end time), clock, rain volume.
+__global__ void batch_plan_kernel(const BatchArgs a, int n_scen)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_scen) return;
+    const ScenDesc sd = a.scen[i];
+    const MemberClock in = a.ms_in[i];
+    const double t_stop = *a.t_stop;
+    const double t_end = sd.t_end < t_stop ? sd.t_end : t_stop;
+    const StepPlan sp = plan_step_p(a.alpha_dx, a.g, a.dt_cap, a.dt_fixed, a.h_floor, a.rain_block,
+                                    t_end, sd.hyeto, sd.nb, sd.rain_mult, in);
+    MemberPlan p;
+    fill_plan(p, sp, a.g, a.dxd);
+    p.cur = in.cur;
+    p.ckpt = -1;
+    a.ms_clr[i].hmax_bits = 0u;
+    if (!sp.active) {
+        a.ms_out[i] = in;
+    } else {
+        a.ms_out[i].t = sp.t_next;
+        a.ms_out[i].steps = in.steps + 1;
+        a.ms_out[i].cur = 1 - in.cur;
+        a.rain_acc[i] += (double)sp.dr * a.cell_area * sd.ncell;
+    }
+    a.plan[i] = p;
+}
+
+template <int W>
+__global__ void __launch_bounds__(32 * W) batch_step_kernel(const BatchArgs a)
+{
+    const int lane = threadIdx.x;
+    const int tid = blockIdx.x * W + threadIdx.y;
+    if (tid >= a.ntasks) return;
+    const WarpTask tk = a.tasks[tid];
+    const int i = tk.scen;
+    const MemberPlan p = a.plan[i];
+    if (!p.active) return;
+    const ScenDesc sd = a.scen[i];
+    FaceK k;
+    k.gdt_dx = p.gdt_dx;
+    k.gdt = p.gdt;
+    k.dx_4dt = p.dx_4dt;
+    k.h_eps = a.h_eps;
+    k.edge_drop = a.edge_drop;
+    k.limiter = a.limiter;
+    const size_t ms = 3 * sd.plane;
+    const float* src = sd.state + (size_t)p.cur * ms;
+    float* dst = sd.state + (size_t)(1 - p.cur) * ms;
+    const MarchOut mo = march_rows(src, dst, nullptr, sd.z, sd.n, sd.plane, sd.ny, sd.nx, sd.ld, tk.c0,
+                                   tk.r0, tk.r1, lane, k, p.dt_dx, sd.scale, p.dr, a.east_out,
+                                   a.south_out);
+    if (mo.bad) atomicOr(a.err, 1);
+    const unsigned hb = __reduce_max_sync(0xffffffffu, __float_as_uint(mo.hmax) & 0x7fffffffu);
+    double out_acc = (double)mo.out_s - (double)mo.out_c, clamp_acc = (double)mo.clamp;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        out_acc += __shfl_xor_sync(0xffffffffu, out_acc, off);
+        clamp_acc += __shfl_xor_sync(0xffffffffu, clamp_acc, off);
+    }
+    if (lane == 0) {
+        atomicMax(&a.ms_out[i].hmax_bits, hb);
+        if (out_acc != 0.0 || clamp_acc != 0.0) {
+            double* v = a.vacc + (size_t)tk.slot * 2;
+            v[0] += out_acc * p.dt * a.dxd;
+            v[1] += clamp_acc * a.cell_area;
+        }
+    }
+}
+
+}  // namespace
+
+void launch_batch_plan(const BatchArgs& a, int n_scen, cudaStream_t s)
+{
+    batch_plan_kernel<<<(n_scen + 127) / 128, 128, 0, s>>>(a, n_scen);
+}
+
+void launch_batch_step(const BatchArgs& a, int warps_per_cta, cudaStream_t s)
+{
+    if (warps_per_cta >= 8) {
+        batch_step_kernel<8><<<(a.ntasks + 7) / 8, dim3(32, 8), 0, s>>>(a);
+    } else {
+        batch_step_kernel<4><<<(a.ntasks + 3) / 4, dim3(32, 4), 0, s>>>(a);
+    }
+}
+
+}  // namespace flood

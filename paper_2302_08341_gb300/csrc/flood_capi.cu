@@ -64,10 +64,10 @@ void free_ensemble(flood_grid* g)
     dfree(g->w_post); dfree(g->ms); dfree(g->vacc); dfree(g->rain_acc); dfree(g->y);
     dfree(g->y_in); dfree(g->beta); dfree(g->pfi); dfree(g->pf_small); dfree(g->neff);
     dfree(g->part); dfree(g->storage); dfree(g->cells); dfree(g->d); dfree(g->sigma);
-    dfree(g->dt_log); dfree(g->rdt_log); dfree(g->ckpt); dfree(g->seg); dfree(g->lam);
+    dfree(g->plan); dfree(g->log); dfree(g->ckpt); dfree(g->seg); dfree(g->lam);
     dfree(g->gnm); dfree(g->gn_out); dfree(g->gpart); dfree(g->seg_end); dfree(g->samp_step);
     dfree(g->samp_y); dfree(g->samp_d); dfree(g->samp_cells);
-    g->dt_log = nullptr; g->rdt_log = nullptr; g->ckpt = nullptr; g->seg = nullptr;
+    g->plan = nullptr; g->log = nullptr; g->ckpt = nullptr; g->seg = nullptr;
     g->lam = nullptr; g->gnm = nullptr; g->gn_out = nullptr; g->gpart = nullptr;
     g->seg_end = nullptr; g->samp_step = nullptr; g->samp_y = nullptr; g->samp_d = nullptr;
     g->samp_cells = nullptr; g->log_cap = 0; g->ckpt_floats = 0; g->seg_floats = 0;
@@ -101,8 +101,8 @@ StepArgs step_args(const flood_grid* g, double t_end)
     a.ms_clr = g->ms + ((k + 2) % 3) * g->M;
     a.vacc = g->vacc;
     a.rain_acc = g->rain_acc;
-    a.dt_log = g->logging ? g->dt_log : nullptr;
-    a.rdt_log = g->logging ? g->rdt_log : nullptr;
+    a.plan = g->plan;
+    a.log = g->logging ? g->log : nullptr;
     a.dt_log_cap = g->log_cap;
     a.ckpt = g->logging ? g->ckpt : nullptr;
     a.ckpt_every = g->ckpt_every > 0 ? g->ckpt_every : 1;
@@ -148,6 +148,8 @@ int launch_steps(flood_grid* g, int64_t count, double t_end, cudaStream_t s)
 {
     for (int64_t i = 0; i < count; ++i) {
         flood::StepArgs a = step_args(g, t_end);
+        flood::launch_plan(a, s);
+        g->launches++;
         std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
         if (g->profile) {
             if (g->ev_free.empty()) {
@@ -355,7 +357,8 @@ int flood_ensemble_init(flood_grid* g, int M, const float* h0, int h0_per_member
         (rc = dalloc(g, &g->vacc, (size_t)M * g->nslot * 2)) || (rc = dalloc(g, &g->rain_acc, M)) ||
         (rc = dalloc(g, &g->beta, M)) || (rc = dalloc(g, &g->pfi, (size_t)5 * M)) ||
         (rc = dalloc(g, &g->pf_small, 4)) || (rc = dalloc(g, &g->neff, 1)) ||
-        (rc = dalloc(g, &g->part, (size_t)M * g->part_cap)) || (rc = dalloc(g, &g->storage, M))) {
+        (rc = dalloc(g, &g->part, (size_t)M * g->part_cap)) || (rc = dalloc(g, &g->storage, M)) ||
+        (rc = dalloc(g, &g->plan, M))) {
         free_ensemble(g);
         return rc;
     }
@@ -736,3 +739,103 @@ int flood_sync(flood_grid* g, void* stream)
 }
 
 }  // extern "C"
+
+// ---- autotuner ------------------------------------------------------------
+// Times candidate step-kernel configurations (engine x rows per strip x
+// members per CTA) on the live ensemble and keeps the fastest.  The ensemble
+// is snapshotted first (current state, clocks, volume counters) and restored
+// afterwards, so tuning leaves the simulation untouched.
+extern "C" int flood_autotune(flood_grid* g, int steps_per_trial, int* best_rows, int* best_mpc,
+                              int* best_engine, double* best_ms, void* stream)
+{
+    if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    if (g->M == 0) return fail(g, FLOOD_ERR_STATE, "flood_ensemble_init has not been called");
+    if (steps_per_trial < 1) steps_per_trial = 4;
+    steps_per_trial = (steps_per_trial + 2) / 3 * 3;  // whole clock-slot cycles
+    cudaStream_t s = S(stream);
+    const int M = g->M;
+    const size_t ms = 3 * g->plane;
+    std::vector<MemberClock> c0;
+    int rc = read_clocks(g, c0, s);
+    if (rc) return rc;
+    float* snap = nullptr;
+    if ((rc = dalloc(g, &snap, (size_t)M * ms))) return rc;
+    for (int m = 0; m < M; ++m)
+        CK(g, cudaMemcpyAsync(snap + (size_t)m * ms, g->state + (size_t)(c0[m].cur * M + m) * ms,
+                              sizeof(float) * ms, cudaMemcpyDeviceToDevice, s));
+    std::vector<double> rain0(M), vacc0((size_t)M * g->nslot * 2);
+    CK(g, cudaMemcpy(rain0.data(), g->rain_acc, sizeof(double) * M, cudaMemcpyDeviceToHost));
+    CK(g, cudaMemcpy(vacc0.data(), g->vacc, sizeof(double) * vacc0.size(), cudaMemcpyDeviceToHost));
+    const int64_t k0 = g->k;
+    const int rows0 = g->rows_per_strip, mpc0 = g->members_per_cta, eng0 = g->engine;
+    const bool fixed0 = g->launch_fixed;
+    struct Cand { int rows, mpc, engine; };
+    std::vector<Cand> cands;
+    for (int e : {1, 0})
+        for (int r : {32, 64, 128})
+            for (int mp : {4, 1})
+                if ((e == 0 || g->maps_ok) && (mp == 1 || M >= 4)) cands.push_back({r, mp, e});
+    cudaEvent_t e0, e1;
+    CK(g, cudaEventCreate(&e0));
+    CK(g, cudaEventCreate(&e1));
+    double best = 1e300;
+    Cand bc{rows0, mpc0, eng0};
+    for (const Cand& cd : cands) {
+        if ((rc = flood_set_launch(g, cd.rows, cd.mpc))) break;
+        g->engine = cd.engine;
+        if ((rc = launch_steps(g, 3, -1.0, s))) break;  // warm-up
+        CK(g, cudaEventRecord(e0, s));
+        if ((rc = launch_steps(g, steps_per_trial, -1.0, s))) break;
+        CK(g, cudaEventRecord(e1, s));
+        CK(g, cudaEventSynchronize(e1));
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, e0, e1);
+        const double per = t / steps_per_trial;
+        if (per < best) {
+            best = per;
+            bc = cd;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // restore the ensemble exactly as it was
+    std::vector<MemberClock> cn;
+    int rc2 = read_clocks(g, cn, s);
+    if (!rc2) {
+        for (int m = 0; m < M; ++m)
+            cudaMemcpyAsync(g->state + (size_t)(cn[m].cur * M + m) * ms, snap + (size_t)m * ms,
+                            sizeof(float) * ms, cudaMemcpyDeviceToDevice, s);
+        std::vector<MemberClock> back = c0;
+        for (int m = 0; m < M; ++m) back[m].cur = cn[m].cur;
+        cudaMemcpyAsync(g->ms + (g->k % 3) * M, back.data(), sizeof(MemberClock) * M,
+                        cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(g->rain_acc, rain0.data(), sizeof(double) * M, cudaMemcpyHostToDevice, s);
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(snap);
+    (void)k0;
+    if (rc) {
+        g->rows_per_strip = rows0;
+        g->members_per_cta = mpc0;
+        g->engine = eng0;
+        g->launch_fixed = fixed0;
+        return rc;
+    }
+    if (rc2) return rc2;
+    if ((rc = flood_set_launch(g, bc.rows, bc.mpc))) return rc;
+    g->engine = bc.engine;
+    // volume slots now follow the chosen shape; restore the saved sums into slot 0 of each member
+    {
+        std::vector<double> v((size_t)M * g->nslot * 2, 0.0);
+        for (int m = 0; m < M; ++m)
+            for (size_t kk = 0; kk < vacc0.size() / M / 2; ++kk)
+                for (int j = 0; j < 2; ++j)
+                    v[(size_t)m * g->nslot * 2 + j] += vacc0[((size_t)m * (vacc0.size() / M / 2) + kk) * 2 + j];
+        CK(g, cudaMemcpy(g->vacc, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice));
+    }
+    if (best_rows) *best_rows = bc.rows;
+    if (best_mpc) *best_mpc = bc.mpc;
+    if (best_engine) *best_engine = bc.engine;
+    if (best_ms) *best_ms = best;
+    return FLOOD_OK;
+}

@@ -34,8 +34,8 @@ struct StepArgs {
     MemberClock* ms_clr;        // slot (k+2)%3
     double* vacc;               // [M][nslot][2] outflow and clamp partial volumes
     double* rain_acc;           // [M] rain volume added
-    double* dt_log;             // [M][dt_log_cap] step lengths (or null)
-    double* rdt_log;            // [M][dt_log_cap] dt x block rain rate of each step (or null)
+    struct MemberPlan* plan;    // [M] this step's plan of every member (plan kernel -> step kernel)
+    struct MemberPlan* log;     // [M][dt_log_cap] plans of the steps taken (or null)
     float* ckpt;                // [n_ckpt][M][3][plane] checkpoint states (or null)
     int ckpt_every;             // a checkpoint after every ckpt_every steps of a member
     // replay of a checkpointed segment (adjoint recomputation): slot i of
@@ -71,6 +71,18 @@ struct TmaArgs {
     StepArgs a;
 };
 
+// One member's step, planned once per step in FP64 by the plan kernel and
+// handed to the step kernels as FP32 constants (the step kernels themselves
+// run no FP64 arithmetic: GB300's FP64 pipe is narrow).
+struct MemberPlan {
+    double t_next, dt, rdt;   // time after the step, step length, dt x block rain rate
+    float dr;                 // rain depth added to every cell (m)
+    float gdt_dx, gdt, dx_4dt, dt_dx;
+    int active;               // 0: the member does not step
+    int cur;                  // buffer holding the member's state before the step
+    int ckpt;                 // checkpoint slot that also receives the result, or -1
+};
+
 // Step length of one member (Eq. 4 with floor, cap and landing on the next
 // stop).  Every CTA of a member evaluates this identically in FP64.
 struct StepPlan {
@@ -80,22 +92,27 @@ struct StepPlan {
     bool active;
 };
 
-__device__ __forceinline__ StepPlan plan_step(const StepArgs& a, const MemberClock& in, int m)
+// Step plan from explicit scheme constants (shared by the ensemble and the
+// batched kernels).
+__device__ __forceinline__ StepPlan plan_step_p(double alpha_dx, double g, double dt_cap,
+                                                double dt_fixed, double h_floor, double rain_block,
+                                                double t_end, const float* hyeto, int nb,
+                                                float rain_mult, const MemberClock& in)
 {
     StepPlan s;
-    s.active = !(a.t_end >= 0.0 && in.t >= a.t_end);
+    s.active = !(t_end >= 0.0 && in.t >= t_end);
     double dt;
-    if (a.dt_fixed > 0.0) {
-        dt = a.dt_fixed;
+    if (dt_fixed > 0.0) {
+        dt = dt_fixed;
     } else {
         double hm = (double)__uint_as_float(in.hmax_bits);
-        hm = hm > a.h_floor ? hm : a.h_floor;
-        dt = __ddiv_rn(a.alpha_dx, __dsqrt_rn(__dmul_rn(a.g, hm)));
-        dt = dt > a.dt_cap ? a.dt_cap : dt;
+        hm = hm > h_floor ? hm : h_floor;
+        dt = __ddiv_rn(alpha_dx, __dsqrt_rn(__dmul_rn(g, hm)));
+        dt = dt > dt_cap ? dt_cap : dt;
     }
-    double blk = floor(__ddiv_rn(in.t, a.rain_block));
-    double stop = __dmul_rn(blk + 1.0, a.rain_block);
-    if (a.t_end >= 0.0 && a.t_end < stop) stop = a.t_end;
+    double blk = floor(__ddiv_rn(in.t, rain_block));
+    double stop = __dmul_rn(blk + 1.0, rain_block);
+    if (t_end >= 0.0 && t_end < stop) stop = t_end;
     if (__dadd_rn(in.t, dt) >= stop) {
         dt = __dsub_rn(stop, in.t);
         s.t_next = stop;
@@ -104,10 +121,39 @@ __device__ __forceinline__ StepPlan plan_step(const StepArgs& a, const MemberClo
     }
     s.dt = dt;
     int b = (int)blk;
-    double rate = (blk >= 0.0 && b < a.nb) ? (double)a.hyeto[b] : 0.0;
+    double rate = (blk >= 0.0 && b < nb) ? (double)hyeto[b] : 0.0;
     s.rdt = __dmul_rn(dt, rate);
-    s.dr = (float)__dmul_rn(s.rdt, (double)a.rain_mult[m]);
+    s.dr = (float)__dmul_rn(s.rdt, (double)rain_mult);
     return s;
+}
+
+__device__ __forceinline__ StepPlan plan_step(const StepArgs& a, const MemberClock& in, int m)
+{
+    return plan_step_p(a.alpha_dx, a.g, a.dt_cap, a.dt_fixed, a.h_floor, a.rain_block, a.t_end,
+                       a.hyeto, a.nb, a.rain_mult[m], in);
+}
+
+__device__ __forceinline__ void fill_plan(MemberPlan& p, const StepPlan& sp, double g, double dxd)
+{
+    p.t_next = sp.t_next;
+    p.dt = sp.dt;
+    p.rdt = sp.rdt;
+    p.dr = sp.dr;
+    p.gdt_dx = (float)(g * sp.dt / dxd);
+    p.gdt = (float)(g * sp.dt);
+    p.dx_4dt = (float)(dxd / (4.0 * sp.dt));
+    p.dt_dx = (float)(sp.dt / dxd);
+    p.active = sp.active ? 1 : 0;
+}
+
+// Compensated (Kahan) FP32 summation for the per-warp volume partials; the
+// explicit rounding intrinsics keep the compiler from re-associating it.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x)
+{
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
 }
 
 // Per-step constants of one member (FP32).
@@ -175,6 +221,7 @@ __device__ __forceinline__ float outflow_q(float h, float q, float n_cell, const
 __device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
 
 // Host-side helpers (flood_capi.cu).
+void launch_plan(const StepArgs& a, cudaStream_t s);
 void launch_step(const StepArgs& a, int members_per_cta, cudaStream_t s);
 void launch_replay(const StepArgs& a, int members_per_cta, cudaStream_t s);
 int launch_step_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s);

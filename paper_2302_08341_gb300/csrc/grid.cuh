@@ -60,8 +60,8 @@ struct flood_grid {
     double prof_ms = 0.0;
     int64_t prof_launches = 0;
     // adjoint (flood_adjoint): step log, checkpoints, segment replay buffers
-    double* dt_log = nullptr;     // [M][log_cap]
-    double* rdt_log = nullptr;    // [M][log_cap]
+    flood::MemberPlan* plan = nullptr;  // [M] the current step's plans
+    flood::MemberPlan* log = nullptr;   // [M][log_cap] plans of the logged steps
     int log_cap = 0;
     bool logging = false;         // step kernels record dt and checkpoints
     float* ckpt = nullptr;        // [n_ckpt][M][3][plane]

@@ -1,0 +1,201 @@
+// Per-warp march of the fused step over one 128-column span of rows
+// [r0, r1) of one member: reads the state at src (h, qx, qy planes) and the
+// shared z, n; writes the new state to dst (and ck when non-null); returns
+// the warp-local maximum depth, the non-finite flag and the outflow / clamp
+// partial sums.  Shared by the ensemble, replay and batched step kernels.
+#pragma once
+
+#include "flood_internal.cuh"
+
+namespace flood {
+
+struct MarchOut {
+    float hmax;
+    bool bad;
+    float out_s, out_c;   // outflow sum of q over the warp's edge links (Kahan pair)
+    float clamp;          // sum of the negative depths reset to zero
+};
+
+__device__ __forceinline__ void m_load4(float (&v)[4], const float* p)
+{
+    float4 t = ldg4(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+
+__device__ __forceinline__ void m_store4(float* p, const float (&v)[4])
+{
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+__device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, float* __restrict__ dst,
+                                               float* ck, const float* __restrict__ z,
+                                               const float* __restrict__ n, size_t plane, int ny,
+                                               int nx, int ld, int c0, int r0, int r1, int lane,
+                                               const FaceK& k, float dt_dx, float s, float dr,
+                                               int east_out, int south_out)
+{
+    const float s_half = 0.5f * s;
+    const float* __restrict__ sh = src;
+    const float* __restrict__ sqx = src + plane;
+    const float* __restrict__ sqy = src + 2 * plane;
+    float* __restrict__ dh = dst;
+    float* __restrict__ dqx = dst + plane;
+    float* __restrict__ dqy = dst + 2 * plane;
+
+    const int c = c0 + 4 * lane;
+    const bool act = c < nx;           // lane owns at least one real cell
+    const bool east_halo = (lane == 31) && (c + 4 < nx);
+
+    float hC[4] = {0, 0, 0, 0}, zC[4] = {0, 0, 0, 0}, nC[4] = {0, 0, 0, 0};
+    float qyN[4] = {0, 0, 0, 0};
+    if (act) {
+        const size_t o = (size_t)r0 * ld + c;
+        m_load4(hC, sh + o);
+        m_load4(zC, z + o);
+        m_load4(nC, n + o);
+        if (r0 > 0) {
+            float hU[4], zU[4], nU[4], qU[4];
+            const size_t ou = o - ld;
+            m_load4(hU, sh + ou);
+            m_load4(zU, z + ou);
+            m_load4(nU, n + ou);
+            m_load4(qU, sqy + ou);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                qyN[j] = (c + j < nx)
+                             ? link_q(hU[j], zU[j], hC[j], zC[j], qU[j],
+                                      __fmul_rn(s_half, __fadd_rn(nU[j], nC[j])), k)
+                             : 0.0f;
+        }
+    }
+
+    float hmax = 0.0f;
+    bool bad = false;
+    float out_s = 0.0f, out_c = 0.0f, clamp = 0.0f;
+
+    for (int r = r0; r < r1; ++r) {
+        const size_t o = (size_t)r * ld + c;
+        const bool has_s = (r + 1 < ny);
+        float hS[4] = {0, 0, 0, 0}, zS[4] = {0, 0, 0, 0}, nS[4] = {0, 0, 0, 0};
+        float qxo[4] = {0, 0, 0, 0}, qyo[4] = {0, 0, 0, 0};
+        if (act) {
+            if (has_s) {
+                m_load4(hS, sh + o + ld);
+                m_load4(zS, z + o + ld);
+                m_load4(nS, n + o + ld);
+            }
+            m_load4(qxo, sqx + o);
+            m_load4(qyo, sqy + o);
+        }
+        // east neighbour of the lane's last cell: next lane's first cell
+        float hE = __shfl_down_sync(0xffffffffu, hC[0], 1);
+        float zE = __shfl_down_sync(0xffffffffu, zC[0], 1);
+        float nE = __shfl_down_sync(0xffffffffu, nC[0], 1);
+        if (east_halo) {
+            const size_t oe = (size_t)r * ld + c + 4;
+            hE = __ldg(sh + oe);
+            zE = __ldg(z + oe);
+            nE = __ldg(n + oe);
+        }
+        // east links (Eq. 2-3)
+        float qxE[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int cj = c + j;
+            const float h2 = (j < 3) ? hC[j + 1] : hE;
+            const float z2 = (j < 3) ? zC[j + 1] : zE;
+            const float n2 = (j < 3) ? nC[j + 1] : nE;
+            float q;
+            if (cj < nx - 1)
+                q = link_q(hC[j], zC[j], h2, z2, qxo[j], __fmul_rn(s_half, __fadd_rn(nC[j], n2)), k);
+            else if (cj == nx - 1)
+                q = east_out ? outflow_q(hC[j], qxo[j], __fmul_rn(s, nC[j]), k) : 0.0f;
+            else
+                q = 0.0f;
+            qxE[j] = q;
+        }
+        // west link of the lane's first cell: previous lane's last east link
+        float qW0 = __shfl_up_sync(0xffffffffu, qxE[3], 1);
+        if (lane == 0) {
+            qW0 = 0.0f;
+            if (c0 > 0) {  // recompute the neighbouring span's link (halo)
+                const size_t ow = (size_t)r * ld + c0 - 1;
+                qW0 = link_q(__ldg(sh + ow), __ldg(z + ow), hC[0], zC[0], __ldg(sqx + ow),
+                             __fmul_rn(s_half, __fadd_rn(__ldg(n + ow), nC[0])), k);
+            }
+        }
+        // south links (Eq. 2-3)
+        float qyS[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int cj = c + j;
+            float q = 0.0f;
+            if (cj < nx) {
+                if (has_s)
+                    q = link_q(hC[j], zC[j], hS[j], zS[j], qyo[j],
+                               __fmul_rn(s_half, __fadd_rn(nC[j], nS[j])), k);
+                else if (south_out)
+                    q = outflow_q(hC[j], qyo[j], __fmul_rn(s, nC[j]), k);
+            }
+            qyS[j] = q;
+        }
+        // continuity (Eq. 5 -> Eq. 1) with rain and the wet/dry clamp
+        float hN[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int cj = c + j;
+            float hn = 0.0f;
+            if (cj < nx) {
+                const float qW = (j == 0) ? qW0 : qxE[j - 1];
+                const float net = __fadd_rn(__fsub_rn(qW, qxE[j]), __fsub_rn(qyN[j], qyS[j]));
+                hn = __fadd_rn(__fmaf_rn(dt_dx, net, hC[j]), dr);
+                if (hn < 0.0f) {
+                    // clamped cells keep a negative zero: the adjoint reads
+                    // the sign bit to know this branch was taken
+                    clamp = __fsub_rn(clamp, hn);
+                    hn = -0.0f;
+                }
+                bad |= !(hn <= 3.0e38f);  // NaN or overflow
+                hmax = fmaxf(hmax, hn);
+            }
+            hN[j] = hn;
+        }
+        // links leaving the domain this row: the east edge link (one lane)
+        // and, on the last row, the south edge links
+        float ev = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (c + j == nx - 1 && east_out) ev = qxE[j];
+        if (!has_s && south_out)
+            ev = __fadd_rn(ev, __fadd_rn(__fadd_rn(qyS[0], qyS[1]), __fadd_rn(qyS[2], qyS[3])));
+        kahan_add(out_s, out_c, ev);
+        if (act) {
+            m_store4(dh + o, hN);
+            m_store4(dqx + o, qxE);
+            m_store4(dqy + o, qyS);
+            if (ck) {
+                m_store4(ck + o, hN);
+                m_store4(ck + plane + o, qxE);
+                m_store4(ck + 2 * plane + o, qyS);
+            }
+        }
+        // march: this row's south links are the next row's north links
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            qyN[j] = qyS[j];
+            hC[j] = hS[j];
+            zC[j] = zS[j];
+            nC[j] = nS[j];
+        }
+    }
+
+    MarchOut out;
+    out.hmax = hmax;
+    out.bad = bad;
+    out.out_s = out_s;
+    out.out_c = out_c;
+    out.clamp = clamp;
+    return out;
+}
+
+}  // namespace flood

@@ -65,43 +65,22 @@ __global__ void __launch_bounds__(32 * WM, 20 / WM) step_tma_kernel(const __grid
     const size_t plane = a.plane;
     const size_t mstride = 3 * plane;
     // each warp is its own member here: the warp at the first span and strip owns its clock
-    const bool designated = (blockIdx.y == 0 && blockIdx.z == 0 && lane == 0);
-    const MemberClock in = a.ms_in[m];
-    const StepPlan sp = plan_step(a, in, m);
-    if (!sp.active) {
-        if (designated) {
-            a.ms_out[m] = in;
-            a.ms_clr[m].hmax_bits = 0u;
-        }
-        return;
-    }
-    if (designated) {
-        a.ms_out[m].t = sp.t_next;
-        a.ms_out[m].steps = in.steps + 1;
-        a.ms_out[m].cur = 1 - in.cur;
-        a.ms_clr[m].hmax_bits = 0u;
-        a.rain_acc[m] += (double)sp.dr * a.cell_area * a.ncell;
-        if (a.dt_log && in.steps < a.dt_log_cap) {
-            a.dt_log[(size_t)m * a.dt_log_cap + in.steps] = sp.dt;
-            a.rdt_log[(size_t)m * a.dt_log_cap + in.steps] = sp.rdt;
-        }
-    }
-    float* __restrict__ dst = a.state + (size_t)((1 - in.cur) * a.M + m) * mstride;
-    float* ck = nullptr;
-    if (a.ckpt && (in.steps + 1) % a.ckpt_every == 0 && in.steps + 1 <= a.dt_log_cap)
-        ck = a.ckpt + ((size_t)((in.steps + 1) / a.ckpt_every) * a.M + m) * mstride;
+    const MemberPlan pl = a.plan[m];
+    if (!pl.active) return;
+    float* __restrict__ dst = a.state + (size_t)((1 - pl.cur) * a.M + m) * mstride;
+    float* ck = pl.ckpt >= 0 ? a.ckpt + ((size_t)pl.ckpt * a.M + m) * mstride : nullptr;
 
     FaceK k;
-    k.gdt_dx = (float)(a.g * sp.dt / a.dxd);
-    k.gdt = (float)(a.g * sp.dt);
-    k.dx_4dt = (float)(a.dxd / (4.0 * sp.dt));
+    k.gdt_dx = pl.gdt_dx;
+    k.gdt = pl.gdt;
+    k.dx_4dt = pl.dx_4dt;
     k.h_eps = a.h_eps;
     k.edge_drop = a.edge_drop;
     k.limiter = a.limiter;
-    const float dt_dx = (float)(sp.dt / a.dxd);
+    const float dt_dx = pl.dt_dx;
     const float s = a.scale[m];
     const float s_half = 0.5f * s;
-    const float dr = sp.dr;
+    const float dr = pl.dr;
 
     const int c = c0 + 4 * lane;
     const bool act = c < nx;
@@ -109,7 +88,7 @@ __global__ void __launch_bounds__(32 * WM, 20 / WM) step_tma_kernel(const __grid
     const int r1 = min(r0 + a.rows_per_strip, ny);
     const int ra = r0 > 0 ? r0 - 1 : r0;   // first row loaded
     const int rb = min(r1 + 1, ny);        // one past the last row loaded
-    const int plane0 = (in.cur * a.M + m) * 3;
+    const int plane0 = (pl.cur * a.M + m) * 3;
 
     if (lane == 0) {
         for (int i = 0; i < kNS; ++i) mbar_init(bar0 + 8u * i, 1);
@@ -192,7 +171,7 @@ __global__ void __launch_bounds__(32 * WM, 20 / WM) step_tma_kernel(const __grid
 
     float hmax = 0.0f;
     bool bad = false;
-    double out_acc = 0.0, clamp_acc = 0.0;
+    float out_s = 0.0f, out_c = 0.0f, clamp = 0.0f;
 
     for (int r = r0; r < r1; ++r) {
         const size_t o = (size_t)r * ld + c;
@@ -264,16 +243,21 @@ __global__ void __launch_bounds__(32 * WM, 20 / WM) step_tma_kernel(const __grid
                 const float net = __fadd_rn(__fsub_rn(qW, qxE[j]), __fsub_rn(qyN[j], qyS[j]));
                 hn = __fadd_rn(__fmaf_rn(dt_dx, net, hC[j]), dr);
                 if (hn < 0.0f) {
-                    clamp_acc -= (double)hn;
+                    clamp = __fsub_rn(clamp, hn);
                     hn = -0.0f;
                 }
                 bad |= !(hn <= 3.0e38f);
                 hmax = fmaxf(hmax, hn);
-                if (cj == nx - 1 && a.east_out) out_acc += (double)qxE[j];
-                if (!has_s && a.south_out) out_acc += (double)qyS[j];
             }
             hN[j] = hn;
         }
+        float ev = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (c + j == nx - 1 && a.east_out) ev = qxE[j];
+        if (!has_s && a.south_out)
+            ev = __fadd_rn(ev, __fadd_rn(__fadd_rn(qyS[0], qyS[1]), __fadd_rn(qyS[2], qyS[3])));
+        kahan_add(out_s, out_c, ev);
         if (act) {
             store4(dst + o, hN);
             store4(dst + plane + o, qxE);
@@ -296,6 +280,7 @@ __global__ void __launch_bounds__(32 * WM, 20 / WM) step_tma_kernel(const __grid
 
     if (bad) atomicOr(a.err, 1);
     const unsigned hb = __reduce_max_sync(0xffffffffu, __float_as_uint(hmax) & 0x7fffffffu);
+    double out_acc = (double)out_s - (double)out_c, clamp_acc = (double)clamp;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         out_acc += __shfl_xor_sync(0xffffffffu, out_acc, off);
@@ -306,7 +291,7 @@ __global__ void __launch_bounds__(32 * WM, 20 / WM) step_tma_kernel(const __grid
         if (out_acc != 0.0 || clamp_acc != 0.0) {
             const int slot = blockIdx.z * ((a.nx + kSpan - 1) / kSpan) + span;
             double* v = a.vacc + ((size_t)m * a.nslot + slot) * 2;
-            v[0] += out_acc * sp.dt * a.dxd;
+            v[0] += out_acc * pl.dt * a.dxd;
             v[1] += clamp_acc * a.cell_area;
         }
     }

@@ -60,7 +60,9 @@ def test_adjoint_agrees_with_central_differences(capi):
     reference: the GPU adjoint's rain-multiplier and Manning-scale gradients
     within 1e-3, the per-cell Manning gradient on 32 random wet cells within
     1e-3 (median) and 1e-2 (worst).  Central differences of the GPU's own FP32
-    forward agree within 1e-2 (FP32 rounding of the two runs bounds them)."""
+    forward (eps = 2e-2, since FP32 rounding of the two runs swamps smaller
+    steps, so the difference also carries O(eps^2) curvature) agree within
+    5e-2."""
     terr, h0, rm, sc, hy, cells, d, ns, sdt = _wet_case(M=1, seed=33)
     hy = synth.hyetograph_constant(100.0, 600.0)
     p = capi.Params.default(dt_fixed=0.5)
@@ -84,9 +86,10 @@ def test_adjoint_agrees_with_central_differences(capi):
         a, b = f64(e)
         fd = (a - b) / (2 * e)
         assert abs(fd - out[key][0]) <= 1e-3 * abs(fd), (key, fd, out[key][0])
-        a, b = f32(e)
-        fd32 = (a - b) / (2 * e)
-        assert abs(fd32 - out[key][0]) <= 1e-2 * abs(fd), (key, fd32, out[key][0])
+        e32 = 2e-2 * x0  # FP32 rounding of the two runs swamps smaller steps
+        a, b = f32(e32)
+        fd32 = (a - b) / (2 * e32)
+        assert abs(fd32 - out[key][0]) <= 5e-2 * abs(fd), (key, fd32, out[key][0])
 
     g = out["grad_n"].astype(np.float64)
     rng = np.random.default_rng(7)
@@ -145,7 +148,7 @@ def test_autograd_function_returns_the_adjoint_gradients(capi):
     loss.backward()
     ref = _gpu_adjoint(capi, terr, np.broadcast_to(h0, (2,) + h0.shape).copy(), rm, sc, hy, cells,
                        d, sdt)
-    assert abs(float(loss) - ref["loss"].sum()) <= 1e-12 * ref["loss"].sum()
+    assert abs(loss.item() - ref["loss"].sum()) <= 1e-12 * ref["loss"].sum()
     assert np.array_equal(n_t.grad.cpu().numpy(), ref["grad_n"])
     assert np.allclose(rm_t.grad.cpu().numpy(), ref["grad_rain"], rtol=1e-6)
     assert np.allclose(h0_t.grad.cpu().numpy(), ref["grad_h0"].sum(axis=0), rtol=1e-5, atol=1e-9)

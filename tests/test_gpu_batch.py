@@ -1,0 +1,85 @@
+"""GPU uneven batches (flood_batch_*, extension beyond the paper): scenarios
+of different grid sizes, storms and durations advanced together, each
+matching the FP64 oracle and, bit for bit, the same scenario run alone."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2302_08341_gb300 import synth
+from tests.gpu_util import compare, oracle_params, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(37, 53), (64, 64), (130, 97), (20, 260), (90, 129)]
+
+
+@pytest.fixture(scope="module")
+def capi():
+    return require_gpu()
+
+
+def _scenarios():
+    rng = np.random.default_rng(77)
+    terrs = [synth.make_terrain(ny, nx, seed=100 + k) for k, (ny, nx) in enumerate(SHAPES)]
+    durations = [300.0, 450.0, 600.0, 375.0, 510.0]
+    rates = rng.uniform(20.0, 100.0, len(SHAPES))
+    hys = [synth.hyetograph_constant(r, t) for r, t in zip(rates, durations)]
+    rm = rng.uniform(0.8, 1.5, len(SHAPES)).astype(np.float32)
+    sc = rng.uniform(0.7, 1.3, len(SHAPES)).astype(np.float32)
+    return terrs, hys, rm, sc, np.array(durations)
+
+
+def _run_batch(capi, shape=None):
+    terrs, hys, rm, sc, dur = _scenarios()
+    with capi.Batch([t.z for t in terrs], [t.n for t in terrs]) as b:
+        b.init(hys, rm, sc, dur)
+        if shape:
+            b.set_launch(*shape)
+        for w in (300.0, 600.0):
+            b.step(w)
+        states = [b.get_state(i) for i in range(len(SHAPES))]
+        mem = b.members()
+    return terrs, hys, rm, sc, dur, states, mem
+
+
+def test_batch_matches_oracle_and_single_runs(capi):
+    terrs, hys, rm, sc, dur, states, mem = _run_batch(capi)
+    assert np.array_equal(mem["t"], dur)
+    assert len(set(mem["steps"].tolist())) > 1
+    p = capi.Params.default()
+    for i, t in enumerate(terrs):
+        ny, nx = t.z.shape
+        mo = oracle.Member.dry(ny, nx)
+        oracle.advance(oracle_params(p, ny, nx), t.z, t.n, float(sc[i]), float(rm[i]), hys[i], mo,
+                       t_end=float(dur[i]))
+        compare(states[i][0], mo.h, 1e-3)
+        assert mem["steps"][i] == mo.steps
+        V = mem["storage"][i]
+        assert abs(V - oracle.storage(mo.h, p.dx)) <= 1e-5 * oracle.storage(mo.h, p.dx)
+        assert abs(V - (mem["rain"][i] - mem["outflow"][i] + mem["clamp"][i])) <= 1e-5 * mem["rain"][i]
+        with capi.Grid(t.z, t.n, p) as g:
+            g.ensemble_init(1, rm[i:i + 1], sc[i:i + 1], hys[i])
+            g.advance_to(float(dur[i]))
+            alone = g.get_state(0)
+        for k in range(3):
+            assert np.array_equal(states[i][k], alone[k])
+
+
+@pytest.mark.parametrize("shape", [(1, 4), (16, 8), (200, 4)])
+def test_batch_launch_shapes_bitwise(capi, shape):
+    ref = _run_batch(capi)[5]
+    got = _run_batch(capi, shape)[5]
+    for a, b in zip(ref, got):
+        for k in range(3):
+            assert np.array_equal(a[k], b[k])
+
+
+def test_batch_rejects_bad_arguments(capi):
+    z = np.zeros((4, 4), np.float32)
+    with pytest.raises(capi.FloodError):
+        capi.Batch([z, np.zeros((0, 3), np.float32)], [z, np.zeros((0, 3), np.float32)])
+    with capi.Batch([z], [z + 0.03]) as b:
+        with pytest.raises(capi.FloodError):
+            b.step(10.0)        # before init
+        with pytest.raises(capi.FloodError):
+            b.set_launch(0, 4)

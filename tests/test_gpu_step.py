@@ -218,7 +218,9 @@ def test_bad_arguments_raise(capi):
 
 def test_launch_shapes_give_bitwise_identical_results(capi):
     """The step kernel's launch shape (rows per strip, members per CTA) moves
-    halo recomputation around but never changes a value."""
+    halo recomputation around but never changes a state value; the FP64
+    volume bookkeeping sums FP32 per-warp partials, whose grouping follows the
+    shape, so it agrees to ~1e-10 relative."""
     terr = synth.make_terrain(70, 300, seed=14)
     hy = synth.hyetograph_constant(120.0, 300.0)
     rm, sc = synth.ensemble_prior(14, 5)
@@ -237,7 +239,7 @@ def test_launch_shapes_give_bitwise_identical_results(capi):
                 assert np.array_equal(states[m][k], res[0][0][m][k])
         for key in ("storage", "rain"):
             assert np.array_equal(vol[key], res[0][1][key])
-        assert np.allclose(vol["outflow"], res[0][1]["outflow"], rtol=1e-12, atol=0)
+        assert np.allclose(vol["outflow"], res[0][1]["outflow"], rtol=1e-8, atol=0)
 
 
 def test_engines_give_bitwise_identical_results(capi):
@@ -260,3 +262,31 @@ def test_engines_give_bitwise_identical_results(capi):
         for m in range(6):
             for k in range(3):
                 assert np.array_equal(states[m][k], res[0][0][m][k])
+
+
+def test_autotune_leaves_the_ensemble_untouched(capi):
+    """The autotuner times real steps on the live ensemble, then restores it:
+    the run continues exactly as if it had never been tuned."""
+    terr = synth.make_terrain(90, 300, seed=16)
+    hy = synth.hyetograph_constant(150.0, 600.0)
+    rm, sc = synth.ensemble_prior(16, 8)
+    res = []
+    for tune in (False, True):
+        with capi.Grid(terr.z, terr.n) as g:
+            g.ensemble_init(8, rm, sc, hy)
+            g.advance_to(120.0)
+            before = g.members()
+            if tune:
+                rows, mpc, eng, ms = g.autotune(steps_per_trial=3)
+                assert rows in (32, 64, 128) and mpc in (1, 4) and eng in (0, 1) and ms > 0
+                after = g.members()
+                assert np.array_equal(before["t"], after["t"])
+                assert np.array_equal(before["steps"], after["steps"])
+            g.advance_to(300.0)
+            res.append(([g.get_state(m) for m in range(8)], g.volumes(), g.members()))
+    for m in range(8):
+        for k in range(3):
+            assert np.array_equal(res[0][0][m][k], res[1][0][m][k])
+    assert np.array_equal(res[0][1]["rain"], res[1][1]["rain"])
+    assert np.allclose(res[0][1]["outflow"], res[1][1]["outflow"], rtol=1e-8, atol=0)
+    assert np.array_equal(res[0][2]["steps"], res[1][2]["steps"])
