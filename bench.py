@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--members", type=int, default=96)
     ap.add_argument("--no-extensions", action="store_true",
                     help="skip the adjoint and uneven-batch measurements")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch configuration (profiling runs)")
     args = ap.parse_args()
     global NY, NX, M
     NY, NX, M = args.ny, args.nx, args.members
@@ -371,9 +373,11 @@ def run_gb300(args):
     for w in range(1, args.warmup + 1):
         window(g, w, d_all[w - 1], beta_all[w - 1], draws[w - 1][0], outs)
     torch.cuda.synchronize(device)
-    rows_t, mpc_t, eng_t, ms_t = g.autotune(steps_per_trial=6, stream=stream)
-    tuned = {"rows_per_strip": rows_t, "members_per_cta": mpc_t, "engine": eng_t,
-             "ms_per_step": ms_t}
+    tuned = None
+    if not args.no_autotune:
+        rows_t, mpc_t, eng_t, ms_t = g.autotune(steps_per_trial=6, stream=stream)
+        tuned = {"rows_per_strip": rows_t, "members_per_cta": mpc_t, "engine": eng_t,
+                 "ms_per_step": ms_t}
 
     # timed windows from a fresh ensemble (the 1 h storm from t = 0)
     g.ensemble_init(M, rm, sc, hy, stream=stream)

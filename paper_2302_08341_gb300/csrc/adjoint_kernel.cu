@@ -47,24 +47,24 @@ __device__ __forceinline__ LinkD link_d(float h1, float z1, float h2, float z2, 
                                         const FaceK& k, float L)
 {
     LinkD r{0.0f, 0.0f, 0.0f, 0.0f};
-    const float zm = fmaxf(z1, z2);
-    const float a1 = __fadd_rn(h1, __fsub_rn(z1, zm));
-    const float a2 = __fadd_rn(h2, __fsub_rn(z2, zm));
+    const float dz = __fsub_rn(z2, z1);
+    const float a1 = __fsub_rn(h1, fmaxf(dz, 0.0f));
+    const float a2 = __fadd_rn(h2, fminf(dz, 0.0f));
     const float hf = fmaxf(a1, a2);
     if (!(hf > k.h_eps)) return r;
     const bool first = a1 >= a2;
-    const float dS = __fadd_rn(__fsub_rn(z2, z1), __fsub_rn(h2, h1));
+    const float dS = __fadd_rn(dz, __fsub_rn(h2, h1));
     const float num = __fmaf_rn(-__fmul_rn(k.gdt_dx, hf), dS, q);
     const float c = __fmul_rn(__fmul_rn(k.gdt, __fmul_rn(nl, nl)), fabsf(q));
     const float fric = __fmul_rn(c, inv_h73(hf));
     const float D = __fadd_rn(1.0f, fric);
-    const float qs = __fdividef(num, D);
+    const float invD = rcp_approx(D);
+    const float qs = __fmul_rn(num, invD);
     if (k.limiter) {
         const float lim = __fmul_rn(qs > 0.0f ? h1 : h2, k.dx_4dt);
         if (qs > lim) { r.dh1 = L; return r; }
         if (qs < -lim) { r.dh2 = -L; return r; }
     }
-    const float invD = __fdividef(1.0f, D);
     const float t = __fmul_rn(fric, invD);                      // fric / D in [0, 1)
     // dq'/dhf = -G dS / D + (7/3) q' t / hf ; dq'/d(dx S) = -G hf / D
     const float dq_dhf = __fmaf_rn(-k.gdt_dx * dS, invD, 2.33333333f * __fdividef(qs * t, hf));
@@ -86,10 +86,10 @@ __device__ __forceinline__ LinkD outflow_d(float h, float q, float ncell, const 
     const float c = __fmul_rn(__fmul_rn(k.gdt, __fmul_rn(ncell, ncell)), fabsf(q));
     const float fric = __fmul_rn(c, inv_h73(h));
     const float D = __fadd_rn(1.0f, fric);
-    const float qs = __fdividef(num, D);
+    const float invD = rcp_approx(D);
+    const float qs = __fmul_rn(num, invD);
     if (k.limiter && qs > __fmul_rn(h, k.dx_4dt)) { r.dh1 = L; return r; }
     if (!(qs > 0.0f)) return r;
-    const float invD = __fdividef(1.0f, D);
     const float t = __fmul_rn(fric, invD);
     r.dh1 = __fmaf_rn(k.gdt_dx * k.edge_drop, invD, 2.33333333f * __fdividef(qs * t, h));
     r.dq = invD - (q == 0.0f ? 0.0f : __fdividef(qs * t, q));

@@ -166,12 +166,33 @@ struct FaceK {
     int limiter;
 };
 
-// h^(-7/3) from the hardware base-2 logarithm and exponential
-// (h^(-7/3) = 2^(-7/3 log2 h)); capped so that h -> 0 gives a finite, huge
-// friction factor (q' -> 0) and q = 0 still gives exactly zero friction.
+// Hardware approximate base-2 logarithm, base-2 exponential and reciprocal
+// (one special-function-unit instruction each, denormals flushed to zero).
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// h^(-7/3) = 2^(-7/3 log2 h), capped so that h -> 0 (or h <= 0, which only
+// occurs on links that carry no flow) gives a finite, huge friction factor
+// and q = 0 still gives exactly zero friction.
 __device__ __forceinline__ float inv_h73(float h)
 {
-    return fminf(exp2f(__fmul_rn(-2.33333333f, __log2f(h))), 1.0e30f);
+    return fminf(ex2_approx(__fmul_rn(-2.33333333f, lg2_approx(h))), 1.0e30f);
 }
 
 // Eq. 2 given the flow depth hf, dx * S_surf (dS), the old flux q and the
@@ -181,7 +202,7 @@ __device__ __forceinline__ float eq2(float hf, float dS, float q, float n_link, 
     const float num = __fmaf_rn(-__fmul_rn(k.gdt_dx, hf), dS, q);
     const float c = __fmul_rn(__fmul_rn(k.gdt, __fmul_rn(n_link, n_link)), fabsf(q));
     const float fr = __fmul_rn(c, inv_h73(hf));
-    return __fdividef(num, __fadd_rn(1.0f, fr));
+    return __fmul_rn(num, rcp_approx(__fadd_rn(1.0f, fr)));
 }
 
 // Eq. 3 then Eq. 2 on one interior link (cell 1 on the low-index side, cell
@@ -194,16 +215,17 @@ __device__ __forceinline__ float eq2(float hf, float dS, float q, float n_link, 
 __device__ __forceinline__ float link_q(float h1, float z1, float h2, float z2, float q,
                                         float n_link, const FaceK& k)
 {
-    const float zm = fmaxf(z1, z2);
-    // h_flow = max(eta1, eta2) - max(z1, z2), formed from bed differences so
-    // the large bed elevation cancels exactly
-    const float hf = fmaxf(__fadd_rn(h1, __fsub_rn(z1, zm)), __fadd_rn(h2, __fsub_rn(z2, zm)));
+    // h_flow = max(eta1, eta2) - max(z1, z2) = max(h1 - max(dz, 0), h2 + min(dz, 0))
+    // with dz = z2 - z1: the large bed elevation cancels exactly
+    const float dz = __fsub_rn(z2, z1);
+    const float hf = fmaxf(__fsub_rn(h1, fmaxf(dz, 0.0f)), __fadd_rn(h2, fminf(dz, 0.0f)));
     // dx * S_surf = (z2 - z1) + (h2 - h1)
-    const float dS = __fadd_rn(__fsub_rn(z2, z1), __fsub_rn(h2, h1));
+    const float dS = __fadd_rn(dz, __fsub_rn(h2, h1));
     float qn = eq2(hf, dS, q, n_link, k);
     if (k.limiter) {
-        const float lim = __fmul_rn(qn > 0.0f ? h1 : h2, k.dx_4dt);
-        qn = fminf(fmaxf(qn, -lim), lim);
+        // |q'| <= h_upstream dx / (4 dt): with h1, h2 >= 0 the two one-sided
+        // clamps equal the clamp by the depth of the cell the flow leaves
+        qn = fmaxf(fminf(qn, __fmul_rn(h1, k.dx_4dt)), -__fmul_rn(h2, k.dx_4dt));
     }
     return hf > k.h_eps ? qn : 0.0f;
 }

@@ -27,6 +27,74 @@ __device__ __forceinline__ void m_store4(float* p, const float (&v)[4])
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
+// The links of one row of a lane's four cells: east links (Eq. 2-3, or the
+// free-outflow edge) and south links.  INTERIOR: all four cells and their
+// east neighbours lie inside the grid, so no per-cell edge tests are needed.
+template <bool INTERIOR>
+__device__ __forceinline__ void row_links(const float (&hC)[4], const float (&zC)[4],
+                                          const float (&nC)[4], const float (&hS)[4],
+                                          const float (&zS)[4], const float (&nS)[4],
+                                          const float (&qxo)[4], const float (&qyo)[4], float hE,
+                                          float zE, float nE, bool has_s, int c, int nx, float s,
+                                          float s_half, const FaceK& k, int east_out,
+                                          int south_out, float (&qxE)[4], float (&qyS)[4])
+{
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int cj = c + j;
+        const float h2 = (j < 3) ? hC[j + 1] : hE;
+        const float z2 = (j < 3) ? zC[j + 1] : zE;
+        const float n2 = (j < 3) ? nC[j + 1] : nE;
+        float q;
+        if (INTERIOR || cj < nx - 1)
+            q = link_q(hC[j], zC[j], h2, z2, qxo[j], __fmul_rn(s_half, __fadd_rn(nC[j], n2)), k);
+        else if (cj == nx - 1)
+            q = east_out ? outflow_q(hC[j], qxo[j], __fmul_rn(s, nC[j]), k) : 0.0f;
+        else
+            q = 0.0f;
+        qxE[j] = q;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float q = 0.0f;
+        if (INTERIOR || c + j < nx) {
+            if (has_s)
+                q = link_q(hC[j], zC[j], hS[j], zS[j], qyo[j],
+                           __fmul_rn(s_half, __fadd_rn(nC[j], nS[j])), k);
+            else if (south_out)
+                q = outflow_q(hC[j], qyo[j], __fmul_rn(s, nC[j]), k);
+        }
+        qyS[j] = q;
+    }
+}
+
+// Continuity (Eq. 5 -> Eq. 1) with rain and the wet/dry clamp for a lane's
+// four cells.  Clamped cells keep a negative zero: the adjoint reads the sign
+// bit to know that branch was taken.
+template <bool INTERIOR>
+__device__ __forceinline__ void row_depths(const float (&hC)[4], const float (&qxE)[4],
+                                           const float (&qyN)[4], const float (&qyS)[4], float qW0,
+                                           int c, int nx, float dt_dx, float dr, float& clamp,
+                                           float& hmax, float& hsum, float (&hN)[4])
+{
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float hn = 0.0f;
+        if (INTERIOR || c + j < nx) {
+            const float qW = (j == 0) ? qW0 : qxE[j - 1];
+            const float net = __fadd_rn(__fsub_rn(qW, qxE[j]), __fsub_rn(qyN[j], qyS[j]));
+            hn = __fadd_rn(__fmaf_rn(dt_dx, net, hC[j]), dr);
+            if (hn < 0.0f) {
+                clamp = __fsub_rn(clamp, hn);
+                hn = -0.0f;
+            }
+            hmax = fmaxf(hmax, hn);
+        }
+        hsum += hn;
+        hN[j] = hn;
+    }
+}
+
 __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, float* __restrict__ dst,
                                                float* ck, const float* __restrict__ z,
                                                const float* __restrict__ n, size_t plane, int ny,
@@ -45,6 +113,7 @@ __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, fl
     const int c = c0 + 4 * lane;
     const bool act = c < nx;           // lane owns at least one real cell
     const bool east_halo = (lane == 31) && (c + 4 < nx);
+    const bool interior = (c + 4 < nx);  // all four cells and their east neighbours inside
 
     float hC[4] = {0, 0, 0, 0}, zC[4] = {0, 0, 0, 0}, nC[4] = {0, 0, 0, 0};
     float qyN[4] = {0, 0, 0, 0};
@@ -73,6 +142,7 @@ __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, fl
     bool bad = false;
     float out_s = 0.0f, out_c = 0.0f, clamp = 0.0f;
 
+#pragma unroll 2
     for (int r = r0; r < r1; ++r) {
         const size_t o = (size_t)r * ld + c;
         const bool has_s = (r + 1 < ny);
@@ -97,23 +167,13 @@ __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, fl
             zE = __ldg(z + oe);
             nE = __ldg(n + oe);
         }
-        // east links (Eq. 2-3)
-        float qxE[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int cj = c + j;
-            const float h2 = (j < 3) ? hC[j + 1] : hE;
-            const float z2 = (j < 3) ? zC[j + 1] : zE;
-            const float n2 = (j < 3) ? nC[j + 1] : nE;
-            float q;
-            if (cj < nx - 1)
-                q = link_q(hC[j], zC[j], h2, z2, qxo[j], __fmul_rn(s_half, __fadd_rn(nC[j], n2)), k);
-            else if (cj == nx - 1)
-                q = east_out ? outflow_q(hC[j], qxo[j], __fmul_rn(s, nC[j]), k) : 0.0f;
-            else
-                q = 0.0f;
-            qxE[j] = q;
-        }
+        float qxE[4], qyS[4];
+        if (interior)
+            row_links<true>(hC, zC, nC, hS, zS, nS, qxo, qyo, hE, zE, nE, has_s, c, nx, s, s_half, k,
+                            east_out, south_out, qxE, qyS);
+        else
+            row_links<false>(hC, zC, nC, hS, zS, nS, qxo, qyo, hE, zE, nE, has_s, c, nx, s, s_half, k,
+                             east_out, south_out, qxE, qyS);
         // west link of the lane's first cell: previous lane's last east link
         float qW0 = __shfl_up_sync(0xffffffffu, qxE[3], 1);
         if (lane == 0) {
@@ -124,42 +184,13 @@ __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, fl
                              __fmul_rn(s_half, __fadd_rn(__ldg(n + ow), nC[0])), k);
             }
         }
-        // south links (Eq. 2-3)
-        float qyS[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int cj = c + j;
-            float q = 0.0f;
-            if (cj < nx) {
-                if (has_s)
-                    q = link_q(hC[j], zC[j], hS[j], zS[j], qyo[j],
-                               __fmul_rn(s_half, __fadd_rn(nC[j], nS[j])), k);
-                else if (south_out)
-                    q = outflow_q(hC[j], qyo[j], __fmul_rn(s, nC[j]), k);
-            }
-            qyS[j] = q;
-        }
-        // continuity (Eq. 5 -> Eq. 1) with rain and the wet/dry clamp
         float hN[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int cj = c + j;
-            float hn = 0.0f;
-            if (cj < nx) {
-                const float qW = (j == 0) ? qW0 : qxE[j - 1];
-                const float net = __fadd_rn(__fsub_rn(qW, qxE[j]), __fsub_rn(qyN[j], qyS[j]));
-                hn = __fadd_rn(__fmaf_rn(dt_dx, net, hC[j]), dr);
-                if (hn < 0.0f) {
-                    // clamped cells keep a negative zero: the adjoint reads
-                    // the sign bit to know this branch was taken
-                    clamp = __fsub_rn(clamp, hn);
-                    hn = -0.0f;
-                }
-                bad |= !(hn <= 3.0e38f);  // NaN or overflow
-                hmax = fmaxf(hmax, hn);
-            }
-            hN[j] = hn;
-        }
+        float hsum = 0.0f;
+        if (interior)
+            row_depths<true>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN);
+        else
+            row_depths<false>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN);
+        bad |= !(hsum <= 3.0e38f);  // a NaN or overflow anywhere in the row
         // links leaving the domain this row: the east edge link (one lane)
         // and, on the last row, the south edge links
         float ev = 0.0f;

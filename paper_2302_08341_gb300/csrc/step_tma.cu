@@ -14,7 +14,7 @@
 // flight, and returns.
 #include <cudaTypedefs.h>
 
-#include "flood_internal.cuh"
+#include "march.cuh"
 #include "tma.cuh"
 
 namespace flood {
@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(32 * WM, 20 / WM) step_tma_kernel(const __grid
 
     const int c = c0 + 4 * lane;
     const bool act = c < nx;
+    const bool interior = (c + 4 < nx);
     const int r0 = blockIdx.z * a.rows_per_strip;
     const int r1 = min(r0 + a.rows_per_strip, ny);
     const int ra = r0 > 0 ? r0 - 1 : r0;   // first row loaded
@@ -196,22 +197,13 @@ __global__ void __launch_bounds__(32 * WM, 20 / WM) step_tma_kernel(const __grid
         }
         // east neighbour of the lane's last cell, straight from the tile
         const float hE = P[x0 + 4], zE = P[kZ + x0 + 4], nE = P[kN + x0 + 4];
-        float qxE[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int cj = c + j;
-            const float h2 = (j < 3) ? hC[j + 1] : hE;
-            const float z2 = (j < 3) ? zC[j + 1] : zE;
-            const float n2 = (j < 3) ? nC[j + 1] : nE;
-            float q;
-            if (cj < nx - 1)
-                q = link_q(hC[j], zC[j], h2, z2, qxo[j], __fmul_rn(s_half, __fadd_rn(nC[j], n2)), k);
-            else if (cj == nx - 1)
-                q = a.east_out ? outflow_q(hC[j], qxo[j], __fmul_rn(s, nC[j]), k) : 0.0f;
-            else
-                q = 0.0f;
-            qxE[j] = q;
-        }
+        float qxE[4], qyS[4];
+        if (interior)
+            row_links<true>(hC, zC, nC, hS, zS, nS, qxo, qyo, hE, zE, nE, has_s, c, nx, s, s_half, k,
+                            a.east_out, a.south_out, qxE, qyS);
+        else
+            row_links<false>(hC, zC, nC, hS, zS, nS, qxo, qyo, hE, zE, nE, has_s, c, nx, s, s_half, k,
+                             a.east_out, a.south_out, qxE, qyS);
         float qW0 = __shfl_up_sync(0xffffffffu, qxE[3], 1);
         if (lane == 0) {
             qW0 = 0.0f;
@@ -219,38 +211,13 @@ __global__ void __launch_bounds__(32 * WM, 20 / WM) step_tma_kernel(const __grid
                 qW0 = link_q(P[3], P[kZ + 3], hC[0], zC[0], P[kBox + 3],
                              __fmul_rn(s_half, __fadd_rn(P[kN + 3], nC[0])), k);
         }
-        float qyS[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int cj = c + j;
-            float q = 0.0f;
-            if (cj < nx) {
-                if (has_s)
-                    q = link_q(hC[j], zC[j], hS[j], zS[j], qyo[j],
-                               __fmul_rn(s_half, __fadd_rn(nC[j], nS[j])), k);
-                else if (a.south_out)
-                    q = outflow_q(hC[j], qyo[j], __fmul_rn(s, nC[j]), k);
-            }
-            qyS[j] = q;
-        }
         float hN[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int cj = c + j;
-            float hn = 0.0f;
-            if (cj < nx) {
-                const float qW = (j == 0) ? qW0 : qxE[j - 1];
-                const float net = __fadd_rn(__fsub_rn(qW, qxE[j]), __fsub_rn(qyN[j], qyS[j]));
-                hn = __fadd_rn(__fmaf_rn(dt_dx, net, hC[j]), dr);
-                if (hn < 0.0f) {
-                    clamp = __fsub_rn(clamp, hn);
-                    hn = -0.0f;
-                }
-                bad |= !(hn <= 3.0e38f);
-                hmax = fmaxf(hmax, hn);
-            }
-            hN[j] = hn;
-        }
+        float hsum = 0.0f;
+        if (interior)
+            row_depths<true>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN);
+        else
+            row_depths<false>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN);
+        bad |= !(hsum <= 3.0e38f);
         float ev = 0.0f;
 #pragma unroll
         for (int j = 0; j < 4; ++j)
