@@ -322,6 +322,37 @@ int flood_batch_members(flood_batch* b, double* t, int64_t* steps, double* stora
 /* Step kernels launched so far (graph replays count every launch). */
 int64_t flood_batch_launch_count(const flood_batch* b);
 
+/* ==== Allocation-free volume reduction ======================================
+ * The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory -- code running inside a stream capture, under a
+ * device-memory budget owned by an embedding application, or in a real-time
+ * loop that must never wait on the allocator. */
+
+/* Largest number of rows flood_storage_static accepts (its block partials
+ * live in a fixed device array of FLOOD_STATIC_MAX_ROWS / 16 doubles, 32 KB,
+ * held by every device that loads the library until the process exits). */
+#define FLOOD_STATIC_MAX_ROWS 65536
+
+/*
+ * flood_storage_static -- *out = dx^2 * sum of h over a depth field, in FP64,
+ * without allocating anything.
+ *   h    device pointer to ny rows of ld floats (only the first nx of each row
+ *        are summed); the caller owns it
+ *   out  device pointer to one double; the caller owns it
+ * Same arithmetic and order as the storage reported by flood_volume_report,
+ * so the two agree bit for bit on the same field.  Asynchronous on `stream`.
+ * The first call on a device (with that device current) looks up the device
+ * address of the library's partials array; make that first call before any
+ * stream capture.  Every call on a device shares that array and overwrites
+ * the part it uses: calls that can overlap on the GPU (unordered streams)
+ * race and must be serialised by the caller.
+ * Errors: FLOOD_ERR_ARG (NULL pointer, ny > FLOOD_STATIC_MAX_ROWS, ld < nx,
+ * dx <= 0), FLOOD_ERR_CUDA; message from flood_storage_static_error().
+ */
+int flood_storage_static(const float* h, int ny, int nx, int ld, double dx, double* out,
+                         void* stream);
+const char* flood_storage_static_error(void);
+
 #ifdef __cplusplus
 }
 #endif

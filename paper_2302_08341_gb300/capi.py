@@ -28,7 +28,8 @@ EXPORTED = ["flood_default_params", "flood_last_error", "flood_create_grid", "fl
             "flood_adjoint", "flood_adjoint_timing", "flood_batch_create", "flood_batch_destroy",
             "flood_batch_last_error", "flood_batch_init", "flood_batch_step",
             "flood_batch_set_launch", "flood_batch_get_state", "flood_batch_members",
-            "flood_batch_launch_count", "flood_autotune"]
+            "flood_batch_launch_count", "flood_autotune", "flood_storage_static",
+            "flood_storage_static_error"]
 
 
 class FloodError(RuntimeError):
@@ -103,6 +104,9 @@ def lib(path: str = LIB_PATH):
     L.flood_adjoint.argtypes = [_VP, C.POINTER(LossSpec), C.c_int, _VP, _VP, _VP, _VP, _VP, _VP]
     L.flood_adjoint_timing.argtypes = [_VP, _VP, _VP]
     L.flood_autotune.argtypes = [_VP, C.c_int, _VP, _VP, _VP, _VP, _VP]
+    L.flood_storage_static.argtypes = [_VP, C.c_int, C.c_int, C.c_int, C.c_double, _VP, _VP]
+    L.flood_storage_static_error.argtypes = []
+    L.flood_storage_static_error.restype = C.c_char_p
     L.flood_batch_create.argtypes = [C.POINTER(_VP), C.c_int, _VP, _VP, _VP, _VP,
                                      C.POINTER(Params)]
     L.flood_batch_destroy.argtypes = [_VP]
@@ -117,7 +121,8 @@ def lib(path: str = LIB_PATH):
     L.flood_batch_launch_count.restype = C.c_int64
     for name in EXPORTED:
         if name not in ("flood_default_params", "flood_last_error", "flood_launch_count",
-                        "flood_batch_last_error", "flood_batch_launch_count"):
+                        "flood_batch_last_error", "flood_batch_launch_count",
+                        "flood_storage_static_error"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
