@@ -42,7 +42,11 @@ BYTES_STATIC = 8.0          # z, n (FP32) per cell per tile pass
 MEMBERS_PER_TILE = 4        # members sharing one static-field tile pass
 ALGO_BYTES = BYTES_STATE + BYTES_STATIC / MEMBERS_PER_TILE
 KERNEL_SOURCES = ["paper_2302_08341_gb300/csrc/step_kernel.cu",
+                  "paper_2302_08341_gb300/csrc/step_tma.cu",
+                  "paper_2302_08341_gb300/csrc/tma.cuh",
+                  "paper_2302_08341_gb300/csrc/march.cuh",
                   "paper_2302_08341_gb300/csrc/flood_internal.cuh"]
+BYTES_SINGLE = BYTES_STATE + BYTES_STATIC  # one member per static-field pass
 
 
 def parse():
@@ -76,16 +80,22 @@ def kernel_hash():
 
 def traffic_per_unit():
     """DRAM bytes per member-cell-step of the step kernel from the committed
-    ncu summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "step_kernel_2000x2000x96.json")
+    ncu summary, if it was taken on the current kernel source (the summary
+    carries `kernel_sha:` and `dram_bytes_per_member_cell_step:` lines)."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.md")
     try:
         with open(path) as f:
-            d = json.load(f)
+            kv = dict(l.strip().strip("`").split(":", 1) for l in f
+                      if l.strip().strip("`").split(":", 1)[0] in
+                      ("kernel_sha", "dram_bytes_per_member_cell_step"))
     except (OSError, ValueError):
         return None
-    if d.get("kernel_sha") != kernel_hash():
+    if kv.get("kernel_sha", "").strip() != kernel_hash():
         return None
-    return d.get("dram_bytes_per_member_cell_step")
+    try:
+        return float(kv["dram_bytes_per_member_cell_step"])
+    except (KeyError, ValueError):
+        return None
 
 
 def peaks():
@@ -293,6 +303,56 @@ def batch_measure(capi):
             "all_finished": bool(np.all(mem["t"] == dur)), "gpu_launches": launches}
 
 
+def plain_vs_fused(g, tuned, stream, device, ncell, hbm_peak):
+    """The same ensemble advanced one 300 s window by the fused ensemble step
+    (one launch per step for all members) and the next window by the plain
+    form (one launch per member per step, bed and roughness read per member,
+    with the strip height that suits a single member picked by a short
+    sweep); member-cell-steps/s of each on this GPU."""
+    import torch
+    fused_engine = tuned["engine"] if tuned else 1
+    fused_shape = (tuned["rows_per_strip"], tuned["members_per_cta"]) if tuned else (0, 0)
+    t = float(g.members()["t"].max())
+
+    def timed(span):
+        nonlocal t
+        s0 = g.members()["steps"].sum()
+        l0 = g.launch_count
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(device)
+        e0.record(stream)
+        t += span
+        g.advance_to(t, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        ms = e0.elapsed_time(e1)
+        units = float(g.members()["steps"].sum() - s0) * ncell
+        return units / (ms * 1e-3), ms, g.launch_count - l0
+
+    out = {}
+    g.set_engine(2)
+    sweep = {}
+    for rows in (4, 8, 16, 32):
+        g.set_launch(rows, 1)
+        sweep[rows] = timed(10.0)[0]
+    plain_rows = max(sweep, key=sweep.get)
+    for name, eng, shape, nbytes in (("fused", fused_engine, fused_shape, ALGO_BYTES),
+                                     ("plain_per_member", 2, (plain_rows, 1), BYTES_SINGLE)):
+        g.set_engine(eng)
+        g.set_launch(*shape)
+        v, ms, launches = timed(WINDOW)
+        out[name] = {"value": v, "unit": "member-cell-steps/s", "ms_per_window": ms,
+                     "gpu_launches": launches, "rows_per_strip": shape[0],
+                     "algorithmic_bytes_per_member_cell_step": nbytes,
+                     "hbm_frac_whole_window": v * nbytes / 1e9 / hbm_peak}
+    out["plain_rows_sweep"] = {str(k): v for k, v in sweep.items()}
+    g.set_engine(fused_engine)
+    g.set_launch(*fused_shape)
+    out["fused_over_plain"] = out["fused"]["value"] / out["plain_per_member"]["value"]
+    out["config"] = "one 300 s window each, after the timed windows, no particle filter"
+    return out
+
+
 def run_reference(args):
     world, rank, local = dist_setup(args)
     if rank != 0:
@@ -445,12 +505,18 @@ def run_gb300(args):
         e2e = {"value": e_units / (e_ms * 1e-3), "unit": "member-cell-steps/s",
                "h2d_bytes_per_step": G * 8 + M * 4,
                "d2h_bytes_per_step": M * 8 + M * 4 + 8 + 4 + M * G * 4}
+    plain = None
+    if not args.no_extensions and world == 1:
+        plain = plain_vs_fused(g, tuned, stream, device, ncell, hbm_peak)
     g.close()
     extensions = {}
     if not args.no_extensions and world == 1:
         extensions["adjoint"] = adjoint_measure(capi)
         extensions["batched"] = batch_measure(capi)
+        extensions["batched"]["hbm_frac_whole_window"] = (
+            extensions["batched"]["value"] * BYTES_SINGLE / 1e9 / hbm_peak)
         extensions["autotune"] = tuned
+        extensions["plain_vs_fused"] = plain
 
     if rank != 0:
         if world > 1:

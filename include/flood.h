@@ -261,8 +261,11 @@ int flood_set_launch(flood_grid* g, int rows_per_strip, int members_per_cta);
 int flood_get_launch(const flood_grid* g, int* rows_per_strip, int* members_per_cta);
 
 /* Step-kernel engine: 0 = direct float4 loads, 1 = rows staged through shared
- * memory by the tensor memory accelerator (default where available).  Both
- * give identical results.  Errors: FLOOD_ERR_ARG. */
+ * memory by the tensor memory accelerator (default where available), 2 = the
+ * plain form kept for comparison: one launch per member per step with direct
+ * loads (the bed and roughness are then read once per member, not once per
+ * tile of several members).  All give identical results.  Errors:
+ * FLOOD_ERR_ARG. */
 int flood_set_engine(flood_grid* g, int engine);
 
 /* Autotuner: time every step-kernel configuration (engine x rows per strip

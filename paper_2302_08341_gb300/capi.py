@@ -328,7 +328,8 @@ class Grid:
         _check(lib().flood_set_launch(self.h, int(rows_per_strip), int(members_per_cta)), self.h)
 
     def set_engine(self, engine):
-        """0: direct loads, 1: TMA-staged tiles (identical results)."""
+        """0: direct loads, 1: TMA-staged tiles, 2: one launch per member per
+        step (the plain form, for comparison); identical results."""
         _check(lib().flood_set_engine(self.h, int(engine)), self.h)
 
     def get_launch(self):

@@ -167,6 +167,9 @@ int launch_steps(flood_grid* g, int64_t count, double t_end, cudaStream_t s)
             t.static_map = g->static_map;
             t.a = a;
             flood::launch_step_tma(t, g->members_per_cta, s);
+        } else if (g->engine == 2) {
+            flood::launch_step_per_member(a, s);
+            g->launches += g->M - 1;
         } else {
             flood::launch_step(a, g->members_per_cta, s);
         }
@@ -718,7 +721,7 @@ int flood_set_launch(flood_grid* g, int rows_per_strip, int members_per_cta)
 int flood_set_engine(flood_grid* g, int engine)
 {
     if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
-    if (engine != 0 && engine != 1) return fail(g, FLOOD_ERR_ARG, "engine must be 0 or 1");
+    if (engine < 0 || engine > 2) return fail(g, FLOOD_ERR_ARG, "engine must be 0, 1 or 2");
     g->engine = engine;
     return FLOOD_OK;
 }

@@ -46,6 +46,7 @@ struct StepArgs {
     const int* seg_end;         // [M]
     int seg_first, replay_i;
     int* err;                   // device error word (bit 0: non-finite depth)
+    int m_base;                 // first member of this launch (one-launch-per-member form)
     size_t plane;               // ny * ld
     int ny, nx, ld, M, nb;
     int rows_per_strip;
@@ -245,6 +246,7 @@ __device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpre
 // Host-side helpers (flood_capi.cu).
 void launch_plan(const StepArgs& a, cudaStream_t s);
 void launch_step(const StepArgs& a, int members_per_cta, cudaStream_t s);
+void launch_step_per_member(const StepArgs& a, cudaStream_t s);
 void launch_replay(const StepArgs& a, int members_per_cta, cudaStream_t s);
 int launch_step_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s);
 int tma_box_cols();

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(32 * WM * WC, FLOOD_STEP_MIN_BLOCKS * 4 / (WM 
     const int lane = threadIdx.x;
     const int wm = threadIdx.y % WM;
     const int wc = threadIdx.y / WM;
-    const int m = blockIdx.x * WM + wm;
+    const int m = a.m_base + blockIdx.x * WM + wm;
     const int span = blockIdx.y * WC + wc;
     const int c0 = span * kSpan;
     if (m >= a.M || c0 >= a.nx) return;  // whole warps only: no block barriers below
@@ -167,6 +167,21 @@ void launch_step(const StepArgs& a, int members_per_cta, cudaStream_t s)
         step_kernel<1, 4, false><<<grid, block, 0, s>>>(a);
         break;
     }
+    }
+}
+
+// The plain form, for comparison: one launch per member per step, each
+// covering one member's grid with 4 spans per CTA (as a single deterministic
+// model would be launched), so the bed and roughness are read once per member.
+void launch_step_per_member(const StepArgs& a, cudaStream_t s)
+{
+    const int spans = (a.nx + kSpan - 1) / kSpan;
+    const int strips = (a.ny + a.rows_per_strip - 1) / a.rows_per_strip;
+    dim3 grid(1, (spans + 3) / 4, strips), block(32, 4);
+    StepArgs b = a;
+    for (int m = 0; m < a.M; ++m) {
+        b.m_base = m;
+        step_kernel<1, 4, false><<<grid, block, 0, s>>>(b);
     }
 }
 

@@ -243,13 +243,15 @@ def test_launch_shapes_give_bitwise_identical_results(capi):
 
 
 def test_engines_give_bitwise_identical_results(capi):
-    """Direct-load and TMA-staged step kernels: same values, bit for bit, on a
-    ragged grid (spans, strips and both grid edges exercised)."""
+    """Direct-load, TMA-staged and one-launch-per-member step kernels: same
+    values, bit for bit, on a ragged grid (spans, strips and both grid edges
+    exercised)."""
     terr = synth.make_terrain(75, 261, seed=15)
     hy = synth.hyetograph_constant(150.0, 300.0)
     rm, sc = synth.ensemble_prior(15, 6)
     res = []
-    for engine, shape in [(0, (0, 0)), (1, (0, 0)), (1, (5, 1)), (1, (64, 4)), (0, (7, 4))]:
+    for engine, shape in [(0, (0, 0)), (1, (0, 0)), (1, (5, 1)), (1, (64, 4)), (0, (7, 4)),
+                          (2, (0, 0)), (2, (16, 1))]:
         with capi.Grid(terr.z, terr.n) as g:
             g.ensemble_init(6, rm, sc, hy)
             g.set_engine(engine)
