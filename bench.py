@@ -64,6 +64,9 @@ def parse():
                     help="skip the adjoint and uneven-batch measurements")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch configuration (profiling runs)")
+    ap.add_argument("--only", choices=["adjoint", "batch", "calibration"],
+                    help="run one extension measurement alone and print it (profiling runs)")
+    ap.add_argument("--calibration-windows", type=int, default=3)
     args = ap.parse_args()
     global NY, NX, M
     NY, NX, M = args.ny, args.nx, args.members
@@ -303,6 +306,69 @@ def batch_measure(capi):
             "all_finished": bool(np.all(mem["t"] == dur)), "gpu_launches": launches}
 
 
+def calibration_measure(capi, windows=3):
+    """Ensemble gradient calibration + particle filter: 2000 x 2000 cells, 96
+    members, a shared 64 x 64 roughness factor field over the base Manning
+    field.  Per 300 s window: the adjoint of the window (loss: squared misfit
+    of the 6 gauges at its end, summed over members), one calibration step
+    on the rain multipliers and the field, then the gauge sample and the
+    particle filter.  The first window sizes the adjoint's buffers (about
+    190 GB of checkpoints and replay states) and is not counted."""
+    import torch
+    from paper_2302_08341_gb300 import synth
+    terr = synth.make_terrain(NY, NX, seed=4)
+    hy = synth.hyetograph_triangular(60.0, 1200.0, 3600.0)
+    rm, sc = synth.ensemble_prior(4, M)
+    cells = synth.gauge_cells(terr, G, seed=4)
+    trm, tsc = synth.ensemble_prior(1004, 1)
+    obs = []
+    with capi.Grid(terr.z, terr.n) as t:
+        t.ensemble_init(1, trm, tsc, hy)
+        for w in range(1, windows + 1):
+            t.advance_to(WINDOW * w)
+            obs.append(synth.observe(t.gauge_sample(cells)[0], seed=4, window=w))
+    stream = torch.cuda.current_stream()
+    rows = []
+    with capi.Grid(terr.z, terr.n) as g:
+        g.ensemble_init(M, rm, sc, hy, stream=stream)
+        g.set_roughness_factor(np.ones((64, 64), np.float32), stream=stream)
+        for w in range(1, windows + 1):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            s0 = g.members()["steps"].sum()
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            out = g.adjoint(cells, obs[w - 1][None, :], WINDOW, grad_h0=False, stream=stream)
+            ev[1].record(stream)
+            loss = g.calibration_step(stream=stream)
+            ev[2].record(stream)
+            u, beta = synth.pf_draws(4, w, M)
+            g.gauge_sample(cells, stream=stream)
+            pf = g.pf_assimilate(obs[w - 1], 0.05, u, beta, stream=stream)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            member_steps = float(g.members()["steps"].sum() - s0)
+            rows.append({"window_ms": ev[0].elapsed_time(ev[3]),
+                         "adjoint_ms": ev[0].elapsed_time(ev[1]),
+                         "adjoint_forward_ms": out["forward_ms"],
+                         "adjoint_reverse_ms": out["reverse_ms"],
+                         "calibration_step_ms": ev[1].elapsed_time(ev[2]),
+                         "pf_ms": ev[2].elapsed_time(ev[3]),
+                         "loss": float(np.sum(loss)), "neff": float(pf["neff"]),
+                         "member_cell_steps": member_steps * NY * NX})
+    timed = rows[1:] if len(rows) > 1 else rows
+    avg = {k: float(np.mean([r[k] for r in timed])) for k in timed[0]}
+    return {"config": f"{NY}x{NX} cells, {M} members, 64x64 roughness factor field, 6 gauges, "
+                      f"{len(timed)} timed 300 s windows after one that sizes the buffers",
+            "ms_per_window": avg["window_ms"], "adjoint_ms": avg["adjoint_ms"],
+            "adjoint_forward_ms": avg["adjoint_forward_ms"],
+            "adjoint_reverse_ms": avg["adjoint_reverse_ms"],
+            "adj_over_fwd": avg["adjoint_reverse_ms"] / avg["adjoint_forward_ms"],
+            "calibration_step_ms": avg["calibration_step_ms"], "pf_ms": avg["pf_ms"],
+            "forward_member_cell_steps_per_s": avg["member_cell_steps"] /
+            (avg["adjoint_forward_ms"] * 1e-3),
+            "loss_by_window": [r["loss"] for r in rows], "neff_by_window": [r["neff"] for r in rows]}
+
+
 def plain_vs_fused(g, tuned, stream, device, ncell, hbm_peak):
     """The same ensemble advanced one 300 s window by the fused ensemble step
     (one launch per step for all members) and the next window by the plain
@@ -513,6 +579,7 @@ def run_gb300(args):
     if not args.no_extensions and world == 1:
         extensions["adjoint"] = adjoint_measure(capi)
         extensions["batched"] = batch_measure(capi)
+        extensions["calibration"] = calibration_measure(capi, windows=args.calibration_windows)
         extensions["batched"]["hbm_frac_whole_window"] = (
             extensions["batched"]["value"] * BYTES_SINGLE / 1e9 / hbm_peak)
         extensions["autotune"] = tuned
@@ -546,8 +613,27 @@ def run_gb300(args):
         dist.destroy_process_group()
 
 
+def run_only(args):
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2302_08341_gb300 import capi
+    capi.lib()
+    if args.only == "adjoint":
+        res = adjoint_measure(capi)
+    elif args.only == "batch":
+        res = batch_measure(capi)
+    else:
+        res = calibration_measure(capi, windows=args.calibration_windows)
+    print(json.dumps({"only": args.only, "members": M, "cells": NY * NX, **res}))
+
+
 def main():
     args = parse()
+    if args.only:
+        run_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -215,6 +215,52 @@ int flood_adjoint(flood_grid* g, const flood_loss_spec* loss, int ckpt_every, fl
  * (with checkpointing) and of its reverse pass (replay included). */
 int flood_adjoint_timing(const flood_grid* g, double* forward_ms, double* reverse_ms);
 
+/* ==== Gradient calibration (extension: the paper estimates its uncertain
+ * inputs with the particle filter alone, Section 2.2 / 4.4) ================
+ * Roughness as the base field times a coarse factor field: fine cell (r, c)
+ * lies in block (floor(r cy / ny), floor(c cx / nx)) and uses
+ *     n(r, c) = n0(r, c) * f[block],
+ * n0 the base field given to flood_create_grid.  The calibration step moves
+ * the per-member rain multipliers and f along the gradients of the last
+ * flood_adjoint. */
+
+/* Set the factor field: f [cy][cx] FP32, host or device, every value > 0;
+ * 1 <= cy <= ny, 1 <= cx <= nx.  Rewrites the roughness field on the device
+ * (n0 is kept from the first call).  Synchronous.
+ * Errors: FLOOD_ERR_ARG, FLOOD_ERR_OOM, FLOOD_ERR_CUDA. */
+int flood_set_roughness_factor(flood_grid* g, int cy, int cx, const float* f, void* stream);
+
+/* The factor field in use: writes its shape and, if f is not NULL, its
+ * values ([cy][cx] FP32, host or device).  Synchronous.
+ * Errors: FLOOD_ERR_STATE if no factor field was set. */
+int flood_get_roughness_factor(flood_grid* g, int* cy, int* cx, float* f);
+
+/* Gradient of the last flood_adjoint's total loss L = sum_i L_i with respect
+ * to the factor field: grad[b] = sum over the cells of block b of
+ * n0 * dL/dn, in FP64 (a fixed-order reduction per block).  grad: [cy][cx]
+ * FP64, host or device.  The adjoint must have been given grad_n and nothing
+ * may have changed the ensemble since (a step, the particle filter, set
+ * state / members / factor).  Synchronous.
+ * Errors: FLOOD_ERR_STATE (no factor field, or no such adjoint). */
+int flood_roughness_factor_grad(flood_grid* g, double* grad, void* stream);
+
+/*
+ * flood_calibration_step -- one descent step from the last flood_adjoint
+ * (same precondition as flood_roughness_factor_grad; grad_n is only needed
+ * when a factor field is set).  In log-parameter space with the Polyak step
+ * of a loss whose minimum is zero, each component clipped to [-delta, delta]:
+ *   member i:  m_i <- m_i exp(clip(-eta L_i / g_i)),  g_i = m_i dL_i/dm_i
+ *   field:     f_b <- f_b exp(clip(-eta L G_b / |G|^2)),  G_b = f_b dL/df_b,
+ *              L = sum_i L_i, then n = n0 * f
+ * (g_i = 0 or |G| = 0 leaves the parameter unchanged).  L_i is recomputed on
+ * the device from the adjoint's recorded gauge outputs.  loss_out [N] FP64
+ * (host or device, or NULL) receives L_i.  After the step the adjoint is
+ * spent: another step needs another flood_adjoint.  Synchronous.
+ * Errors: FLOOD_ERR_ARG (eta <= 0, delta <= 0), FLOOD_ERR_STATE.
+ */
+int flood_calibration_step(flood_grid* g, double eta, double delta, double* loss_out,
+                           void* stream);
+
 /* Copy member m's state out / in: h, qx, qy as [ny][nx] FP32 in the link
  * convention above (any may be NULL).  Asynchronous. */
 int flood_get_state(flood_grid* g, int member, float* h, float* qx, float* qy, void* stream);

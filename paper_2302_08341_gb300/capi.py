@@ -29,7 +29,8 @@ EXPORTED = ["flood_default_params", "flood_last_error", "flood_create_grid", "fl
             "flood_batch_last_error", "flood_batch_init", "flood_batch_step",
             "flood_batch_set_launch", "flood_batch_get_state", "flood_batch_members",
             "flood_batch_launch_count", "flood_autotune", "flood_storage_static",
-            "flood_storage_static_error"]
+            "flood_storage_static_error", "flood_set_roughness_factor",
+            "flood_get_roughness_factor", "flood_roughness_factor_grad", "flood_calibration_step"]
 
 
 class FloodError(RuntimeError):
@@ -105,6 +106,10 @@ def lib(path: str = LIB_PATH):
     L.flood_adjoint_timing.argtypes = [_VP, _VP, _VP]
     L.flood_autotune.argtypes = [_VP, C.c_int, _VP, _VP, _VP, _VP, _VP]
     L.flood_storage_static.argtypes = [_VP, C.c_int, C.c_int, C.c_int, C.c_double, _VP, _VP]
+    L.flood_set_roughness_factor.argtypes = [_VP, C.c_int, C.c_int, _VP, _VP]
+    L.flood_get_roughness_factor.argtypes = [_VP, _VP, _VP, _VP]
+    L.flood_roughness_factor_grad.argtypes = [_VP, _VP, _VP]
+    L.flood_calibration_step.argtypes = [_VP, C.c_double, C.c_double, _VP, _VP]
     L.flood_storage_static_error.argtypes = []
     L.flood_storage_static_error.restype = C.c_char_p
     L.flood_batch_create.argtypes = [C.POINTER(_VP), C.c_int, _VP, _VP, _VP, _VP,
@@ -372,6 +377,43 @@ class Grid:
         _check(lib().flood_adjoint_timing(self.h, C.byref(f), C.byref(r)), self.h)
         out["forward_ms"], out["reverse_ms"] = f.value, r.value
         return out
+
+    def set_roughness_factor(self, f, stream=None):
+        """Roughness n = n0 * f[block] over a coarse [cy][cx] factor field
+        (flood_set_roughness_factor); f: numpy array or torch tensor."""
+        if hasattr(f, "data_ptr"):
+            cy, cx = f.shape
+            _check(lib().flood_set_roughness_factor(self.h, int(cy), int(cx), C.c_void_p(f.data_ptr()),
+                                                    stream_handle(stream)), self.h)
+            return
+        f = np.ascontiguousarray(f, dtype=np.float32)
+        cy, cx = f.shape
+        _check(lib().flood_set_roughness_factor(self.h, int(cy), int(cx), f.ctypes.data,
+                                                stream_handle(stream)), self.h)
+
+    def roughness_factor(self):
+        cy = C.c_int(); cx = C.c_int()
+        _check(lib().flood_get_roughness_factor(self.h, C.byref(cy), C.byref(cx), None), self.h)
+        f = np.zeros((cy.value, cx.value), np.float32)
+        _check(lib().flood_get_roughness_factor(self.h, None, None, f.ctypes.data), self.h)
+        return f
+
+    def roughness_factor_grad(self, stream=None):
+        """dL/df of the last adjoint (flood_roughness_factor_grad)."""
+        cy = C.c_int(); cx = C.c_int()
+        _check(lib().flood_get_roughness_factor(self.h, C.byref(cy), C.byref(cx), None), self.h)
+        out = np.zeros((cy.value, cx.value))
+        _check(lib().flood_roughness_factor_grad(self.h, out.ctypes.data, stream_handle(stream)),
+               self.h)
+        return out
+
+    def calibration_step(self, eta=1.0, delta=0.2, stream=None):
+        """One clipped Polyak step from the last adjoint (flood_calibration_step);
+        returns the per-member losses it used."""
+        loss = np.zeros(self.M)
+        _check(lib().flood_calibration_step(self.h, float(eta), float(delta), loss.ctypes.data,
+                                            stream_handle(stream)), self.h)
+        return loss
 
     @property
     def launch_count(self):

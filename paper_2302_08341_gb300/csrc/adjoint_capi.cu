@@ -311,6 +311,12 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
     CK(g, cudaMemcpyAsync(g->ms + (g->k % 3) * M, ce.data(), sizeof(MemberClock) * M,
                           cudaMemcpyHostToDevice, s));
     CK(g, cudaStreamSynchronize(s));
+    // what a calibration step may use: the gradients of this ensemble as it is now
+    g->adj_epoch = g->epoch;
+    g->adj_gn = grad_n != nullptr;
+    g->adj_ns = ns;
+    g->adj_G = G;
+    g->adj_nslot = g->nslot;
     return FLOOD_OK;
 }
 

@@ -66,7 +66,8 @@ void free_ensemble(flood_grid* g)
     dfree(g->part); dfree(g->storage); dfree(g->cells); dfree(g->d); dfree(g->sigma);
     dfree(g->plan); dfree(g->log); dfree(g->ckpt); dfree(g->seg); dfree(g->lam);
     dfree(g->gnm); dfree(g->gn_out); dfree(g->gpart); dfree(g->seg_end); dfree(g->samp_step);
-    dfree(g->samp_y); dfree(g->samp_d); dfree(g->samp_cells);
+    dfree(g->samp_y); dfree(g->samp_d); dfree(g->samp_cells); dfree(g->closs);
+    g->closs = nullptr; g->closs_cap = 0;
     g->plan = nullptr; g->log = nullptr; g->ckpt = nullptr; g->seg = nullptr;
     g->lam = nullptr; g->gnm = nullptr; g->gn_out = nullptr; g->gpart = nullptr;
     g->seg_end = nullptr; g->samp_step = nullptr; g->samp_y = nullptr; g->samp_d = nullptr;
@@ -146,6 +147,7 @@ void collect_profile(flood_grid* g)
 
 int launch_steps(flood_grid* g, int64_t count, double t_end, cudaStream_t s)
 {
+    g->epoch++;
     for (int64_t i = 0; i < count; ++i) {
         flood::StepArgs a = step_args(g, t_end);
         flood::launch_plan(a, s);
@@ -328,6 +330,7 @@ int flood_destroy(flood_grid* g)
     free_ensemble(g);
     dfree(g->zn);
     dfree(g->err);
+    dfree(g->n0); dfree(g->fac); dfree(g->fgrad);
     delete g;
     return FLOOD_OK;
 }
@@ -343,6 +346,7 @@ int flood_ensemble_init(flood_grid* g, int M, const float* h0, int h0_per_member
     if (!(t0 >= 0.0)) return fail(g, FLOOD_ERR_ARG, "t0 must be >= 0");
     cudaStream_t s = S(stream);
     CK(g, cudaStreamSynchronize(s));
+    g->epoch++;
     free_ensemble(g);
     g->M = M;
     g->nb = n_blocks;
@@ -485,6 +489,7 @@ int pf_assimilate(flood_grid* g, int G, const float* y, const double* d, const d
         return fail(g, FLOOD_ERR_ARG, "need n_gauges >= 1, d, sigma (or sigma_rel) and beta");
     if (!(u >= 0.0 && u < 1.0)) return fail(g, FLOOD_ERR_ARG, "u must lie in [0, 1)");
     cudaStream_t s = S(stream);
+    g->epoch++;
     if (!y && G != g->G)
         return fail(g, FLOOD_ERR_STATE, "y is NULL but no gauge sample of this size exists");
     if (G > g->G_cap) {
@@ -590,6 +595,7 @@ int flood_set_state(flood_grid* g, int member, const float* h, const float* qx, 
     if (g->M == 0) return fail(g, FLOOD_ERR_STATE, "flood_ensemble_init has not been called");
     if (member < 0 || member >= g->M) return fail(g, FLOOD_ERR_ARG, "member out of range");
     cudaStream_t s = S(stream);
+    g->epoch++;
     MemberClock* slot = g->ms + (g->k % 3) * g->M + member;
     MemberClock c;
     CK(g, cudaMemcpyAsync(&c, slot, sizeof(c), cudaMemcpyDeviceToHost, s));
@@ -638,6 +644,7 @@ int flood_set_members(flood_grid* g, const float* rain_mult, const float* mannin
     if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
     if (g->M == 0) return fail(g, FLOOD_ERR_STATE, "flood_ensemble_init has not been called");
     const int M = g->M;
+    g->epoch++;
     CK(g, cudaDeviceSynchronize());
     if (rain_mult) CK(g, cudaMemcpy(g->rain_mult, rain_mult, sizeof(float) * M, cudaMemcpyDefault));
     if (manning_scale) CK(g, cudaMemcpy(g->scale, manning_scale, sizeof(float) * M, cudaMemcpyDefault));

@@ -79,6 +79,17 @@ struct flood_grid {
     double* samp_d = nullptr;     // [ns][G]
     int32_t* samp_cells = nullptr;
     double adj_fwd_ms = 0.0, adj_rev_ms = 0.0;
+    // gradient calibration (calibrate.cu)
+    float* n0 = nullptr;          // [ny][ld] base roughness, kept once a factor field is set
+    float* fac = nullptr;         // [fcy][fcx] roughness factor field
+    double* fgrad = nullptr;      // [fcy][fcx] dL/df of the last adjoint
+    double* closs = nullptr;      // [closs_cap] per-member losses of the last adjoint
+    int fcy = 0, fcx = 0, closs_cap = 0;
+    uint64_t epoch = 0;           // bumped by every change of the ensemble or of its inputs
+    uint64_t adj_epoch = ~0ull;   // epoch right after the last flood_adjoint
+    bool adj_gn = false;          // that adjoint computed the Manning gradient
+    int adj_ns = 0, adj_G = 0;    // its samples and gauges (samp_y, samp_d)
+    int adj_nslot = 0;            // volume slots per member in its gpart
     std::string msg;
 };
 
