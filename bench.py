@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--only", choices=["adjoint", "batch", "calibration"],
                     help="run one extension measurement alone and print it (profiling runs)")
     ap.add_argument("--calibration-windows", type=int, default=3)
+    ap.add_argument("--engine", type=int, choices=[0, 1], default=None,
+                    help="step-kernel engine for --only batch (default: the library's)")
     args = ap.parse_args()
     global NY, NX, M
     NY, NX, M = args.ny, args.nx, args.members
@@ -270,7 +272,7 @@ def adjoint_measure(capi):
             "adj_over_fwd": res["reverse_ms"] / res["forward_ms"]}
 
 
-def batch_measure(capi):
+def batch_measure(capi, engine=None):
     """Uneven batch: 64 scenarios, square sides U{512..2048}, own DEM seeds,
     rain U[20, 100] mm/h, durations U[900, 3600] s, advanced in 300 s windows
     by graph-replayed batched launches; member-cell-steps/s over the batch."""
@@ -283,6 +285,10 @@ def batch_measure(capi):
     ones = np.ones(len(scen), np.float32)
     cells = np.array([s.ny * s.nx for s in scen], np.float64)
     with capi.Batch([t.z for t in terrs], [t.n for t in terrs]) as b:
+        if engine is not None:
+            b.set_engine(engine)
+        else:
+            engine = 1
         b.init(hys, ones, ones, dur)
         b.step(300.0)                      # warm-up window (graph capture)
         b.init(hys, ones, ones, dur)
@@ -303,7 +309,8 @@ def batch_measure(capi):
                       "U[900,3600] s, 300 s windows, CUDA-graph replayed batched step",
             "value": units / (ms * 1e-3), "unit": "member-cell-steps/s", "ms": ms,
             "total_cells": float(cells.sum()), "member_cell_steps": units,
-            "all_finished": bool(np.all(mem["t"] == dur)), "gpu_launches": launches}
+            "all_finished": bool(np.all(mem["t"] == dur)), "gpu_launches": launches,
+            "engine": "tma" if engine == 1 else "direct loads"}
 
 
 def calibration_measure(capi, windows=3):
@@ -623,7 +630,7 @@ def run_only(args):
     if args.only == "adjoint":
         res = adjoint_measure(capi)
     elif args.only == "batch":
-        res = batch_measure(capi)
+        res = batch_measure(capi, engine=args.engine)
     else:
         res = calibration_measure(capi, windows=args.calibration_windows)
     print(json.dumps({"only": args.only, "members": M, "cells": NY * NX, **res}))

@@ -360,6 +360,13 @@ int flood_batch_step(flood_batch* b, double t_stop, void* stream);
  * results do not depend on it.  Synchronous. */
 int flood_batch_set_launch(flood_batch* b, int rows_per_strip, int warps_per_cta);
 
+/* Step-kernel engine of the batch: 0 = direct float4 loads, 1 = rows staged
+ * through shared memory by the tensor memory accelerator, each scenario with
+ * its own tensor maps (the default where available).  Identical results.
+ * Synchronous.  Errors: FLOOD_ERR_ARG, FLOOD_ERR_STATE (engine 1 without
+ * tensor maps). */
+int flood_batch_set_engine(flood_batch* b, int engine);
+
 /* Scenario i's state as [ny[i]][nx[i]] FP32 arrays (any may be NULL). */
 int flood_batch_get_state(flood_batch* b, int i, float* h, float* qx, float* qy, void* stream);
 

@@ -30,7 +30,8 @@ EXPORTED = ["flood_default_params", "flood_last_error", "flood_create_grid", "fl
             "flood_batch_set_launch", "flood_batch_get_state", "flood_batch_members",
             "flood_batch_launch_count", "flood_autotune", "flood_storage_static",
             "flood_storage_static_error", "flood_set_roughness_factor",
-            "flood_get_roughness_factor", "flood_roughness_factor_grad", "flood_calibration_step"]
+            "flood_get_roughness_factor", "flood_roughness_factor_grad", "flood_calibration_step",
+            "flood_batch_set_engine"]
 
 
 class FloodError(RuntimeError):
@@ -120,6 +121,7 @@ def lib(path: str = LIB_PATH):
     L.flood_batch_init.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _VP]
     L.flood_batch_step.argtypes = [_VP, C.c_double, _VP]
     L.flood_batch_set_launch.argtypes = [_VP, C.c_int, C.c_int]
+    L.flood_batch_set_engine.argtypes = [_VP, C.c_int]
     L.flood_batch_get_state.argtypes = [_VP, C.c_int, _VP, _VP, _VP, _VP]
     L.flood_batch_members.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _VP]
     L.flood_batch_launch_count.argtypes = [_VP]
@@ -479,6 +481,10 @@ class Batch:
     def set_launch(self, rows_per_strip, warps_per_cta=4):
         _bcheck(lib().flood_batch_set_launch(self.h, int(rows_per_strip), int(warps_per_cta)),
                 self.h)
+
+    def set_engine(self, engine):
+        """0: direct loads, 1: TMA-staged rows (identical results)."""
+        _bcheck(lib().flood_batch_set_engine(self.h, int(engine)), self.h)
 
     def get_state(self, i, stream=None):
         ny, nx = self.shapes[i]

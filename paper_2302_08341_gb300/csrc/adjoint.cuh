@@ -24,9 +24,23 @@ struct AdjArgs {
     double g, dxd;
     float h_eps, edge_drop;
     int limiter, east_out, south_out;
+    int* err;                // device error word (bit 1: a bounded wait gave up)
+};
+
+// Tensor maps of the TMA-staged adjoint (adjoint_tma.cu): 136-column boxes of
+// one row.
+struct AdjTmaArgs {
+    CUtensorMap seg_map;     // seg as (ld, ny, slots * M * 3), box of 3 planes (h, qx, qy)
+    CUtensorMap seg1_map;    // the same memory, box of 1 plane (the depth after a step)
+    CUtensorMap lam_map;     // lam as (ld, ny, 2 * M * 3), box of 3 planes
+    CUtensorMap static_map;  // z, n as (ld, ny, 2), box of 2 planes
+    CUtensorMap gn_map;      // per-member Manning gradients as (ld, ny, M), box of 1 plane
+    AdjArgs a;
 };
 
 void launch_adjoint(const AdjArgs& a, int members_per_cta, cudaStream_t s);
+void launch_adjoint_tma(const AdjTmaArgs& t, int members_per_cta, cudaStream_t s);
+int adjoint_tma_box_cols();
 void launch_seed(const AdjArgs& a, const int32_t* sample_step, const float* y, const double* d,
                  const int32_t* cells, int ns, int G, cudaStream_t s);
 void launch_reduce_members(const float* gm, int M, int ny, int nx, int ld, size_t plane, float* out,

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "adjoint.cuh"
+#include "tma.cuh"
 #include "grid.cuh"
 #include "pf_kernels.cuh"
 
@@ -208,6 +209,25 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
                           cudaMemcpyHostToDevice, s));
     CK(g, cudaMemcpyAsync(g->samp_d, d.data(), sizeof(double) * ns * G, cudaMemcpyHostToDevice, s));
 
+    // tensor maps of the TMA-staged reverse stencil (direct loads otherwise)
+    flood::AdjTmaArgs tma{};
+    // (short strips never fill the copy pipeline: direct loads do better there)
+    bool use_tma = g->engine == 1 && g->maps_ok && g->rows_per_strip >= 16;
+    if (use_tma) {
+        const int bc = flood::adjoint_tma_box_cols();
+        const uint64_t s1 = sizeof(float) * g->ld, s2 = sizeof(float) * g->plane;
+        use_tma =
+            flood::encode_map_3d(&tma.seg_map, g->seg, g->ld, g->ny, (uint64_t)(K + 1) * M * 3, s1,
+                                 s2, bc, 1, 3) == 0 &&
+            flood::encode_map_3d(&tma.seg1_map, g->seg, g->ld, g->ny, (uint64_t)(K + 1) * M * 3, s1,
+                                 s2, bc, 1, 1) == 0 &&
+            flood::encode_map_3d(&tma.lam_map, g->lam, g->ld, g->ny, (uint64_t)2 * M * 3, s1, s2, bc,
+                                 1, 3) == 0 &&
+            (!grad_n || flood::encode_map_3d(&tma.gn_map, g->gnm, g->ld, g->ny, (uint64_t)M, s1, s2,
+                                             bc, 1, 1) == 0);
+        tma.static_map = g->static_map;
+    }
+
     const int kmax = *std::max_element(K_m.begin(), K_m.end());
     const int n_seg = (kmax + K - 1) / K;
     int lam_in = 0;
@@ -258,11 +278,17 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
         b.limiter = g->p.limiter;
         b.east_out = g->p.east_outflow;
         b.south_out = g->p.south_outflow;
+        b.err = g->err;
         for (int i = 0; i < len; ++i) {
             b.rev_i = i;
             b.lam_in = lam_in;
             flood::launch_seed(b, g->samp_step, g->samp_y, g->samp_d, g->samp_cells, ns, G, s);
-            flood::launch_adjoint(b, g->members_per_cta, s);
+            if (use_tma) {
+                tma.a = b;
+                flood::launch_adjoint_tma(tma, g->members_per_cta, s);
+            } else {
+                flood::launch_adjoint(b, g->members_per_cta, s);
+            }
             g->launches += 2;
             lam_in = 1 - lam_in;
         }

@@ -41,9 +41,12 @@ struct BatchArgs {
     double alpha_dx, g, dt_cap, dt_fixed, h_floor, rain_block, dxd, cell_area;
     float h_eps, edge_drop;
     int limiter, east_out, south_out;
+    const CUtensorMap* maps;   // [S][2] per scenario: state (ld, ny, 6 planes), z and n (ld, ny, 2)
 };
 
 void launch_batch_plan(const BatchArgs& a, int n_scen, cudaStream_t s);
 void launch_batch_step(const BatchArgs& a, int warps_per_cta, cudaStream_t s);
+void launch_batch_step_tma(const BatchArgs& a, int warps_per_cta, cudaStream_t s);
+int batch_tma_prepare();  // shared-memory attributes; call before any stream capture
 
 }  // namespace flood

@@ -10,6 +10,7 @@
 #include "../../include/flood.h"
 #include "batch.cuh"
 #include "pf_kernels.cuh"
+#include "tma.cuh"
 
 using flood::MemberClock;
 
@@ -43,6 +44,8 @@ struct flood_batch {
     double* t_stop = nullptr;         // device scalar
     flood::MemberPlan* plan = nullptr; // [S]
     int rows_per_strip = 64, warps_per_cta = 4;
+    int engine = 0;                   // 0: direct loads, 1: TMA-staged rows
+    CUtensorMap* d_maps = nullptr;    // [S][2] tensor maps of each scenario
     bool initialised = false;
     int64_t k = 0, launches = 0;
     cudaGraphExec_t graph = nullptr;
@@ -139,6 +142,7 @@ flood::BatchArgs batch_args(const flood_batch* b, int64_t k)
     a.limiter = b->p.limiter;
     a.east_out = b->p.east_outflow;
     a.south_out = b->p.south_outflow;
+    a.maps = b->d_maps;
     return a;
 }
 
@@ -151,7 +155,10 @@ int ensure_graph(flood_batch* b)
     for (int i = 0; i < kGraphSteps; ++i) {
         const flood::BatchArgs a = batch_args(b, i);
         flood::launch_batch_plan(a, b->S, b->cap_stream);
-        flood::launch_batch_step(a, b->warps_per_cta, b->cap_stream);
+        if (b->engine == 1)
+            flood::launch_batch_step_tma(a, b->warps_per_cta, b->cap_stream);
+        else
+            flood::launch_batch_step(a, b->warps_per_cta, b->cap_stream);
     }
     BCK(b, cudaStreamEndCapture(b->cap_stream, &gr));
     cudaError_t e = cudaGraphInstantiate(&b->graph, gr, 0);
@@ -255,6 +262,31 @@ int flood_batch_create(flood_batch** out, int n, const int32_t* ny, const int32_
         flood_batch_destroy(b);
         return rc;
     }
+    // tensor maps of every scenario for the TMA-staged step (direct loads if
+    // the encoder is unavailable)
+    {
+        std::vector<CUtensorMap> maps((size_t)2 * n);
+        bool ok = flood::batch_tma_prepare() == 0;
+        for (int i = 0; ok && i < n; ++i) {
+            const uint64_t s1 = sizeof(float) * b->ld[i], s2 = sizeof(float) * b->desc[i].plane;
+            ok = flood::encode_map_3d(&maps[2 * i], b->state[i], b->ld[i], b->ny[i], 6, s1, s2,
+                                      flood::tma_box_cols(), 1, 3) == 0 &&
+                 flood::encode_map_3d(&maps[2 * i + 1], b->zn[i], b->ld[i], b->ny[i], 2, s1, s2,
+                                      flood::tma_box_cols(), 1, 2) == 0;
+        }
+        if (ok) {
+            e = cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * maps.size());
+            if (e == cudaSuccess)
+                e = cudaMemcpy(b->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                               cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                int rc = bad(e);
+                flood_batch_destroy(b);
+                return rc;
+            }
+            b->engine = 1;
+        }
+    }
     int rc = build_tasks(b);
     if (rc) {
         g_batch_msg = b->msg;
@@ -275,7 +307,7 @@ int flood_batch_destroy(flood_batch* b)
     for (float* p : b->state) if (p) cudaFree(p);
     for (float* p : b->hyeto) if (p) cudaFree(p);
     void* bufs[] = {b->d_desc, b->d_tasks, b->ms, b->vacc, b->rain_acc, b->storage, b->part,
-                    b->err, b->t_stop, b->plan};
+                    b->err, b->t_stop, b->plan, b->d_maps};
     for (void* p : bufs) if (p) cudaFree(p);
     delete b;
     return FLOOD_OK;
@@ -317,6 +349,17 @@ int flood_batch_init(flood_batch* b, const float* const* hyetographs, const int3
     BCK(b, cudaStreamSynchronize(s));
     b->k = 0;
     b->initialised = true;
+    return FLOOD_OK;
+}
+
+int flood_batch_set_engine(flood_batch* b, int engine)
+{
+    if (!b) return bfail(nullptr, FLOOD_ERR_ARG, "batch is NULL");
+    if (engine != 0 && engine != 1) return bfail(b, FLOOD_ERR_ARG, "engine must be 0 or 1");
+    if (engine == 1 && !b->d_maps) return bfail(b, FLOOD_ERR_STATE, "no tensor maps: direct loads only");
+    BCK(b, cudaDeviceSynchronize());
+    b->engine = engine;
+    drop_graph(b);
     return FLOOD_OK;
 }
 

@@ -6,6 +6,7 @@
 // end time) are idle.
 #include "batch.cuh"
 #include "march.cuh"
+#include "tma_march.cuh"
 
 namespace flood {
 
@@ -82,7 +83,75 @@ __global__ void __launch_bounds__(32 * W) batch_step_kernel(const BatchArgs a)
     }
 }
 
+// TMA-staged form of batch_step_kernel (same results, bit for bit): the
+// task's rows stream through shared memory by the scenario's own tensor maps.
+template <int W>
+__global__ void __launch_bounds__(32 * W, 20 / W) batch_tma_kernel(const BatchArgs a)
+{
+    extern __shared__ unsigned char smem_raw[];
+    const int lane = threadIdx.x;
+    const int w = threadIdx.y;
+    const int tid = blockIdx.x * W + w;
+    if (tid >= a.ntasks) return;  // whole warps; no block-wide barriers below
+    const WarpTask tk = a.tasks[tid];
+    const int i = tk.scen;
+    const MemberPlan p = a.plan[i];
+    if (!p.active) return;
+    if (*reinterpret_cast<volatile const int*>(a.err) & 2) return;  // an earlier wait gave up
+    const ScenDesc sd = a.scen[i];
+    FaceK k;
+    k.gdt_dx = p.gdt_dx;
+    k.gdt = p.gdt;
+    k.dx_4dt = p.dx_4dt;
+    k.h_eps = a.h_eps;
+    k.edge_drop = a.edge_drop;
+    k.limiter = a.limiter;
+    uint32_t bar0;
+    unsigned char* my_stages;
+    tma_march_smem(smem_raw, W, w, bar0, my_stages);
+    float* dst = sd.state + (size_t)(1 - p.cur) * 3 * sd.plane;
+    MarchOut mo;
+    if (!tma_march(a.maps + 2 * i, a.maps + 2 * i + 1, p.cur * 3, bar0, my_stages, dst, nullptr,
+                   a.err, sd.plane, sd.ny, sd.nx, sd.ld, tk.c0, tk.r0, tk.r1, lane, k, p.dt_dx,
+                   sd.scale, p.dr, a.east_out, a.south_out, mo))
+        return;
+    if (mo.bad) atomicOr(a.err, 1);
+    const unsigned hb = __reduce_max_sync(0xffffffffu, __float_as_uint(mo.hmax) & 0x7fffffffu);
+    double out_acc = (double)mo.out_s - (double)mo.out_c, clamp_acc = (double)mo.clamp;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        out_acc += __shfl_xor_sync(0xffffffffu, out_acc, off);
+        clamp_acc += __shfl_xor_sync(0xffffffffu, clamp_acc, off);
+    }
+    if (lane == 0) {
+        atomicMax(&a.ms_out[i].hmax_bits, hb);
+        if (out_acc != 0.0 || clamp_acc != 0.0) {
+            double* v = a.vacc + (size_t)tk.slot * 2;
+            v[0] += out_acc * p.dt * a.dxd;
+            v[1] += clamp_acc * a.cell_area;
+        }
+    }
+}
+
 }  // namespace
+
+int batch_tma_prepare()
+{
+    cudaError_t e = cudaFuncSetAttribute(batch_tma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tma_march_smem_bytes(4));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_tma_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tma_march_smem_bytes(8));
+    return e == cudaSuccess ? 0 : -1;
+}
+
+void launch_batch_step_tma(const BatchArgs& a, int warps_per_cta, cudaStream_t s)
+{
+    if (warps_per_cta >= 8)
+        batch_tma_kernel<8><<<(a.ntasks + 7) / 8, dim3(32, 8), tma_march_smem_bytes(8), s>>>(a);
+    else
+        batch_tma_kernel<4><<<(a.ntasks + 3) / 4, dim3(32, 4), tma_march_smem_bytes(4), s>>>(a);
+}
 
 void launch_batch_plan(const BatchArgs& a, int n_scen, cudaStream_t s)
 {

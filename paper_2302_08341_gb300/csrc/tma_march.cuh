@@ -1,0 +1,246 @@
+// The TMA-staged march of one warp over a 128-column span of rows
+// [r0, r1) of one grid (an ensemble member or a batched scenario), shared by
+// the ensemble (step_tma.cu) and batched (batch_kernel.cu) step kernels.
+//
+// The warp's rows arrive through a ring of kTmaNS shared-memory stages filled
+// by the tensor memory accelerator: one 3-D tiled copy brings a row of h, qx
+// and qy (136 columns: the span plus 4 halo columns each side, zero-filled
+// past the grid's edges), another the same row of z and n.  Lane 0 keeps
+// kTmaNS - 1 rows in flight ahead of the row being computed, so the memory
+// latency is covered by the warp's own pipeline; the halo comes with the
+// tile, so no scalar edge loads remain.  Every mbarrier wait is bounded: on
+// timeout the march records FLOOD_ERR_TIMEOUT in the error word, waits
+// (bounded) for its own copies in flight, and returns false.
+#pragma once
+
+#include "march.cuh"
+#include "tma.cuh"
+
+namespace flood {
+
+constexpr int kTmaSpan = 128;
+constexpr int kTmaNS = 4;                          // stages per warp
+constexpr int kTmaBox = kTmaSpan + 8;              // columns per tile row
+constexpr int kTmaStaticOff = 1664;                // bytes: z, n after h, qx, qy (128-aligned)
+constexpr int kTmaStageBytes = 2816;               // 128-aligned stage size
+constexpr uint32_t kTmaTx = kTmaBox * 3 * 4 + kTmaBox * 2 * 4;  // bytes landing per stage
+constexpr long long kTmaWaitBudget = 200000000LL;  // clock cycles (~0.1 s) before giving up
+
+// Dynamic shared memory of a CTA of `warps` warps: barriers, then each warp's
+// stages.
+__host__ __device__ constexpr size_t tma_march_smem_bytes(int warps)
+{
+    return 128 + 128 * ((8 * kTmaNS * warps + 127) / 128) + (size_t)kTmaNS * kTmaStageBytes * warps;
+}
+
+// This warp's barriers and stages inside the CTA's dynamic shared memory.
+__device__ __forceinline__ void tma_march_smem(unsigned char* smem_raw, int warps, int w,
+                                               uint32_t& bar0, unsigned char*& my_stages)
+{
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+    bar0 = smem_u32(base) + 8u * kTmaNS * w;
+    my_stages = base + 128 * ((8 * kTmaNS * warps + 127) / 128) + kTmaNS * kTmaStageBytes * w;
+}
+
+__device__ __forceinline__ void tma_lds4(float (&v)[4], const float* p)
+{
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+
+__device__ __forceinline__ void tma_store4(float* p, const float (&v)[4])
+{
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// state_map: (ld, ny, planes) with the source h, qx, qy at planes
+// [plane0, plane0 + 3); static_map: (ld, ny, 2) with z then n.  Writes the
+// new state to dst (and ck when non-null).  Returns false if a wait gave up.
+__device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CUtensorMap* static_map,
+                                          int plane0, uint32_t bar0, unsigned char* my_stages,
+                                          float* __restrict__ dst, float* ck, int* err, size_t plane,
+                                          int ny, int nx, int ld, int c0, int r0, int r1, int lane,
+                                          const FaceK& k, float dt_dx, float s, float dr,
+                                          int east_out, int south_out, MarchOut& out)
+{
+    constexpr int kNS = kTmaNS;
+    constexpr int kBox = kTmaBox;
+    constexpr int kStaticOff = kTmaStaticOff;
+    constexpr int kStageBytes = kTmaStageBytes;
+    constexpr uint32_t kTx = kTmaTx;
+    constexpr int kZ = kStaticOff / 4;
+    constexpr int kN = kZ + kBox;
+    constexpr long long kWaitBudget = kTmaWaitBudget;
+    const uint32_t stage0 = smem_u32(my_stages);
+    const float s_half = 0.5f * s;
+
+    const int c = c0 + 4 * lane;
+    const bool act = c < nx;
+    const bool interior = (c + 4 < nx);
+    const int ra = r0 > 0 ? r0 - 1 : r0;   // first row loaded
+    const int rb = min(r1 + 1, ny);        // one past the last row loaded
+
+    if (lane == 0) {
+        for (int i = 0; i < kNS; ++i) mbar_init(bar0 + 8u * i, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    int issued = ra;  // rows [ra, issued) have been requested
+    auto issue = [&](int row) {
+        const int sidx = (row - ra) % kNS;
+        const uint32_t bar = bar0 + 8u * sidx;
+        const uint32_t dsts = stage0 + kStageBytes * sidx;
+        mbar_arrive_expect_tx(bar, kTx);
+        tma_load_3d(dsts, state_map, c0 - 4, row, plane0, bar);
+        tma_load_3d(dsts + kStaticOff, static_map, c0 - 4, row, 0, bar);
+    };
+    for (; issued < rb && issued < ra + kNS; ++issued)
+        if (lane == 0) issue(issued);
+    auto wait_row = [&](int row) -> bool {
+        const int kk = row - ra;
+        return mbar_wait_bounded(bar0 + 8u * (kk % kNS), (kk / kNS) & 1, kWaitBudget);
+    };
+    auto row_ptr = [&](int row) -> const float* {
+        return reinterpret_cast<const float*>(my_stages + kStageBytes * ((row - ra) % kNS));
+    };
+    // recycle the stage of `row` for the next row in line
+    auto release = [&](int row) {
+        __syncwarp();
+        if (issued < rb) {
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                issue(issued);
+            }
+            ++issued;
+        }
+        (void)row;
+    };
+    int waited = ra;  // rows [ra, waited) have landed
+    bool ok = true;
+    auto drain_and_fail = [&]() {
+        if (lane == 0) atomicOr(err, 2);
+        for (int row = waited; row < issued; ++row) wait_row(row);  // bounded each
+    };
+
+    const int x0 = 4 + 4 * lane;  // this lane's first cell in a tile row
+    float hC[4] = {0, 0, 0, 0}, zC[4] = {0, 0, 0, 0}, nC[4] = {0, 0, 0, 0};
+    float qyN[4] = {0, 0, 0, 0};
+    if (r0 > 0) {
+        ok = wait_row(r0 - 1);
+        if (ok) waited = r0;
+    }
+    if (ok) {
+        ok = wait_row(r0);
+        if (ok) waited = r0 + 1;
+    }
+    if (!ok) {
+        drain_and_fail();
+        return false;
+    }
+    {
+        const float* P = row_ptr(r0);
+        tma_lds4(hC, P + x0);
+        tma_lds4(zC, P + kZ + x0);
+        tma_lds4(nC, P + kN + x0);
+        if (r0 > 0) {
+            const float* U = row_ptr(r0 - 1);
+            float hU[4], zU[4], nU[4], qU[4];
+            tma_lds4(hU, U + x0);
+            tma_lds4(zU, U + kZ + x0);
+            tma_lds4(nU, U + kN + x0);
+            tma_lds4(qU, U + 2 * kBox + x0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                qyN[j] = (c + j < nx)
+                             ? link_q(hU[j], zU[j], hC[j], zC[j], qU[j],
+                                      __fmul_rn(s_half, __fadd_rn(nU[j], nC[j])), k)
+                             : 0.0f;
+            release(r0 - 1);
+        }
+    }
+
+    float hmax = 0.0f;
+    bool bad = false;
+    float out_s = 0.0f, out_c = 0.0f, clamp = 0.0f;
+
+    for (int r = r0; r < r1; ++r) {
+        const size_t o = (size_t)r * ld + c;
+        const bool has_s = (r + 1 < ny);
+        if (has_s) {
+            if (!wait_row(r + 1)) {
+                drain_and_fail();
+                return false;
+            }
+            waited = r + 2;
+        }
+        const float* P = row_ptr(r);
+        float hS[4] = {0, 0, 0, 0}, zS[4] = {0, 0, 0, 0}, nS[4] = {0, 0, 0, 0};
+        float qxo[4], qyo[4];
+        tma_lds4(qxo, P + kBox + x0);
+        tma_lds4(qyo, P + 2 * kBox + x0);
+        if (has_s) {
+            const float* Q = row_ptr(r + 1);
+            tma_lds4(hS, Q + x0);
+            tma_lds4(zS, Q + kZ + x0);
+            tma_lds4(nS, Q + kN + x0);
+        }
+        // east neighbour of the lane's last cell, straight from the tile
+        const float hE = P[x0 + 4], zE = P[kZ + x0 + 4], nE = P[kN + x0 + 4];
+        float qxE[4], qyS[4];
+        if (interior)
+            row_links<true>(hC, zC, nC, hS, zS, nS, qxo, qyo, hE, zE, nE, has_s, c, nx, s, s_half, k,
+                            east_out, south_out, qxE, qyS);
+        else
+            row_links<false>(hC, zC, nC, hS, zS, nS, qxo, qyo, hE, zE, nE, has_s, c, nx, s, s_half, k,
+                             east_out, south_out, qxE, qyS);
+        float qW0 = __shfl_up_sync(0xffffffffu, qxE[3], 1);
+        if (lane == 0) {
+            qW0 = 0.0f;
+            if (c0 > 0)  // the neighbouring span's last link, from the tile's halo
+                qW0 = link_q(P[3], P[kZ + 3], hC[0], zC[0], P[kBox + 3],
+                             __fmul_rn(s_half, __fadd_rn(P[kN + 3], nC[0])), k);
+        }
+        float hN[4];
+        float hsum = 0.0f;
+        if (interior)
+            row_depths<true>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN);
+        else
+            row_depths<false>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN);
+        bad |= !(hsum <= 3.0e38f);
+        float ev = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (c + j == nx - 1 && east_out) ev = qxE[j];
+        if (!has_s && south_out)
+            ev = __fadd_rn(ev, __fadd_rn(__fadd_rn(qyS[0], qyS[1]), __fadd_rn(qyS[2], qyS[3])));
+        kahan_add(out_s, out_c, ev);
+        if (act) {
+            tma_store4(dst + o, hN);
+            tma_store4(dst + plane + o, qxE);
+            tma_store4(dst + 2 * plane + o, qyS);
+            if (ck) {
+                tma_store4(ck + o, hN);
+                tma_store4(ck + plane + o, qxE);
+                tma_store4(ck + 2 * plane + o, qyS);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            qyN[j] = qyS[j];
+            hC[j] = hS[j];
+            zC[j] = zS[j];
+            nC[j] = nS[j];
+        }
+        release(r);
+    }
+
+    out.hmax = hmax;
+    out.bad = bad;
+    out.out_s = out_s;
+    out.out_c = out_c;
+    out.clamp = clamp;
+    return true;
+}
+
+}  // namespace flood

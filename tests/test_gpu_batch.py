@@ -29,12 +29,14 @@ def _scenarios():
     return terrs, hys, rm, sc, np.array(durations)
 
 
-def _run_batch(capi, shape=None):
+def _run_batch(capi, shape=None, engine=None):
     terrs, hys, rm, sc, dur = _scenarios()
     with capi.Batch([t.z for t in terrs], [t.n for t in terrs]) as b:
         b.init(hys, rm, sc, dur)
         if shape:
             b.set_launch(*shape)
+        if engine is not None:
+            b.set_engine(engine)
         for w in (300.0, 600.0):
             b.step(w)
         states = [b.get_state(i) for i in range(len(SHAPES))]
@@ -72,6 +74,17 @@ def test_batch_launch_shapes_bitwise(capi, shape):
     for a, b in zip(ref, got):
         for k in range(3):
             assert np.array_equal(a[k], b[k])
+
+
+@pytest.mark.parametrize("shape", [None, (7, 8)])
+def test_batch_engines_bitwise(capi, shape):
+    """Direct-load and TMA-staged batched kernels: the same states, bit for
+    bit, for every scenario."""
+    a = _run_batch(capi, shape, engine=0)[5]
+    b = _run_batch(capi, shape, engine=1)[5]
+    for x, y in zip(a, b):
+        for k in range(3):
+            assert np.array_equal(x[k], y[k])
 
 
 def test_batch_rejects_bad_arguments(capi):
