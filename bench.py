@@ -194,6 +194,14 @@ def sum_over_ranks(x, world, device):
     return float(t.item())
 
 
+def job_value(units, ms, world, device):
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (weak scaling: each rank runs its own replica)."""
+    ms_max = max_over_ranks(ms, world, device)
+    units_all = sum_over_ranks(units, world, device)
+    return units_all / (ms_max * 1e-3), ms_max
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -533,9 +541,7 @@ def run_gb300(args):
     gpu_launches = g.launch_count - launches0
     units = float(g.members()["steps"].sum() - steps0) * ncell
     member_steps = units / ncell
-    ms_max = max_over_ranks(ms, world, device)
-    units_all = sum_over_ranks(units, world, device)
-    value = units_all / (ms_max * 1e-3)
+    value, ms_max = job_value(units, ms, world, device)
 
     # roofline of the step kernel: algorithmic bytes / measured kernel time
     hbm_peak, peak_kind = peaks()
