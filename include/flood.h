@@ -215,6 +215,35 @@ int flood_adjoint(flood_grid* g, const flood_loss_spec* loss, int ckpt_every, fl
  * (with checkpointing) and of its reverse pass (replay included). */
 int flood_adjoint_timing(const flood_grid* g, double* forward_ms, double* reverse_ms);
 
+/* ==== Ensemble products (Section 4.4, Figs. 15-16) ==========================
+ * Per member, the running maximum depth hmax_i(r, c) over every step since
+ * tracking was turned on; from those and the particle weights w_i, per cell:
+ *   exceedance  P = sum_i w_i [hmax_i >= threshold]   (FP64 sum in member
+ *               order, the threshold rounded to FP32, result FP32)
+ *   percentile  h_a = the smallest hmax_i whose weighted empirical
+ *               distribution value W_i = sum of w_j over members j with
+ *               hmax_j <= hmax_i (FP64, member order) reaches a; where
+ *               rounding leaves every W_i below a, the largest hmax_i. */
+
+/* Turn tracking on (1: the maxima start at the current depths) or off (0).
+ * While on, every step also raises the maxima (8 more bytes per
+ * member-cell-step), and a resampling copies a particle's maxima along with
+ * its state.  Errors: FLOOD_ERR_STATE (before flood_ensemble_init),
+ * FLOOD_ERR_OOM. */
+int flood_track_max_depth(flood_grid* g, int on, void* stream);
+
+/* Member m's running maximum depth as [ny][nx] FP32 (host or device).
+ * Synchronous.  Errors: FLOOD_ERR_STATE (not tracking), FLOOD_ERR_ARG. */
+int flood_get_max_depth(flood_grid* g, int member, float* out, void* stream);
+
+/* The products above with the current particle weights.  exceed: [ny][nx]
+ * FP32 or NULL; levels: n_levels (0..16) values in (0, 1]; pct:
+ * [n_levels][ny][nx] FP32.  Host or device outputs.  Synchronous.  Errors:
+ * FLOOD_ERR_STATE (not tracking), FLOOD_ERR_ARG (levels, more than 384
+ * members or 65535 rows), FLOOD_ERR_OOM. */
+int flood_ensemble_products(flood_grid* g, double threshold, int n_levels, const double* levels,
+                            float* exceed, float* pct, void* stream);
+
 /* ==== Gradient calibration (extension: the paper estimates its uncertain
  * inputs with the particle filter alone, Section 2.2 / 4.4) ================
  * Roughness as the base field times a coarse factor field: fine cell (r, c)

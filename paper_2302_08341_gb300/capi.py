@@ -31,7 +31,8 @@ EXPORTED = ["flood_default_params", "flood_last_error", "flood_create_grid", "fl
             "flood_batch_launch_count", "flood_autotune", "flood_storage_static",
             "flood_storage_static_error", "flood_set_roughness_factor",
             "flood_get_roughness_factor", "flood_roughness_factor_grad", "flood_calibration_step",
-            "flood_batch_set_engine"]
+            "flood_batch_set_engine", "flood_track_max_depth", "flood_get_max_depth",
+            "flood_ensemble_products"]
 
 
 class FloodError(RuntimeError):
@@ -122,6 +123,9 @@ def lib(path: str = LIB_PATH):
     L.flood_batch_step.argtypes = [_VP, C.c_double, _VP]
     L.flood_batch_set_launch.argtypes = [_VP, C.c_int, C.c_int]
     L.flood_batch_set_engine.argtypes = [_VP, C.c_int]
+    L.flood_track_max_depth.argtypes = [_VP, C.c_int, _VP]
+    L.flood_get_max_depth.argtypes = [_VP, C.c_int, _VP, _VP]
+    L.flood_ensemble_products.argtypes = [_VP, C.c_double, C.c_int, _VP, _VP, _VP, _VP]
     L.flood_batch_get_state.argtypes = [_VP, C.c_int, _VP, _VP, _VP, _VP]
     L.flood_batch_members.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _VP]
     L.flood_batch_launch_count.argtypes = [_VP]
@@ -379,6 +383,28 @@ class Grid:
         _check(lib().flood_adjoint_timing(self.h, C.byref(f), C.byref(r)), self.h)
         out["forward_ms"], out["reverse_ms"] = f.value, r.value
         return out
+
+    def track_max_depth(self, on=True, stream=None):
+        """Running maximum depth of every member (flood_track_max_depth)."""
+        _check(lib().flood_track_max_depth(self.h, 1 if on else 0, stream_handle(stream)), self.h)
+
+    def max_depth(self, member, stream=None):
+        out = np.zeros((self.ny, self.nx), np.float32)
+        _check(lib().flood_get_max_depth(self.h, int(member), out.ctypes.data,
+                                         stream_handle(stream)), self.h)
+        return out
+
+    def ensemble_products(self, threshold=0.2, levels=(0.1, 0.5, 0.9), stream=None):
+        """Exceedance probability of the maximum depth and its percentile
+        maps (flood_ensemble_products); host arrays."""
+        lv = np.ascontiguousarray(levels, dtype=np.float64)
+        exceed = np.zeros((self.ny, self.nx), np.float32)
+        pct = np.zeros((len(lv), self.ny, self.nx), np.float32)
+        _check(lib().flood_ensemble_products(self.h, float(threshold), len(lv),
+                                             lv.ctypes.data if len(lv) else None, exceed.ctypes.data,
+                                             pct.ctypes.data if len(lv) else None,
+                                             stream_handle(stream)), self.h)
+        return exceed, pct
 
     def set_roughness_factor(self, f, stream=None):
         """Roughness n = n0 * f[block] over a coarse [cy][cx] factor field

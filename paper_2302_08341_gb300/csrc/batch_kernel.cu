@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(32 * W) batch_step_kernel(const BatchArgs a)
     const size_t ms = 3 * sd.plane;
     const float* src = sd.state + (size_t)p.cur * ms;
     float* dst = sd.state + (size_t)(1 - p.cur) * ms;
-    const MarchOut mo = march_rows(src, dst, nullptr, sd.z, sd.n, sd.plane, sd.ny, sd.nx, sd.ld, tk.c0,
+    const MarchOut mo = march_rows(src, dst, nullptr, nullptr, sd.z, sd.n, sd.plane, sd.ny, sd.nx, sd.ld, tk.c0,
                                    tk.r0, tk.r1, lane, k, p.dt_dx, sd.scale, p.dr, a.east_out,
                                    a.south_out);
     if (mo.bad) atomicOr(a.err, 1);
@@ -111,8 +111,8 @@ __global__ void __launch_bounds__(32 * W, 20 / W) batch_tma_kernel(const BatchAr
     tma_march_smem(smem_raw, W, w, bar0, my_stages);
     float* dst = sd.state + (size_t)(1 - p.cur) * 3 * sd.plane;
     MarchOut mo;
-    if (!tma_march(a.maps + 2 * i, a.maps + 2 * i + 1, p.cur * 3, bar0, my_stages, dst, nullptr,
-                   a.err, sd.plane, sd.ny, sd.nx, sd.ld, tk.c0, tk.r0, tk.r1, lane, k, p.dt_dx,
+    if (!tma_march<false>(a.maps + 2 * i, a.maps + 2 * i + 1, p.cur * 3, bar0, my_stages, dst, nullptr,
+                   nullptr, a.err, sd.plane, sd.ny, sd.nx, sd.ld, tk.c0, tk.r0, tk.r1, lane, k, p.dt_dx,
                    sd.scale, p.dr, a.east_out, a.south_out, mo))
         return;
     if (mo.bad) atomicOr(a.err, 1);

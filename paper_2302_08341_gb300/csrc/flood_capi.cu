@@ -67,7 +67,8 @@ void free_ensemble(flood_grid* g)
     dfree(g->plan); dfree(g->log); dfree(g->ckpt); dfree(g->seg); dfree(g->lam);
     dfree(g->gnm); dfree(g->gn_out); dfree(g->gpart); dfree(g->seg_end); dfree(g->samp_step);
     dfree(g->samp_y); dfree(g->samp_d); dfree(g->samp_cells); dfree(g->closs);
-    g->closs = nullptr; g->closs_cap = 0;
+    dfree(g->hmax_field);
+    g->closs = nullptr; g->closs_cap = 0; g->hmax_field = nullptr; g->track_max = false;
     g->plan = nullptr; g->log = nullptr; g->ckpt = nullptr; g->seg = nullptr;
     g->lam = nullptr; g->gnm = nullptr; g->gn_out = nullptr; g->gpart = nullptr;
     g->seg_end = nullptr; g->samp_step = nullptr; g->samp_y = nullptr; g->samp_d = nullptr;
@@ -108,6 +109,7 @@ StepArgs step_args(const flood_grid* g, double t_end)
     a.ckpt = g->logging ? g->ckpt : nullptr;
     a.ckpt_every = g->ckpt_every > 0 ? g->ckpt_every : 1;
     a.err = g->err;
+    a.hmax_field = g->track_max ? g->hmax_field : nullptr;
     a.plane = g->plane;
     a.ny = g->ny; a.nx = g->nx; a.ld = g->ld; a.M = g->M; a.nb = g->nb;
     a.rows_per_strip = g->rows_per_strip;
@@ -538,6 +540,10 @@ int pf_assimilate(flood_grid* g, int G, const float* y, const double* d, const d
     flood::launch_pf(a, s);
     flood::launch_copy(g->state, a.ms, a.n_copy, a.copy_dst, a.copy_src, M, g->plane, g->n_sm, s);
     g->launches += 2;
+    if (g->track_max) {
+        flood::launch_copy_planes(g->hmax_field, a.n_copy, a.copy_dst, a.copy_src, g->plane, g->n_sm, s);
+        g->launches++;
+    }
     CK(g, cudaGetLastError());
     if (weights_out) CK(g, cudaMemcpyAsync(weights_out, g->w_post, sizeof(double) * M, cudaMemcpyDefault, s));
     if (idx_out) CK(g, cudaMemcpyAsync(idx_out, a.idx, sizeof(int32_t) * M, cudaMemcpyDefault, s));
@@ -779,6 +785,8 @@ extern "C" int flood_autotune(flood_grid* g, int steps_per_trial, int* best_rows
     const int64_t k0 = g->k;
     const int rows0 = g->rows_per_strip, mpc0 = g->members_per_cta, eng0 = g->engine;
     const bool fixed0 = g->launch_fixed;
+    const bool track0 = g->track_max;  // trial steps must not raise the running maxima
+    g->track_max = false;
     struct Cand { int rows, mpc, engine; };
     std::vector<Cand> cands;
     for (int e : {1, 0})
@@ -823,6 +831,7 @@ extern "C" int flood_autotune(flood_grid* g, int steps_per_trial, int* best_rows
     }
     cudaStreamSynchronize(s);
     cudaFree(snap);
+    g->track_max = track0;
     (void)k0;
     if (rc) {
         g->rows_per_strip = rows0;

@@ -47,6 +47,7 @@ struct StepArgs {
     int seg_first, replay_i;
     int* err;                   // device error word (bit 0: non-finite depth)
     int m_base;                 // first member of this launch (one-launch-per-member form)
+    float* hmax_field;          // [M][plane] running maximum depth (or null: not tracked)
     size_t plane;               // ny * ld
     int ny, nx, ld, M, nb;
     int rows_per_strip;

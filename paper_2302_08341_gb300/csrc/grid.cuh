@@ -79,6 +79,9 @@ struct flood_grid {
     double* samp_d = nullptr;     // [ns][G]
     int32_t* samp_cells = nullptr;
     double adj_fwd_ms = 0.0, adj_rev_ms = 0.0;
+    // ensemble products (products.cu)
+    float* hmax_field = nullptr;  // [M][plane] running maximum depth of each member
+    bool track_max = false;
     // gradient calibration (calibrate.cu)
     float* n0 = nullptr;          // [ny][ld] base roughness, kept once a factor field is set
     float* fac = nullptr;         // [fcy][fcx] roughness factor field
@@ -108,6 +111,8 @@ int launch_steps(flood_grid* g, int64_t count, double t_end, cudaStream_t s);
 int read_clocks(flood_grid* g, std::vector<MemberClock>& out, cudaStream_t s);
 int check_err(flood_grid* g);
 void collect_profile(flood_grid* g);
+void launch_copy_planes(float* field, const int32_t* n_copy, const int32_t* dsts, const int32_t* srcs,
+                        size_t plane, int n_sm, cudaStream_t s);
 
 }  // namespace flood
 

@@ -1,6 +1,7 @@
 // Per-warp march of the fused step over one 128-column span of rows
 // [r0, r1) of one member: reads the state at src (h, qx, qy planes) and the
-// shared z, n; writes the new state to dst (and ck when non-null); returns
+// shared z, n; writes the new state to dst (and ck when non-null), raises the
+// running maximum depth at hm (when non-null) to the new depth; returns
 // the warp-local maximum depth, the non-finite flag and the outflow / clamp
 // partial sums.  Shared by the ensemble, replay and batched step kernels.
 #pragma once
@@ -96,7 +97,7 @@ __device__ __forceinline__ void row_depths(const float (&hC)[4], const float (&q
 }
 
 __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, float* __restrict__ dst,
-                                               float* ck, const float* __restrict__ z,
+                                               float* ck, float* hm, const float* __restrict__ z,
                                                const float* __restrict__ n, size_t plane, int ny,
                                                int nx, int ld, int c0, int r0, int r1, int lane,
                                                const FaceK& k, float dt_dx, float s, float dr,
@@ -208,6 +209,12 @@ __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, fl
                 m_store4(ck + o, hN);
                 m_store4(ck + plane + o, qxE);
                 m_store4(ck + 2 * plane + o, qyS);
+            }
+            if (hm) {  // loaded here, not ahead: registers are scarce in this kernel
+                const float4 hmo = *reinterpret_cast<const float4*>(hm + o);
+                *reinterpret_cast<float4*>(hm + o) =
+                    make_float4(fmaxf(hmo.x, hN[0]), fmaxf(hmo.y, hN[1]), fmaxf(hmo.z, hN[2]),
+                                fmaxf(hmo.w, hN[3]));
             }
         }
         // march: this row's south links are the next row's north links

@@ -103,7 +103,8 @@ __global__ void __launch_bounds__(32 * WM * WC, FLOOD_STEP_MIN_BLOCKS * 4 / (WM 
 
     const int r0 = blockIdx.z * a.rows_per_strip;
     const int r1 = min(r0 + a.rows_per_strip, ny);
-    const MarchOut mo = march_rows(src, dst, ck, a.z, a.n, plane, ny, nx, ld, c0, r0, r1, lane, k,
+    float* hm = (!REPLAY && a.hmax_field) ? a.hmax_field + (size_t)m * plane : nullptr;
+    const MarchOut mo = march_rows(src, dst, ck, hm, a.z, a.n, plane, ny, nx, ld, c0, r0, r1, lane, k,
                                    p.dt_dx, a.scale[m], p.dr, a.east_out, a.south_out);
     if (mo.bad) atomicOr(a.err, 1);
     if (REPLAY) return;

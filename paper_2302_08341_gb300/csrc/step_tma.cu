@@ -12,7 +12,7 @@ namespace {
 
 constexpr int kSpan = kTmaSpan;
 
-template <int WM>
+template <int WM, bool TRACK_MAX>
 __global__ void __launch_bounds__(32 * WM, 20 / WM) step_tma_kernel(const __grid_constant__ TmaArgs t)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -47,7 +47,8 @@ __global__ void __launch_bounds__(32 * WM, 20 / WM) step_tma_kernel(const __grid
     const int r0 = blockIdx.z * a.rows_per_strip;
     const int r1 = min(r0 + a.rows_per_strip, a.ny);
     MarchOut mo;
-    if (!tma_march(&t.state_map, &t.static_map, (pl.cur * a.M + m) * 3, bar0, my_stages, dst, ck,
+    float* hm = TRACK_MAX ? a.hmax_field + (size_t)m * a.plane : nullptr;
+    if (!tma_march<TRACK_MAX>(&t.state_map, &t.static_map, (pl.cur * a.M + m) * 3, bar0, my_stages, dst, ck, hm,
                    a.err, a.plane, a.ny, a.nx, a.ld, c0, r0, r1, lane, k, pl.dt_dx, a.scale[m],
                    pl.dr, a.east_out, a.south_out, mo))
         return;
@@ -104,7 +105,10 @@ int encode_map_3d(CUtensorMap* map, const void* base, uint64_t d0, uint64_t d1, 
 
 int tma_box_cols() { return kTmaBox; }
 
-int launch_step_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
+namespace {
+
+template <bool TRACK_MAX>
+void launch_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
 {
     const StepArgs& a = t.a;
     const int spans = (a.nx + kSpan - 1) / kSpan;
@@ -113,16 +117,27 @@ int launch_step_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
         static bool attr = false;
         const size_t shm = tma_smem_bytes<4>();
         if (!attr) {
-            cudaFuncSetAttribute(step_tma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+            cudaFuncSetAttribute(step_tma_kernel<4, TRACK_MAX>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
             attr = true;
         }
         dim3 grid((a.M + 3) / 4, spans, strips), block(32, 4);
-        step_tma_kernel<4><<<grid, block, shm, s>>>(t);
+        step_tma_kernel<4, TRACK_MAX><<<grid, block, shm, s>>>(t);
     } else {
         const size_t shm = tma_smem_bytes<1>();
         dim3 grid(a.M, spans, strips), block(32, 1);
-        step_tma_kernel<1><<<grid, block, shm, s>>>(t);
+        step_tma_kernel<1, TRACK_MAX><<<grid, block, shm, s>>>(t);
     }
+}
+
+}  // namespace
+
+int launch_step_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
+{
+    if (t.a.hmax_field)
+        launch_tma<true>(t, members_per_cta, s);
+    else
+        launch_tma<false>(t, members_per_cta, s);
     return 0;
 }
 

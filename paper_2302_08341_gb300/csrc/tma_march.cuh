@@ -56,10 +56,14 @@ __device__ __forceinline__ void tma_store4(float* p, const float (&v)[4])
 
 // state_map: (ld, ny, planes) with the source h, qx, qy at planes
 // [plane0, plane0 + 3); static_map: (ld, ny, 2) with z then n.  Writes the
-// new state to dst (and ck when non-null).  Returns false if a wait gave up.
+// new state to dst (and ck when non-null); TRACK_MAX: also raises the
+// running maximum depth at hm (a separate instantiation, so the plain step
+// carries no trace of it).  Returns false if a wait gave up.
+template <bool TRACK_MAX>
 __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CUtensorMap* static_map,
                                           int plane0, uint32_t bar0, unsigned char* my_stages,
-                                          float* __restrict__ dst, float* ck, int* err, size_t plane,
+                                          float* __restrict__ dst, float* ck, float* hm, int* err,
+                                          size_t plane,
                                           int ny, int nx, int ld, int c0, int r0, int r1, int lane,
                                           const FaceK& k, float dt_dx, float s, float dr,
                                           int east_out, int south_out, MarchOut& out)
@@ -177,6 +181,8 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
         const float* P = row_ptr(r);
         float hS[4] = {0, 0, 0, 0}, zS[4] = {0, 0, 0, 0}, nS[4] = {0, 0, 0, 0};
         float qxo[4], qyo[4];
+        float4 hmo = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (TRACK_MAX && act) hmo = *reinterpret_cast<const float4*>(hm + o);
         tma_lds4(qxo, P + kBox + x0);
         tma_lds4(qyo, P + 2 * kBox + x0);
         if (has_s) {
@@ -224,6 +230,10 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
                 tma_store4(ck + plane + o, qxE);
                 tma_store4(ck + 2 * plane + o, qyS);
             }
+            if (TRACK_MAX)
+                *reinterpret_cast<float4*>(hm + o) =
+                    make_float4(fmaxf(hmo.x, hN[0]), fmaxf(hmo.y, hN[1]), fmaxf(hmo.z, hN[2]),
+                                fmaxf(hmo.w, hN[3]));
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {

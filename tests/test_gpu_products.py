@@ -1,0 +1,131 @@
+"""GPU ensemble products (Section 4.4, Figs. 15-16): the running maximum
+depth kept by the step kernels (bit for bit the maximum of the stepped
+states, through a resampling that moves histories with their particles),
+against the FP64 oracle's trajectory, and the exceedance / percentile maps
+against the oracle's products of the same maxima and weights (bit for
+bit), up to the full 2000 x 2000 x 96 ensemble on sampled rows."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import products as prod
+from paper_2302_08341_gb300 import synth
+from tests.gpu_util import compare, oracle_params, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    return require_gpu()
+
+
+@pytest.mark.parametrize("engine", [0, 1])
+def test_tracked_maximum_is_the_maximum_of_the_steps(capi, engine):
+    ny, nx, M = 45, 150, 5
+    terr = synth.make_terrain(ny, nx, seed=51)
+    hy = synth.hyetograph_constant(120.0, 600.0)
+    rm, sc = synth.ensemble_prior(51, M)
+    p = capi.Params.default(dt_fixed=0.5)   # members stay in step with one another
+    with capi.Grid(terr.z, terr.n, p) as g:
+        g.ensemble_init(M, rm, sc, hy)
+        g.set_engine(engine)
+        g.advance_to(60.0)
+        g.track_max_depth(True)
+        host = np.array([g.get_state(m)[0] for m in range(M)])
+        for i in range(40):
+            g.step(1)
+            host = np.maximum(host, np.array([g.get_state(m)[0] for m in range(M)]))
+            if i == 20:   # a forced resampling moves each particle's history with it
+                y = g.gauge_sample(np.array([5 * nx + 7, 30 * nx + 100], np.int32))
+                u, beta = synth.pf_draws(51, 1, M)
+                pf = g.pf_assimilate(y[0].astype(np.float64), 0.05, u, beta, force=True)
+                src = oracle.assign_slots(pf["idx"])
+                host = host[src]
+        got = np.array([g.max_depth(m) for m in range(M)])
+    assert np.array_equal(got, host)
+
+
+def test_maximum_follows_the_oracle_trajectory(capi):
+    ny, nx = 64, 96
+    terr = synth.make_terrain(ny, nx, seed=52)
+    hy = synth.hyetograph_constant(80.0, 600.0)
+    p = capi.Params.default(dt_fixed=0.5)
+    with capi.Grid(terr.z, terr.n, p) as g:
+        g.ensemble_init(1, np.ones(1, np.float32), np.ones(1, np.float32), hy)
+        g.track_max_depth(True)
+        g.advance_to(300.0)
+        got = g.max_depth(0)
+    op = oracle_params(p, ny, nx)
+    mo = oracle.Member.dry(ny, nx)
+    hmax = mo.h.copy()
+    for _ in range(600):
+        oracle.advance(op, terr.z, terr.n, 1.0, 1.0, hy, mo, max_steps=1)
+        hmax = prod.running_max(hmax, mo.h)
+    assert mo.t == 300.0
+    compare(got, hmax, 1e-3)
+
+
+def test_products_equal_the_oracle_products_of_the_same_maxima(capi):
+    ny, nx, M = 40, 70, 12
+    terr = synth.make_terrain(ny, nx, seed=53)
+    hy = synth.hyetograph_triangular(60.0, 1200.0, 3600.0)
+    rm, sc = synth.ensemble_prior(53, M)
+    rm = (rm * 3.0).astype(np.float32)
+    cells = synth.gauge_cells(terr, 4, seed=53)
+    with capi.Grid(terr.z, terr.n) as g:
+        g.ensemble_init(M, rm, sc, hy)
+        g.track_max_depth(True)
+        g.advance_to(600.0)
+        y = g.gauge_sample(cells)
+        u, beta = synth.pf_draws(53, 1, M)
+        # no resampling: the weights stay unequal
+        g.pf_assimilate(y[3].astype(np.float64), 0.05, u, beta, n_thr_frac=1e-9)
+        w = g.members()["weights"]
+        levels = (0.1, 0.25, 0.5, 0.9, 1.0)
+        exceed, pct = g.ensemble_products(0.05, levels)
+        hm = np.array([g.max_depth(m) for m in range(M)])
+    assert np.ptp(w) > 0
+    assert np.array_equal(exceed, prod.exceedance(hm, w, 0.05).astype(np.float32))
+    assert np.array_equal(pct, prod.percentiles(hm, w, levels))
+    assert 0 < exceed.max() <= 1.0
+
+
+def test_products_refuse_bad_calls(capi):
+    terr = synth.make_terrain(16, 20, seed=54)
+    hy = synth.hyetograph_constant(50.0, 300.0)
+    with capi.Grid(terr.z, terr.n) as g:
+        g.ensemble_init(2, np.ones(2, np.float32), np.ones(2, np.float32), hy)
+        with pytest.raises(capi.FloodError):
+            g.ensemble_products(0.2)
+        g.track_max_depth(True)
+        with pytest.raises(capi.FloodError):
+            g.ensemble_products(0.2, (0.0,))
+        with pytest.raises(capi.FloodError):
+            g.ensemble_products(0.2, (1.5,))
+        g.track_max_depth(False)
+        with pytest.raises(capi.FloodError):
+            g.max_depth(0)
+
+
+def test_full_size_products_on_sampled_rows(capi):
+    """2000 x 2000 cells, 96 members, one 300 s window with the maxima
+    tracked, in the benchmark's launch configuration: the products on five
+    sampled rows against the oracle's products of the same maxima."""
+    ny = nx = 2000
+    M = 96
+    terr = synth.make_terrain(ny, nx, seed=1)
+    hy = synth.hyetograph_triangular(60.0, 1200.0, 3600.0)
+    rm, sc = synth.ensemble_prior(1, M)
+    with capi.Grid(terr.z, terr.n) as g:
+        g.ensemble_init(M, rm, sc, hy)
+        g.track_max_depth(True)
+        g.advance_to(300.0)
+        levels = (0.1, 0.5, 0.9)
+        exceed, pct = g.ensemble_products(0.01, levels)
+        w = g.members()["weights"]
+        rows = np.random.default_rng(1).choice(ny, 5, replace=False)
+        hm = np.array([g.max_depth(m)[rows] for m in range(M)])
+    assert np.array_equal(exceed[rows], prod.exceedance(hm, w, 0.01).astype(np.float32))
+    assert np.array_equal(pct[:, rows], prod.percentiles(hm, w, levels))
+    assert exceed.max() > 0
