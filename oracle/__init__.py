@@ -44,11 +44,12 @@ class OrcParams(C.Structure):
                 ("alpha", C.c_double), ("dt_cap", C.c_double), ("dt_fixed", C.c_double),
                 ("h_eps", C.c_double), ("h_floor", C.c_double), ("rain_block", C.c_double),
                 ("edge_slope", C.c_double), ("limiter", C.c_int), ("east_outflow", C.c_int),
-                ("south_outflow", C.c_int)]
+                ("south_outflow", C.c_int), ("rc", C.c_void_p), ("drain", C.c_void_p)]
 
 
 class OrcVolumes(C.Structure):
-    _fields_ = [("rain", C.c_double), ("outflow", C.c_double), ("clamp", C.c_double)]
+    _fields_ = [("rain", C.c_double), ("outflow", C.c_double), ("clamp", C.c_double),
+                ("drained", C.c_double)]
 
 
 _D = C.POINTER(C.c_double)
@@ -152,9 +153,21 @@ class Params:
     limiter: int = 1
     east_outflow: int = 1
     south_outflow: int = 0
+    # land cover (Section 4.1): per-cell runoff coefficient and drainage rate
+    # (m/s), float64 [ny, nx] arrays held here, or None
+    rc: np.ndarray | None = None
+    drain: np.ndarray | None = None
 
     def c(self) -> OrcParams:
-        return OrcParams(*(getattr(self, f) for f, _ in OrcParams._fields_))
+        vals = []
+        for f, _ in OrcParams._fields_:
+            v = getattr(self, f)
+            if f in ("rc", "drain"):
+                if v is not None:
+                    assert v.dtype == np.float64 and v.flags.c_contiguous and v.shape == (self.ny, self.nx)
+                    v = v.ctypes.data
+            vals.append(v)
+        return OrcParams(*vals)
 
 
 def dt(p: Params, hmax: float, t: float, t_end: float = -1.0):
@@ -178,6 +191,7 @@ class Member:
     rain: float = 0.0
     outflow: float = 0.0
     clamp: float = 0.0
+    drained: float = 0.0
     steps: int = 0
 
     @staticmethod
@@ -193,10 +207,10 @@ def step(p: Params, z, n, scale, rain, dt_, m: Member):
     """One iteration (Eq. 2-3 on every link, Eq. 5 and Eq. 1 on every cell)."""
     z = np.ascontiguousarray(z, np.float64); n = np.ascontiguousarray(n, np.float64)
     qxn = np.empty_like(m.qx); qyn = np.empty_like(m.qy)
-    v = OrcVolumes(m.rain, m.outflow, m.clamp)
+    v = OrcVolumes(m.rain, m.outflow, m.clamp, m.drained)
     lib().orc_step(C.byref(p.c()), _d(z), _d(n), scale, rain, dt_, _d(m.h), _d(m.qx), _d(m.qy),
                    _d(qxn), _d(qyn), C.byref(v))
-    m.rain, m.outflow, m.clamp = v.rain, v.outflow, v.clamp
+    m.rain, m.outflow, m.clamp, m.drained = v.rain, v.outflow, v.clamp, v.drained
     m.steps += 1
 
 
@@ -207,14 +221,14 @@ def advance(p: Params, z, n, scale, rain_mult, hyeto, m: Member, t_end=-1.0, max
     z = np.ascontiguousarray(z, np.float64); n = np.ascontiguousarray(n, np.float64)
     hy = np.ascontiguousarray(hyeto, np.float64)
     t = C.c_double(m.t)
-    v = OrcVolumes(m.rain, m.outflow, m.clamp)
+    v = OrcVolumes(m.rain, m.outflow, m.clamp, m.drained)
     cap = (max_steps if max_steps > 0 else 2_000_000) if log_dt else 0
     log = np.zeros(max(cap, 1))
     k = lib().orc_advance(C.byref(p.c()), _d(z), _d(n), float(scale), float(rain_mult),
                           _d(hy), len(hy), _d(m.h), _d(m.qx), _d(m.qy), C.byref(t), float(t_end),
                           int(max_steps), C.byref(v), _d(log) if log_dt else None, cap)
     m.t = t.value
-    m.rain, m.outflow, m.clamp = v.rain, v.outflow, v.clamp
+    m.rain, m.outflow, m.clamp, m.drained = v.rain, v.outflow, v.clamp, v.drained
     m.steps += k
     return log[:k].copy() if log_dt else k
 
@@ -247,7 +261,7 @@ class Ensemble:
         return st
 
     def volumes(self):
-        return np.array([[v.rain, v.outflow, v.clamp] for v in self.vol])
+        return np.array([[v.rain, v.outflow, v.clamp, v.drained] for v in self.vol])
 
     def storage(self):
         dx = self.p.dx

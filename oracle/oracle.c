@@ -56,6 +56,11 @@ typedef struct {
     int limiter;          /* 1: |q| <= h_upstream dx / (4 dt) on each link   */
     int east_outflow;     /* 1: free outflow through the east edge           */
     int south_outflow;    /* 1: free outflow through the south edge          */
+    /* Land cover (Section 4.1), both NULL when absent: per cell, the fraction
+       of the rain that stays on the surface (the runoff coefficient) and the
+       drainage rate (m/s) that removes water while there is any. */
+    const double* rc;
+    const double* drain;
 } orc_params;
 
 /* Volume bookkeeping of one member (m^3), all in FP64. */
@@ -63,6 +68,7 @@ typedef struct {
     double rain;     /* rain volume added                                     */
     double outflow;  /* volume that left through free-outflow edges           */
     double clamp;    /* volume added by resetting negative depths to zero     */
+    double drained;  /* volume removed by drainage (land cover)               */
 } orc_volumes;
 
 #define IX(r, c) ((size_t)(r) * (size_t)nx + (size_t)(c))
@@ -192,7 +198,17 @@ void orc_step(const orc_params* p, const double* z, const double* n, double scal
         for (int c = 0; c < nx; ++c) {
             double dV = qx_new[IQX(r, c)] * dx - qx_new[IQX(r, c + 1)] * dx
                       + qy_new[IQY(r, c)] * dx - qy_new[IQY(r + 1, c)] * dx;     /* Eq. 5 */
-            double hn = h[IX(r, c)] + dt * dV / (dx * dx) + dt * rain;           /* Eq. 1 */
+            const double rcv = p->rc ? p->rc[IX(r, c)] : 1.0;
+            double hn = h[IX(r, c)] + dt * dV / (dx * dx) + dt * rain * rcv;     /* Eq. 1 */
+            if (p->drain) {
+                /* drainage takes at most the water present after this step's
+                   fluxes and rain */
+                double sink = dt * p->drain[IX(r, c)];
+                const double avail = hn > 0.0 ? hn : 0.0;
+                if (sink > avail) sink = avail;
+                hn -= sink;
+                vol->drained += sink * dx * dx;
+            }
             if (hn < 0.0) {
                 vol->clamp += -hn * dx * dx;
                 hn = 0.0;
@@ -202,7 +218,13 @@ void orc_step(const orc_params* p, const double* z, const double* n, double scal
     }
     for (int r = 0; r < ny; ++r) vol->outflow += dt * qx_new[IQX(r, nx)] * dx;
     for (int c = 0; c < nx; ++c) vol->outflow += dt * qy_new[IQY(ny, c)] * dx;
-    vol->rain += dt * rain * dx * dx * (double)ny * (double)nx;
+    if (p->rc) {
+        double area = 0.0;
+        for (size_t i = 0; i < (size_t)ny * (size_t)nx; ++i) area += p->rc[i];
+        vol->rain += dt * rain * dx * dx * area;
+    } else {
+        vol->rain += dt * rain * dx * dx * (double)ny * (double)nx;
+    }
     memcpy(qx, qx_new, sizeof(double) * (size_t)ny * (size_t)(nx + 1));
     memcpy(qy, qy_new, sizeof(double) * (size_t)(ny + 1) * (size_t)nx);
 }
@@ -551,6 +573,7 @@ double orc_loss_and_grad(const orc_params* p, const double* z, const double* n, 
                          long* n_steps_out)
 {
     const int ny = p->ny, nx = p->nx;
+    if (p->rc || p->drain) return NAN;  /* the reverse mode covers the scheme without land cover */
     const size_t nc = (size_t)ny * nx, nqx = (size_t)ny * (nx + 1), nqy = (size_t)(ny + 1) * nx;
     const size_t per = nc + nqx + nqy;
     long cap = 1024, nst = 0;

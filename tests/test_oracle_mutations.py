@@ -12,6 +12,7 @@ import sys
 
 import oracle
 from tests import test_oracle_adjoint as A
+from tests import test_oracle_land_cover as LC
 from tests import test_oracle_pf as P
 from tests import test_oracle_scheme as S
 
@@ -41,6 +42,10 @@ PINS = [
     functools.partial(A.test_dot_product_identity_per_step, regime="drying"),
     functools.partial(A.test_dot_product_identity_per_step, regime="outflow"),
     A.test_closed_form_uniform_rain_on_flat_box,
+    LC.test_flat_box_rain_above_drainage_closed_form,
+    LC.test_flat_box_drainage_above_rain_takes_all,
+    LC.test_volume_balance_with_land_cover_exact_to_1e12,
+    LC.test_wall_cells_stay_dry_and_pass_no_flow,
 ]
 
 # (name, original text, planted mistake)
@@ -58,7 +63,12 @@ MUTATIONS = [
     ("Eq 5 x/y index swap", "qx_new[IQX(r, c)] * dx - qx_new[IQX(r, c + 1)] * dx",
      "qx_new[IQX(r, c)] * dx - qx_new[IQX(r, c)] * dx"),
     ("Eq 1 divides by dx only", "dt * dV / (dx * dx)", "dt * dV / dx"),
-    ("rain without dt", "+ dt * rain;", "+ rain;"),
+    ("rain without dt", "+ dt * rain * rcv;", "+ rain * rcv;"),
+    ("runoff coefficient ignored", "+ dt * rain * rcv;", "+ dt * rain;"),
+    ("drainage not limited by the water present", "if (sink > avail) sink = avail;", ""),
+    ("drainage without dt", "double sink = dt * p->drain[IX(r, c)];",
+     "double sink = p->drain[IX(r, c)];"),
+    ("rain volume ignores the runoff coefficient", "area += p->rc[i];", "area += 1.0;"),
     ("x-link roughness not averaged", "scale * 0.5 * (n[IX(r, c - 1)] + n[IX(r, c)])",
      "scale * n[IX(r, c)]"),
     ("roughness scale dropped on y links", "double nl = scale * 0.5 * (n[IX(r - 1, c)]",
