@@ -64,7 +64,7 @@ def parse():
                     help="skip the adjoint and uneven-batch measurements")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch configuration (profiling runs)")
-    ap.add_argument("--only", choices=["adjoint", "batch", "calibration"],
+    ap.add_argument("--only", choices=["adjoint", "batch", "calibration", "land_cover"],
                     help="run one extension measurement alone and print it (profiling runs)")
     ap.add_argument("--calibration-windows", type=int, default=3)
     ap.add_argument("--engine", type=int, choices=[0, 1], default=None,
@@ -434,6 +434,42 @@ def plain_vs_fused(g, tuned, stream, device, ncell, hbm_peak):
     return out
 
 
+def land_cover_measure(capi):
+    """Land cover (Section 4.1) on the benchmark ensemble: 2000 x 2000 cells,
+    96 members with their own class roughness (Table 1 ranges) and drainage
+    rate, green land / water / hardened ground / cells outside the domain;
+    the second 300 s window of the storm is timed (the first warms up)."""
+    import torch
+    from paper_2302_08341_gb300 import synth
+    terr = synth.make_terrain(NY, NX, seed=SEED)
+    cls = synth.land_cover(terr, seed=SEED)
+    hy = synth.hyetograph_triangular(60.0, 1200.0, 3600.0)
+    rm, sc = synth.ensemble_prior(SEED, M)
+    n_m, d_m = synth.land_prior(SEED, M)
+    stream = torch.cuda.current_stream()
+    with capi.Grid(terr.z, terr.n) as g:
+        g.set_land_cover(cls, synth.LAND_CLASSES)
+        g.ensemble_init(M, rm, sc, hy, stream=stream)
+        g.set_land_params(n_m, d_m)
+        g.advance_to(WINDOW, stream=stream)
+        s0 = g.members()["steps"].sum()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g.advance_to(2 * WINDOW, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        units = float(g.members()["steps"].sum() - s0) * NY * NX
+        vol = g.volumes()
+        drained = g.drained()
+    return {"config": f"{NY}x{NX} cells, {M} members, 4 land classes "
+                      f"({100 * (cls == 3).mean():.1f} % of the cells outside the domain), "
+                      "second 300 s window",
+            "value": units / (ms * 1e-3), "unit": "member-cell-steps/s", "ms_per_window": ms,
+            "drained_share_of_rain": float(np.mean(drained / vol["rain"]))}
+
+
 def products_measure(g, stream, device, ncell, fused_value):
     """Section 4.4's products on the benchmark ensemble: one 300 s window with
     every member's running maximum depth kept by the step kernel (8 more
@@ -624,6 +660,7 @@ def run_gb300(args):
         extensions["adjoint"] = adjoint_measure(capi)
         extensions["batched"] = batch_measure(capi)
         extensions["calibration"] = calibration_measure(capi, windows=args.calibration_windows)
+        extensions["land_cover"] = land_cover_measure(capi)
         extensions["batched"]["hbm_frac_whole_window"] = (
             extensions["batched"]["value"] * BYTES_SINGLE / 1e9 / hbm_peak)
         extensions["autotune"] = tuned
@@ -669,6 +706,8 @@ def run_only(args):
         res = adjoint_measure(capi)
     elif args.only == "batch":
         res = batch_measure(capi, engine=args.engine)
+    elif args.only == "land_cover":
+        res = land_cover_measure(capi)
     else:
         res = calibration_measure(capi, windows=args.calibration_windows)
     print(json.dumps({"only": args.only, "members": M, "cells": NY * NX, **res}))

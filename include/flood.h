@@ -215,6 +215,47 @@ int flood_adjoint(flood_grid* g, const flood_loss_spec* loss, int ckpt_every, fl
  * (with checkpointing) and of its reverse pass (replay included). */
 int flood_adjoint_timing(const flood_grid* g, double* forward_ms, double* reverse_ms);
 
+/* ==== Land cover (Section 4.1, Table 1) =====================================
+ * A class per cell (at most 4 classes), each with a Manning n (the members'
+ * default; Table 1 gives 0.15 green land, 0.020 water bodies, 0.017
+ * hardened ground), a runoff coefficient (the share of the rain that stays
+ * on the surface: 0.9 on green land), a drainage flag (the pipe network's
+ * drainage capacity I_drn applies: hardened ground) and an outside-the-
+ * domain flag.  Per member: the Manning n of every class and the drainage
+ * rate, the uncertain inputs of the paper's ensemble; a resampling carries
+ * them with their particle.  Each step then uses, per cell,
+ *   n = the member's n of the cell's class (times its Manning scale),
+ *   h* = h + dt/dx (net inflow) + runoff(class) * rain depth,
+ *   h' = h* - min(drains(class) * drainage rate * dt, max(h*, 0)),
+ * and reports the drained volume (flood_drained_volume); storage = rain -
+ * outflow + clamp - drained.  Cells outside the domain get their bed raised
+ * to 1e6 m and no rain, so no link into them carries flow (Eq. 3).
+ * Not covered: flood_adjoint (refused), the batched API. */
+typedef struct {
+    float n;        /* Manning n of the class (s m^-1/3), > 0 */
+    float runoff;   /* share of the rain that stays on the surface, [0, 1] */
+    int drains;     /* 1: the member's drainage rate applies to the class */
+    int outside;    /* 1: cells of the class lie outside the domain */
+} flood_land_class;
+
+/* Set the land cover once per grid: cls [ny][nx] uint8 (< n_classes <= 4),
+ * host or device.  Per-member parameters start at the classes' n and no
+ * drainage (also after a later flood_ensemble_init).  Synchronous.
+ * Errors: FLOOD_ERR_ARG, FLOOD_ERR_STATE (set twice), FLOOD_ERR_OOM. */
+int flood_set_land_cover(flood_grid* g, const uint8_t* cls, int n_classes,
+                         const flood_land_class* classes);
+
+/* Per-member land-cover parameters: n_class [N][n_classes] (> 0) and
+ * drain_rate [N] (m/s, >= 0), host or device; either may be NULL (kept).
+ * Synchronous.  Errors: FLOOD_ERR_STATE (no land cover or ensemble),
+ * FLOOD_ERR_ARG. */
+int flood_set_land_params(flood_grid* g, const float* n_class, const float* drain_rate);
+int flood_get_land_params(flood_grid* g, float* n_class, float* drain_rate);
+
+/* Volume removed by drainage so far, per member [N] FP64 (m^3; zeros
+ * without land cover).  Synchronous. */
+int flood_drained_volume(flood_grid* g, double* drained);
+
 /* ==== Ensemble products (Section 4.4, Figs. 15-16) ==========================
  * Per member, the running maximum depth hmax_i(r, c) over every step since
  * tracking was turned on; from those and the particle weights w_i, per cell:

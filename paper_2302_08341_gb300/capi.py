@@ -32,7 +32,14 @@ EXPORTED = ["flood_default_params", "flood_last_error", "flood_create_grid", "fl
             "flood_storage_static_error", "flood_set_roughness_factor",
             "flood_get_roughness_factor", "flood_roughness_factor_grad", "flood_calibration_step",
             "flood_batch_set_engine", "flood_track_max_depth", "flood_get_max_depth",
-            "flood_ensemble_products"]
+            "flood_ensemble_products", "flood_set_land_cover", "flood_set_land_params",
+            "flood_get_land_params", "flood_drained_volume"]
+
+
+class LandClass(C.Structure):
+    """flood_land_class: Manning n, runoff coefficient, drainage and
+    outside-the-domain flags of one land-cover class (Section 4.1)."""
+    _fields_ = [("n", C.c_float), ("runoff", C.c_float), ("drains", C.c_int), ("outside", C.c_int)]
 
 
 class FloodError(RuntimeError):
@@ -123,6 +130,10 @@ def lib(path: str = LIB_PATH):
     L.flood_batch_step.argtypes = [_VP, C.c_double, _VP]
     L.flood_batch_set_launch.argtypes = [_VP, C.c_int, C.c_int]
     L.flood_batch_set_engine.argtypes = [_VP, C.c_int]
+    L.flood_set_land_cover.argtypes = [_VP, _VP, C.c_int, C.POINTER(LandClass)]
+    L.flood_set_land_params.argtypes = [_VP, _VP, _VP]
+    L.flood_get_land_params.argtypes = [_VP, _VP, _VP]
+    L.flood_drained_volume.argtypes = [_VP, _VP]
     L.flood_track_max_depth.argtypes = [_VP, C.c_int, _VP]
     L.flood_get_max_depth.argtypes = [_VP, C.c_int, _VP, _VP]
     L.flood_ensemble_products.argtypes = [_VP, C.c_double, C.c_int, _VP, _VP, _VP, _VP]
@@ -382,6 +393,32 @@ class Grid:
         f = C.c_double(); r = C.c_double()
         _check(lib().flood_adjoint_timing(self.h, C.byref(f), C.byref(r)), self.h)
         out["forward_ms"], out["reverse_ms"] = f.value, r.value
+        return out
+
+    def set_land_cover(self, cls, classes):
+        """cls: [ny][nx] uint8 class per cell; classes: list of (n, runoff,
+        drains, outside) tuples (flood_set_land_cover)."""
+        cls = np.ascontiguousarray(cls, dtype=np.uint8)
+        tab = (LandClass * len(classes))(*[LandClass(float(n), float(r), int(d), int(o))
+                                           for n, r, d, o in classes])
+        self._lc_K = len(classes)
+        _check(lib().flood_set_land_cover(self.h, cls.ctypes.data, len(classes), tab), self.h)
+
+    def set_land_params(self, n_class=None, drain_rate=None):
+        nc = None if n_class is None else np.ascontiguousarray(n_class, np.float32)
+        dr = None if drain_rate is None else np.ascontiguousarray(drain_rate, np.float32)
+        _check(lib().flood_set_land_params(self.h, None if nc is None else nc.ctypes.data,
+                                           None if dr is None else dr.ctypes.data), self.h)
+
+    def land_params(self):
+        n = np.zeros((self.M, self._lc_K), np.float32)
+        d = np.zeros(self.M, np.float32)
+        _check(lib().flood_get_land_params(self.h, n.ctypes.data, d.ctypes.data), self.h)
+        return n, d
+
+    def drained(self):
+        out = np.zeros(self.M)
+        _check(lib().flood_drained_volume(self.h, out.ctypes.data), self.h)
         return out
 
     def track_max_depth(self, on=True, stream=None):

@@ -68,6 +68,7 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
     if (!L || L->n_samples < 1 || !(L->sample_dt > 0) || L->n_gauges < 1 || !L->cells || !L->d)
         return flood::fail(g, FLOOD_ERR_ARG, "invalid flood_loss_spec");
     if (ckpt_every < 0) return flood::fail(g, FLOOD_ERR_ARG, "ckpt_every must be >= 0");
+    if (g->lc_on) return flood::fail(g, FLOOD_ERR_ARG, "the adjoint does not cover land cover");
     cudaStream_t s = S(stream);
     const int M = g->M, ns = L->n_samples, G = L->n_gauges;
     const size_t ms = 3 * g->plane;

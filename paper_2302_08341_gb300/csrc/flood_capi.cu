@@ -67,8 +67,9 @@ void free_ensemble(flood_grid* g)
     dfree(g->plan); dfree(g->log); dfree(g->ckpt); dfree(g->seg); dfree(g->lam);
     dfree(g->gnm); dfree(g->gn_out); dfree(g->gpart); dfree(g->seg_end); dfree(g->samp_step);
     dfree(g->samp_y); dfree(g->samp_d); dfree(g->samp_cells); dfree(g->closs);
-    dfree(g->hmax_field);
+    dfree(g->hmax_field); dfree(g->lc_n); dfree(g->lc_drain); dfree(g->dacc);
     g->closs = nullptr; g->closs_cap = 0; g->hmax_field = nullptr; g->track_max = false;
+    g->lc_n = nullptr; g->lc_drain = nullptr; g->dacc = nullptr;
     g->plan = nullptr; g->log = nullptr; g->ckpt = nullptr; g->seg = nullptr;
     g->lam = nullptr; g->gnm = nullptr; g->gn_out = nullptr; g->gpart = nullptr;
     g->seg_end = nullptr; g->samp_step = nullptr; g->samp_y = nullptr; g->samp_d = nullptr;
@@ -110,6 +111,17 @@ StepArgs step_args(const flood_grid* g, double t_end)
     a.ckpt_every = g->ckpt_every > 0 ? g->ckpt_every : 1;
     a.err = g->err;
     a.hmax_field = g->track_max ? g->hmax_field : nullptr;
+    a.lc_on = g->lc_on ? 1 : 0;
+    if (g->lc_on) {
+        a.cls = g->cls8;
+        a.lc_n = g->lc_n;
+        a.lc_drain = g->lc_drain;
+        for (int q = 0; q < 4; ++q) {
+            a.lc_runoff[q] = g->lc_runoff[q];
+            a.lc_drains[q] = g->lc_drains[q];
+        }
+        a.dacc = g->dacc;
+    }
     a.plane = g->plane;
     a.ny = g->ny; a.nx = g->nx; a.ld = g->ld; a.M = g->M; a.nb = g->nb;
     a.rows_per_strip = g->rows_per_strip;
@@ -123,7 +135,7 @@ StepArgs step_args(const flood_grid* g, double t_end)
     a.rain_block = g->p.rain_block;
     a.dxd = g->p.dx;
     a.cell_area = g->p.dx * g->p.dx;
-    a.ncell = (double)g->ny * (double)g->nx;
+    a.ncell = g->lc_on ? g->lc_rain_cells : (double)g->ny * (double)g->nx;
     a.dx = (float)g->p.dx;
     a.h_eps = (float)g->p.h_eps;
     a.edge_drop = (float)(g->p.edge_slope * g->p.dx);
@@ -171,7 +183,7 @@ int launch_steps(flood_grid* g, int64_t count, double t_end, cudaStream_t s)
             t.static_map = g->static_map;
             t.a = a;
             flood::launch_step_tma(t, g->members_per_cta, s);
-        } else if (g->engine == 2) {
+        } else if (g->engine == 2 && !g->lc_on) {
             flood::launch_step_per_member(a, s);
             g->launches += g->M - 1;
         } else {
@@ -223,6 +235,14 @@ int ensure_vacc(flood_grid* g, int need)
     int rc = dalloc(g, &g->vacc, nw.size());
     if (rc) return rc;
     CK(g, cudaMemcpy(g->vacc, nw.data(), sizeof(double) * nw.size(), cudaMemcpyHostToDevice));
+    if (g->dacc) {  // drained volume (land cover): the same folding
+        std::vector<double> od((size_t)M * g->nslot), nd((size_t)M * need, 0.0);
+        CK(g, cudaMemcpy(od.data(), g->dacc, sizeof(double) * od.size(), cudaMemcpyDeviceToHost));
+        for (int m = 0; m < M; ++m)
+            for (int k = 0; k < g->nslot; ++k) nd[(size_t)m * need] += od[(size_t)m * g->nslot + k];
+        if ((rc = dalloc(g, &g->dacc, nd.size()))) return rc;
+        CK(g, cudaMemcpy(g->dacc, nd.data(), sizeof(double) * nd.size(), cudaMemcpyHostToDevice));
+    }
     g->nslot = need;
     return FLOOD_OK;
 }
@@ -400,6 +420,7 @@ int flood_ensemble_init(flood_grid* g, int M, const float* h0, int h0_per_member
     g->launches++;
     CK(g, cudaGetLastError());
     CK(g, cudaStreamSynchronize(s));
+    if (g->lc_on && (rc = flood::land_ensemble_init(g))) return rc;
     return FLOOD_OK;
 }
 
@@ -540,6 +561,10 @@ int pf_assimilate(flood_grid* g, int G, const float* y, const double* d, const d
     flood::launch_pf(a, s);
     flood::launch_copy(g->state, a.ms, a.n_copy, a.copy_dst, a.copy_src, M, g->plane, g->n_sm, s);
     g->launches += 2;
+    if (g->lc_on) {  // land-cover parameters follow their particle
+        flood::launch_land_permute(g->lc_n, g->lc_drain, a.src, a.resampled, M, s);
+        g->launches++;
+    }
     if (g->track_max) {
         flood::launch_copy_planes(g->hmax_field, a.n_copy, a.copy_dst, a.copy_src, g->plane, g->n_sm, s);
         g->launches++;
@@ -779,9 +804,15 @@ extern "C" int flood_autotune(flood_grid* g, int steps_per_trial, int* best_rows
     for (int m = 0; m < M; ++m)
         CK(g, cudaMemcpyAsync(snap + (size_t)m * ms, g->state + (size_t)(c0[m].cur * M + m) * ms,
                               sizeof(float) * ms, cudaMemcpyDeviceToDevice, s));
-    std::vector<double> rain0(M), vacc0((size_t)M * g->nslot * 2);
+    std::vector<double> rain0(M), vacc0((size_t)M * g->nslot * 2), drained0(M, 0.0);
     CK(g, cudaMemcpy(rain0.data(), g->rain_acc, sizeof(double) * M, cudaMemcpyDeviceToHost));
     CK(g, cudaMemcpy(vacc0.data(), g->vacc, sizeof(double) * vacc0.size(), cudaMemcpyDeviceToHost));
+    if (g->dacc) {
+        std::vector<double> d0((size_t)M * g->nslot);
+        CK(g, cudaMemcpy(d0.data(), g->dacc, sizeof(double) * d0.size(), cudaMemcpyDeviceToHost));
+        for (int m = 0; m < M; ++m)
+            for (int k = 0; k < g->nslot; ++k) drained0[m] += d0[(size_t)m * g->nslot + k];
+    }
     const int64_t k0 = g->k;
     const int rows0 = g->rows_per_strip, mpc0 = g->members_per_cta, eng0 = g->engine;
     const bool fixed0 = g->launch_fixed;
@@ -851,6 +882,11 @@ extern "C" int flood_autotune(flood_grid* g, int steps_per_trial, int* best_rows
                 for (int j = 0; j < 2; ++j)
                     v[(size_t)m * g->nslot * 2 + j] += vacc0[((size_t)m * (vacc0.size() / M / 2) + kk) * 2 + j];
         CK(g, cudaMemcpy(g->vacc, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice));
+        if (g->dacc) {
+            std::vector<double> d((size_t)M * g->nslot, 0.0);
+            for (int m = 0; m < M; ++m) d[(size_t)m * g->nslot] = drained0[m];
+            CK(g, cudaMemcpy(g->dacc, d.data(), sizeof(double) * d.size(), cudaMemcpyHostToDevice));
+        }
     }
     if (best_rows) *best_rows = bc.rows;
     if (best_mpc) *best_mpc = bc.mpc;

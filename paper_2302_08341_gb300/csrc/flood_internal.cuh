@@ -48,6 +48,14 @@ struct StepArgs {
     int* err;                   // device error word (bit 0: non-finite depth)
     int m_base;                 // first member of this launch (one-launch-per-member form)
     float* hmax_field;          // [M][plane] running maximum depth (or null: not tracked)
+    // land cover (Section 4.1; lc_on = 0: none)
+    int lc_on;
+    const uint8_t* cls;         // [ny][ld] class of every cell (< 4)
+    const float* lc_n;          // [M][4] Manning n of each class, per member
+    const float* lc_drain;      // [M] drainage rate (m/s), per member
+    float lc_runoff[4];         // fraction of the rain that stays, per class
+    float lc_drains[4];         // 1: the member's drainage applies to the class
+    double* dacc;               // [M][nslot] drained volume partials
     size_t plane;               // ny * ld
     int ny, nx, ld, M, nb;
     int rows_per_strip;
@@ -243,6 +251,51 @@ __device__ __forceinline__ float outflow_q(float h, float q, float n_cell, const
 }
 
 __device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+
+// Land cover of one member for one step (Section 4.1): per class, the
+// Manning n, the rain depth that stays on the surface and the drainage
+// depth.  Classes are 0..3, four to a 32-bit word (one lane's four cells).
+struct LandK {
+    const uint8_t* cls;  // [ny][ld]
+    float n[4];
+    float dr[4];
+    float dd[4];
+};
+
+__device__ __forceinline__ float sel4(uint32_t k, const float (&t)[4])
+{
+    return k == 0 ? t[0] : (k == 1 ? t[1] : (k == 2 ? t[2] : t[3]));
+}
+
+__device__ __forceinline__ uint32_t cls_word(const uint8_t* cls, size_t o)
+{
+    return *reinterpret_cast<const uint32_t*>(cls + o);
+}
+
+__device__ __forceinline__ uint32_t cls_at(uint32_t w, int j) { return (w >> (8 * j)) & 0xffu; }
+
+__device__ __forceinline__ void land_n4(float (&nv)[4], uint32_t w, const LandK& lk)
+{
+#pragma unroll
+    for (int j = 0; j < 4; ++j) nv[j] = sel4(cls_at(w, j), lk.n);
+}
+
+// This member's land-cover constants for a step: dr = its rain depth, dt
+// the step length.
+__device__ __forceinline__ LandK land_k(const StepArgs& a, int m, float dr, double dt)
+{
+    LandK lk;
+    lk.cls = a.cls;
+    const float dtf = (float)dt;
+    const float drain = a.lc_drain[m];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        lk.n[q] = a.lc_n[(size_t)m * 4 + q];
+        lk.dr[q] = __fmul_rn(dr, a.lc_runoff[q]);
+        lk.dd[q] = __fmul_rn(__fmul_rn(drain, a.lc_drains[q]), dtf);
+    }
+    return lk;
+}
 
 // Host-side helpers (flood_capi.cu).
 void launch_plan(const StepArgs& a, cudaStream_t s);

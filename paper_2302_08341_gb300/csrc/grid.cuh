@@ -79,6 +79,17 @@ struct flood_grid {
     double* samp_d = nullptr;     // [ns][G]
     int32_t* samp_cells = nullptr;
     double adj_fwd_ms = 0.0, adj_rev_ms = 0.0;
+    // land cover (land_cover.cu; Section 4.1)
+    bool lc_on = false;
+    int lc_K = 0;
+    uint8_t* cls8 = nullptr;      // [ny][ld] class of every cell
+    float lc_n0[4] = {0, 0, 0, 0};       // class Manning n (the members' default)
+    float lc_runoff[4] = {1, 1, 1, 1};   // fraction of the rain that stays
+    float lc_drains[4] = {0, 0, 0, 0};   // 1: the member's drainage applies
+    double lc_rain_cells = 0.0;   // sum over cells of the runoff fraction
+    float* lc_n = nullptr;        // [M][4] per-member class roughness
+    float* lc_drain = nullptr;    // [M] per-member drainage rate (m/s)
+    double* dacc = nullptr;       // [M][nslot] drained volume partials
     // ensemble products (products.cu)
     float* hmax_field = nullptr;  // [M][plane] running maximum depth of each member
     bool track_max = false;
@@ -113,6 +124,9 @@ int check_err(flood_grid* g);
 void collect_profile(flood_grid* g);
 void launch_copy_planes(float* field, const int32_t* n_copy, const int32_t* dsts, const int32_t* srcs,
                         size_t plane, int n_sm, cudaStream_t s);
+int land_ensemble_init(flood_grid* g);  // per-member land-cover defaults after flood_ensemble_init
+void launch_land_permute(float* lc_n, float* lc_drain, const int32_t* src, const int32_t* resampled,
+                         int M, cudaStream_t s);
 
 }  // namespace flood
 

@@ -1,0 +1,198 @@
+// Land cover (Section 4.1, Table 1): a class per cell, with per-class runoff
+// coefficient (the share of the rain that stays on the surface), drainage
+// (the drainage capacity of the pipe network on hardened ground) and Manning
+// n, and cells outside the domain.  The class's roughness and the drainage
+// rate are the per-member uncertain inputs of the paper's ensemble; they
+// follow their particle through a resampling.
+//
+// Cells outside the domain get a bed out of reach (kWallZ) and no rain, so
+// Eq. 3 gives every link into them a zero flow depth: they never get wet and
+// nothing crosses them.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "grid.cuh"
+
+#define CK FLOOD_CK
+
+namespace {
+
+cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+constexpr float kWallZ = 1.0e6f;  // m: a bed no water level reaches
+constexpr int kMaxClasses = 4;
+
+// After a resampling, slot s takes particle src[s]'s parameters (one CTA).
+__global__ void land_permute_kernel(float* __restrict__ lc_n, float* __restrict__ lc_drain,
+                                    const int32_t* __restrict__ src,
+                                    const int32_t* __restrict__ resampled, int M)
+{
+    if (!*resampled) return;
+    extern __shared__ float old[];  // [M][4] then [M]
+    for (int i = threadIdx.x; i < M * 4; i += blockDim.x) old[i] = lc_n[i];
+    for (int i = threadIdx.x; i < M; i += blockDim.x) old[M * 4 + i] = lc_drain[i];
+    __syncthreads();
+    for (int s = threadIdx.x; s < M; s += blockDim.x) {
+        const int p = src[s];
+        for (int q = 0; q < 4; ++q) lc_n[s * 4 + q] = old[p * 4 + q];
+        lc_drain[s] = old[M * 4 + p];
+    }
+}
+
+}  // namespace
+
+namespace flood {
+
+void launch_land_permute(float* lc_n, float* lc_drain, const int32_t* src, const int32_t* resampled,
+                         int M, cudaStream_t s)
+{
+    land_permute_kernel<<<1, 256, sizeof(float) * 5 * M, s>>>(lc_n, lc_drain, src, resampled, M);
+}
+
+// Per-member defaults after flood_ensemble_init: the classes' own n, no
+// drainage; drained volume cleared.
+int land_ensemble_init(flood_grid* g)
+{
+    const int M = g->M;
+    int rc;
+    if ((rc = dalloc(g, &g->lc_n, (size_t)M * 4)) || (rc = dalloc(g, &g->lc_drain, M)) ||
+        (rc = dalloc(g, &g->dacc, (size_t)M * g->nslot)))
+        return rc;
+    std::vector<float> n((size_t)M * 4);
+    for (int m = 0; m < M; ++m)
+        for (int q = 0; q < 4; ++q) n[(size_t)m * 4 + q] = g->lc_n0[q];
+    std::vector<float> d(M, 0.0f);
+    FLOOD_CK(g, cudaMemcpy(g->lc_n, n.data(), sizeof(float) * n.size(), cudaMemcpyHostToDevice));
+    FLOOD_CK(g, cudaMemcpy(g->lc_drain, d.data(), sizeof(float) * M, cudaMemcpyHostToDevice));
+    FLOOD_CK(g, cudaMemset(g->dacc, 0, sizeof(double) * M * g->nslot));
+    return FLOOD_OK;
+}
+
+}  // namespace flood
+
+extern "C" int flood_set_land_cover(flood_grid* g, const uint8_t* cls, int n_classes,
+                                    const flood_land_class* classes)
+{
+    if (!g) return flood::fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    if (g->lc_on) return flood::fail(g, FLOOD_ERR_STATE, "land cover is already set");
+    if (!cls || !classes || n_classes < 1 || n_classes > kMaxClasses)
+        return flood::fail(g, FLOOD_ERR_ARG, "need cls, 1..4 classes and their table");
+    for (int q = 0; q < n_classes; ++q) {
+        const flood_land_class& k = classes[q];
+        if (!(k.n > 0.0f) || !(k.runoff >= 0.0f && k.runoff <= 1.0f) ||
+            (k.drains != 0 && k.drains != 1) || (k.outside != 0 && k.outside != 1))
+            return flood::fail(g, FLOOD_ERR_ARG, "class needs n > 0, runoff in [0, 1], flags 0/1");
+    }
+    const size_t cells = (size_t)g->ny * g->nx;
+    std::vector<uint8_t> hc(cells);
+    CK(g, cudaMemcpy(hc.data(), cls, cells, cudaMemcpyDefault));
+    std::vector<float> runoff(kMaxClasses, 1.0f), drains(kMaxClasses, 0.0f), n0(kMaxClasses, 0.05f);
+    for (int q = 0; q < n_classes; ++q) {
+        runoff[q] = classes[q].outside ? 0.0f : classes[q].runoff;
+        drains[q] = classes[q].outside ? 0.0f : (float)classes[q].drains;
+        n0[q] = classes[q].n;
+    }
+    double rain_cells = 0.0;
+    std::vector<uint8_t> pad((size_t)g->ny * g->ld, 0);
+    bool any_outside = false;
+    for (int r = 0; r < g->ny; ++r)
+        for (int c = 0; c < g->nx; ++c) {
+            const uint8_t k = hc[(size_t)r * g->nx + c];
+            if (k >= n_classes) return flood::fail(g, FLOOD_ERR_ARG, "class index out of range");
+            pad[(size_t)r * g->ld + c] = k;
+            rain_cells += runoff[k];
+            any_outside |= classes[k].outside != 0;
+        }
+    // the bed of cells outside the domain moves out of reach
+    if (any_outside) {
+        std::vector<float> z(g->plane);
+        CK(g, cudaMemcpy(z.data(), g->z, sizeof(float) * g->plane, cudaMemcpyDeviceToHost));
+        for (int r = 0; r < g->ny; ++r)
+            for (int c = 0; c < g->nx; ++c)
+                if (classes[hc[(size_t)r * g->nx + c]].outside) z[(size_t)r * g->ld + c] = kWallZ;
+        CK(g, cudaMemcpy(g->z, z.data(), sizeof(float) * g->plane, cudaMemcpyHostToDevice));
+    }
+    int rc = flood::dalloc(g, &g->cls8, pad.size());
+    if (rc) return rc;
+    CK(g, cudaMemcpy(g->cls8, pad.data(), pad.size(), cudaMemcpyHostToDevice));
+    for (int q = 0; q < kMaxClasses; ++q) {
+        g->lc_runoff[q] = runoff[q];
+        g->lc_drains[q] = drains[q];
+        g->lc_n0[q] = n0[q];
+    }
+    g->lc_K = n_classes;
+    g->lc_rain_cells = rain_cells;
+    g->lc_on = true;
+    g->epoch++;
+    if (g->M && (rc = flood::land_ensemble_init(g))) return rc;
+    return FLOOD_OK;
+}
+
+extern "C" int flood_set_land_params(flood_grid* g, const float* n_class, const float* drain_rate)
+{
+    if (!g) return flood::fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    if (!g->lc_on || !g->M) return flood::fail(g, FLOOD_ERR_STATE, "needs land cover and an ensemble");
+    const int M = g->M, K = g->lc_K;
+    CK(g, cudaDeviceSynchronize());
+    if (n_class) {
+        std::vector<float> in((size_t)M * K), n((size_t)M * 4);
+        CK(g, cudaMemcpy(in.data(), n_class, sizeof(float) * in.size(), cudaMemcpyDefault));
+        for (int m = 0; m < M; ++m)
+            for (int q = 0; q < 4; ++q) {
+                const float v = q < K ? in[(size_t)m * K + q] : g->lc_n0[q];
+                if (!(v > 0.0f) || !std::isfinite(v))
+                    return flood::fail(g, FLOOD_ERR_ARG, "class roughness must be positive");
+                n[(size_t)m * 4 + q] = v;
+            }
+        CK(g, cudaMemcpy(g->lc_n, n.data(), sizeof(float) * n.size(), cudaMemcpyHostToDevice));
+    }
+    if (drain_rate) {
+        std::vector<float> d(M);
+        CK(g, cudaMemcpy(d.data(), drain_rate, sizeof(float) * M, cudaMemcpyDefault));
+        for (float v : d)
+            if (!(v >= 0.0f) || !std::isfinite(v))
+                return flood::fail(g, FLOOD_ERR_ARG, "drainage rates must be >= 0");
+        CK(g, cudaMemcpy(g->lc_drain, d.data(), sizeof(float) * M, cudaMemcpyHostToDevice));
+    }
+    g->epoch++;
+    return FLOOD_OK;
+}
+
+extern "C" int flood_get_land_params(flood_grid* g, float* n_class, float* drain_rate)
+{
+    if (!g) return flood::fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    if (!g->lc_on || !g->M) return flood::fail(g, FLOOD_ERR_STATE, "needs land cover and an ensemble");
+    const int M = g->M, K = g->lc_K;
+    CK(g, cudaDeviceSynchronize());
+    if (n_class) {
+        std::vector<float> n((size_t)M * 4), out((size_t)M * K);
+        CK(g, cudaMemcpy(n.data(), g->lc_n, sizeof(float) * n.size(), cudaMemcpyDeviceToHost));
+        for (int m = 0; m < M; ++m)
+            for (int q = 0; q < K; ++q) out[(size_t)m * K + q] = n[(size_t)m * 4 + q];
+        CK(g, cudaMemcpy(n_class, out.data(), sizeof(float) * out.size(), cudaMemcpyDefault));
+    }
+    if (drain_rate) CK(g, cudaMemcpy(drain_rate, g->lc_drain, sizeof(float) * M, cudaMemcpyDefault));
+    return FLOOD_OK;
+}
+
+extern "C" int flood_drained_volume(flood_grid* g, double* drained)
+{
+    if (!g) return flood::fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    if (!g->M) return flood::fail(g, FLOOD_ERR_STATE, "flood_ensemble_init has not been called");
+    if (!drained) return flood::fail(g, FLOOD_ERR_ARG, "drained is NULL");
+    const int M = g->M;
+    if (!g->dacc) {
+        std::fill(drained, drained + M, 0.0);
+        return FLOOD_OK;
+    }
+    CK(g, cudaDeviceSynchronize());
+    std::vector<double> d((size_t)M * g->nslot);
+    CK(g, cudaMemcpy(d.data(), g->dacc, sizeof(double) * d.size(), cudaMemcpyDeviceToHost));
+    for (int m = 0; m < M; ++m) {
+        double acc = 0.0;
+        for (int k = 0; k < g->nslot; ++k) acc += d[(size_t)m * g->nslot + k];
+        drained[m] = acc;
+    }
+    return FLOOD_OK;
+}

@@ -15,6 +15,7 @@ struct MarchOut {
     bool bad;
     float out_s, out_c;   // outflow sum of q over the warp's edge links (Kahan pair)
     float clamp;          // sum of the negative depths reset to zero
+    float drn_s, drn_c;   // drained depth (land cover; Kahan pair)
 };
 
 __device__ __forceinline__ void m_load4(float (&v)[4], const float* p)
@@ -71,12 +72,16 @@ __device__ __forceinline__ void row_links(const float (&hC)[4], const float (&zC
 
 // Continuity (Eq. 5 -> Eq. 1) with rain and the wet/dry clamp for a lane's
 // four cells.  Clamped cells keep a negative zero: the adjoint reads the sign
-// bit to know that branch was taken.
-template <bool INTERIOR>
+// bit to know that branch was taken.  LC (land cover, Section 4.1): the rain
+// that stays depends on the cell's class, and the class's drainage then
+// removes at most the water present.
+template <bool INTERIOR, bool LC = false>
 __device__ __forceinline__ void row_depths(const float (&hC)[4], const float (&qxE)[4],
                                            const float (&qyN)[4], const float (&qyS)[4], float qW0,
                                            int c, int nx, float dt_dx, float dr, float& clamp,
-                                           float& hmax, float& hsum, float (&hN)[4])
+                                           float& hmax, float& hsum, float (&hN)[4],
+                                           uint32_t clsw = 0, const LandK* lk = nullptr,
+                                           float* drn_s = nullptr, float* drn_c = nullptr)
 {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -84,7 +89,15 @@ __device__ __forceinline__ void row_depths(const float (&hC)[4], const float (&q
         if (INTERIOR || c + j < nx) {
             const float qW = (j == 0) ? qW0 : qxE[j - 1];
             const float net = __fadd_rn(__fsub_rn(qW, qxE[j]), __fsub_rn(qyN[j], qyS[j]));
-            hn = __fadd_rn(__fmaf_rn(dt_dx, net, hC[j]), dr);
+            if (LC) {
+                const uint32_t kc = cls_at(clsw, j);
+                hn = __fadd_rn(__fmaf_rn(dt_dx, net, hC[j]), sel4(kc, lk->dr));
+                const float sink = fminf(sel4(kc, lk->dd), fmaxf(hn, 0.0f));
+                hn = __fsub_rn(hn, sink);
+                kahan_add(*drn_s, *drn_c, sink);
+            } else {
+                hn = __fadd_rn(__fmaf_rn(dt_dx, net, hC[j]), dr);
+            }
             if (hn < 0.0f) {
                 clamp = __fsub_rn(clamp, hn);
                 hn = -0.0f;
@@ -96,12 +109,14 @@ __device__ __forceinline__ void row_depths(const float (&hC)[4], const float (&q
     }
 }
 
+template <bool LC = false>
 __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, float* __restrict__ dst,
                                                float* ck, float* hm, const float* __restrict__ z,
                                                const float* __restrict__ n, size_t plane, int ny,
                                                int nx, int ld, int c0, int r0, int r1, int lane,
                                                const FaceK& k, float dt_dx, float s, float dr,
-                                               int east_out, int south_out)
+                                               int east_out, int south_out,
+                                               const LandK* lk = nullptr)
 {
     const float s_half = 0.5f * s;
     const float* __restrict__ sh = src;
@@ -118,17 +133,26 @@ __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, fl
 
     float hC[4] = {0, 0, 0, 0}, zC[4] = {0, 0, 0, 0}, nC[4] = {0, 0, 0, 0};
     float qyN[4] = {0, 0, 0, 0};
+    uint32_t clsC = 0;  // land classes of the lane's four cells in the current row
     if (act) {
         const size_t o = (size_t)r0 * ld + c;
         m_load4(hC, sh + o);
         m_load4(zC, z + o);
-        m_load4(nC, n + o);
+        if (LC) {
+            clsC = cls_word(lk->cls, o);
+            land_n4(nC, clsC, *lk);
+        } else {
+            m_load4(nC, n + o);
+        }
         if (r0 > 0) {
             float hU[4], zU[4], nU[4], qU[4];
             const size_t ou = o - ld;
             m_load4(hU, sh + ou);
             m_load4(zU, z + ou);
-            m_load4(nU, n + ou);
+            if (LC)
+                land_n4(nU, cls_word(lk->cls, ou), *lk);
+            else
+                m_load4(nU, n + ou);
             m_load4(qU, sqy + ou);
 #pragma unroll
             for (int j = 0; j < 4; ++j)
@@ -141,7 +165,7 @@ __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, fl
 
     float hmax = 0.0f;
     bool bad = false;
-    float out_s = 0.0f, out_c = 0.0f, clamp = 0.0f;
+    float out_s = 0.0f, out_c = 0.0f, clamp = 0.0f, drn_s = 0.0f, drn_c = 0.0f;
 
 #pragma unroll 2
     for (int r = r0; r < r1; ++r) {
@@ -149,11 +173,17 @@ __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, fl
         const bool has_s = (r + 1 < ny);
         float hS[4] = {0, 0, 0, 0}, zS[4] = {0, 0, 0, 0}, nS[4] = {0, 0, 0, 0};
         float qxo[4] = {0, 0, 0, 0}, qyo[4] = {0, 0, 0, 0};
+        uint32_t clsS = 0;
         if (act) {
             if (has_s) {
                 m_load4(hS, sh + o + ld);
                 m_load4(zS, z + o + ld);
-                m_load4(nS, n + o + ld);
+                if (LC) {
+                    clsS = cls_word(lk->cls, o + ld);
+                    land_n4(nS, clsS, *lk);
+                } else {
+                    m_load4(nS, n + o + ld);
+                }
             }
             m_load4(qxo, sqx + o);
             m_load4(qyo, sqy + o);
@@ -166,7 +196,7 @@ __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, fl
             const size_t oe = (size_t)r * ld + c + 4;
             hE = __ldg(sh + oe);
             zE = __ldg(z + oe);
-            nE = __ldg(n + oe);
+            nE = LC ? sel4(lk->cls[oe], lk->n) : __ldg(n + oe);
         }
         float qxE[4], qyS[4];
         if (interior)
@@ -181,16 +211,19 @@ __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, fl
             qW0 = 0.0f;
             if (c0 > 0) {  // recompute the neighbouring span's link (halo)
                 const size_t ow = (size_t)r * ld + c0 - 1;
+                const float nw = LC ? sel4(lk->cls[ow], lk->n) : __ldg(n + ow);
                 qW0 = link_q(__ldg(sh + ow), __ldg(z + ow), hC[0], zC[0], __ldg(sqx + ow),
-                             __fmul_rn(s_half, __fadd_rn(__ldg(n + ow), nC[0])), k);
+                             __fmul_rn(s_half, __fadd_rn(nw, nC[0])), k);
             }
         }
         float hN[4];
         float hsum = 0.0f;
         if (interior)
-            row_depths<true>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN);
+            row_depths<true, LC>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN,
+                                 clsC, lk, &drn_s, &drn_c);
         else
-            row_depths<false>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN);
+            row_depths<false, LC>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN,
+                                  clsC, lk, &drn_s, &drn_c);
         bad |= !(hsum <= 3.0e38f);  // a NaN or overflow anywhere in the row
         // links leaving the domain this row: the east edge link (one lane)
         // and, on the last row, the south edge links
@@ -225,6 +258,7 @@ __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, fl
             zC[j] = zS[j];
             nC[j] = nS[j];
         }
+        clsC = clsS;
     }
 
     MarchOut out;
@@ -233,6 +267,8 @@ __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, fl
     out.out_s = out_s;
     out.out_c = out_c;
     out.clamp = clamp;
+    out.drn_s = drn_s;
+    out.drn_c = drn_c;
     return out;
 }
 

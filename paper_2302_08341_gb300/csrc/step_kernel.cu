@@ -62,7 +62,7 @@ __global__ void plan_kernel(const StepArgs a)
 // REPLAY = false: an ordinary step with the plan of this step.  REPLAY =
 // true: recompute a logged step of a checkpointed segment, bit for bit, for
 // the adjoint.
-template <int WM, int WC, bool REPLAY>
+template <int WM, int WC, bool REPLAY, bool LC = false>
 __global__ void __launch_bounds__(32 * WM * WC, FLOOD_STEP_MIN_BLOCKS * 4 / (WM * WC)) step_kernel(const StepArgs a)
 {
     const int lane = threadIdx.x;
@@ -104,27 +104,33 @@ __global__ void __launch_bounds__(32 * WM * WC, FLOOD_STEP_MIN_BLOCKS * 4 / (WM 
     const int r0 = blockIdx.z * a.rows_per_strip;
     const int r1 = min(r0 + a.rows_per_strip, ny);
     float* hm = (!REPLAY && a.hmax_field) ? a.hmax_field + (size_t)m * plane : nullptr;
-    const MarchOut mo = march_rows(src, dst, ck, hm, a.z, a.n, plane, ny, nx, ld, c0, r0, r1, lane, k,
-                                   p.dt_dx, a.scale[m], p.dr, a.east_out, a.south_out);
+    LandK lk;
+    if (LC) lk = land_k(a, m, p.dr, p.dt);
+    const MarchOut mo = march_rows<LC>(src, dst, ck, hm, a.z, a.n, plane, ny, nx, ld, c0, r0, r1,
+                                       lane, k, p.dt_dx, a.scale[m], p.dr, a.east_out, a.south_out,
+                                       &lk);
     if (mo.bad) atomicOr(a.err, 1);
     if (REPLAY) return;
     // warp reductions: max depth (order-free); volume partials widened to
     // FP64 once per warp and reduced in a fixed order
     const unsigned hb = __reduce_max_sync(0xffffffffu, __float_as_uint(mo.hmax) & 0x7fffffffu);
     double out_acc = (double)mo.out_s - (double)mo.out_c, clamp_acc = (double)mo.clamp;
+    double drn_acc = LC ? (double)mo.drn_s - (double)mo.drn_c : 0.0;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         out_acc += __shfl_xor_sync(0xffffffffu, out_acc, off);
         clamp_acc += __shfl_xor_sync(0xffffffffu, clamp_acc, off);
+        if (LC) drn_acc += __shfl_xor_sync(0xffffffffu, drn_acc, off);
     }
     if (lane == 0) {
         atomicMax(&a.ms_out[m].hmax_bits, hb);
+        const int slot = blockIdx.z * ((a.nx + kSpan - 1) / kSpan) + span;
         if (out_acc != 0.0 || clamp_acc != 0.0) {
-            const int slot = blockIdx.z * ((a.nx + kSpan - 1) / kSpan) + span;
             double* v = a.vacc + ((size_t)m * a.nslot + slot) * 2;
             v[0] += out_acc * p.dt * a.dxd;
             v[1] += clamp_acc * a.cell_area;
         }
+        if (LC && drn_acc != 0.0) a.dacc[(size_t)m * a.nslot + slot] += drn_acc * a.cell_area;
     }
 }
 
@@ -147,6 +153,16 @@ void launch_step(const StepArgs& a, int members_per_cta, cudaStream_t s)
 {
     const int spans = (a.nx + kSpan - 1) / kSpan;
     const int strips = (a.ny + a.rows_per_strip - 1) / a.rows_per_strip;
+    if (a.lc_on) {  // land cover: 4 members per CTA, or one member over 4 spans
+        if (members_per_cta >= 4) {
+            dim3 grid((a.M + 3) / 4, spans, strips), block(32, 4);
+            step_kernel<4, 1, false, true><<<grid, block, 0, s>>>(a);
+        } else {
+            dim3 grid(a.M, (spans + 3) / 4, strips), block(32, 4);
+            step_kernel<1, 4, false, true><<<grid, block, 0, s>>>(a);
+        }
+        return;
+    }
     switch (members_per_cta) {
     case 8: {
         dim3 grid((a.M + 7) / 8, spans, strips), block(32, 8);

@@ -12,7 +12,7 @@ namespace {
 
 constexpr int kSpan = kTmaSpan;
 
-template <int WM, bool TRACK_MAX>
+template <int WM, bool TRACK_MAX, bool LC>
 __global__ void __launch_bounds__(32 * WM, 20 / WM) step_tma_kernel(const __grid_constant__ TmaArgs t)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -48,27 +48,33 @@ __global__ void __launch_bounds__(32 * WM, 20 / WM) step_tma_kernel(const __grid
     const int r1 = min(r0 + a.rows_per_strip, a.ny);
     MarchOut mo;
     float* hm = TRACK_MAX ? a.hmax_field + (size_t)m * a.plane : nullptr;
-    if (!tma_march<TRACK_MAX>(&t.state_map, &t.static_map, (pl.cur * a.M + m) * 3, bar0, my_stages, dst, ck, hm,
-                   a.err, a.plane, a.ny, a.nx, a.ld, c0, r0, r1, lane, k, pl.dt_dx, a.scale[m],
-                   pl.dr, a.east_out, a.south_out, mo))
+    LandK lk;
+    if (LC) lk = land_k(a, m, pl.dr, pl.dt);
+    if (!tma_march<TRACK_MAX, LC>(&t.state_map, &t.static_map, (pl.cur * a.M + m) * 3, bar0,
+                                  my_stages, dst, ck, hm, a.err, a.plane, a.ny, a.nx, a.ld, c0, r0,
+                                  r1, lane, k, pl.dt_dx, a.scale[m], pl.dr, a.east_out, a.south_out,
+                                  mo, &lk))
         return;
 
     if (mo.bad) atomicOr(a.err, 1);
     const unsigned hb = __reduce_max_sync(0xffffffffu, __float_as_uint(mo.hmax) & 0x7fffffffu);
     double out_acc = (double)mo.out_s - (double)mo.out_c, clamp_acc = (double)mo.clamp;
+    double drn_acc = LC ? (double)mo.drn_s - (double)mo.drn_c : 0.0;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         out_acc += __shfl_xor_sync(0xffffffffu, out_acc, off);
         clamp_acc += __shfl_xor_sync(0xffffffffu, clamp_acc, off);
+        if (LC) drn_acc += __shfl_xor_sync(0xffffffffu, drn_acc, off);
     }
     if (lane == 0) {
         atomicMax(&a.ms_out[m].hmax_bits, hb);
+        const int slot = blockIdx.z * ((a.nx + kSpan - 1) / kSpan) + span;
         if (out_acc != 0.0 || clamp_acc != 0.0) {
-            const int slot = blockIdx.z * ((a.nx + kSpan - 1) / kSpan) + span;
             double* v = a.vacc + ((size_t)m * a.nslot + slot) * 2;
             v[0] += out_acc * pl.dt * a.dxd;
             v[1] += clamp_acc * a.cell_area;
         }
+        if (LC && drn_acc != 0.0) a.dacc[(size_t)m * a.nslot + slot] += drn_acc * a.cell_area;
     }
 }
 
@@ -107,7 +113,7 @@ int tma_box_cols() { return kTmaBox; }
 
 namespace {
 
-template <bool TRACK_MAX>
+template <bool TRACK_MAX, bool LC>
 void launch_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
 {
     const StepArgs& a = t.a;
@@ -117,16 +123,16 @@ void launch_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
         static bool attr = false;
         const size_t shm = tma_smem_bytes<4>();
         if (!attr) {
-            cudaFuncSetAttribute(step_tma_kernel<4, TRACK_MAX>,
+            cudaFuncSetAttribute(step_tma_kernel<4, TRACK_MAX, LC>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
             attr = true;
         }
         dim3 grid((a.M + 3) / 4, spans, strips), block(32, 4);
-        step_tma_kernel<4, TRACK_MAX><<<grid, block, shm, s>>>(t);
+        step_tma_kernel<4, TRACK_MAX, LC><<<grid, block, shm, s>>>(t);
     } else {
         const size_t shm = tma_smem_bytes<1>();
         dim3 grid(a.M, spans, strips), block(32, 1);
-        step_tma_kernel<1, TRACK_MAX><<<grid, block, shm, s>>>(t);
+        step_tma_kernel<1, TRACK_MAX, LC><<<grid, block, shm, s>>>(t);
     }
 }
 
@@ -134,10 +140,18 @@ void launch_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
 
 int launch_step_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
 {
-    if (t.a.hmax_field)
-        launch_tma<true>(t, members_per_cta, s);
-    else
-        launch_tma<false>(t, members_per_cta, s);
+    const bool track = t.a.hmax_field != nullptr;
+    if (t.a.lc_on) {
+        if (track)
+            launch_tma<true, true>(t, members_per_cta, s);
+        else
+            launch_tma<false, true>(t, members_per_cta, s);
+    } else {
+        if (track)
+            launch_tma<true, false>(t, members_per_cta, s);
+        else
+            launch_tma<false, false>(t, members_per_cta, s);
+    }
     return 0;
 }
 

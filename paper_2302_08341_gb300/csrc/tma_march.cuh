@@ -57,16 +57,19 @@ __device__ __forceinline__ void tma_store4(float* p, const float (&v)[4])
 // state_map: (ld, ny, planes) with the source h, qx, qy at planes
 // [plane0, plane0 + 3); static_map: (ld, ny, 2) with z then n.  Writes the
 // new state to dst (and ck when non-null); TRACK_MAX: also raises the
-// running maximum depth at hm (a separate instantiation, so the plain step
-// carries no trace of it).  Returns false if a wait gave up.
-template <bool TRACK_MAX>
+// running maximum depth at hm; LC: land cover (roughness by class from lk,
+// the class's share of the rain and its drainage).  Each is a separate
+// instantiation, so the plain step carries no trace of them.  Returns false
+// if a wait gave up.
+template <bool TRACK_MAX, bool LC = false>
 __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CUtensorMap* static_map,
                                           int plane0, uint32_t bar0, unsigned char* my_stages,
                                           float* __restrict__ dst, float* ck, float* hm, int* err,
                                           size_t plane,
                                           int ny, int nx, int ld, int c0, int r0, int r1, int lane,
                                           const FaceK& k, float dt_dx, float s, float dr,
-                                          int east_out, int south_out, MarchOut& out)
+                                          int east_out, int south_out, MarchOut& out,
+                                          const LandK* lk = nullptr)
 {
     constexpr int kNS = kTmaNS;
     constexpr int kBox = kTmaBox;
@@ -142,17 +145,30 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
         drain_and_fail();
         return false;
     }
+    // land classes (LC): the current row's, and the next row's loaded one
+    // iteration ahead of its use
+    uint32_t clsC = 0, clsNext = 0;
+    if (LC && act) {
+        clsC = cls_word(lk->cls, (size_t)r0 * ld + c);
+        if (r0 + 1 < ny) clsNext = cls_word(lk->cls, (size_t)(r0 + 1) * ld + c);
+    }
     {
         const float* P = row_ptr(r0);
         tma_lds4(hC, P + x0);
         tma_lds4(zC, P + kZ + x0);
-        tma_lds4(nC, P + kN + x0);
+        if (LC)
+            land_n4(nC, clsC, *lk);
+        else
+            tma_lds4(nC, P + kN + x0);
         if (r0 > 0) {
             const float* U = row_ptr(r0 - 1);
             float hU[4], zU[4], nU[4], qU[4];
             tma_lds4(hU, U + x0);
             tma_lds4(zU, U + kZ + x0);
-            tma_lds4(nU, U + kN + x0);
+            if (LC)
+                land_n4(nU, act ? cls_word(lk->cls, (size_t)(r0 - 1) * ld + c) : 0u, *lk);
+            else
+                tma_lds4(nU, U + kN + x0);
             tma_lds4(qU, U + 2 * kBox + x0);
 #pragma unroll
             for (int j = 0; j < 4; ++j)
@@ -166,7 +182,7 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
 
     float hmax = 0.0f;
     bool bad = false;
-    float out_s = 0.0f, out_c = 0.0f, clamp = 0.0f;
+    float out_s = 0.0f, out_c = 0.0f, clamp = 0.0f, drn_s = 0.0f, drn_c = 0.0f;
 
     for (int r = r0; r < r1; ++r) {
         const size_t o = (size_t)r * ld + c;
@@ -185,14 +201,29 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
         if (TRACK_MAX && act) hmo = *reinterpret_cast<const float4*>(hm + o);
         tma_lds4(qxo, P + kBox + x0);
         tma_lds4(qyo, P + 2 * kBox + x0);
+        uint32_t clsS = 0;
+        if (LC) {
+            clsS = clsNext;
+            if (act && r + 2 < ny) clsNext = cls_word(lk->cls, o + 2 * (size_t)ld);
+        }
         if (has_s) {
             const float* Q = row_ptr(r + 1);
             tma_lds4(hS, Q + x0);
             tma_lds4(zS, Q + kZ + x0);
-            tma_lds4(nS, Q + kN + x0);
+            if (LC)
+                land_n4(nS, clsS, *lk);
+            else
+                tma_lds4(nS, Q + kN + x0);
         }
         // east neighbour of the lane's last cell, straight from the tile
-        const float hE = P[x0 + 4], zE = P[kZ + x0 + 4], nE = P[kN + x0 + 4];
+        const float hE = P[x0 + 4], zE = P[kZ + x0 + 4];
+        float nE;
+        if (LC) {
+            nE = __shfl_down_sync(0xffffffffu, nC[0], 1);
+            if (lane == 31 && c + 4 < nx) nE = sel4(lk->cls[o + 4], lk->n);
+        } else {
+            nE = P[kN + x0 + 4];
+        }
         float qxE[4], qyS[4];
         if (interior)
             row_links<true>(hC, zC, nC, hS, zS, nS, qxo, qyo, hE, zE, nE, has_s, c, nx, s, s_half, k,
@@ -203,16 +234,20 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
         float qW0 = __shfl_up_sync(0xffffffffu, qxE[3], 1);
         if (lane == 0) {
             qW0 = 0.0f;
-            if (c0 > 0)  // the neighbouring span's last link, from the tile's halo
+            if (c0 > 0) {  // the neighbouring span's last link, from the tile's halo
+                const float nW = LC ? sel4(lk->cls[o - 1], lk->n) : P[kN + 3];
                 qW0 = link_q(P[3], P[kZ + 3], hC[0], zC[0], P[kBox + 3],
-                             __fmul_rn(s_half, __fadd_rn(P[kN + 3], nC[0])), k);
+                             __fmul_rn(s_half, __fadd_rn(nW, nC[0])), k);
+            }
         }
         float hN[4];
         float hsum = 0.0f;
         if (interior)
-            row_depths<true>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN);
+            row_depths<true, LC>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN,
+                                 clsC, lk, &drn_s, &drn_c);
         else
-            row_depths<false>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN);
+            row_depths<false, LC>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN,
+                                  clsC, lk, &drn_s, &drn_c);
         bad |= !(hsum <= 3.0e38f);
         float ev = 0.0f;
 #pragma unroll
@@ -242,6 +277,7 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
             zC[j] = zS[j];
             nC[j] = nS[j];
         }
+        clsC = clsS;
         release(r);
     }
 
@@ -250,6 +286,8 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
     out.out_s = out_s;
     out.out_c = out_c;
     out.clamp = clamp;
+    out.drn_s = drn_s;
+    out.drn_c = drn_c;
     return true;
 }
 

@@ -211,3 +211,51 @@ def uneven_batch(n: int = 64, side=(512, 2048), rain=(20.0, 100.0),
                             rain_mm_h=float(rng.uniform(*rain)),
                             duration_s=float(rng.uniform(*duration))))
     return out
+
+
+# ---- land cover (Section 4.1, Table 1) -------------------------------------
+# classes: 0 green land, 1 water bodies, 2 hardened ground, 3 outside the domain
+LAND_CLASSES = [
+    # (Manning n of the deterministic model (Table 1), runoff coefficient,
+    #  drainage applies, outside the domain)
+    (0.15, 0.9, 0, 0),    # green land: 10 % of the rain infiltrates
+    (0.020, 1.0, 0, 0),   # water bodies: no infiltration
+    (0.017, 1.0, 1, 0),   # hardened ground: the pipe network drains I_drn
+    (0.05, 0.0, 0, 1),    # outside the domain
+]
+N_RANGES = [(0.08, 0.22), (0.016, 0.030), (0.010, 0.022), (0.05, 0.05)]  # Table 1 ensemble
+I_DRN_MM_H = 12.0
+
+
+def land_cover(terrain: Terrain, seed: int, n_ponds: int = 6, pond_side=(8, 30),
+               corner_frac: float = 0.25) -> np.ndarray:
+    """Class per cell (uint8): roads and buildings are hardened ground, a few
+    rectangular ponds are water bodies, the rest green land; two quarter
+    discs of radius ``corner_frac`` x min(ny, nx) at the western (upstream)
+    corners lie outside the domain, so the domain is irregular and its
+    outflow edge stays open."""
+    rng = np.random.default_rng(seed)
+    ny, nx = terrain.z.shape
+    cls = np.zeros((ny, nx), np.uint8)
+    cls[terrain.road | terrain.building] = 2
+    for _ in range(n_ponds):
+        h = int(rng.integers(pond_side[0], pond_side[1] + 1)); w = int(rng.integers(pond_side[0], pond_side[1] + 1))
+        h = min(h, ny); w = min(w, nx)
+        r0 = int(rng.integers(0, ny - h + 1)); c0 = int(rng.integers(0, nx - w + 1))
+        blk = cls[r0:r0 + h, c0:c0 + w]
+        blk[blk == 0] = 1
+    rad = corner_frac * min(ny, nx)
+    rr, cc = np.mgrid[0:ny, 0:nx]
+    out = ((rr ** 2 + cc ** 2) < rad ** 2) | (((ny - 1 - rr) ** 2 + cc ** 2) < rad ** 2)
+    cls[out] = 3
+    return cls
+
+
+def land_prior(seed: int, n_members: int, drain_spread: float = 0.5):
+    """Per-member land-cover parameters: Manning n of every class uniform
+    over Table 1's ensemble range, and the drainage rate I_drn = 12 mm/h
+    times U[1 - spread, 1 + spread] (m/s).  Returns ([M, 4], [M]) float32."""
+    rng = np.random.default_rng(seed + 777)
+    n = np.stack([rng.uniform(lo, hi, n_members) for lo, hi in N_RANGES], axis=1)
+    d = I_DRN_MM_H * MM_PER_H * rng.uniform(1.0 - drain_spread, 1.0 + drain_spread, n_members)
+    return n.astype(np.float32), d.astype(np.float32)

@@ -1,0 +1,186 @@
+"""GPU land cover (Section 4.1, Table 1): per-class roughness and runoff
+coefficient, drainage on hardened ground, cells outside the domain, with
+the per-member class roughness and drainage rate as the ensemble's
+uncertain inputs; against the FP64 oracle, bit for bit across engines and
+launch shapes, through a resampling, and at the full 2000 x 2000 x 96 size
+on sampled patches."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2302_08341_gb300 import synth
+from tests.gpu_util import compare, oracle_member_from_gpu, oracle_params, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+WALL_Z = np.float32(1.0e6)
+
+
+@pytest.fixture(scope="module")
+def capi():
+    return require_gpu()
+
+
+def _oracle_fields(terr, cls, n_m, drain_m):
+    """The fields the oracle needs for one member, from the same FP32 inputs
+    the device uses."""
+    tab = synth.LAND_CLASSES
+    outside = np.array([c[3] for c in tab], bool)
+    runoff = np.where(outside, 0.0, np.array([c[1] for c in tab], np.float32)).astype(np.float64)
+    drains = np.where(outside, 0, np.array([c[2] for c in tab])).astype(np.float64)
+    z = np.where(outside[cls], WALL_Z, terr.z).astype(np.float32)
+    n = np.asarray(n_m, np.float32)[cls].astype(np.float64)
+    rc = runoff[cls]
+    dr = float(np.float32(drain_m)) * drains[cls]
+    return z, n, np.ascontiguousarray(rc), np.ascontiguousarray(dr), outside[cls]
+
+
+def _run(capi, terr, cls, hy, rm, sc, n_m, d_m, t_end, engine=None, shape=None, params=None):
+    M = len(rm)
+    with capi.Grid(terr.z, terr.n, params) as g:
+        g.set_land_cover(cls, synth.LAND_CLASSES)
+        g.ensemble_init(M, rm, sc, hy)
+        g.set_land_params(n_m, d_m)
+        if engine is not None:
+            g.set_engine(engine)
+        if shape is not None:
+            g.set_launch(*shape)
+        g.advance_to(t_end)
+        g.sync()
+        states = [g.get_state(m) for m in range(M)]
+        return states, g.members(), g.volumes(), g.drained()
+
+
+def test_land_cover_follows_the_oracle(capi):
+    ny, nx, M = 64, 100, 3
+    terr = synth.make_terrain(ny, nx, seed=61)
+    cls = synth.land_cover(terr, seed=61, pond_side=(6, 14))
+    assert set(np.unique(cls)) == {0, 1, 2, 3}
+    hy = synth.hyetograph_constant(100.0, 600.0)
+    rm, sc = synth.ensemble_prior(61, M)
+    n_m, d_m = synth.land_prior(61, M)
+    p = capi.Params.default()
+    states, mem, vol, drained = _run(capi, terr, cls, hy, rm, sc, n_m, d_m, 600.0, params=p)
+    for m in range(M):
+        z, n, rc, dr, out = _oracle_fields(terr, cls, n_m[m], d_m[m])
+        op = oracle_params(p, ny, nx)
+        op.rc, op.drain = rc, dr
+        mo = oracle.Member.dry(ny, nx)
+        oracle.advance(op, z, n, float(sc[m]), float(rm[m]), hy, mo, t_end=600.0)
+        h = states[m][0]
+        compare(h, mo.h, 1e-3)
+        assert np.all(h[out] == 0.0) and np.all(mo.h[out] == 0.0)
+        assert mo.drained > 0
+        assert abs(drained[m] - mo.drained) <= 1e-3 * mo.drained
+        assert abs(vol["rain"][m] - mo.rain) <= 1e-6 * mo.rain
+        V = vol["storage"][m]
+        assert abs(V - oracle.storage(mo.h, p.dx)) <= 1e-5 * oracle.storage(mo.h, p.dx)
+        bal = V - (vol["rain"][m] - vol["outflow"][m] + vol["clamp"][m] - drained[m])
+        assert abs(bal) <= 1e-5 * vol["rain"][m]
+
+
+@pytest.mark.parametrize("case", [(0, (16, 4)), (0, (7, 1)), (1, (0, 0)), (1, (5, 1)), (1, (64, 4))])
+def test_land_cover_engines_and_shapes_bitwise(capi, case):
+    ny, nx, M = 45, 150, 5
+    terr = synth.make_terrain(ny, nx, seed=62)
+    cls = synth.land_cover(terr, seed=62, pond_side=(5, 12))
+    hy = synth.hyetograph_constant(120.0, 300.0)
+    rm, sc = synth.ensemble_prior(62, M)
+    n_m, d_m = synth.land_prior(62, M)
+    ref = _run(capi, terr, cls, hy, rm, sc, n_m, d_m, 240.0, engine=1)
+    got = _run(capi, terr, cls, hy, rm, sc, n_m, d_m, 240.0, engine=case[0], shape=case[1])
+    for m in range(M):
+        for k in range(3):
+            assert np.array_equal(got[0][m][k], ref[0][m][k])
+    assert np.array_equal(got[1]["steps"], ref[1]["steps"])
+    assert np.allclose(got[3], ref[3], rtol=1e-8, atol=0)
+
+
+def test_resampling_carries_land_parameters(capi):
+    ny, nx, M = 32, 48, 6
+    terr = synth.make_terrain(ny, nx, seed=63)
+    cls = synth.land_cover(terr, seed=63, pond_side=(4, 8))
+    hy = synth.hyetograph_constant(80.0, 300.0)
+    rm, sc = synth.ensemble_prior(63, M)
+    n_m, d_m = synth.land_prior(63, M)
+    with capi.Grid(terr.z, terr.n) as g:
+        g.set_land_cover(cls, synth.LAND_CLASSES)
+        g.ensemble_init(M, rm, sc, hy)
+        g.set_land_params(n_m, d_m)
+        g.advance_to(120.0)
+        y = g.gauge_sample(np.array([5 * nx + 30, 20 * nx + 40], np.int32))
+        u, beta = synth.pf_draws(63, 1, M)
+        # a sharp observation of member 2: the resampling duplicates it
+        pf = g.pf_assimilate(y[2].astype(np.float64), 0.001, u, beta, force=True)
+        n2, d2 = g.land_params()
+    src = oracle.assign_slots(pf["idx"])
+    assert len(set(src.tolist())) < M
+    assert np.array_equal(n2, n_m[src]) and np.array_equal(d2, d_m[src])
+
+
+def test_land_cover_refusals(capi):
+    terr = synth.make_terrain(24, 30, seed=64)
+    cls = synth.land_cover(terr, seed=64, pond_side=(3, 5))
+    hy = synth.hyetograph_constant(50.0, 300.0)
+    with capi.Grid(terr.z, terr.n) as g:
+        bad = cls.copy(); bad[0, 0] = 7
+        with pytest.raises(capi.FloodError):
+            g.set_land_cover(bad, synth.LAND_CLASSES)
+        g.set_land_cover(cls, synth.LAND_CLASSES)
+        with pytest.raises(capi.FloodError):
+            g.set_land_cover(cls, synth.LAND_CLASSES)
+        g.ensemble_init(2, np.ones(2, np.float32), np.ones(2, np.float32), hy)
+        with pytest.raises(capi.FloodError):
+            g.set_land_params(drain_rate=np.array([-1.0, 0.0], np.float32))
+        with pytest.raises(capi.FloodError):   # the adjoint does not cover land cover
+            g.adjoint(np.array([40], np.int32), np.zeros((1, 1)), 30.0)
+
+
+def test_full_size_land_cover_window(capi):
+    """2000 x 2000 cells, 96 members with their own class roughness and
+    drainage, one 300 s window of the triangular storm in the benchmark's
+    launch configuration: the volume balance of every member, the outside
+    cells dry, and one further step against the oracle on sampled patches of
+    three members."""
+    ny = nx = 2000
+    M = 96
+    terr = synth.make_terrain(ny, nx, seed=1)
+    cls = synth.land_cover(terr, seed=1)
+    hy = synth.hyetograph_triangular(60.0, 1200.0, 3600.0)
+    rm, sc = synth.ensemble_prior(1, M)
+    n_m, d_m = synth.land_prior(1, M)
+    p = capi.Params.default()
+    sample = [0, 47, 95]
+    with capi.Grid(terr.z, terr.n, p) as g:
+        g.set_land_cover(cls, synth.LAND_CLASSES)
+        g.ensemble_init(M, rm, sc, hy)
+        g.set_land_params(n_m, d_m)
+        g.advance_to(300.0)
+        g.sync()
+        vol = g.volumes()
+        drained = g.drained()
+        bal = vol["storage"] - (vol["rain"] - vol["outflow"] + vol["clamp"] - drained)
+        assert np.all(np.abs(bal) <= 1e-5 * vol["rain"])
+        assert np.all(drained > 0)
+        mem0 = g.members()
+        before = {m: g.get_state(m) for m in sample}
+        g.step(1)
+        mem1 = g.members()
+        after = {m: g.get_state(m) for m in sample}
+    rng = np.random.default_rng(2)
+    for m in sample:
+        dt = mem1["t"][m] - mem0["t"][m]
+        h, qx, qy = before[m]
+        z, n, rc, dr, out = _oracle_fields(terr, cls, n_m[m], d_m[m])
+        assert np.all(h[out] == 0.0) and h.min() >= 0.0
+        for (rc0, cc0) in [tuple(rng.integers(40, 1960, 2)) for _ in range(2)]:
+            r0, r1, c0, c1 = rc0 - 33, rc0 + 33, cc0 - 33, cc0 + 33
+            sub = oracle_params(p, r1 - r0, c1 - c0)
+            sub.east_outflow = 0
+            sub.rc = np.ascontiguousarray(rc[r0:r1, c0:c1])
+            sub.drain = np.ascontiguousarray(dr[r0:r1, c0:c1])
+            mo = oracle_member_from_gpu(h[r0:r1, c0:c1], qx[r0:r1, c0:c1], qy[r0:r1, c0:c1])
+            rate = float(hy[1]) if mem0["t"][m] >= 300.0 else float(hy[0])
+            oracle.step(sub, z[r0:r1, c0:c1], n[r0:r1, c0:c1], float(sc[m]), rate * float(rm[m]),
+                        dt, mo)
+            compare(after[m][0][r0:r1, c0:c1][1:-1, 1:-1], mo.h[1:-1, 1:-1], 2e-5)
