@@ -255,16 +255,17 @@ __device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpre
 // Land cover of one member for one step (Section 4.1): per class, the
 // Manning n, the rain depth that stays on the surface and the drainage
 // depth.  Classes are 0..3, four to a 32-bit word (one lane's four cells).
+// The four-entry tables live in lanes 0..3 (lane q holds class q & 3's
+// entries) and are read by shuffle, so every lane of the warp must take
+// part in each lookup.
 struct LandK {
     const uint8_t* cls;  // [ny][ld]
-    float n[4];
-    float dr[4];
-    float dd[4];
+    float n, dr, dd;     // this lane's entries: class (lane & 3)
 };
 
-__device__ __forceinline__ float sel4(uint32_t k, const float (&t)[4])
+__device__ __forceinline__ float land_get(float v, uint32_t k)
 {
-    return k == 0 ? t[0] : (k == 1 ? t[1] : (k == 2 ? t[2] : t[3]));
+    return __shfl_sync(0xffffffffu, v, (int)k);
 }
 
 __device__ __forceinline__ uint32_t cls_word(const uint8_t* cls, size_t o)
@@ -277,23 +278,30 @@ __device__ __forceinline__ uint32_t cls_at(uint32_t w, int j) { return (w >> (8 
 __device__ __forceinline__ void land_n4(float (&nv)[4], uint32_t w, const LandK& lk)
 {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) nv[j] = sel4(cls_at(w, j), lk.n);
+    for (int j = 0; j < 4; ++j) nv[j] = land_get(lk.n, cls_at(w, j));
 }
 
-// This member's land-cover constants for a step: dr = its rain depth, dt
-// the step length.
-__device__ __forceinline__ LandK land_k(const StepArgs& a, int m, float dr, double dt)
+// The rain and drainage depths of a lane's four cells (whole warp).
+__device__ __forceinline__ void land_src4(float (&drv)[4], float (&ddv)[4], uint32_t w,
+                                          const LandK& lk)
+{
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        drv[j] = land_get(lk.dr, cls_at(w, j));
+        ddv[j] = land_get(lk.dd, cls_at(w, j));
+    }
+}
+
+// This member's land-cover tables for a step: dr = its rain depth, dt the
+// step length.
+__device__ __forceinline__ LandK land_k(const StepArgs& a, int m, float dr, double dt, int lane)
 {
     LandK lk;
     lk.cls = a.cls;
-    const float dtf = (float)dt;
-    const float drain = a.lc_drain[m];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        lk.n[q] = a.lc_n[(size_t)m * 4 + q];
-        lk.dr[q] = __fmul_rn(dr, a.lc_runoff[q]);
-        lk.dd[q] = __fmul_rn(__fmul_rn(drain, a.lc_drains[q]), dtf);
-    }
+    const int q = lane & 3;
+    lk.n = a.lc_n[(size_t)m * 4 + q];
+    lk.dr = __fmul_rn(dr, a.lc_runoff[q]);
+    lk.dd = __fmul_rn(__fmul_rn(a.lc_drain[m], a.lc_drains[q]), (float)dt);
     return lk;
 }
 

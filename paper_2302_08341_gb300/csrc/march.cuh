@@ -80,7 +80,7 @@ __device__ __forceinline__ void row_depths(const float (&hC)[4], const float (&q
                                            const float (&qyN)[4], const float (&qyS)[4], float qW0,
                                            int c, int nx, float dt_dx, float dr, float& clamp,
                                            float& hmax, float& hsum, float (&hN)[4],
-                                           uint32_t clsw = 0, const LandK* lk = nullptr,
+                                           const float* drv = nullptr, const float* ddv = nullptr,
                                            float* drn_s = nullptr, float* drn_c = nullptr)
 {
 #pragma unroll
@@ -90,9 +90,8 @@ __device__ __forceinline__ void row_depths(const float (&hC)[4], const float (&q
             const float qW = (j == 0) ? qW0 : qxE[j - 1];
             const float net = __fadd_rn(__fsub_rn(qW, qxE[j]), __fsub_rn(qyN[j], qyS[j]));
             if (LC) {
-                const uint32_t kc = cls_at(clsw, j);
-                hn = __fadd_rn(__fmaf_rn(dt_dx, net, hC[j]), sel4(kc, lk->dr));
-                const float sink = fminf(sel4(kc, lk->dd), fmaxf(hn, 0.0f));
+                hn = __fadd_rn(__fmaf_rn(dt_dx, net, hC[j]), drv[j]);
+                const float sink = fminf(ddv[j], fmaxf(hn, 0.0f));
                 hn = __fsub_rn(hn, sink);
                 kahan_add(*drn_s, *drn_c, sink);
             } else {
@@ -134,25 +133,41 @@ __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, fl
     float hC[4] = {0, 0, 0, 0}, zC[4] = {0, 0, 0, 0}, nC[4] = {0, 0, 0, 0};
     float qyN[4] = {0, 0, 0, 0};
     uint32_t clsC = 0;  // land classes of the lane's four cells in the current row
+    // classes of the cells just east and west of the span (current row, and
+    // the next row's loaded one iteration ahead)
+    uint32_t eC = 0, wC = 0, eN = 0, wN = 0;
+    if (LC) {
+        if (c0 + 128 < nx) eC = lk->cls[(size_t)r0 * ld + c0 + 128];
+        if (c0 > 0) wC = lk->cls[(size_t)r0 * ld + c0 - 1];
+    }
+    // land classes (LC): looked up by the whole warp (shuffles), outside
+    // any lane-dependent branch
+    uint32_t clsU = 0;
+    if (LC) {
+        if (act) {
+            clsC = cls_word(lk->cls, (size_t)r0 * ld + c);
+            if (r0 > 0) clsU = cls_word(lk->cls, (size_t)(r0 - 1) * ld + c);
+        }
+        land_n4(nC, clsC, *lk);
+    }
+    float nUl[4] = {0, 0, 0, 0};
+    if (LC && r0 > 0) land_n4(nUl, clsU, *lk);
     if (act) {
         const size_t o = (size_t)r0 * ld + c;
         m_load4(hC, sh + o);
         m_load4(zC, z + o);
-        if (LC) {
-            clsC = cls_word(lk->cls, o);
-            land_n4(nC, clsC, *lk);
-        } else {
-            m_load4(nC, n + o);
-        }
+        if (!LC) m_load4(nC, n + o);
         if (r0 > 0) {
             float hU[4], zU[4], nU[4], qU[4];
             const size_t ou = o - ld;
             m_load4(hU, sh + ou);
             m_load4(zU, z + ou);
-            if (LC)
-                land_n4(nU, cls_word(lk->cls, ou), *lk);
-            else
+            if (LC) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) nU[j] = nUl[j];
+            } else {
                 m_load4(nU, n + ou);
+            }
             m_load4(qU, sqy + ou);
 #pragma unroll
             for (int j = 0; j < 4; ++j)
@@ -174,19 +189,29 @@ __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, fl
         float hS[4] = {0, 0, 0, 0}, zS[4] = {0, 0, 0, 0}, nS[4] = {0, 0, 0, 0};
         float qxo[4] = {0, 0, 0, 0}, qyo[4] = {0, 0, 0, 0};
         uint32_t clsS = 0;
+        if (LC && has_s) {
+            const size_t rs = (size_t)(r + 1) * ld;
+            if (c0 + 128 < nx) eN = lk->cls[rs + c0 + 128];
+            if (c0 > 0) wN = lk->cls[rs + c0 - 1];
+        }
         if (act) {
             if (has_s) {
                 m_load4(hS, sh + o + ld);
                 m_load4(zS, z + o + ld);
-                if (LC) {
+                if (LC)
                     clsS = cls_word(lk->cls, o + ld);
-                    land_n4(nS, clsS, *lk);
-                } else {
+                else
                     m_load4(nS, n + o + ld);
-                }
             }
             m_load4(qxo, sqx + o);
             m_load4(qyo, sqy + o);
+        }
+        float nEl = 0.0f, nWl = 0.0f, drv[4], ddv[4];
+        if (LC) {
+            if (has_s) land_n4(nS, clsS, *lk);
+            nEl = land_get(lk->n, eC);
+            nWl = land_get(lk->n, wC);
+            land_src4(drv, ddv, clsC, *lk);
         }
         // east neighbour of the lane's last cell: next lane's first cell
         float hE = __shfl_down_sync(0xffffffffu, hC[0], 1);
@@ -196,7 +221,7 @@ __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, fl
             const size_t oe = (size_t)r * ld + c + 4;
             hE = __ldg(sh + oe);
             zE = __ldg(z + oe);
-            nE = LC ? sel4(lk->cls[oe], lk->n) : __ldg(n + oe);
+            nE = LC ? nEl : __ldg(n + oe);
         }
         float qxE[4], qyS[4];
         if (interior)
@@ -211,7 +236,7 @@ __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, fl
             qW0 = 0.0f;
             if (c0 > 0) {  // recompute the neighbouring span's link (halo)
                 const size_t ow = (size_t)r * ld + c0 - 1;
-                const float nw = LC ? sel4(lk->cls[ow], lk->n) : __ldg(n + ow);
+                const float nw = LC ? nWl : __ldg(n + ow);
                 qW0 = link_q(__ldg(sh + ow), __ldg(z + ow), hC[0], zC[0], __ldg(sqx + ow),
                              __fmul_rn(s_half, __fadd_rn(nw, nC[0])), k);
             }
@@ -220,10 +245,10 @@ __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, fl
         float hsum = 0.0f;
         if (interior)
             row_depths<true, LC>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN,
-                                 clsC, lk, &drn_s, &drn_c);
+                                 drv, ddv, &drn_s, &drn_c);
         else
             row_depths<false, LC>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN,
-                                  clsC, lk, &drn_s, &drn_c);
+                                  drv, ddv, &drn_s, &drn_c);
         bad |= !(hsum <= 3.0e38f);  // a NaN or overflow anywhere in the row
         // links leaving the domain this row: the east edge link (one lane)
         // and, on the last row, the south edge links
@@ -259,6 +284,8 @@ __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, fl
             nC[j] = nS[j];
         }
         clsC = clsS;
+        eC = eN;
+        wC = wN;
     }
 
     MarchOut out;

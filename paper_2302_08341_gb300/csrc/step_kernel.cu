@@ -63,7 +63,8 @@ __global__ void plan_kernel(const StepArgs a)
 // true: recompute a logged step of a checkpointed segment, bit for bit, for
 // the adjoint.
 template <int WM, int WC, bool REPLAY, bool LC = false>
-__global__ void __launch_bounds__(32 * WM * WC, FLOOD_STEP_MIN_BLOCKS * 4 / (WM * WC)) step_kernel(const StepArgs a)
+__global__ void __launch_bounds__(32 * WM * WC, (LC ? 4 : FLOOD_STEP_MIN_BLOCKS) * 4 / (WM * WC))
+    step_kernel(const StepArgs a)
 {
     const int lane = threadIdx.x;
     const int wm = threadIdx.y % WM;
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(32 * WM * WC, FLOOD_STEP_MIN_BLOCKS * 4 / (WM 
     const int r1 = min(r0 + a.rows_per_strip, ny);
     float* hm = (!REPLAY && a.hmax_field) ? a.hmax_field + (size_t)m * plane : nullptr;
     LandK lk;
-    if (LC) lk = land_k(a, m, p.dr, p.dt);
+    if (LC) lk = land_k(a, m, p.dr, p.dt, lane);
     const MarchOut mo = march_rows<LC>(src, dst, ck, hm, a.z, a.n, plane, ny, nx, ld, c0, r0, r1,
                                        lane, k, p.dt_dx, a.scale[m], p.dr, a.east_out, a.south_out,
                                        &lk);

@@ -12,8 +12,10 @@ namespace {
 
 constexpr int kSpan = kTmaSpan;
 
+// The land-cover form holds its class tables in registers: it gets more of
+// them (four CTAs of four warps per SM instead of five) rather than spill.
 template <int WM, bool TRACK_MAX, bool LC>
-__global__ void __launch_bounds__(32 * WM, 20 / WM) step_tma_kernel(const __grid_constant__ TmaArgs t)
+__global__ void __launch_bounds__(32 * WM, (LC ? 16 : 20) / WM) step_tma_kernel(const __grid_constant__ TmaArgs t)
 {
     extern __shared__ unsigned char smem_raw[];
     const StepArgs& a = t.a;
@@ -49,7 +51,7 @@ __global__ void __launch_bounds__(32 * WM, 20 / WM) step_tma_kernel(const __grid
     MarchOut mo;
     float* hm = TRACK_MAX ? a.hmax_field + (size_t)m * a.plane : nullptr;
     LandK lk;
-    if (LC) lk = land_k(a, m, pl.dr, pl.dt);
+    if (LC) lk = land_k(a, m, pl.dr, pl.dt, lane);
     if (!tma_march<TRACK_MAX, LC>(&t.state_map, &t.static_map, (pl.cur * a.M + m) * 3, bar0,
                                   my_stages, dst, ck, hm, a.err, a.plane, a.ny, a.nx, a.ld, c0, r0,
                                   r1, lane, k, pl.dt_dx, a.scale[m], pl.dr, a.east_out, a.south_out,

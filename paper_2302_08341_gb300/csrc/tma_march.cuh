@@ -146,11 +146,17 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
         return false;
     }
     // land classes (LC): the current row's, and the next row's loaded one
-    // iteration ahead of its use
-    uint32_t clsC = 0, clsNext = 0;
-    if (LC && act) {
-        clsC = cls_word(lk->cls, (size_t)r0 * ld + c);
-        if (r0 + 1 < ny) clsNext = cls_word(lk->cls, (size_t)(r0 + 1) * ld + c);
+    // iteration ahead of its use; likewise the classes of the cells just
+    // east and west of the span (every lane loads the same two bytes)
+    uint32_t clsC = 0, clsNext = 0, eC = 0, wC = 0, eN = 0, wN = 0;
+    const bool has_e = c0 + kTmaSpan < nx, has_w = c0 > 0;
+    if (LC) {
+        if (act) {
+            clsC = cls_word(lk->cls, (size_t)r0 * ld + c);
+            if (r0 + 1 < ny) clsNext = cls_word(lk->cls, (size_t)(r0 + 1) * ld + c);
+        }
+        if (has_e) eC = lk->cls[(size_t)r0 * ld + c0 + kTmaSpan];
+        if (has_w) wC = lk->cls[(size_t)r0 * ld + c0 - 1];
     }
     {
         const float* P = row_ptr(r0);
@@ -165,7 +171,7 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
             float hU[4], zU[4], nU[4], qU[4];
             tma_lds4(hU, U + x0);
             tma_lds4(zU, U + kZ + x0);
-            if (LC)
+            if (LC)  // whole warp: the lookups are shuffles
                 land_n4(nU, act ? cls_word(lk->cls, (size_t)(r0 - 1) * ld + c) : 0u, *lk);
             else
                 tma_lds4(nU, U + kN + x0);
@@ -205,6 +211,11 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
         if (LC) {
             clsS = clsNext;
             if (act && r + 2 < ny) clsNext = cls_word(lk->cls, o + 2 * (size_t)ld);
+            if (has_s) {
+                const size_t rs = (size_t)(r + 1) * ld;
+                if (has_e) eN = lk->cls[rs + c0 + kTmaSpan];
+                if (has_w) wN = lk->cls[rs + c0 - 1];
+            }
         }
         if (has_s) {
             const float* Q = row_ptr(r + 1);
@@ -218,9 +229,13 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
         // east neighbour of the lane's last cell, straight from the tile
         const float hE = P[x0 + 4], zE = P[kZ + x0 + 4];
         float nE;
+        float nWl = 0.0f, drv[4], ddv[4];
         if (LC) {
             nE = __shfl_down_sync(0xffffffffu, nC[0], 1);
-            if (lane == 31 && c + 4 < nx) nE = sel4(lk->cls[o + 4], lk->n);
+            const float nEl = land_get(lk->n, eC);
+            if (lane == 31) nE = nEl;  // unused past the grid's east edge
+            nWl = land_get(lk->n, wC);
+            land_src4(drv, ddv, clsC, *lk);
         } else {
             nE = P[kN + x0 + 4];
         }
@@ -235,7 +250,7 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
         if (lane == 0) {
             qW0 = 0.0f;
             if (c0 > 0) {  // the neighbouring span's last link, from the tile's halo
-                const float nW = LC ? sel4(lk->cls[o - 1], lk->n) : P[kN + 3];
+                const float nW = LC ? nWl : P[kN + 3];
                 qW0 = link_q(P[3], P[kZ + 3], hC[0], zC[0], P[kBox + 3],
                              __fmul_rn(s_half, __fadd_rn(nW, nC[0])), k);
             }
@@ -244,10 +259,10 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
         float hsum = 0.0f;
         if (interior)
             row_depths<true, LC>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN,
-                                 clsC, lk, &drn_s, &drn_c);
+                                 drv, ddv, &drn_s, &drn_c);
         else
             row_depths<false, LC>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN,
-                                  clsC, lk, &drn_s, &drn_c);
+                                  drv, ddv, &drn_s, &drn_c);
         bad |= !(hsum <= 3.0e38f);
         float ev = 0.0f;
 #pragma unroll
@@ -278,6 +293,8 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
             nC[j] = nS[j];
         }
         clsC = clsS;
+        eC = eN;
+        wC = wN;
         release(r);
     }
 
