@@ -373,3 +373,18 @@ def loss_and_grad(p: Params, z, n, scale, rain_mult, hyeto, h0, sample_dt, d, ce
                                    C.byref(nst))
     return dict(loss=loss, grad_n=gn, grad_h0=gh, grad_rain=gr.value, grad_scale=gs.value,
                 steps=nst.value)
+
+
+def section_flow(m: Member, dx: float, axis: int, fixed: int, start: int, end: int) -> float:
+    """Discharge (m^3/s) through a straight section of links, positive toward
+    increasing index: axis 0 sums the links east of cells (r, fixed) for r in
+    [start, end); axis 1 the links south of cells (fixed, c) for c in
+    [start, end).  Q = sum of q * dx (the link discharges of Eq. 5)."""
+    if axis == 0:
+        q = m.qx[start:end, fixed + 1]      # oracle link c lies between cells c-1 and c
+    else:
+        q = m.qy[fixed + 1, start:end]
+    acc = 0.0
+    for v in q:
+        acc += float(v) * dx
+    return acc
