@@ -215,6 +215,26 @@ int flood_adjoint(flood_grid* g, const flood_loss_spec* loss, int ckpt_every, fl
  * (with checkpointing) and of its reverse pass (replay included). */
 int flood_adjoint_timing(const flood_grid* g, double* forward_ms, double* reverse_ms);
 
+/* ==== Streamflow gauges (the stream gauges of Section 4.1 / 4.4) ============
+ * A section is a straight line of links: axis 0, the links east of cells
+ * (r, fixed) for rows r in [start, end); axis 1, the links south of cells
+ * (fixed, c) for columns c in [start, end).  Its discharge is
+ * Q = sum of q dx over those links (m^3/s, positive toward increasing index);
+ * fixed = nx - 1 (axis 0) or ny - 1 (axis 1) gives the outflow through an
+ * edge.  Observed with a relative error (Section 4.4: sigma = 0.05 d), these
+ * feed pf_assimilate as caller-supplied outputs y. */
+typedef struct {
+    int axis;       /* 0: x links, 1: y links */
+    int fixed;      /* the column (axis 0) or row (axis 1) of the cells */
+    int start, end; /* the rows (axis 0) or columns (axis 1), [start, end) */
+} flood_section;
+
+/* q_out [N][n_sections] FP32 (host or device): every member's discharge
+ * through every section (FP64 sums).  Synchronous.  Errors: FLOOD_ERR_ARG
+ * (a section outside the grid), FLOOD_ERR_STATE, FLOOD_ERR_OOM. */
+int flood_flow_sample(flood_grid* g, int n_sections, const flood_section* sections,
+                      float* q_out, void* stream);
+
 /* ==== Land cover (Section 4.1, Table 1) =====================================
  * A class per cell (at most 4 classes), each with a Manning n (the members'
  * default; Table 1 gives 0.15 green land, 0.020 water bodies, 0.017

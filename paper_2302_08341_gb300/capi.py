@@ -33,13 +33,19 @@ EXPORTED = ["flood_default_params", "flood_last_error", "flood_create_grid", "fl
             "flood_get_roughness_factor", "flood_roughness_factor_grad", "flood_calibration_step",
             "flood_batch_set_engine", "flood_track_max_depth", "flood_get_max_depth",
             "flood_ensemble_products", "flood_set_land_cover", "flood_set_land_params",
-            "flood_get_land_params", "flood_drained_volume"]
+            "flood_get_land_params", "flood_drained_volume", "flood_flow_sample"]
 
 
 class LandClass(C.Structure):
     """flood_land_class: Manning n, runoff coefficient, drainage and
     outside-the-domain flags of one land-cover class (Section 4.1)."""
     _fields_ = [("n", C.c_float), ("runoff", C.c_float), ("drains", C.c_int), ("outside", C.c_int)]
+
+
+class Section(C.Structure):
+    """flood_section: a straight line of links (axis 0: east links of cells
+    (r, fixed), r in [start, end); axis 1: south links of cells (fixed, c))."""
+    _fields_ = [("axis", C.c_int), ("fixed", C.c_int), ("start", C.c_int), ("end", C.c_int)]
 
 
 class FloodError(RuntimeError):
@@ -134,6 +140,7 @@ def lib(path: str = LIB_PATH):
     L.flood_set_land_params.argtypes = [_VP, _VP, _VP]
     L.flood_get_land_params.argtypes = [_VP, _VP, _VP]
     L.flood_drained_volume.argtypes = [_VP, _VP]
+    L.flood_flow_sample.argtypes = [_VP, C.c_int, C.POINTER(Section), _VP, _VP]
     L.flood_track_max_depth.argtypes = [_VP, C.c_int, _VP]
     L.flood_get_max_depth.argtypes = [_VP, C.c_int, _VP, _VP]
     L.flood_ensemble_products.argtypes = [_VP, C.c_double, C.c_int, _VP, _VP, _VP, _VP]
@@ -415,6 +422,15 @@ class Grid:
         d = np.zeros(self.M, np.float32)
         _check(lib().flood_get_land_params(self.h, n.ctypes.data, d.ctypes.data), self.h)
         return n, d
+
+    def flow_sample(self, sections, stream=None):
+        """Discharge (m^3/s) of every member through every section
+        (flood_flow_sample); sections: (axis, fixed, start, end) tuples."""
+        tab = (Section * len(sections))(*[Section(*map(int, s)) for s in sections])
+        out = np.zeros((self.M, len(sections)), np.float32)
+        _check(lib().flood_flow_sample(self.h, len(sections), tab, out.ctypes.data,
+                                       stream_handle(stream)), self.h)
+        return out
 
     def drained(self):
         out = np.zeros(self.M)
