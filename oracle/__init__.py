@@ -44,12 +44,14 @@ class OrcParams(C.Structure):
                 ("alpha", C.c_double), ("dt_cap", C.c_double), ("dt_fixed", C.c_double),
                 ("h_eps", C.c_double), ("h_floor", C.c_double), ("rain_block", C.c_double),
                 ("edge_slope", C.c_double), ("limiter", C.c_int), ("east_outflow", C.c_int),
-                ("south_outflow", C.c_int), ("rc", C.c_void_p), ("drain", C.c_void_p)]
+                ("south_outflow", C.c_int), ("rc", C.c_void_p), ("drain", C.c_void_p),
+                ("inflow", C.c_void_p), ("inflow_blocks", C.c_int), ("inflow_r0", C.c_int),
+                ("inflow_r1", C.c_int), ("inflow_q", C.c_double)]
 
 
 class OrcVolumes(C.Structure):
     _fields_ = [("rain", C.c_double), ("outflow", C.c_double), ("clamp", C.c_double),
-                ("drained", C.c_double)]
+                ("drained", C.c_double), ("inflow", C.c_double)]
 
 
 _D = C.POINTER(C.c_double)
@@ -157,15 +159,27 @@ class Params:
     # (m/s), float64 [ny, nx] arrays held here, or None
     rc: np.ndarray | None = None
     drain: np.ndarray | None = None
+    # inflow hydrograph: discharge per rain block (m^3/s, float64 array held
+    # here, or None) through the west edge links of rows [inflow_r0, inflow_r1)
+    inflow: np.ndarray | None = None
+    inflow_r0: int = 0
+    inflow_r1: int = 0
+    inflow_q: float = 0.0
 
     def c(self) -> OrcParams:
         vals = []
         for f, _ in OrcParams._fields_:
-            v = getattr(self, f)
+            v = getattr(self, f, None)
             if f in ("rc", "drain"):
                 if v is not None:
                     assert v.dtype == np.float64 and v.flags.c_contiguous and v.shape == (self.ny, self.nx)
                     v = v.ctypes.data
+            elif f == "inflow":
+                if v is not None:
+                    assert v.dtype == np.float64 and v.flags.c_contiguous and v.ndim == 1
+                    v = v.ctypes.data
+            elif f == "inflow_blocks":
+                v = 0 if self.inflow is None else len(self.inflow)
             vals.append(v)
         return OrcParams(*vals)
 
@@ -192,6 +206,7 @@ class Member:
     outflow: float = 0.0
     clamp: float = 0.0
     drained: float = 0.0
+    inflow: float = 0.0
     steps: int = 0
 
     @staticmethod
@@ -207,10 +222,10 @@ def step(p: Params, z, n, scale, rain, dt_, m: Member):
     """One iteration (Eq. 2-3 on every link, Eq. 5 and Eq. 1 on every cell)."""
     z = np.ascontiguousarray(z, np.float64); n = np.ascontiguousarray(n, np.float64)
     qxn = np.empty_like(m.qx); qyn = np.empty_like(m.qy)
-    v = OrcVolumes(m.rain, m.outflow, m.clamp, m.drained)
+    v = OrcVolumes(m.rain, m.outflow, m.clamp, m.drained, m.inflow)
     lib().orc_step(C.byref(p.c()), _d(z), _d(n), scale, rain, dt_, _d(m.h), _d(m.qx), _d(m.qy),
                    _d(qxn), _d(qyn), C.byref(v))
-    m.rain, m.outflow, m.clamp, m.drained = v.rain, v.outflow, v.clamp, v.drained
+    m.rain, m.outflow, m.clamp, m.drained, m.inflow = v.rain, v.outflow, v.clamp, v.drained, v.inflow
     m.steps += 1
 
 
@@ -221,14 +236,14 @@ def advance(p: Params, z, n, scale, rain_mult, hyeto, m: Member, t_end=-1.0, max
     z = np.ascontiguousarray(z, np.float64); n = np.ascontiguousarray(n, np.float64)
     hy = np.ascontiguousarray(hyeto, np.float64)
     t = C.c_double(m.t)
-    v = OrcVolumes(m.rain, m.outflow, m.clamp, m.drained)
+    v = OrcVolumes(m.rain, m.outflow, m.clamp, m.drained, m.inflow)
     cap = (max_steps if max_steps > 0 else 2_000_000) if log_dt else 0
     log = np.zeros(max(cap, 1))
     k = lib().orc_advance(C.byref(p.c()), _d(z), _d(n), float(scale), float(rain_mult),
                           _d(hy), len(hy), _d(m.h), _d(m.qx), _d(m.qy), C.byref(t), float(t_end),
                           int(max_steps), C.byref(v), _d(log) if log_dt else None, cap)
     m.t = t.value
-    m.rain, m.outflow, m.clamp, m.drained = v.rain, v.outflow, v.clamp, v.drained
+    m.rain, m.outflow, m.clamp, m.drained, m.inflow = v.rain, v.outflow, v.clamp, v.drained, v.inflow
     m.steps += k
     return log[:k].copy() if log_dt else k
 
@@ -261,7 +276,7 @@ class Ensemble:
         return st
 
     def volumes(self):
-        return np.array([[v.rain, v.outflow, v.clamp, v.drained] for v in self.vol])
+        return np.array([[v.rain, v.outflow, v.clamp, v.drained, v.inflow] for v in self.vol])
 
     def storage(self):
         dx = self.p.dx

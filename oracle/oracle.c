@@ -61,6 +61,13 @@ typedef struct {
        drainage rate (m/s) that removes water while there is any. */
     const double* rc;
     const double* drain;
+    /* Inflow hydrograph (NULL when absent): a discharge series (m^3/s, one
+       value per rain block) entering through the west edge links of rows
+       [inflow_r0, inflow_r1), spread evenly over them; inflow_q is the flux
+       per unit width (m^2/s) of the current step, set by orc_advance. */
+    const double* inflow;
+    int inflow_blocks, inflow_r0, inflow_r1;
+    double inflow_q;
 } orc_params;
 
 /* Volume bookkeeping of one member (m^3), all in FP64. */
@@ -69,6 +76,7 @@ typedef struct {
     double outflow;  /* volume that left through free-outflow edges           */
     double clamp;    /* volume added by resetting negative depths to zero     */
     double drained;  /* volume removed by drainage (land cover)               */
+    double inflow;   /* volume that entered through an inflow boundary         */
 } orc_volumes;
 
 #define IX(r, c) ((size_t)(r) * (size_t)nx + (size_t)(c))
@@ -121,8 +129,11 @@ double orc_link_flux(const orc_params* p, double h1, double z1, double h2, doubl
     if (hflow <= p->h_eps) return 0.0;
     double S = (eta2 - eta1) / p->dx;                  /* water-surface slope */
     double num = q - p->g * hflow * dt * S;
-    /* friction term g n^2 |q_t| dt / h_flow^(7/3); exactly 0 when q_t = 0 */
-    double fric = q == 0.0 ? 0.0 : p->g * nl * nl * fabs(q) * dt / pow(hflow, 7.0 / 3.0);
+    /* friction term g n^2 |q_t| dt / h_flow^(7/3); exactly 0 when q_t = 0.
+       |q_t| multiplies h_flow^(-7/3) first, so that a vanishing flow depth
+       (a wetting front's denormal depths) gives infinite friction, i.e. no
+       flow, instead of 0/0 from two underflows. */
+    double fric = q == 0.0 ? 0.0 : p->g * nl * nl * dt * (fabs(q) * pow(hflow, -7.0 / 3.0));
     double den = 1.0 + fric;
     double qn = num / den;                                          /* Eq. 2 */
     if (p->limiter) {
@@ -160,7 +171,9 @@ void orc_step(const orc_params* p, const double* z, const double* n, double scal
         for (int c = 0; c <= nx; ++c) {
             double qn;
             if (c == 0) {
-                qn = 0.0;                                          /* west wall */
+                qn = (p->inflow && r >= p->inflow_r0 && r < p->inflow_r1)
+                         ? p->inflow_q                                 /* inflow */
+                         : 0.0;                                        /* west wall */
             } else if (c == nx) {
                 qn = p->east_outflow
                          ? outflow_flux(p, h[IX(r, nx - 1)], z[IX(r, nx - 1)], qx[IQX(r, nx)],
@@ -217,6 +230,7 @@ void orc_step(const orc_params* p, const double* z, const double* n, double scal
         }
     }
     for (int r = 0; r < ny; ++r) vol->outflow += dt * qx_new[IQX(r, nx)] * dx;
+    for (int r = 0; r < ny; ++r) vol->inflow += dt * qx_new[IQX(r, 0)] * dx;
     for (int c = 0; c < nx; ++c) vol->outflow += dt * qy_new[IQY(ny, c)] * dx;
     if (p->rc) {
         double area = 0.0;
@@ -261,7 +275,11 @@ long orc_advance(const orc_params* p, const double* z, const double* n, double s
         double t_next;
         double dt = orc_dt(p, orc_hmax(ny, nx, h), *t, t_end, &t_next);
         double rain = orc_rain_rate(p, hyeto, n_blocks, *t) * rain_mult;
-        orc_step(p, z, n, scale, rain, dt, h, qx, qy, qx_new, qy_new, vol);
+        orc_params ps = *p;
+        if (p->inflow)
+            ps.inflow_q = orc_rain_rate(p, p->inflow, p->inflow_blocks, *t) /
+                          (p->dx * (double)(p->inflow_r1 - p->inflow_r0));
+        orc_step(&ps, z, n, scale, rain, dt, h, qx, qy, qx_new, qy_new, vol);
         if (dt_log && steps < dt_log_cap) dt_log[steps] = dt;
         *t = t_next;
         ++steps;
@@ -411,7 +429,7 @@ static double link_flux_d(const orc_params* p, double h1, double z1, double h2, 
     int first = eta1 >= eta2;            /* which argument of max(eta1, eta2) */
     double S = (eta2 - eta1) / p->dx;
     double num = q - p->g * hflow * dt * S;
-    double fric = q == 0.0 ? 0.0 : p->g * nl * nl * fabs(q) * dt / pow(hflow, 7.0 / 3.0);
+    double fric = q == 0.0 ? 0.0 : p->g * nl * nl * dt * (fabs(q) * pow(hflow, -7.0 / 3.0));
     double den = 1.0 + fric;
     double qn = num / den;                                          /* Eq. 2 */
     if (p->limiter) {
@@ -573,7 +591,8 @@ double orc_loss_and_grad(const orc_params* p, const double* z, const double* n, 
                          long* n_steps_out)
 {
     const int ny = p->ny, nx = p->nx;
-    if (p->rc || p->drain) return NAN;  /* the reverse mode covers the scheme without land cover */
+    if (p->rc || p->drain || p->inflow) return NAN;  /* the reverse mode covers neither land cover
+                                                        nor inflow boundaries */
     const size_t nc = (size_t)ny * nx, nqx = (size_t)ny * (nx + 1), nqy = (size_t)(ny + 1) * nx;
     const size_t per = nc + nqx + nqy;
     long cap = 1024, nst = 0;

@@ -12,6 +12,7 @@ import sys
 
 import oracle
 from tests import test_oracle_adjoint as A
+from tests import test_oracle_inflow as IN
 from tests import test_oracle_land_cover as LC
 from tests import test_oracle_pf as P
 from tests import test_oracle_scheme as S
@@ -46,13 +47,16 @@ PINS = [
     LC.test_flat_box_drainage_above_rain_takes_all,
     LC.test_volume_balance_with_land_cover_exact_to_1e12,
     LC.test_wall_cells_stay_dry_and_pass_no_flow,
+    IN.test_closed_box_stores_the_inflow_exactly,
+    IN.test_piecewise_series_lands_on_block_edges,
+    IN.test_volume_balance_with_inflow_and_rain_to_1e12,
 ]
 
 # (name, original text, planted mistake)
 MUTATIONS = [
-    ("friction exponent 4/3", "pow(hflow, 7.0 / 3.0)", "pow(hflow, 4.0 / 3.0)"),
-    ("friction n instead of n^2", "p->g * nl * nl * fabs(q)", "p->g * nl * fabs(q)"),
-    ("friction without dt", "fabs(q) * dt / pow", "fabs(q) / pow"),
+    ("friction exponent 4/3", "pow(hflow, -7.0 / 3.0)", "pow(hflow, -4.0 / 3.0)"),
+    ("friction n instead of n^2", "p->g * nl * nl * dt * (fabs(q)", "p->g * nl * dt * (fabs(q)"),
+    ("friction without dt", "p->g * nl * nl * dt * (fabs(q)", "p->g * nl * nl * (fabs(q)"),
     ("slope sign flipped", "(eta2 - eta1) / p->dx", "(eta1 - eta2) / p->dx"),
     ("gravity term without g", "q - p->g * hflow * dt * S", "q - hflow * dt * S"),
     ("Eq 3 as max depth", "fmax(eta1, eta2) - fmax(z1, z2)", "fmax(h1, h2)"),
@@ -69,6 +73,10 @@ MUTATIONS = [
     ("drainage without dt", "double sink = dt * p->drain[IX(r, c)];",
      "double sink = p->drain[IX(r, c)];"),
     ("rain volume ignores the runoff coefficient", "area += p->rc[i];", "area += 1.0;"),
+    ("inflow leaves instead of entering", "? p->inflow_q", "? -p->inflow_q"),
+    ("inflow not spread over the segment", "(p->dx * (double)(p->inflow_r1 - p->inflow_r0))",
+     "p->dx"),
+    ("inflow volume not counted", "vol->inflow += dt * qx_new[IQX(r, 0)] * dx;", ""),
     ("x-link roughness not averaged", "scale * 0.5 * (n[IX(r, c - 1)] + n[IX(r, c)])",
      "scale * n[IX(r, c)]"),
     ("roughness scale dropped on y links", "double nl = scale * 0.5 * (n[IX(r - 1, c)]",
