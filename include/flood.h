@@ -215,6 +215,18 @@ int flood_adjoint(flood_grid* g, const flood_loss_spec* loss, int ckpt_every, fl
  * (with checkpointing) and of its reverse pass (replay included). */
 int flood_adjoint_timing(const flood_grid* g, double* forward_ms, double* reverse_ms);
 
+/* ==== Inflow hydrograph boundary ============================================
+ * A discharge series Q (m^3/s, one value per rain block, FP32) entering the
+ * domain through the west-edge links of rows [r0, r1), spread evenly: each
+ * such link carries q = Q / (dx (r1 - r0)) into the domain instead of the
+ * wall's zero (every member alike); the inflow volume is reported by
+ * flood_inflow_volume and storage = rain + inflow - outflow + clamp
+ * (- drained).  n_blocks = 0 removes the boundary.  Synchronous.
+ * Errors: FLOOD_ERR_ARG (rows outside the grid, negative or non-finite
+ * discharges).  Not covered by flood_adjoint (refused). */
+int flood_set_inflow(flood_grid* g, int r0, int r1, const float* series, int n_blocks);
+int flood_inflow_volume(flood_grid* g, double* volume);
+
 /* ==== Streamflow gauges (the stream gauges of Section 4.1 / 4.4) ============
  * A section is a straight line of links: axis 0, the links east of cells
  * (r, fixed) for rows r in [start, end); axis 1, the links south of cells

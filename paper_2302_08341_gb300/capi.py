@@ -33,7 +33,8 @@ EXPORTED = ["flood_default_params", "flood_last_error", "flood_create_grid", "fl
             "flood_get_roughness_factor", "flood_roughness_factor_grad", "flood_calibration_step",
             "flood_batch_set_engine", "flood_track_max_depth", "flood_get_max_depth",
             "flood_ensemble_products", "flood_set_land_cover", "flood_set_land_params",
-            "flood_get_land_params", "flood_drained_volume", "flood_flow_sample"]
+            "flood_get_land_params", "flood_drained_volume", "flood_flow_sample", "flood_set_inflow",
+            "flood_inflow_volume"]
 
 
 class LandClass(C.Structure):
@@ -141,6 +142,8 @@ def lib(path: str = LIB_PATH):
     L.flood_get_land_params.argtypes = [_VP, _VP, _VP]
     L.flood_drained_volume.argtypes = [_VP, _VP]
     L.flood_flow_sample.argtypes = [_VP, C.c_int, C.POINTER(Section), _VP, _VP]
+    L.flood_set_inflow.argtypes = [_VP, C.c_int, C.c_int, _VP, C.c_int]
+    L.flood_inflow_volume.argtypes = [_VP, _VP]
     L.flood_track_max_depth.argtypes = [_VP, C.c_int, _VP]
     L.flood_get_max_depth.argtypes = [_VP, C.c_int, _VP, _VP]
     L.flood_ensemble_products.argtypes = [_VP, C.c_double, C.c_int, _VP, _VP, _VP, _VP]
@@ -422,6 +425,18 @@ class Grid:
         d = np.zeros(self.M, np.float32)
         _check(lib().flood_get_land_params(self.h, n.ctypes.data, d.ctypes.data), self.h)
         return n, d
+
+    def set_inflow(self, r0, r1, series):
+        """Inflow hydrograph through the west-edge links of rows [r0, r1):
+        discharge per rain block (m^3/s) (flood_set_inflow)."""
+        q = np.ascontiguousarray(series, np.float32)
+        _check(lib().flood_set_inflow(self.h, int(r0), int(r1), q.ctypes.data if len(q) else None,
+                                      len(q)), self.h)
+
+    def inflow_volume(self):
+        out = np.zeros(self.M)
+        _check(lib().flood_inflow_volume(self.h, out.ctypes.data), self.h)
+        return out
 
     def flow_sample(self, sections, stream=None):
         """Discharge (m^3/s) of every member through every section

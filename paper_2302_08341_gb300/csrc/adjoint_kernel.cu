@@ -76,6 +76,8 @@ __global__ void __launch_bounds__(32 * WM * WC, 4) adjoint_kernel(const AdjArgs 
     k.h_eps = a.h_eps;
     k.edge_drop = a.edge_drop;
     k.limiter = a.limiter;
+    k.q_in = 0.0f;  // no inflow boundary here
+    k.in_r0 = k.in_r1 = 0;
     const float L = k.dx_4dt;
     const float T = pl.dt_dx;
     const float s = a.scale[m];

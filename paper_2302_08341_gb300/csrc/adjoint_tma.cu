@@ -94,6 +94,8 @@ __global__ void __launch_bounds__(32 * WM, WM == 4 ? 3 : 12) adjoint_tma_kernel(
     k.h_eps = a.h_eps;
     k.edge_drop = a.edge_drop;
     k.limiter = a.limiter;
+    k.q_in = 0.0f;  // no inflow boundary here
+    k.in_r0 = k.in_r1 = 0;
     const float L = k.dx_4dt;
     const float T = pl.dt_dx;
     const float s = a.scale[m];

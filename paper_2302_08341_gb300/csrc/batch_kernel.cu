@@ -59,6 +59,8 @@ __global__ void __launch_bounds__(32 * W) batch_step_kernel(const BatchArgs a)
     k.h_eps = a.h_eps;
     k.edge_drop = a.edge_drop;
     k.limiter = a.limiter;
+    k.q_in = 0.0f;  // no inflow boundary here
+    k.in_r0 = k.in_r1 = 0;
     const size_t ms = 3 * sd.plane;
     const float* src = sd.state + (size_t)p.cur * ms;
     float* dst = sd.state + (size_t)(1 - p.cur) * ms;
@@ -106,6 +108,8 @@ __global__ void __launch_bounds__(32 * W, 20 / W) batch_tma_kernel(const BatchAr
     k.h_eps = a.h_eps;
     k.edge_drop = a.edge_drop;
     k.limiter = a.limiter;
+    k.q_in = 0.0f;  // no inflow boundary here
+    k.in_r0 = k.in_r1 = 0;
     uint32_t bar0;
     unsigned char* my_stages;
     tma_march_smem(smem_raw, W, w, bar0, my_stages);

@@ -68,6 +68,8 @@ void free_ensemble(flood_grid* g)
     dfree(g->gnm); dfree(g->gn_out); dfree(g->gpart); dfree(g->seg_end); dfree(g->samp_step);
     dfree(g->samp_y); dfree(g->samp_d); dfree(g->samp_cells); dfree(g->closs);
     dfree(g->hmax_field); dfree(g->lc_n); dfree(g->lc_drain); dfree(g->dacc);
+    dfree(g->inflow_acc);
+    g->inflow_acc = nullptr;
     g->closs = nullptr; g->closs_cap = 0; g->hmax_field = nullptr; g->track_max = false;
     g->lc_n = nullptr; g->lc_drain = nullptr; g->dacc = nullptr;
     g->plan = nullptr; g->log = nullptr; g->ckpt = nullptr; g->seg = nullptr;
@@ -136,6 +138,13 @@ StepArgs step_args(const flood_grid* g, double t_end)
     a.dxd = g->p.dx;
     a.cell_area = g->p.dx * g->p.dx;
     a.ncell = g->lc_on ? g->lc_rain_cells : (double)g->ny * (double)g->nx;
+    if (g->inflow && g->inflow_acc) {
+        a.inflow = g->inflow;
+        a.inflow_blocks = g->inflow_blocks;
+        a.in_r0 = g->in_r0;
+        a.in_r1 = g->in_r1;
+        a.inflow_acc = g->inflow_acc;
+    }
     a.dx = (float)g->p.dx;
     a.h_eps = (float)g->p.h_eps;
     a.edge_drop = (float)(g->p.edge_slope * g->p.dx);
@@ -353,6 +362,7 @@ int flood_destroy(flood_grid* g)
     dfree(g->zn);
     dfree(g->err);
     dfree(g->n0); dfree(g->fac); dfree(g->fgrad);
+    dfree(g->inflow);
     delete g;
     return FLOOD_OK;
 }
@@ -384,6 +394,7 @@ int flood_ensemble_init(flood_grid* g, int M, const float* h0, int h0_per_member
         (rc = dalloc(g, &g->hyeto, n_blocks)) || (rc = dalloc(g, &g->w, M)) ||
         (rc = dalloc(g, &g->w_post, M)) || (rc = dalloc(g, &g->ms, (size_t)3 * M)) ||
         (rc = dalloc(g, &g->vacc, (size_t)M * g->nslot * 2)) || (rc = dalloc(g, &g->rain_acc, M)) ||
+        (rc = dalloc(g, &g->inflow_acc, M)) ||
         (rc = dalloc(g, &g->beta, M)) || (rc = dalloc(g, &g->pfi, (size_t)5 * M)) ||
         (rc = dalloc(g, &g->pf_small, 4)) || (rc = dalloc(g, &g->neff, 1)) ||
         (rc = dalloc(g, &g->part, (size_t)M * g->part_cap)) || (rc = dalloc(g, &g->storage, M)) ||
@@ -414,6 +425,7 @@ int flood_ensemble_init(flood_grid* g, int M, const float* h0, int h0_per_member
     CK(g, cudaMemcpyAsync(g->ms, ms.data(), sizeof(MemberClock) * 3 * M, cudaMemcpyHostToDevice, s));
     CK(g, cudaMemsetAsync(g->vacc, 0, sizeof(double) * M * g->nslot * 2, s));
     CK(g, cudaMemsetAsync(g->rain_acc, 0, sizeof(double) * M, s));
+    CK(g, cudaMemsetAsync(g->inflow_acc, 0, sizeof(double) * M, s));
     CK(g, cudaMemsetAsync(g->err, 0, sizeof(int), s));
     g->k = 0;
     flood::launch_hmax(g->state, g->ms, M, g->ny, g->nx, g->ld, g->plane, g->n_sm, s);
@@ -807,6 +819,8 @@ extern "C" int flood_autotune(flood_grid* g, int steps_per_trial, int* best_rows
     std::vector<double> rain0(M), vacc0((size_t)M * g->nslot * 2), drained0(M, 0.0);
     CK(g, cudaMemcpy(rain0.data(), g->rain_acc, sizeof(double) * M, cudaMemcpyDeviceToHost));
     CK(g, cudaMemcpy(vacc0.data(), g->vacc, sizeof(double) * vacc0.size(), cudaMemcpyDeviceToHost));
+    std::vector<double> inflow0(M);
+    CK(g, cudaMemcpy(inflow0.data(), g->inflow_acc, sizeof(double) * M, cudaMemcpyDeviceToHost));
     if (g->dacc) {
         std::vector<double> d0((size_t)M * g->nslot);
         CK(g, cudaMemcpy(d0.data(), g->dacc, sizeof(double) * d0.size(), cudaMemcpyDeviceToHost));
@@ -859,6 +873,7 @@ extern "C" int flood_autotune(flood_grid* g, int steps_per_trial, int* best_rows
         cudaMemcpyAsync(g->ms + (g->k % 3) * M, back.data(), sizeof(MemberClock) * M,
                         cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(g->rain_acc, rain0.data(), sizeof(double) * M, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(g->inflow_acc, inflow0.data(), sizeof(double) * M, cudaMemcpyHostToDevice, s);
     }
     cudaStreamSynchronize(s);
     cudaFree(snap);

@@ -56,6 +56,10 @@ struct StepArgs {
     float lc_runoff[4];         // fraction of the rain that stays, per class
     float lc_drains[4];         // 1: the member's drainage applies to the class
     double* dacc;               // [M][nslot] drained volume partials
+    // inflow hydrograph through west-edge rows [in_r0, in_r1) (inflow = null: none)
+    const float* inflow;        // [inflow_blocks] discharge per rain block (m^3/s)
+    int inflow_blocks, in_r0, in_r1;
+    double* inflow_acc;         // [M] inflow volume
     size_t plane;               // ny * ld
     int ny, nx, ld, M, nb;
     int rows_per_strip;
@@ -91,6 +95,7 @@ struct MemberPlan {
     int active;               // 0: the member does not step
     int cur;                  // buffer holding the member's state before the step
     int ckpt;                 // checkpoint slot that also receives the result, or -1
+    float q_in;               // inflow flux per unit width of this step (m^2/s), 0 without
 };
 
 // Step length of one member (Eq. 4 with floor, cap and landing on the next
@@ -174,6 +179,8 @@ struct FaceK {
     float h_eps;      // no flow unless the flow depth exceeds this (0: Eq. 2-3 as printed)
     float edge_drop;  // bed drop over one cell past a free-outflow edge
     int limiter;
+    float q_in;       // inflow flux per unit width through west-edge rows [in_r0, in_r1)
+    int in_r0, in_r1;
 };
 
 // Hardware approximate base-2 logarithm, base-2 exponential and reciprocal

@@ -90,6 +90,10 @@ struct flood_grid {
     float* lc_n = nullptr;        // [M][4] per-member class roughness
     float* lc_drain = nullptr;    // [M] per-member drainage rate (m/s)
     double* dacc = nullptr;       // [M][nslot] drained volume partials
+    // inflow hydrograph (inflow.cu)
+    float* inflow = nullptr;      // [inflow_blocks] discharge per rain block (m^3/s)
+    int inflow_blocks = 0, in_r0 = 0, in_r1 = 0;
+    double* inflow_acc = nullptr; // [M] inflow volume
     // ensemble products (products.cu)
     float* hmax_field = nullptr;  // [M][plane] running maximum depth of each member
     bool track_max = false;

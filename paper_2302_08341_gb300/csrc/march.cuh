@@ -233,7 +233,7 @@ __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, fl
         // west link of the lane's first cell: previous lane's last east link
         float qW0 = __shfl_up_sync(0xffffffffu, qxE[3], 1);
         if (lane == 0) {
-            qW0 = 0.0f;
+            qW0 = (r >= k.in_r0 && r < k.in_r1) ? k.q_in : 0.0f;  // west edge: wall or inflow
             if (c0 > 0) {  // recompute the neighbouring span's link (halo)
                 const size_t ow = (size_t)r * ld + c0 - 1;
                 const float nw = LC ? nWl : __ldg(n + ow);

@@ -43,6 +43,14 @@ __global__ void plan_kernel(const StepArgs a)
     fill_plan(p, sp, a.g, a.dxd);
     p.cur = in.cur;
     p.ckpt = -1;
+    p.q_in = 0.0f;
+    if (a.inflow && sp.active) {  // the block's discharge spread over the inflow rows
+        const double blk = floor(__ddiv_rn(in.t, a.rain_block));
+        const int b = (int)blk;
+        const double Q = (blk >= 0.0 && b < a.inflow_blocks) ? (double)a.inflow[b] : 0.0;
+        p.q_in = (float)(Q / (a.dxd * (double)(a.in_r1 - a.in_r0)));
+        a.inflow_acc[m] += (double)p.q_in * a.dxd * (double)(a.in_r1 - a.in_r0) * sp.dt;
+    }
     a.ms_clr[m].hmax_bits = 0u;  // the slot the next step's maximum goes to
     if (!sp.active) {
         a.ms_out[m] = in;
@@ -101,6 +109,9 @@ __global__ void __launch_bounds__(32 * WM * WC, (LC ? 4 : FLOOD_STEP_MIN_BLOCKS)
     k.h_eps = a.h_eps;
     k.edge_drop = a.edge_drop;
     k.limiter = a.limiter;
+    k.q_in = p.q_in;
+    k.in_r0 = a.in_r0;
+    k.in_r1 = a.in_r1;
 
     const int r0 = blockIdx.z * a.rows_per_strip;
     const int r1 = min(r0 + a.rows_per_strip, ny);

@@ -45,6 +45,9 @@ __global__ void __launch_bounds__(32 * WM, (LC ? 16 : 20) / WM) step_tma_kernel(
     k.h_eps = a.h_eps;
     k.edge_drop = a.edge_drop;
     k.limiter = a.limiter;
+    k.q_in = pl.q_in;
+    k.in_r0 = a.in_r0;
+    k.in_r1 = a.in_r1;
 
     const int r0 = blockIdx.z * a.rows_per_strip;
     const int r1 = min(r0 + a.rows_per_strip, a.ny);

@@ -248,7 +248,7 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
                              east_out, south_out, qxE, qyS);
         float qW0 = __shfl_up_sync(0xffffffffu, qxE[3], 1);
         if (lane == 0) {
-            qW0 = 0.0f;
+            qW0 = (r >= k.in_r0 && r < k.in_r1) ? k.q_in : 0.0f;  // west edge: wall or inflow
             if (c0 > 0) {  // the neighbouring span's last link, from the tile's halo
                 const float nW = LC ? nWl : P[kN + 3];
                 qW0 = link_q(P[3], P[kZ + 3], hC[0], zC[0], P[kBox + 3],
