@@ -208,6 +208,13 @@ def barrier(world):
         dist.barrier()
 
 
+def workload_config():
+    """The benchmark workload, the same for both arms."""
+    return {"workload": f"ensemble flood + particle filter: {NY}x{NX} cells (3 m), {M} members, "
+                        "300 s assimilation windows, 1 h triangular storm",
+            "cells": NY * NX, "members": M, "gauges": G, "window_s": WINDOW}
+
+
 def make_inputs():
     from paper_2302_08341_gb300 import synth
     terr = synth.make_terrain(NY, NX, seed=SEED)
@@ -541,8 +548,8 @@ def run_reference(args):
         "unit": "member-cell-steps/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"ensemble flood {NY}x{NX} cells x {M} members, 300 s windows "
-                               "(oracle sample)", "cells": NY * NX, "members": M},
+        "config": {**workload_config(), "parallelism": "replicas1",
+                   "sample": "oracle, one member, two steps per benchmark step"},
         "cpu_baseline": {"value": v, "unit": "member-cell-steps/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": v, "unit": "member-cell-steps/s", "h2d_bytes_per_step": 0,
@@ -694,10 +701,8 @@ def run_gb300(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"ensemble flood + particle filter: {NY}x{NX} cells (3 m), "
-                               f"{M} members, 300 s assimilation windows, 1 h triangular storm",
-                   "cells": ncell, "members": M, "gauges": G, "window_s": WINDOW,
-                   "member_steps": member_steps, "parallelism": f"replicas{world}",
+        "config": {**workload_config(), "member_steps": member_steps,
+                   "parallelism": f"replicas{world}",
                    "l2": "state 9.2 GB >> 129 MB L2 (no flush needed)"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
         "clocks": clk.summary(),
