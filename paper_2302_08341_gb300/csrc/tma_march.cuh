@@ -25,6 +25,7 @@ constexpr int kTmaStaticOff = 1664;                // bytes: z, n after h, qx, q
 constexpr int kTmaStageBytes = 2816;               // 128-aligned stage size
 constexpr uint32_t kTmaTx = kTmaBox * 3 * 4 + kTmaBox * 2 * 4;  // bytes landing per stage
 constexpr long long kTmaWaitBudget = 200000000LL;  // clock cycles (~0.1 s) before giving up
+static_assert((kTmaNS & (kTmaNS - 1)) == 0, "ring index arithmetic needs a power of two");
 
 // Dynamic shared memory of a CTA of `warps` warps: barriers, then each warp's
 // stages.
@@ -85,6 +86,7 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
     const int c = c0 + 4 * lane;
     const bool act = c < nx;
     const bool interior = (c + 4 < nx);
+    const bool edge_warp = c0 + kTmaSpan >= nx;  // the span holds the grid's last column
     const int ra = r0 > 0 ? r0 - 1 : r0;   // first row loaded
     const int rb = min(r1 + 1, ny);        // one past the last row loaded
 
@@ -95,7 +97,7 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
     __syncwarp();
     int issued = ra;  // rows [ra, issued) have been requested
     auto issue = [&](int row) {
-        const int sidx = (row - ra) % kNS;
+        const unsigned sidx = (unsigned)(row - ra) & (kNS - 1);
         const uint32_t bar = bar0 + 8u * sidx;
         const uint32_t dsts = stage0 + kStageBytes * sidx;
         mbar_arrive_expect_tx(bar, kTx);
@@ -106,10 +108,12 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
         if (lane == 0) issue(issued);
     auto wait_row = [&](int row) -> bool {
         const int kk = row - ra;
-        return mbar_wait_bounded(bar0 + 8u * (kk % kNS), (kk / kNS) & 1, kWaitBudget);
+        return mbar_wait_bounded(bar0 + 8u * ((unsigned)kk & (kNS - 1)), ((unsigned)kk / kNS) & 1,
+                                 kWaitBudget);
     };
     auto row_ptr = [&](int row) -> const float* {
-        return reinterpret_cast<const float*>(my_stages + kStageBytes * ((row - ra) % kNS));
+        return reinterpret_cast<const float*>(my_stages +
+                                              kStageBytes * ((unsigned)(row - ra) & (kNS - 1)));
     };
     // recycle the stage of `row` for the next row in line
     auto release = [&](int row) {
@@ -264,13 +268,17 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
             row_depths<false, LC>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN,
                                   drv, ddv, &drn_s, &drn_c);
         bad |= !(hsum <= 3.0e38f);
-        float ev = 0.0f;
+        if ((edge_warp && east_out) || (!has_s && south_out)) {  // the same for the whole warp
+            // links leaving the domain this row: the east edge link (one lane)
+            // and, on the last row, the south edge links
+            float ev = 0.0f;
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (c + j == nx - 1 && east_out) ev = qxE[j];
-        if (!has_s && south_out)
-            ev = __fadd_rn(ev, __fadd_rn(__fadd_rn(qyS[0], qyS[1]), __fadd_rn(qyS[2], qyS[3])));
-        kahan_add(out_s, out_c, ev);
+            for (int j = 0; j < 4; ++j)
+                if (c + j == nx - 1 && east_out) ev = qxE[j];
+            if (!has_s && south_out)
+                ev = __fadd_rn(ev, __fadd_rn(__fadd_rn(qyS[0], qyS[1]), __fadd_rn(qyS[2], qyS[3])));
+            kahan_add(out_s, out_c, ev);
+        }
         if (act) {
             tma_store4(dst + o, hN);
             tma_store4(dst + plane + o, qxE);
