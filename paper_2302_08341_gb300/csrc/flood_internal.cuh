@@ -229,6 +229,9 @@ __device__ __forceinline__ float eq2(float hf, float dS, float q, float n_link, 
 // intrinsics, so a link computed twice (by the tile that owns it and, as a
 // halo, by its neighbour) gives bit-identical values and the update stays
 // exactly conservative.
+// LIM: 1 or 0 fixes the limiter on or off at compile time (the step kernels
+// instantiate both), -1 reads it from k.
+template <int LIM = -1>
 __device__ __forceinline__ float link_q(float h1, float z1, float h2, float z2, float q,
                                         float n_link, const FaceK& k)
 {
@@ -239,7 +242,7 @@ __device__ __forceinline__ float link_q(float h1, float z1, float h2, float z2, 
     // dx * S_surf = (z2 - z1) + (h2 - h1)
     const float dS = __fadd_rn(dz, __fsub_rn(h2, h1));
     float qn = eq2(hf, dS, q, n_link, k);
-    if (k.limiter) {
+    if (LIM == 1 || (LIM < 0 && k.limiter)) {
         // |q'| <= h_upstream dx / (4 dt): with h1, h2 >= 0 the two one-sided
         // clamps equal the clamp by the depth of the cell the flow leaves
         qn = fmaxf(fminf(qn, __fmul_rn(h1, k.dx_4dt)), -__fmul_rn(h2, k.dx_4dt));
@@ -250,10 +253,11 @@ __device__ __forceinline__ float link_q(float h1, float z1, float h2, float z2, 
 // Free-outflow edge link: a ghost cell continuing the bed at the edge slope
 // with the edge cell's depth, so h_flow = h and dx * S = -edge_slope * dx;
 // only outward flow passes.
+template <int LIM = -1>
 __device__ __forceinline__ float outflow_q(float h, float q, float n_cell, const FaceK& k)
 {
     float qn = eq2(h, -k.edge_drop, q, n_cell, k);
-    if (k.limiter) qn = fminf(qn, __fmul_rn(h, k.dx_4dt));
+    if (LIM == 1 || (LIM < 0 && k.limiter)) qn = fminf(qn, __fmul_rn(h, k.dx_4dt));
     return h > k.h_eps ? fmaxf(qn, 0.0f) : 0.0f;
 }
 

@@ -32,7 +32,7 @@ __device__ __forceinline__ void m_store4(float* p, const float (&v)[4])
 // The links of one row of a lane's four cells: east links (Eq. 2-3, or the
 // free-outflow edge) and south links.  INTERIOR: all four cells and their
 // east neighbours lie inside the grid, so no per-cell edge tests are needed.
-template <bool INTERIOR>
+template <bool INTERIOR, int LIM = -1>
 __device__ __forceinline__ void row_links(const float (&hC)[4], const float (&zC)[4],
                                           const float (&nC)[4], const float (&hS)[4],
                                           const float (&zS)[4], const float (&nS)[4],
@@ -49,9 +49,9 @@ __device__ __forceinline__ void row_links(const float (&hC)[4], const float (&zC
         const float n2 = (j < 3) ? nC[j + 1] : nE;
         float q;
         if (INTERIOR || cj < nx - 1)
-            q = link_q(hC[j], zC[j], h2, z2, qxo[j], __fmul_rn(s_half, __fadd_rn(nC[j], n2)), k);
+            q = link_q<LIM>(hC[j], zC[j], h2, z2, qxo[j], __fmul_rn(s_half, __fadd_rn(nC[j], n2)), k);
         else if (cj == nx - 1)
-            q = east_out ? outflow_q(hC[j], qxo[j], __fmul_rn(s, nC[j]), k) : 0.0f;
+            q = east_out ? outflow_q<LIM>(hC[j], qxo[j], __fmul_rn(s, nC[j]), k) : 0.0f;
         else
             q = 0.0f;
         qxE[j] = q;
@@ -61,10 +61,10 @@ __device__ __forceinline__ void row_links(const float (&hC)[4], const float (&zC
         float q = 0.0f;
         if (INTERIOR || c + j < nx) {
             if (has_s)
-                q = link_q(hC[j], zC[j], hS[j], zS[j], qyo[j],
+                q = link_q<LIM>(hC[j], zC[j], hS[j], zS[j], qyo[j],
                            __fmul_rn(s_half, __fadd_rn(nC[j], nS[j])), k);
             else if (south_out)
-                q = outflow_q(hC[j], qyo[j], __fmul_rn(s, nC[j]), k);
+                q = outflow_q<LIM>(hC[j], qyo[j], __fmul_rn(s, nC[j]), k);
         }
         qyS[j] = q;
     }

@@ -14,7 +14,7 @@ constexpr int kSpan = kTmaSpan;
 
 // The land-cover form holds its class tables in registers: it gets more of
 // them (four CTAs of four warps per SM instead of five) rather than spill.
-template <int WM, bool TRACK_MAX, bool LC>
+template <int WM, bool TRACK_MAX, bool LC, int LIM>
 __global__ void __launch_bounds__(32 * WM, (LC ? 16 : 20) / WM) step_tma_kernel(const __grid_constant__ TmaArgs t)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(32 * WM, (LC ? 16 : 20) / WM) step_tma_kernel(
     float* hm = TRACK_MAX ? a.hmax_field + (size_t)m * a.plane : nullptr;
     LandK lk;
     if (LC) lk = land_k(a, m, pl.dr, pl.dt, lane);
-    if (!tma_march<TRACK_MAX, LC>(&t.state_map, &t.static_map, (pl.cur * a.M + m) * 3, bar0,
+    if (!tma_march<TRACK_MAX, LC, LIM>(&t.state_map, &t.static_map, (pl.cur * a.M + m) * 3, bar0,
                                   my_stages, dst, ck, hm, a.err, a.plane, a.ny, a.nx, a.ld, c0, r0,
                                   r1, lane, k, pl.dt_dx, a.scale[m], pl.dr, a.east_out, a.south_out,
                                   mo, &lk))
@@ -118,7 +118,7 @@ int tma_box_cols() { return kTmaBox; }
 
 namespace {
 
-template <bool TRACK_MAX, bool LC>
+template <bool TRACK_MAX, bool LC, int LIM>
 void launch_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
 {
     const StepArgs& a = t.a;
@@ -128,16 +128,16 @@ void launch_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
         static bool attr = false;
         const size_t shm = tma_smem_bytes<4>();
         if (!attr) {
-            cudaFuncSetAttribute(step_tma_kernel<4, TRACK_MAX, LC>,
+            cudaFuncSetAttribute(step_tma_kernel<4, TRACK_MAX, LC, LIM>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
             attr = true;
         }
         dim3 grid((a.M + 3) / 4, spans, strips), block(32, 4);
-        step_tma_kernel<4, TRACK_MAX, LC><<<grid, block, shm, s>>>(t);
+        step_tma_kernel<4, TRACK_MAX, LC, LIM><<<grid, block, shm, s>>>(t);
     } else {
         const size_t shm = tma_smem_bytes<1>();
         dim3 grid(a.M, spans, strips), block(32, 1);
-        step_tma_kernel<1, TRACK_MAX, LC><<<grid, block, shm, s>>>(t);
+        step_tma_kernel<1, TRACK_MAX, LC, LIM><<<grid, block, shm, s>>>(t);
     }
 }
 
@@ -146,16 +146,21 @@ void launch_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
 int launch_step_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
 {
     const bool track = t.a.hmax_field != nullptr;
+    const bool lim = t.a.limiter != 0;
     if (t.a.lc_on) {
         if (track)
-            launch_tma<true, true>(t, members_per_cta, s);
+            lim ? launch_tma<true, true, 1>(t, members_per_cta, s)
+                : launch_tma<true, true, 0>(t, members_per_cta, s);
         else
-            launch_tma<false, true>(t, members_per_cta, s);
+            lim ? launch_tma<false, true, 1>(t, members_per_cta, s)
+                : launch_tma<false, true, 0>(t, members_per_cta, s);
     } else {
         if (track)
-            launch_tma<true, false>(t, members_per_cta, s);
+            lim ? launch_tma<true, false, 1>(t, members_per_cta, s)
+                : launch_tma<true, false, 0>(t, members_per_cta, s);
         else
-            launch_tma<false, false>(t, members_per_cta, s);
+            lim ? launch_tma<false, false, 1>(t, members_per_cta, s)
+                : launch_tma<false, false, 0>(t, members_per_cta, s);
     }
     return 0;
 }

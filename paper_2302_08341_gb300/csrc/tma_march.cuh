@@ -62,7 +62,7 @@ __device__ __forceinline__ void tma_store4(float* p, const float (&v)[4])
 // the class's share of the rain and its drainage).  Each is a separate
 // instantiation, so the plain step carries no trace of them.  Returns false
 // if a wait gave up.
-template <bool TRACK_MAX, bool LC = false>
+template <bool TRACK_MAX, bool LC = false, int LIM = -1>
 __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CUtensorMap* static_map,
                                           int plane0, uint32_t bar0, unsigned char* my_stages,
                                           float* __restrict__ dst, float* ck, float* hm, int* err,
@@ -183,7 +183,7 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 qyN[j] = (c + j < nx)
-                             ? link_q(hU[j], zU[j], hC[j], zC[j], qU[j],
+                             ? link_q<LIM>(hU[j], zU[j], hC[j], zC[j], qU[j],
                                       __fmul_rn(s_half, __fadd_rn(nU[j], nC[j])), k)
                              : 0.0f;
             release(r0 - 1);
@@ -194,6 +194,7 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
     bool bad = false;
     float out_s = 0.0f, out_c = 0.0f, clamp = 0.0f, drn_s = 0.0f, drn_c = 0.0f;
 
+#pragma unroll 2
     for (int r = r0; r < r1; ++r) {
         const size_t o = (size_t)r * ld + c;
         const bool has_s = (r + 1 < ny);
@@ -245,17 +246,17 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
         }
         float qxE[4], qyS[4];
         if (interior)
-            row_links<true>(hC, zC, nC, hS, zS, nS, qxo, qyo, hE, zE, nE, has_s, c, nx, s, s_half, k,
+            row_links<true, LIM>(hC, zC, nC, hS, zS, nS, qxo, qyo, hE, zE, nE, has_s, c, nx, s, s_half, k,
                             east_out, south_out, qxE, qyS);
         else
-            row_links<false>(hC, zC, nC, hS, zS, nS, qxo, qyo, hE, zE, nE, has_s, c, nx, s, s_half, k,
+            row_links<false, LIM>(hC, zC, nC, hS, zS, nS, qxo, qyo, hE, zE, nE, has_s, c, nx, s, s_half, k,
                              east_out, south_out, qxE, qyS);
         float qW0 = __shfl_up_sync(0xffffffffu, qxE[3], 1);
         if (lane == 0) {
             qW0 = (r >= k.in_r0 && r < k.in_r1) ? k.q_in : 0.0f;  // west edge: wall or inflow
             if (c0 > 0) {  // the neighbouring span's last link, from the tile's halo
                 const float nW = LC ? nWl : P[kN + 3];
-                qW0 = link_q(P[3], P[kZ + 3], hC[0], zC[0], P[kBox + 3],
+                qW0 = link_q<LIM>(P[3], P[kZ + 3], hC[0], zC[0], P[kBox + 3],
                              __fmul_rn(s_half, __fadd_rn(nW, nC[0])), k);
             }
         }
