@@ -45,6 +45,7 @@ KERNEL_SOURCES = ["paper_2302_08341_gb300/csrc/step_kernel.cu",
                   "paper_2302_08341_gb300/csrc/step_tma.cu",
                   "paper_2302_08341_gb300/csrc/tma.cuh",
                   "paper_2302_08341_gb300/csrc/march.cuh",
+                  "paper_2302_08341_gb300/csrc/tma_march.cuh",
                   "paper_2302_08341_gb300/csrc/flood_internal.cuh"]
 BYTES_SINGLE = BYTES_STATE + BYTES_STATIC  # one member per static-field pass
 
