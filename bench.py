@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 
 NY = NX = 2000
 M = 96
+ROWS = None
 G = 6
 WINDOW = 300.0
 SEED = 1
@@ -68,11 +69,13 @@ def parse():
     ap.add_argument("--only", choices=["adjoint", "batch", "calibration", "land_cover"],
                     help="run one extension measurement alone and print it (profiling runs)")
     ap.add_argument("--calibration-windows", type=int, default=3)
+    ap.add_argument("--rows-per-strip", type=int, default=None,
+                    help="strip height for --only calibration (profiling smaller cases)")
     ap.add_argument("--engine", type=int, choices=[0, 1], default=None,
                     help="step-kernel engine for --only batch (default: the library's)")
     args = ap.parse_args()
-    global NY, NX, M
-    NY, NX, M = args.ny, args.nx, args.members
+    global NY, NX, M, ROWS
+    NY, NX, M, ROWS = args.ny, args.nx, args.members, args.rows_per_strip
     return args
 
 
@@ -355,6 +358,8 @@ def calibration_measure(capi, windows=3):
     with capi.Grid(terr.z, terr.n) as g:
         g.ensemble_init(M, rm, sc, hy, stream=stream)
         g.set_roughness_factor(np.ones((64, 64), np.float32), stream=stream)
+        if ROWS:
+            g.set_launch(ROWS, 4 if M >= 4 else 1)
         for w in range(1, windows + 1):
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             s0 = g.members()["steps"].sum()

@@ -211,10 +211,11 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
                           cudaMemcpyHostToDevice, s));
     CK(g, cudaMemcpyAsync(g->samp_d, d.data(), sizeof(double) * ns * G, cudaMemcpyHostToDevice, s));
 
-    // tensor maps of the TMA-staged reverse stencil (direct loads otherwise)
+    // tensor maps of the TMA-staged replay and reverse stencil (direct loads
+    // otherwise); short strips never fill the reverse stencil's copy
+    // pipeline, so those keep its direct-load form
     flood::AdjTmaArgs tma{};
-    // (short strips never fill the copy pipeline: direct loads do better there)
-    bool use_tma = g->engine == 1 && g->maps_ok && g->rows_per_strip >= 16;
+    bool use_tma = g->engine == 1 && g->maps_ok;
     if (use_tma) {
         const int bc = flood::adjoint_tma_box_cols();
         const uint64_t s1 = sizeof(float) * g->ld, s2 = sizeof(float) * g->plane;
@@ -229,6 +230,8 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
                                              bc, 1, 1) == 0);
         tma.static_map = g->static_map;
     }
+    const bool tma_replay = use_tma;
+    const bool tma_reverse = use_tma && g->rows_per_strip >= 16;
 
     const int kmax = *std::max_element(K_m.begin(), K_m.end());
     const int n_seg = (kmax + K - 1) / K;
@@ -252,9 +255,19 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
         a.seg = g->seg;
         a.seg_end = g->seg_end;
         a.seg_first = first;
+        flood::TmaArgs rt;
+        if (tma_replay) {
+            rt.state_map = tma.seg_map;
+            rt.static_map = g->static_map;
+        }
         for (int i = 0; i < len; ++i) {
             a.replay_i = i;
-            flood::launch_replay(a, g->members_per_cta, s);
+            if (tma_replay) {
+                rt.a = a;
+                flood::launch_replay_tma(rt, g->members_per_cta, s);
+            } else {
+                flood::launch_replay(a, g->members_per_cta, s);
+            }
             g->launches++;
         }
         flood::AdjArgs b{};
@@ -285,7 +298,7 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
             b.rev_i = i;
             b.lam_in = lam_in;
             flood::launch_seed(b, g->samp_step, g->samp_y, g->samp_d, g->samp_cells, ns, G, s);
-            if (use_tma) {
+            if (tma_reverse) {
                 tma.a = b;
                 flood::launch_adjoint_tma(tma, g->members_per_cta, s);
             } else {

@@ -38,7 +38,7 @@ __device__ __forceinline__ void store4(float* p, const float (&v)[4])
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
-template <int WM, int WC>
+template <int WM, int WC, int LIM>
 __global__ void __launch_bounds__(32 * WM * WC, 4) adjoint_kernel(const AdjArgs a)
 {
     const int lane = threadIdx.x;
@@ -78,10 +78,10 @@ __global__ void __launch_bounds__(32 * WM * WC, 4) adjoint_kernel(const AdjArgs 
     k.limiter = a.limiter;
     k.q_in = 0.0f;  // no inflow boundary here
     k.in_r0 = k.in_r1 = 0;
-    const float L = k.dx_4dt;
     const float T = pl.dt_dx;
     const float s = a.scale[m];
     const float s_half = 0.5f * s;
+    const bool interior = c0 + kSpan < nx;  // no east edge in this span
 
     const float* __restrict__ st = a.seg + ((size_t)(j - a.seg_first) * a.M + m) * mstride;
     const float* __restrict__ sh = st;
@@ -109,13 +109,13 @@ __global__ void __launch_bounds__(32 * WM * WC, 4) adjoint_kernel(const AdjArgs 
             load4(lqU, lin + 2 * plane + u); load4(haU, h1p + u); load4(lhU, lin + u);
 #pragma unroll
             for (int q = 0; q < 4; ++q) lU[q] = masked(haU[q], lhU[q]);
-            north_carry(hU, zU, nU, qU, lqU, lU, hC, zC, nC, lC, c, nx, s_half, T, L, k, carH,
-                        carN);
+            north_carry<LIM>(hU, zU, nU, qU, lqU, lU, hC, zC, nC, lC, c, nx, s_half, T, k, carH,
+                             carN);
         }
     }
 
-    // FP32 compensated partials (sum of lambda~ for the rain gradient, of
-    // mu * dq'/dn * n for the scale gradient), widened to FP64 once per warp
+    // FP32 compensated sums of the rows' partials (lambda~ for the rain
+    // gradient, mu n dq'/dn for the scale gradient), widened to FP64 once per warp
     float gr_s = 0.0f, gr_c = 0.0f, gs_s = 0.0f, gs_c = 0.0f;
     for (int r = r0; r < r1; ++r) {
         const size_t o = (size_t)r * ld + c;
@@ -150,9 +150,17 @@ __global__ void __launch_bounds__(32 * WM * WC, 4) adjoint_kernel(const AdjArgs 
             wi.l = masked(__ldg(h1p + w), __ldg(lin + w));
         }
         float lh[4], lx[4], ly[4], gnr[4];
-        adjoint_row(hC, zC, nC, lC, hS, zS, nS, lS, qxo, qyo, lqx, lqy, hE, zE, nE, lE, c0 > 0, wi,
-                    has_s, c, nx, lane, s, s_half, T, L, k, a.east_out, a.south_out, carH, carN,
-                    gr_s, gr_c, gs_s, gs_c, lh, lx, ly, gnr);
+        float gr_row = 0.0f, gs_row = 0.0f;
+        if (interior)
+            adjoint_row<true, LIM>(hC, zC, nC, lC, hS, zS, nS, lS, qxo, qyo, lqx, lqy, hE, zE, nE,
+                                   lE, c0 > 0, wi, has_s, c, nx, lane, s, s_half, T, k, a.east_out,
+                                   a.south_out, carH, carN, gr_row, gs_row, lh, lx, ly, gnr);
+        else
+            adjoint_row<false, LIM>(hC, zC, nC, lC, hS, zS, nS, lS, qxo, qyo, lqx, lqy, hE, zE, nE,
+                                    lE, c0 > 0, wi, has_s, c, nx, lane, s, s_half, T, k, a.east_out,
+                                    a.south_out, carH, carN, gr_row, gs_row, lh, lx, ly, gnr);
+        kahan_add(gr_s, gr_c, gr_row);
+        kahan_add(gs_s, gs_c, gs_row);
         if (act) {
             store4(lout + o, lh);
             store4(lout + plane + o, lx);
@@ -169,7 +177,7 @@ __global__ void __launch_bounds__(32 * WM * WC, 4) adjoint_kernel(const AdjArgs 
         }
     }
     adjoint_partials(a.gpart, a.nslot, m, blockIdx.z * ((a.nx + kSpan - 1) / kSpan) + span, lane,
-                     gr_s, gr_c, gs_s, gs_c, pl.rdt);
+                     gr_s, gr_c, gs_s, gs_c, pl.rdt, 1.0 / (double)s);
 }
 
 // Loss sensitivity at observation times: the state after step j is observed
@@ -205,19 +213,28 @@ __global__ void reduce_members_kernel(const float* __restrict__ gm, int M, int n
     out[t] = acc;
 }
 
-}  // namespace
-
-void launch_adjoint(const AdjArgs& a, int members_per_cta, cudaStream_t s)
+template <int LIM>
+void launch_adjoint_lim(const AdjArgs& a, int members_per_cta, cudaStream_t s)
 {
     const int spans = (a.nx + kSpan - 1) / kSpan;
     const int strips = (a.ny + a.rows_per_strip - 1) / a.rows_per_strip;
     if (members_per_cta >= 4) {
         dim3 grid((a.M + 3) / 4, spans, strips), block(32, 4);
-        adjoint_kernel<4, 1><<<grid, block, 0, s>>>(a);
+        adjoint_kernel<4, 1, LIM><<<grid, block, 0, s>>>(a);
     } else {
         dim3 grid(a.M, (spans + 3) / 4, strips), block(32, 4);
-        adjoint_kernel<1, 4><<<grid, block, 0, s>>>(a);
+        adjoint_kernel<1, 4, LIM><<<grid, block, 0, s>>>(a);
     }
+}
+
+}  // namespace
+
+void launch_adjoint(const AdjArgs& a, int members_per_cta, cudaStream_t s)
+{
+    if (a.limiter)
+        launch_adjoint_lim<1>(a, members_per_cta, s);
+    else
+        launch_adjoint_lim<0>(a, members_per_cta, s);
 }
 
 void launch_seed(const AdjArgs& a, const int32_t* sample_step, const float* y, const double* d,

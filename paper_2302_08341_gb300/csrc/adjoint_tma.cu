@@ -52,7 +52,7 @@ __device__ __forceinline__ void store4(float* p, const float (&v)[4])
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
-template <int WM>
+template <int WM, int LIM>
 __global__ void __launch_bounds__(32 * WM, WM == 4 ? 3 : 12) adjoint_tma_kernel(
     const __grid_constant__ AdjTmaArgs t)
 {
@@ -96,10 +96,10 @@ __global__ void __launch_bounds__(32 * WM, WM == 4 ? 3 : 12) adjoint_tma_kernel(
     k.limiter = a.limiter;
     k.q_in = 0.0f;  // no inflow boundary here
     k.in_r0 = k.in_r1 = 0;
-    const float L = k.dx_4dt;
     const float T = pl.dt_dx;
     const float s = a.scale[m];
     const float s_half = 0.5f * s;
+    const bool interior = c0 + kSpan < nx;  // no east edge in this span
     float* __restrict__ gn = a.gn ? a.gn + (size_t)m * plane : nullptr;
 
     unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -198,14 +198,14 @@ __global__ void __launch_bounds__(32 * WM, WM == 4 ? 3 : 12) adjoint_tma_kernel(
 #pragma unroll
             for (int q = 0; q < 4; ++q) lU[q] = masked(haU[q], lhU[q]);
             if (act)
-                north_carry(hU, zU, nU, qU, lqU, lU, hC, zC, nC, lC, c, nx, s_half, T, L, k,
-                            carH, carN);
+                north_carry<LIM>(hU, zU, nU, qU, lqU, lU, hC, zC, nC, lC, c, nx, s_half, T, k,
+                                 carH, carN);
             release();
         }
     }
 
-    // FP32 compensated partials (sum of lambda~ for the rain gradient, of
-    // mu * dq'/dn * n for the scale gradient), widened to FP64 once per warp
+    // FP32 compensated sums of the rows' partials (lambda~ for the rain
+    // gradient, mu n dq'/dn for the scale gradient), widened to FP64 once per warp
     float gr_s = 0.0f, gr_c = 0.0f, gs_s = 0.0f, gs_c = 0.0f;
     for (int r = r0; r < r1; ++r) {
         const size_t o = (size_t)r * ld + c;
@@ -246,9 +246,17 @@ __global__ void __launch_bounds__(32 * WM, WM == 4 ? 3 : 12) adjoint_tma_kernel(
             wi.l = masked(P[kHa + 3], P[kLam + 3]);
         }
         float lh[4], lx[4], ly[4], gnr[4];
-        adjoint_row(hC, zC, nC, lC, hS, zS, nS, lS, qxo, qyo, lqx, lqy, hE, zE, nE, lE, c0 > 0, wi,
-                    has_s, c, nx, lane, s, s_half, T, L, k, a.east_out, a.south_out, carH, carN,
-                    gr_s, gr_c, gs_s, gs_c, lh, lx, ly, gnr);
+        float gr_row = 0.0f, gs_row = 0.0f;
+        if (interior)
+            adjoint_row<true, LIM>(hC, zC, nC, lC, hS, zS, nS, lS, qxo, qyo, lqx, lqy, hE, zE, nE,
+                                   lE, c0 > 0, wi, has_s, c, nx, lane, s, s_half, T, k, a.east_out,
+                                   a.south_out, carH, carN, gr_row, gs_row, lh, lx, ly, gnr);
+        else
+            adjoint_row<false, LIM>(hC, zC, nC, lC, hS, zS, nS, lS, qxo, qyo, lqx, lqy, hE, zE, nE,
+                                    lE, c0 > 0, wi, has_s, c, nx, lane, s, s_half, T, k, a.east_out,
+                                    a.south_out, carH, carN, gr_row, gs_row, lh, lx, ly, gnr);
+        kahan_add(gr_s, gr_c, gr_row);
+        kahan_add(gs_s, gs_c, gs_row);
         if (act) {
             store4(lout + o, lh);
             store4(lout + plane + o, lx);
@@ -268,7 +276,7 @@ __global__ void __launch_bounds__(32 * WM, WM == 4 ? 3 : 12) adjoint_tma_kernel(
         release();
     }
     adjoint_partials(a.gpart, a.nslot, m, blockIdx.z * ((a.nx + kSpan - 1) / kSpan) + span, lane,
-                     gr_s, gr_c, gs_s, gs_c, pl.rdt);
+                     gr_s, gr_c, gs_s, gs_c, pl.rdt, 1.0 / (double)s);
 }
 
 template <int WM>
@@ -277,9 +285,8 @@ size_t adj_smem_bytes()
     return 128 + 128 * ((8 * kNS * WM + 127) / 128) + (size_t)kNS * kStageBytes * WM;
 }
 
-}  // namespace
-
-void launch_adjoint_tma(const AdjTmaArgs& t, int members_per_cta, cudaStream_t s)
+template <int LIM>
+void launch_adjoint_tma_lim(const AdjTmaArgs& t, int members_per_cta, cudaStream_t s)
 {
     const AdjArgs& a = t.a;
     const int spans = (a.nx + kSpan - 1) / kSpan;
@@ -288,17 +295,27 @@ void launch_adjoint_tma(const AdjTmaArgs& t, int members_per_cta, cudaStream_t s
         static bool attr = false;
         const size_t shm = adj_smem_bytes<4>();
         if (!attr) {
-            cudaFuncSetAttribute(adjoint_tma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)shm);
+            cudaFuncSetAttribute(adjoint_tma_kernel<4, LIM>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
             attr = true;
         }
         dim3 grid((a.M + 3) / 4, spans, strips), block(32, 4);
-        adjoint_tma_kernel<4><<<grid, block, shm, s>>>(t);
+        adjoint_tma_kernel<4, LIM><<<grid, block, shm, s>>>(t);
     } else {
         const size_t shm = adj_smem_bytes<1>();
         dim3 grid(a.M, spans, strips), block(32, 1);
-        adjoint_tma_kernel<1><<<grid, block, shm, s>>>(t);
+        adjoint_tma_kernel<1, LIM><<<grid, block, shm, s>>>(t);
     }
+}
+
+}  // namespace
+
+void launch_adjoint_tma(const AdjTmaArgs& t, int members_per_cta, cudaStream_t s)
+{
+    if (t.a.limiter)
+        launch_adjoint_tma_lim<1>(t, members_per_cta, s);
+    else
+        launch_adjoint_tma_lim<0>(t, members_per_cta, s);
 }
 
 int adjoint_tma_box_cols() { return kBox; }

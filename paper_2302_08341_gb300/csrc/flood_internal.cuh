@@ -322,6 +322,8 @@ void launch_step(const StepArgs& a, int members_per_cta, cudaStream_t s);
 void launch_step_per_member(const StepArgs& a, cudaStream_t s);
 void launch_replay(const StepArgs& a, int members_per_cta, cudaStream_t s);
 int launch_step_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s);
+// t.state_map over the adjoint's segment slots (box: 3 planes)
+void launch_replay_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s);
 int tma_box_cols();
 int step_nslot(int ny, int nx, int rows_per_strip);
 

@@ -83,6 +83,52 @@ __global__ void __launch_bounds__(32 * WM, (LC ? 16 : 20) / WM) step_tma_kernel(
     }
 }
 
+// Replay of a logged step of a checkpointed segment for the adjoint: the
+// same march as step_tma_kernel (so the recomputed states agree bit for bit
+// with the forward's), reading the segment's slot replay_i and writing slot
+// replay_i + 1, with the member's plan taken from the step log.
+template <int WM, int LIM>
+__global__ void __launch_bounds__(32 * WM, 20 / WM) replay_tma_kernel(const __grid_constant__ TmaArgs t)
+{
+    extern __shared__ unsigned char smem_raw[];
+    const StepArgs& a = t.a;
+    const int lane = threadIdx.x;
+    const int w = threadIdx.y;
+    const int m = blockIdx.x * WM + w;
+    const int c0 = blockIdx.y * kSpan;
+    if (m >= a.M || c0 >= a.nx) return;  // whole warps; no block-wide barriers below
+    if (*reinterpret_cast<volatile const int*>(a.err) & 2) return;
+    const int j = a.seg_first + a.replay_i;
+    if (j >= a.seg_end[m]) return;
+
+    uint32_t bar0;
+    unsigned char* my_stages;
+    tma_march_smem(smem_raw, WM, w, bar0, my_stages);
+
+    const size_t mstride = 3 * a.plane;
+    const MemberPlan pl = a.log[(size_t)m * a.dt_log_cap + j];
+    float* __restrict__ dst = a.seg + ((size_t)(a.replay_i + 1) * a.M + m) * mstride;
+    FaceK k;
+    k.gdt_dx = pl.gdt_dx;
+    k.gdt = pl.gdt;
+    k.dx_4dt = pl.dx_4dt;
+    k.h_eps = a.h_eps;
+    k.edge_drop = a.edge_drop;
+    k.limiter = a.limiter;
+    k.q_in = pl.q_in;
+    k.in_r0 = a.in_r0;
+    k.in_r1 = a.in_r1;
+    const int r0 = blockIdx.z * a.rows_per_strip;
+    const int r1 = min(r0 + a.rows_per_strip, a.ny);
+    MarchOut mo;
+    if (!tma_march<false, false, LIM>(&t.state_map, &t.static_map, (a.replay_i * a.M + m) * 3, bar0,
+                                      my_stages, dst, nullptr, nullptr, a.err, a.plane, a.ny, a.nx,
+                                      a.ld, c0, r0, r1, lane, k, pl.dt_dx, a.scale[m], pl.dr,
+                                      a.east_out, a.south_out, mo))
+        return;
+    if (mo.bad) atomicOr(a.err, 1);
+}
+
 template <int WM>
 size_t tma_smem_bytes()
 {
@@ -141,7 +187,38 @@ void launch_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
     }
 }
 
+template <int LIM>
+void launch_replay_lim(const TmaArgs& t, int members_per_cta, cudaStream_t s)
+{
+    const StepArgs& a = t.a;
+    const int spans = (a.nx + kSpan - 1) / kSpan;
+    const int strips = (a.ny + a.rows_per_strip - 1) / a.rows_per_strip;
+    if (members_per_cta >= 4) {
+        static bool attr = false;
+        const size_t shm = tma_smem_bytes<4>();
+        if (!attr) {
+            cudaFuncSetAttribute(replay_tma_kernel<4, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)shm);
+            attr = true;
+        }
+        dim3 grid((a.M + 3) / 4, spans, strips), block(32, 4);
+        replay_tma_kernel<4, LIM><<<grid, block, shm, s>>>(t);
+    } else {
+        const size_t shm = tma_smem_bytes<1>();
+        dim3 grid(a.M, spans, strips), block(32, 1);
+        replay_tma_kernel<1, LIM><<<grid, block, shm, s>>>(t);
+    }
+}
+
 }  // namespace
+
+void launch_replay_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
+{
+    if (t.a.limiter)
+        launch_replay_lim<1>(t, members_per_cta, s);
+    else
+        launch_replay_lim<0>(t, members_per_cta, s);
+}
 
 int launch_step_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
 {
