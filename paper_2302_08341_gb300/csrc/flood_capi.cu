@@ -191,7 +191,8 @@ int launch_steps(flood_grid* g, int64_t count, double t_end, cudaStream_t s)
             t.state_map = g->state_map;
             t.static_map = g->static_map;
             t.a = a;
-            flood::launch_step_tma(t, g->members_per_cta, s);
+            if (flood::launch_step_tma(t, g->members_per_cta, s))
+                return fail(g, FLOOD_ERR_STATE, "checkpointed steps do not cover land cover");
         } else if (g->engine == 2 && !g->lc_on) {
             flood::launch_step_per_member(a, s);
             g->launches += g->M - 1;

@@ -14,7 +14,9 @@ constexpr int kSpan = kTmaSpan;
 
 // The land-cover form holds its class tables in registers: it gets more of
 // them (four CTAs of four warps per SM instead of five) rather than spill.
-template <int WM, bool TRACK_MAX, bool LC, int LIM>
+// CK: the step may write checkpoints (the adjoint's logged forward); the
+// ordinary step is compiled without that path.
+template <int WM, bool TRACK_MAX, bool LC, int LIM, bool CK>
 __global__ void __launch_bounds__(32 * WM, (LC ? 16 : 20) / WM) step_tma_kernel(const __grid_constant__ TmaArgs t)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -36,7 +38,7 @@ __global__ void __launch_bounds__(32 * WM, (LC ? 16 : 20) / WM) step_tma_kernel(
     const MemberPlan pl = a.plan[m];
     if (!pl.active) return;
     float* __restrict__ dst = a.state + (size_t)((1 - pl.cur) * a.M + m) * mstride;
-    float* ck = pl.ckpt >= 0 ? a.ckpt + ((size_t)pl.ckpt * a.M + m) * mstride : nullptr;
+    float* ck = (CK && pl.ckpt >= 0) ? a.ckpt + ((size_t)pl.ckpt * a.M + m) * mstride : nullptr;
 
     FaceK k;
     k.gdt_dx = pl.gdt_dx;
@@ -164,7 +166,7 @@ int tma_box_cols() { return kTmaBox; }
 
 namespace {
 
-template <bool TRACK_MAX, bool LC, int LIM>
+template <bool TRACK_MAX, bool LC, int LIM, bool CK>
 void launch_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
 {
     const StepArgs& a = t.a;
@@ -174,16 +176,16 @@ void launch_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
         static bool attr = false;
         const size_t shm = tma_smem_bytes<4>();
         if (!attr) {
-            cudaFuncSetAttribute(step_tma_kernel<4, TRACK_MAX, LC, LIM>,
+            cudaFuncSetAttribute(step_tma_kernel<4, TRACK_MAX, LC, LIM, CK>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
             attr = true;
         }
         dim3 grid((a.M + 3) / 4, spans, strips), block(32, 4);
-        step_tma_kernel<4, TRACK_MAX, LC, LIM><<<grid, block, shm, s>>>(t);
+        step_tma_kernel<4, TRACK_MAX, LC, LIM, CK><<<grid, block, shm, s>>>(t);
     } else {
         const size_t shm = tma_smem_bytes<1>();
         dim3 grid(a.M, spans, strips), block(32, 1);
-        step_tma_kernel<1, TRACK_MAX, LC, LIM><<<grid, block, shm, s>>>(t);
+        step_tma_kernel<1, TRACK_MAX, LC, LIM, CK><<<grid, block, shm, s>>>(t);
     }
 }
 
@@ -224,20 +226,28 @@ int launch_step_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
 {
     const bool track = t.a.hmax_field != nullptr;
     const bool lim = t.a.limiter != 0;
-    if (t.a.lc_on) {
+    if (t.a.ckpt) {  // the adjoint's logged forward, which land cover never reaches
+        if (t.a.lc_on) return -1;
         if (track)
-            lim ? launch_tma<true, true, 1>(t, members_per_cta, s)
-                : launch_tma<true, true, 0>(t, members_per_cta, s);
+            lim ? launch_tma<true, false, 1, true>(t, members_per_cta, s)
+                : launch_tma<true, false, 0, true>(t, members_per_cta, s);
         else
-            lim ? launch_tma<false, true, 1>(t, members_per_cta, s)
-                : launch_tma<false, true, 0>(t, members_per_cta, s);
+            lim ? launch_tma<false, false, 1, true>(t, members_per_cta, s)
+                : launch_tma<false, false, 0, true>(t, members_per_cta, s);
+    } else if (t.a.lc_on) {
+        if (track)
+            lim ? launch_tma<true, true, 1, false>(t, members_per_cta, s)
+                : launch_tma<true, true, 0, false>(t, members_per_cta, s);
+        else
+            lim ? launch_tma<false, true, 1, false>(t, members_per_cta, s)
+                : launch_tma<false, true, 0, false>(t, members_per_cta, s);
     } else {
         if (track)
-            lim ? launch_tma<true, false, 1>(t, members_per_cta, s)
-                : launch_tma<true, false, 0>(t, members_per_cta, s);
+            lim ? launch_tma<true, false, 1, false>(t, members_per_cta, s)
+                : launch_tma<true, false, 0, false>(t, members_per_cta, s);
         else
-            lim ? launch_tma<false, false, 1>(t, members_per_cta, s)
-                : launch_tma<false, false, 0>(t, members_per_cta, s);
+            lim ? launch_tma<false, false, 1, false>(t, members_per_cta, s)
+                : launch_tma<false, false, 0, false>(t, members_per_cta, s);
     }
     return 0;
 }
