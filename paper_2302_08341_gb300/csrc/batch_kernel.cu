@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(32 * W) batch_step_kernel(const BatchArgs a)
                                    tk.r0, tk.r1, lane, k, p.dt_dx, sd.scale, p.dr, a.east_out,
                                    a.south_out);
     if (mo.bad) atomicOr(a.err, 1);
-    const unsigned hb = __reduce_max_sync(0xffffffffu, __float_as_uint(mo.hmax) & 0x7fffffffu);
+    const unsigned hb = __reduce_max_sync(0xffffffffu, mo.bad ? 0u : __float_as_uint(mo.hmax) & 0x7fffffffu);
     double out_acc = (double)mo.out_s - (double)mo.out_c, clamp_acc = (double)mo.clamp;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(32 * W, 20 / W) batch_tma_kernel(const BatchAr
                    sd.scale, p.dr, a.east_out, a.south_out, mo))
         return;
     if (mo.bad) atomicOr(a.err, 1);
-    const unsigned hb = __reduce_max_sync(0xffffffffu, __float_as_uint(mo.hmax) & 0x7fffffffu);
+    const unsigned hb = __reduce_max_sync(0xffffffffu, mo.bad ? 0u : __float_as_uint(mo.hmax) & 0x7fffffffu);
     double out_acc = (double)mo.out_s - (double)mo.out_c, clamp_acc = (double)mo.clamp;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {

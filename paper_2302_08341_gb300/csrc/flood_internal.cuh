@@ -197,6 +197,13 @@ __device__ __forceinline__ float ex2_approx(float x)
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+// max that propagates a NaN operand (fmaxf returns the other one)
+__device__ __forceinline__ float fmax_nan(float a, float b)
+{
+    float y;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(y) : "f"(a), "f"(b));
+    return y;
+}
 __device__ __forceinline__ float rcp_approx(float x)
 {
     float y;

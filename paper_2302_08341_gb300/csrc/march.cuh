@@ -79,7 +79,7 @@ template <bool INTERIOR, bool LC = false>
 __device__ __forceinline__ void row_depths(const float (&hC)[4], const float (&qxE)[4],
                                            const float (&qyN)[4], const float (&qyS)[4], float qW0,
                                            int c, int nx, float dt_dx, float dr, float& clamp,
-                                           float& hmax, float& hsum, float (&hN)[4],
+                                           float& hmax, float (&hN)[4],
                                            const float* drv = nullptr, const float* ddv = nullptr,
                                            float* drn_s = nullptr, float* drn_c = nullptr)
 {
@@ -101,9 +101,8 @@ __device__ __forceinline__ void row_depths(const float (&hC)[4], const float (&q
                 clamp = __fsub_rn(clamp, hn);
                 hn = -0.0f;
             }
-            hmax = fmaxf(hmax, hn);
+            hmax = fmax_nan(hmax, hn);  // a NaN anywhere stays in the maximum
         }
-        hsum += hn;
         hN[j] = hn;
     }
 }
@@ -179,7 +178,6 @@ __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, fl
     }
 
     float hmax = 0.0f;
-    bool bad = false;
     float out_s = 0.0f, out_c = 0.0f, clamp = 0.0f, drn_s = 0.0f, drn_c = 0.0f;
 
 #pragma unroll 2
@@ -242,14 +240,12 @@ __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, fl
             }
         }
         float hN[4];
-        float hsum = 0.0f;
         if (interior)
-            row_depths<true, LC>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN,
+            row_depths<true, LC>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hN,
                                  drv, ddv, &drn_s, &drn_c);
         else
-            row_depths<false, LC>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN,
+            row_depths<false, LC>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hN,
                                   drv, ddv, &drn_s, &drn_c);
-        bad |= !(hsum <= 3.0e38f);  // a NaN or overflow anywhere in the row
         // links leaving the domain this row: the east edge link (one lane)
         // and, on the last row, the south edge links
         float ev = 0.0f;
@@ -290,7 +286,7 @@ __device__ __forceinline__ MarchOut march_rows(const float* __restrict__ src, fl
 
     MarchOut out;
     out.hmax = hmax;
-    out.bad = bad;
+    out.bad = !(hmax <= 3.0e38f);  // a NaN or an overflow anywhere
     out.out_s = out_s;
     out.out_c = out_c;
     out.clamp = clamp;

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(32 * WM * WC, (LC ? 4 : FLOOD_STEP_MIN_BLOCKS)
     if (REPLAY) return;
     // warp reductions: max depth (order-free); volume partials widened to
     // FP64 once per warp and reduced in a fixed order
-    const unsigned hb = __reduce_max_sync(0xffffffffu, __float_as_uint(mo.hmax) & 0x7fffffffu);
+    const unsigned hb = __reduce_max_sync(0xffffffffu, mo.bad ? 0u : __float_as_uint(mo.hmax) & 0x7fffffffu);
     double out_acc = (double)mo.out_s - (double)mo.out_c, clamp_acc = (double)mo.clamp;
     double drn_acc = LC ? (double)mo.drn_s - (double)mo.drn_c : 0.0;
 #pragma unroll

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(32 * WM, (LC ? 16 : 20) / WM) step_tma_kernel(
         return;
 
     if (mo.bad) atomicOr(a.err, 1);
-    const unsigned hb = __reduce_max_sync(0xffffffffu, __float_as_uint(mo.hmax) & 0x7fffffffu);
+    const unsigned hb = __reduce_max_sync(0xffffffffu, mo.bad ? 0u : __float_as_uint(mo.hmax) & 0x7fffffffu);
     double out_acc = (double)mo.out_s - (double)mo.out_c, clamp_acc = (double)mo.clamp;
     double drn_acc = LC ? (double)mo.drn_s - (double)mo.drn_c : 0.0;
 #pragma unroll

@@ -191,7 +191,6 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
     }
 
     float hmax = 0.0f;
-    bool bad = false;
     float out_s = 0.0f, out_c = 0.0f, clamp = 0.0f, drn_s = 0.0f, drn_c = 0.0f;
 
 #pragma unroll 2
@@ -261,14 +260,12 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
             }
         }
         float hN[4];
-        float hsum = 0.0f;
         if (interior)
-            row_depths<true, LC>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN,
+            row_depths<true, LC>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hN,
                                  drv, ddv, &drn_s, &drn_c);
         else
-            row_depths<false, LC>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hsum, hN,
+            row_depths<false, LC>(hC, qxE, qyN, qyS, qW0, c, nx, dt_dx, dr, clamp, hmax, hN,
                                   drv, ddv, &drn_s, &drn_c);
-        bad |= !(hsum <= 3.0e38f);
         if ((edge_warp && east_out) || (!has_s && south_out)) {  // the same for the whole warp
             // links leaving the domain this row: the east edge link (one lane)
             // and, on the last row, the south edge links
@@ -308,7 +305,7 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
     }
 
     out.hmax = hmax;
-    out.bad = bad;
+    out.bad = !(hmax <= 3.0e38f);  // a NaN or an overflow anywhere
     out.out_s = out_s;
     out.out_c = out_c;
     out.clamp = clamp;
