@@ -255,7 +255,7 @@ class Ensemble:
         self.p, self.M = p, M
         ny, nx = p.ny, p.nx
         self.h = np.zeros((M, ny, nx)) if h0 is None else np.array(
-            np.broadcast_to(h0, (M, ny, nx)), dtype=np.float64)
+            np.broadcast_to(h0, (M, ny, nx)), dtype=np.float64, order="C")
         self.qx = np.zeros((M, ny, nx + 1))
         self.qy = np.zeros((M, ny + 1, nx))
         self.t = np.zeros(M)

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(32 * W) batch_step_kernel(const BatchArgs a)
 
 // TMA-staged form of batch_step_kernel (same results, bit for bit): the
 // task's rows stream through shared memory by the scenario's own tensor maps.
-template <int W>
+template <int W, int LIM>
 __global__ void __launch_bounds__(32 * W, 20 / W) batch_tma_kernel(const BatchArgs a)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(32 * W, 20 / W) batch_tma_kernel(const BatchAr
     tma_march_smem(smem_raw, W, w, bar0, my_stages);
     float* dst = sd.state + (size_t)(1 - p.cur) * 3 * sd.plane;
     MarchOut mo;
-    if (!tma_march<false>(a.maps + 2 * i, a.maps + 2 * i + 1, p.cur * 3, bar0, my_stages, dst, nullptr,
+    if (!tma_march<false, false, LIM>(a.maps + 2 * i, a.maps + 2 * i + 1, p.cur * 3, bar0, my_stages, dst, nullptr,
                    nullptr, a.err, sd.plane, sd.ny, sd.nx, sd.ld, tk.c0, tk.r0, tk.r1, lane, k, p.dt_dx,
                    sd.scale, p.dr, a.east_out, a.south_out, mo))
         return;
@@ -141,20 +141,33 @@ __global__ void __launch_bounds__(32 * W, 20 / W) batch_tma_kernel(const BatchAr
 
 int batch_tma_prepare()
 {
-    cudaError_t e = cudaFuncSetAttribute(batch_tma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tma_march_smem_bytes(4));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(batch_tma_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tma_march_smem_bytes(8));
+    cudaError_t e = cudaSuccess;
+    for (auto f : {batch_tma_kernel<4, 0>, batch_tma_kernel<4, 1>})
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)tma_march_smem_bytes(4));
+    for (auto f : {batch_tma_kernel<8, 0>, batch_tma_kernel<8, 1>})
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)tma_march_smem_bytes(8));
     return e == cudaSuccess ? 0 : -1;
 }
 
+// the limiter is fixed at compile time (one instantiation per setting)
 void launch_batch_step_tma(const BatchArgs& a, int warps_per_cta, cudaStream_t s)
 {
-    if (warps_per_cta >= 8)
-        batch_tma_kernel<8><<<(a.ntasks + 7) / 8, dim3(32, 8), tma_march_smem_bytes(8), s>>>(a);
-    else
-        batch_tma_kernel<4><<<(a.ntasks + 3) / 4, dim3(32, 4), tma_march_smem_bytes(4), s>>>(a);
+    const unsigned g8 = (a.ntasks + 7) / 8, g4 = (a.ntasks + 3) / 4;
+    if (warps_per_cta >= 8) {
+        if (a.limiter)
+            batch_tma_kernel<8, 1><<<g8, dim3(32, 8), tma_march_smem_bytes(8), s>>>(a);
+        else
+            batch_tma_kernel<8, 0><<<g8, dim3(32, 8), tma_march_smem_bytes(8), s>>>(a);
+    } else {
+        if (a.limiter)
+            batch_tma_kernel<4, 1><<<g4, dim3(32, 4), tma_march_smem_bytes(4), s>>>(a);
+        else
+            batch_tma_kernel<4, 0><<<g4, dim3(32, 4), tma_march_smem_bytes(4), s>>>(a);
+    }
 }
 
 void launch_batch_plan(const BatchArgs& a, int n_scen, cudaStream_t s)
