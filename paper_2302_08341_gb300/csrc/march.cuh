@@ -83,6 +83,7 @@ __device__ __forceinline__ void row_depths(const float (&hC)[4], const float (&q
                                            const float* drv = nullptr, const float* ddv = nullptr,
                                            float* drn_s = nullptr, float* drn_c = nullptr)
 {
+    float row_sink = 0.0f;  // LC: the row's drained depth, compensated once per row
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         float hn = 0.0f;
@@ -93,7 +94,7 @@ __device__ __forceinline__ void row_depths(const float (&hC)[4], const float (&q
                 hn = __fadd_rn(__fmaf_rn(dt_dx, net, hC[j]), drv[j]);
                 const float sink = fminf(ddv[j], fmaxf(hn, 0.0f));
                 hn = __fsub_rn(hn, sink);
-                kahan_add(*drn_s, *drn_c, sink);
+                row_sink = __fadd_rn(row_sink, sink);
             } else {
                 hn = __fadd_rn(__fmaf_rn(dt_dx, net, hC[j]), dr);
             }
@@ -105,6 +106,7 @@ __device__ __forceinline__ void row_depths(const float (&hC)[4], const float (&q
         }
         hN[j] = hn;
     }
+    if (LC) kahan_add(*drn_s, *drn_c, row_sink);
 }
 
 template <bool LC = false>

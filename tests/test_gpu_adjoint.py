@@ -154,13 +154,14 @@ def test_autograd_function_returns_the_adjoint_gradients(capi):
     assert np.allclose(h0_t.grad.cpu().numpy(), ref["grad_h0"].sum(axis=0), rtol=1e-5, atol=1e-9)
 
 
-@pytest.mark.parametrize("M", [1, 5])
-def test_adjoint_engines_give_bitwise_identical_gradients(capi, M):
-    """Direct-load and TMA-staged reverse stencils: the same gradients, bit
-    for bit, on a ragged grid (two spans, partial strips, both outflow edges)
-    with members that take different numbers of steps."""
+@pytest.mark.parametrize("M,limiter", [(1, 1), (5, 1), (5, 0)])
+def test_adjoint_engines_give_bitwise_identical_gradients(capi, M, limiter):
+    """Direct-load and TMA-staged replay and reverse stencils: the same
+    gradients, bit for bit, on a ragged grid (two spans, partial strips, both
+    outflow edges) with members that take different numbers of steps, with
+    the limiter compiled in and out."""
     terr, h0, rm, sc, hy, cells, d, ns, sdt = _wet_case(ny=45, nx=150, M=M, seed=39, depth=0.6)
-    p = capi.Params.default(south_outflow=1)
+    p = capi.Params.default(south_outflow=1, limiter=limiter)
     res = []
     for engine in (0, 1):
         with capi.Grid(terr.z, terr.n, p) as g:
