@@ -416,6 +416,21 @@ int flood_get_launch(const flood_grid* g, int* rows_per_strip, int* members_per_
  * FLOOD_ERR_ARG. */
 int flood_set_engine(flood_grid* g, int engine);
 
+/* Failure-detection hook: the number of SM clock cycles each bounded wait of
+ * the TMA step kernel for a staged row may take before the kernel gives up
+ * (default 2e8, about 0.1 s; cycles < 0 restores it).  A kernel that gives
+ * up first waits, with the default limit, for every copy it still has in
+ * flight, records FLOOD_ERR_TIMEOUT in the grid's error word and returns; the
+ * next synchronising call (flood_step with t_end, flood_sync, a state read)
+ * reports FLOOD_ERR_TIMEOUT, and every later step is a no-op until
+ * flood_ensemble_init clears the word.  0 reduces each wait to a single
+ * non-blocking test, which gives up on a row whose copy is still in flight:
+ * that is how the tests reach the path.  A changed budget applies to the
+ * plain step (no running maximum, land cover or checkpoints; a step with
+ * them returns FLOOD_ERR_STATE), which is compiled separately so that the
+ * ordinary step keeps its limit as a constant.  Errors: FLOOD_ERR_ARG. */
+int flood_set_wait_budget(flood_grid* g, int64_t cycles);
+
 /* Autotuner: time every step-kernel configuration (engine x rows per strip
  * {32, 64, 128} x members per CTA {4, 1}) for steps_per_trial steps on the
  * live ensemble, keep the fastest, and restore the ensemble (state, clocks,

@@ -25,6 +25,7 @@ EXPORTED = ["flood_default_params", "flood_last_error", "flood_create_grid", "fl
             "pf_resample_systematic", "flood_get_state", "flood_set_state", "flood_get_members",
             "flood_set_members", "flood_volume_report", "flood_launch_count", "flood_sync",
             "flood_profile", "flood_set_launch", "flood_get_launch", "flood_set_engine",
+            "flood_set_wait_budget",
             "flood_adjoint", "flood_adjoint_timing", "flood_batch_create", "flood_batch_destroy",
             "flood_batch_last_error", "flood_batch_init", "flood_batch_step",
             "flood_batch_set_launch", "flood_batch_get_state", "flood_batch_members",
@@ -120,6 +121,7 @@ def lib(path: str = LIB_PATH):
     L.flood_set_engine.argtypes = [_VP, C.c_int]
     L.flood_adjoint.argtypes = [_VP, C.POINTER(LossSpec), C.c_int, _VP, _VP, _VP, _VP, _VP, _VP]
     L.flood_adjoint_timing.argtypes = [_VP, _VP, _VP]
+    L.flood_set_wait_budget.argtypes = [_VP, C.c_int64]
     L.flood_autotune.argtypes = [_VP, C.c_int, _VP, _VP, _VP, _VP, _VP]
     L.flood_storage_static.argtypes = [_VP, C.c_int, C.c_int, C.c_int, C.c_double, _VP, _VP]
     L.flood_set_roughness_factor.argtypes = [_VP, C.c_int, C.c_int, _VP, _VP]
@@ -363,6 +365,11 @@ class Grid:
         """0: direct loads, 1: TMA-staged tiles, 2: one launch per member per
         step (the plain form, for comparison); identical results."""
         _check(lib().flood_set_engine(self.h, int(engine)), self.h)
+
+    def set_wait_budget(self, cycles):
+        """Clock-cycle limit of the TMA step kernel's row waits (< 0: the
+        default); a failure-detection hook (flood_set_wait_budget)."""
+        _check(lib().flood_set_wait_budget(self.h, int(cycles)), self.h)
 
     def get_launch(self):
         r = C.c_int(); m = C.c_int()

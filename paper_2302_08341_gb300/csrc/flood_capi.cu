@@ -112,6 +112,7 @@ StepArgs step_args(const flood_grid* g, double t_end)
     a.ckpt = g->logging ? g->ckpt : nullptr;
     a.ckpt_every = g->ckpt_every > 0 ? g->ckpt_every : 1;
     a.err = g->err;
+    a.wait_budget = g->wait_budget < 0 ? flood::kTmaWaitBudgetDefault : g->wait_budget;
     a.hmax_field = g->track_max ? g->hmax_field : nullptr;
     a.lc_on = g->lc_on ? 1 : 0;
     if (g->lc_on) {
@@ -191,8 +192,10 @@ int launch_steps(flood_grid* g, int64_t count, double t_end, cudaStream_t s)
             t.state_map = g->state_map;
             t.static_map = g->static_map;
             t.a = a;
-            if (flood::launch_step_tma(t, g->members_per_cta, s))
-                return fail(g, FLOOD_ERR_STATE, "checkpointed steps do not cover land cover");
+            if (const int e = flood::launch_step_tma(t, g->members_per_cta, s))
+                return fail(g, FLOOD_ERR_STATE,
+                            e == -1 ? "checkpointed steps do not cover land cover"
+                                    : "a changed wait budget covers the plain step only");
         } else if (g->engine == 2 && !g->lc_on) {
             flood::launch_step_per_member(a, s);
             g->launches += g->M - 1;
@@ -774,6 +777,13 @@ int flood_set_engine(flood_grid* g, int engine)
     if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
     if (engine < 0 || engine > 2) return fail(g, FLOOD_ERR_ARG, "engine must be 0, 1 or 2");
     g->engine = engine;
+    return FLOOD_OK;
+}
+
+int flood_set_wait_budget(flood_grid* g, int64_t cycles)
+{
+    if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    g->wait_budget = cycles < 0 ? -1 : (long long)cycles;
     return FLOOD_OK;
 }
 

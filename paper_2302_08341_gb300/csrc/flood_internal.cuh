@@ -9,6 +9,10 @@
 
 namespace flood {
 
+// Default limit of a bounded mbarrier wait for a staged tile, in SM clock
+// cycles (about 0.1 s).
+constexpr long long kTmaWaitBudgetDefault = 200000000LL;
+
 // Per-member scalars.  Kept in three rotating slots so that a step kernel can
 // read its inputs from one slot, build the next slot (the new clock, the new
 // maximum depth by atomicMax) and clear the slot after that, without any
@@ -46,6 +50,7 @@ struct StepArgs {
     const int* seg_end;         // [M]
     int seg_first, replay_i;
     int* err;                   // device error word (bit 0: non-finite depth)
+    long long wait_budget;      // clock cycles a TMA row wait of the step may take
     int m_base;                 // first member of this launch (one-launch-per-member form)
     float* hmax_field;          // [M][plane] running maximum depth (or null: not tracked)
     // land cover (Section 4.1; lc_on = 0: none)

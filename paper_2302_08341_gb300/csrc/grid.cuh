@@ -17,6 +17,7 @@ struct flood_grid {
     float* n = nullptr;           // = zn + plane
     int n_sm = 0;
     int engine = 1;               // 0: direct loads, 1: TMA-staged tiles
+    long long wait_budget = -1;   // TMA row-wait limit of the step in clock cycles (< 0: default)
     CUtensorMap static_map{};
     CUtensorMap state_map{};
     bool maps_ok = false;

@@ -16,7 +16,7 @@ constexpr int kSpan = kTmaSpan;
 // them (four CTAs of four warps per SM instead of five) rather than spill.
 // CK: the step may write checkpoints (the adjoint's logged forward); the
 // ordinary step is compiled without that path.
-template <int WM, bool TRACK_MAX, bool LC, int LIM, bool CK>
+template <int WM, bool TRACK_MAX, bool LC, int LIM, bool CK, bool HOOK = false>
 __global__ void __launch_bounds__(32 * WM, (LC ? 16 : 20) / WM) step_tma_kernel(const __grid_constant__ TmaArgs t)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -57,10 +57,10 @@ __global__ void __launch_bounds__(32 * WM, (LC ? 16 : 20) / WM) step_tma_kernel(
     float* hm = TRACK_MAX ? a.hmax_field + (size_t)m * a.plane : nullptr;
     LandK lk;
     if (LC) lk = land_k(a, m, pl.dr, pl.dt, lane);
-    if (!tma_march<TRACK_MAX, LC, LIM>(&t.state_map, &t.static_map, (pl.cur * a.M + m) * 3, bar0,
+    if (!tma_march<TRACK_MAX, LC, LIM, HOOK>(&t.state_map, &t.static_map, (pl.cur * a.M + m) * 3, bar0,
                                   my_stages, dst, ck, hm, a.err, a.plane, a.ny, a.nx, a.ld, c0, r0,
                                   r1, lane, k, pl.dt_dx, a.scale[m], pl.dr, a.east_out, a.south_out,
-                                  mo, &lk))
+                                  mo, &lk, a.wait_budget))
         return;
 
     if (mo.bad) atomicOr(a.err, 1);
@@ -166,7 +166,7 @@ int tma_box_cols() { return kTmaBox; }
 
 namespace {
 
-template <bool TRACK_MAX, bool LC, int LIM, bool CK>
+template <bool TRACK_MAX, bool LC, int LIM, bool CK, bool HOOK = false>
 void launch_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
 {
     const StepArgs& a = t.a;
@@ -176,16 +176,16 @@ void launch_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
         static bool attr = false;
         const size_t shm = tma_smem_bytes<4>();
         if (!attr) {
-            cudaFuncSetAttribute(step_tma_kernel<4, TRACK_MAX, LC, LIM, CK>,
+            cudaFuncSetAttribute(step_tma_kernel<4, TRACK_MAX, LC, LIM, CK, HOOK>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
             attr = true;
         }
         dim3 grid((a.M + 3) / 4, spans, strips), block(32, 4);
-        step_tma_kernel<4, TRACK_MAX, LC, LIM, CK><<<grid, block, shm, s>>>(t);
+        step_tma_kernel<4, TRACK_MAX, LC, LIM, CK, HOOK><<<grid, block, shm, s>>>(t);
     } else {
         const size_t shm = tma_smem_bytes<1>();
         dim3 grid(a.M, spans, strips), block(32, 1);
-        step_tma_kernel<1, TRACK_MAX, LC, LIM, CK><<<grid, block, shm, s>>>(t);
+        step_tma_kernel<1, TRACK_MAX, LC, LIM, CK, HOOK><<<grid, block, shm, s>>>(t);
     }
 }
 
@@ -226,6 +226,12 @@ int launch_step_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
 {
     const bool track = t.a.hmax_field != nullptr;
     const bool lim = t.a.limiter != 0;
+    if (t.a.wait_budget != kTmaWaitBudgetDefault) {  // the failure-detection hook: plain step only
+        if (track || t.a.lc_on || t.a.ckpt) return -2;
+        lim ? launch_tma<false, false, 1, false, true>(t, members_per_cta, s)
+            : launch_tma<false, false, 0, false, true>(t, members_per_cta, s);
+        return 0;
+    }
     if (t.a.ckpt) {  // the adjoint's logged forward, which land cover never reaches
         if (t.a.lc_on) return -1;
         if (track)

@@ -48,10 +48,27 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity)
     return done != 0;
 }
 
+// One non-blocking test of the phase (try_wait may suspend the thread for a
+// while; test_wait never does).
+__device__ __forceinline__ bool mbar_test_now(uint32_t bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
 // Wait for the phase with the given parity to complete, giving up after
-// `budget` clock cycles.  Returns false on timeout.
+// `budget` clock cycles (budget <= 0: a single non-blocking test).  Returns
+// false on timeout.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long budget)
 {
+    if (budget <= 0) return mbar_test_now(bar, parity);
     if (mbar_test(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_test(bar, parity))

@@ -24,7 +24,7 @@ constexpr int kTmaBox = kTmaSpan + 8;              // columns per tile row
 constexpr int kTmaStaticOff = 1664;                // bytes: z, n after h, qx, qy (128-aligned)
 constexpr int kTmaStageBytes = 2816;               // 128-aligned stage size
 constexpr uint32_t kTmaTx = kTmaBox * 3 * 4 + kTmaBox * 2 * 4;  // bytes landing per stage
-constexpr long long kTmaWaitBudget = 200000000LL;  // clock cycles (~0.1 s) before giving up
+constexpr long long kTmaWaitBudget = kTmaWaitBudgetDefault;  // clock cycles before giving up
 static_assert((kTmaNS & (kTmaNS - 1)) == 0, "ring index arithmetic needs a power of two");
 
 // Dynamic shared memory of a CTA of `warps` warps: barriers, then each warp's
@@ -61,8 +61,10 @@ __device__ __forceinline__ void tma_store4(float* p, const float (&v)[4])
 // running maximum depth at hm; LC: land cover (roughness by class from lk,
 // the class's share of the rain and its drainage).  Each is a separate
 // instantiation, so the plain step carries no trace of them.  Returns false
-// if a wait gave up.
-template <bool TRACK_MAX, bool LC = false, int LIM = -1>
+// if a wait gave up.  WAIT_HOOK: each row wait may take wait_budget clock
+// cycles instead of kTmaWaitBudget (a failure-detection hook; the copies
+// still in flight are always drained with the full kTmaWaitBudget).
+template <bool TRACK_MAX, bool LC = false, int LIM = -1, bool WAIT_HOOK = false>
 __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CUtensorMap* static_map,
                                           int plane0, uint32_t bar0, unsigned char* my_stages,
                                           float* __restrict__ dst, float* ck, float* hm, int* err,
@@ -70,7 +72,8 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
                                           int ny, int nx, int ld, int c0, int r0, int r1, int lane,
                                           const FaceK& k, float dt_dx, float s, float dr,
                                           int east_out, int south_out, MarchOut& out,
-                                          const LandK* lk = nullptr)
+                                          const LandK* lk = nullptr,
+                                          long long wait_budget = kTmaWaitBudget)
 {
     constexpr int kNS = kTmaNS;
     constexpr int kBox = kTmaBox;
@@ -106,10 +109,13 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
     };
     for (; issued < rb && issued < ra + kNS; ++issued)
         if (lane == 0) issue(issued);
-    auto wait_row = [&](int row) -> bool {
+    auto wait_row_for = [&](int row, long long budget) -> bool {
         const int kk = row - ra;
         return mbar_wait_bounded(bar0 + 8u * ((unsigned)kk & (kNS - 1)), ((unsigned)kk / kNS) & 1,
-                                 kWaitBudget);
+                                 budget);
+    };
+    auto wait_row = [&](int row) -> bool {
+        return wait_row_for(row, WAIT_HOOK ? wait_budget : kWaitBudget);
     };
     auto row_ptr = [&](int row) -> const float* {
         return reinterpret_cast<const float*>(my_stages +
@@ -131,7 +137,8 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
     bool ok = true;
     auto drain_and_fail = [&]() {
         if (lane == 0) atomicOr(err, 2);
-        for (int row = waited; row < issued; ++row) wait_row(row);  // bounded each
+        // every copy still in flight lands before the warp leaves (bounded each)
+        for (int row = waited; row < issued; ++row) wait_row_for(row, kWaitBudget);
     };
 
     const int x0 = 4 + 4 * lane;  // this lane's first cell in a tile row

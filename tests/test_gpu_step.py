@@ -202,6 +202,40 @@ def test_nan_input_is_reported_at_sync(capi):
         assert e.value.code == -5
 
 
+def test_staged_tile_wait_that_runs_out_is_reported_and_recoverable(capi):
+    """Failure detection without a fault: with a zero wait budget every TMA
+    row wait of the step kernel is a single non-blocking test, which gives up
+    on a row whose copy is still in flight; the
+    kernel drains its own copies, records the timeout and returns, the next
+    synchronising call reports FLOOD_ERR_TIMEOUT, and after
+    flood_ensemble_init clears the error word the same grid runs the steps
+    again to the same state as a fresh grid."""
+    terr = synth.make_terrain(256, 256, seed=17)
+    hy = synth.hyetograph_constant(80.0, 300.0)
+    rm, sc = synth.ensemble_prior(17, 4)
+    with capi.Grid(terr.z, terr.n) as ref:
+        ref.ensemble_init(4, rm, sc, hy)
+        ref.set_engine(1)
+        ref.advance_to(30.0)
+        want = [ref.get_state(m) for m in range(4)]
+    with capi.Grid(terr.z, terr.n) as g:
+        g.ensemble_init(4, rm, sc, hy)
+        g.set_engine(1)
+        g.set_wait_budget(0)
+        with pytest.raises(capi.FloodError) as e:
+            g.advance_to(30.0)
+        assert e.value.code == -4
+        with pytest.raises(capi.FloodError) as e:
+            g.sync()                       # sticky until the ensemble is initialised again
+        assert e.value.code == -4
+        g.set_wait_budget(-1)
+        g.ensemble_init(4, rm, sc, hy)
+        g.advance_to(30.0)
+        for m in range(4):
+            for k in range(3):
+                assert np.array_equal(g.get_state(m)[k], want[m][k])
+
+
 def test_bad_arguments_raise(capi):
     z = np.zeros((4, 4), np.float32)
     with capi.Grid(z, z + 0.03) as g:
