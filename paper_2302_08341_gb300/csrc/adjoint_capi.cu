@@ -63,6 +63,7 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
                              double* grad_rain, double* grad_scale, float* grad_h0, double* loss_out,
                              void* stream)
 {
+    const flood::TraceRange range("flood_adjoint");
     if (!g) return flood::fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
     if (g->M == 0) return flood::fail(g, FLOOD_ERR_STATE, "flood_ensemble_init has not been called");
     if (!L || L->n_samples < 1 || !(L->sample_dt > 0) || L->n_gauges < 1 || !L->cells || !L->d)

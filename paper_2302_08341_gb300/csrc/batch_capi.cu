@@ -9,6 +9,7 @@
 
 #include "../../include/flood.h"
 #include "batch.cuh"
+#include "trace.cuh"
 #include "pf_kernels.cuh"
 #include "tma.cuh"
 
@@ -394,6 +395,7 @@ int flood_batch_set_launch(flood_batch* b, int rows_per_strip, int warps_per_cta
 
 int flood_batch_step(flood_batch* b, double t_stop, void* stream)
 {
+    const flood::TraceRange range("flood_batch_step");
     if (!b) return bfail(nullptr, FLOOD_ERR_ARG, "batch is NULL");
     if (!b->initialised) return bfail(b, FLOOD_ERR_STATE, "flood_batch_init has not been called");
     if (!(t_stop >= 0.0)) return bfail(b, FLOOD_ERR_ARG, "t_stop must be >= 0");

@@ -212,6 +212,7 @@ extern "C" int flood_roughness_factor_grad(flood_grid* g, double* grad, void* st
 extern "C" int flood_calibration_step(flood_grid* g, double eta, double delta, double* loss_out,
                                       void* stream)
 {
+    const flood::TraceRange range("flood_calibration_step");
     if (!g) return flood::fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
     if (!(eta > 0.0) || !(delta > 0.0))
         return flood::fail(g, FLOOD_ERR_ARG, "eta and delta must be positive");

@@ -442,6 +442,7 @@ int flood_ensemble_init(flood_grid* g, int M, const float* h0, int h0_per_member
 
 int flood_step(flood_grid* g, int n_steps, double t_end, void* stream)
 {
+    const flood::TraceRange range("flood_step");
     if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
     if (g->M == 0) return fail(g, FLOOD_ERR_STATE, "flood_ensemble_init has not been called");
     cudaStream_t s = S(stream);
@@ -522,6 +523,7 @@ int pf_assimilate(flood_grid* g, int G, const float* y, const double* d, const d
                   const float* beta, double* weights_out, int32_t* idx_out, double* neff_out,
                   int32_t* resampled_out, void* stream)
 {
+    const flood::TraceRange range("pf_assimilate");
     if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
     if (g->M == 0) return fail(g, FLOOD_ERR_STATE, "flood_ensemble_init has not been called");
     if (G < 1 || !d || (!sigma && !(sigma_rel > 0)) || !beta)

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "flood_internal.cuh"
+#include "trace.cuh"
 
 struct flood_grid {
     int ny = 0, nx = 0, ld = 0;

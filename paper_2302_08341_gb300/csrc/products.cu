@@ -163,6 +163,7 @@ extern "C" int flood_get_max_depth(flood_grid* g, int member, float* out, void* 
 extern "C" int flood_ensemble_products(flood_grid* g, double threshold, int n_levels,
                                        const double* levels, float* exceed, float* pct, void* stream)
 {
+    const flood::TraceRange range("flood_ensemble_products");
     if (!g) return flood::fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
     if (!g->hmax_field || !g->track_max)
         return flood::fail(g, FLOOD_ERR_STATE, "maximum depth is not being tracked");

@@ -204,3 +204,49 @@ def test_full_size_ensemble_sampled_parity(capi):
             ha = after[m][0][r0:r1, c0:c1]
             compare(ha[1:-1, 1:-1], mo.h[1:-1, 1:-1], 2e-5)
             compare(after[m][1][r0:r1, c0:c1][1:-1, :-1], mo.qx[1:-1, 1:-1], 5e-5)
+
+
+def test_resume_at_a_window_boundary_is_bit_exact(capi):
+    """Checkpoint / resume through the ABI: the states, clocks, rain
+    multipliers, Manning scales and weights read out at a window boundary
+    (after the particle filter) and fed to a new grid (ensemble_init with
+    per-member depths and the saved time, set_state, set_members) continue
+    to exactly the states of the run that was never interrupted."""
+    ny, nx, M = 64, 96, 6
+    terr = synth.make_terrain(ny, nx, seed=21)
+    hy = synth.hyetograph_triangular(60.0, 1200.0, 3600.0)
+    rm, sc = synth.ensemble_prior(21, M)
+    cells = synth.gauge_cells(terr, 3, seed=21)
+    u, beta = synth.pf_draws(21, 1, M)
+
+    def first_window(g):
+        g.ensemble_init(M, rm, sc, hy)
+        g.advance_to(300.0)
+        y = g.gauge_sample(cells)
+        d = y.astype(np.float64).mean(axis=0) * 1.1
+        g.pf_assimilate(d, 0.05, u, beta, y=y, force=True)
+
+    with capi.Grid(terr.z, terr.n) as a:
+        first_window(a)
+        a.advance_to(600.0)
+        want = [a.get_state(m) for m in range(M)]
+        want_mem = a.members()
+    with capi.Grid(terr.z, terr.n) as b:
+        first_window(b)
+        saved = [b.get_state(m) for m in range(M)]
+        mem = b.members()
+    assert np.all(mem["t"] == 300.0)
+    with capi.Grid(terr.z, terr.n) as c:
+        c.ensemble_init(M, mem["rain_mult"], mem["scale"], hy,
+                        h0=np.stack([s[0] for s in saved]), t0=300.0)
+        for m in range(M):
+            c.set_state(m, *saved[m])
+        c.set_members(weights=mem["weights"])
+        c.advance_to(600.0)
+        got = [c.get_state(m) for m in range(M)]
+        got_mem = c.members()
+    for m in range(M):
+        for k in range(3):
+            assert np.array_equal(got[m][k], want[m][k]), (m, k)
+    assert np.array_equal(got_mem["t"], want_mem["t"])
+    assert np.array_equal(got_mem["weights"], want_mem["weights"])
