@@ -71,7 +71,7 @@ def parse():
     ap.add_argument("--calibration-windows", type=int, default=3)
     ap.add_argument("--rows-per-strip", type=int, default=None,
                     help="strip height for --only calibration (profiling smaller cases)")
-    ap.add_argument("--engine", type=int, choices=[0, 1], default=None,
+    ap.add_argument("--engine", type=int, choices=[0, 1, 2], default=None,
                     help="step-kernel engine for --only batch (default: the library's)")
     args = ap.parse_args()
     global NY, NX, M, ROWS
@@ -347,12 +347,15 @@ def batch_measure(capi, engine=None):
         mem = b.members()
         launches = b.launch_count - l0
     units = float((mem["steps"] * cells).sum())
+    form = {0: "direct loads, CUDA-graph replayed per-step launches",
+            1: "TMA-staged rows, CUDA-graph replayed per-step launches",
+            2: "TMA-staged rows, one persistent cooperative launch per window"}[engine]
     return {"config": "64 scenarios, sides U{512..2048}, rain U[20,100] mm/h, durations "
-                      "U[900,3600] s, 300 s windows, CUDA-graph replayed batched step",
+                      "U[900,3600] s, 300 s windows, batched step: " + form,
             "value": units / (ms * 1e-3), "unit": "member-cell-steps/s", "ms": ms,
             "total_cells": float(cells.sum()), "member_cell_steps": units,
             "all_finished": bool(np.all(mem["t"] == dur)), "gpu_launches": launches,
-            "engine": "tma" if engine == 1 else "direct loads"}
+            "engine": {0: "direct loads", 1: "tma", 2: "tma persistent"}[engine]}
 
 
 def calibration_measure(capi, windows=3):
@@ -709,10 +712,15 @@ def run_gb300(args):
     if not args.no_extensions and world == 1:
         extensions["adjoint"] = adjoint_measure(capi)
         extensions["batched"] = batch_measure(capi)
+        pers = batch_measure(capi, engine=2)
+        extensions["batched"]["persistent"] = {
+            k: pers[k] for k in ("value", "unit", "ms", "all_finished", "gpu_launches", "engine")}
         extensions["calibration"] = calibration_measure(capi, windows=args.calibration_windows)
         extensions["land_cover"] = land_cover_measure(capi)
         extensions["batched"]["hbm_frac_whole_window"] = (
             extensions["batched"]["value"] * BYTES_SINGLE / 1e9 / hbm_peak)
+        extensions["batched"]["persistent"]["hbm_frac_whole_window"] = (
+            extensions["batched"]["persistent"]["value"] * BYTES_SINGLE / 1e9 / hbm_peak)
         extensions["autotune"] = tuned
         extensions["plain_vs_fused"] = plain
         extensions["products"] = products

@@ -468,9 +468,10 @@ int flood_batch_init(flood_batch* b, const float* const* hyetographs, const int3
                      void* stream);
 
 /* Advance every scenario to min(t_stop, t_end[i]) (a window end), each with
- * its own steps.  Synchronises `stream` between graph replays to follow the
- * scenarios' clocks.  Errors: FLOOD_ERR_STATE (before init, or no progress),
- * FLOOD_ERR_NAN. */
+ * its own steps.  Synchronises `stream` between graph replays (engines 0-1)
+ * or after the persistent launch (engine 2) to follow the scenarios' clocks.
+ * Errors: FLOOD_ERR_STATE (before init, or no progress), FLOOD_ERR_NAN,
+ * FLOOD_ERR_TIMEOUT. */
 int flood_batch_step(flood_batch* b, double t_stop, void* stream);
 
 /* Launch shape: rows per warp strip (1..4096) and warps per CTA (4 or 8);
@@ -479,9 +480,14 @@ int flood_batch_set_launch(flood_batch* b, int rows_per_strip, int warps_per_cta
 
 /* Step-kernel engine of the batch: 0 = direct float4 loads, 1 = rows staged
  * through shared memory by the tensor memory accelerator, each scenario with
- * its own tensor maps (the default where available).  Identical results.
- * Synchronous.  Errors: FLOOD_ERR_ARG, FLOOD_ERR_STATE (engine 1 without
- * tensor maps). */
+ * its own tensor maps (the default where available), replayed as CUDA graphs
+ * of one plan and one step launch per step; 2 = the same TMA-staged march in
+ * one persistent cooperative launch per flood_batch_step call, looping plan
+ * phase -> grid barrier -> step phase (warps draw tasks from a counter) ->
+ * grid barrier until every scenario has reached the stop.  The barrier waits
+ * are bounded: one that runs out makes the call return FLOOD_ERR_TIMEOUT.
+ * Identical results.  Synchronous.  Errors: FLOOD_ERR_ARG, FLOOD_ERR_STATE
+ * (engines 1-2 without tensor maps, engine 2 without cooperative launch). */
 int flood_batch_set_engine(flood_batch* b, int engine);
 
 /* Scenario i's state as [ny[i]][nx[i]] FP32 arrays (any may be NULL). */

@@ -584,7 +584,9 @@ class Batch:
                 self.h)
 
     def set_engine(self, engine):
-        """0: direct loads, 1: TMA-staged rows (identical results)."""
+        """0: direct loads, 1: TMA-staged rows (graph-replayed launches), 2: the
+        TMA-staged march in one persistent launch per step call (identical
+        results)."""
         _bcheck(lib().flood_batch_set_engine(self.h, int(engine)), self.h)
 
     def get_state(self, i, stream=None):

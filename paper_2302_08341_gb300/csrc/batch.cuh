@@ -44,7 +44,28 @@ struct BatchArgs {
     const CUtensorMap* maps;   // [S][2] per scenario: state (ld, ny, 6 planes), z and n (ld, ny, 2)
 };
 
+// The persistent form: one cooperative launch loops plan phase -> grid
+// barrier -> step phase (warps draw tasks from a counter) -> grid barrier
+// until no scenario is active (or max_steps).  The barrier is a counter and
+// a generation word with bounded spins: a wait that runs out sets bit 2 of
+// the error word (FLOOD_ERR_TIMEOUT) and every CTA leaves at its next
+// barrier.
+struct PersistArgs {
+    BatchArgs a;               // ms_in/ms_out/ms_clr unused: slots rotate with k
+    MemberClock* ms;           // [3][S]
+    int S;
+    int max_steps;
+    int64_t k0;                // the batch's step counter when launched
+    unsigned* bar;             // [2] arrivals, generation
+    unsigned* task_next;       // [2] next task of the step phase, by step parity
+    int* any_active;           // [2] some scenario steps, by step parity
+    int64_t* steps_done;       // steps the launch advanced the clocks by
+    long long budget;          // clock cycles a barrier wait may take
+    int* diag;                 // [8] where the first wait gave up (kind, step, CTA, ...)
+};
+
 void launch_batch_plan(const BatchArgs& a, int n_scen, cudaStream_t s);
+cudaError_t launch_batch_persistent(const PersistArgs& q, cudaStream_t s);
 void launch_batch_step(const BatchArgs& a, int warps_per_cta, cudaStream_t s);
 void launch_batch_step_tma(const BatchArgs& a, int warps_per_cta, cudaStream_t s);
 int batch_tma_prepare();  // shared-memory attributes; call before any stream capture

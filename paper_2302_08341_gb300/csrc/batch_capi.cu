@@ -45,7 +45,11 @@ struct flood_batch {
     double* t_stop = nullptr;         // device scalar
     flood::MemberPlan* plan = nullptr; // [S]
     int rows_per_strip = 64, warps_per_cta = 4;
-    int engine = 0;                   // 0: direct loads, 1: TMA-staged rows
+    int engine = 0;                   // 0: direct loads, 1: TMA-staged rows, 2: persistent
+    unsigned* pbar = nullptr;         // persistent form: barrier words [2], task counters [2]
+    int* pact = nullptr;              // [2] some scenario steps, by step parity
+    int64_t* pdone = nullptr;         // steps the last persistent launch advanced the clocks by
+    int* pdiag = nullptr;             // [8] where a persistent launch's first wait gave up
     CUtensorMap* d_maps = nullptr;    // [S][2] tensor maps of each scenario
     bool initialised = false;
     int64_t k = 0, launches = 0;
@@ -176,6 +180,7 @@ int read_batch_clocks(flood_batch* b, std::vector<MemberClock>& c, cudaStream_t 
     BCK(b, cudaStreamSynchronize(s));
     int err = 0;
     BCK(b, cudaMemcpy(&err, b->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err & 2) return bfail(b, FLOOD_ERR_TIMEOUT, "a bounded device wait gave up");
     if (err) return bfail(b, FLOOD_ERR_NAN, "a kernel produced a non-finite depth");
     return FLOOD_OK;
 }
@@ -308,7 +313,7 @@ int flood_batch_destroy(flood_batch* b)
     for (float* p : b->state) if (p) cudaFree(p);
     for (float* p : b->hyeto) if (p) cudaFree(p);
     void* bufs[] = {b->d_desc, b->d_tasks, b->ms, b->vacc, b->rain_acc, b->storage, b->part,
-                    b->err, b->t_stop, b->plan, b->d_maps};
+                    b->err, b->t_stop, b->plan, b->d_maps, b->pbar, b->pact, b->pdone, b->pdiag};
     for (void* p : bufs) if (p) cudaFree(p);
     delete b;
     return FLOOD_OK;
@@ -356,8 +361,18 @@ int flood_batch_init(flood_batch* b, const float* const* hyetographs, const int3
 int flood_batch_set_engine(flood_batch* b, int engine)
 {
     if (!b) return bfail(nullptr, FLOOD_ERR_ARG, "batch is NULL");
-    if (engine != 0 && engine != 1) return bfail(b, FLOOD_ERR_ARG, "engine must be 0 or 1");
-    if (engine == 1 && !b->d_maps) return bfail(b, FLOOD_ERR_STATE, "no tensor maps: direct loads only");
+    if (engine < 0 || engine > 2) return bfail(b, FLOOD_ERR_ARG, "engine must be 0, 1 or 2");
+    if (engine >= 1 && !b->d_maps) return bfail(b, FLOOD_ERR_STATE, "no tensor maps: direct loads only");
+    if (engine == 2) {
+        int dev = 0, coop = 0;
+        BCK(b, cudaGetDevice(&dev));
+        BCK(b, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        if (!coop) return bfail(b, FLOOD_ERR_STATE, "the device has no cooperative launch");
+        if (!b->pbar) BCK(b, cudaMalloc(&b->pbar, sizeof(unsigned) * 4));
+        if (!b->pact) BCK(b, cudaMalloc(&b->pact, sizeof(int) * 2));
+        if (!b->pdone) BCK(b, cudaMalloc(&b->pdone, sizeof(int64_t)));
+        if (!b->pdiag) BCK(b, cudaMalloc(&b->pdiag, sizeof(int) * 8));
+    }
     BCK(b, cudaDeviceSynchronize());
     b->engine = engine;
     drop_graph(b);
@@ -400,7 +415,7 @@ int flood_batch_step(flood_batch* b, double t_stop, void* stream)
     if (!b->initialised) return bfail(b, FLOOD_ERR_STATE, "flood_batch_init has not been called");
     if (!(t_stop >= 0.0)) return bfail(b, FLOOD_ERR_ARG, "t_stop must be >= 0");
     cudaStream_t s = S_(stream);
-    int rc = ensure_graph(b);
+    int rc = b->engine == 2 ? FLOOD_OK : ensure_graph(b);
     if (rc) return rc;
     BCK(b, cudaMemcpyAsync(b->t_stop, &t_stop, sizeof(double), cudaMemcpyHostToDevice, s));
     std::vector<MemberClock> c;
@@ -431,6 +446,38 @@ int flood_batch_step(flood_batch* b, double t_stop, void* stream)
             return bfail(b, FLOOD_ERR_STATE, "scenarios stopped advancing toward t_stop");
         if (need > (int64_t)1 << 26) return bfail(b, FLOOD_ERR_STATE, "too many steps to t_stop");
         last = tmin;
+        if (b->engine == 2) {  // one persistent launch runs every scenario to the stop
+            flood::PersistArgs q{};
+            q.a = batch_args(b, 0);
+            q.ms = b->ms;
+            q.S = b->S;
+            q.max_steps = (int)std::min<int64_t>(2 * need + 64, INT32_MAX / 2);
+            q.k0 = b->k;
+            q.bar = b->pbar;
+            q.task_next = b->pbar + 2;
+            q.any_active = b->pact;
+            q.steps_done = b->pdone;
+            q.budget = flood::kTmaWaitBudgetDefault;
+            q.diag = b->pdiag;
+            BCK(b, cudaMemsetAsync(b->pdiag, 0, sizeof(int) * 8, s));
+            BCK(b, cudaMemsetAsync(b->pbar, 0, sizeof(unsigned) * 4, s));
+            BCK(b, cudaMemsetAsync(b->pact, 0, sizeof(int) * 2, s));
+            BCK(b, flood::launch_batch_persistent(q, s));
+            int64_t done = 0;
+            BCK(b, cudaMemcpyAsync(&done, b->pdone, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            BCK(b, cudaStreamSynchronize(s));
+            b->k += done;
+            b->launches += 1;
+            int dg[8];
+            BCK(b, cudaMemcpy(dg, b->pdiag, sizeof(dg), cudaMemcpyDeviceToHost));
+            if (dg[0])
+                return bfail(b, FLOOD_ERR_TIMEOUT,
+                             std::string(dg[0] == 1 ? "grid barrier" : "staged-row wait") +
+                                 " gave up at step " + std::to_string(dg[1]) + " in CTA " +
+                                 std::to_string(dg[2]) + " of " + std::to_string(dg[5]) + " (" +
+                                 std::to_string(dg[3]) + ", " + std::to_string(dg[4]) + ")");
+            continue;
+        }
         const int64_t reps = (need + kGraphSteps - 1) / kGraphSteps;
         for (int64_t r = 0; r < reps; ++r) BCK(b, cudaGraphLaunch(b->graph, s));
         b->k += reps * kGraphSteps;

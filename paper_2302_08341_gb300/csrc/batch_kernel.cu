@@ -137,6 +137,242 @@ __global__ void __launch_bounds__(32 * W, 20 / W) batch_tma_kernel(const BatchAr
     }
 }
 
+// ---- persistent form ------------------------------------------------------
+
+// Loads that bypass L1: data another SM wrote earlier in the same launch.
+template <class T>
+__device__ __forceinline__ T ld_cg(const T* p)
+{
+    static_assert(sizeof(T) % 8 == 0, "8-byte words");
+    T v;
+    auto* d = reinterpret_cast<unsigned long long*>(&v);
+    auto* q = reinterpret_cast<const unsigned long long*>(p);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(T) / 8); ++i) d[i] = __ldcg(q + i);
+    return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Generic-proxy stores of one step are read by the tensor memory
+// accelerator (async proxy) in the next: a proxy fence on both sides of the
+// barrier.
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// The first wait of the launch that gave up: kind (1: grid barrier, 2: a
+// staged-row wait), step, CTA and two words of context.
+__device__ __forceinline__ void record_wait(const PersistArgs& q, int kind, int j, int x, int y)
+{
+    if (atomicCAS(q.diag, 0, kind) == 0) {
+        q.diag[1] = j;
+        q.diag[2] = blockIdx.x;
+        q.diag[3] = x;
+        q.diag[4] = y;
+        q.diag[5] = gridDim.x;
+    }
+}
+
+// Plan of step j of scenario i (as batch_plan_kernel), by one thread.
+__device__ __forceinline__ void plan_one(const PersistArgs& q, int i, int j, double t_stop)
+{
+    const BatchArgs& a = q.a;
+    const int64_t k = q.k0 + j;
+    const MemberClock* ms_in = q.ms + (k % 3) * q.S;
+    MemberClock* ms_out = q.ms + ((k + 1) % 3) * q.S;
+    MemberClock* ms_clr = q.ms + ((k + 2) % 3) * q.S;
+    const ScenDesc sd = a.scen[i];
+    const MemberClock in = ld_cg(ms_in + i);
+    const double t_end = sd.t_end < t_stop ? sd.t_end : t_stop;
+    const StepPlan sp = plan_step_p(a.alpha_dx, a.g, a.dt_cap, a.dt_fixed, a.h_floor, a.rain_block,
+                                    t_end, sd.hyeto, sd.nb, sd.rain_mult, in);
+    MemberPlan p;
+    fill_plan(p, sp, a.g, a.dxd);
+    p.cur = in.cur;
+    p.ckpt = -1;
+    p.q_in = 0.0f;
+    ms_clr[i].hmax_bits = 0u;
+    if (!sp.active) {
+        ms_out[i] = in;
+    } else {  // the maximum slot was cleared two steps ago: the step phase raises it
+        ms_out[i].t = sp.t_next;
+        ms_out[i].steps = in.steps + 1;
+        ms_out[i].cur = 1 - in.cur;
+        atomicAdd(a.rain_acc + i, (double)sp.dr * a.cell_area * sd.ncell);
+        atomicOr(q.any_active + (j & 1), 1);
+    }
+    a.plan[i] = p;
+}
+
+// Grid-wide barrier of a cooperative launch with a bounded spin; the CTA
+// that arrives last plans step j for every scenario (the previous step's
+// maxima are complete by then) before it releases the others, unless j is
+// past the launch's last step.  Returns false if this wait or an earlier one
+// anywhere gave up.
+__device__ __forceinline__ bool grid_barrier_plan(const PersistArgs& q, int j, double t_stop,
+                                                  int* flag_s)
+{
+    const bool plan = j < q.max_steps;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nt = blockDim.x * blockDim.y;
+    fence_proxy_async_global();
+    __syncthreads();
+    unsigned gen = 0;
+    if (tid == 0) {
+        __threadfence();
+        gen = ld_acquire_u32(q.bar + 1);
+        *flag_s = atomicAdd(q.bar, 1u) == gridDim.x - 1 ? 1 : 0;
+    }
+    __syncthreads();
+    const bool last = *flag_s == 1;
+    if (last && plan) {
+        __threadfence();
+        if (tid == 0) {  // both were last used two steps ago
+            q.task_next[j & 1] = 0u;
+            q.any_active[j & 1] = 0;
+        }
+        __syncthreads();
+        for (int i = tid; i < q.S; i += nt) plan_one(q, i, j, t_stop);
+        __syncthreads();
+    }
+    if (last && tid == 0) {
+        atomicExch(q.bar, 0u);
+        __threadfence();
+        atomicAdd(q.bar + 1, 1u);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int ok = 1;
+        if (!last) {
+            const long long t0 = clock64();
+            while (ld_acquire_u32(q.bar + 1) == gen) {
+                if (clock64() - t0 > q.budget) {
+                    atomicOr(q.a.err, 2);
+                    record_wait(q, 1, j, (int)ld_acquire_u32(q.bar), (int)gen);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (*reinterpret_cast<volatile const int*>(q.a.err) & 2) ok = 0;
+        *flag_s = ok ? 2 : 3;
+    }
+    __syncthreads();
+    fence_proxy_async_global();
+    return *flag_s == 2;
+}
+
+// One warp task of the step phase (the batch_tma_kernel body, with the plan
+// read past L1 and the volume slots updated atomically: a task may run on a
+// different SM each step).
+// Returns false if a wait of the march gave up (the warp then takes no
+// further task: its barriers may still have a copy in flight).
+template <int LIM>
+__device__ __forceinline__ bool persistent_task(const PersistArgs& q, int j, int t, MemberClock* ms_out,
+                                                int lane, uint32_t bar0, unsigned char* my_stages)
+{
+    const BatchArgs& a = q.a;
+    const WarpTask tk = a.tasks[t];
+    const int i = tk.scen;
+    const MemberPlan p = ld_cg(a.plan + i);
+    if (!p.active) return true;
+    const ScenDesc sd = a.scen[i];
+    FaceK k;
+    k.gdt_dx = p.gdt_dx;
+    k.gdt = p.gdt;
+    k.dx_4dt = p.dx_4dt;
+    k.h_eps = a.h_eps;
+    k.edge_drop = a.edge_drop;
+    k.limiter = a.limiter;
+    k.q_in = 0.0f;  // no inflow boundary here
+    k.in_r0 = k.in_r1 = 0;
+    float* dst = sd.state + (size_t)(1 - p.cur) * 3 * sd.plane;
+    MarchOut mo;
+    const bool ok = tma_march<false, false, LIM>(a.maps + 2 * i, a.maps + 2 * i + 1, p.cur * 3, bar0,
+                                                 my_stages, dst, nullptr, nullptr, a.err, sd.plane,
+                                                 sd.ny, sd.nx, sd.ld, tk.c0, tk.r0, tk.r1, lane, k,
+                                                 p.dt_dx, sd.scale, p.dr, a.east_out, a.south_out, mo);
+    if (!ok) {
+        if (lane == 0) record_wait(q, 2, j, t, i);
+        return false;
+    }
+    // the warp's barriers and stages serve its next task: retire the barriers
+    // (every copy has landed) and order the stages' generic reads before the
+    // next task's copies overwrite them
+    __syncwarp();
+    if (lane == 0) {
+        fence_proxy_async_smem();
+        for (int s = 0; s < kTmaNS; ++s) mbar_inval(bar0 + 8u * s);
+    }
+    __syncwarp();
+    if (mo.bad) atomicOr(a.err, 1);
+    const unsigned hb = __reduce_max_sync(0xffffffffu, mo.bad ? 0u : __float_as_uint(mo.hmax) & 0x7fffffffu);
+    double out_acc = (double)mo.out_s - (double)mo.out_c, clamp_acc = (double)mo.clamp;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        out_acc += __shfl_xor_sync(0xffffffffu, out_acc, off);
+        clamp_acc += __shfl_xor_sync(0xffffffffu, clamp_acc, off);
+    }
+    if (lane == 0) {
+        atomicMax(&ms_out[i].hmax_bits, hb);
+        if (out_acc != 0.0 || clamp_acc != 0.0) {
+            double* v = a.vacc + (size_t)tk.slot * 2;
+            atomicAdd(v, out_acc * p.dt * a.dxd);
+            atomicAdd(v + 1, clamp_acc * a.cell_area);
+        }
+    }
+    return true;
+}
+
+template <int W, int LIM>
+__global__ void __launch_bounds__(32 * W, 20 / W) batch_persistent_kernel(const __grid_constant__ PersistArgs q)
+{
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ int flag_s;
+    const BatchArgs& a = q.a;
+    const int lane = threadIdx.x;
+    const int w = threadIdx.y;
+    const bool first_thread = blockIdx.x == 0 && w == 0 && lane == 0;
+    uint32_t bar0;
+    unsigned char* my_stages;
+    tma_march_smem(smem_raw, W, w, bar0, my_stages);
+    const double t_stop = *a.t_stop;
+    int done = 0;
+    if (grid_barrier_plan(q, 0, t_stop, &flag_s)) {  // plans step 0
+        done = q.max_steps;
+        for (int j = 0; j < q.max_steps; ++j) {
+            if (__ldcg(q.any_active + (j & 1)) == 0) {  // every scenario has arrived
+                done = j + 1;
+                break;
+            }
+            const int64_t k = q.k0 + j;
+            MemberClock* ms_out = q.ms + ((k + 1) % 3) * q.S;
+            // step phase: each warp draws tasks until the table is exhausted
+            for (;;) {
+                unsigned t = 0;
+                if (lane == 0) t = atomicAdd(q.task_next + (j & 1), 1u);
+                t = __shfl_sync(0xffffffffu, t, 0);
+                if (t >= (unsigned)a.ntasks) break;
+                if (!persistent_task<LIM>(q, j, (int)t, ms_out, lane, bar0, my_stages)) break;
+            }
+            if (!grid_barrier_plan(q, j + 1, t_stop, &flag_s)) {  // plans step j + 1
+                done = j + 1;
+                break;
+            }
+        }
+    }
+    if (first_thread) *q.steps_done = done;
+}
+
 }  // namespace
 
 int batch_tma_prepare()
@@ -168,6 +404,24 @@ void launch_batch_step_tma(const BatchArgs& a, int warps_per_cta, cudaStream_t s
         else
             batch_tma_kernel<4, 0><<<g4, dim3(32, 4), tma_march_smem_bytes(4), s>>>(a);
     }
+}
+
+// One cooperative launch (its CTAs are resident together, which the grid
+// barrier needs): as many CTAs of four warps as fit on the GPU.
+cudaError_t launch_batch_persistent(const PersistArgs& q, cudaStream_t s)
+{
+    auto f = q.a.limiter ? batch_persistent_kernel<4, 1> : batch_persistent_kernel<4, 0>;
+    const size_t shm = tma_march_smem_bytes(4);
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    int dev = 0, nsm = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, 128, shm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    void* args[] = {const_cast<PersistArgs*>(&q)};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(f), dim3(nsm * per_sm),
+                                       dim3(32, 4), args, shm, s);
 }
 
 void launch_batch_plan(const BatchArgs& a, int n_scen, cudaStream_t s)

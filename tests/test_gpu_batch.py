@@ -78,13 +78,34 @@ def test_batch_launch_shapes_bitwise(capi, shape):
 
 @pytest.mark.parametrize("shape", [None, (7, 8)])
 def test_batch_engines_bitwise(capi, shape):
-    """Direct-load and TMA-staged batched kernels: the same states, bit for
-    bit, for every scenario."""
-    a = _run_batch(capi, shape, engine=0)[5]
-    b = _run_batch(capi, shape, engine=1)[5]
-    for x, y in zip(a, b):
-        for k in range(3):
-            assert np.array_equal(x[k], y[k])
+    """Direct-load and TMA-staged batched kernels, graph-replayed or in one
+    persistent launch: the same states, bit for bit, for every scenario, and
+    the same clocks and volume bookkeeping."""
+    runs = [_run_batch(capi, shape, engine=e) for e in (0, 1, 2)]
+    for r in runs[1:]:
+        for x, y in zip(runs[0][5], r[5]):
+            for k in range(3):
+                assert np.array_equal(x[k], y[k])
+        for key in ("t", "steps", "rain", "outflow", "clamp", "storage"):
+            assert np.array_equal(runs[1][6][key], r[6][key]), key
+
+
+def test_persistent_batch_runs_windows_in_one_launch_each(capi):
+    """The persistent engine advances a window in one launch (plus nothing
+    else on the device), and scenarios that already ended stay put."""
+    terrs, hys, rm, sc, dur = _scenarios()
+    with capi.Batch([t.z for t in terrs], [t.n for t in terrs]) as b:
+        b.init(hys, rm, sc, dur)
+        b.set_engine(2)
+        n0 = b.launch_count
+        b.step(300.0)
+        assert b.launch_count - n0 == 1
+        t1 = b.members()["t"]
+        assert np.array_equal(t1, np.minimum(dur, 300.0))
+        b.step(300.0)                     # nothing left to do: no launch
+        assert b.launch_count - n0 == 1
+        b.step(1000.0)
+        assert np.array_equal(b.members()["t"], dur)
 
 
 def test_batch_rejects_bad_arguments(capi):
