@@ -356,13 +356,16 @@ __global__ void __launch_bounds__(32 * W, 20 / W) batch_persistent_kernel(const 
             }
             const int64_t k = q.k0 + j;
             MemberClock* ms_out = q.ms + ((k + 1) % 3) * q.S;
-            // step phase: each warp draws tasks until the table is exhausted
-            for (;;) {
-                unsigned t = 0;
-                if (lane == 0) t = atomicAdd(q.task_next + (j & 1), 1u);
-                t = __shfl_sync(0xffffffffu, t, 0);
-                if (t >= (unsigned)a.ntasks) break;
+            // step phase: warp w takes task w, then draws the tasks past the
+            // first round from a counter (no burst of draws at the start)
+            const unsigned nw = gridDim.x * W;
+            unsigned t = blockIdx.x * W + w;
+            while (t < (unsigned)a.ntasks) {
                 if (!persistent_task<LIM>(q, j, (int)t, ms_out, lane, bar0, my_stages)) break;
+                if (nw >= (unsigned)a.ntasks) break;
+                unsigned d = 0;
+                if (lane == 0) d = atomicAdd(q.task_next + (j & 1), 1u);
+                t = nw + __shfl_sync(0xffffffffu, d, 0);
             }
             if (!grid_barrier_plan(q, j + 1, t_stop, &flag_s)) {  // plans step j + 1
                 done = j + 1;
