@@ -710,17 +710,26 @@ def run_gb300(args):
     g.close()
     extensions = {}
     if not args.no_extensions and world == 1:
-        extensions["adjoint"] = adjoint_measure(capi)
-        extensions["batched"] = batch_measure(capi)
-        pers = batch_measure(capi, engine=2)
-        extensions["batched"]["persistent"] = {
-            k: pers[k] for k in ("value", "unit", "ms", "all_finished", "gpu_launches", "engine")}
-        extensions["calibration"] = calibration_measure(capi, windows=args.calibration_windows)
-        extensions["land_cover"] = land_cover_measure(capi)
-        extensions["batched"]["hbm_frac_whole_window"] = (
-            extensions["batched"]["value"] * BYTES_SINGLE / 1e9 / hbm_peak)
-        extensions["batched"]["persistent"]["hbm_frac_whole_window"] = (
-            extensions["batched"]["persistent"]["value"] * BYTES_SINGLE / 1e9 / hbm_peak)
+        # a failing extension is reported on the line instead of losing it
+        def guarded(fn, *a, **kw):
+            try:
+                return fn(*a, **kw)
+            except Exception as e:  # noqa: BLE001
+                return {"error": f"{type(e).__name__}: {e}"}
+
+        extensions["adjoint"] = guarded(adjoint_measure, capi)
+        extensions["batched"] = guarded(batch_measure, capi)
+        pers = guarded(batch_measure, capi, engine=2)
+        if "error" not in extensions["batched"]:
+            extensions["batched"]["hbm_frac_whole_window"] = (
+                extensions["batched"]["value"] * BYTES_SINGLE / 1e9 / hbm_peak)
+            extensions["batched"]["persistent"] = pers if "error" in pers else {
+                **{k: pers[k] for k in ("value", "unit", "ms", "all_finished", "gpu_launches",
+                                        "engine")},
+                "hbm_frac_whole_window": pers["value"] * BYTES_SINGLE / 1e9 / hbm_peak}
+        extensions["calibration"] = guarded(calibration_measure, capi,
+                                            windows=args.calibration_windows)
+        extensions["land_cover"] = guarded(land_cover_measure, capi)
         extensions["autotune"] = tuned
         extensions["plain_vs_fused"] = plain
         extensions["products"] = products
