@@ -70,7 +70,7 @@ def parse():
                     help="run one extension measurement alone and print it (profiling runs)")
     ap.add_argument("--calibration-windows", type=int, default=3)
     ap.add_argument("--rows-per-strip", type=int, default=None,
-                    help="strip height for --only calibration (profiling smaller cases)")
+                    help="strip height for --only calibration and --only batch")
     ap.add_argument("--engine", type=int, choices=[0, 1, 2], default=None,
                     help="step-kernel engine for --only batch (default: the library's)")
     args = ap.parse_args()
@@ -314,7 +314,7 @@ def adjoint_measure(capi):
             "adj_over_fwd": res["reverse_ms"] / res["forward_ms"]}
 
 
-def batch_measure(capi, engine=None):
+def batch_measure(capi, engine=None, rows=None, tune=False):
     """Uneven batch: 64 scenarios, square sides U{512..2048}, own DEM seeds,
     rain U[20, 100] mm/h, durations U[900, 3600] s, advanced in 300 s windows
     by graph-replayed batched launches; member-cell-steps/s over the batch."""
@@ -326,13 +326,21 @@ def batch_measure(capi, engine=None):
     dur = np.array([s.duration_s for s in scen])
     ones = np.ones(len(scen), np.float32)
     cells = np.array([s.ny * s.nx for s in scen], np.float64)
+    tuned = None
     with capi.Batch([t.z for t in terrs], [t.n for t in terrs]) as b:
         if engine is not None:
             b.set_engine(engine)
         else:
             engine = 1
+        rows = rows or ROWS
+        if rows:
+            b.set_launch(rows, 4)
         b.init(hys, ones, ones, dur)
         b.step(300.0)                      # warm-up window (graph capture)
+        if tune:                           # on the live batch after the first window
+            r, w, e, t = b.autotune(30.0)
+            tuned = {"rows_per_strip": r, "warps_per_cta": w, "engine": e, "trial_ms": t}
+            engine, rows = e, r
         b.init(hys, ones, ones, dur)
         stream = torch.cuda.current_stream()
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
@@ -355,7 +363,8 @@ def batch_measure(capi, engine=None):
             "value": units / (ms * 1e-3), "unit": "member-cell-steps/s", "ms": ms,
             "total_cells": float(cells.sum()), "member_cell_steps": units,
             "all_finished": bool(np.all(mem["t"] == dur)), "gpu_launches": launches,
-            "engine": {0: "direct loads", 1: "tma", 2: "tma persistent"}[engine]}
+            "engine": {0: "direct loads", 1: "tma", 2: "tma persistent"}[engine],
+            "rows_per_strip": rows or 64, "autotune": tuned}
 
 
 def calibration_measure(capi, windows=3):
@@ -718,14 +727,15 @@ def run_gb300(args):
                 return {"error": f"{type(e).__name__}: {e}"}
 
         extensions["adjoint"] = guarded(adjoint_measure, capi)
-        extensions["batched"] = guarded(batch_measure, capi)
-        pers = guarded(batch_measure, capi, engine=2)
+        extensions["batched"] = guarded(batch_measure, capi, tune=True)
+        pers = guarded(batch_measure, capi, engine=2,
+                       rows=extensions["batched"].get("rows_per_strip"))
         if "error" not in extensions["batched"]:
             extensions["batched"]["hbm_frac_whole_window"] = (
                 extensions["batched"]["value"] * BYTES_SINGLE / 1e9 / hbm_peak)
             extensions["batched"]["persistent"] = pers if "error" in pers else {
                 **{k: pers[k] for k in ("value", "unit", "ms", "all_finished", "gpu_launches",
-                                        "engine")},
+                                        "engine", "rows_per_strip")},
                 "hbm_frac_whole_window": pers["value"] * BYTES_SINGLE / 1e9 / hbm_peak}
         extensions["calibration"] = guarded(calibration_measure, capi,
                                             windows=args.calibration_windows)
@@ -771,7 +781,7 @@ def run_only(args):
     if args.only == "adjoint":
         res = adjoint_measure(capi)
     elif args.only == "batch":
-        res = batch_measure(capi, engine=args.engine)
+        res = batch_measure(capi, engine=args.engine, tune=args.engine is None and not ROWS)
     elif args.only == "land_cover":
         res = land_cover_measure(capi)
     else:

@@ -501,6 +501,20 @@ int flood_batch_members(flood_batch* b, double* t, int64_t* steps, double* stora
 /* Step kernels launched so far (graph replays count every launch). */
 int64_t flood_batch_launch_count(const flood_batch* b);
 
+/* Autotuner of the batched step: time every configuration (rows per strip
+ * {16, 32, 64} x warps per CTA {4, 8} with the graph-replayed TMA engine, and
+ * {16, 32, 64} x 4 warps with the persistent engine where the device has
+ * cooperative launch; direct loads without tensor maps) on the live batch,
+ * each advancing every scenario trial_s seconds past the latest current time
+ * (after an untimed run of the same trial), keep the fastest, and put the
+ * batch back exactly as it was (states, clocks, rain and volume sums).
+ * Writes the choice and its trial time (ms); any output may be NULL.
+ * Synchronous.  Errors: FLOOD_ERR_ARG (trial_s <= 0), FLOOD_ERR_STATE (before
+ * flood_batch_init), FLOOD_ERR_OOM (the state snapshot), and those of
+ * flood_batch_step. */
+int flood_batch_autotune(flood_batch* b, double trial_s, int* best_rows, int* best_warps,
+                         int* best_engine, double* best_ms, void* stream);
+
 /* ==== Allocation-free volume reduction ======================================
  * The paper has no counterpart: this is a service for callers that cannot
  * allocate device memory -- code running inside a stream capture, under a

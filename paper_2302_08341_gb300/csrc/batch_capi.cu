@@ -548,4 +548,123 @@ int flood_batch_members(flood_batch* b, double* t, int64_t* steps, double* stora
 
 int64_t flood_batch_launch_count(const flood_batch* b) { return b ? b->launches : 0; }
 
+int flood_batch_autotune(flood_batch* b, double trial_s, int* best_rows, int* best_warps,
+                         int* best_engine, double* best_ms, void* stream)
+{
+    if (!b) return bfail(nullptr, FLOOD_ERR_ARG, "batch is NULL");
+    if (!b->initialised) return bfail(b, FLOOD_ERR_STATE, "flood_batch_init has not been called");
+    if (!(trial_s > 0.0)) return bfail(b, FLOOD_ERR_ARG, "trial_s must be > 0");
+    cudaStream_t s = S_(stream);
+    const int S = b->S;
+    BCK(b, cudaStreamSynchronize(s));
+    // the batch as it is: clocks (all three slots), each scenario's current
+    // state, rain and per-scenario volume sums
+    std::vector<MemberClock> ms0((size_t)3 * S);
+    BCK(b, cudaMemcpy(ms0.data(), b->ms, sizeof(MemberClock) * ms0.size(), cudaMemcpyDeviceToHost));
+    const MemberClock* c0 = ms0.data() + (b->k % 3) * S;
+    std::vector<double> rain0(S), per((size_t)S * 2, 0.0), v((size_t)b->nslot * 2);
+    BCK(b, cudaMemcpy(rain0.data(), b->rain_acc, sizeof(double) * S, cudaMemcpyDeviceToHost));
+    BCK(b, cudaMemcpy(v.data(), b->vacc, sizeof(double) * v.size(), cudaMemcpyDeviceToHost));
+    for (const auto& t : b->tasks) {
+        per[(size_t)t.scen * 2] += v[(size_t)t.slot * 2];
+        per[(size_t)t.scen * 2 + 1] += v[(size_t)t.slot * 2 + 1];
+    }
+    size_t total = 0;
+    for (int i = 0; i < S; ++i) total += 3 * b->desc[i].plane;
+    float* snap = nullptr;
+    BCK(b, cudaMalloc(&snap, sizeof(float) * total));
+    auto copy_states = [&](bool save) -> cudaError_t {
+        size_t off = 0;
+        for (int i = 0; i < S; ++i) {
+            const size_t n = 3 * b->desc[i].plane;
+            float* cur = b->state[i] + (size_t)c0[i].cur * n;
+            cudaError_t e = cudaMemcpyAsync(save ? snap + off : cur, save ? cur : snap + off,
+                                            sizeof(float) * n, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return e;
+            off += n;
+        }
+        return cudaSuccess;
+    };
+    const int64_t k0 = b->k;
+    // put the batch back as it was, in the current task layout
+    auto restore = [&]() -> int {
+        BCK(b, copy_states(false));
+        BCK(b, cudaMemcpyAsync(b->ms, ms0.data(), sizeof(MemberClock) * ms0.size(),
+                               cudaMemcpyHostToDevice, s));
+        BCK(b, cudaMemcpyAsync(b->rain_acc, rain0.data(), sizeof(double) * S, cudaMemcpyHostToDevice, s));
+        std::vector<double> nv((size_t)b->nslot * 2, 0.0);
+        for (int i = 0; i < S; ++i) {
+            nv[(size_t)b->slot0[i] * 2] = per[(size_t)i * 2];
+            nv[(size_t)b->slot0[i] * 2 + 1] = per[(size_t)i * 2 + 1];
+        }
+        BCK(b, cudaMemcpyAsync(b->vacc, nv.data(), sizeof(double) * nv.size(), cudaMemcpyHostToDevice, s));
+        BCK(b, cudaMemsetAsync(b->err, 0, sizeof(int), s));
+        BCK(b, cudaStreamSynchronize(s));
+        b->k = k0;
+        return FLOOD_OK;
+    };
+    int rc = FLOOD_OK;
+    {
+        const cudaError_t e = copy_states(true);
+        if (e != cudaSuccess) {
+            cudaFree(snap);
+            return bfail(b, FLOOD_ERR_CUDA, std::string("snapshot: ") + cudaGetErrorString(e));
+        }
+    }
+    double t_from = 0.0;
+    for (int i = 0; i < S; ++i) t_from = std::max(t_from, std::min(c0[i].t, b->desc[i].t_end));
+    const double t_trial = t_from + trial_s;
+    struct Cand { int rows, warps, engine; };
+    std::vector<Cand> cands;
+    int dev = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    for (int r : {16, 32, 64}) {
+        if (b->d_maps) {
+            cands.push_back({r, 4, 1});
+            cands.push_back({r, 8, 1});
+            if (coop) cands.push_back({r, 4, 2});
+        } else {
+            cands.push_back({r, 4, 0});
+            cands.push_back({r, 8, 0});
+        }
+    }
+    const int rows0 = b->rows_per_strip, warps0 = b->warps_per_cta, eng0 = b->engine;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e300;
+    Cand bc{rows0, warps0, eng0};
+    for (const Cand& cd : cands) {
+        if ((rc = flood_batch_set_launch(b, cd.rows, cd.warps))) break;
+        if ((rc = flood_batch_set_engine(b, cd.engine))) break;
+        if ((rc = restore())) break;
+        if ((rc = flood_batch_step(b, t_trial, stream))) break;  // warm-up: graph capture, caches
+        if ((rc = restore())) break;
+        cudaEventRecord(e0, s);
+        if ((rc = flood_batch_step(b, t_trial, stream))) break;
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (t < best) {
+            best = t;
+            bc = cd;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int rc2 = flood_batch_set_launch(b, rc ? rows0 : bc.rows, rc ? warps0 : bc.warps);
+    if (!rc2) rc2 = flood_batch_set_engine(b, rc ? eng0 : bc.engine);
+    if (!rc2) rc2 = restore();
+    cudaFree(snap);
+    if (rc) return rc;
+    if (rc2) return rc2;
+    if (best_rows) *best_rows = bc.rows;
+    if (best_warps) *best_warps = bc.warps;
+    if (best_engine) *best_engine = bc.engine;
+    if (best_ms) *best_ms = best;
+    return FLOOD_OK;
+}
+
 }  // extern "C"

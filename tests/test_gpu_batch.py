@@ -108,6 +108,30 @@ def test_persistent_batch_runs_windows_in_one_launch_each(capi):
         assert np.array_equal(b.members()["t"], dur)
 
 
+def test_batch_autotune_leaves_the_batch_unchanged(capi):
+    """The batched-step autotuner times its candidates on the live batch and
+    puts it back: continuing after the tuning reaches the same states, clocks
+    and rain, bit for bit, as a run that was never tuned."""
+    terrs, hys, rm, sc, dur = _scenarios()
+    res = []
+    for tune in (False, True):
+        with capi.Batch([t.z for t in terrs], [t.n for t in terrs]) as b:
+            b.init(hys, rm, sc, dur)
+            b.step(300.0)
+            if tune:
+                rows, warps, engine, ms = b.autotune(20.0)
+                assert rows in (16, 32, 64) and warps in (4, 8) and engine in (1, 2) and ms > 0
+            b.step(600.0)
+            res.append(([b.get_state(i) for i in range(len(SHAPES))], b.members()))
+    for x, y in zip(res[0][0], res[1][0]):
+        for k in range(3):
+            assert np.array_equal(x[k], y[k])
+    for key in ("t", "steps", "rain"):
+        assert np.array_equal(res[0][1][key], res[1][1][key]), key
+    for key in ("outflow", "clamp", "storage"):
+        assert np.allclose(res[0][1][key], res[1][1][key], rtol=1e-9, atol=1e-12), key
+
+
 def test_batch_rejects_bad_arguments(capi):
     z = np.zeros((4, 4), np.float32)
     with pytest.raises(capi.FloodError):
