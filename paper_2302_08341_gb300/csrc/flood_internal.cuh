@@ -87,6 +87,7 @@ struct StepArgs {
 struct TmaArgs {
     CUtensorMap state_map;
     CUtensorMap static_map;
+    CUtensorMap hm_map;     // running maxima (ld, ny, M), box 128 x 1 x 1 (tracking only)
     StepArgs a;
 };
 

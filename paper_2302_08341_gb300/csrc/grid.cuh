@@ -21,6 +21,7 @@ struct flood_grid {
     long long wait_budget = -1;   // TMA row-wait limit of the step in clock cycles (< 0: default)
     CUtensorMap static_map{};
     CUtensorMap state_map{};
+    CUtensorMap hm_map;          // running maxima, for the TMA step (tracking)
     bool maps_ok = false;
     // ensemble
     int M = 0, nb = 0;

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "grid.cuh"
+#include "tma.cuh"
 
 #define CK FLOOD_CK
 
@@ -138,6 +139,9 @@ extern "C" int flood_track_max_depth(flood_grid* g, int on, void* stream)
     if (!g->hmax_field) {
         int rc = flood::dalloc(g, &g->hmax_field, (size_t)g->M * g->plane);
         if (rc) return rc;
+        if (flood::encode_map_3d(&g->hm_map, g->hmax_field, g->ld, g->ny, (uint64_t)g->M,
+                                 sizeof(float) * g->ld, sizeof(float) * g->plane, 128, 1, 1) != 0)
+            return flood::fail(g, FLOOD_ERR_CUDA, "tensor map of the running maxima");
     }
     init_max_kernel<<<g->n_sm * 4, 512, 0, s>>>(g->state, g->ms + (g->k % 3) * g->M, g->M, g->plane,
                                                 g->hmax_field);

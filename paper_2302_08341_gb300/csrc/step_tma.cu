@@ -17,7 +17,7 @@ constexpr int kSpan = kTmaSpan;
 // CK: the step may write checkpoints (the adjoint's logged forward); the
 // ordinary step is compiled without that path.
 template <int WM, bool TRACK_MAX, bool LC, int LIM, bool CK, bool HOOK = false>
-__global__ void __launch_bounds__(32 * WM, (LC ? 16 : 20) / WM) step_tma_kernel(const __grid_constant__ TmaArgs t)
+__global__ void __launch_bounds__(32 * WM, (LC || TRACK_MAX ? 16 : 20) / WM) step_tma_kernel(const __grid_constant__ TmaArgs t)
 {
     extern __shared__ unsigned char smem_raw[];
     const StepArgs& a = t.a;
@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(32 * WM, (LC ? 16 : 20) / WM) step_tma_kernel(
 
     uint32_t bar0;
     unsigned char* my_stages;
-    tma_march_smem(smem_raw, WM, w, bar0, my_stages);
+    tma_march_smem(smem_raw, WM, w, bar0, my_stages, TRACK_MAX ? kTmaStageBytesHm : kTmaStageBytes);
 
     const size_t mstride = 3 * a.plane;
     // each warp is its own member here: the warp at the first span and strip owns its clock
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(32 * WM, (LC ? 16 : 20) / WM) step_tma_kernel(
     if (!tma_march<TRACK_MAX, LC, LIM, HOOK>(&t.state_map, &t.static_map, (pl.cur * a.M + m) * 3, bar0,
                                   my_stages, dst, ck, hm, a.err, a.plane, a.ny, a.nx, a.ld, c0, r0,
                                   r1, lane, k, pl.dt_dx, a.scale[m], pl.dr, a.east_out, a.south_out,
-                                  mo, &lk, a.wait_budget))
+                                  mo, &lk, a.wait_budget, &t.hm_map, m))
         return;
 
     if (mo.bad) atomicOr(a.err, 1);
@@ -131,10 +131,10 @@ __global__ void __launch_bounds__(32 * WM, 20 / WM) replay_tma_kernel(const __gr
     if (mo.bad) atomicOr(a.err, 1);
 }
 
-template <int WM>
+template <int WM, bool TRACK = false>
 size_t tma_smem_bytes()
 {
-    return tma_march_smem_bytes(WM);
+    return tma_march_smem_bytes(WM, TRACK ? kTmaStageBytesHm : kTmaStageBytes);
 }
 
 }  // namespace
@@ -174,7 +174,7 @@ void launch_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
     const int strips = (a.ny + a.rows_per_strip - 1) / a.rows_per_strip;
     if (members_per_cta >= 4) {
         static bool attr = false;
-        const size_t shm = tma_smem_bytes<4>();
+        const size_t shm = tma_smem_bytes<4, TRACK_MAX>();
         if (!attr) {
             cudaFuncSetAttribute(step_tma_kernel<4, TRACK_MAX, LC, LIM, CK, HOOK>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
@@ -183,7 +183,7 @@ void launch_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
         dim3 grid((a.M + 3) / 4, spans, strips), block(32, 4);
         step_tma_kernel<4, TRACK_MAX, LC, LIM, CK, HOOK><<<grid, block, shm, s>>>(t);
     } else {
-        const size_t shm = tma_smem_bytes<1>();
+        const size_t shm = tma_smem_bytes<1, TRACK_MAX>();
         dim3 grid(a.M, spans, strips), block(32, 1);
         step_tma_kernel<1, TRACK_MAX, LC, LIM, CK, HOOK><<<grid, block, shm, s>>>(t);
     }

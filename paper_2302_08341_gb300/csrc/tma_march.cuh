@@ -29,19 +29,22 @@ static_assert((kTmaNS & (kTmaNS - 1)) == 0, "ring index arithmetic needs a power
 
 // Dynamic shared memory of a CTA of `warps` warps: barriers, then each warp's
 // stages.
-__host__ __device__ constexpr size_t tma_march_smem_bytes(int warps)
+__host__ __device__ constexpr size_t tma_march_smem_bytes(int warps, int stage_bytes = kTmaStageBytes)
 {
-    return 128 + 128 * ((8 * kTmaNS * warps + 127) / 128) + (size_t)kTmaNS * kTmaStageBytes * warps;
+    return 128 + 128 * ((8 * kTmaNS * warps + 127) / 128) + (size_t)kTmaNS * stage_bytes * warps;
 }
+constexpr int kTmaHmOff = kTmaStageBytes;              // running maxima: 128 floats after z, n
+constexpr int kTmaStageBytesHm = kTmaStageBytes + 512;
 
 // This warp's barriers and stages inside the CTA's dynamic shared memory.
 __device__ __forceinline__ void tma_march_smem(unsigned char* smem_raw, int warps, int w,
-                                               uint32_t& bar0, unsigned char*& my_stages)
+                                               uint32_t& bar0, unsigned char*& my_stages,
+                                               int stage_bytes = kTmaStageBytes)
 {
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
     bar0 = smem_u32(base) + 8u * kTmaNS * w;
-    my_stages = base + 128 * ((8 * kTmaNS * warps + 127) / 128) + kTmaNS * kTmaStageBytes * w;
+    my_stages = base + 128 * ((8 * kTmaNS * warps + 127) / 128) + kTmaNS * stage_bytes * w;
 }
 
 __device__ __forceinline__ void tma_lds4(float (&v)[4], const float* p)
@@ -58,7 +61,9 @@ __device__ __forceinline__ void tma_store4(float* p, const float (&v)[4])
 // state_map: (ld, ny, planes) with the source h, qx, qy at planes
 // [plane0, plane0 + 3); static_map: (ld, ny, 2) with z then n.  Writes the
 // new state to dst (and ck when non-null); TRACK_MAX: also raises the
-// running maximum depth at hm; LC: land cover (roughness by class from lk,
+// running maximum depth at hm, whose old values arrive with each row through
+// hm_map (member plane hm_plane, 128 columns from c0; a 3.3 KB stage, so four
+// CTAs of four warps per SM); LC: land cover (roughness by class from lk,
 // the class's share of the rain and its drainage).  Each is a separate
 // instantiation, so the plain step carries no trace of them.  Returns false
 // if a wait gave up.  WAIT_HOOK: each row wait may take wait_budget clock
@@ -73,13 +78,14 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
                                           const FaceK& k, float dt_dx, float s, float dr,
                                           int east_out, int south_out, MarchOut& out,
                                           const LandK* lk = nullptr,
-                                          long long wait_budget = kTmaWaitBudget)
+                                          long long wait_budget = kTmaWaitBudget,
+                                          const CUtensorMap* hm_map = nullptr, int hm_plane = 0)
 {
     constexpr int kNS = kTmaNS;
     constexpr int kBox = kTmaBox;
     constexpr int kStaticOff = kTmaStaticOff;
-    constexpr int kStageBytes = kTmaStageBytes;
-    constexpr uint32_t kTx = kTmaTx;
+    constexpr int kStageBytes = TRACK_MAX ? kTmaStageBytesHm : kTmaStageBytes;
+    constexpr uint32_t kTx = kTmaTx + (TRACK_MAX ? 512u : 0u);
     constexpr int kZ = kStaticOff / 4;
     constexpr int kN = kZ + kBox;
     constexpr long long kWaitBudget = kTmaWaitBudget;
@@ -106,6 +112,7 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
         mbar_arrive_expect_tx(bar, kTx);
         tma_load_3d(dsts, state_map, c0 - 4, row, plane0, bar);
         tma_load_3d(dsts + kStaticOff, static_map, c0 - 4, row, 0, bar);
+        if (TRACK_MAX) tma_load_3d(dsts + kTmaHmOff, hm_map, c0, row, hm_plane, bar);
     };
     for (; issued < rb && issued < ra + kNS; ++issued)
         if (lane == 0) issue(issued);
@@ -215,7 +222,7 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
         float hS[4] = {0, 0, 0, 0}, zS[4] = {0, 0, 0, 0}, nS[4] = {0, 0, 0, 0};
         float qxo[4], qyo[4];
         float4 hmo = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (TRACK_MAX && act) hmo = *reinterpret_cast<const float4*>(hm + o);
+        if (TRACK_MAX) hmo = *reinterpret_cast<const float4*>(P + kTmaHmOff / 4 + 4 * lane);
         tma_lds4(qxo, P + kBox + x0);
         tma_lds4(qyo, P + 2 * kBox + x0);
         uint32_t clsS = 0;
