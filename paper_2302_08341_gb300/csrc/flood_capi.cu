@@ -192,6 +192,7 @@ int launch_steps(flood_grid* g, int64_t count, double t_end, cudaStream_t s)
             t.state_map = g->state_map;
             t.static_map = g->static_map;
             if (a.hmax_field) t.hm_map = g->hm_map;
+            if (a.lc_on) t.cls_map = g->cls_map;
             t.a = a;
             if (const int e = flood::launch_step_tma(t, g->members_per_cta, s))
                 return fail(g, FLOOD_ERR_STATE,

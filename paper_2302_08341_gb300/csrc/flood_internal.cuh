@@ -88,6 +88,7 @@ struct TmaArgs {
     CUtensorMap state_map;
     CUtensorMap static_map;
     CUtensorMap hm_map;     // running maxima (ld, ny, M), box 128 x 1 x 1 (tracking only)
+    CUtensorMap cls_map;    // land classes (ld, ny, 1) as bytes, box 160 x 1 x 1 (land cover only)
     StepArgs a;
 };
 
@@ -338,6 +339,9 @@ int launch_step_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s);
 // t.state_map over the adjoint's segment slots (box: 3 planes)
 void launch_replay_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s);
 int tma_box_cols();
+int encode_map_3d_u8(CUtensorMap* map, const void* base, uint64_t d0, uint64_t d1, uint64_t d2,
+                     uint64_t stride1_bytes, uint64_t stride2_bytes, uint32_t b0, uint32_t b1,
+                     uint32_t b2);
 int step_nslot(int ny, int nx, int rows_per_strip);
 
 }  // namespace flood

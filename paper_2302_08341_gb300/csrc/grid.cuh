@@ -22,6 +22,7 @@ struct flood_grid {
     CUtensorMap static_map{};
     CUtensorMap state_map{};
     CUtensorMap hm_map;          // running maxima, for the TMA step (tracking)
+    CUtensorMap cls_map;         // land classes as bytes, for the TMA step (land cover)
     bool maps_ok = false;
     // ensemble
     int M = 0, nb = 0;

@@ -116,6 +116,9 @@ extern "C" int flood_set_land_cover(flood_grid* g, const uint8_t* cls, int n_cla
     int rc = flood::dalloc(g, &g->cls8, pad.size());
     if (rc) return rc;
     CK(g, cudaMemcpy(g->cls8, pad.data(), pad.size(), cudaMemcpyHostToDevice));
+    if (flood::encode_map_3d_u8(&g->cls_map, g->cls8, g->ld, g->ny, 1, g->ld, (uint64_t)g->ld * g->ny,
+                                160, 1, 1) != 0)
+        return flood::fail(g, FLOOD_ERR_CUDA, "tensor map of the land classes");
     for (int q = 0; q < kMaxClasses; ++q) {
         g->lc_runoff[q] = runoff[q];
         g->lc_drains[q] = drains[q];

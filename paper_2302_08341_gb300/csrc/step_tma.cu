@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(32 * WM, (LC || TRACK_MAX ? 16 : 20) / WM) ste
 
     uint32_t bar0;
     unsigned char* my_stages;
-    tma_march_smem(smem_raw, WM, w, bar0, my_stages, TRACK_MAX ? kTmaStageBytesHm : kTmaStageBytes);
+    tma_march_smem(smem_raw, WM, w, bar0, my_stages, tma_stage_bytes(TRACK_MAX, LC));
 
     const size_t mstride = 3 * a.plane;
     // each warp is its own member here: the warp at the first span and strip owns its clock
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(32 * WM, (LC || TRACK_MAX ? 16 : 20) / WM) ste
     if (!tma_march<TRACK_MAX, LC, LIM, HOOK>(&t.state_map, &t.static_map, (pl.cur * a.M + m) * 3, bar0,
                                   my_stages, dst, ck, hm, a.err, a.plane, a.ny, a.nx, a.ld, c0, r0,
                                   r1, lane, k, pl.dt_dx, a.scale[m], pl.dr, a.east_out, a.south_out,
-                                  mo, &lk, a.wait_budget, &t.hm_map, m))
+                                  mo, &lk, a.wait_budget, &t.hm_map, m, &t.cls_map))
         return;
 
     if (mo.bad) atomicOr(a.err, 1);
@@ -131,16 +131,21 @@ __global__ void __launch_bounds__(32 * WM, 20 / WM) replay_tma_kernel(const __gr
     if (mo.bad) atomicOr(a.err, 1);
 }
 
-template <int WM, bool TRACK = false>
+template <int WM, bool TRACK = false, bool LC = false>
 size_t tma_smem_bytes()
 {
-    return tma_march_smem_bytes(WM, TRACK ? kTmaStageBytesHm : kTmaStageBytes);
+    return tma_march_smem_bytes(WM, tma_stage_bytes(TRACK, LC));
 }
 
 }  // namespace
 
-int encode_map_3d(CUtensorMap* map, const void* base, uint64_t d0, uint64_t d1, uint64_t d2,
-                  uint64_t stride1_bytes, uint64_t stride2_bytes, uint32_t b0, uint32_t b1, uint32_t b2)
+namespace {
+
+// A tiled 3-D tensor map through the driver's encoder, obtained by the
+// runtime's entry-point query (no link against libcuda).
+int encode_map_3d_as(CUtensorMapDataType type, CUtensorMap* map, const void* base, uint64_t d0,
+                     uint64_t d1, uint64_t d2, uint64_t stride1_bytes, uint64_t stride2_bytes,
+                     uint32_t b0, uint32_t b1, uint32_t b2)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -156,10 +161,27 @@ int encode_map_3d(CUtensorMap* map, const void* base, uint64_t d0, uint64_t d1, 
     const cuuint64_t strides[2] = {stride1_bytes, stride2_bytes};
     const cuuint32_t box[3] = {b0, b1, b2};
     const cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides,
-                        box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    CUresult r = encode(map, type, 3, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : -2;
+}
+
+}  // namespace
+
+int encode_map_3d(CUtensorMap* map, const void* base, uint64_t d0, uint64_t d1, uint64_t d2,
+                  uint64_t stride1_bytes, uint64_t stride2_bytes, uint32_t b0, uint32_t b1, uint32_t b2)
+{
+    return encode_map_3d_as(CU_TENSOR_MAP_DATA_TYPE_FLOAT32, map, base, d0, d1, d2, stride1_bytes,
+                            stride2_bytes, b0, b1, b2);
+}
+
+int encode_map_3d_u8(CUtensorMap* map, const void* base, uint64_t d0, uint64_t d1, uint64_t d2,
+                     uint64_t stride1_bytes, uint64_t stride2_bytes, uint32_t b0, uint32_t b1,
+                     uint32_t b2)
+{
+    return encode_map_3d_as(CU_TENSOR_MAP_DATA_TYPE_UINT8, map, base, d0, d1, d2, stride1_bytes,
+                            stride2_bytes, b0, b1, b2);
 }
 
 int tma_box_cols() { return kTmaBox; }
@@ -174,7 +196,7 @@ void launch_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
     const int strips = (a.ny + a.rows_per_strip - 1) / a.rows_per_strip;
     if (members_per_cta >= 4) {
         static bool attr = false;
-        const size_t shm = tma_smem_bytes<4, TRACK_MAX>();
+        const size_t shm = tma_smem_bytes<4, TRACK_MAX, LC>();
         if (!attr) {
             cudaFuncSetAttribute(step_tma_kernel<4, TRACK_MAX, LC, LIM, CK, HOOK>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
@@ -183,7 +205,7 @@ void launch_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
         dim3 grid((a.M + 3) / 4, spans, strips), block(32, 4);
         step_tma_kernel<4, TRACK_MAX, LC, LIM, CK, HOOK><<<grid, block, shm, s>>>(t);
     } else {
-        const size_t shm = tma_smem_bytes<1, TRACK_MAX>();
+        const size_t shm = tma_smem_bytes<1, TRACK_MAX, LC>();
         dim3 grid(a.M, spans, strips), block(32, 1);
         step_tma_kernel<1, TRACK_MAX, LC, LIM, CK, HOOK><<<grid, block, shm, s>>>(t);
     }

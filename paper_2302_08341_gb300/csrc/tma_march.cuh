@@ -35,6 +35,12 @@ __host__ __device__ constexpr size_t tma_march_smem_bytes(int warps, int stage_b
 }
 constexpr int kTmaHmOff = kTmaStageBytes;              // running maxima: 128 floats after z, n
 constexpr int kTmaStageBytesHm = kTmaStageBytes + 512;
+// land classes: 160 bytes (columns c0 - 16 .. c0 + 143) after the maxima, if any
+__host__ __device__ constexpr int tma_cls_off(bool track) { return kTmaStageBytes + (track ? 512 : 0); }
+__host__ __device__ constexpr int tma_stage_bytes(bool track, bool lc)
+{
+    return tma_cls_off(track) + (lc ? 256 : 0);
+}
 
 // This warp's barriers and stages inside the CTA's dynamic shared memory.
 __device__ __forceinline__ void tma_march_smem(unsigned char* smem_raw, int warps, int w,
@@ -64,7 +70,8 @@ __device__ __forceinline__ void tma_store4(float* p, const float (&v)[4])
 // running maximum depth at hm, whose old values arrive with each row through
 // hm_map (member plane hm_plane, 128 columns from c0; a 3.3 KB stage, so four
 // CTAs of four warps per SM); LC: land cover (roughness by class from lk,
-// the class's share of the rain and its drainage).  Each is a separate
+// the class's share of the rain and its drainage; the class bytes of each
+// row, columns c0 - 16 .. c0 + 143, arrive with the row through cls_map).  Each is a separate
 // instantiation, so the plain step carries no trace of them.  Returns false
 // if a wait gave up.  WAIT_HOOK: each row wait may take wait_budget clock
 // cycles instead of kTmaWaitBudget (a failure-detection hook; the copies
@@ -79,13 +86,15 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
                                           int east_out, int south_out, MarchOut& out,
                                           const LandK* lk = nullptr,
                                           long long wait_budget = kTmaWaitBudget,
-                                          const CUtensorMap* hm_map = nullptr, int hm_plane = 0)
+                                          const CUtensorMap* hm_map = nullptr, int hm_plane = 0,
+                                          const CUtensorMap* cls_map = nullptr)
 {
     constexpr int kNS = kTmaNS;
     constexpr int kBox = kTmaBox;
     constexpr int kStaticOff = kTmaStaticOff;
-    constexpr int kStageBytes = TRACK_MAX ? kTmaStageBytesHm : kTmaStageBytes;
-    constexpr uint32_t kTx = kTmaTx + (TRACK_MAX ? 512u : 0u);
+    constexpr int kStageBytes = tma_stage_bytes(TRACK_MAX, LC);
+    constexpr int kClsOff = tma_cls_off(TRACK_MAX);
+    constexpr uint32_t kTx = kTmaTx + (TRACK_MAX ? 512u : 0u) + (LC ? 160u : 0u);
     constexpr int kZ = kStaticOff / 4;
     constexpr int kN = kZ + kBox;
     constexpr long long kWaitBudget = kTmaWaitBudget;
@@ -113,6 +122,19 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
         tma_load_3d(dsts, state_map, c0 - 4, row, plane0, bar);
         tma_load_3d(dsts + kStaticOff, static_map, c0 - 4, row, 0, bar);
         if (TRACK_MAX) tma_load_3d(dsts + kTmaHmOff, hm_map, c0, row, hm_plane, bar);
+        if (LC) tma_load_3d(dsts + kClsOff, cls_map, c0 - 16, row, 0, bar);
+    };
+    // land classes of a staged row: the lane's four cells, and the cells just
+    // east and west of the span
+    auto cls_of = [&](const float* P) -> uint32_t {
+        return *reinterpret_cast<const uint32_t*>(reinterpret_cast<const unsigned char*>(P) +
+                                                  kClsOff + 16 + 4 * lane);
+    };
+    auto cls_e = [&](const float* P) -> uint32_t {
+        return reinterpret_cast<const unsigned char*>(P)[kClsOff + 16 + kTmaSpan];
+    };
+    auto cls_w = [&](const float* P) -> uint32_t {
+        return reinterpret_cast<const unsigned char*>(P)[kClsOff + 15];
     };
     for (; issued < rb && issued < ra + kNS; ++issued)
         if (lane == 0) issue(issued);
@@ -163,21 +185,16 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
         drain_and_fail();
         return false;
     }
-    // land classes (LC): the current row's, and the next row's loaded one
-    // iteration ahead of its use; likewise the classes of the cells just
-    // east and west of the span (every lane loads the same two bytes)
-    uint32_t clsC = 0, clsNext = 0, eC = 0, wC = 0, eN = 0, wN = 0;
-    const bool has_e = c0 + kTmaSpan < nx, has_w = c0 > 0;
-    if (LC) {
-        if (act) {
-            clsC = cls_word(lk->cls, (size_t)r0 * ld + c);
-            if (r0 + 1 < ny) clsNext = cls_word(lk->cls, (size_t)(r0 + 1) * ld + c);
-        }
-        if (has_e) eC = lk->cls[(size_t)r0 * ld + c0 + kTmaSpan];
-        if (has_w) wC = lk->cls[(size_t)r0 * ld + c0 - 1];
-    }
+    // land classes (LC): they come with each staged row (zeros past the
+    // grid's edges, where no link uses them)
+    uint32_t clsC = 0, eC = 0, wC = 0, eN = 0, wN = 0;
     {
         const float* P = row_ptr(r0);
+        if (LC) {
+            clsC = cls_of(P);
+            eC = cls_e(P);
+            wC = cls_w(P);
+        }
         tma_lds4(hC, P + x0);
         tma_lds4(zC, P + kZ + x0);
         if (LC)
@@ -190,7 +207,7 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
             tma_lds4(hU, U + x0);
             tma_lds4(zU, U + kZ + x0);
             if (LC)  // whole warp: the lookups are shuffles
-                land_n4(nU, act ? cls_word(lk->cls, (size_t)(r0 - 1) * ld + c) : 0u, *lk);
+                land_n4(nU, cls_of(U), *lk);
             else
                 tma_lds4(nU, U + kN + x0);
             tma_lds4(qU, U + 2 * kBox + x0);
@@ -226,17 +243,13 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
         tma_lds4(qxo, P + kBox + x0);
         tma_lds4(qyo, P + 2 * kBox + x0);
         uint32_t clsS = 0;
-        if (LC) {
-            clsS = clsNext;
-            if (act && r + 2 < ny) clsNext = cls_word(lk->cls, o + 2 * (size_t)ld);
-            if (has_s) {
-                const size_t rs = (size_t)(r + 1) * ld;
-                if (has_e) eN = lk->cls[rs + c0 + kTmaSpan];
-                if (has_w) wN = lk->cls[rs + c0 - 1];
-            }
-        }
         if (has_s) {
             const float* Q = row_ptr(r + 1);
+            if (LC) {
+                clsS = cls_of(Q);
+                eN = cls_e(Q);
+                wN = cls_w(Q);
+            }
             tma_lds4(hS, Q + x0);
             tma_lds4(zS, Q + kZ + x0);
             if (LC)
