@@ -34,7 +34,6 @@ __host__ __device__ constexpr size_t tma_march_smem_bytes(int warps, int stage_b
     return 128 + 128 * ((8 * kTmaNS * warps + 127) / 128) + (size_t)kTmaNS * stage_bytes * warps;
 }
 constexpr int kTmaHmOff = kTmaStageBytes;              // running maxima: 128 floats after z, n
-constexpr int kTmaStageBytesHm = kTmaStageBytes + 512;
 // land classes: 160 bytes (columns c0 - 16 .. c0 + 143) after the maxima, if any
 __host__ __device__ constexpr int tma_cls_off(bool track) { return kTmaStageBytes + (track ? 512 : 0); }
 __host__ __device__ constexpr int tma_stage_bytes(bool track, bool lc)
