@@ -223,7 +223,9 @@ int flood_adjoint_timing(const flood_grid* g, double* forward_ms, double* revers
  * flood_inflow_volume and storage = rain + inflow - outflow + clamp
  * (- drained).  n_blocks = 0 removes the boundary.  Synchronous.
  * Errors: FLOOD_ERR_ARG (rows outside the grid, negative or non-finite
- * discharges).  Not covered by flood_adjoint (refused). */
+ * discharges).  flood_adjoint covers it: the inflow flux is prescribed, so it
+ * has no derivative of its own, but it enters the depths (and the clamp
+ * decisions) that every other derivative is taken at. */
 int flood_set_inflow(flood_grid* g, int r0, int r1, const float* series, int n_blocks);
 int flood_inflow_volume(flood_grid* g, double* volume);
 

@@ -476,7 +476,11 @@ void orc_step_adjoint(const orc_params* p, const double* z, const double* n, dou
     double* dx1 = (double*)calloc(nqx * 4, sizeof(double));   /* d/dh1, d/dh2, d/dq, d/dnl */
     double* dy1 = (double*)calloc(nqy * 4, sizeof(double));
     double* lt = (double*)calloc((size_t)ny * nx, sizeof(double));
-    /* recompute the forward links with their derivatives */
+    /* recompute the forward links with their derivatives; an inflow link on
+       the west edge is prescribed (no derivative) but enters the depth that
+       decides the clamp */
+    if (p->inflow)
+        for (int r = p->inflow_r0; r < p->inflow_r1; ++r) qxn[IQX(r, 0)] = p->inflow_q;
     for (int r = 0; r < ny; ++r)
         for (int c = 1; c <= nx; ++c) {
             double* dd = dx1 + IQX(r, c) * 4;
@@ -591,14 +595,14 @@ double orc_loss_and_grad(const orc_params* p, const double* z, const double* n, 
                          long* n_steps_out)
 {
     const int ny = p->ny, nx = p->nx;
-    if (p->rc || p->drain || p->inflow) return NAN;  /* the reverse mode covers neither land cover
-                                                        nor inflow boundaries */
+    if (p->rc || p->drain) return NAN;  /* the reverse mode does not cover land cover */
     const size_t nc = (size_t)ny * nx, nqx = (size_t)ny * (nx + 1), nqy = (size_t)(ny + 1) * nx;
     const size_t per = nc + nqx + nqy;
     long cap = 1024, nst = 0;
     double* traj = (double*)malloc(sizeof(double) * per * (size_t)(cap + 1));
     double* dts = (double*)malloc(sizeof(double) * (size_t)cap);
     double* rates = (double*)malloc(sizeof(double) * (size_t)cap);
+    double* qins = (double*)malloc(sizeof(double) * (size_t)cap);   /* inflow flux per step */
     int* sample_after = (int*)malloc(sizeof(int) * (size_t)cap);   /* sample index or -1 */
     double* h = (double*)malloc(sizeof(double) * nc);
     double* qx = (double*)calloc(nqx, sizeof(double));
@@ -616,6 +620,7 @@ double orc_loss_and_grad(const orc_params* p, const double* z, const double* n, 
                 traj = (double*)realloc(traj, sizeof(double) * per * (size_t)(cap + 1));
                 dts = (double*)realloc(dts, sizeof(double) * (size_t)cap);
                 rates = (double*)realloc(rates, sizeof(double) * (size_t)cap);
+                qins = (double*)realloc(qins, sizeof(double) * (size_t)cap);
                 sample_after = (int*)realloc(sample_after, sizeof(int) * (size_t)cap);
             }
             double* st = traj + per * (size_t)nst;
@@ -625,9 +630,14 @@ double orc_loss_and_grad(const orc_params* p, const double* z, const double* n, 
             double t_next;
             double dt = orc_dt(p, orc_hmax(ny, nx, h), t, t_end, &t_next);
             double rate = orc_rain_rate(p, hyeto, n_blocks, t);
-            orc_step(p, z, n, scale, rate * rain_mult, dt, h, qx, qy, qxs, qys, &vol);
+            orc_params ps = *p;
+            if (p->inflow)
+                ps.inflow_q = orc_rain_rate(p, p->inflow, p->inflow_blocks, t) /
+                              (p->dx * (double)(p->inflow_r1 - p->inflow_r0));
+            orc_step(&ps, z, n, scale, rate * rain_mult, dt, h, qx, qy, qxs, qys, &vol);
             dts[nst] = dt;
             rates[nst] = rate;
+            qins[nst] = ps.inflow_q;
             sample_after[nst] = -1;
             t = t_next;
             ++nst;
@@ -655,12 +665,14 @@ double orc_loss_and_grad(const orc_params* p, const double* z, const double* n, 
                 lh[cells[g]] += 2.0 * (hk1[cells[g]] - d[(size_t)s * G + g]);
         }
         const double* st = traj + per * (size_t)k;
-        orc_step_adjoint(p, z, n, scale, rates[k], rain_mult, dts[k], st, st + nc, st + nc + nqx,
+        orc_params ps = *p;
+        ps.inflow_q = qins[k];
+        orc_step_adjoint(&ps, z, n, scale, rates[k], rain_mult, dts[k], st, st + nc, st + nc + nqx,
                          lh, lqx, lqy, grad_n, grad_rain, grad_scale);
     }
     memcpy(grad_h0, lh, sizeof(double) * nc);
     if (n_steps_out) *n_steps_out = nst;
-    free(lh); free(lqx); free(lqy); free(traj); free(dts); free(rates); free(sample_after);
+    free(lh); free(lqx); free(lqy); free(traj); free(dts); free(rates); free(qins); free(sample_after);
     free(h); free(qx); free(qy); free(qxs); free(qys);
     return loss;
 }

@@ -70,7 +70,6 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
         return flood::fail(g, FLOOD_ERR_ARG, "invalid flood_loss_spec");
     if (ckpt_every < 0) return flood::fail(g, FLOOD_ERR_ARG, "ckpt_every must be >= 0");
     if (g->lc_on) return flood::fail(g, FLOOD_ERR_ARG, "the adjoint does not cover land cover");
-    if (g->inflow) return flood::fail(g, FLOOD_ERR_ARG, "the adjoint does not cover inflow boundaries");
     cudaStream_t s = S(stream);
     const int M = g->M, ns = L->n_samples, G = L->n_gauges;
     const size_t ms = 3 * g->plane;
