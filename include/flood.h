@@ -492,6 +492,15 @@ int flood_batch_set_launch(flood_batch* b, int rows_per_strip, int warps_per_cta
  * (engines 1-2 without tensor maps, engine 2 without cooperative launch). */
 int flood_batch_set_engine(flood_batch* b, int engine);
 
+/* Failure-detection hook of the persistent batched form: the number of SM
+ * clock cycles a CTA may wait at the grid barrier (default 2e8, about 0.1 s;
+ * cycles < 0 restores it).  A wait that runs out records FLOOD_ERR_TIMEOUT in
+ * the batch's error word and every CTA leaves at its next barrier (no copy is
+ * in flight at a barrier); the flood_batch_step call returns FLOOD_ERR_TIMEOUT
+ * and flood_batch_init clears the word.  0 makes a CTA that is not the last
+ * to arrive give up at once.  Errors: FLOOD_ERR_ARG. */
+int flood_batch_set_wait_budget(flood_batch* b, int64_t cycles);
+
 /* Scenario i's state as [ny[i]][nx[i]] FP32 arrays (any may be NULL). */
 int flood_batch_get_state(flood_batch* b, int i, float* h, float* qx, float* qy, void* stream);
 

@@ -35,7 +35,7 @@ EXPORTED = ["flood_default_params", "flood_last_error", "flood_create_grid", "fl
             "flood_batch_set_engine", "flood_track_max_depth", "flood_get_max_depth",
             "flood_ensemble_products", "flood_set_land_cover", "flood_set_land_params",
             "flood_get_land_params", "flood_drained_volume", "flood_flow_sample", "flood_set_inflow",
-            "flood_inflow_volume", "flood_batch_autotune"]
+            "flood_inflow_volume", "flood_batch_autotune", "flood_batch_set_wait_budget"]
 
 
 class LandClass(C.Structure):
@@ -123,6 +123,7 @@ def lib(path: str = LIB_PATH):
     L.flood_adjoint_timing.argtypes = [_VP, _VP, _VP]
     L.flood_set_wait_budget.argtypes = [_VP, C.c_int64]
     L.flood_batch_autotune.argtypes = [_VP, C.c_double, _VP, _VP, _VP, _VP, _VP]
+    L.flood_batch_set_wait_budget.argtypes = [_VP, C.c_int64]
     L.flood_autotune.argtypes = [_VP, C.c_int, _VP, _VP, _VP, _VP, _VP]
     L.flood_storage_static.argtypes = [_VP, C.c_int, C.c_int, C.c_int, C.c_double, _VP, _VP]
     L.flood_set_roughness_factor.argtypes = [_VP, C.c_int, C.c_int, _VP, _VP]
@@ -583,6 +584,11 @@ class Batch:
     def set_launch(self, rows_per_strip, warps_per_cta=4):
         _bcheck(lib().flood_batch_set_launch(self.h, int(rows_per_strip), int(warps_per_cta)),
                 self.h)
+
+    def set_wait_budget(self, cycles):
+        """Clock-cycle limit of the persistent form's grid-barrier waits (< 0:
+        the default); a failure-detection hook (flood_batch_set_wait_budget)."""
+        _bcheck(lib().flood_batch_set_wait_budget(self.h, int(cycles)), self.h)
 
     def autotune(self, trial_s=30.0, stream=None):
         """Pick the fastest batched-step configuration on the live batch, which

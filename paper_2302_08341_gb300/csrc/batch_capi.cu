@@ -50,6 +50,7 @@ struct flood_batch {
     int* pact = nullptr;              // [2] some scenario steps, by step parity
     int64_t* pdone = nullptr;         // steps the last persistent launch advanced the clocks by
     int* pdiag = nullptr;             // [8] where a persistent launch's first wait gave up
+    long long wait_budget = -1;       // grid-barrier wait limit in clock cycles (< 0: default)
     CUtensorMap* d_maps = nullptr;    // [S][2] tensor maps of each scenario
     bool initialised = false;
     int64_t k = 0, launches = 0;
@@ -379,6 +380,13 @@ int flood_batch_set_engine(flood_batch* b, int engine)
     return FLOOD_OK;
 }
 
+int flood_batch_set_wait_budget(flood_batch* b, int64_t cycles)
+{
+    if (!b) return bfail(nullptr, FLOOD_ERR_ARG, "batch is NULL");
+    b->wait_budget = cycles < 0 ? -1 : (long long)cycles;
+    return FLOOD_OK;
+}
+
 int flood_batch_set_launch(flood_batch* b, int rows_per_strip, int warps_per_cta)
 {
     if (!b) return bfail(nullptr, FLOOD_ERR_ARG, "batch is NULL");
@@ -457,7 +465,7 @@ int flood_batch_step(flood_batch* b, double t_stop, void* stream)
             q.task_next = b->pbar + 2;
             q.any_active = b->pact;
             q.steps_done = b->pdone;
-            q.budget = flood::kTmaWaitBudgetDefault;
+            q.budget = b->wait_budget < 0 ? flood::kTmaWaitBudgetDefault : b->wait_budget;
             q.diag = b->pdiag;
             BCK(b, cudaMemsetAsync(b->pdiag, 0, sizeof(int) * 8, s));
             BCK(b, cudaMemsetAsync(b->pbar, 0, sizeof(unsigned) * 4, s));

@@ -132,6 +132,32 @@ def test_batch_autotune_leaves_the_batch_unchanged(capi):
         assert np.allclose(res[0][1][key], res[1][1][key], rtol=1e-9, atol=1e-12), key
 
 
+def test_persistent_barrier_wait_that_runs_out_is_reported_and_recoverable(capi):
+    """Failure detection of the persistent form without a fault: with a zero
+    barrier budget every CTA that is not the last to arrive gives up at
+    once; the step call returns FLOOD_ERR_TIMEOUT, and after flood_batch_init
+    the same batch runs to a fresh batch's states bit for bit."""
+    terrs, hys, rm, sc, dur = _scenarios()
+    with capi.Batch([t.z for t in terrs], [t.n for t in terrs]) as ref:
+        ref.init(hys, rm, sc, dur)
+        ref.set_engine(2)
+        ref.step(300.0)
+        want = [ref.get_state(i) for i in range(len(SHAPES))]
+    with capi.Batch([t.z for t in terrs], [t.n for t in terrs]) as b:
+        b.init(hys, rm, sc, dur)
+        b.set_engine(2)
+        b.set_wait_budget(0)
+        with pytest.raises(capi.FloodError) as e:
+            b.step(300.0)
+        assert e.value.code == -4
+        b.set_wait_budget(-1)
+        b.init(hys, rm, sc, dur)
+        b.step(300.0)
+        for i in range(len(SHAPES)):
+            for k in range(3):
+                assert np.array_equal(b.get_state(i)[k], want[i][k])
+
+
 def test_batch_rejects_bad_arguments(capi):
     z = np.zeros((4, 4), np.float32)
     with pytest.raises(capi.FloodError):
