@@ -96,6 +96,39 @@ def test_land_cover_engines_and_shapes_bitwise(capi, case):
     assert np.allclose(got[3], ref[3], rtol=1e-8, atol=0)
 
 
+@pytest.mark.parametrize("engine", [0, 1])
+def test_tracked_maximum_with_land_cover(capi, engine):
+    """Land cover with the running maximum tracked (the TMA form then stages
+    the maxima and the class bytes in the same row stage): the maxima are
+    bit for bit the maximum of the stepped states, and the states equal the
+    untracked run's."""
+    ny, nx, M = 45, 150, 5
+    terr = synth.make_terrain(ny, nx, seed=63)
+    cls = synth.land_cover(terr, seed=63, pond_side=(5, 12))
+    hy = synth.hyetograph_constant(120.0, 300.0)
+    rm, sc = synth.ensemble_prior(63, M)
+    n_m, d_m = synth.land_prior(63, M)
+    p = capi.Params.default(dt_fixed=0.5)
+    plain = _run(capi, terr, cls, hy, rm, sc, n_m, d_m, 40.0, engine=engine, params=p)[0]
+    with capi.Grid(terr.z, terr.n, p) as g:
+        g.set_land_cover(cls, synth.LAND_CLASSES)
+        g.ensemble_init(M, rm, sc, hy)
+        g.set_land_params(n_m, d_m)
+        g.set_engine(engine)
+        g.advance_to(20.0)
+        g.track_max_depth(True)
+        host = np.array([g.get_state(m)[0] for m in range(M)])
+        for _ in range(40):
+            g.step(1)
+            host = np.maximum(host, np.array([g.get_state(m)[0] for m in range(M)]))
+        got = np.array([g.max_depth(m) for m in range(M)])
+        states = [g.get_state(m) for m in range(M)]
+    assert np.array_equal(got, host)
+    for m in range(M):
+        for k in range(3):
+            assert np.array_equal(states[m][k], plain[m][k])
+
+
 def test_resampling_carries_land_parameters(capi):
     ny, nx, M = 32, 48, 6
     terr = synth.make_terrain(ny, nx, seed=63)
