@@ -527,14 +527,19 @@ void orc_step_adjoint(const orc_params* p, const double* z, const double* n, dou
                                          z[IX(r, c)], qy[IQY(r, c)], nl, dt, &dd[0], &dd[1], &dd[2],
                                          &dd[3]);
         }
-    /* continuity: the clamp passes no sensitivity */
+    /* continuity: the clamp passes no sensitivity, nor does drainage that
+       takes all the water present (land cover: the depth left is then 0
+       whatever the depth before it); the rain that stays is runoff x rain */
     double gr = 0.0;
     for (int r = 0; r < ny; ++r)
         for (int c = 0; c < nx; ++c) {
+            const double rcv = p->rc ? p->rc[IX(r, c)] : 1.0;
             double hpre = h[IX(r, c)] + T * (qxn[IQX(r, c)] - qxn[IQX(r, c + 1)] + qyn[IQY(r, c)] -
-                                             qyn[IQY(r + 1, c)]) + dt * rate * rain_mult;
-            lt[IX(r, c)] = hpre < 0.0 ? 0.0 : lh[IX(r, c)];
-            gr += lt[IX(r, c)] * dt * rate;
+                                             qyn[IQY(r + 1, c)]) + dt * rate * rain_mult * rcv;
+            int pass = hpre >= 0.0;
+            if (p->drain && hpre > 0.0 && hpre <= dt * p->drain[IX(r, c)]) pass = 0;
+            lt[IX(r, c)] = pass ? lh[IX(r, c)] : 0.0;
+            gr += lt[IX(r, c)] * dt * rate * rcv;
         }
     *grad_rain += gr;
     /* sensitivity to each new link flux, then back through Eq. 2-3 */
@@ -595,7 +600,6 @@ double orc_loss_and_grad(const orc_params* p, const double* z, const double* n, 
                          long* n_steps_out)
 {
     const int ny = p->ny, nx = p->nx;
-    if (p->rc || p->drain) return NAN;  /* the reverse mode does not cover land cover */
     const size_t nc = (size_t)ny * nx, nqx = (size_t)ny * (nx + 1), nqy = (size_t)(ny + 1) * nx;
     const size_t per = nc + nqx + nqy;
     long cap = 1024, nst = 0;

@@ -88,3 +88,64 @@ def test_wall_cells_stay_dry_and_pass_no_flow():
     wy[:-1, :] |= wall
     assert np.all(m.qy[wy] == 0.0)
     assert abs(oracle.storage(m.h, p.dx) - (m.rain - m.outflow + m.clamp)) <= 1e-12 * m.rain
+
+
+def test_adjoint_with_land_cover_matches_central_differences():
+    """The reverse mode with land cover (class roughness as the n field, the
+    runoff coefficient on the rain, drainage that leaves water behind) in
+    the fully wet regime with a fixed step schedule: central differences of
+    the forward oracle."""
+    ny, nx = 10, 14
+    rng = np.random.default_rng(9)
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    z = 0.004 * 3.0 * (nx - 1 - xx) + 0.05 * np.sin(0.7 * yy) * np.cos(0.5 * xx)
+    cls = rng.integers(0, 3, (ny, nx))
+    n = np.array([0.05, 0.03, 0.035])[cls]
+    h0 = 0.35 + 0.1 * np.exp(-((yy - ny / 2) ** 2 + (xx - nx / 3) ** 2) / 8.0)
+    p = oracle.Params(ny=ny, nx=nx, dt_cap=0.5, dt_fixed=0.5)
+    p.rc = np.array([0.9, 1.0, 1.0])[cls].astype(np.float64)
+    p.drain = np.array([0.0, 0.0, 20.0 / 3.6e6])[cls].astype(np.float64)
+    hy = np.array([40.0, 10.0]) / 3.6e6
+    cells = np.array([3 * nx + 4, 6 * nx + 9, 8 * nx + 12], np.int32)
+    d = np.array([[0.40, 0.33, 0.30], [0.38, 0.35, 0.31], [0.36, 0.34, 0.33]])
+
+    def loss(n_, scale, rm, h0_):
+        return oracle.loss_and_grad(p, z, n_, scale, rm, hy, h0_, 20.0, d, cells)["loss"]
+
+    res = oracle.loss_and_grad(p, z, n, 1.1, 1.3, hy, h0, 20.0, d, cells)
+    assert np.isfinite(res["loss"]) and res["steps"] == 120
+    eps = 1e-6
+    fd = (loss(n, 1.1, 1.3 + eps, h0) - loss(n, 1.1, 1.3 - eps, h0)) / (2 * eps)
+    assert abs(fd - res["grad_rain"]) <= 1e-6 * abs(fd) + 1e-12
+    fd = (loss(n, 1.1 + eps, 1.3, h0) - loss(n, 1.1 - eps, 1.3, h0)) / (2 * eps)
+    assert abs(fd - res["grad_scale"]) <= 1e-5 * abs(fd) + 1e-12
+    # a step of 1e-6 in one cell's depth can cross a switch of max(eta) on a
+    # link (the derivative there is one-sided), 1e-7 stays clear of it
+    for i in rng.choice(ny * nx, 6, replace=False):
+        for name, arr in (("grad_n", n), ("grad_h0", h0)):
+            e = 1e-7
+            ap = arr.copy(); ap.flat[i] += e
+            am = arr.copy(); am.flat[i] -= e
+            if name == "grad_n":
+                fd = (loss(ap, 1.1, 1.3, h0) - loss(am, 1.1, 1.3, h0)) / (2 * e)
+            else:
+                fd = (loss(n, 1.1, 1.3, ap) - loss(n, 1.1, 1.3, am)) / (2 * e)
+            g = res[name].flat[i]
+            assert abs(fd - g) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(res[name]).max()), (name, i, fd, g)
+
+
+def test_adjoint_drainage_that_takes_everything_passes_nothing():
+    """Closed form: on a flat closed box whose drainage per step exceeds the
+    water present, every cell is emptied at the first step, so the observed
+    depths (0) depend neither on the initial depth nor on the rain
+    multiplier; without the drained branch the gradients would be 2 (0 - d)
+    per observation."""
+    p, z, n = _flat_box(ny=6, nx=8, rc=1.0, drain=3600.0 / 3.6e6)   # 1 m/h ≫ the 1 mm present
+    p.dt_fixed = 0.5
+    h0 = np.full(z.shape, 1e-3)
+    hy = np.array([10.0]) / 3.6e6
+    cells = np.array([9, 20], np.int32)
+    d = np.array([[0.01, 0.02]])
+    res = oracle.loss_and_grad(p, z, n, 1.0, 1.0, hy, h0, 5.0, d, cells)
+    assert np.isclose(res["loss"], 0.01 ** 2 + 0.02 ** 2, rtol=1e-12)
+    assert np.all(res["grad_h0"] == 0.0) and res["grad_rain"] == 0.0
