@@ -47,6 +47,8 @@ PINS = [
     LC.test_flat_box_drainage_above_rain_takes_all,
     LC.test_volume_balance_with_land_cover_exact_to_1e12,
     LC.test_wall_cells_stay_dry_and_pass_no_flow,
+    LC.test_adjoint_with_land_cover_matches_central_differences,
+    LC.test_adjoint_drainage_that_takes_everything_passes_nothing,
     IN.test_closed_box_stores_the_inflow_exactly,
     IN.test_piecewise_series_lands_on_block_edges,
     IN.test_volume_balance_with_inflow_and_rain_to_1e12,
@@ -99,8 +101,12 @@ MUTATIONS = [
     ("adjoint friction exponent", "-(7.0 / 3.0) * fric / hflow", "-(4.0 / 3.0) * fric / hflow"),
     ("adjoint slope sign", "*d_h1 = (first ? dq_dhf : 0.0) - dq_dS / p->dx;",
      "*d_h1 = (first ? dq_dhf : 0.0) + dq_dS / p->dx;"),
-    ("adjoint clamp passes sensitivity", "lt[IX(r, c)] = hpre < 0.0 ? 0.0 : lh[IX(r, c)];",
+    ("adjoint clamp passes sensitivity", "lt[IX(r, c)] = pass ? lh[IX(r, c)] : 0.0;",
      "lt[IX(r, c)] = lh[IX(r, c)];"),
+    ("adjoint drained cell passes sensitivity",
+     "if (p->drain && hpre > 0.0 && hpre <= dt * p->drain[IX(r, c)]) pass = 0;", ""),
+    ("adjoint rain gradient without the runoff coefficient",
+     "gr += lt[IX(r, c)] * dt * rate * rcv;", "gr += lt[IX(r, c)] * dt * rate;"),
     ("adjoint limiter on the wrong cell", "*d_h1 = p->dx / (4.0 * dt);\n            return lim;",
      "*d_h2 = p->dx / (4.0 * dt);\n            return lim;"),
     ("adjoint continuity without dt/dx", "double mu = lqx[IQX(r, c)] - T * lt[IX(r, c - 1)]",
@@ -112,7 +118,7 @@ MUTATIONS = [
      "dd[0] = a;"),
     ("adjoint loss without the 2", "lh[cells[g]] += 2.0 * (hk1[cells[g]]",
      "lh[cells[g]] += (hk1[cells[g]]"),
-    ("adjoint rain without dt", "gr += lt[IX(r, c)] * dt * rate;", "gr += lt[IX(r, c)] * rate;"),
+    ("adjoint rain without dt", "gr += lt[IX(r, c)] * dt * rate * rcv;", "gr += lt[IX(r, c)] * rate * rcv;"),
 ]
 
 
