@@ -264,7 +264,12 @@ int flood_flow_sample(flood_grid* g, int n_sections, const flood_section* sectio
  * and reports the drained volume (flood_drained_volume); storage = rain -
  * outflow + clamp - drained.  Cells outside the domain get their bed raised
  * to 1e6 m and no rain, so no link into them carries flow (Eq. 3).
- * Not covered: flood_adjoint (refused), the batched API. */
+ * flood_adjoint covers it: the Manning gradients are then taken with
+ * respect to each member's own n at each cell (the class's), the rain
+ * multiplier's gradient weighs each cell by its runoff coefficient, and a
+ * cell that drainage emptied (h* > 0 and h' = 0) passes no sensitivity, like
+ * a clamped one.  The drainage rate is held fixed.  Not covered: the batched
+ * API, a roughness factor field (refused either way). */
 typedef struct {
     float n;        /* Manning n of the class (s m^-1/3), > 0 */
     float runoff;   /* share of the rain that stays on the surface, [0, 1] */
@@ -275,7 +280,8 @@ typedef struct {
 /* Set the land cover once per grid: cls [ny][nx] uint8 (< n_classes <= 4),
  * host or device.  Per-member parameters start at the classes' n and no
  * drainage (also after a later flood_ensemble_init).  Synchronous.
- * Errors: FLOOD_ERR_ARG, FLOOD_ERR_STATE (set twice), FLOOD_ERR_OOM. */
+ * Errors: FLOOD_ERR_ARG, FLOOD_ERR_STATE (set twice, or a roughness factor
+ * field is set), FLOOD_ERR_OOM. */
 int flood_set_land_cover(flood_grid* g, const uint8_t* cls, int n_classes,
                          const flood_land_class* classes);
 
@@ -289,6 +295,14 @@ int flood_get_land_params(flood_grid* g, float* n_class, float* drain_rate);
 /* Volume removed by drainage so far, per member [N] FP64 (m^3; zeros
  * without land cover).  Synchronous. */
 int flood_drained_volume(flood_grid* g, double* drained);
+
+/* dL_i/dn_k for every member i and class k from the last flood_adjoint,
+ * which must have been given grad_n and must be the last call to change the
+ * ensemble: the member's per-cell Manning gradients summed over the cells of
+ * each class (FP64, a fixed order).  grad [N][n_classes] FP64, host memory.
+ * Synchronous.  Errors: FLOOD_ERR_ARG, FLOOD_ERR_STATE (no land cover, no
+ * fresh adjoint, or one without grad_n), FLOOD_ERR_OOM, FLOOD_ERR_CUDA. */
+int flood_adjoint_land_grad(flood_grid* g, double* grad, void* stream);
 
 /* ==== Ensemble products (Section 4.4, Figs. 15-16) ==========================
  * Per member, the running maximum depth hmax_i(r, c) over every step since
@@ -331,7 +345,8 @@ int flood_ensemble_products(flood_grid* g, double threshold, int n_levels, const
 /* Set the factor field: f [cy][cx] FP32, host or device, every value > 0;
  * 1 <= cy <= ny, 1 <= cx <= nx.  Rewrites the roughness field on the device
  * (n0 is kept from the first call).  Synchronous.
- * Errors: FLOOD_ERR_ARG, FLOOD_ERR_OOM, FLOOD_ERR_CUDA. */
+ * Errors: FLOOD_ERR_ARG, FLOOD_ERR_STATE (land cover is set: the roughness
+ * then comes from the classes), FLOOD_ERR_OOM, FLOOD_ERR_CUDA. */
 int flood_set_roughness_factor(flood_grid* g, int cy, int cx, const float* f, void* stream);
 
 /* The factor field in use: writes its shape and, if f is not NULL, its

@@ -35,7 +35,8 @@ EXPORTED = ["flood_default_params", "flood_last_error", "flood_create_grid", "fl
             "flood_batch_set_engine", "flood_track_max_depth", "flood_get_max_depth",
             "flood_ensemble_products", "flood_set_land_cover", "flood_set_land_params",
             "flood_get_land_params", "flood_drained_volume", "flood_flow_sample", "flood_set_inflow",
-            "flood_inflow_volume", "flood_batch_autotune", "flood_batch_set_wait_budget"]
+            "flood_inflow_volume", "flood_batch_autotune", "flood_batch_set_wait_budget",
+            "flood_adjoint_land_grad"]
 
 
 class LandClass(C.Structure):
@@ -145,6 +146,7 @@ def lib(path: str = LIB_PATH):
     L.flood_set_land_params.argtypes = [_VP, _VP, _VP]
     L.flood_get_land_params.argtypes = [_VP, _VP, _VP]
     L.flood_drained_volume.argtypes = [_VP, _VP]
+    L.flood_adjoint_land_grad.argtypes = [_VP, _VP, _VP]
     L.flood_flow_sample.argtypes = [_VP, C.c_int, C.POINTER(Section), _VP, _VP]
     L.flood_set_inflow.argtypes = [_VP, C.c_int, C.c_int, _VP, C.c_int]
     L.flood_inflow_volume.argtypes = [_VP, _VP]
@@ -459,6 +461,14 @@ class Grid:
     def drained(self):
         out = np.zeros(self.M)
         _check(lib().flood_drained_volume(self.h, out.ctypes.data), self.h)
+        return out
+
+    def adjoint_land_grad(self, stream=None):
+        """dL_i/dn_k per member and land-cover class from the last adjoint
+        (flood_adjoint_land_grad): [M][n_classes] FP64."""
+        out = np.zeros((self.M, self._lc_K))
+        _check(lib().flood_adjoint_land_grad(self.h, out.ctypes.data, stream_handle(stream)),
+               self.h)
         return out
 
     def track_max_depth(self, on=True, stream=None):

@@ -12,7 +12,9 @@ struct AdjArgs {
     float* gn;               // [M][plane] per-member dL/dn_base (or null)
     double* gpart;           // [M][nslot][2] per-warp partials of dL/d(rain mult), dL/d(scale)
     const float* z;
-    const float* n;
+    const float* n;          // Manning n of member m at n + m * n_mstride
+    size_t n_mstride;        // 0 (one field for all members) or plane (land cover)
+    const float* rw;         // [ny][ld] fraction of the rain that stays (land cover), or null
     const float* scale;      // [M]
     const MemberPlan* log;   // [M][dt_log_cap] plans of the recorded steps
     const int* seg_end;      // [M] first step index past this segment, per member
@@ -33,7 +35,8 @@ struct AdjTmaArgs {
     CUtensorMap seg_map;     // seg as (ld, ny, slots * M * 3), box of 3 planes (h, qx, qy)
     CUtensorMap seg1_map;    // the same memory, box of 1 plane (the depth after a step)
     CUtensorMap lam_map;     // lam as (ld, ny, 2 * M * 3), box of 3 planes
-    CUtensorMap static_map;  // z, n as (ld, ny, 2), box of 2 planes
+    CUtensorMap static_map;  // z, n as (ld, ny, 2), box of 2 planes; land cover: z and the
+                             // members' n fields as (ld, ny, 1 + M), box of 1 plane
     CUtensorMap gn_map;      // per-member Manning gradients as (ld, ny, M), box of 1 plane
     AdjArgs a;
 };

@@ -69,7 +69,6 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
     if (!L || L->n_samples < 1 || !(L->sample_dt > 0) || L->n_gauges < 1 || !L->cells || !L->d)
         return flood::fail(g, FLOOD_ERR_ARG, "invalid flood_loss_spec");
     if (ckpt_every < 0) return flood::fail(g, FLOOD_ERR_ARG, "ckpt_every must be >= 0");
-    if (g->lc_on) return flood::fail(g, FLOOD_ERR_ARG, "the adjoint does not cover land cover");
     cudaStream_t s = S(stream);
     const int M = g->M, ns = L->n_samples, G = L->n_gauges;
     const size_t ms = 3 * g->plane;
@@ -211,6 +210,11 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
                           cudaMemcpyHostToDevice, s));
     CK(g, cudaMemcpyAsync(g->samp_d, d.data(), sizeof(double) * ns * G, cudaMemcpyHostToDevice, s));
 
+    // land cover: each member's Manning n field and the share of the rain
+    // that stays, from the classes (the step looks them up per cell)
+    const size_t plane = g->plane;
+    if (g->lc_on && (rc = flood::land_adjoint_fields(g, s))) return rc;
+
     // tensor maps of the TMA-staged replay and reverse stencil (direct loads
     // otherwise); short strips never fill the reverse stencil's copy
     // pipeline, so those keep its direct-load form
@@ -228,7 +232,11 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
                                  1, 3) == 0 &&
             (!grad_n || flood::encode_map_3d(&tma.gn_map, g->gnm, g->ld, g->ny, (uint64_t)M, s1, s2,
                                              bc, 1, 1) == 0);
-        tma.static_map = g->static_map;
+        if (g->lc_on)
+            use_tma = use_tma && flood::encode_map_3d(&tma.static_map, g->lc_adj, g->ld, g->ny,
+                                                      (uint64_t)M + 1, s1, s2, bc, 1, 1) == 0;
+        else
+            tma.static_map = g->static_map;
     }
     const bool tma_replay = use_tma;
     const bool tma_reverse = use_tma && g->rows_per_strip >= 16;
@@ -259,6 +267,7 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
         if (tma_replay) {
             rt.state_map = tma.seg_map;
             rt.static_map = g->static_map;
+            if (g->lc_on) rt.cls_map = g->cls_map;
         }
         for (int i = 0; i < len; ++i) {
             a.replay_i = i;
@@ -276,7 +285,9 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
         b.gn = grad_n ? g->gnm : nullptr;
         b.gpart = g->gpart;
         b.z = g->z;
-        b.n = g->n;
+        b.n = g->lc_on ? g->lc_adj + plane : g->n;
+        b.n_mstride = g->lc_on ? plane : 0;
+        b.rw = g->lc_on ? g->lc_adj + (size_t)(M + 1) * plane : nullptr;
         b.scale = g->scale;
         b.log = g->log;
         b.seg_end = g->seg_end;

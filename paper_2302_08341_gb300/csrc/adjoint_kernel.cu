@@ -38,7 +38,9 @@ __device__ __forceinline__ void store4(float* p, const float (&v)[4])
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
-template <int WM, int WC, int LIM>
+// RW: land cover (per-member Manning n fields, rain weighed by the runoff
+// coefficient).
+template <int WM, int WC, int LIM, bool RW = false>
 __global__ void __launch_bounds__(32 * WM * WC, 4) adjoint_kernel(const AdjArgs a)
 {
     const int lane = threadIdx.x;
@@ -89,7 +91,7 @@ __global__ void __launch_bounds__(32 * WM * WC, 4) adjoint_kernel(const AdjArgs 
     const float* __restrict__ sqy = st + 2 * plane;
     const float* __restrict__ h1p = st + (size_t)a.M * mstride;  // depth after the step
     const float* __restrict__ z = a.z;
-    const float* __restrict__ n = a.n;
+    const float* __restrict__ n = a.n + (size_t)m * a.n_mstride;
     float* __restrict__ gn = a.gn ? a.gn + (size_t)m * plane : nullptr;
     const bool east_halo = (lane == 31) && (c + 4 < nx);
 
@@ -151,14 +153,18 @@ __global__ void __launch_bounds__(32 * WM * WC, 4) adjoint_kernel(const AdjArgs 
         }
         float lh[4], lx[4], ly[4], gnr[4];
         float gr_row = 0.0f, gs_row = 0.0f;
+        float rwv[4] = {0, 0, 0, 0};
+        if (RW && act) load4(rwv, a.rw + o);
         if (interior)
-            adjoint_row<true, LIM>(hC, zC, nC, lC, hS, zS, nS, lS, qxo, qyo, lqx, lqy, hE, zE, nE,
-                                   lE, c0 > 0, wi, has_s, c, nx, lane, s, s_half, T, k, a.east_out,
-                                   a.south_out, carH, carN, gr_row, gs_row, lh, lx, ly, gnr);
+            adjoint_row<true, LIM, RW>(hC, zC, nC, lC, hS, zS, nS, lS, qxo, qyo, lqx, lqy, hE, zE,
+                                       nE, lE, c0 > 0, wi, has_s, c, nx, lane, s, s_half, T, k,
+                                       a.east_out, a.south_out, carH, carN, gr_row, gs_row, lh, lx,
+                                       ly, gnr, rwv);
         else
-            adjoint_row<false, LIM>(hC, zC, nC, lC, hS, zS, nS, lS, qxo, qyo, lqx, lqy, hE, zE, nE,
-                                    lE, c0 > 0, wi, has_s, c, nx, lane, s, s_half, T, k, a.east_out,
-                                    a.south_out, carH, carN, gr_row, gs_row, lh, lx, ly, gnr);
+            adjoint_row<false, LIM, RW>(hC, zC, nC, lC, hS, zS, nS, lS, qxo, qyo, lqx, lqy, hE, zE,
+                                        nE, lE, c0 > 0, wi, has_s, c, nx, lane, s, s_half, T, k,
+                                        a.east_out, a.south_out, carH, carN, gr_row, gs_row, lh, lx,
+                                        ly, gnr, rwv);
         kahan_add(gr_s, gr_c, gr_row);
         kahan_add(gs_s, gs_c, gs_row);
         if (act) {
@@ -213,17 +219,17 @@ __global__ void reduce_members_kernel(const float* __restrict__ gm, int M, int n
     out[t] = acc;
 }
 
-template <int LIM>
+template <int LIM, bool RW>
 void launch_adjoint_lim(const AdjArgs& a, int members_per_cta, cudaStream_t s)
 {
     const int spans = (a.nx + kSpan - 1) / kSpan;
     const int strips = (a.ny + a.rows_per_strip - 1) / a.rows_per_strip;
     if (members_per_cta >= 4) {
         dim3 grid((a.M + 3) / 4, spans, strips), block(32, 4);
-        adjoint_kernel<4, 1, LIM><<<grid, block, 0, s>>>(a);
+        adjoint_kernel<4, 1, LIM, RW><<<grid, block, 0, s>>>(a);
     } else {
         dim3 grid(a.M, (spans + 3) / 4, strips), block(32, 4);
-        adjoint_kernel<1, 4, LIM><<<grid, block, 0, s>>>(a);
+        adjoint_kernel<1, 4, LIM, RW><<<grid, block, 0, s>>>(a);
     }
 }
 
@@ -231,10 +237,12 @@ void launch_adjoint_lim(const AdjArgs& a, int members_per_cta, cudaStream_t s)
 
 void launch_adjoint(const AdjArgs& a, int members_per_cta, cudaStream_t s)
 {
-    if (a.limiter)
-        launch_adjoint_lim<1>(a, members_per_cta, s);
+    if (a.rw)
+        a.limiter ? launch_adjoint_lim<1, true>(a, members_per_cta, s)
+                  : launch_adjoint_lim<0, true>(a, members_per_cta, s);
     else
-        launch_adjoint_lim<0>(a, members_per_cta, s);
+        a.limiter ? launch_adjoint_lim<1, false>(a, members_per_cta, s)
+                  : launch_adjoint_lim<0, false>(a, members_per_cta, s);
 }
 
 void launch_seed(const AdjArgs& a, const int32_t* sample_step, const float* y, const double* d,

@@ -135,8 +135,10 @@ struct WestIn {
 // north-link carries, and adds this row's rain partial (sum of lambda~) and
 // scale partial (sum of mu n dq'/dn over the lane's links, to be divided by
 // the scale) to gr_row and gs_row.  INTERIOR: the span lies wholly inside the
-// grid with an interior link east of its last cell (c0 + 128 < nx).
-template <bool INTERIOR, int LIM>
+// grid with an interior link east of its last cell (c0 + 128 < nx).  RW: the
+// rain partial weighs each cell by rw, the fraction of the rain that stays
+// on it (land cover, Section 4.1).
+template <bool INTERIOR, int LIM, bool RW = false>
 __device__ __forceinline__ void adjoint_row(
     const float (&hC)[4], const float (&zC)[4], const float (&nC)[4], const float (&lC)[4],
     const float (&hS)[4], const float (&zS)[4], const float (&nS)[4], const float (&lS)[4],
@@ -144,7 +146,7 @@ __device__ __forceinline__ void adjoint_row(
     float hE, float zE, float nE, float lE, bool west_halo, const WestIn& wi, bool has_s, int c,
     int nx, int lane, float s, float s_half, float T, const FaceK& k, int east_out,
     int south_out, float (&carH)[4], float (&carN)[4], float& gr_row, float& gs_row,
-    float (&lh)[4], float (&lx)[4], float (&ly)[4], float (&gnr)[4])
+    float (&lh)[4], float (&lx)[4], float (&ly)[4], float (&gnr)[4], const float* rw = nullptr)
 {
     const LinkD zero{0.0f, 0.0f, 0.0f, 0.0f};
     // east links: mu = lambda_q' + T (lambda~_east - lambda~_here); per link
@@ -209,7 +211,7 @@ __device__ __forceinline__ void adjoint_row(
                 mu = lqy[q] - T * lC[q];
                 w = inv_nsum(nC[q]);
             }
-            gr_row += lC[q];
+            gr_row = RW ? __fmaf_rn(lC[q], rw[q], gr_row) : gr_row + lC[q];
         }
         const float G = mu * d.g2;
         gs_row += G;

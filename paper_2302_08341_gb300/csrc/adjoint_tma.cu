@@ -40,6 +40,15 @@ static_assert(kLam * 4 >= (kHa + kBox) * 4 && kLam % 32 == 0, "stage layout");
 static_assert(kZ * 4 >= (kLam + 3 * kBox) * 4 && kZ % 32 == 0, "stage layout");
 static_assert(kGn * 4 >= (kN + kBox) * 4 && kGn % 32 == 0, "stage layout");
 static_assert(kStageBytes >= (kGn + kBox) * 4 && kStageBytes % 128 == 0, "stage layout");
+// Land cover: the roughness is the member's own plane, a copy of its own that
+// must start on a 128-byte boundary like every other part, so the roughness
+// and the Manning gradient move up and the stage grows by one 128-byte line.
+constexpr int kNLc = 1152;
+constexpr int kGnLc = 1312;
+constexpr int kStageBytesLc = 5888;
+static_assert(kNLc * 4 >= (kZ + kBox) * 4 && kNLc % 32 == 0, "stage layout");
+static_assert(kGnLc * 4 >= (kNLc + kBox) * 4 && kGnLc % 32 == 0, "stage layout");
+static_assert(kStageBytesLc >= (kGnLc + kBox) * 4 && kStageBytesLc % 128 == 0, "stage layout");
 
 __device__ __forceinline__ void lds4(float (&v)[4], const float* p)
 {
@@ -52,10 +61,15 @@ __device__ __forceinline__ void store4(float* p, const float (&v)[4])
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
-template <int WM, int LIM>
+// LC: land cover (the member's own roughness plane, rain weighed by the
+// runoff coefficient, read directly: one plane shared by all members).
+template <int WM, int LIM, bool LC = false>
 __global__ void __launch_bounds__(32 * WM, WM == 4 ? 3 : 12) adjoint_tma_kernel(
     const __grid_constant__ AdjTmaArgs t)
 {
+    constexpr int kN = LC ? kNLc : kZ + kBox;
+    constexpr int kGn = LC ? kGnLc : flood::kGn;
+    constexpr int kStageBytes = LC ? kStageBytesLc : flood::kStageBytes;
     extern __shared__ unsigned char smem_raw[];
     const AdjArgs& a = t.a;
     const int lane = threadIdx.x;
@@ -130,7 +144,12 @@ __global__ void __launch_bounds__(32 * WM, WM == 4 ? 3 : 12) adjoint_tma_kernel(
         tma_load_3d(dsts + 4 * kSt, &t.seg_map, c0 - 4, row, p_before, bar);
         tma_load_3d(dsts + 4 * kHa, &t.seg1_map, c0 - 4, row, p_after, bar);
         tma_load_3d(dsts + 4 * kLam, &t.lam_map, c0 - 4, row, p_lam, bar);
-        tma_load_3d(dsts + 4 * kZ, &t.static_map, c0 - 4, row, 0, bar);
+        if (LC) {
+            tma_load_3d(dsts + 4 * kZ, &t.static_map, c0 - 4, row, 0, bar);
+            tma_load_3d(dsts + 4 * kN, &t.static_map, c0 - 4, row, 1 + m, bar);
+        } else {
+            tma_load_3d(dsts + 4 * kZ, &t.static_map, c0 - 4, row, 0, bar);
+        }
         if (gn) tma_load_3d(dsts + 4 * kGn, &t.gn_map, c0 - 4, row, m, bar);
     };
     for (; issued < rb && issued < ra + kNS; ++issued)
@@ -247,14 +266,21 @@ __global__ void __launch_bounds__(32 * WM, WM == 4 ? 3 : 12) adjoint_tma_kernel(
         }
         float lh[4], lx[4], ly[4], gnr[4];
         float gr_row = 0.0f, gs_row = 0.0f;
+        float rwv[4] = {0, 0, 0, 0};
+        if (LC && act) {
+            const float4 v = ldg4(a.rw + o);
+            rwv[0] = v.x; rwv[1] = v.y; rwv[2] = v.z; rwv[3] = v.w;
+        }
         if (interior)
-            adjoint_row<true, LIM>(hC, zC, nC, lC, hS, zS, nS, lS, qxo, qyo, lqx, lqy, hE, zE, nE,
-                                   lE, c0 > 0, wi, has_s, c, nx, lane, s, s_half, T, k, a.east_out,
-                                   a.south_out, carH, carN, gr_row, gs_row, lh, lx, ly, gnr);
+            adjoint_row<true, LIM, LC>(hC, zC, nC, lC, hS, zS, nS, lS, qxo, qyo, lqx, lqy, hE, zE,
+                                       nE, lE, c0 > 0, wi, has_s, c, nx, lane, s, s_half, T, k,
+                                       a.east_out, a.south_out, carH, carN, gr_row, gs_row, lh, lx,
+                                       ly, gnr, rwv);
         else
-            adjoint_row<false, LIM>(hC, zC, nC, lC, hS, zS, nS, lS, qxo, qyo, lqx, lqy, hE, zE, nE,
-                                    lE, c0 > 0, wi, has_s, c, nx, lane, s, s_half, T, k, a.east_out,
-                                    a.south_out, carH, carN, gr_row, gs_row, lh, lx, ly, gnr);
+            adjoint_row<false, LIM, LC>(hC, zC, nC, lC, hS, zS, nS, lS, qxo, qyo, lqx, lqy, hE, zE,
+                                        nE, lE, c0 > 0, wi, has_s, c, nx, lane, s, s_half, T, k,
+                                        a.east_out, a.south_out, carH, carN, gr_row, gs_row, lh, lx,
+                                        ly, gnr, rwv);
         kahan_add(gr_s, gr_c, gr_row);
         kahan_add(gs_s, gs_c, gs_row);
         if (act) {
@@ -279,13 +305,14 @@ __global__ void __launch_bounds__(32 * WM, WM == 4 ? 3 : 12) adjoint_tma_kernel(
                      gr_s, gr_c, gs_s, gs_c, pl.rdt, 1.0 / (double)s);
 }
 
-template <int WM>
+template <int WM, bool LC>
 size_t adj_smem_bytes()
 {
-    return 128 + 128 * ((8 * kNS * WM + 127) / 128) + (size_t)kNS * kStageBytes * WM;
+    return 128 + 128 * ((8 * kNS * WM + 127) / 128) +
+           (size_t)kNS * (LC ? kStageBytesLc : kStageBytes) * WM;
 }
 
-template <int LIM>
+template <int LIM, bool LC>
 void launch_adjoint_tma_lim(const AdjTmaArgs& t, int members_per_cta, cudaStream_t s)
 {
     const AdjArgs& a = t.a;
@@ -293,18 +320,18 @@ void launch_adjoint_tma_lim(const AdjTmaArgs& t, int members_per_cta, cudaStream
     const int strips = (a.ny + a.rows_per_strip - 1) / a.rows_per_strip;
     if (members_per_cta >= 4 && a.M >= 4) {
         static bool attr = false;
-        const size_t shm = adj_smem_bytes<4>();
+        const size_t shm = adj_smem_bytes<4, LC>();
         if (!attr) {
-            cudaFuncSetAttribute(adjoint_tma_kernel<4, LIM>,
+            cudaFuncSetAttribute(adjoint_tma_kernel<4, LIM, LC>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
             attr = true;
         }
         dim3 grid((a.M + 3) / 4, spans, strips), block(32, 4);
-        adjoint_tma_kernel<4, LIM><<<grid, block, shm, s>>>(t);
+        adjoint_tma_kernel<4, LIM, LC><<<grid, block, shm, s>>>(t);
     } else {
-        const size_t shm = adj_smem_bytes<1>();
+        const size_t shm = adj_smem_bytes<1, LC>();
         dim3 grid(a.M, spans, strips), block(32, 1);
-        adjoint_tma_kernel<1, LIM><<<grid, block, shm, s>>>(t);
+        adjoint_tma_kernel<1, LIM, LC><<<grid, block, shm, s>>>(t);
     }
 }
 
@@ -312,10 +339,12 @@ void launch_adjoint_tma_lim(const AdjTmaArgs& t, int members_per_cta, cudaStream
 
 void launch_adjoint_tma(const AdjTmaArgs& t, int members_per_cta, cudaStream_t s)
 {
-    if (t.a.limiter)
-        launch_adjoint_tma_lim<1>(t, members_per_cta, s);
+    if (t.a.rw)
+        t.a.limiter ? launch_adjoint_tma_lim<1, true>(t, members_per_cta, s)
+                    : launch_adjoint_tma_lim<0, true>(t, members_per_cta, s);
     else
-        launch_adjoint_tma_lim<0>(t, members_per_cta, s);
+        t.a.limiter ? launch_adjoint_tma_lim<1, false>(t, members_per_cta, s)
+                    : launch_adjoint_tma_lim<0, false>(t, members_per_cta, s);
 }
 
 int adjoint_tma_box_cols() { return kBox; }

@@ -154,6 +154,8 @@ extern "C" int flood_set_roughness_factor(flood_grid* g, int cy, int cx, const f
                                           void* stream)
 {
     if (!g) return flood::fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    if (g->lc_on)
+        return flood::fail(g, FLOOD_ERR_STATE, "with land cover the roughness comes from the classes");
     if (!f || cy < 1 || cx < 1 || cy > g->ny || cx > g->nx)
         return flood::fail(g, FLOOD_ERR_ARG, "need f and 1 <= cy <= ny, 1 <= cx <= nx");
     std::vector<float> hf((size_t)cy * cx);

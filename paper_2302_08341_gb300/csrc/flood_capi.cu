@@ -68,8 +68,8 @@ void free_ensemble(flood_grid* g)
     dfree(g->gnm); dfree(g->gn_out); dfree(g->gpart); dfree(g->seg_end); dfree(g->samp_step);
     dfree(g->samp_y); dfree(g->samp_d); dfree(g->samp_cells); dfree(g->closs);
     dfree(g->hmax_field); dfree(g->lc_n); dfree(g->lc_drain); dfree(g->dacc);
-    dfree(g->inflow_acc);
-    g->inflow_acc = nullptr;
+    dfree(g->inflow_acc); dfree(g->lc_adj); dfree(g->lc_cgrad);
+    g->inflow_acc = nullptr; g->lc_adj = nullptr; g->lc_cgrad = nullptr;
     g->closs = nullptr; g->closs_cap = 0; g->hmax_field = nullptr; g->track_max = false;
     g->lc_n = nullptr; g->lc_drain = nullptr; g->dacc = nullptr;
     g->plan = nullptr; g->log = nullptr; g->ckpt = nullptr; g->seg = nullptr;
@@ -194,10 +194,8 @@ int launch_steps(flood_grid* g, int64_t count, double t_end, cudaStream_t s)
             if (a.hmax_field) t.hm_map = g->hm_map;
             if (a.lc_on) t.cls_map = g->cls_map;
             t.a = a;
-            if (const int e = flood::launch_step_tma(t, g->members_per_cta, s))
-                return fail(g, FLOOD_ERR_STATE,
-                            e == -1 ? "checkpointed steps do not cover land cover"
-                                    : "a changed wait budget covers the plain step only");
+            if (flood::launch_step_tma(t, g->members_per_cta, s))
+                return fail(g, FLOOD_ERR_STATE, "a changed wait budget covers the plain step only");
         } else if (g->engine == 2 && !g->lc_on) {
             flood::launch_step_per_member(a, s);
             g->launches += g->M - 1;

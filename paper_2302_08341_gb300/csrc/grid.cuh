@@ -94,6 +94,9 @@ struct flood_grid {
     float* lc_n = nullptr;        // [M][4] per-member class roughness
     float* lc_drain = nullptr;    // [M] per-member drainage rate (m/s)
     double* dacc = nullptr;       // [M][nslot] drained volume partials
+    float* lc_adj = nullptr;      // [M + 2][plane] the reverse pass's fields: the bed, each
+                                  // member's Manning n, the share of the rain that stays
+    double* lc_cgrad = nullptr;   // [M][4] per-class Manning gradients of the last adjoint
     // inflow hydrograph (inflow.cu)
     float* inflow = nullptr;      // [inflow_blocks] discharge per rain block (m^3/s)
     int inflow_blocks = 0, in_r0 = 0, in_r1 = 0;
@@ -133,6 +136,8 @@ void collect_profile(flood_grid* g);
 void launch_copy_planes(float* field, const int32_t* n_copy, const int32_t* dsts, const int32_t* srcs,
                         size_t plane, int n_sm, cudaStream_t s);
 int land_ensemble_init(flood_grid* g);  // per-member land-cover defaults after flood_ensemble_init
+// Fill g->lc_adj from the classes and the members' current class roughness.
+int land_adjoint_fields(flood_grid* g, cudaStream_t s);
 void launch_land_permute(float* lc_n, float* lc_drain, const int32_t* src, const int32_t* resampled,
                          int M, cudaStream_t s);
 

@@ -40,9 +40,76 @@ __global__ void land_permute_kernel(float* __restrict__ lc_n, float* __restrict_
     }
 }
 
+// The reverse pass's land-cover fields (one thread per cell of the padded
+// plane): plane 0 the bed, plane 1 + m member m's Manning n (its class's, as
+// the step looks it up), plane M + 1 the share of the rain that stays.
+__global__ void land_adjoint_fields_kernel(float* __restrict__ out, const float* __restrict__ z,
+                                           const uint8_t* __restrict__ cls,
+                                           const float* __restrict__ lc_n, float4 runoff, int M,
+                                           size_t plane)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < plane;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int k = cls[i];
+        out[i] = z[i];
+        for (int m = 0; m < M; ++m) out[(size_t)(1 + m) * plane + i] = lc_n[(size_t)m * 4 + k];
+        out[(size_t)(M + 1) * plane + i] =
+            k == 0 ? runoff.x : k == 1 ? runoff.y : k == 2 ? runoff.z : runoff.w;
+    }
+}
+
+// dL_m/dn of each class for member m (one CTA per member): the per-cell
+// Manning gradients of the member summed over the cells of each class, in
+// FP64 and a fixed order (deterministic).
+constexpr int kGradThreads = 256;
+
+__global__ void __launch_bounds__(kGradThreads) land_class_grad_kernel(
+    const float* __restrict__ gnm, const uint8_t* __restrict__ cls, int ny, int nx, int ld,
+    size_t plane, double* __restrict__ out)
+{
+    const int m = blockIdx.x;
+    const float* g = gnm + (size_t)m * plane;
+    double acc[kMaxClasses] = {0.0, 0.0, 0.0, 0.0};
+    const size_t cells = (size_t)ny * nx;
+    for (size_t i = threadIdx.x; i < cells; i += kGradThreads) {
+        const size_t o = (i / nx) * ld + i % nx;
+        const double v = g[o];
+        const int k = cls[o];
+#pragma unroll
+        for (int q = 0; q < kMaxClasses; ++q) acc[q] += (k == q) ? v : 0.0;
+    }
+    __shared__ double red[kMaxClasses][kGradThreads];
+#pragma unroll
+    for (int q = 0; q < kMaxClasses; ++q) red[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int w = kGradThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int q = 0; q < kMaxClasses; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < kMaxClasses) out[(size_t)m * kMaxClasses + threadIdx.x] = red[threadIdx.x][0];
+}
+
 }  // namespace
 
 namespace flood {
+
+int land_adjoint_fields(flood_grid* g, cudaStream_t s)
+{
+    const int M = g->M;
+    if (!g->lc_adj) {
+        const int rc = dalloc(g, &g->lc_adj, (size_t)(M + 2) * g->plane);
+        if (rc) return rc;
+    }
+    const float4 ro = make_float4(g->lc_runoff[0], g->lc_runoff[1], g->lc_runoff[2], g->lc_runoff[3]);
+    const unsigned blocks = (unsigned)std::min<size_t>((g->plane + 255) / 256, 4096);
+    land_adjoint_fields_kernel<<<blocks, 256, 0, s>>>(g->lc_adj, g->z, g->cls8, g->lc_n, ro, M,
+                                                      g->plane);
+    g->launches++;
+    CK(g, cudaGetLastError());
+    return FLOOD_OK;
+}
 
 void launch_land_permute(float* lc_n, float* lc_drain, const int32_t* src, const int32_t* resampled,
                          int M, cudaStream_t s)
@@ -76,6 +143,8 @@ extern "C" int flood_set_land_cover(flood_grid* g, const uint8_t* cls, int n_cla
 {
     if (!g) return flood::fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
     if (g->lc_on) return flood::fail(g, FLOOD_ERR_STATE, "land cover is already set");
+    if (g->fac)
+        return flood::fail(g, FLOOD_ERR_STATE, "a roughness factor field is set: land cover replaces it");
     if (!cls || !classes || n_classes < 1 || n_classes > kMaxClasses)
         return flood::fail(g, FLOOD_ERR_ARG, "need cls, 1..4 classes and their table");
     for (int q = 0; q < n_classes; ++q) {
@@ -197,5 +266,33 @@ extern "C" int flood_drained_volume(flood_grid* g, double* drained)
         for (int k = 0; k < g->nslot; ++k) acc += d[(size_t)m * g->nslot + k];
         drained[m] = acc;
     }
+    return FLOOD_OK;
+}
+
+extern "C" int flood_adjoint_land_grad(flood_grid* g, double* grad, void* stream)
+{
+    if (!g) return flood::fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    if (!grad) return flood::fail(g, FLOOD_ERR_ARG, "grad is NULL");
+    if (!g->lc_on) return flood::fail(g, FLOOD_ERR_STATE, "no land cover is set");
+    if (g->adj_epoch != g->epoch)
+        return flood::fail(g, FLOOD_ERR_STATE,
+                           "no flood_adjoint since the ensemble last changed (or its step was spent)");
+    if (!g->adj_gn || !g->gnm)
+        return flood::fail(g, FLOOD_ERR_STATE, "the last flood_adjoint was not given grad_n");
+    const int M = g->M, K = g->lc_K;
+    cudaStream_t s = S(stream);
+    if (!g->lc_cgrad) {
+        const int rc = flood::dalloc(g, &g->lc_cgrad, (size_t)M * kMaxClasses);
+        if (rc) return rc;
+    }
+    land_class_grad_kernel<<<M, kGradThreads, 0, s>>>(g->gnm, g->cls8, g->ny, g->nx, g->ld, g->plane,
+                                                      g->lc_cgrad);
+    g->launches++;
+    CK(g, cudaGetLastError());
+    std::vector<double> h((size_t)M * kMaxClasses);
+    CK(g, cudaMemcpyAsync(h.data(), g->lc_cgrad, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+    CK(g, cudaStreamSynchronize(s));
+    for (int m = 0; m < M; ++m)
+        for (int q = 0; q < K; ++q) grad[(size_t)m * K + q] = h[(size_t)m * kMaxClasses + q];
     return FLOOD_OK;
 }

@@ -72,7 +72,8 @@ __device__ __forceinline__ void row_links(const float (&hC)[4], const float (&zC
 
 // Continuity (Eq. 5 -> Eq. 1) with rain and the wet/dry clamp for a lane's
 // four cells.  Clamped cells keep a negative zero: the adjoint reads the sign
-// bit to know that branch was taken.  LC (land cover, Section 4.1): the rain
+// bit to know that branch was taken (and so do cells that land-cover
+// drainage emptied).  LC (land cover, Section 4.1): the rain
 // that stays depends on the cell's class, and the class's drainage then
 // removes at most the water present.
 template <bool INTERIOR, bool LC = false>
@@ -91,9 +92,13 @@ __device__ __forceinline__ void row_depths(const float (&hC)[4], const float (&q
             const float qW = (j == 0) ? qW0 : qxE[j - 1];
             const float net = __fadd_rn(__fsub_rn(qW, qxE[j]), __fsub_rn(qyN[j], qyS[j]));
             if (LC) {
-                hn = __fadd_rn(__fmaf_rn(dt_dx, net, hC[j]), drv[j]);
-                const float sink = fminf(ddv[j], fmaxf(hn, 0.0f));
-                hn = __fsub_rn(hn, sink);
+                const float hp = __fadd_rn(__fmaf_rn(dt_dx, net, hC[j]), drv[j]);
+                const float sink = fminf(ddv[j], fmaxf(hp, 0.0f));
+                hn = __fsub_rn(hp, sink);
+                // drainage that took all the water present leaves a depth
+                // that does not depend on the one before: marked like a
+                // clamped cell
+                if (hp > 0.0f && sink == hp) hn = -0.0f;
                 row_sink = __fadd_rn(row_sink, sink);
             } else {
                 hn = __fadd_rn(__fmaf_rn(dt_dx, net, hC[j]), dr);

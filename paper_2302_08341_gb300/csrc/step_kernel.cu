@@ -220,10 +220,16 @@ void launch_replay(const StepArgs& a, int members_per_cta, cudaStream_t s)
     const int strips = (a.ny + a.rows_per_strip - 1) / a.rows_per_strip;
     if (members_per_cta >= 4) {
         dim3 grid((a.M + 3) / 4, spans, strips), block(32, 4);
-        step_kernel<4, 1, true><<<grid, block, 0, s>>>(a);
+        if (a.lc_on)
+            step_kernel<4, 1, true, true><<<grid, block, 0, s>>>(a);
+        else
+            step_kernel<4, 1, true><<<grid, block, 0, s>>>(a);
     } else {
         dim3 grid(a.M, (spans + 3) / 4, strips), block(32, 4);
-        step_kernel<1, 4, true><<<grid, block, 0, s>>>(a);
+        if (a.lc_on)
+            step_kernel<1, 4, true, true><<<grid, block, 0, s>>>(a);
+        else
+            step_kernel<1, 4, true><<<grid, block, 0, s>>>(a);
     }
 }
 

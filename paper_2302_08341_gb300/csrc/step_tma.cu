@@ -88,9 +88,10 @@ __global__ void __launch_bounds__(32 * WM, (LC || TRACK_MAX ? 16 : 20) / WM) ste
 // Replay of a logged step of a checkpointed segment for the adjoint: the
 // same march as step_tma_kernel (so the recomputed states agree bit for bit
 // with the forward's), reading the segment's slot replay_i and writing slot
-// replay_i + 1, with the member's plan taken from the step log.
-template <int WM, int LIM>
-__global__ void __launch_bounds__(32 * WM, 20 / WM) replay_tma_kernel(const __grid_constant__ TmaArgs t)
+// replay_i + 1, with the member's plan taken from the step log.  LC: with
+// land cover (the class bytes ride in the stage, as in the step).
+template <int WM, int LIM, bool LC = false>
+__global__ void __launch_bounds__(32 * WM, (LC ? 16 : 20) / WM) replay_tma_kernel(const __grid_constant__ TmaArgs t)
 {
     extern __shared__ unsigned char smem_raw[];
     const StepArgs& a = t.a;
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(32 * WM, 20 / WM) replay_tma_kernel(const __gr
 
     uint32_t bar0;
     unsigned char* my_stages;
-    tma_march_smem(smem_raw, WM, w, bar0, my_stages);
+    tma_march_smem(smem_raw, WM, w, bar0, my_stages, tma_stage_bytes(false, LC));
 
     const size_t mstride = 3 * a.plane;
     const MemberPlan pl = a.log[(size_t)m * a.dt_log_cap + j];
@@ -123,10 +124,13 @@ __global__ void __launch_bounds__(32 * WM, 20 / WM) replay_tma_kernel(const __gr
     const int r0 = blockIdx.z * a.rows_per_strip;
     const int r1 = min(r0 + a.rows_per_strip, a.ny);
     MarchOut mo;
-    if (!tma_march<false, false, LIM>(&t.state_map, &t.static_map, (a.replay_i * a.M + m) * 3, bar0,
-                                      my_stages, dst, nullptr, nullptr, a.err, a.plane, a.ny, a.nx,
-                                      a.ld, c0, r0, r1, lane, k, pl.dt_dx, a.scale[m], pl.dr,
-                                      a.east_out, a.south_out, mo))
+    LandK lk;
+    if (LC) lk = land_k(a, m, pl.dr, pl.dt, lane);
+    if (!tma_march<false, LC, LIM>(&t.state_map, &t.static_map, (a.replay_i * a.M + m) * 3, bar0,
+                                   my_stages, dst, nullptr, nullptr, a.err, a.plane, a.ny, a.nx,
+                                   a.ld, c0, r0, r1, lane, k, pl.dt_dx, a.scale[m], pl.dr,
+                                   a.east_out, a.south_out, mo, &lk, kTmaWaitBudget, nullptr, 0,
+                                   &t.cls_map))
         return;
     if (mo.bad) atomicOr(a.err, 1);
 }
@@ -211,7 +215,7 @@ void launch_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
     }
 }
 
-template <int LIM>
+template <int LIM, bool LC>
 void launch_replay_lim(const TmaArgs& t, int members_per_cta, cudaStream_t s)
 {
     const StepArgs& a = t.a;
@@ -219,18 +223,18 @@ void launch_replay_lim(const TmaArgs& t, int members_per_cta, cudaStream_t s)
     const int strips = (a.ny + a.rows_per_strip - 1) / a.rows_per_strip;
     if (members_per_cta >= 4) {
         static bool attr = false;
-        const size_t shm = tma_smem_bytes<4>();
+        const size_t shm = tma_smem_bytes<4, false, LC>();
         if (!attr) {
-            cudaFuncSetAttribute(replay_tma_kernel<4, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)shm);
+            cudaFuncSetAttribute(replay_tma_kernel<4, LIM, LC>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
             attr = true;
         }
         dim3 grid((a.M + 3) / 4, spans, strips), block(32, 4);
-        replay_tma_kernel<4, LIM><<<grid, block, shm, s>>>(t);
+        replay_tma_kernel<4, LIM, LC><<<grid, block, shm, s>>>(t);
     } else {
-        const size_t shm = tma_smem_bytes<1>();
+        const size_t shm = tma_smem_bytes<1, false, LC>();
         dim3 grid(a.M, spans, strips), block(32, 1);
-        replay_tma_kernel<1, LIM><<<grid, block, shm, s>>>(t);
+        replay_tma_kernel<1, LIM, LC><<<grid, block, shm, s>>>(t);
     }
 }
 
@@ -238,10 +242,12 @@ void launch_replay_lim(const TmaArgs& t, int members_per_cta, cudaStream_t s)
 
 void launch_replay_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
 {
-    if (t.a.limiter)
-        launch_replay_lim<1>(t, members_per_cta, s);
+    if (t.a.lc_on)
+        t.a.limiter ? launch_replay_lim<1, true>(t, members_per_cta, s)
+                    : launch_replay_lim<0, true>(t, members_per_cta, s);
     else
-        launch_replay_lim<0>(t, members_per_cta, s);
+        t.a.limiter ? launch_replay_lim<1, false>(t, members_per_cta, s)
+                    : launch_replay_lim<0, false>(t, members_per_cta, s);
 }
 
 int launch_step_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
@@ -249,14 +255,20 @@ int launch_step_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
     const bool track = t.a.hmax_field != nullptr;
     const bool lim = t.a.limiter != 0;
     if (t.a.wait_budget != kTmaWaitBudgetDefault) {  // the failure-detection hook: plain step only
-        if (track || t.a.lc_on || t.a.ckpt) return -2;
+        if (track || t.a.lc_on || t.a.ckpt) return -1;
         lim ? launch_tma<false, false, 1, false, true>(t, members_per_cta, s)
             : launch_tma<false, false, 0, false, true>(t, members_per_cta, s);
         return 0;
     }
-    if (t.a.ckpt) {  // the adjoint's logged forward, which land cover never reaches
-        if (t.a.lc_on) return -1;
-        if (track)
+    if (t.a.ckpt) {  // the adjoint's logged forward
+        if (t.a.lc_on) {
+            if (track)
+                lim ? launch_tma<true, true, 1, true>(t, members_per_cta, s)
+                    : launch_tma<true, true, 0, true>(t, members_per_cta, s);
+            else
+                lim ? launch_tma<false, true, 1, true>(t, members_per_cta, s)
+                    : launch_tma<false, true, 0, true>(t, members_per_cta, s);
+        } else if (track)
             lim ? launch_tma<true, false, 1, true>(t, members_per_cta, s)
                 : launch_tma<true, false, 0, true>(t, members_per_cta, s);
         else

@@ -165,8 +165,6 @@ def test_land_cover_refusals(capi):
         g.ensemble_init(2, np.ones(2, np.float32), np.ones(2, np.float32), hy)
         with pytest.raises(capi.FloodError):
             g.set_land_params(drain_rate=np.array([-1.0, 0.0], np.float32))
-        with pytest.raises(capi.FloodError):   # the adjoint does not cover land cover
-            g.adjoint(np.array([40], np.int32), np.zeros((1, 1)), 30.0)
 
 
 def test_full_size_land_cover_window(capi):

@@ -1,0 +1,138 @@
+"""GPU reverse mode across land cover (Section 4.1, Table 1): each member's
+class roughness as its n field, the rain gradient weighed by the runoff
+coefficient, drainage that empties a cell passing no sensitivity; against
+the FP64 oracle's adjoint with the same land cover, per-class Manning
+gradients, a closed form, and bit for bit across engines."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2302_08341_gb300 import synth
+from tests.gpu_util import oracle_params, require_gpu
+from tests.test_gpu_land_cover import _oracle_fields
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    return require_gpu()
+
+
+def _wet_land_case(ny=40, nx=64, M=2, seed=71):
+    """Wet everywhere inside the domain (so every derivative is taken away
+    from the wet/dry kinks), the classes of the synthetic city with two
+    outside corners, drainage on hardened ground below the water present."""
+    terr = synth.make_terrain(ny, nx, seed=seed, building_frac=0.0)
+    cls = synth.land_cover(terr, seed=seed, n_ponds=3, pond_side=(4, 9))
+    outside = cls == 3
+    zmax = float(terr.z.max())
+    h0 = np.maximum(0.15 + 0.4 * (zmax - terr.z) / max(zmax, 1e-6), 0.15).astype(np.float32)
+    h0[outside] = 0.0
+    rng = np.random.default_rng(seed)
+    rm = rng.uniform(0.8, 1.3, M).astype(np.float32)
+    sc = rng.uniform(0.8, 1.2, M).astype(np.float32)
+    n_m, d_m = synth.land_prior(seed, M)
+    hy = synth.hyetograph_triangular(60.0, 1200.0, 3600.0)
+    inside = np.flatnonzero(~outside.ravel())
+    cells = inside[np.linspace(0, inside.size - 1, 5).astype(int)].astype(np.int32)
+    ns, sdt = 5, 30.0
+    d = (h0.ravel()[cells][None, :] + rng.normal(0, 0.02, (ns, cells.size))).astype(np.float64)
+    return terr, cls, h0, rm, sc, n_m, d_m, hy, cells, d, sdt
+
+
+def _gpu_adjoint(capi, case, engine=None, shape=None, ckpt_every=0):
+    terr, cls, h0, rm, sc, n_m, d_m, hy, cells, d, sdt = case
+    with capi.Grid(terr.z, terr.n, capi.Params.default()) as g:
+        g.set_land_cover(cls, synth.LAND_CLASSES)
+        g.ensemble_init(len(rm), rm, sc, hy, h0=h0)
+        g.set_land_params(n_m, d_m)
+        if engine is not None:
+            g.set_engine(engine)
+        if shape is not None:
+            g.set_launch(*shape)
+        out = g.adjoint(cells, d, sdt, ckpt_every=ckpt_every)
+        out["class"] = g.adjoint_land_grad()
+    return out
+
+
+def test_land_cover_adjoint_matches_the_oracle_adjoint(capi):
+    case = _wet_land_case()
+    terr, cls, h0, rm, sc, n_m, d_m, hy, cells, d, sdt = case
+    ny, nx = terr.z.shape
+    out = _gpu_adjoint(capi, case)
+    p = capi.Params.default()
+    gn_sum = np.zeros((ny, nx))
+    for m in range(len(rm)):
+        z, n, rc, dr, _ = _oracle_fields(terr, cls, n_m[m], d_m[m])
+        op = oracle_params(p, ny, nx)
+        op.rc, op.drain = rc, dr
+        r = oracle.loss_and_grad(op, z, n, float(sc[m]), float(rm[m]), hy, h0.astype(np.float64),
+                                 sdt, d, cells)
+        assert abs(out["loss"][m] - r["loss"]) <= 1e-4 * r["loss"]
+        assert abs(out["grad_rain"][m] - r["grad_rain"]) <= 2e-3 * abs(r["grad_rain"])
+        assert abs(out["grad_scale"][m] - r["grad_scale"]) <= 2e-3 * abs(r["grad_scale"])
+        gh = out["grad_h0"][m]
+        assert np.max(np.abs(gh - r["grad_h0"])) <= 2e-3 * np.max(np.abs(r["grad_h0"]))
+        gn_sum += r["grad_n"]
+        want = np.array([r["grad_n"][cls == k].sum() for k in range(4)])
+        got = out["class"][m]
+        assert np.all(np.abs(got - want) <= 2e-3 * np.max(np.abs(want)) + 1e-12), (m, got, want)
+    assert np.max(np.abs(out["grad_n"] - gn_sum)) <= 2e-3 * np.max(np.abs(gn_sum))
+    # the runoff weighting matters here: green land keeps 90 % of the rain
+    assert np.any(cls == 0) and np.any(cls == 2)
+
+
+def test_drainage_that_empties_every_cell_passes_nothing(capi):
+    """Closed form: a flat closed box of hardened ground whose drainage per
+    step exceeds the rain that falls on it stays dry; the gauge depths (0)
+    depend neither on the initial depths nor on the rain multiplier."""
+    ny, nx = 12, 40
+    z = np.zeros((ny, nx), np.float32)
+    n = np.full((ny, nx), 0.03, np.float32)
+    cls = np.full((ny, nx), 2, np.uint8)
+    p = capi.Params.default(east_outflow=0)
+    hy = synth.hyetograph_constant(30.0, 600.0)
+    cells = np.array([5 * nx + 7, 9 * nx + 30], np.int32)
+    d = np.array([[0.01, 0.02], [0.015, 0.01]])
+    for engine in (0, 1):
+        with capi.Grid(z, n, p) as g:
+            g.set_land_cover(cls, synth.LAND_CLASSES)
+            g.ensemble_init(2, np.ones(2, np.float32), np.ones(2, np.float32), hy)
+            g.set_land_params(drain_rate=np.full(2, 100.0 / 3.6e6, np.float32))
+            g.set_engine(engine)
+            out = g.adjoint(cells, d, 60.0)
+            cg = g.adjoint_land_grad()
+        assert np.allclose(out["loss"], (d ** 2).sum(), rtol=1e-12)
+        assert np.all(out["grad_h0"] == 0.0) and np.all(out["grad_rain"] == 0.0)
+        assert np.all(out["grad_n"] == 0.0) and np.all(cg == 0.0)
+
+
+@pytest.mark.parametrize("M,shape", [(1, (16, 1)), (5, (16, 4)), (5, (32, 4))])
+def test_land_cover_adjoint_engines_bitwise(capi, M, shape):
+    """Direct-load and TMA-staged logged forward, replay and reverse stencil
+    with land cover: the same loss and gradients, bit for bit."""
+    case = _wet_land_case(ny=45, nx=150, M=M, seed=72)
+    res = [_gpu_adjoint(capi, case, engine=e, shape=shape, ckpt_every=5) for e in (0, 1)]
+    for key in ("loss", "grad_rain", "grad_scale", "grad_n", "grad_h0", "class"):
+        assert np.array_equal(res[0][key], res[1][key]), key
+
+
+def test_land_cover_adjoint_refusals(capi):
+    terr = synth.make_terrain(24, 30, seed=73)
+    cls = synth.land_cover(terr, seed=73, pond_side=(3, 5))
+    hy = synth.hyetograph_constant(50.0, 300.0)
+    with capi.Grid(terr.z, terr.n) as g:
+        g.set_land_cover(cls, synth.LAND_CLASSES)
+        g.ensemble_init(2, np.ones(2, np.float32), np.ones(2, np.float32), hy)
+        with pytest.raises(capi.FloodError):   # no adjoint yet
+            g.adjoint_land_grad()
+        with pytest.raises(capi.FloodError):   # the roughness comes from the classes
+            g.set_roughness_factor(np.ones((2, 2), np.float32))
+        g.adjoint(np.array([40], np.int32), np.zeros((1, 1)), 30.0, grad_n=False)
+        with pytest.raises(capi.FloodError):   # that adjoint had no Manning gradient
+            g.adjoint_land_grad()
+    with capi.Grid(terr.z, terr.n) as g:
+        g.set_roughness_factor(np.ones((2, 2), np.float32))
+        with pytest.raises(capi.FloodError):   # land cover would replace the factor field
+            g.set_land_cover(cls, synth.LAND_CLASSES)
