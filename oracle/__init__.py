@@ -94,11 +94,12 @@ def load(path: str):
         L.orc_assign_slots.argtypes = [C.c_int, _I32, _I32]
         L.orc_step_adjoint.restype = None
         L.orc_step_adjoint.argtypes = [C.POINTER(OrcParams), _D, _D, C.c_double, C.c_double,
-                                       C.c_double, C.c_double, _D, _D, _D, _D, _D, _D, _D, _D, _D]
+                                       C.c_double, C.c_double, _D, _D, _D, _D, _D, _D, _D, _D, _D,
+                                       _D]
         L.orc_loss_and_grad.restype = C.c_double
         L.orc_loss_and_grad.argtypes = [C.POINTER(OrcParams), _D, _D, C.c_double, C.c_double, _D,
                                         C.c_int, _D, C.c_double, C.c_int, C.c_int, _I32, _D, _D,
-                                        _D, _D, _D, C.POINTER(C.c_long)]
+                                        _D, _D, _D, _D, C.POINTER(C.c_long)]
     return L
 
 
@@ -366,14 +367,16 @@ def step_adjoint(p: Params, z, n, scale, rate, rain_mult, dt_, m: Member, lh, lq
     gr = C.c_double(0.0); gs = C.c_double(0.0)
     lib().orc_step_adjoint(C.byref(p.c()), _d(z), _d(n), float(scale), float(rate),
                            float(rain_mult), float(dt_), _d(m.h), _d(m.qx), _d(m.qy), _d(lh),
-                           _d(lqx), _d(lqy), _d(gn), C.byref(gr), C.byref(gs))
+                           _d(lqx), _d(lqy), _d(gn), C.byref(gr), C.byref(gs), None)
     return gn, gr.value, gs.value
 
 
 def loss_and_grad(p: Params, z, n, scale, rain_mult, hyeto, h0, sample_dt, d, cells):
     """Gauge-misfit loss sum_s sum_g (h(t_s)[cell_g] - d[s][g])^2 at
     t_s = s * sample_dt and its gradients with respect to the base Manning
-    field, the initial depth, the rain multiplier and the Manning scale."""
+    field, the initial depth, the rain multiplier and the Manning scale,
+    and (land cover) grad_drain = dL/d(kappa) for the drainage field p.drain
+    scaled by kappa, at kappa = 1."""
     z = np.ascontiguousarray(z, np.float64); n = np.ascontiguousarray(n, np.float64)
     hy = np.ascontiguousarray(hyeto, np.float64)
     h0 = np.ascontiguousarray(np.broadcast_to(h0, z.shape), np.float64)
@@ -381,13 +384,13 @@ def loss_and_grad(p: Params, z, n, scale, rain_mult, hyeto, h0, sample_dt, d, ce
     cells = np.ascontiguousarray(cells, np.int32)
     ns, G = d.shape
     gn = np.zeros(z.shape); gh = np.zeros(z.shape)
-    gr = C.c_double(); gs = C.c_double(); nst = C.c_long()
+    gr = C.c_double(); gs = C.c_double(); gk = C.c_double(); nst = C.c_long()
     loss = lib().orc_loss_and_grad(C.byref(p.c()), _d(z), _d(n), float(scale), float(rain_mult),
                                    _d(hy), len(hy), _d(h0), float(sample_dt), ns, G, _i32(cells),
                                    _d(d), _d(gn), _d(gh), C.byref(gr), C.byref(gs),
-                                   C.byref(nst))
+                                   C.byref(gk), C.byref(nst))
     return dict(loss=loss, grad_n=gn, grad_h0=gh, grad_rain=gr.value, grad_scale=gs.value,
-                steps=nst.value)
+                grad_drain=gk.value, steps=nst.value)
 
 
 def section_flow(m: Member, dx: float, axis: int, fixed: int, start: int, end: int) -> float:

@@ -462,11 +462,12 @@ static double link_flux_d(const orc_params* p, double h1, double z1, double h2, 
  * (lh, lqx, lqy) hold the loss's sensitivities to the step's outputs on entry
  * and to its inputs on exit.  grad_n (per cell) accumulates dL/dn_base,
  * *grad_rain dL/d(rain multiplier) given the block rate, *grad_scale
- * dL/d(Manning scale). */
+ * dL/d(Manning scale), and *grad_drain (if not NULL; land cover)
+ * dL/d(kappa) for the drainage field scaled by kappa, at kappa = 1. */
 void orc_step_adjoint(const orc_params* p, const double* z, const double* n, double scale,
                       double rate, double rain_mult, double dt, const double* h, const double* qx,
                       const double* qy, double* lh, double* lqx, double* lqy, double* grad_n,
-                      double* grad_rain, double* grad_scale)
+                      double* grad_rain, double* grad_scale, double* grad_drain)
 {
     const int ny = p->ny, nx = p->nx;
     const double dx = p->dx, T = dt / dx;
@@ -529,8 +530,10 @@ void orc_step_adjoint(const orc_params* p, const double* z, const double* n, dou
         }
     /* continuity: the clamp passes no sensitivity, nor does drainage that
        takes all the water present (land cover: the depth left is then 0
-       whatever the depth before it); the rain that stays is runoff x rain */
-    double gr = 0.0;
+       whatever the depth before it); the rain that stays is runoff x rain;
+       drainage that leaves water behind removes dt x drain, all of it
+       sensitive to the drainage rate */
+    double gr = 0.0, gk = 0.0;
     for (int r = 0; r < ny; ++r)
         for (int c = 0; c < nx; ++c) {
             const double rcv = p->rc ? p->rc[IX(r, c)] : 1.0;
@@ -540,8 +543,11 @@ void orc_step_adjoint(const orc_params* p, const double* z, const double* n, dou
             if (p->drain && hpre > 0.0 && hpre <= dt * p->drain[IX(r, c)]) pass = 0;
             lt[IX(r, c)] = pass ? lh[IX(r, c)] : 0.0;
             gr += lt[IX(r, c)] * dt * rate * rcv;
+            if (p->drain && hpre > dt * p->drain[IX(r, c)])
+                gk -= lt[IX(r, c)] * dt * p->drain[IX(r, c)];
         }
     *grad_rain += gr;
+    if (grad_drain) *grad_drain += gk;
     /* sensitivity to each new link flux, then back through Eq. 2-3 */
     double* lh_new = (double*)calloc((size_t)ny * nx, sizeof(double));
     for (size_t i = 0; i < (size_t)ny * nx; ++i) lh_new[i] = lt[i];
@@ -591,13 +597,14 @@ void orc_step_adjoint(const orc_params* p, const double* z, const double* n, dou
 /* Loss L = sum over sample times t_s = s * sample_dt (s = 1..ns) and gauges
  * g of (h(t_s)[cells[g]] - d[s-1][g])^2 for one member started from h0 (links
  * at rest) at t = 0, and its gradients: grad_n [ny*nx] (base Manning field),
- * grad_h0 [ny*nx], *grad_rain (rain multiplier), *grad_scale (Manning scale).
+ * grad_h0 [ny*nx], *grad_rain (rain multiplier), *grad_scale (Manning scale),
+ * *grad_drain (land cover: the drainage field scaled by kappa, at kappa = 1).
  * Stores the whole trajectory (small grids only).  Returns the loss. */
 double orc_loss_and_grad(const orc_params* p, const double* z, const double* n, double scale,
                          double rain_mult, const double* hyeto, int n_blocks, const double* h0,
                          double sample_dt, int ns, int G, const int32_t* cells, const double* d,
                          double* grad_n, double* grad_h0, double* grad_rain, double* grad_scale,
-                         long* n_steps_out)
+                         double* grad_drain, long* n_steps_out)
 {
     const int ny = p->ny, nx = p->nx;
     const size_t nc = (size_t)ny * nx, nqx = (size_t)ny * (nx + 1), nqy = (size_t)(ny + 1) * nx;
@@ -659,6 +666,7 @@ double orc_loss_and_grad(const orc_params* p, const double* z, const double* n, 
     for (size_t i = 0; i < nc; ++i) grad_n[i] = 0.0;
     *grad_rain = 0.0;
     *grad_scale = 0.0;
+    *grad_drain = 0.0;
     for (long k = nst - 1; k >= 0; --k) {
         if (sample_after[k] >= 0) {
             /* the state after step k is observed: h_{k+1} is the next stored
@@ -672,7 +680,7 @@ double orc_loss_and_grad(const orc_params* p, const double* z, const double* n, 
         orc_params ps = *p;
         ps.inflow_q = qins[k];
         orc_step_adjoint(&ps, z, n, scale, rates[k], rain_mult, dts[k], st, st + nc, st + nc + nqx,
-                         lh, lqx, lqy, grad_n, grad_rain, grad_scale);
+                         lh, lqx, lqy, grad_n, grad_rain, grad_scale, grad_drain);
     }
     memcpy(grad_h0, lh, sizeof(double) * nc);
     if (n_steps_out) *n_steps_out = nst;

@@ -119,6 +119,15 @@ def test_adjoint_with_land_cover_matches_central_differences():
     assert abs(fd - res["grad_rain"]) <= 1e-6 * abs(fd) + 1e-12
     fd = (loss(n, 1.1 + eps, 1.3, h0) - loss(n, 1.1 - eps, 1.3, h0)) / (2 * eps)
     assert abs(fd - res["grad_scale"]) <= 1e-5 * abs(fd) + 1e-12
+    drain = p.drain.copy()
+    lk = []
+    for k in (1.0 + eps, 1.0 - eps):
+        p.drain = np.ascontiguousarray(drain * k)
+        lk.append(loss(n, 1.1, 1.3, h0))
+    p.drain = drain
+    fd = (lk[0] - lk[1]) / (2 * eps)
+    assert res["grad_drain"] != 0.0
+    assert abs(fd - res["grad_drain"]) <= 1e-5 * abs(fd) + 1e-12
     # a step of 1e-6 in one cell's depth can cross a switch of max(eta) on a
     # link (the derivative there is one-sided), 1e-7 stays clear of it
     for i in rng.choice(ny * nx, 6, replace=False):
@@ -149,3 +158,21 @@ def test_adjoint_drainage_that_takes_everything_passes_nothing():
     res = oracle.loss_and_grad(p, z, n, 1.0, 1.0, hy, h0, 5.0, d, cells)
     assert np.isclose(res["loss"], 0.01 ** 2 + 0.02 ** 2, rtol=1e-12)
     assert np.all(res["grad_h0"] == 0.0) and res["grad_rain"] == 0.0
+
+
+def test_adjoint_flat_box_rain_above_drainage_closed_form():
+    """Closed form: on a flat closed box of one class the depth is
+    h(t) = (c r m - kappa d) t everywhere, so with e = h(t_s) - d_s the
+    gradients are dL/dm = sum 2 e c r t_s and dL/dkappa = -sum 2 e d t_s."""
+    r, c, dr, m = 60.0 / 3.6e6, 0.9, 12.0 / 3.6e6, 1.2
+    p, z, n = _flat_box(rc=c, drain=dr)
+    hy = np.array([r])
+    cells = np.array([14, 60, 100], np.int32)
+    sdt, ns = 30.0, 4
+    ts = sdt * np.arange(1, ns + 1)
+    obs = np.array([[0.0004, 0.0009, 0.0002]] * ns) * np.arange(1, ns + 1)[:, None]
+    res = oracle.loss_and_grad(p, z, n, 1.0, m, hy, 0.0, sdt, obs, cells)
+    e = (c * r * m - dr) * ts[:, None] - obs
+    assert np.isclose(res["loss"], (e ** 2).sum(), rtol=1e-10)
+    assert np.isclose(res["grad_rain"], (2 * e * c * r * ts[:, None]).sum(), rtol=1e-9)
+    assert np.isclose(res["grad_drain"], -(2 * e * dr * ts[:, None]).sum(), rtol=1e-9)

@@ -49,6 +49,7 @@ PINS = [
     LC.test_wall_cells_stay_dry_and_pass_no_flow,
     LC.test_adjoint_with_land_cover_matches_central_differences,
     LC.test_adjoint_drainage_that_takes_everything_passes_nothing,
+    LC.test_adjoint_flat_box_rain_above_drainage_closed_form,
     IN.test_closed_box_stores_the_inflow_exactly,
     IN.test_piecewise_series_lands_on_block_edges,
     IN.test_volume_balance_with_inflow_and_rain_to_1e12,
@@ -105,6 +106,10 @@ MUTATIONS = [
      "lt[IX(r, c)] = lh[IX(r, c)];"),
     ("adjoint drained cell passes sensitivity",
      "if (p->drain && hpre > 0.0 && hpre <= dt * p->drain[IX(r, c)]) pass = 0;", ""),
+    ("adjoint drainage gradient without dt",
+     "gk -= lt[IX(r, c)] * dt * p->drain[IX(r, c)];", "gk -= lt[IX(r, c)] * p->drain[IX(r, c)];"),
+    ("adjoint drainage gradient with the wrong sign",
+     "gk -= lt[IX(r, c)] * dt * p->drain[IX(r, c)];", "gk += lt[IX(r, c)] * dt * p->drain[IX(r, c)];"),
     ("adjoint rain gradient without the runoff coefficient",
      "gr += lt[IX(r, c)] * dt * rate * rcv;", "gr += lt[IX(r, c)] * dt * rate;"),
     ("adjoint limiter on the wrong cell", "*d_h1 = p->dx / (4.0 * dt);\n            return lim;",
