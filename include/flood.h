@@ -268,7 +268,8 @@ int flood_flow_sample(flood_grid* g, int n_sections, const flood_section* sectio
  * respect to each member's own n at each cell (the class's), the rain
  * multiplier's gradient weighs each cell by its runoff coefficient, and a
  * cell that drainage emptied (h* > 0 and h' = 0) passes no sensitivity, like
- * a clamped one.  The drainage rate is held fixed.  Not covered: the batched
+ * a clamped one; the drainage rate's gradient comes from flood_adjoint_land_grad.
+ * Not covered: the batched
  * API, a roughness factor field (refused either way). */
 typedef struct {
     float n;        /* Manning n of the class (s m^-1/3), > 0 */
@@ -296,13 +297,19 @@ int flood_get_land_params(flood_grid* g, float* n_class, float* drain_rate);
  * without land cover).  Synchronous. */
 int flood_drained_volume(flood_grid* g, double* drained);
 
-/* dL_i/dn_k for every member i and class k from the last flood_adjoint,
- * which must have been given grad_n and must be the last call to change the
- * ensemble: the member's per-cell Manning gradients summed over the cells of
- * each class (FP64, a fixed order).  grad [N][n_classes] FP64, host memory.
- * Synchronous.  Errors: FLOOD_ERR_ARG, FLOOD_ERR_STATE (no land cover, no
- * fresh adjoint, or one without grad_n), FLOOD_ERR_OOM, FLOOD_ERR_CUDA. */
-int flood_adjoint_land_grad(flood_grid* g, double* grad, void* stream);
+/* Land-cover gradients of the last flood_adjoint, which must be the last
+ * call to change the ensemble.  Host memory, either may be NULL:
+ *   grad_n_class [N][n_classes] FP64  dL_i/dn_k: member i's per-cell Manning
+ *                gradients summed over the cells of class k (FP64, a fixed
+ *                order; needs an adjoint that was given grad_n)
+ *   grad_drain   [N] FP64  dL_i/d(drainage rate of i): minus dt times the
+ *                sensitivity to the depth after the step, summed over the
+ *                steps and the cells of draining classes that drainage left
+ *                wet (a cell it emptied passes nothing)
+ * Synchronous.  Errors: FLOOD_ERR_STATE (no land cover, no fresh adjoint, or
+ * grad_n_class after one without grad_n), FLOOD_ERR_OOM, FLOOD_ERR_CUDA. */
+int flood_adjoint_land_grad(flood_grid* g, double* grad_n_class, double* grad_drain,
+                            void* stream);
 
 /* ==== Ensemble products (Section 4.4, Figs. 15-16) ==========================
  * Per member, the running maximum depth hmax_i(r, c) over every step since

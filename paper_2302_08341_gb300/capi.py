@@ -146,7 +146,7 @@ def lib(path: str = LIB_PATH):
     L.flood_set_land_params.argtypes = [_VP, _VP, _VP]
     L.flood_get_land_params.argtypes = [_VP, _VP, _VP]
     L.flood_drained_volume.argtypes = [_VP, _VP]
-    L.flood_adjoint_land_grad.argtypes = [_VP, _VP, _VP]
+    L.flood_adjoint_land_grad.argtypes = [_VP, _VP, _VP, _VP]
     L.flood_flow_sample.argtypes = [_VP, C.c_int, C.POINTER(Section), _VP, _VP]
     L.flood_set_inflow.argtypes = [_VP, C.c_int, C.c_int, _VP, C.c_int]
     L.flood_inflow_volume.argtypes = [_VP, _VP]
@@ -463,13 +463,15 @@ class Grid:
         _check(lib().flood_drained_volume(self.h, out.ctypes.data), self.h)
         return out
 
-    def adjoint_land_grad(self, stream=None):
-        """dL_i/dn_k per member and land-cover class from the last adjoint
-        (flood_adjoint_land_grad): [M][n_classes] FP64."""
-        out = np.zeros((self.M, self._lc_K))
-        _check(lib().flood_adjoint_land_grad(self.h, out.ctypes.data, stream_handle(stream)),
-               self.h)
-        return out
+    def adjoint_land_grad(self, classes=True, stream=None):
+        """Land-cover gradients of the last adjoint (flood_adjoint_land_grad):
+        (dL_i/dn_k as [M][n_classes] FP64 or None, dL_i/d(drainage rate)
+        as [M] FP64)."""
+        gn = np.zeros((self.M, self._lc_K)) if classes else None
+        gd = np.zeros(self.M)
+        _check(lib().flood_adjoint_land_grad(self.h, ptr(gn), gd.ctypes.data,
+                                             stream_handle(stream)), self.h)
+        return gn, gd
 
     def track_max_depth(self, on=True, stream=None):
         """Running maximum depth of every member (flood_track_max_depth)."""

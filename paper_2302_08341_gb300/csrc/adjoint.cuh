@@ -15,6 +15,8 @@ struct AdjArgs {
     const float* n;          // Manning n of member m at n + m * n_mstride
     size_t n_mstride;        // 0 (one field for all members) or plane (land cover)
     const float* rw;         // [ny][ld] fraction of the rain that stays (land cover), or null
+    const float* dflag;      // [ny][ld] 1 where the member's drainage applies (land cover)
+    double* gdpart;          // [M][nslot] per-warp partials of dL/d(drainage rate) (land cover)
     const float* scale;      // [M]
     const MemberPlan* log;   // [M][dt_log_cap] plans of the recorded steps
     const int* seg_end;      // [M] first step index past this segment, per member

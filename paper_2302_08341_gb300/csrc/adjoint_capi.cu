@@ -206,6 +206,11 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
     }
     CK(g, cudaMemsetAsync(g->lam, 0, sizeof(float) * 2 * M * ms, s));
     CK(g, cudaMemsetAsync(g->gpart, 0, sizeof(double) * M * g->nslot * 2, s));
+    if (g->lc_on) {
+        have = 0;
+        if ((rc = grow(g, &g->gdpart, have, (size_t)M * g->nslot))) return rc;
+        CK(g, cudaMemsetAsync(g->gdpart, 0, sizeof(double) * M * g->nslot, s));
+    }
     CK(g, cudaMemcpyAsync(g->samp_step, samp_step.data(), sizeof(int32_t) * ns * M,
                           cudaMemcpyHostToDevice, s));
     CK(g, cudaMemcpyAsync(g->samp_d, d.data(), sizeof(double) * ns * G, cudaMemcpyHostToDevice, s));
@@ -288,6 +293,8 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
         b.n = g->lc_on ? g->lc_adj + plane : g->n;
         b.n_mstride = g->lc_on ? plane : 0;
         b.rw = g->lc_on ? g->lc_adj + (size_t)(M + 1) * plane : nullptr;
+        b.dflag = g->lc_on ? g->lc_adj + (size_t)(M + 2) * plane : nullptr;
+        b.gdpart = g->lc_on ? g->gdpart : nullptr;
         b.scale = g->scale;
         b.log = g->log;
         b.seg_end = g->seg_end;
@@ -355,6 +362,14 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
             if (grad_rain) grad_rain[m] = gr;
             if (grad_scale) grad_scale[m] = gs;
         }
+    }
+    g->adj_gdrain.assign(M, 0.0);
+    if (g->lc_on) {
+        std::vector<double> gp((size_t)M * g->nslot);
+        CK(g, cudaMemcpyAsync(gp.data(), g->gdpart, sizeof(double) * gp.size(), cudaMemcpyDeviceToHost, s));
+        CK(g, cudaStreamSynchronize(s));
+        for (int m = 0; m < M; ++m)
+            for (int k = 0; k < g->nslot; ++k) g->adj_gdrain[m] += gp[(size_t)m * g->nslot + k];
     }
     // clocks keep counting from where they were
     std::vector<MemberClock> ce;

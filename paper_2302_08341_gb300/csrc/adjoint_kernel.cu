@@ -39,9 +39,9 @@ __device__ __forceinline__ void store4(float* p, const float (&v)[4])
 }
 
 // RW: land cover (per-member Manning n fields, rain weighed by the runoff
-// coefficient).
+// coefficient, drainage partials), with the registers of three CTAs per SM.
 template <int WM, int WC, int LIM, bool RW = false>
-__global__ void __launch_bounds__(32 * WM * WC, 4) adjoint_kernel(const AdjArgs a)
+__global__ void __launch_bounds__(32 * WM * WC, RW ? 3 : 4) adjoint_kernel(const AdjArgs a)
 {
     const int lane = threadIdx.x;
     const int wm = threadIdx.y % WM;
@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(32 * WM * WC, 4) adjoint_kernel(const AdjArgs 
     // FP32 compensated sums of the rows' partials (lambda~ for the rain
     // gradient, mu n dq'/dn for the scale gradient), widened to FP64 once per warp
     float gr_s = 0.0f, gr_c = 0.0f, gs_s = 0.0f, gs_c = 0.0f;
+    float gd_s = 0.0f, gd_c = 0.0f;  // land cover: drainage partials
     for (int r = r0; r < r1; ++r) {
         const size_t o = (size_t)r * ld + c;
         const bool has_s = (r + 1 < ny);
@@ -154,7 +155,15 @@ __global__ void __launch_bounds__(32 * WM * WC, 4) adjoint_kernel(const AdjArgs 
         float lh[4], lx[4], ly[4], gnr[4];
         float gr_row = 0.0f, gs_row = 0.0f;
         float rwv[4] = {0, 0, 0, 0};
-        if (RW && act) load4(rwv, a.rw + o);
+        if (RW) {
+            float dfv[4] = {0, 0, 0, 0}, haC[4] = {0, 0, 0, 0};
+            if (act) {
+                load4(rwv, a.rw + o);
+                load4(dfv, a.dflag + o);
+                load4(haC, h1p + o);
+            }
+            kahan_add(gd_s, gd_c, drain_row(lC, haC, dfv));
+        }
         if (interior)
             adjoint_row<true, LIM, RW>(hC, zC, nC, lC, hS, zS, nS, lS, qxo, qyo, lqx, lqy, hE, zE,
                                        nE, lE, c0 > 0, wi, has_s, c, nx, lane, s, s_half, T, k,
@@ -182,8 +191,10 @@ __global__ void __launch_bounds__(32 * WM * WC, 4) adjoint_kernel(const AdjArgs 
             hC[q] = hS[q]; zC[q] = zS[q]; nC[q] = nS[q]; lC[q] = lS[q];
         }
     }
-    adjoint_partials(a.gpart, a.nslot, m, blockIdx.z * ((a.nx + kSpan - 1) / kSpan) + span, lane,
-                     gr_s, gr_c, gs_s, gs_c, pl.rdt, 1.0 / (double)s);
+    const int slot = blockIdx.z * ((a.nx + kSpan - 1) / kSpan) + span;
+    adjoint_partials(a.gpart, a.nslot, m, slot, lane, gr_s, gr_c, gs_s, gs_c, pl.rdt,
+                     1.0 / (double)s);
+    if (RW) adjoint_drain_partial(a.gdpart, a.nslot, m, slot, lane, gd_s, gd_c, pl.dt);
 }
 
 // Loss sensitivity at observation times: the state after step j is observed

@@ -227,6 +227,29 @@ __device__ __forceinline__ void adjoint_row(
     }
 }
 
+// Land cover: the warp's drainage partial (sum over the cells that drainage
+// left wet of lambda~), widened to FP64 and summed over lanes, times -dt
+// (dL/d(drainage rate)), added to the warp's slot.
+__device__ __forceinline__ void adjoint_drain_partial(double* gdpart, int nslot, int m, int slot,
+                                                      int lane, float gd_s, float gd_c, double dt)
+{
+    double g = ((double)gd_s - (double)gd_c) * -dt;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) g += __shfl_xor_sync(0xffffffffu, g, off);
+    if (lane == 0) gdpart[(size_t)m * nslot + slot] += g;
+}
+
+// The drainage partial of a lane's four cells in one row: lambda~ of the
+// cells of a draining class (df = 1) that the step left wet.
+__device__ __forceinline__ float drain_row(const float (&lC)[4], const float (&ha)[4],
+                                           const float (&df)[4])
+{
+    float acc = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc += ha[q] > 0.0f ? lC[q] * df[q] : 0.0f;
+    return acc;
+}
+
 // The warp's rain and scale partials, widened to FP64, summed over lanes
 // and added to the warp's slot (one slot per span and strip).  rdt: the
 // step's rain depth per unit multiplier; rs: 1 / scale.

@@ -226,6 +226,7 @@ __global__ void __launch_bounds__(32 * WM, WM == 4 ? 3 : 12) adjoint_tma_kernel(
     // FP32 compensated sums of the rows' partials (lambda~ for the rain
     // gradient, mu n dq'/dn for the scale gradient), widened to FP64 once per warp
     float gr_s = 0.0f, gr_c = 0.0f, gs_s = 0.0f, gs_c = 0.0f;
+    float gd_s = 0.0f, gd_c = 0.0f;  // land cover: drainage partials
     for (int r = r0; r < r1; ++r) {
         const size_t o = (size_t)r * ld + c;
         const bool has_s = (r + 1 < ny);
@@ -267,9 +268,16 @@ __global__ void __launch_bounds__(32 * WM, WM == 4 ? 3 : 12) adjoint_tma_kernel(
         float lh[4], lx[4], ly[4], gnr[4];
         float gr_row = 0.0f, gs_row = 0.0f;
         float rwv[4] = {0, 0, 0, 0};
-        if (LC && act) {
-            const float4 v = ldg4(a.rw + o);
-            rwv[0] = v.x; rwv[1] = v.y; rwv[2] = v.z; rwv[3] = v.w;
+        if (LC) {
+            float dfv[4] = {0, 0, 0, 0}, haC[4];
+            if (act) {
+                const float4 v = ldg4(a.rw + o);
+                rwv[0] = v.x; rwv[1] = v.y; rwv[2] = v.z; rwv[3] = v.w;
+                const float4 f = ldg4(a.dflag + o);
+                dfv[0] = f.x; dfv[1] = f.y; dfv[2] = f.z; dfv[3] = f.w;
+            }
+            lds4(haC, P + kHa + x0);
+            kahan_add(gd_s, gd_c, drain_row(lC, haC, dfv));
         }
         if (interior)
             adjoint_row<true, LIM, LC>(hC, zC, nC, lC, hS, zS, nS, lS, qxo, qyo, lqx, lqy, hE, zE,
@@ -301,8 +309,10 @@ __global__ void __launch_bounds__(32 * WM, WM == 4 ? 3 : 12) adjoint_tma_kernel(
         }
         release();
     }
-    adjoint_partials(a.gpart, a.nslot, m, blockIdx.z * ((a.nx + kSpan - 1) / kSpan) + span, lane,
-                     gr_s, gr_c, gs_s, gs_c, pl.rdt, 1.0 / (double)s);
+    const int vslot = blockIdx.z * ((a.nx + kSpan - 1) / kSpan) + span;
+    adjoint_partials(a.gpart, a.nslot, m, vslot, lane, gr_s, gr_c, gs_s, gs_c, pl.rdt,
+                     1.0 / (double)s);
+    if (LC) adjoint_drain_partial(a.gdpart, a.nslot, m, vslot, lane, gd_s, gd_c, pl.dt);
 }
 
 template <int WM, bool LC>

@@ -94,8 +94,11 @@ struct flood_grid {
     float* lc_n = nullptr;        // [M][4] per-member class roughness
     float* lc_drain = nullptr;    // [M] per-member drainage rate (m/s)
     double* dacc = nullptr;       // [M][nslot] drained volume partials
-    float* lc_adj = nullptr;      // [M + 2][plane] the reverse pass's fields: the bed, each
-                                  // member's Manning n, the share of the rain that stays
+    float* lc_adj = nullptr;      // [M + 3][plane] the reverse pass's fields: the bed, each
+                                  // member's Manning n, the share of the rain that stays,
+                                  // the drainage flag
+    double* gdpart = nullptr;     // [M][nslot] drainage-rate gradient partials
+    std::vector<double> adj_gdrain;  // [M] dL/d(drainage rate) of the last adjoint
     double* lc_cgrad = nullptr;   // [M][4] per-class Manning gradients of the last adjoint
     // inflow hydrograph (inflow.cu)
     float* inflow = nullptr;      // [inflow_blocks] discharge per rain block (m^3/s)

@@ -42,11 +42,12 @@ __global__ void land_permute_kernel(float* __restrict__ lc_n, float* __restrict_
 
 // The reverse pass's land-cover fields (one thread per cell of the padded
 // plane): plane 0 the bed, plane 1 + m member m's Manning n (its class's, as
-// the step looks it up), plane M + 1 the share of the rain that stays.
+// the step looks it up), plane M + 1 the share of the rain that stays, plane
+// M + 2 the drainage flag.
 __global__ void land_adjoint_fields_kernel(float* __restrict__ out, const float* __restrict__ z,
                                            const uint8_t* __restrict__ cls,
-                                           const float* __restrict__ lc_n, float4 runoff, int M,
-                                           size_t plane)
+                                           const float* __restrict__ lc_n, float4 runoff,
+                                           float4 drains, int M, size_t plane)
 {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < plane;
          i += (size_t)gridDim.x * blockDim.x) {
@@ -55,6 +56,8 @@ __global__ void land_adjoint_fields_kernel(float* __restrict__ out, const float*
         for (int m = 0; m < M; ++m) out[(size_t)(1 + m) * plane + i] = lc_n[(size_t)m * 4 + k];
         out[(size_t)(M + 1) * plane + i] =
             k == 0 ? runoff.x : k == 1 ? runoff.y : k == 2 ? runoff.z : runoff.w;
+        out[(size_t)(M + 2) * plane + i] =
+            k == 0 ? drains.x : k == 1 ? drains.y : k == 2 ? drains.z : drains.w;
     }
 }
 
@@ -99,12 +102,13 @@ int land_adjoint_fields(flood_grid* g, cudaStream_t s)
 {
     const int M = g->M;
     if (!g->lc_adj) {
-        const int rc = dalloc(g, &g->lc_adj, (size_t)(M + 2) * g->plane);
+        const int rc = dalloc(g, &g->lc_adj, (size_t)(M + 3) * g->plane);
         if (rc) return rc;
     }
     const float4 ro = make_float4(g->lc_runoff[0], g->lc_runoff[1], g->lc_runoff[2], g->lc_runoff[3]);
+    const float4 dr = make_float4(g->lc_drains[0], g->lc_drains[1], g->lc_drains[2], g->lc_drains[3]);
     const unsigned blocks = (unsigned)std::min<size_t>((g->plane + 255) / 256, 4096);
-    land_adjoint_fields_kernel<<<blocks, 256, 0, s>>>(g->lc_adj, g->z, g->cls8, g->lc_n, ro, M,
+    land_adjoint_fields_kernel<<<blocks, 256, 0, s>>>(g->lc_adj, g->z, g->cls8, g->lc_n, ro, dr, M,
                                                       g->plane);
     g->launches++;
     CK(g, cudaGetLastError());
@@ -269,17 +273,19 @@ extern "C" int flood_drained_volume(flood_grid* g, double* drained)
     return FLOOD_OK;
 }
 
-extern "C" int flood_adjoint_land_grad(flood_grid* g, double* grad, void* stream)
+extern "C" int flood_adjoint_land_grad(flood_grid* g, double* grad_n_class, double* grad_drain,
+                                       void* stream)
 {
     if (!g) return flood::fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
-    if (!grad) return flood::fail(g, FLOOD_ERR_ARG, "grad is NULL");
     if (!g->lc_on) return flood::fail(g, FLOOD_ERR_STATE, "no land cover is set");
-    if (g->adj_epoch != g->epoch)
+    if (g->adj_epoch != g->epoch || (int)g->adj_gdrain.size() != g->M)
         return flood::fail(g, FLOOD_ERR_STATE,
                            "no flood_adjoint since the ensemble last changed (or its step was spent)");
+    const int M = g->M, K = g->lc_K;
+    if (grad_drain) std::copy(g->adj_gdrain.begin(), g->adj_gdrain.end(), grad_drain);
+    if (!grad_n_class) return FLOOD_OK;
     if (!g->adj_gn || !g->gnm)
         return flood::fail(g, FLOOD_ERR_STATE, "the last flood_adjoint was not given grad_n");
-    const int M = g->M, K = g->lc_K;
     cudaStream_t s = S(stream);
     if (!g->lc_cgrad) {
         const int rc = flood::dalloc(g, &g->lc_cgrad, (size_t)M * kMaxClasses);
@@ -293,6 +299,6 @@ extern "C" int flood_adjoint_land_grad(flood_grid* g, double* grad, void* stream
     CK(g, cudaMemcpyAsync(h.data(), g->lc_cgrad, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
     CK(g, cudaStreamSynchronize(s));
     for (int m = 0; m < M; ++m)
-        for (int q = 0; q < K; ++q) grad[(size_t)m * K + q] = h[(size_t)m * kMaxClasses + q];
+        for (int q = 0; q < K; ++q) grad_n_class[(size_t)m * K + q] = h[(size_t)m * kMaxClasses + q];
     return FLOOD_OK;
 }

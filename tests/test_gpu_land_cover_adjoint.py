@@ -1,8 +1,9 @@
 """GPU reverse mode across land cover (Section 4.1, Table 1): each member's
 class roughness as its n field, the rain gradient weighed by the runoff
-coefficient, drainage that empties a cell passing no sensitivity; against
-the FP64 oracle's adjoint with the same land cover, per-class Manning
-gradients, a closed form, and bit for bit across engines."""
+coefficient, drainage that empties a cell passing no sensitivity, the
+drainage rate's gradient; against the FP64 oracle's adjoint with the same
+land cover, per-class Manning gradients, closed forms, and bit for bit
+across engines."""
 import numpy as np
 import pytest
 
@@ -52,7 +53,7 @@ def _gpu_adjoint(capi, case, engine=None, shape=None, ckpt_every=0):
         if shape is not None:
             g.set_launch(*shape)
         out = g.adjoint(cells, d, sdt, ckpt_every=ckpt_every)
-        out["class"] = g.adjoint_land_grad()
+        out["class"], out["drain"] = g.adjoint_land_grad()
     return out
 
 
@@ -75,6 +76,11 @@ def test_land_cover_adjoint_matches_the_oracle_adjoint(capi):
         gh = out["grad_h0"][m]
         assert np.max(np.abs(gh - r["grad_h0"])) <= 2e-3 * np.max(np.abs(r["grad_h0"]))
         gn_sum += r["grad_n"]
+        # the oracle differentiates a factor on the drainage field; the
+        # device, the member's drainage rate (the field's value where it drains)
+        want_d = r["grad_drain"] / float(d_m[m])
+        assert want_d != 0.0
+        assert abs(out["drain"][m] - want_d) <= 2e-3 * abs(want_d)
         want = np.array([r["grad_n"][cls == k].sum() for k in range(4)])
         got = out["class"][m]
         assert np.all(np.abs(got - want) <= 2e-3 * np.max(np.abs(want)) + 1e-12), (m, got, want)
@@ -102,10 +108,43 @@ def test_drainage_that_empties_every_cell_passes_nothing(capi):
             g.set_land_params(drain_rate=np.full(2, 100.0 / 3.6e6, np.float32))
             g.set_engine(engine)
             out = g.adjoint(cells, d, 60.0)
-            cg = g.adjoint_land_grad()
+            cg, gd = g.adjoint_land_grad()
         assert np.allclose(out["loss"], (d ** 2).sum(), rtol=1e-12)
         assert np.all(out["grad_h0"] == 0.0) and np.all(out["grad_rain"] == 0.0)
-        assert np.all(out["grad_n"] == 0.0) and np.all(cg == 0.0)
+        assert np.all(out["grad_n"] == 0.0) and np.all(cg == 0.0) and np.all(gd == 0.0)
+
+
+def test_drainage_gradient_closed_form(capi):
+    """Closed form: on a flat closed box of hardened ground whose rain r m
+    exceeds its drainage d, h(t) = (r m - d) t everywhere; with
+    e = h(t_s) - obs_s, dL/dd = -sum 2 e t_s and dL/dm = sum 2 e r t_s."""
+    ny, nx = 12, 40
+    z = np.zeros((ny, nx), np.float32)
+    n = np.full((ny, nx), 0.03, np.float32)
+    cls = np.full((ny, nx), 2, np.uint8)
+    p = capi.Params.default(east_outflow=0)
+    r, dr = 60.0 / 3.6e6, 12.0 / 3.6e6
+    hy = synth.hyetograph_constant(60.0, 600.0)
+    rm = np.array([1.0, 1.3], np.float32)
+    cells = np.array([5 * nx + 7, 9 * nx + 30], np.int32)
+    ts = 30.0 * np.arange(1, 5)
+    obs = np.array([[0.0004, 0.0009]] * 4) * np.arange(1, 5)[:, None]
+    for engine in (0, 1):
+        with capi.Grid(z, n, p) as g:
+            g.set_land_cover(cls, synth.LAND_CLASSES)
+            g.ensemble_init(2, rm, np.ones(2, np.float32), hy)
+            g.set_land_params(drain_rate=np.full(2, dr, np.float32))
+            g.set_engine(engine)
+            out = g.adjoint(cells, obs, 30.0)
+            _, gd = g.adjoint_land_grad(classes=False)
+        for m in range(2):
+            rate = float(np.float32(hy[0])) * float(rm[m])
+            e = (rate - float(np.float32(dr))) * ts[:, None] - obs
+            assert abs(out["loss"][m] - (e ** 2).sum()) <= 1e-4 * (e ** 2).sum()
+            want_d = -(2 * e * ts[:, None]).sum()
+            assert abs(gd[m] - want_d) <= 1e-3 * abs(want_d)
+            want_r = (2 * e * float(np.float32(hy[0])) * ts[:, None]).sum()
+            assert abs(out["grad_rain"][m] - want_r) <= 1e-3 * abs(want_r)
 
 
 @pytest.mark.parametrize("M,shape", [(1, (16, 1)), (5, (16, 4)), (5, (32, 4))])
@@ -114,7 +153,7 @@ def test_land_cover_adjoint_engines_bitwise(capi, M, shape):
     with land cover: the same loss and gradients, bit for bit."""
     case = _wet_land_case(ny=45, nx=150, M=M, seed=72)
     res = [_gpu_adjoint(capi, case, engine=e, shape=shape, ckpt_every=5) for e in (0, 1)]
-    for key in ("loss", "grad_rain", "grad_scale", "grad_n", "grad_h0", "class"):
+    for key in ("loss", "grad_rain", "grad_scale", "grad_n", "grad_h0", "class", "drain"):
         assert np.array_equal(res[0][key], res[1][key]), key
 
 
@@ -132,6 +171,8 @@ def test_land_cover_adjoint_refusals(capi):
         g.adjoint(np.array([40], np.int32), np.zeros((1, 1)), 30.0, grad_n=False)
         with pytest.raises(capi.FloodError):   # that adjoint had no Manning gradient
             g.adjoint_land_grad()
+        _, gd = g.adjoint_land_grad(classes=False)  # the drainage gradient needs none
+        assert gd.shape == (2,)
     with capi.Grid(terr.z, terr.n) as g:
         g.set_roughness_factor(np.ones((2, 2), np.float32))
         with pytest.raises(capi.FloodError):   # land cover would replace the factor field
