@@ -177,3 +177,29 @@ def test_land_cover_adjoint_refusals(capi):
         g.set_roughness_factor(np.ones((2, 2), np.float32))
         with pytest.raises(capi.FloodError):   # land cover would replace the factor field
             g.set_land_cover(cls, synth.LAND_CLASSES)
+
+
+def test_autograd_function_with_land_cover(capi):
+    """The torch.autograd.Function over the land-cover adjoint returns the
+    C ABI's gradients for the class roughness, drainage rate, rain
+    multiplier and initial depth."""
+    torch = pytest.importorskip("torch")
+    from paper_2302_08341_gb300.autograd import land_gauge_misfit
+    case = _wet_land_case(M=2, seed=74)
+    terr, cls, h0, rm, sc, n_m, d_m, hy, cells, d, sdt = case
+    ref = _gpu_adjoint(capi, case)
+    dev = torch.device("cuda")
+    nc_t = torch.tensor(n_m, device=dev, requires_grad=True)
+    dr_t = torch.tensor(d_m, device=dev, requires_grad=True)
+    rm_t = torch.tensor(rm, device=dev, requires_grad=True)
+    h0_t = torch.tensor(h0, device=dev, requires_grad=True)
+    loss = land_gauge_misfit(nc_t, dr_t, rm_t, h0_t, torch.tensor(terr.z, device=dev),
+                             torch.tensor(terr.n, device=dev), cls, synth.LAND_CLASSES,
+                             torch.tensor(sc, device=dev), torch.tensor(hy, device=dev), cells, d,
+                             sdt)
+    loss.backward()
+    assert abs(loss.item() - ref["loss"].sum()) <= 1e-12 * ref["loss"].sum()
+    assert np.allclose(nc_t.grad.cpu().numpy(), ref["class"], rtol=1e-6)
+    assert np.allclose(dr_t.grad.cpu().numpy(), ref["drain"], rtol=1e-6)
+    assert np.allclose(rm_t.grad.cpu().numpy(), ref["grad_rain"], rtol=1e-6)
+    assert np.allclose(h0_t.grad.cpu().numpy(), ref["grad_h0"].sum(axis=0), rtol=1e-5, atol=1e-9)
