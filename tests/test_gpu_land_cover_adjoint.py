@@ -203,3 +203,61 @@ def test_autograd_function_with_land_cover(capi):
     assert np.allclose(dr_t.grad.cpu().numpy(), ref["drain"], rtol=1e-6)
     assert np.allclose(rm_t.grad.cpu().numpy(), ref["grad_rain"], rtol=1e-6)
     assert np.allclose(h0_t.grad.cpu().numpy(), ref["grad_h0"].sum(axis=0), rtol=1e-5, atol=1e-9)
+
+
+def test_full_size_land_cover_adjoint_window(capi):
+    """2000 x 2000 cells, 96 members with their own class roughness and
+    drainage rate, as the benchmark runs them: one 300 s window's adjoint
+    after a 300 s spin-up against central differences of the whole
+    ensemble's loss in the drainage rates (+-5 %) and the rain multipliers
+    (+-1 %) over that window (the differences also move the CFL step
+    schedule, which the adjoint holds fixed: a small effect here, inside the
+    3 % allowed), and the per-class gradients against the Manning gradient
+    field."""
+    ny = nx = 2000
+    M = 96
+    terr = synth.make_terrain(ny, nx, seed=1)
+    cls = synth.land_cover(terr, seed=1)
+    hy = synth.hyetograph_triangular(60.0, 1200.0, 3600.0)
+    rm, sc = synth.ensemble_prior(1, M)
+    n_m, d_m = synth.land_prior(1, M)
+    p = capi.Params.default()
+    cells = synth.gauge_cells(terr, 6, seed=1)
+    cells = cells[cls.ravel()[cells] != 3]
+    obs = np.full((5, len(cells)), 0.1)
+
+    def run(drain_f=1.0, rain_f=1.0, adjoint=False):
+        with capi.Grid(terr.z, terr.n, p) as g:
+            g.set_land_cover(cls, synth.LAND_CLASSES)
+            g.ensemble_init(M, rm, sc, hy)
+            g.set_land_params(n_m, d_m)
+            g.advance_to(300.0)
+            # the adjoint takes the state at 300 s as its input: the inputs
+            # are perturbed for the window alone
+            g.set_members(rain_mult=(rm * np.float32(rain_f)).astype(np.float32))
+            g.set_land_params(drain_rate=(d_m * np.float32(drain_f)).astype(np.float32))
+            if adjoint:
+                out = g.adjoint(cells, obs, 60.0)
+                gc, gd = g.adjoint_land_grad()
+                return out, gc, gd
+            L = np.zeros(M)
+            for s in range(1, 6):
+                g.advance_to(300.0 + 60.0 * s)
+                y = g.gauge_sample(cells).astype(np.float64)
+                L += ((y - obs[s - 1]) ** 2).sum(axis=1)
+            return L
+
+    out, gc, gd = run(adjoint=True)
+    L0 = run()
+    assert np.allclose(out["loss"], L0, rtol=1e-6)
+    eps = 0.05
+    dL = (run(drain_f=1 + eps) - run(drain_f=1 - eps)).sum()
+    want = (gd * d_m.astype(np.float64)).sum() * 2 * eps
+    assert abs(want) > 0 and abs(dL - want) <= 0.03 * abs(dL), (dL, want)
+    eps = 0.01
+    dL = (run(rain_f=1 + eps) - run(rain_f=1 - eps)).sum()
+    want = (out["grad_rain"] * rm.astype(np.float64)).sum() * 2 * eps
+    assert abs(dL - want) <= 0.03 * abs(dL), (dL, want)
+    # the class gradients partition the member-summed Manning gradient field
+    tot = float(out["grad_n"].astype(np.float64).sum())
+    assert abs(gc.sum() - tot) <= 1e-3 * np.abs(out["grad_n"]).astype(np.float64).sum()
