@@ -184,3 +184,46 @@ def test_full_size_ensemble_calibration_window(capi):
     assert np.allclose(mem["rain_mult"], m_or, rtol=2e-7)
     assert np.allclose(f_new, f_or, rtol=2e-7)
     assert np.all(np.abs(np.log(f_new)) <= 0.2 * (1 + 1e-6))
+
+
+def test_full_size_adjoint_against_central_differences(capi):
+    """2000 x 2000 cells, 96 members, a 64 x 64 factor field, one 300 s
+    window from the dry start observed every 60 s by 6 gauges, in the
+    launch configuration the benchmark uses: the adjoint's rain-multiplier,
+    Manning-scale and factor-field gradients against central differences of
+    the whole ensemble's loss (every member's rain multiplier, every
+    member's scale, every factor moved by +-1 %), within 3 % (the
+    differences also move the CFL step schedule the adjoint holds fixed)."""
+    ny = nx = 2000
+    M, G, cy, cx = 96, 6, 64, 64
+    terr = synth.make_terrain(ny, nx, seed=4)
+    hy = synth.hyetograph_triangular(60.0, 1200.0, 3600.0)
+    rm, sc = synth.ensemble_prior(4, M)
+    cells = synth.gauge_cells(terr, G, seed=4)
+    obs = np.full((5, G), 0.05)
+    f = np.ones((cy, cx), np.float32)
+
+    def run(rain_f=1.0, scale_f=1.0, fac_f=1.0, adjoint=False):
+        with capi.Grid(terr.z, terr.n) as g:
+            g.ensemble_init(M, (rm * np.float32(rain_f)).astype(np.float32),
+                            (sc * np.float32(scale_f)).astype(np.float32), hy)
+            g.set_roughness_factor((f * np.float32(fac_f)).astype(np.float32))
+            if adjoint:
+                out = g.adjoint(cells, obs, 60.0, grad_h0=False)
+                return out, g.roughness_factor_grad()
+            L = np.zeros(M)
+            for s in range(1, 6):
+                g.advance_to(60.0 * s)
+                y = g.gauge_sample(cells).astype(np.float64)
+                L += ((y - obs[s - 1]) ** 2).sum(axis=1)
+            return L
+
+    out, Gf = run(adjoint=True)
+    assert np.allclose(out["loss"], run(), rtol=1e-6)
+    eps = 0.01
+    for key, kw, want in (
+            ("rain", "rain_f", (out["grad_rain"] * rm.astype(np.float64)).sum()),
+            ("scale", "scale_f", (out["grad_scale"] * sc.astype(np.float64)).sum()),
+            ("factor", "fac_f", (Gf.astype(np.float64) * f).sum())):
+        dL = (run(**{kw: 1 + eps}) - run(**{kw: 1 - eps})).sum() / (2 * eps)
+        assert want != 0.0 and abs(dL - want) <= 0.03 * abs(dL), (key, dL, want)
