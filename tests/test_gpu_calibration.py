@@ -2,7 +2,8 @@
 factor field, its gradient from the adjoint against the FP64 oracle adjoint
 taken through the oracle's factor map, the calibration step against the
 oracle's rule, the order checks, and the full-size ensemble (2000 x 2000
-cells, 96 members, 64 x 64 field, one 300 s window) on sampled blocks."""
+cells, 96 members, 64 x 64 field, one 300 s window) on sampled blocks and
+against central differences of the ensemble loss."""
 import numpy as np
 import pytest
 
