@@ -62,12 +62,13 @@ def test_gradients_match_central_differences_fully_wet():
             assert abs(fd - g) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(res[name]).max()), (name, i, fd, g)
 
 
-@pytest.mark.parametrize("regime", ["wet", "limited", "drying", "outflow"])
+@pytest.mark.parametrize("regime", ["wet", "limited", "drying", "outflow", "land_cover"])
 def test_dot_product_identity_per_step(regime):
     """<J v, w> = <v, J^T w> for one step, J by central differences of the
     forward step in every input (h, qx, qy, n), J^T by the adjoint; in the
     wet regime, with links held by the limiter, with cells clamped at zero
-    depth (limiter off), and with a free-outflow edge."""
+    depth (limiter off), with a free-outflow edge, and with land cover
+    (runoff coefficients, cells that drainage empties, cells it leaves wet)."""
     p, z, n, h0, hy, cells, d = _setup()
     ny, nx = z.shape
     rng = np.random.default_rng(3)
@@ -87,6 +88,16 @@ def test_dot_product_identity_per_step(regime):
         qx[:, 1:nx] = rng.normal(0, 0.4, (ny, nx - 1))
     elif regime == "outflow":
         qx[:, nx] = np.abs(rng.normal(0, 0.05, ny))
+    elif regime == "land_cover":
+        p.east_outflow = 0
+        h = 0.002 + 0.004 * rng.random((ny, nx))
+        qx[:, 1:nx] = rng.normal(0, 0.002, (ny, nx - 1))
+        qy[1:ny, :] = rng.normal(0, 0.002, (ny - 1, nx))
+        u = rng.random((ny, nx))
+        p.rc = np.ascontiguousarray(np.where(rng.random((ny, nx)) < 0.5, 0.9, 1.0))
+        # a third emptied (drainage 2 cm per step), a third drained in part
+        p.drain = np.ascontiguousarray(np.where(u < 1 / 3, 0.02 / dt,
+                                                np.where(u < 2 / 3, 0.0005 / dt, 0.0)))
     else:
         p.east_outflow = 0
     m = oracle.Member(h=h, qx=qx, qy=qy)
@@ -107,6 +118,8 @@ def test_dot_product_identity_per_step(regime):
         assert np.isclose(np.abs(base.qx[:, 1:nx]), lim, rtol=1e-13).sum() >= 3
     if regime == "drying":
         assert (base.h == 0).sum() >= 3
+    if regime == "land_cover":
+        assert (base.h == 0).sum() >= 10 and (base.h[u > 1 / 3] > 0).all()
     e = 1e-7
     a, b = fwd(e), fwd(-e)
     Jv = [(a.h - b.h) / (2 * e), (a.qx - b.qx) / (2 * e), (a.qy - b.qy) / (2 * e)]

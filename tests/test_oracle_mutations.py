@@ -42,6 +42,7 @@ PINS = [
     functools.partial(A.test_dot_product_identity_per_step, regime="limited"),
     functools.partial(A.test_dot_product_identity_per_step, regime="drying"),
     functools.partial(A.test_dot_product_identity_per_step, regime="outflow"),
+    functools.partial(A.test_dot_product_identity_per_step, regime="land_cover"),
     A.test_closed_form_uniform_rain_on_flat_box,
     LC.test_flat_box_rain_above_drainage_closed_form,
     LC.test_flat_box_drainage_above_rain_takes_all,
