@@ -13,8 +13,10 @@ update is an extension.  Its pieces, written out plainly:
 * one descent step in log-parameter space with the Polyak step length of a
   loss whose minimum is zero, step = -eta * L * g / |g|^2 for the gradient g
   with respect to the log-parameters, every component clipped to
-  [-delta, delta]: per member for its rain multiplier (its own loss L_i), and
-  jointly for the shared factor field (the total loss L = sum_i L_i).
+  [-delta, delta]: per member for its rain multiplier (its own loss L_i),
+  jointly for the shared factor field (the total loss L = sum_i L_i), and,
+  with land cover (Section 4.1), jointly per member for its Manning n of
+  every class and its drainage rate (its own loss L_i).
 """
 from __future__ import annotations
 
@@ -72,3 +74,22 @@ def calibration_step(loss, grad_rain, rain_mult, factor=None, factor_grad_=None,
     L = float(np.sum(loss))
     f_new = f * np.exp(_clip(-eta * L * G / s2, delta)) if s2 > 0.0 else f.copy()
     return m_new, f_new
+
+
+def land_step(loss, grad_class, n_class, grad_drain, drain, eta=1.0, delta=0.2):
+    """One joint step per member on its land-cover parameters: theta_i =
+    (n_i1 .. n_iK, d_i), G = theta_i * dL_i/dtheta_i (log-parameter
+    gradient), step = clip(-eta L_i G / |G|^2, delta) (no step where |G| = 0).
+    Returns (new n_class [M][K], new drain [M])."""
+    loss = np.asarray(loss, np.float64)
+    n = np.asarray(n_class, np.float64)
+    d = np.asarray(drain, np.float64)
+    Gn = n * np.asarray(grad_class, np.float64)
+    Gd = d * np.asarray(grad_drain, np.float64)
+    s2 = np.sum(Gn * Gn, axis=1) + Gd * Gd
+    n_new, d_new = n.copy(), d.copy()
+    for i in range(len(loss)):
+        if s2[i] > 0.0:
+            n_new[i] = n[i] * np.exp(_clip(-eta * loss[i] * Gn[i] / s2[i], delta))
+            d_new[i] = d[i] * np.exp(_clip(-eta * loss[i] * Gd[i] / s2[i], delta))
+    return n_new, d_new

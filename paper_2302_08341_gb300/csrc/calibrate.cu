@@ -220,7 +220,7 @@ extern "C" int flood_calibration_step(flood_grid* g, double eta, double delta, d
         return flood::fail(g, FLOOD_ERR_ARG, "eta and delta must be positive");
     if (g->M == 0) return flood::fail(g, FLOOD_ERR_STATE, "flood_ensemble_init has not been called");
     const bool field = g->fac != nullptr;
-    int rc = check_fresh_adjoint(g, field);
+    int rc = check_fresh_adjoint(g, field || g->lc_on);
     if (rc) return rc;
     cudaStream_t s = S(stream);
     if (g->closs_cap < g->M) {
@@ -251,6 +251,7 @@ extern "C" int flood_calibration_step(flood_grid* g, double eta, double delta, d
     g->launches++;
     if (field) launch_apply(g, s);
     CK(g, cudaGetLastError());
+    if (g->lc_on && (rc = flood::land_calibration_step(g, g->closs, eta, delta, s))) return rc;
     if (loss_out)
         CK(g, cudaMemcpyAsync(loss_out, g->closs, sizeof(double) * g->M, cudaMemcpyDefault, s));
     CK(g, cudaStreamSynchronize(s));

@@ -68,8 +68,9 @@ void free_ensemble(flood_grid* g)
     dfree(g->gnm); dfree(g->gn_out); dfree(g->gpart); dfree(g->seg_end); dfree(g->samp_step);
     dfree(g->samp_y); dfree(g->samp_d); dfree(g->samp_cells); dfree(g->closs);
     dfree(g->hmax_field); dfree(g->lc_n); dfree(g->lc_drain); dfree(g->dacc);
-    dfree(g->inflow_acc); dfree(g->lc_adj); dfree(g->lc_cgrad); dfree(g->gdpart);
+    dfree(g->inflow_acc); dfree(g->lc_adj); dfree(g->lc_cgrad); dfree(g->gdpart); dfree(g->lc_dgrad);
     g->inflow_acc = nullptr; g->lc_adj = nullptr; g->lc_cgrad = nullptr; g->gdpart = nullptr;
+    g->lc_dgrad = nullptr;
     g->adj_gdrain.clear();
     g->closs = nullptr; g->closs_cap = 0; g->hmax_field = nullptr; g->track_max = false;
     g->lc_n = nullptr; g->lc_drain = nullptr; g->dacc = nullptr;

@@ -100,6 +100,7 @@ struct flood_grid {
     double* gdpart = nullptr;     // [M][nslot] drainage-rate gradient partials
     std::vector<double> adj_gdrain;  // [M] dL/d(drainage rate) of the last adjoint
     double* lc_cgrad = nullptr;   // [M][4] per-class Manning gradients of the last adjoint
+    double* lc_dgrad = nullptr;   // [M] drainage-rate gradients (device copy, calibration)
     // inflow hydrograph (inflow.cu)
     float* inflow = nullptr;      // [inflow_blocks] discharge per rain block (m^3/s)
     int inflow_blocks = 0, in_r0 = 0, in_r1 = 0;
@@ -141,6 +142,9 @@ void launch_copy_planes(float* field, const int32_t* n_copy, const int32_t* dsts
 int land_ensemble_init(flood_grid* g);  // per-member land-cover defaults after flood_ensemble_init
 // Fill g->lc_adj from the classes and the members' current class roughness.
 int land_adjoint_fields(flood_grid* g, cudaStream_t s);
+// The calibration step on the land-cover parameters (loss: [M] on the device).
+int land_calibration_step(flood_grid* g, const double* loss, double eta, double delta,
+                          cudaStream_t s);
 void launch_land_permute(float* lc_n, float* lc_drain, const int32_t* src, const int32_t* resampled,
                          int M, cudaStream_t s);
 

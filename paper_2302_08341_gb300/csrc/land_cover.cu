@@ -98,6 +98,56 @@ __global__ void __launch_bounds__(kGradThreads) land_class_grad_kernel(
 
 namespace flood {
 
+// One joint step per member on its land-cover parameters (the class
+// roughness and the drainage rate) in log-parameter space with the Polyak
+// length of its own loss: G = theta * dL/dtheta, step = clip(-eta L G / |G|^2,
+// delta); no step where |G| = 0.
+__global__ void land_calib_kernel(float* __restrict__ lc_n, float* __restrict__ lc_drain,
+                                  const double* __restrict__ cgrad, const double* __restrict__ dgrad,
+                                  const double* __restrict__ loss, int M, int K, double eta,
+                                  double delta)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    double G[kMaxClasses + 1], s2 = 0.0;
+    for (int q = 0; q < K; ++q) {
+        G[q] = (double)lc_n[(size_t)m * 4 + q] * cgrad[(size_t)m * kMaxClasses + q];
+        s2 += G[q] * G[q];
+    }
+    G[K] = (double)lc_drain[m] * dgrad[m];
+    s2 += G[K] * G[K];
+    if (!(s2 > 0.0)) return;
+    const double c = -eta * loss[m] / s2;
+    for (int q = 0; q < K; ++q) {
+        const double n = (double)lc_n[(size_t)m * 4 + q];
+        lc_n[(size_t)m * 4 + q] = (float)(n * exp(fmin(fmax(c * G[q], -delta), delta)));
+    }
+    const double d = (double)lc_drain[m];
+    lc_drain[m] = (float)(d * exp(fmin(fmax(c * G[K], -delta), delta)));
+}
+
+int land_calibration_step(flood_grid* g, const double* loss, double eta, double delta, cudaStream_t s)
+{
+    const int M = g->M;
+    if (!g->lc_cgrad) {
+        const int rc = dalloc(g, &g->lc_cgrad, (size_t)M * kMaxClasses);
+        if (rc) return rc;
+    }
+    if (!g->lc_dgrad) {
+        const int rc = dalloc(g, &g->lc_dgrad, (size_t)M);
+        if (rc) return rc;
+    }
+    land_class_grad_kernel<<<M, kGradThreads, 0, s>>>(g->gnm, g->cls8, g->ny, g->nx, g->ld, g->plane,
+                                                      g->lc_cgrad);
+    CK(g, cudaMemcpyAsync(g->lc_dgrad, g->adj_gdrain.data(), sizeof(double) * M,
+                          cudaMemcpyHostToDevice, s));
+    land_calib_kernel<<<(M + 127) / 128, 128, 0, s>>>(g->lc_n, g->lc_drain, g->lc_cgrad, g->lc_dgrad,
+                                                      loss, M, g->lc_K, eta, delta);
+    g->launches += 2;
+    CK(g, cudaGetLastError());
+    return FLOOD_OK;
+}
+
 int land_adjoint_fields(flood_grid* g, cudaStream_t s)
 {
     const int M = g->M;

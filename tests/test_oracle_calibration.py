@@ -185,3 +185,25 @@ def test_pins_catch_planted_calibration_mistakes(name, old, new):
     mod = types.ModuleType("calibration_mutant")
     exec(compile(src.replace(old, new), "calibration_mutant.py", "exec"), mod.__dict__)
     assert _pins_fail(mod), name
+
+
+def test_land_step_removes_eta_of_a_linear_loss_to_first_order():
+    """For L linear in the log-parameters, the joint step changes L by
+    -eta L to first order (no clipping): sum_j G_j step_j = -eta L; a member
+    with zero gradient does not move; the drainage rate moves with the
+    classes' roughness."""
+    rng = np.random.default_rng(11)
+    n = rng.uniform(0.02, 0.2, (3, 3))
+    d = rng.uniform(1e-6, 5e-6, 3)
+    gc = rng.normal(0, 1.0, (3, 3)); gc[1] = 0.0
+    gd = rng.normal(0, 1e5, 3); gd[1] = 0.0
+    loss = np.array([0.02, 0.5, 0.03])
+    eta = 1e-3
+    n2, d2 = CAL.land_step(loss, gc, n, gd, d, eta=eta, delta=10.0)
+    for i in (0, 2):
+        dl = np.sum(n[i] * gc[i] * np.log(n2[i] / n[i])) + d[i] * gd[i] * np.log(d2[i] / d[i])
+        assert np.isclose(dl, -eta * loss[i], rtol=1e-12)
+        assert d2[i] != d[i]
+    assert np.array_equal(n2[1], n[1]) and d2[1] == d[1]
+    n3, _ = CAL.land_step(loss, gc, n, gd, d, eta=10.0, delta=0.05)
+    assert np.all(np.abs(np.log(n3 / n)) <= 0.05 * (1 + 1e-12))
