@@ -33,7 +33,10 @@
  * Section 4.1, Manning normal flow, seiche period sqrt(g h), lake at rest,
  * uniform rain, exact volume balance, x/y transposition symmetry; scipy's
  * Gaussian density for Eq. 9-11, brute-force enumeration of systematic
- * resampling).  No function is left without a pin.
+ * resampling; Eq. 4 at a known maximum depth through the evolution loop, a
+ * gauge sample of a field whose values name their member and cell, the
+ * ensemble loop equal to each member evolved alone).  No function is left
+ * without a pin.
  */
 #include <math.h>
 #include <stdint.h>

@@ -12,6 +12,7 @@ import sys
 
 import oracle
 from tests import test_oracle_adjoint as A
+from tests import test_oracle_helpers as H
 from tests import test_oracle_inflow as IN
 from tests import test_oracle_land_cover as LC
 from tests import test_oracle_pf as P
@@ -54,6 +55,10 @@ PINS = [
     IN.test_closed_box_stores_the_inflow_exactly,
     IN.test_piecewise_series_lands_on_block_edges,
     IN.test_volume_balance_with_inflow_and_rain_to_1e12,
+    H.test_steps_at_rest_take_eq4_of_section_4_1_depth,
+    functools.partial(H.test_the_deepest_cell_decides_the_step, where=(5, 7)),
+    H.test_gauge_sample_reads_the_member_and_cell_it_names,
+    functools.partial(H.test_ensemble_loop_equals_each_member_alone, nthreads=4),
 ]
 
 # (name, original text, planted mistake)
@@ -125,6 +130,19 @@ MUTATIONS = [
     ("adjoint loss without the 2", "lh[cells[g]] += 2.0 * (hk1[cells[g]]",
      "lh[cells[g]] += (hk1[cells[g]]"),
     ("adjoint rain without dt", "gr += lt[IX(r, c)] * dt * rate * rcv;", "gr += lt[IX(r, c)] * rate * rcv;"),
+    ("h_max over the first row only",
+     "for (size_t i = 0; i < (size_t)ny * (size_t)nx; ++i) m = h[i] > m ? h[i] : m;",
+     "for (size_t i = 0; i < (size_t)nx; ++i) m = h[i] > m ? h[i] : m;"),
+    ("h_max as the minimum", "m = h[i] > m ? h[i] : m;", "m = h[i] < m ? h[i] : m;"),
+    ("h_max as the mean depth",
+     "for (size_t i = 0; i < (size_t)ny * (size_t)nx; ++i) m = h[i] > m ? h[i] : m;\n    return m;",
+     "for (size_t i = 0; i < (size_t)ny * (size_t)nx; ++i) m += h[i];\n    return m / ((double)ny * nx);"),
+    ("gauge member stride of the gauge count", "h[(size_t)m * ncell + cells[g]]",
+     "h[(size_t)m * G + cells[g]]"),
+    ("gauge outputs transposed", "y[(size_t)m * G + g] =", "y[(size_t)g * M + m] ="),
+    ("ensemble qx offset by the cell count", "qx + m * nqx", "qx + m * nc"),
+    ("ensemble members share one clock", "&t[m], t_end", "&t[0], t_end"),
+    ("ensemble members share one scale", "scale[m], rain_mult[m]", "scale[0], rain_mult[m]"),
 ]
 
 
