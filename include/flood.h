@@ -373,15 +373,19 @@ int flood_roughness_factor_grad(flood_grid* g, double* grad, void* stream);
 /*
  * flood_calibration_step -- one descent step from the last flood_adjoint
  * (same precondition as flood_roughness_factor_grad; grad_n is only needed
- * when a factor field or land cover is set).  In log-parameter space with the
- * Polyak step of a loss whose minimum is zero, each component clipped to
- * [-delta, delta]:
+ * when a factor field is set).  In log-parameter space with the Polyak step
+ * of a loss whose minimum is zero, each component clipped to [-delta, delta]:
  *   member i:  m_i <- m_i exp(clip(-eta L_i / g_i)),  g_i = m_i dL_i/dm_i
  *   field:     f_b <- f_b exp(clip(-eta L G_b / |G|^2)),  G_b = f_b dL/df_b,
  *              L = sum_i L_i, then n = n0 * f
- *   land cover, member i, jointly over theta = (its n of every class, its
- *              drainage rate): theta_j <- theta_j exp(clip(-eta L_i G_j /
- *              |G|^2)), G_j = theta_j dL_i/dtheta_j (flood_adjoint_land_grad)
+ *   land cover, member i: one joint step over all of its parameters,
+ *              theta = (its rain multiplier, its n of every class, its
+ *              drainage rate), in place of the member step above:
+ *              theta_j <- theta_j exp(clip(-eta L_i G_j / |G|^2)),
+ *              G_j = theta_j dL_i/dtheta_j (flood_adjoint_land_grad), so the
+ *              step removes eta L_i to first order once; after an adjoint
+ *              without grad_n the class roughness stays and the step runs
+ *              over the rain multiplier and drainage rate
  * (g_i = 0 or |G| = 0 leaves the parameters unchanged).  L_i is recomputed on
  * the device from the adjoint's recorded gauge outputs.  loss_out [N] FP64
  * (host or device, or NULL) receives L_i.  After the step the adjoint is

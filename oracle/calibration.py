@@ -15,8 +15,10 @@ update is an extension.  Its pieces, written out plainly:
   with respect to the log-parameters, every component clipped to
   [-delta, delta]: per member for its rain multiplier (its own loss L_i),
   jointly for the shared factor field (the total loss L = sum_i L_i), and,
-  with land cover (Section 4.1), jointly per member for its Manning n of
-  every class and its drainage rate (its own loss L_i).
+  with land cover (Section 4.1), one joint step per member over all of its
+  parameters -- rain multiplier, Manning n of every class and drainage rate --
+  for its own loss L_i (a separate step on the rain multiplier beside one on
+  the land-cover parameters would remove 2 eta L_i to first order).
 """
 from __future__ import annotations
 
@@ -76,20 +78,29 @@ def calibration_step(loss, grad_rain, rain_mult, factor=None, factor_grad_=None,
     return m_new, f_new
 
 
-def land_step(loss, grad_class, n_class, grad_drain, drain, eta=1.0, delta=0.2):
-    """One joint step per member on its land-cover parameters: theta_i =
-    (n_i1 .. n_iK, d_i), G = theta_i * dL_i/dtheta_i (log-parameter
-    gradient), step = clip(-eta L_i G / |G|^2, delta) (no step where |G| = 0).
-    Returns (new n_class [M][K], new drain [M])."""
+def land_step(loss, grad_rain, rain_mult, grad_class, n_class, grad_drain, drain, eta=1.0,
+              delta=0.2):
+    """One joint step per member over theta_i = (m_i, n_i1 .. n_iK, d_i), its
+    rain multiplier, class roughness and drainage rate: G = theta_i *
+    dL_i/dtheta_i (the log-parameter gradient), step = clip(-eta L_i G /
+    |G|^2, delta), no step where |G| = 0.  To first order (no clipping) the
+    member's loss changes by sum_j G_j step_j = -eta L_i.  grad_class may be
+    None (no per-cell Manning gradients): the class roughness then stays and
+    the step runs over (m_i, d_i).  Returns (new m [M], new n_class [M][K],
+    new drain [M])."""
     loss = np.asarray(loss, np.float64)
+    m = np.asarray(rain_mult, np.float64)
     n = np.asarray(n_class, np.float64)
     d = np.asarray(drain, np.float64)
-    Gn = n * np.asarray(grad_class, np.float64)
+    Gm = m * np.asarray(grad_rain, np.float64)
+    Gn = np.zeros_like(n) if grad_class is None else n * np.asarray(grad_class, np.float64)
     Gd = d * np.asarray(grad_drain, np.float64)
-    s2 = np.sum(Gn * Gn, axis=1) + Gd * Gd
-    n_new, d_new = n.copy(), d.copy()
+    s2 = Gm * Gm + np.sum(Gn * Gn, axis=1) + Gd * Gd
+    m_new, n_new, d_new = m.copy(), n.copy(), d.copy()
     for i in range(len(loss)):
         if s2[i] > 0.0:
-            n_new[i] = n[i] * np.exp(_clip(-eta * loss[i] * Gn[i] / s2[i], delta))
-            d_new[i] = d[i] * np.exp(_clip(-eta * loss[i] * Gd[i] / s2[i], delta))
-    return n_new, d_new
+            c = -eta * loss[i] / s2[i]
+            m_new[i] = m[i] * np.exp(_clip(c * Gm[i], delta))
+            n_new[i] = n[i] * np.exp(_clip(c * Gn[i], delta))
+            d_new[i] = d[i] * np.exp(_clip(c * Gd[i], delta))
+    return m_new, n_new, d_new

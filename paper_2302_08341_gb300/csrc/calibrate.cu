@@ -71,6 +71,8 @@ struct CalArgs {
     const double* gpart;   // [M][nslot][2] per-warp dL/d(rain multiplier), dL/d(scale)
     float* rain_mult;      // [M] in / out
     double* loss;          // [M] out
+    double* rain_grad;     // [M] out: dL_i/d(rain multiplier), for the joint step (land cover)
+    int joint;             // 1: the rain multiplier moves in the joint land-cover step instead
     float* fac;            // [B] in / out (or null)
     const double* fgrad;   // [B]
     int ns, G, M, nslot, B;
@@ -79,8 +81,10 @@ struct CalArgs {
 
 __device__ __forceinline__ double clip(double x, double d) { return fmin(fmax(x, -d), d); }
 
-// Single CTA: per-member loss and rain step, then the field step (its
-// squared gradient norm by a fixed-order tree).
+// Single CTA: per-member loss and rain step (with land cover only the loss
+// and the rain gradient: the joint step takes the rain multiplier with the
+// land-cover parameters), then the field step (its squared gradient norm by
+// a fixed-order tree).
 __global__ void __launch_bounds__(kCalThreads) calib_kernel(const CalArgs a)
 {
     for (int m = threadIdx.x; m < a.M; m += blockDim.x) {
@@ -94,6 +98,10 @@ __global__ void __launch_bounds__(kCalThreads) calib_kernel(const CalArgs a)
         a.loss[m] = L;
         double gm = 0.0;  // the same order as the rain gradient flood_adjoint reports
         for (int k = 0; k < a.nslot; ++k) gm += a.gpart[((size_t)m * a.nslot + k) * 2];
+        if (a.joint) {
+            a.rain_grad[m] = gm;
+            continue;
+        }
         const double mi = (double)a.rain_mult[m];
         const double gt = mi * gm;
         const double st = gt != 0.0 ? clip(-a.eta * L / gt, a.delta) : 0.0;
@@ -220,11 +228,11 @@ extern "C" int flood_calibration_step(flood_grid* g, double eta, double delta, d
         return flood::fail(g, FLOOD_ERR_ARG, "eta and delta must be positive");
     if (g->M == 0) return flood::fail(g, FLOOD_ERR_STATE, "flood_ensemble_init has not been called");
     const bool field = g->fac != nullptr;
-    int rc = check_fresh_adjoint(g, field || g->lc_on);
+    int rc = check_fresh_adjoint(g, field);
     if (rc) return rc;
     cudaStream_t s = S(stream);
     if (g->closs_cap < g->M) {
-        if ((rc = flood::dalloc(g, &g->closs, g->M))) return rc;
+        if ((rc = flood::dalloc(g, &g->closs, 2 * (size_t)g->M))) return rc;
         g->closs_cap = g->M;
     }
     if (field) {
@@ -238,6 +246,8 @@ extern "C" int flood_calibration_step(flood_grid* g, double eta, double delta, d
     a.gpart = g->gpart;
     a.rain_mult = g->rain_mult;
     a.loss = g->closs;
+    a.rain_grad = g->closs + g->M;
+    a.joint = g->lc_on ? 1 : 0;
     a.fac = g->fac;
     a.fgrad = g->fgrad;
     a.ns = g->adj_ns;
@@ -251,7 +261,8 @@ extern "C" int flood_calibration_step(flood_grid* g, double eta, double delta, d
     g->launches++;
     if (field) launch_apply(g, s);
     CK(g, cudaGetLastError());
-    if (g->lc_on && (rc = flood::land_calibration_step(g, g->closs, eta, delta, s))) return rc;
+    if (g->lc_on && (rc = flood::land_calibration_step(g, g->closs, g->closs + g->M, eta, delta, s)))
+        return rc;
     if (loss_out)
         CK(g, cudaMemcpyAsync(loss_out, g->closs, sizeof(double) * g->M, cudaMemcpyDefault, s));
     CK(g, cudaStreamSynchronize(s));

@@ -112,7 +112,7 @@ struct flood_grid {
     float* n0 = nullptr;          // [ny][ld] base roughness, kept once a factor field is set
     float* fac = nullptr;         // [fcy][fcx] roughness factor field
     double* fgrad = nullptr;      // [fcy][fcx] dL/df of the last adjoint
-    double* closs = nullptr;      // [closs_cap] per-member losses of the last adjoint
+    double* closs = nullptr;      // [2][closs_cap] per-member losses and rain gradients
     int fcy = 0, fcx = 0, closs_cap = 0;
     uint64_t epoch = 0;           // bumped by every change of the ensemble or of its inputs
     uint64_t adj_epoch = ~0ull;   // epoch right after the last flood_adjoint
@@ -142,9 +142,11 @@ void launch_copy_planes(float* field, const int32_t* n_copy, const int32_t* dsts
 int land_ensemble_init(flood_grid* g);  // per-member land-cover defaults after flood_ensemble_init
 // Fill g->lc_adj from the classes and the members' current class roughness.
 int land_adjoint_fields(flood_grid* g, cudaStream_t s);
-// The calibration step on the land-cover parameters (loss: [M] on the device).
-int land_calibration_step(flood_grid* g, const double* loss, double eta, double delta,
-                          cudaStream_t s);
+// The calibration step with land cover: one joint step per member over its
+// rain multiplier and land-cover parameters (loss, rain_grad: [M] on the
+// device, rain_grad = dL_i/d(rain multiplier of i)).
+int land_calibration_step(flood_grid* g, const double* loss, const double* rain_grad, double eta,
+                          double delta, cudaStream_t s);
 void launch_land_permute(float* lc_n, float* lc_drain, const int32_t* src, const int32_t* resampled,
                          int M, cudaStream_t s);
 

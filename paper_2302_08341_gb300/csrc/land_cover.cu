@@ -98,24 +98,30 @@ __global__ void __launch_bounds__(kGradThreads) land_class_grad_kernel(
 
 namespace flood {
 
-// One joint step per member on its land-cover parameters (the class
-// roughness and the drainage rate) in log-parameter space with the Polyak
-// length of its own loss: G = theta * dL/dtheta, step = clip(-eta L G / |G|^2,
-// delta); no step where |G| = 0.
-__global__ void land_calib_kernel(float* __restrict__ lc_n, float* __restrict__ lc_drain,
+// One joint step per member over all of its parameters -- the rain
+// multiplier, the class roughness and the drainage rate -- in log-parameter
+// space with the Polyak length of its own loss: G = theta * dL/dtheta,
+// step = clip(-eta L G / |G|^2, delta); no step where |G| = 0.  One step for
+// the whole vector removes eta L to first order (a rain step beside a
+// land-cover step would remove it twice).  cgrad may be null (no per-cell
+// Manning gradients): the class roughness then stays.
+__global__ void land_calib_kernel(float* __restrict__ rain_mult, float* __restrict__ lc_n,
+                                  float* __restrict__ lc_drain, const double* __restrict__ rgrad,
                                   const double* __restrict__ cgrad, const double* __restrict__ dgrad,
                                   const double* __restrict__ loss, int M, int K, double eta,
                                   double delta)
 {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
-    double G[kMaxClasses + 1], s2 = 0.0;
+    double G[kMaxClasses + 2], s2 = 0.0;
     for (int q = 0; q < K; ++q) {
-        G[q] = (double)lc_n[(size_t)m * 4 + q] * cgrad[(size_t)m * kMaxClasses + q];
+        G[q] = cgrad ? (double)lc_n[(size_t)m * 4 + q] * cgrad[(size_t)m * kMaxClasses + q] : 0.0;
         s2 += G[q] * G[q];
     }
     G[K] = (double)lc_drain[m] * dgrad[m];
     s2 += G[K] * G[K];
+    G[K + 1] = (double)rain_mult[m] * rgrad[m];
+    s2 += G[K + 1] * G[K + 1];
     if (!(s2 > 0.0)) return;
     const double c = -eta * loss[m] / s2;
     for (int q = 0; q < K; ++q) {
@@ -124,12 +130,16 @@ __global__ void land_calib_kernel(float* __restrict__ lc_n, float* __restrict__ 
     }
     const double d = (double)lc_drain[m];
     lc_drain[m] = (float)(d * exp(fmin(fmax(c * G[K], -delta), delta)));
+    const double r = (double)rain_mult[m];
+    rain_mult[m] = (float)(r * exp(fmin(fmax(c * G[K + 1], -delta), delta)));
 }
 
-int land_calibration_step(flood_grid* g, const double* loss, double eta, double delta, cudaStream_t s)
+int land_calibration_step(flood_grid* g, const double* loss, const double* rain_grad, double eta,
+                          double delta, cudaStream_t s)
 {
     const int M = g->M;
-    if (!g->lc_cgrad) {
+    const bool classes = g->adj_gn && g->gnm;
+    if (classes && !g->lc_cgrad) {
         const int rc = dalloc(g, &g->lc_cgrad, (size_t)M * kMaxClasses);
         if (rc) return rc;
     }
@@ -137,13 +147,17 @@ int land_calibration_step(flood_grid* g, const double* loss, double eta, double 
         const int rc = dalloc(g, &g->lc_dgrad, (size_t)M);
         if (rc) return rc;
     }
-    land_class_grad_kernel<<<M, kGradThreads, 0, s>>>(g->gnm, g->cls8, g->ny, g->nx, g->ld, g->plane,
-                                                      g->lc_cgrad);
+    if (classes) {
+        land_class_grad_kernel<<<M, kGradThreads, 0, s>>>(g->gnm, g->cls8, g->ny, g->nx, g->ld,
+                                                          g->plane, g->lc_cgrad);
+        g->launches++;
+    }
     CK(g, cudaMemcpyAsync(g->lc_dgrad, g->adj_gdrain.data(), sizeof(double) * M,
                           cudaMemcpyHostToDevice, s));
-    land_calib_kernel<<<(M + 127) / 128, 128, 0, s>>>(g->lc_n, g->lc_drain, g->lc_cgrad, g->lc_dgrad,
+    land_calib_kernel<<<(M + 127) / 128, 128, 0, s>>>(g->rain_mult, g->lc_n, g->lc_drain, rain_grad,
+                                                      classes ? g->lc_cgrad : nullptr, g->lc_dgrad,
                                                       loss, M, g->lc_K, eta, delta);
-    g->launches += 2;
+    g->launches++;
     CK(g, cudaGetLastError());
     return FLOOD_OK;
 }

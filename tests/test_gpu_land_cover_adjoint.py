@@ -264,9 +264,10 @@ def test_full_size_land_cover_adjoint_window(capi):
 
 
 def test_calibration_step_moves_the_land_parameters_by_the_oracle_rule(capi):
-    """With land cover the calibration step also takes one joint step per
-    member on its class roughness and drainage rate, by the oracle's rule
-    applied to the adjoint's gradients; the rain multipliers follow theirs."""
+    """With land cover the calibration step takes one joint step per member
+    over its rain multiplier, class roughness and drainage rate, by the
+    oracle's rule applied to the adjoint's gradients (so the member's loss
+    moves by -eta L_i to first order once, not once per parameter group)."""
     from oracle import calibration as cal
     case = _wet_land_case(M=3, seed=75)
     terr, cls, h0, rm, sc, n_m, d_m, hy, cells, d, sdt = case
@@ -277,14 +278,42 @@ def test_calibration_step_moves_the_land_parameters_by_the_oracle_rule(capi):
         out = g.adjoint(cells, d, sdt, grad_h0=False)
         gc, gd = g.adjoint_land_grad()
         n0, d0 = g.land_params()
+        rm0 = g.members()["rain_mult"]
         loss = g.calibration_step()
         n1, d1 = g.land_params()
         rm1 = g.members()["rain_mult"]
         with pytest.raises(capi.FloodError):   # the gradients are spent
             g.calibration_step()
     assert np.allclose(loss, out["loss"], rtol=1e-12)
-    n_or, d_or = cal.land_step(out["loss"], gc, n0, gd, d0)
+    m_or, n_or, d_or = cal.land_step(out["loss"], out["grad_rain"], rm0, gc, n0, gd, d0)
     assert np.allclose(n1, n_or, rtol=2e-7) and np.allclose(d1, d_or, rtol=2e-7)
-    assert not np.allclose(n1, n0, rtol=1e-6) and np.all(d1 != d0)
-    m_or, _ = cal.calibration_step(out["loss"], out["grad_rain"], rm)
     assert np.allclose(rm1, m_or, rtol=2e-7)
+    assert not np.allclose(n1, n0, rtol=1e-6) and np.all(d1 != d0) and np.all(rm1 != rm0)
+    # the separate rain step it replaces would have moved the multipliers further
+    m_sep, _ = cal.calibration_step(out["loss"], out["grad_rain"], rm0)
+    assert np.all(np.abs(np.log(rm1 / rm0)) < np.abs(np.log(m_sep / rm0)))
+
+
+def test_calibration_step_without_manning_gradients_moves_rain_and_drainage(capi):
+    """An adjoint without grad_n still allows the step: the class roughness
+    stays and the joint step runs over the rain multiplier and the drainage
+    rate, by the oracle's rule without class gradients."""
+    from oracle import calibration as cal
+    case = _wet_land_case(M=3, seed=76)
+    terr, cls, h0, rm, sc, n_m, d_m, hy, cells, d, sdt = case
+    with capi.Grid(terr.z, terr.n, capi.Params.default()) as g:
+        g.set_land_cover(cls, synth.LAND_CLASSES)
+        g.ensemble_init(len(rm), rm, sc, hy, h0=h0)
+        g.set_land_params(n_m, d_m)
+        out = g.adjoint(cells, d, sdt, grad_h0=False, grad_n=False)
+        _, gd = g.adjoint_land_grad(classes=False)
+        n0, d0 = g.land_params()
+        rm0 = g.members()["rain_mult"]
+        loss = g.calibration_step()
+        n1, d1 = g.land_params()
+        rm1 = g.members()["rain_mult"]
+    assert np.allclose(loss, out["loss"], rtol=1e-12)
+    m_or, n_or, d_or = cal.land_step(out["loss"], out["grad_rain"], rm0, None, n0, gd, d0)
+    assert np.array_equal(n1, n0)
+    assert np.allclose(d1, d_or, rtol=2e-7) and np.allclose(rm1, m_or, rtol=2e-7)
+    assert np.all(d1 != d0) and np.all(rm1 != rm0)

@@ -117,6 +117,56 @@ def pin_clip(cal):
     assert np.array_equal(f_new, np.ones((1, 2)))            # zero field gradient
 
 
+def pin_land_first_order(cal):
+    """For L_i linear in the log-parameters, the joint step over the rain
+    multiplier, the class roughness and the drainage rate changes L_i by
+    -eta L_i to first order (no clipping): sum_j G_j step_j = -eta L_i, once,
+    not once per parameter group; a member with zero gradient does not move;
+    all three groups move together; without class gradients the class
+    roughness stays and the rain multiplier and drainage rate still remove
+    eta L_i; a tight clip bounds every component."""
+    rng = np.random.default_rng(11)
+    m = rng.uniform(0.5, 2.0, 3)
+    n = rng.uniform(0.02, 0.2, (3, 3))
+    d = rng.uniform(1e-6, 5e-6, 3)
+    gm = rng.normal(0, 0.5, 3); gm[1] = 0.0
+    gc = rng.normal(0, 1.0, (3, 3)); gc[1] = 0.0
+    gd = rng.normal(0, 1e5, 3); gd[1] = 0.0
+    loss = np.array([0.02, 0.5, 0.03])
+    eta = 1e-3
+
+    def change(m2, n2, d2, i, with_class=True):
+        dl = m[i] * gm[i] * np.log(m2[i] / m[i]) + d[i] * gd[i] * np.log(d2[i] / d[i])
+        if with_class:
+            dl += np.sum(n[i] * gc[i] * np.log(n2[i] / n[i]))
+        return dl
+
+    m2, n2, d2 = cal.land_step(loss, gm, m, gc, n, gd, d, eta=eta, delta=10.0)
+    for i in (0, 2):
+        assert np.isclose(change(m2, n2, d2, i), -eta * loss[i], rtol=1e-12)
+        assert d2[i] != d[i] and m2[i] != m[i] and np.all(n2[i] != n[i])
+    assert m2[1] == m[1] and np.array_equal(n2[1], n[1]) and d2[1] == d[1]
+    m4, n4, d4 = cal.land_step(loss, gm, m, None, n, gd, d, eta=eta, delta=10.0)
+    assert np.array_equal(n4, n)
+    for i in (0, 2):
+        assert np.isclose(change(m4, n4, d4, i, with_class=False), -eta * loss[i], rtol=1e-12)
+    _, n3, _ = cal.land_step(loss, gm, m, gc, n, gd, d, eta=10.0, delta=0.05)
+    assert np.all(np.abs(np.log(n3 / n)) <= 0.05 * (1 + 1e-12))
+
+
+def pin_land_reduces_to_rain(cal):
+    """With zero land-cover gradients the joint step is the rain
+    multiplier's own Polyak step (calibration_step without a field)."""
+    rng = np.random.default_rng(12)
+    m = rng.uniform(0.5, 2.0, 4)
+    gm = rng.normal(0, 0.5, 4)
+    loss = rng.uniform(0.01, 0.1, 4)
+    n = np.full((4, 2), 0.05); d = np.full(4, 2e-6)
+    m2, n2, d2 = cal.land_step(loss, gm, m, np.zeros((4, 2)), n, np.zeros(4), d)
+    m_ref, _ = cal.calibration_step(loss, gm, m)
+    assert np.allclose(m2, m_ref, rtol=1e-15) and np.array_equal(n2, n) and np.array_equal(d2, d)
+
+
 @pytest.mark.parametrize("ny,nx,cy,cx", [(11, 15, 3, 4), (9, 14, 2, 5)])
 def test_factor_gradient_matches_central_differences(ny, nx, cy, cx):
     pin_factor_gradient(CAL, ny, nx, cy, cx)
@@ -146,6 +196,14 @@ def test_clip_and_zero_gradient():
     pin_clip(CAL)
 
 
+def test_land_step_removes_eta_of_a_linear_loss_to_first_order():
+    pin_land_first_order(CAL)
+
+
+def test_land_step_is_the_polyak_step_of_the_calibration_when_only_rain_moves():
+    pin_land_reduces_to_rain(CAL)
+
+
 # plausible mistakes in the calibration oracle; each must fail some pin
 MUTATIONS = [
     ("block index rounded up", "return (r * cy) // ny, (c * cx) // nx",
@@ -162,13 +220,22 @@ MUTATIONS = [
      "np.exp(_clip(eta * L * G / s2, delta))"),
     ("clip one-sided", "return np.minimum(np.maximum(x, -delta), delta)",
      "return np.minimum(x, delta)"),
+    ("joint step leaves the rain multiplier out of |G|^2",
+     "s2 = Gm * Gm + np.sum(Gn * Gn, axis=1) + Gd * Gd", "s2 = np.sum(Gn * Gn, axis=1) + Gd * Gd"),
+    ("joint step leaves the rain multiplier in place",
+     "m_new[i] = m[i] * np.exp(_clip(c * Gm[i], delta))", "pass"),
+    ("drainage gradient not in log space", "Gd = d * np.asarray(grad_drain, np.float64)",
+     "Gd = np.asarray(grad_drain, np.float64)"),
+    ("joint step takes the rain multiplier's own Polyak length",
+     "c = -eta * loss[i] / s2[i]", "c = -eta * loss[i] / (Gm[i] * Gm[i] + 1e-300)"),
 ]
 
 
 def _pins_fail(mod):
     pins = [lambda: pin_factor_gradient(mod, 11, 15, 3, 4), lambda: pin_block_map(mod),
             lambda: pin_fine_field(mod), lambda: pin_unit_factor(mod),
-            lambda: pin_polyak_member(mod), lambda: pin_polyak_field(mod), lambda: pin_clip(mod)]
+            lambda: pin_polyak_member(mod), lambda: pin_polyak_field(mod), lambda: pin_clip(mod),
+            lambda: pin_land_first_order(mod), lambda: pin_land_reduces_to_rain(mod)]
     for pin in pins:
         try:
             pin()
@@ -185,25 +252,3 @@ def test_pins_catch_planted_calibration_mistakes(name, old, new):
     mod = types.ModuleType("calibration_mutant")
     exec(compile(src.replace(old, new), "calibration_mutant.py", "exec"), mod.__dict__)
     assert _pins_fail(mod), name
-
-
-def test_land_step_removes_eta_of_a_linear_loss_to_first_order():
-    """For L linear in the log-parameters, the joint step changes L by
-    -eta L to first order (no clipping): sum_j G_j step_j = -eta L; a member
-    with zero gradient does not move; the drainage rate moves with the
-    classes' roughness."""
-    rng = np.random.default_rng(11)
-    n = rng.uniform(0.02, 0.2, (3, 3))
-    d = rng.uniform(1e-6, 5e-6, 3)
-    gc = rng.normal(0, 1.0, (3, 3)); gc[1] = 0.0
-    gd = rng.normal(0, 1e5, 3); gd[1] = 0.0
-    loss = np.array([0.02, 0.5, 0.03])
-    eta = 1e-3
-    n2, d2 = CAL.land_step(loss, gc, n, gd, d, eta=eta, delta=10.0)
-    for i in (0, 2):
-        dl = np.sum(n[i] * gc[i] * np.log(n2[i] / n[i])) + d[i] * gd[i] * np.log(d2[i] / d[i])
-        assert np.isclose(dl, -eta * loss[i], rtol=1e-12)
-        assert d2[i] != d[i]
-    assert np.array_equal(n2[1], n[1]) and d2[1] == d[1]
-    n3, _ = CAL.land_step(loss, gc, n, gd, d, eta=10.0, delta=0.05)
-    assert np.all(np.abs(np.log(n3 / n)) <= 0.05 * (1 + 1e-12))

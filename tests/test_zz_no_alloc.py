@@ -4,12 +4,15 @@ It serves callers that cannot allocate device memory: code inside a stream
 capture, code living within a device-memory budget that an embedding
 application owns, and loops that must never wait on the allocator.  Its block
 partials sit in a fixed device array, so each call only reads the caller's
-depth field and writes the caller's output.  Checked here against the
-library's own storage report (same arithmetic, so equal to rounding), on two
-calls in a row through the C ABI.  This file is collected last."""
+depth field and writes the caller's output.  Checked here, on two calls in a
+row through the C ABI, against the library's own storage report (same
+arithmetic and order, so bit for bit) and against the FP64 oracle's storage
+of the same depths (a sum in another order: 1e-12 relative).  This file is
+collected last."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2302_08341_gb300 import synth
 from tests.gpu_util import require_gpu
 
@@ -39,7 +42,9 @@ def test_static_storage_matches_the_volume_report_on_two_calls_in_a_row():
         assert rc == 0, L.flood_storage_static_error()
         stream.synchronize()
         assert vol[m] > 0
-        assert abs(out.item() - vol[m]) <= 1e-12 * vol[m]
+        assert out.item() == vol[m]
+        ref = oracle.storage(depths[m].astype(np.float64), 3.0)
+        assert abs(out.item() - ref) <= 1e-12 * ref
     # sizes beyond the fixed partials array are refused before any launch
     rc = L.flood_storage_static(h.data_ptr(), 65537, 1, 1, 3.0, out.data_ptr(), stream.cuda_stream)
     assert rc == -1 and b"FLOOD_STATIC_MAX_ROWS" in L.flood_storage_static_error()
