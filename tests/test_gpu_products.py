@@ -86,7 +86,7 @@ def test_products_equal_the_oracle_products_of_the_same_maxima(capi):
         exceed, pct = g.ensemble_products(0.05, levels)
         hm = np.array([g.max_depth(m) for m in range(M)])
     assert np.ptp(w) > 0
-    assert np.array_equal(exceed, prod.exceedance(hm, w, 0.05).astype(np.float32))
+    assert np.array_equal(exceed, prod.exceedance(hm, w, 0.05))
     assert np.array_equal(pct, prod.percentiles(hm, w, levels))
     assert 0 < exceed.max() <= 1.0
 
@@ -126,6 +126,40 @@ def test_full_size_products_on_sampled_rows(capi):
         w = g.members()["weights"]
         rows = np.random.default_rng(1).choice(ny, 5, replace=False)
         hm = np.array([g.max_depth(m)[rows] for m in range(M)])
-    assert np.array_equal(exceed[rows], prod.exceedance(hm, w, 0.01).astype(np.float32))
+    assert np.array_equal(exceed[rows], prod.exceedance(hm, w, 0.01))
     assert np.array_equal(pct[:, rows], prod.percentiles(hm, w, levels))
     assert exceed.max() > 0
+
+
+@pytest.mark.parametrize("M", [5, 33, 64, 96, 100, 130])
+@pytest.mark.parametrize("equal", [True, False])
+def test_products_every_kernel_path_bit_for_bit(capi, M, equal):
+    """Every member count the products kernels distinguish (sorted in
+    registers up to 96 members with any weights and up to 128 with equal
+    weights, staged in shared memory beyond), with equal and with unequal
+    weights set directly, on a grid whose rows end in a partial block, with
+    every third member rainless (a group of maxima tied at zero in every
+    cell): the maps equal the oracle's, bit for bit, for six levels (two
+    passes of four)."""
+    ny, nx = 12, 150
+    terr = synth.make_terrain(ny, nx, seed=55)
+    hy = synth.hyetograph_constant(90.0, 600.0)
+    rm, sc = synth.ensemble_prior(55, M)
+    rm[::3] = 0.0                                # rainless members: their maxima tie at zero
+    rng = np.random.default_rng(M)
+    w = np.full(M, 1.0 / M) if equal else rng.random(M) ** 3
+    w = w / w.sum()
+    levels = (0.05, 0.1, 0.5, 0.77, 0.9, 1.0)
+    with capi.Grid(terr.z, terr.n) as g:
+        g.ensemble_init(M, rm, sc, hy)
+        g.track_max_depth(True)
+        g.advance_to(120.0)
+        g.set_members(weights=w)
+        w_dev = g.members()["weights"]
+        exceed, pct = g.ensemble_products(0.003, levels)
+        hm = np.array([g.max_depth(m) for m in range(M)])
+    assert np.array_equal(w_dev, w)
+    assert (hm == 0).sum(axis=0).min() >= (M + 2) // 3   # a tie group in every cell
+    assert np.array_equal(exceed, prod.exceedance(hm, w, 0.003))
+    assert np.array_equal(pct, prod.percentiles(hm, w, levels))
+    assert 0 < exceed.max() <= 1.0
