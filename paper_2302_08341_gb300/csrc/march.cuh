@@ -91,8 +91,12 @@ __device__ __forceinline__ void row_depths(const float (&hC)[4], const float (&q
         if (INTERIOR || c + j < nx) {
             const float qW = (j == 0) ? qW0 : qxE[j - 1];
             const float net = __fadd_rn(__fsub_rn(qW, qxE[j]), __fsub_rn(qyN[j], qyS[j]));
+            // the step's increment (fluxes and rain) is formed first and
+            // added to the depth once: adding the same rain depth to every
+            // cell on its own rounds every cell of a binade the same way,
+            // a bias that builds up in the stored volume
             if (LC) {
-                const float hp = __fadd_rn(__fmaf_rn(dt_dx, net, hC[j]), drv[j]);
+                const float hp = __fadd_rn(hC[j], __fmaf_rn(dt_dx, net, drv[j]));
                 const float sink = fminf(ddv[j], fmaxf(hp, 0.0f));
                 hn = __fsub_rn(hp, sink);
                 // drainage that took all the water present leaves a depth
@@ -101,7 +105,7 @@ __device__ __forceinline__ void row_depths(const float (&hC)[4], const float (&q
                 if (hp > 0.0f && sink == hp) hn = -0.0f;
                 row_sink = __fadd_rn(row_sink, sink);
             } else {
-                hn = __fadd_rn(__fmaf_rn(dt_dx, net, hC[j]), dr);
+                hn = __fadd_rn(hC[j], __fmaf_rn(dt_dx, net, dr));
             }
             if (hn < 0.0f) {
                 clamp = __fsub_rn(clamp, hn);

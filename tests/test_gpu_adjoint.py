@@ -172,3 +172,80 @@ def test_adjoint_engines_give_bitwise_identical_gradients(capi, M, limiter):
     for key in ("loss", "grad_rain", "grad_scale", "grad_n", "grad_h0"):
         assert np.array_equal(res[0][key], res[1][key]), key
     assert np.abs(res[0]["grad_n"]).max() > 0
+
+
+def test_adjoint_at_the_calibration_window_size_follows_the_fp64_adjoint(capi):
+    """The adjoint configuration at the size the FP64 oracle adjoint can
+    still carry: a 128 x 128 copy of the synthetic city (same generator:
+    slope, hills, roads, buildings), one member from a dry start under the
+    triangular storm, the loss over 8 gauges sampled every 60 s for 1800 s,
+    a checkpoint every 64 steps.  The observations come from a hidden truth
+    member run by the oracle.  Against the oracle's reverse mode: loss 1e-4,
+    rain-multiplier and Manning-scale gradients 2e-3 relative, the per-cell
+    Manning and initial-depth gradients 2e-3 of their largest magnitude.
+    Against central differences (1e-3 relative steps) of the FP64 forward
+    model: the rain multiplier 1e-3, and the per-cell Manning gradient on 32
+    wet cells with the largest gradients (1e-3 median, 1e-2 worst)."""
+    import concurrent.futures as cf
+    ny = nx = 128
+    terr = synth.make_terrain(ny, nx, seed=3)
+    hy = synth.hyetograph_triangular(60.0, 1200.0, 3600.0)
+    rm, sc = synth.ensemble_prior(3, 1)
+    cells = synth.gauge_cells(terr, 8, seed=3)
+    p = capi.Params.default()
+    op = oracle_params(p, ny, nx)
+    z = terr.z.astype(np.float64); n64 = terr.n.astype(np.float64)
+    trm, tsc = synth.ensemble_prior(1003, 1)
+    truth = oracle.Member.dry(ny, nx)
+    obs = []
+    for s in range(1, 31):
+        oracle.advance(op, z, n64, float(tsc[0]), float(trm[0]), hy, truth, t_end=60.0 * s)
+        obs.append(synth.observe(truth.h.ravel()[cells], seed=3, window=s))
+    d = np.array(obs)
+    with capi.Grid(terr.z, terr.n, p) as g:
+        g.ensemble_init(1, rm, sc, hy)
+        out = g.adjoint(cells, d, 60.0, ckpt_every=64)
+        h_end = g.get_state(0)[0]
+    r0, s0 = float(rm[0]), float(sc[0])
+    ref = oracle.loss_and_grad(op, z, n64, s0, r0, hy, np.zeros((ny, nx)), 60.0, d, cells)
+    assert ref["steps"] >= 1800
+    assert abs(out["loss"][0] - ref["loss"]) <= 1e-4 * ref["loss"]
+    for key in ("grad_rain", "grad_scale"):
+        assert abs(out[key][0] - ref[key]) <= 2e-3 * abs(ref[key]), (key, out[key][0], ref[key])
+    for key, got in (("grad_n", out["grad_n"]), ("grad_h0", out["grad_h0"][0])):
+        err = np.max(np.abs(got - ref[key])) / np.max(np.abs(ref[key]))
+        assert err <= 2e-3, (key, err)
+
+    def loss64(rm_=r0, n_=n64):
+        m = oracle.Member.dry(ny, nx)
+        L = 0.0
+        for s in range(1, 31):
+            oracle.advance(op, z, n_, s0, rm_, hy, m, t_end=60.0 * s)
+            e = m.h.ravel()[cells] - d[s - 1]
+            L += float(np.dot(e, e))
+        return L
+
+    g_n = out["grad_n"].astype(np.float64).ravel()
+    wet = np.nonzero((h_end.ravel() > 0.01) & (np.abs(g_n) > 1e-3 * np.abs(g_n).max()))[0]
+    pick = wet[np.argsort(-np.abs(g_n[wet]))[:32]]
+    assert len(pick) == 32
+
+    def fd_cell(i):
+        e = 1e-3 * n64.flat[i]
+        a = n64.copy(); a.flat[i] += e
+        b = n64.copy(); b.flat[i] -= e
+        return (loss64(n_=a) - loss64(n_=b)) / (2 * e)
+
+    with cf.ThreadPoolExecutor(max_workers=8) as ex:   # the oracle releases the GIL
+        fds = list(ex.map(fd_cell, pick))
+        e = 1e-3 * r0
+        fr = ex.map(lambda x: loss64(rm_=x), (r0 + e, r0 - e))
+        lp, lm = list(fr)
+    fd_rain = (lp - lm) / (2 * e)
+    assert abs(fd_rain - out["grad_rain"][0]) <= 1e-3 * abs(fd_rain), (fd_rain, out["grad_rain"][0])
+    errs = np.array([abs(f - g_n[i]) / abs(f) for f, i in zip(fds, pick)])
+    print(f"adjoint 128x128 x 1800 s: {ref['steps']} steps, grad_n max err "
+          f"{np.max(np.abs(out['grad_n'] - ref['grad_n'])) / np.max(np.abs(ref['grad_n'])):.2e}, "
+          f"FD rain {abs(fd_rain - out['grad_rain'][0]) / abs(fd_rain):.2e}, "
+          f"FD cells median {np.median(errs):.2e} worst {errs.max():.2e}")
+    assert np.median(errs) <= 1e-3 and errs.max() <= 1e-2, (np.median(errs), errs.max())

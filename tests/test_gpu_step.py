@@ -326,3 +326,44 @@ def test_autotune_leaves_the_ensemble_untouched(capi):
     assert np.array_equal(res[0][1]["rain"], res[1][1]["rain"])
     assert np.allclose(res[0][1]["outflow"], res[1][1]["outflow"], rtol=1e-8, atol=0)
     assert np.array_equal(res[0][2]["steps"], res[1][2]["steps"])
+
+
+@pytest.mark.parametrize("ny,nx", [(37, 129), (70, 300), (5, 7)])
+def test_wet_dry_threshold_one_step_on_dyadic_state(capi, ny, nx):
+    """h_eps = 1e-3 m (links whose flow depth is at most 1 mm carry no flow):
+    one step from the same state on both sides.  Beds are multiples of
+    2^-10 m and depths multiples of 2^-14 m, most of them within a few mm of
+    the threshold, so Eq. 3's flow depth is exact in FP32 and FP64 and both
+    sides switch the same links off; every link and depth then agrees to
+    FP32 rounding, and the threshold is seen to act (links the default
+    h_eps = 0 lets flow carry none here)."""
+    rng = np.random.default_rng(ny * 7 + nx)
+    z = (rng.integers(0, 1536, (ny, nx)) / 1024.0).astype(np.float32)
+    n = rng.uniform(0.02, 0.08, (ny, nx)).astype(np.float32)
+    h = (rng.integers(0, 80, (ny, nx)) / 16384.0).astype(np.float32)
+    deep = rng.random((ny, nx)) < 0.3
+    h[deep] = (rng.integers(0, 8192, deep.sum()) / 16384.0).astype(np.float32)
+    qx = rng.normal(0.0, 0.01, (ny, nx)).astype(np.float32)
+    qy = rng.normal(0.0, 0.01, (ny, nx)).astype(np.float32)
+    qx[:, -1] = np.abs(qx[:, -1])
+    qy[-1, :] = 0.0
+    p = capi.Params.default(dt_fixed=0.2, h_eps=1e-3)
+    hy = np.array([30.0 / 3.6e6], np.float32)
+    with capi.Grid(z, n, p) as g:
+        g.ensemble_init(1, np.array([1.1], np.float32), np.array([0.9], np.float32), hy)
+        g.set_state(0, h, qx, qy)
+        g.step(1)
+        h1, qx1, qy1 = g.get_state(0)
+    op = oracle_params(p, ny, nx)
+    assert op.h_eps == 1e-3
+    mo = oracle_member_from_gpu(h, qx, qy)
+    oracle.step(op, z, n, 0.9, float(hy[0]) * 1.1, 0.2, mo)
+    compare(qx1, mo.qx[:, 1:], 2e-5)
+    compare(qy1, mo.qy[1:, :], 2e-5)
+    compare(h1, mo.h, 5e-6)
+    # the links the threshold switched off: zero on both sides, flowing without it
+    op0 = oracle_params(capi.Params.default(dt_fixed=0.2), ny, nx)
+    m0 = oracle_member_from_gpu(h, qx, qy)
+    oracle.step(op0, z, n, 0.9, float(hy[0]) * 1.1, 0.2, m0)
+    off = (mo.qx[:, 1:] == 0.0) & (m0.qx[:, 1:] != 0.0)
+    assert off.sum() >= 1 and np.all(qx1[off] == 0.0)
