@@ -195,6 +195,15 @@ int launch_steps(flood_grid* g, int64_t count, double t_end, cudaStream_t s)
             t.static_map = g->static_map;
             if (a.hmax_field) t.hm_map = g->hm_map;
             if (a.lc_on) t.cls_map = g->cls_map;
+            // the ordinary step leaves out the tiles wholly outside the domain
+            if (a.lc_on && g->lc_out_mask && !a.ckpt && a.wait_budget == kTmaWaitBudgetDefault) {
+                if (g->tiles_rows != g->rows_per_strip) {
+                    const int rc = land_tiles(g);
+                    if (rc) return rc;
+                }
+                a.tiles = g->tiles;
+                a.n_tiles = g->n_tiles;
+            }
             t.a = a;
             if (flood::launch_step_tma(t, g->members_per_cta, s))
                 return fail(g, FLOOD_ERR_STATE, "a changed wait budget covers the plain step only");
@@ -369,6 +378,7 @@ int flood_destroy(flood_grid* g)
     dfree(g->err);
     dfree(g->n0); dfree(g->fac); dfree(g->fgrad);
     dfree(g->inflow);
+    dfree(g->tiles);
     delete g;
     return FLOOD_OK;
 }
@@ -658,6 +668,8 @@ int flood_set_state(flood_grid* g, int member, const float* h, const float* qx, 
             CK(g, cudaMemcpy2DAsync(base + k * g->plane, sizeof(float) * g->ld, ins[k],
                                     sizeof(float) * g->nx, sizeof(float) * g->nx, g->ny,
                                     cudaMemcpyDefault, s));
+    // cells outside the domain stay dry and at rest whatever was given for them
+    if (g->lc_on) flood::land_zero_outside(g, member, 1, s);
     if (h) {  // refresh the member's maximum depth (input of Eq. 4)
         CK(g, cudaMemsetAsync(&slot->hmax_bits, 0, sizeof(uint32_t), s));
         flood::launch_hmax(g->state, g->ms + (g->k % 3) * g->M, g->M, g->ny, g->nx, g->ld, g->plane,

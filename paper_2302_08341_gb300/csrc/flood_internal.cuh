@@ -65,6 +65,11 @@ struct StepArgs {
     const float* inflow;        // [inflow_blocks] discharge per rain block (m^3/s)
     int inflow_blocks, in_r0, in_r1;
     double* inflow_acc;         // [M] inflow volume
+    // tiles of the ordinary TMA step (null: every (span, strip) tile): the
+    // (span, strip) of each tile holding a cell of the domain; the others
+    // lie wholly outside it, where the state stays zero
+    const int2* tiles;
+    int n_tiles;
     size_t plane;               // ny * ld
     int ny, nx, ld, M, nb;
     int rows_per_strip;

@@ -87,6 +87,11 @@ struct flood_grid {
     bool lc_on = false;
     int lc_K = 0;
     uint8_t* cls8 = nullptr;      // [ny][ld] class of every cell
+    uint8_t lc_out_mask = 0;      // bit q: class q lies outside the domain
+    std::vector<uint8_t> lc_span_out;  // [ny][spans] 1: the row's 128-column span lies wholly
+                                       // outside the domain
+    int2* tiles = nullptr;        // [n_tiles] (span, strip) tiles holding a cell of the domain
+    int n_tiles = 0, tiles_rows = 0;  // built for strips of tiles_rows rows (0: not built)
     float lc_n0[4] = {0, 0, 0, 0};       // class Manning n (the members' default)
     float lc_runoff[4] = {1, 1, 1, 1};   // fraction of the rain that stays
     float lc_drains[4] = {0, 0, 0, 0};   // 1: the member's drainage applies
@@ -147,6 +152,13 @@ int land_adjoint_fields(flood_grid* g, cudaStream_t s);
 // device, rain_grad = dL_i/d(rain multiplier of i)).
 int land_calibration_step(flood_grid* g, const double* loss, const double* rain_grad, double eta,
                           double delta, cudaStream_t s);
+// The (span, strip) tiles of the current strip height that hold a cell of
+// the domain (land cover with cells outside it), rebuilt when the strip
+// height changes.
+int land_tiles(flood_grid* g);
+// Cells outside the domain stay dry and at rest: zero their depth and link
+// fluxes in both state buffers of members [m0, m0 + count).
+void land_zero_outside(flood_grid* g, int m0, int count, cudaStream_t s);
 void launch_land_permute(float* lc_n, float* lc_drain, const int32_t* src, const int32_t* resampled,
                          int M, cudaStream_t s);
 

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "grid.cuh"
+#include "pf_kernels.cuh"
 
 #define CK FLOOD_CK
 
@@ -94,9 +95,58 @@ __global__ void __launch_bounds__(kGradThreads) land_class_grad_kernel(
     if (threadIdx.x < kMaxClasses) out[(size_t)m * kMaxClasses + threadIdx.x] = red[threadIdx.x][0];
 }
 
+// Cells of the classes in `mask` (outside the domain) hold no water and no
+// flow: zero h, qx, qy there in both buffers of members [m0, m0 + count).
+__global__ void zero_outside_kernel(float* __restrict__ state, const uint8_t* __restrict__ cls,
+                                    unsigned mask, int M, int m0, int count, size_t plane)
+{
+    const size_t total = (size_t)2 * count * plane;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const size_t e = t % plane;
+        if (!((mask >> cls[e]) & 1u)) continue;
+        const size_t k = t / plane;              // (buffer, member) pair
+        const int b = (int)(k / count), m = m0 + (int)(k % count);
+        float* base = state + ((size_t)b * M + m) * 3 * plane;
+        base[e] = 0.0f;
+        base[plane + e] = 0.0f;
+        base[2 * plane + e] = 0.0f;
+    }
+}
+
 }  // namespace
 
 namespace flood {
+
+void land_zero_outside(flood_grid* g, int m0, int count, cudaStream_t s)
+{
+    if (!g->lc_out_mask || count < 1) return;
+    zero_outside_kernel<<<g->n_sm * 4, 256, 0, s>>>(g->state, g->cls8, g->lc_out_mask, g->M, m0,
+                                                    count, g->plane);
+    g->launches++;
+}
+
+int land_tiles(flood_grid* g)
+{
+    const int spans = (g->nx + 127) / 128, R = g->rows_per_strip;
+    const int strips = (g->ny + R - 1) / R;
+    std::vector<int2> t;
+    t.reserve((size_t)spans * strips);
+    for (int st = 0; st < strips; ++st)
+        for (int sp = 0; sp < spans; ++sp) {
+            bool inside = false;
+            for (int r = st * R; r < std::min(g->ny, (st + 1) * R) && !inside; ++r)
+                inside = !g->lc_span_out[(size_t)r * spans + sp];
+            if (inside) t.push_back(make_int2(sp, st));
+        }
+    if (t.empty()) t.push_back(make_int2(0, 0));  // a grid wholly outside: one idle tile
+    int rc = dalloc(g, &g->tiles, t.size());
+    if (rc) return rc;
+    CK(g, cudaMemcpy(g->tiles, t.data(), sizeof(int2) * t.size(), cudaMemcpyHostToDevice));
+    g->n_tiles = (int)t.size();
+    g->tiles_rows = R;
+    return FLOOD_OK;
+}
 
 // One joint step per member over all of its parameters -- the rain
 // multiplier, the class roughness and the drainage rate -- in log-parameter
@@ -201,6 +251,21 @@ int land_ensemble_init(flood_grid* g)
     FLOOD_CK(g, cudaMemcpy(g->lc_n, n.data(), sizeof(float) * n.size(), cudaMemcpyHostToDevice));
     FLOOD_CK(g, cudaMemcpy(g->lc_drain, d.data(), sizeof(float) * M, cudaMemcpyHostToDevice));
     FLOOD_CK(g, cudaMemset(g->dacc, 0, sizeof(double) * M * g->nslot));
+    if (g->lc_out_mask) {
+        // cells outside the domain start dry and at rest (the step leaves
+        // the tiles wholly outside it untouched); Eq. 4's maximum depth is
+        // taken again without them
+        land_zero_outside(g, 0, M, 0);
+        MemberClock* slot = g->ms + (g->k % 3) * M;
+        std::vector<MemberClock> c(M);
+        FLOOD_CK(g, cudaMemcpy(c.data(), slot, sizeof(MemberClock) * M, cudaMemcpyDeviceToHost));
+        for (auto& x : c) x.hmax_bits = 0;
+        FLOOD_CK(g, cudaMemcpy(slot, c.data(), sizeof(MemberClock) * M, cudaMemcpyHostToDevice));
+        launch_hmax(g->state, slot, M, g->ny, g->nx, g->ld, g->plane, g->n_sm, 0);
+        g->launches++;
+        FLOOD_CK(g, cudaGetLastError());
+        FLOOD_CK(g, cudaDeviceSynchronize());
+    }
     return FLOOD_OK;
 }
 
@@ -261,6 +326,15 @@ extern "C" int flood_set_land_cover(flood_grid* g, const uint8_t* cls, int n_cla
         g->lc_drains[q] = drains[q];
         g->lc_n0[q] = n0[q];
     }
+    g->lc_out_mask = 0;
+    for (int q = 0; q < n_classes; ++q)
+        if (classes[q].outside) g->lc_out_mask |= (uint8_t)(1u << q);
+    const int spans = (g->nx + 127) / 128;
+    g->lc_span_out.assign((size_t)g->ny * spans, 1);
+    for (int r = 0; r < g->ny; ++r)
+        for (int c = 0; c < g->nx; ++c)
+            if (!classes[hc[(size_t)r * g->nx + c]].outside) g->lc_span_out[(size_t)r * spans + c / 128] = 0;
+    g->tiles_rows = 0;
     g->lc_K = n_classes;
     g->lc_rain_cells = rain_cells;
     g->lc_on = true;

@@ -227,13 +227,42 @@ N_RANGES = [(0.08, 0.22), (0.016, 0.030), (0.010, 0.022), (0.05, 0.05)]  # Table
 I_DRN_MM_H = 12.0
 
 
+def irregular_domain(ny: int, nx: int, active_frac: float, seed: int) -> np.ndarray:
+    """An irregular domain inside its bounding box (True = active), shaped
+    like the paper's study area (Section 4.1: 4,002,457 active cells of 3 m
+    in an 8.2 x 7.6 km box, 58 % of it): a blob whose radius varies smoothly
+    with the angle (random harmonics 2-7), centred a little east of the box
+    centre so that it reaches the eastern (outflow) edge, scaled so that
+    ``active_frac`` of the box is active."""
+    rng = np.random.default_rng([seed, 0xD0A1])
+    k = np.arange(2, 8)
+    amp = rng.uniform(0.03, 0.12, len(k)) / k ** 0.5
+    phase = rng.uniform(0.0, 2.0 * np.pi, len(k))
+    rr, cc = np.mgrid[0:ny, 0:nx]
+    y = (rr - 0.5 * ny) / (0.5 * ny)
+    x = (cc - 0.62 * nx) / (0.5 * nx)
+    theta = np.arctan2(y, x)
+    shape = 1.0 + np.sum(amp[:, None, None] * np.cos(k[:, None, None] * theta + phase[:, None, None]),
+                         axis=0)
+    rad = np.hypot(x, y) / shape
+    lo, hi = 0.0, 3.0
+    for _ in range(60):                       # bisection on the blob's scale
+        mid = 0.5 * (lo + hi)
+        if (rad < mid).mean() < active_frac:
+            lo = mid
+        else:
+            hi = mid
+    return rad < hi
+
+
 def land_cover(terrain: Terrain, seed: int, n_ponds: int = 6, pond_side=(8, 30),
-               corner_frac: float = 0.25) -> np.ndarray:
+               corner_frac: float = 0.25, domain: np.ndarray | None = None) -> np.ndarray:
     """Class per cell (uint8): roads and buildings are hardened ground, a few
     rectangular ponds are water bodies, the rest green land; two quarter
     discs of radius ``corner_frac`` x min(ny, nx) at the western (upstream)
     corners lie outside the domain, so the domain is irregular and its
-    outflow edge stays open."""
+    outflow edge stays open -- or, given ``domain`` (True = active, e.g.
+    ``irregular_domain``), every cell outside it."""
     rng = np.random.default_rng(seed)
     ny, nx = terrain.z.shape
     cls = np.zeros((ny, nx), np.uint8)
@@ -244,9 +273,12 @@ def land_cover(terrain: Terrain, seed: int, n_ponds: int = 6, pond_side=(8, 30),
         r0 = int(rng.integers(0, ny - h + 1)); c0 = int(rng.integers(0, nx - w + 1))
         blk = cls[r0:r0 + h, c0:c0 + w]
         blk[blk == 0] = 1
-    rad = corner_frac * min(ny, nx)
-    rr, cc = np.mgrid[0:ny, 0:nx]
-    out = ((rr ** 2 + cc ** 2) < rad ** 2) | (((ny - 1 - rr) ** 2 + cc ** 2) < rad ** 2)
+    if domain is not None:
+        out = ~np.asarray(domain, bool)
+    else:
+        rad = corner_frac * min(ny, nx)
+        rr, cc = np.mgrid[0:ny, 0:nx]
+        out = ((rr ** 2 + cc ** 2) < rad ** 2) | (((ny - 1 - rr) ** 2 + cc ** 2) < rad ** 2)
     cls[out] = 3
     return cls
 

@@ -215,3 +215,64 @@ def test_full_size_land_cover_window(capi):
             oracle.step(sub, z[r0:r1, c0:c1], n[r0:r1, c0:c1], float(sc[m]), rate * float(rm[m]),
                         dt, mo)
             compare(after[m][0][r0:r1, c0:c1][1:-1, 1:-1], mo.h[1:-1, 1:-1], 2e-5)
+
+
+def test_irregular_domain_skips_outside_tiles_and_follows_the_oracle(capi):
+    """An irregular domain shaped like the paper's study area (Section 4.1:
+    the active cells fill 58 % of their bounding box), here 40 % of a
+    130 x 530 box so that many 128-column x 8-row tiles lie wholly outside
+    it.  The ordinary TMA step launches only the tiles that hold a cell of
+    the domain; the direct-load engine launches them all: both give the same
+    states, clocks and volumes bit for bit, and the oracle (which evolves
+    every cell) agrees.  Water given for cells outside the domain, at the
+    start or by flood_set_state, is dropped: those cells stay dry and at
+    rest."""
+    ny, nx, M = 130, 530, 3
+    terr = synth.make_terrain(ny, nx, seed=64)
+    dom = synth.irregular_domain(ny, nx, 0.40, seed=64)
+    cls = synth.land_cover(terr, seed=64, pond_side=(5, 12), domain=dom)
+    out_cell = cls == 3
+    R = 8
+    tiles_in = sum(dom[a:a + R, b:b + 128].any() for a in range(0, ny, R) for b in range(0, nx, 128))
+    tiles_all = ((ny + R - 1) // R) * ((nx + 127) // 128)
+    assert tiles_in <= 0.7 * tiles_all
+    hy = synth.hyetograph_constant(100.0, 600.0)
+    rm, sc = synth.ensemble_prior(64, M)
+    n_m, d_m = synth.land_prior(64, M)
+    h0 = np.full((ny, nx), 0.02, np.float32)          # water everywhere, outside cells too
+    p = capi.Params.default()
+    res = []
+    for engine in (1, 0):
+        with capi.Grid(terr.z, terr.n, p) as g:
+            g.set_land_cover(cls, synth.LAND_CLASSES)
+            g.ensemble_init(M, rm, sc, hy, h0=h0)
+            g.set_land_params(n_m, d_m)
+            g.set_engine(engine)
+            g.set_launch(R, 1)
+            start = g.get_state(1)
+            assert np.all(start[0][out_cell] == 0.0) and np.all(start[0][~out_cell] == 0.02)
+            g.advance_to(300.0)
+            hh, qx, qy = g.get_state(1)
+            g.set_state(1, hh + 0.01, qx + 0.001, qy)  # outside cells: dropped again
+            g.advance_to(600.0)
+            g.sync()
+            res.append(([g.get_state(m) for m in range(M)], g.members(), g.volumes(), g.drained()))
+    (st1, mem1, vol1, dr1), (st0, mem0, vol0, dr0) = res
+    for m in range(M):
+        for k in range(3):
+            assert np.array_equal(st1[m][k], st0[m][k]), (m, k)
+        assert np.all(st1[m][0][out_cell] == 0.0) and np.all(st1[m][1][out_cell] == 0.0)
+    assert np.array_equal(mem1["steps"], mem0["steps"]) and np.array_equal(mem1["t"], mem0["t"])
+    for key in ("storage", "rain", "outflow", "clamp"):
+        assert np.allclose(vol1[key], vol0[key], rtol=1e-9, atol=1e-9), key
+    # the oracle from the same start (member 0 and 2: no set_state in between)
+    for m in (0, 2):
+        z, n, rc, dr, out = _oracle_fields(terr, cls, n_m[m], d_m[m])
+        op = oracle_params(p, ny, nx)
+        op.rc, op.drain = rc, dr
+        mo = oracle.Member.dry(ny, nx, np.where(out, 0.0, 0.02))
+        oracle.advance(op, z, n, float(sc[m]), float(rm[m]), hy, mo, t_end=600.0)
+        compare(st1[m][0], mo.h, 1e-3)
+        assert np.all(mo.h[out] == 0.0)
+        V = oracle.storage(mo.h, p.dx)
+        assert abs(vol1["storage"][m] - V) <= 1e-5 * V
