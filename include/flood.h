@@ -163,6 +163,11 @@ int flood_gauge_sample(flood_grid* g, int n_gauges, const int32_t* cell_idx, flo
  *   neff_out     N_eff, or 0 when every posterior weight underflowed to zero
  *                (the ensemble is then left unchanged) (or NULL)
  *   resampled_out 1 if the ensemble was resampled, else 0 (or NULL)
+ * The library draws no random numbers: the resampling offset u and the
+ * perturbations beta are the caller's (the tests and the benchmark take them
+ * from numpy's PCG64 stream seeded with (seed, 0xF1, window), u first, then
+ * beta_i = 1 + 0.05 N(0, 1) -- paper_2302_08341_gb300.synth.pf_draws), so a
+ * C caller that wants the same particles must supply the same numbers.
  * Asynchronous (outputs valid after the stream is synchronised).
  * Errors: FLOOD_ERR_ARG (sizes, u outside [0,1)), FLOOD_ERR_STATE.
  */
@@ -263,7 +268,12 @@ int flood_flow_sample(flood_grid* g, int n_sections, const flood_section* sectio
  *   h' = h* - min(drains(class) * drainage rate * dt, max(h*, 0)),
  * and reports the drained volume (flood_drained_volume); storage = rain -
  * outflow + clamp - drained.  Cells outside the domain get their bed raised
- * to 1e6 m and no rain, so no link into them carries flow (Eq. 3).
+ * to 1e6 m and no rain, so no link into them carries flow (Eq. 3); they are
+ * held dry and at rest (flood_set_land_cover, flood_ensemble_init and
+ * flood_set_state zero their depth and link fluxes), so the ordinary step of
+ * the TMA engine launches only the tiles (128 columns x the strip height)
+ * that hold a cell of the domain, with the same results as a step over
+ * every tile.
  * flood_adjoint covers it: the Manning gradients are then taken with
  * respect to each member's own n at each cell (the class's), the rain
  * multiplier's gradient weighs each cell by its runoff coefficient, and a
@@ -314,12 +324,17 @@ int flood_adjoint_land_grad(flood_grid* g, double* grad_n_class, double* grad_dr
 /* ==== Ensemble products (Section 4.4, Figs. 15-16) ==========================
  * Per member, the running maximum depth hmax_i(r, c) over every step since
  * tracking was turned on; from those and the particle weights w_i, per cell:
- *   exceedance  P = sum_i w_i [hmax_i >= threshold]   (FP64 sum in member
- *               order, the threshold rounded to FP32, result FP32)
+ *   exceedance  P = sum_i w_i [hmax_i >= threshold]   (the threshold rounded
+ *               to FP32, result FP32)
  *   percentile  h_a = the smallest hmax_i whose weighted empirical
  *               distribution value W_i = sum of w_j over members j with
- *               hmax_j <= hmax_i (FP64, member order) reaches a; where
- *               rounding leaves every W_i below a, the largest hmax_i. */
+ *               hmax_j <= hmax_i reaches a; where every W_i stays below a,
+ *               the largest hmax_i.
+ * The sums are exact: each weight is rounded once to a whole number of
+ * units of 2^-60 (to nearest, ties to even) and the units are added as
+ * 64-bit integers, so no summation order changes a map; W_i reaches a when
+ * W_i >= ceil(a 2^60) units, and P is the unit sum times 2^-60 rounded to
+ * FP64, then to FP32.  Weights must lie in [0, 1] and sum to about one. */
 
 /* Turn tracking on (1: the maxima start at the current depths) or off (0).
  * While on, every step also raises the maxima (8 more bytes per
@@ -334,9 +349,12 @@ int flood_get_max_depth(flood_grid* g, int member, float* out, void* stream);
 
 /* The products above with the current particle weights.  exceed: [ny][nx]
  * FP32 or NULL; levels: n_levels (0..16) values in (0, 1]; pct:
- * [n_levels][ny][nx] FP32.  Host or device outputs.  Synchronous.  Errors:
- * FLOOD_ERR_STATE (not tracking), FLOOD_ERR_ARG (levels, more than 384
- * members or 65535 rows), FLOOD_ERR_OOM. */
+ * [n_levels][ny][nx] FP32.  Host or device outputs.  One thread per cell
+ * sorts the cell's maxima in registers (up to 96 members, 128 with equal
+ * weights; more members are staged in shared memory).  Synchronous.  Errors:
+ * FLOOD_ERR_STATE (not tracking, or weights outside [0, 1] or summing far
+ * above one), FLOOD_ERR_ARG (levels, more than 384 members or 65535 rows),
+ * FLOOD_ERR_OOM. */
 int flood_ensemble_products(flood_grid* g, double threshold, int n_levels, const double* levels,
                             float* exceed, float* pct, void* stream);
 
@@ -499,6 +517,23 @@ int flood_batch_init(flood_batch* b, const float* const* hyetographs, const int3
                      const float* rain_mult, const float* manning_scale, const double* t_end,
                      void* stream);
 
+/* The same with n_members[i] >= 1 members per scenario (the members of a
+ * scenario are an ensemble, Eq. 6-7: they share its bed, roughness, storm and
+ * end time, and each has its own state, clock and step length (Eq. 4),
+ * rain multiplier and Manning scale).  rain_mult and manning_scale hold one
+ * value per member, scenario by scenario ([sum n_members]).  The warps that
+ * step one tile of a scenario for its different members run next to one
+ * another, so the tile's bed and roughness come from DRAM once for all of
+ * them (Section 3.2's shared definitive data).  Members are indexed
+ * scenario by scenario wherever per-member arrays are returned; with one
+ * member per scenario this is flood_batch_init.  Synchronous.  Errors:
+ * FLOOD_ERR_ARG (a count outside 1..4096, more than 2^20 members in all),
+ * FLOOD_ERR_OOM. */
+int flood_batch_init_members(flood_batch* b, const float* const* hyetographs,
+                             const int32_t* n_blocks, const int32_t* n_members,
+                             const float* rain_mult, const float* manning_scale,
+                             const double* t_end, void* stream);
+
 /* Advance every scenario to min(t_stop, t_end[i]) (a window end), each with
  * its own steps.  Synchronises `stream` between graph replays (engines 0-1)
  * or after the persistent launch (engine 2) to follow the scenarios' clocks.
@@ -531,10 +566,15 @@ int flood_batch_set_engine(flood_batch* b, int engine);
  * to arrive give up at once.  Errors: FLOOD_ERR_ARG. */
 int flood_batch_set_wait_budget(flood_batch* b, int64_t cycles);
 
-/* Scenario i's state as [ny[i]][nx[i]] FP32 arrays (any may be NULL). */
+/* Scenario i's state (its first member) as [ny[i]][nx[i]] FP32 arrays (any
+ * may be NULL). */
 int flood_batch_get_state(flood_batch* b, int i, float* h, float* qx, float* qy, void* stream);
+/* The state of member m of scenario i. */
+int flood_batch_get_member_state(flood_batch* b, int i, int m, float* h, float* qx, float* qy,
+                                 void* stream);
 
-/* Per-scenario clocks and FP64 volumes, each [n] (any may be NULL).
+/* Per-member clocks and FP64 volumes, each [sum of the members], scenario by
+ * scenario ([n] with one member per scenario; any may be NULL).
  * Synchronous. */
 int flood_batch_members(flood_batch* b, double* t, int64_t* steps, double* storage, double* rain,
                         double* outflow, double* clamp);

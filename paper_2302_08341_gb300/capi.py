@@ -36,7 +36,7 @@ EXPORTED = ["flood_default_params", "flood_last_error", "flood_create_grid", "fl
             "flood_ensemble_products", "flood_set_land_cover", "flood_set_land_params",
             "flood_get_land_params", "flood_drained_volume", "flood_flow_sample", "flood_set_inflow",
             "flood_inflow_volume", "flood_batch_autotune", "flood_batch_set_wait_budget",
-            "flood_adjoint_land_grad"]
+            "flood_adjoint_land_grad", "flood_batch_init_members", "flood_batch_get_member_state"]
 
 
 class LandClass(C.Structure):
@@ -154,6 +154,8 @@ def lib(path: str = LIB_PATH):
     L.flood_get_max_depth.argtypes = [_VP, C.c_int, _VP, _VP]
     L.flood_ensemble_products.argtypes = [_VP, C.c_double, C.c_int, _VP, _VP, _VP, _VP]
     L.flood_batch_get_state.argtypes = [_VP, C.c_int, _VP, _VP, _VP, _VP]
+    L.flood_batch_get_member_state.argtypes = [_VP, C.c_int, C.c_int, _VP, _VP, _VP, _VP]
+    L.flood_batch_init_members.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]
     L.flood_batch_members.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _VP]
     L.flood_batch_launch_count.argtypes = [_VP]
     L.flood_batch_launch_count.restype = C.c_int64
@@ -483,15 +485,20 @@ class Grid:
                                          stream_handle(stream)), self.h)
         return out
 
-    def ensemble_products(self, threshold=0.2, levels=(0.1, 0.5, 0.9), stream=None):
+    def ensemble_products(self, threshold=0.2, levels=(0.1, 0.5, 0.9), stream=None, out=None):
         """Exceedance probability of the maximum depth and its percentile
-        maps (flood_ensemble_products); host arrays."""
+        maps (flood_ensemble_products); host arrays, or the caller's buffers
+        out = (exceed [ny][nx], pct [n_levels][ny][nx]), FP32 numpy arrays or
+        torch tensors (device tensors keep the maps on the device)."""
         lv = np.ascontiguousarray(levels, dtype=np.float64)
-        exceed = np.zeros((self.ny, self.nx), np.float32)
-        pct = np.zeros((len(lv), self.ny, self.nx), np.float32)
+        if out is None:
+            exceed = np.zeros((self.ny, self.nx), np.float32)
+            pct = np.zeros((len(lv), self.ny, self.nx), np.float32)
+        else:
+            exceed, pct = out
         _check(lib().flood_ensemble_products(self.h, float(threshold), len(lv),
-                                             lv.ctypes.data if len(lv) else None, exceed.ctypes.data,
-                                             pct.ctypes.data if len(lv) else None,
+                                             lv.ctypes.data if len(lv) else None, ptr(exceed),
+                                             ptr(pct) if len(lv) else None,
                                              stream_handle(stream)), self.h)
         return exceed, pct
 
@@ -545,7 +552,8 @@ def _bcheck(rc, handle=None):
 
 class Batch:
     """Uneven batch of independent scenarios (flood_batch_*): each with its
-    own grid, bed, roughness, storm, Manning scale and duration."""
+    own grid, bed, roughness, storm and duration, and one or more members
+    (each with its own rain multiplier, Manning scale, state and clock)."""
 
     def __init__(self, zs, ns, params: Params | None = None):
         L = lib()
@@ -580,15 +588,29 @@ class Batch:
     def __exit__(self, *a):
         self.close()
 
-    def init(self, hyetographs, rain_mult, scale, t_end, stream=None):
+    def init(self, hyetographs, rain_mult, scale, t_end, stream=None, members=None):
+        """Start every scenario dry at t = 0.  members: per-scenario member
+        counts (None: one each); rain_mult and scale then hold one value per
+        member, scenario by scenario (flood_batch_init_members)."""
         self._hy = [np.ascontiguousarray(h, np.float32) for h in hyetographs]
         hp = (C.c_void_p * self.S)(*[h.ctypes.data for h in self._hy])
         nb = np.array([len(h) for h in self._hy], np.int32)
         rm = np.ascontiguousarray(rain_mult, np.float32)
         sc = np.ascontiguousarray(scale, np.float32)
         te = np.ascontiguousarray(t_end, np.float64)
-        _bcheck(lib().flood_batch_init(self.h, hp, nb.ctypes.data, rm.ctypes.data, sc.ctypes.data,
-                                       te.ctypes.data, stream_handle(stream)), self.h)
+        if members is None:
+            _bcheck(lib().flood_batch_init(self.h, hp, nb.ctypes.data, rm.ctypes.data,
+                                           sc.ctypes.data, te.ctypes.data, stream_handle(stream)),
+                    self.h)
+            self.members_per = np.ones(self.S, np.int32)
+        else:
+            mc = np.ascontiguousarray(members, np.int32)
+            if rm.size != mc.sum() or sc.size != mc.sum():
+                raise ValueError("rain_mult and scale need one value per member")
+            _bcheck(lib().flood_batch_init_members(self.h, hp, nb.ctypes.data, mc.ctypes.data,
+                                                   rm.ctypes.data, sc.ctypes.data, te.ctypes.data,
+                                                   stream_handle(stream)), self.h)
+            self.members_per = mc.copy()
 
     def step(self, t_stop, stream=None):
         _bcheck(lib().flood_batch_step(self.h, float(t_stop), stream_handle(stream)), self.h)
@@ -617,15 +639,19 @@ class Batch:
         results)."""
         _bcheck(lib().flood_batch_set_engine(self.h, int(engine)), self.h)
 
-    def get_state(self, i, stream=None):
+    def get_state(self, i, stream=None, member=0):
+        """State of member `member` of scenario i (h, qx, qy host arrays)."""
         ny, nx = self.shapes[i]
         h = np.zeros((ny, nx), np.float32); qx = np.zeros_like(h); qy = np.zeros_like(h)
-        _bcheck(lib().flood_batch_get_state(self.h, int(i), h.ctypes.data, qx.ctypes.data,
-                                            qy.ctypes.data, stream_handle(stream)), self.h)
+        _bcheck(lib().flood_batch_get_member_state(self.h, int(i), int(member), h.ctypes.data,
+                                                   qx.ctypes.data, qy.ctypes.data,
+                                                   stream_handle(stream)), self.h)
         return h, qx, qy
 
     def members(self):
-        S = self.S
+        """Per-member clocks and volumes, scenario by scenario (per scenario
+        with one member each)."""
+        S = int(np.sum(getattr(self, "members_per", np.ones(self.S))))
         out = dict(t=np.zeros(S), steps=np.zeros(S, np.int64), storage=np.zeros(S),
                    rain=np.zeros(S), outflow=np.zeros(S), clamp=np.zeros(S))
         _bcheck(lib().flood_batch_members(self.h, *(out[k].ctypes.data for k in

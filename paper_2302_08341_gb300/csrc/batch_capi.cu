@@ -24,11 +24,21 @@ thread_local std::string g_batch_msg;
 
 }  // namespace
 
+// A batch holds n_scen scenarios (grid, bed, roughness, storm, end time) and
+// S entries: the members of every scenario, scenario by scenario, each with
+// its own state, clock, rain multiplier and Manning scale.  Everything the
+// step kernels index (descriptors, clocks, plans, tensor maps, tasks) is per
+// entry; the members of a scenario share its bed, roughness and storm.
 struct flood_batch {
-    int S = 0;
+    int S = 0;                        // entries (members of all scenarios)
+    int n_scen = 0;
     flood_params p{};
-    std::vector<int> ny, nx, ld;
-    std::vector<float*> zn, state, hyeto;
+    std::vector<int> ny, nx, ld;      // per entry (the scenario's)
+    std::vector<int> sny, snx, sld;   // per scenario
+    std::vector<int> scen_of;         // [S] the scenario of each entry
+    std::vector<int> first;           // [n_scen + 1] first entry of each scenario
+    std::vector<float*> zn, hyeto;    // per scenario
+    std::vector<float*> state;        // per entry: [2][3][plane]
     std::vector<flood::ScenDesc> desc;
     flood::ScenDesc* d_desc = nullptr;
     std::vector<flood::WarpTask> tasks;
@@ -51,7 +61,8 @@ struct flood_batch {
     int64_t* pdone = nullptr;         // steps the last persistent launch advanced the clocks by
     int* pdiag = nullptr;             // [8] where a persistent launch's first wait gave up
     long long wait_budget = -1;       // grid-barrier wait limit in clock cycles (< 0: default)
-    CUtensorMap* d_maps = nullptr;    // [S][2] tensor maps of each scenario
+    CUtensorMap* d_maps = nullptr;    // [S][2] tensor maps of each entry
+    bool tma_ok = false;              // the tensor-map encoder is available
     bool initialised = false;
     int64_t k = 0, launches = 0;
     cudaGraphExec_t graph = nullptr;
@@ -84,26 +95,38 @@ void drop_graph(flood_batch* b)
 }
 
 // Task table: for each scenario, strips of rows_per_strip rows x 128-column
-// spans, in row-major order so neighbouring warps share halo rows in L2.
+// spans in row-major order (neighbouring warps share halo rows in L2), and
+// for each tile the scenario's members one after another, so that the warps
+// taking one tile for different members are neighbours and the tile's bed
+// and roughness come from DRAM once for all of them (Section 3.2's shared
+// definitive data, as in the ensemble kernel).
 int build_tasks(flood_batch* b)
 {
     b->tasks.clear();
     b->slot0.assign(b->S, 0);
+    std::vector<std::vector<int>> slots(b->S);
+    for (int sc = 0; sc < b->n_scen; ++sc) {
+        const int e0 = b->first[sc], e1 = b->first[sc + 1];
+        const int spans = (b->nx[e0] + kSpan - 1) / kSpan;
+        for (int r0 = 0; r0 < b->ny[e0]; r0 += b->rows_per_strip)
+            for (int sp = 0; sp < spans; ++sp)
+                for (int e = e0; e < e1; ++e) {
+                    flood::WarpTask t;
+                    t.scen = e;
+                    t.c0 = sp * kSpan;
+                    t.r0 = r0;
+                    t.r1 = std::min(r0 + b->rows_per_strip, b->ny[e]);
+                    t.slot = 0;
+                    t.first = (r0 == 0 && sp == 0) ? 1 : 0;
+                    slots[e].push_back((int)b->tasks.size());
+                    b->tasks.push_back(t);
+                }
+    }
+    // volume slots: each entry's tasks own consecutive slots
     int slot = 0;
-    for (int i = 0; i < b->S; ++i) {
-        b->slot0[i] = slot;
-        const int spans = (b->nx[i] + kSpan - 1) / kSpan;
-        for (int r0 = 0; r0 < b->ny[i]; r0 += b->rows_per_strip)
-            for (int sp = 0; sp < spans; ++sp) {
-                flood::WarpTask t;
-                t.scen = i;
-                t.c0 = sp * kSpan;
-                t.r0 = r0;
-                t.r1 = std::min(r0 + b->rows_per_strip, b->ny[i]);
-                t.slot = slot++;
-                t.first = (r0 == 0 && sp == 0) ? 1 : 0;
-                b->tasks.push_back(t);
-            }
+    for (int e = 0; e < b->S; ++e) {
+        b->slot0[e] = slot;
+        for (int ti : slots[e]) b->tasks[ti].slot = slot++;
     }
     if (b->d_tasks) cudaFree(b->d_tasks);
     b->d_tasks = nullptr;
@@ -186,6 +209,84 @@ int read_batch_clocks(flood_batch* b, std::vector<MemberClock>& c, cudaStream_t 
     return FLOOD_OK;
 }
 
+// (Re)build the entries for counts[sc] members of every scenario: each
+// entry's state (zeroed), descriptor, tensor maps, clocks, plans and sums,
+// and the task table.  Frees the previous entries' buffers.
+int set_entries(flood_batch* b, const std::vector<int>& counts)
+{
+    for (float* p : b->state)
+        if (p) cudaFree(p);
+    b->state.clear();
+    void* old[] = {b->d_desc, b->ms, b->rain_acc, b->storage, b->plan, b->d_maps};
+    for (void* p : old)
+        if (p) cudaFree(p);
+    b->d_desc = nullptr; b->ms = nullptr; b->rain_acc = nullptr; b->storage = nullptr;
+    b->plan = nullptr; b->d_maps = nullptr;
+    drop_graph(b);
+    int S = 0;
+    b->first.assign(b->n_scen + 1, 0);
+    for (int sc = 0; sc < b->n_scen; ++sc) {
+        b->first[sc] = S;
+        S += counts[sc];
+    }
+    b->first[b->n_scen] = S;
+    b->S = S;
+    b->scen_of.assign(S, 0);
+    b->ny.assign(S, 0); b->nx.assign(S, 0); b->ld.assign(S, 0);
+    b->state.assign(S, nullptr);
+    b->desc.assign(S, flood::ScenDesc{});
+    for (int sc = 0; sc < b->n_scen; ++sc)
+        for (int e = b->first[sc]; e < b->first[sc + 1]; ++e) {
+            b->scen_of[e] = sc;
+            b->ny[e] = b->sny[sc]; b->nx[e] = b->snx[sc]; b->ld[e] = b->sld[sc];
+            const size_t plane = (size_t)b->sny[sc] * b->sld[sc];
+            BCK(b, cudaMalloc(&b->state[e], sizeof(float) * 6 * plane));
+            BCK(b, cudaMemset(b->state[e], 0, sizeof(float) * 6 * plane));
+            flood::ScenDesc& d = b->desc[e];
+            d.state = b->state[e];
+            d.z = b->zn[sc];
+            d.n = b->zn[sc] + plane;
+            d.hyeto = b->hyeto[sc];
+            d.plane = plane;
+            d.ny = b->sny[sc];
+            d.nx = b->snx[sc];
+            d.ld = b->sld[sc];
+            d.nb = 0;
+            d.rain_mult = 1.0f;
+            d.scale = 1.0f;
+            d.t_end = 0.0;
+            d.ncell = (double)b->sny[sc] * b->snx[sc];
+        }
+    BCK(b, cudaMalloc(&b->ms, sizeof(MemberClock) * 3 * S));
+    BCK(b, cudaMemset(b->ms, 0, sizeof(MemberClock) * 3 * S));
+    BCK(b, cudaMalloc(&b->rain_acc, sizeof(double) * S));
+    BCK(b, cudaMemset(b->rain_acc, 0, sizeof(double) * S));
+    BCK(b, cudaMalloc(&b->storage, sizeof(double) * S));
+    BCK(b, cudaMalloc(&b->plan, sizeof(flood::MemberPlan) * S));
+    BCK(b, cudaMalloc(&b->d_desc, sizeof(flood::ScenDesc) * S));
+    BCK(b, cudaMemcpy(b->d_desc, b->desc.data(), sizeof(flood::ScenDesc) * S, cudaMemcpyHostToDevice));
+    // tensor maps of every entry for the TMA-staged step (direct loads if the
+    // encoder is unavailable): its own state, its scenario's bed and roughness
+    std::vector<CUtensorMap> maps((size_t)2 * S);
+    bool ok = b->tma_ok;
+    for (int e = 0; ok && e < S; ++e) {
+        const int sc = b->scen_of[e];
+        const uint64_t s1 = sizeof(float) * b->ld[e], s2 = sizeof(float) * b->desc[e].plane;
+        ok = flood::encode_map_3d(&maps[2 * e], b->state[e], b->ld[e], b->ny[e], 6, s1, s2,
+                                  flood::tma_box_cols(), 1, 3) == 0 &&
+             flood::encode_map_3d(&maps[2 * e + 1], b->zn[sc], b->ld[e], b->ny[e], 2, s1, s2,
+                                  flood::tma_box_cols(), 1, 2) == 0;
+    }
+    if (ok) {
+        BCK(b, cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * maps.size()));
+        BCK(b, cudaMemcpy(b->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                          cudaMemcpyHostToDevice));
+    } else if (b->engine != 0) {
+        b->engine = 0;
+    }
+    return build_tasks(b);
+}
+
 }  // namespace
 
 extern "C" {
@@ -209,59 +310,37 @@ int flood_batch_create(flood_batch** out, int n, const int32_t* ny, const int32_
         if (ny[i] < 1 || nx[i] < 1 || !z[i] || !n_base[i])
             return bfail(nullptr, FLOOD_ERR_ARG, "scenario with an empty grid or missing field");
     flood_batch* b = new flood_batch();
-    b->S = n;
+    b->n_scen = n;
     b->p = *p;
-    b->ny.assign(ny, ny + n);
-    b->nx.assign(nx, nx + n);
-    b->ld.resize(n);
+    b->sny.assign(ny, ny + n);
+    b->snx.assign(nx, nx + n);
+    b->sld.resize(n);
     b->zn.assign(n, nullptr);
-    b->state.assign(n, nullptr);
     b->hyeto.assign(n, nullptr);
-    b->desc.resize(n);
     auto bad = [&](cudaError_t e) {
         g_batch_msg = std::string("flood_batch_create: ") + cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? FLOOD_ERR_OOM : FLOOD_ERR_CUDA;
     };
     for (int i = 0; i < n; ++i) {
-        b->ld[i] = (nx[i] + 31) / 32 * 32;
-        const size_t plane = (size_t)ny[i] * b->ld[i];
+        b->sld[i] = (nx[i] + 31) / 32 * 32;
+        const size_t plane = (size_t)ny[i] * b->sld[i];
         cudaError_t e = cudaMalloc(&b->zn[i], sizeof(float) * 2 * plane);
-        if (e == cudaSuccess) e = cudaMalloc(&b->state[i], sizeof(float) * 6 * plane);
         if (e == cudaSuccess) e = cudaMemset(b->zn[i], 0, sizeof(float) * 2 * plane);
         if (e == cudaSuccess)
-            e = cudaMemcpy2D(b->zn[i], sizeof(float) * b->ld[i], z[i], sizeof(float) * nx[i],
+            e = cudaMemcpy2D(b->zn[i], sizeof(float) * b->sld[i], z[i], sizeof(float) * nx[i],
                              sizeof(float) * nx[i], ny[i], cudaMemcpyDefault);
         if (e == cudaSuccess)
-            e = cudaMemcpy2D(b->zn[i] + plane, sizeof(float) * b->ld[i], n_base[i], sizeof(float) * nx[i],
+            e = cudaMemcpy2D(b->zn[i] + plane, sizeof(float) * b->sld[i], n_base[i], sizeof(float) * nx[i],
                              sizeof(float) * nx[i], ny[i], cudaMemcpyDefault);
         if (e != cudaSuccess) {
             int rc = bad(e);
             flood_batch_destroy(b);
             return rc;
         }
-        flood::ScenDesc& d = b->desc[i];
-        d.state = b->state[i];
-        d.z = b->zn[i];
-        d.n = b->zn[i] + plane;
-        d.hyeto = nullptr;
-        d.plane = plane;
-        d.ny = ny[i];
-        d.nx = nx[i];
-        d.ld = b->ld[i];
-        d.nb = 0;
-        d.rain_mult = 1.0f;
-        d.scale = 1.0f;
-        d.t_end = 0.0;
-        d.ncell = (double)ny[i] * nx[i];
     }
-    cudaError_t e = cudaMalloc(&b->ms, sizeof(MemberClock) * 3 * n);
-    if (e == cudaSuccess) e = cudaMalloc(&b->rain_acc, sizeof(double) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&b->storage, sizeof(double) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&b->err, sizeof(int));
+    cudaError_t e = cudaMalloc(&b->err, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&b->t_stop, sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&b->plan, sizeof(flood::MemberPlan) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_desc, sizeof(flood::ScenDesc) * n);
-    int maxny = *std::max_element(b->ny.begin(), b->ny.end());
+    int maxny = *std::max_element(b->sny.begin(), b->sny.end());
     b->part_cap = (maxny + 15) / 16;
     if (e == cudaSuccess) e = cudaMalloc(&b->part, sizeof(double) * b->part_cap);
     if (e != cudaSuccess) {
@@ -269,32 +348,9 @@ int flood_batch_create(flood_batch** out, int n, const int32_t* ny, const int32_
         flood_batch_destroy(b);
         return rc;
     }
-    // tensor maps of every scenario for the TMA-staged step (direct loads if
-    // the encoder is unavailable)
-    {
-        std::vector<CUtensorMap> maps((size_t)2 * n);
-        bool ok = flood::batch_tma_prepare() == 0;
-        for (int i = 0; ok && i < n; ++i) {
-            const uint64_t s1 = sizeof(float) * b->ld[i], s2 = sizeof(float) * b->desc[i].plane;
-            ok = flood::encode_map_3d(&maps[2 * i], b->state[i], b->ld[i], b->ny[i], 6, s1, s2,
-                                      flood::tma_box_cols(), 1, 3) == 0 &&
-                 flood::encode_map_3d(&maps[2 * i + 1], b->zn[i], b->ld[i], b->ny[i], 2, s1, s2,
-                                      flood::tma_box_cols(), 1, 2) == 0;
-        }
-        if (ok) {
-            e = cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * maps.size());
-            if (e == cudaSuccess)
-                e = cudaMemcpy(b->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(),
-                               cudaMemcpyHostToDevice);
-            if (e != cudaSuccess) {
-                int rc = bad(e);
-                flood_batch_destroy(b);
-                return rc;
-            }
-            b->engine = 1;
-        }
-    }
-    int rc = build_tasks(b);
+    b->tma_ok = flood::batch_tma_prepare() == 0;
+    b->engine = b->tma_ok ? 1 : 0;
+    int rc = set_entries(b, std::vector<int>(n, 1));  // one member per scenario until init
     if (rc) {
         g_batch_msg = b->msg;
         flood_batch_destroy(b);
@@ -320,30 +376,50 @@ int flood_batch_destroy(flood_batch* b)
     return FLOOD_OK;
 }
 
-int flood_batch_init(flood_batch* b, const float* const* hyetographs, const int32_t* n_blocks,
-                     const float* rain_mult, const float* manning_scale, const double* t_end,
-                     void* stream)
+int flood_batch_init_members(flood_batch* b, const float* const* hyetographs,
+                             const int32_t* n_blocks, const int32_t* n_members,
+                             const float* rain_mult, const float* manning_scale,
+                             const double* t_end, void* stream)
 {
     if (!b) return bfail(nullptr, FLOOD_ERR_ARG, "batch is NULL");
-    if (!hyetographs || !n_blocks || !rain_mult || !manning_scale || !t_end)
+    if (!hyetographs || !n_blocks || !n_members || !rain_mult || !manning_scale || !t_end)
         return bfail(b, FLOOD_ERR_ARG, "every array is required");
     cudaStream_t s = S_(stream);
     BCK(b, cudaStreamSynchronize(s));
-    for (int i = 0; i < b->S; ++i) {
+    std::vector<int> counts(b->n_scen);
+    int64_t total = 0;
+    for (int i = 0; i < b->n_scen; ++i) {
+        if (n_members[i] < 1 || n_members[i] > 4096)
+            return bfail(b, FLOOD_ERR_ARG, "every scenario needs 1..4096 members");
         if (n_blocks[i] < 0 || (n_blocks[i] > 0 && !hyetographs[i]) || !(t_end[i] >= 0.0))
             return bfail(b, FLOOD_ERR_ARG, "bad hyetograph or end time");
+        counts[i] = n_members[i];
+        total += n_members[i];
+    }
+    if (total > (1 << 20)) return bfail(b, FLOOD_ERR_ARG, "more than 2^20 members in all");
+    bool same = (int)total == b->S;
+    for (int i = 0; same && i < b->n_scen; ++i) same = b->first[i + 1] - b->first[i] == counts[i];
+    int rc;
+    if (!same && (rc = set_entries(b, counts))) return rc;
+    for (int i = 0; i < b->n_scen; ++i) {
         if (b->hyeto[i]) cudaFree(b->hyeto[i]);
         b->hyeto[i] = nullptr;
         BCK(b, cudaMalloc(&b->hyeto[i], sizeof(float) * std::max(1, n_blocks[i])));
         if (n_blocks[i] > 0)
             BCK(b, cudaMemcpy(b->hyeto[i], hyetographs[i], sizeof(float) * n_blocks[i], cudaMemcpyDefault));
-        flood::ScenDesc& d = b->desc[i];
+    }
+    std::vector<float> rm(b->S), sc(b->S);
+    BCK(b, cudaMemcpy(rm.data(), rain_mult, sizeof(float) * b->S, cudaMemcpyDefault));
+    BCK(b, cudaMemcpy(sc.data(), manning_scale, sizeof(float) * b->S, cudaMemcpyDefault));
+    for (int e = 0; e < b->S; ++e) {
+        const int i = b->scen_of[e];
+        flood::ScenDesc& d = b->desc[e];
         d.hyeto = b->hyeto[i];
         d.nb = n_blocks[i];
-        d.rain_mult = rain_mult[i];
-        d.scale = manning_scale[i];
+        d.rain_mult = rm[e];
+        d.scale = sc[e];
         d.t_end = t_end[i];
-        BCK(b, cudaMemsetAsync(b->state[i], 0, sizeof(float) * 6 * d.plane, s));
+        BCK(b, cudaMemsetAsync(b->state[e], 0, sizeof(float) * 6 * d.plane, s));
     }
     BCK(b, cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(flood::ScenDesc) * b->S,
                            cudaMemcpyHostToDevice, s));
@@ -357,6 +433,16 @@ int flood_batch_init(flood_batch* b, const float* const* hyetographs, const int3
     b->k = 0;
     b->initialised = true;
     return FLOOD_OK;
+}
+
+int flood_batch_init(flood_batch* b, const float* const* hyetographs, const int32_t* n_blocks,
+                     const float* rain_mult, const float* manning_scale, const double* t_end,
+                     void* stream)
+{
+    if (!b) return bfail(nullptr, FLOOD_ERR_ARG, "batch is NULL");
+    const std::vector<int32_t> ones(b->n_scen, 1);
+    return flood_batch_init_members(b, hyetographs, n_blocks, ones.data(), rain_mult, manning_scale,
+                                    t_end, stream);
 }
 
 int flood_batch_set_engine(flood_batch* b, int engine)
@@ -494,10 +580,14 @@ int flood_batch_step(flood_batch* b, double t_stop, void* stream)
     return FLOOD_OK;
 }
 
-int flood_batch_get_state(flood_batch* b, int i, float* h, float* qx, float* qy, void* stream)
+int flood_batch_get_member_state(flood_batch* b, int scen, int member, float* h, float* qx,
+                                 float* qy, void* stream)
 {
     if (!b) return bfail(nullptr, FLOOD_ERR_ARG, "batch is NULL");
-    if (i < 0 || i >= b->S) return bfail(b, FLOOD_ERR_ARG, "scenario out of range");
+    if (scen < 0 || scen >= b->n_scen) return bfail(b, FLOOD_ERR_ARG, "scenario out of range");
+    if (member < 0 || member >= b->first[scen + 1] - b->first[scen])
+        return bfail(b, FLOOD_ERR_ARG, "member out of range");
+    const int i = b->first[scen] + member;
     cudaStream_t s = S_(stream);
     MemberClock c;
     BCK(b, cudaMemcpyAsync(&c, b->ms + (b->k % 3) * b->S + i, sizeof(c), cudaMemcpyDeviceToHost, s));
@@ -512,6 +602,11 @@ int flood_batch_get_state(flood_batch* b, int i, float* h, float* qx, float* qy,
                                      cudaMemcpyDefault, s));
     BCK(b, cudaStreamSynchronize(s));
     return FLOOD_OK;
+}
+
+int flood_batch_get_state(flood_batch* b, int i, float* h, float* qx, float* qy, void* stream)
+{
+    return flood_batch_get_member_state(b, i, 0, h, qx, qy, stream);
 }
 
 int flood_batch_members(flood_batch* b, double* t, int64_t* steps, double* storage, double* rain,

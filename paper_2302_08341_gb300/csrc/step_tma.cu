@@ -24,7 +24,12 @@ __global__ void __launch_bounds__(32 * WM, (LC || TRACK_MAX ? 16 : 20) / WM) ste
     const int lane = threadIdx.x;
     const int w = threadIdx.y;
     const int m = blockIdx.x * WM + w;
-    const int span = blockIdx.y;
+    int span = blockIdx.y, strip = blockIdx.z;
+    if (a.tiles) {  // only the tiles that hold a cell of the domain are launched
+        const int2 tl = a.tiles[blockIdx.y];
+        span = tl.x;
+        strip = tl.y;
+    }
     const int c0 = span * kSpan;
     if (m >= a.M || c0 >= a.nx) return;  // whole warps; no block-wide barriers below
     if (*reinterpret_cast<volatile const int*>(a.err) & 2) return;  // an earlier wait gave up
@@ -51,7 +56,7 @@ __global__ void __launch_bounds__(32 * WM, (LC || TRACK_MAX ? 16 : 20) / WM) ste
     k.in_r0 = a.in_r0;
     k.in_r1 = a.in_r1;
 
-    const int r0 = blockIdx.z * a.rows_per_strip;
+    const int r0 = strip * a.rows_per_strip;
     const int r1 = min(r0 + a.rows_per_strip, a.ny);
     MarchOut mo;
     float* hm = TRACK_MAX ? a.hmax_field + (size_t)m * a.plane : nullptr;
@@ -75,7 +80,7 @@ __global__ void __launch_bounds__(32 * WM, (LC || TRACK_MAX ? 16 : 20) / WM) ste
     }
     if (lane == 0) {
         atomicMax(&a.ms_out[m].hmax_bits, hb);
-        const int slot = blockIdx.z * ((a.nx + kSpan - 1) / kSpan) + span;
+        const int slot = strip * ((a.nx + kSpan - 1) / kSpan) + span;
         if (out_acc != 0.0 || clamp_acc != 0.0) {
             double* v = a.vacc + ((size_t)m * a.nslot + slot) * 2;
             v[0] += out_acc * pl.dt * a.dxd;
@@ -192,27 +197,37 @@ int tma_box_cols() { return kTmaBox; }
 
 namespace {
 
+template <int WM, bool TRACK_MAX, bool LC, int LIM, bool CK, bool HOOK>
+void launch_tma_wm(const TmaArgs& t, int spans, int strips, cudaStream_t s)
+{
+    static bool attr = false;
+    const size_t shm = tma_smem_bytes<WM, TRACK_MAX, LC>();
+    if (!attr) {
+        cudaFuncSetAttribute(step_tma_kernel<WM, TRACK_MAX, LC, LIM, CK, HOOK>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        attr = true;
+    }
+    dim3 grid((t.a.M + WM - 1) / WM, spans, strips), block(32, WM);
+    step_tma_kernel<WM, TRACK_MAX, LC, LIM, CK, HOOK><<<grid, block, shm, s>>>(t);
+}
+
+// Members per CTA: 4 or 1 for every variant; the plain step also has 2 and 8
+// (the members-per-CTA sweep of the tuner and the benchmark).
 template <bool TRACK_MAX, bool LC, int LIM, bool CK, bool HOOK = false>
 void launch_tma(const TmaArgs& t, int members_per_cta, cudaStream_t s)
 {
     const StepArgs& a = t.a;
-    const int spans = (a.nx + kSpan - 1) / kSpan;
-    const int strips = (a.ny + a.rows_per_strip - 1) / a.rows_per_strip;
-    if (members_per_cta >= 4) {
-        static bool attr = false;
-        const size_t shm = tma_smem_bytes<4, TRACK_MAX, LC>();
-        if (!attr) {
-            cudaFuncSetAttribute(step_tma_kernel<4, TRACK_MAX, LC, LIM, CK, HOOK>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-            attr = true;
-        }
-        dim3 grid((a.M + 3) / 4, spans, strips), block(32, 4);
-        step_tma_kernel<4, TRACK_MAX, LC, LIM, CK, HOOK><<<grid, block, shm, s>>>(t);
-    } else {
-        const size_t shm = tma_smem_bytes<1, TRACK_MAX, LC>();
-        dim3 grid(a.M, spans, strips), block(32, 1);
-        step_tma_kernel<1, TRACK_MAX, LC, LIM, CK, HOOK><<<grid, block, shm, s>>>(t);
-    }
+    const int spans = a.tiles ? a.n_tiles : (a.nx + kSpan - 1) / kSpan;
+    const int strips = a.tiles ? 1 : (a.ny + a.rows_per_strip - 1) / a.rows_per_strip;
+    constexpr bool kPlain = !TRACK_MAX && !LC && !CK && !HOOK;
+    if (kPlain && members_per_cta == 8)
+        launch_tma_wm<kPlain ? 8 : 4, TRACK_MAX, LC, LIM, CK, HOOK>(t, spans, strips, s);
+    else if (members_per_cta >= 4)
+        launch_tma_wm<4, TRACK_MAX, LC, LIM, CK, HOOK>(t, spans, strips, s);
+    else if (kPlain && members_per_cta == 2)
+        launch_tma_wm<kPlain ? 2 : 1, TRACK_MAX, LC, LIM, CK, HOOK>(t, spans, strips, s);
+    else
+        launch_tma_wm<1, TRACK_MAX, LC, LIM, CK, HOOK>(t, spans, strips, s);
 }
 
 template <int LIM, bool LC>

@@ -167,3 +167,95 @@ def test_batch_rejects_bad_arguments(capi):
             b.step(10.0)        # before init
         with pytest.raises(capi.FloodError):
             b.set_launch(0, 4)
+
+
+def test_full_size_uneven_batch_to_the_end_follows_the_oracle(capi):
+    """The uneven batch at its real size: 64 square scenarios of 512^2 to
+    2048^2 cells (108 M in all), rain 20-100 mm/h, 900-3600 s, advanced in
+    300 s windows by the persistent launch with the tuner's 32-row strips
+    until every scenario has ended.  The smallest scenario (520^2, 1733 s)
+    and a mid-size one (1085^2, 1094 s) against the FP64 oracle over their
+    whole duration: depth 1e-3 m, storage 1e-5 relative, the same number
+    of steps; every scenario's own balance to 1e-5 of its rain."""
+    import concurrent.futures as cf
+    scen = synth.uneven_batch(64)
+    terrs = [synth.make_terrain(s.ny, s.nx, seed=s.seed) for s in scen]
+    hys = [synth.hyetograph_constant(s.rain_mm_h, s.duration_s) for s in scen]
+    dur = np.array([s.duration_s for s in scen])
+    ones = np.ones(len(scen), np.float32)
+    picks = (27, 20)
+    assert (scen[27].ny, scen[20].ny) == (520, 1085)
+    with capi.Batch([t.z for t in terrs], [t.n for t in terrs]) as b:
+        b.set_engine(2)
+        b.set_launch(32, 4)
+        b.init(hys, ones, ones, dur)
+        for w in range(1, 13):
+            b.step(300.0 * w)
+        mem = b.members()
+        states = {i: b.get_state(i)[0] for i in picks}
+    assert np.array_equal(mem["t"], dur)
+    bal = mem["storage"] - (mem["rain"] - mem["outflow"] + mem["clamp"])
+    assert np.all(np.abs(bal) <= 1e-5 * mem["rain"])
+    p = capi.Params.default()
+
+    def run(i):
+        ny, nx = terrs[i].z.shape
+        mo = oracle.Member.dry(ny, nx)
+        oracle.advance(oracle_params(p, ny, nx), terrs[i].z, terrs[i].n, 1.0, 1.0, hys[i], mo,
+                       t_end=float(dur[i]))
+        return mo
+
+    with cf.ThreadPoolExecutor(max_workers=len(picks)) as ex:   # the oracle releases the GIL
+        ref = dict(zip(picks, ex.map(run, picks)))
+    for i in picks:
+        err = compare(states[i], ref[i].h, 1e-3)
+        V = oracle.storage(ref[i].h, p.dx)
+        assert abs(mem["storage"][i] - V) <= 1e-5 * V
+        assert mem["steps"][i] == ref[i].steps
+        print(f"batch scenario {i} ({scen[i].ny}^2, {dur[i]:.0f} s): max |dh| {err:.2e} m, "
+              f"storage rel err {abs(mem['storage'][i] - V) / V:.2e}, {ref[i].steps} steps")
+
+
+@pytest.mark.parametrize("engine", [0, 1, 2])
+def test_batch_with_several_members_per_scenario(capi, engine):
+    """Scenarios with 1-4 members each (an ensemble per scenario, every
+    member with its own rain multiplier, Manning scale, state, clock and
+    step length): every member equals, bit for bit, the same member of a
+    single-grid ensemble of its scenario; the batch's per-member volumes
+    close their balance; one member follows the FP64 oracle."""
+    terrs, hys, rm1, sc1, dur = _scenarios()
+    counts = np.array([1, 4, 2, 3, 4], np.int32)
+    rng = np.random.default_rng(78)
+    rm = rng.uniform(0.7, 1.6, counts.sum()).astype(np.float32)
+    sc = rng.uniform(0.7, 1.3, counts.sum()).astype(np.float32)
+    first = np.concatenate([[0], np.cumsum(counts)])
+    with capi.Batch([t.z for t in terrs], [t.n for t in terrs]) as b:
+        b.set_engine(engine)
+        b.init(hys, rm, sc, dur, members=counts)
+        for w in (300.0, 600.0):
+            b.step(w)
+        got = {(i, m): b.get_state(i, member=m) for i in range(len(SHAPES)) for m in range(counts[i])}
+        mem = b.members()
+    assert mem["t"].shape == (counts.sum(),)
+    assert np.array_equal(mem["t"], np.repeat(dur, counts))
+    bal = mem["storage"] - (mem["rain"] - mem["outflow"] + mem["clamp"])
+    assert np.all(np.abs(bal) <= 1e-5 * mem["rain"])
+    p = capi.Params.default()
+    for i, t in enumerate(terrs):
+        sl = slice(first[i], first[i + 1])
+        with capi.Grid(t.z, t.n, p) as g:
+            g.ensemble_init(int(counts[i]), rm[sl], sc[sl], hys[i])
+            g.advance_to(float(dur[i]))
+            steps = g.members()["steps"]
+            for m in range(counts[i]):
+                alone = g.get_state(m)
+                for k in range(3):
+                    assert np.array_equal(got[(i, m)][k], alone[k]), (i, m, k)
+        assert np.array_equal(mem["steps"][sl], steps)
+    # one member of the four-member scenario against the oracle
+    i, m = 1, 2
+    ny, nx = terrs[i].z.shape
+    mo = oracle.Member.dry(ny, nx)
+    oracle.advance(oracle_params(p, ny, nx), terrs[i].z, terrs[i].n, float(sc[first[i] + m]),
+                   float(rm[first[i] + m]), hys[i], mo, t_end=float(dur[i]))
+    compare(got[(i, m)][0], mo.h, 1e-3)
