@@ -66,7 +66,8 @@ def parse():
                     help="skip the adjoint and uneven-batch measurements")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch configuration (profiling runs)")
-    ap.add_argument("--only", choices=["adjoint", "batch", "calibration", "land_cover"],
+    ap.add_argument("--only", choices=["adjoint", "batch", "calibration", "land_cover",
+                                       "masked_domain", "products"],
                     help="run one extension measurement alone and print it (profiling runs)")
     ap.add_argument("--calibration-windows", type=int, default=3)
     ap.add_argument("--rows-per-strip", type=int, default=None,
@@ -77,6 +78,15 @@ def parse():
     global NY, NX, M, ROWS
     NY, NX, M, ROWS = args.ny, args.nx, args.members, args.rows_per_strip
     return args
+
+
+def guarded(fn, *a, **kw):
+    """Run one extension measurement; a failure is reported on the line
+    instead of ending the run."""
+    try:
+        return fn(*a, **kw)
+    except Exception as e:  # noqa: BLE001
+        return {"error": f"{type(e).__name__}: {e}"}
 
 
 def kernel_hash():
@@ -314,18 +324,27 @@ def adjoint_measure(capi):
             "adj_over_fwd": res["reverse_ms"] / res["forward_ms"]}
 
 
-def batch_measure(capi, engine=None, rows=None, tune=False):
+def batch_measure(capi, engine=None, rows=None, tune=False, members=1):
     """Uneven batch: 64 scenarios, square sides U{512..2048}, own DEM seeds,
     rain U[20, 100] mm/h, durations U[900, 3600] s, advanced in 300 s windows
-    by graph-replayed batched launches; member-cell-steps/s over the batch."""
+    by graph-replayed batched launches; member-cell-steps/s over the batch.
+    members > 1: that many members per scenario (rain multiplier LN(0, 0.3),
+    Manning scale U[0.6, 1.4] each), sharing the scenario's bed and
+    roughness tile by tile."""
     import torch
     from paper_2302_08341_gb300 import synth
     scen = synth.uneven_batch(64)
     terrs = [synth.make_terrain(s.ny, s.nx, seed=s.seed) for s in scen]
     hys = [synth.hyetograph_constant(s.rain_mm_h, s.duration_s) for s in scen]
     dur = np.array([s.duration_s for s in scen])
-    ones = np.ones(len(scen), np.float32)
-    cells = np.array([s.ny * s.nx for s in scen], np.float64)
+    counts = np.full(len(scen), members, np.int32)
+    if members > 1:
+        rm, sc = synth.ensemble_prior(SEED + 64, int(counts.sum()))
+    else:
+        rm = sc = np.ones(len(scen), np.float32)
+    mkw = {"members": counts} if members > 1 else {}
+    cells = np.repeat(np.array([s.ny * s.nx for s in scen], np.float64), counts)
+    dur_m = np.repeat(dur, counts)
     tuned = None
     with capi.Batch([t.z for t in terrs], [t.n for t in terrs]) as b:
         if engine is not None:
@@ -335,13 +354,13 @@ def batch_measure(capi, engine=None, rows=None, tune=False):
         rows = rows or ROWS
         if rows:
             b.set_launch(rows, 4)
-        b.init(hys, ones, ones, dur)
+        b.init(hys, rm, sc, dur, **mkw)
         b.step(300.0)                      # warm-up window (graph capture)
         if tune:                           # on the live batch after the first window
             r, w, e, t = b.autotune(30.0)
             tuned = {"rows_per_strip": r, "warps_per_cta": w, "engine": e, "trial_ms": t}
             engine, rows = e, r
-        b.init(hys, ones, ones, dur)
+        b.init(hys, rm, sc, dur, **mkw)
         stream = torch.cuda.current_stream()
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         l0 = b.launch_count
@@ -359,11 +378,14 @@ def batch_measure(capi, engine=None, rows=None, tune=False):
             1: "TMA-staged rows, CUDA-graph replayed per-step launches",
             2: "TMA-staged rows, one persistent cooperative launch per window"}[engine]
     return {"config": "64 scenarios, sides U{512..2048}, rain U[20,100] mm/h, durations "
-                      "U[900,3600] s, 300 s windows, batched step: " + form,
+                      f"U[900,3600] s, {members} member(s) each, 300 s windows, batched step: "
+                      + form,
             "value": units / (ms * 1e-3), "unit": "member-cell-steps/s", "ms": ms,
+            "members_per_scenario": members,
             "total_cells": float(cells.sum()), "member_cell_steps": units,
-            "all_finished": bool(np.all(mem["t"] == dur)), "gpu_launches": launches,
+            "all_finished": bool(np.all(mem["t"] == dur_m)), "gpu_launches": launches,
             "engine": {0: "direct loads", 1: "tma", 2: "tma persistent"}[engine],
+            "engine_id": engine,
             "rows_per_strip": rows or 64, "autotune": tuned}
 
 
@@ -482,6 +504,116 @@ def plain_vs_fused(g, tuned, stream, device, ncell, hbm_peak):
     return out
 
 
+def eta_sweeps(capi, g, tuned, stream, device, terr, hy, rm, sc):
+    """Section 4.4's eta-bar (Eq. 13: the run time of one member, the
+    ensemble's time divided by the members sharing the device) on this GPU,
+    two ways: members per CTA (the paper's thread-block z-dimension, whose
+    warps share one tile of the bed and roughness) on the live 96-member
+    ensemble, and members on the device (a fresh ensemble of n members from
+    a 5 cm wet start); 60 steps each, step-kernel time from CUDA events."""
+    import torch
+    rows = tuned["rows_per_strip"] if tuned else 0
+    eng = tuned["engine"] if tuned else 1
+    t = float(g.members()["t"].max())
+    per_cta = {}
+    g.set_engine(1)
+    for mpc in (1, 2, 4, 8):
+        g.set_launch(rows or 32, mpc)
+        g.profile(True)
+        t += 60.0
+        s0 = g.members()["steps"].sum()
+        g.advance_to(t, stream=stream)
+        kms, kn = g.profile(False)
+        steps = float(g.members()["steps"].sum() - s0)
+        per_cta[str(mpc)] = {"ms_per_step": kms / max(kn, 1),
+                             "eta_bar_us_per_member_step": kms / max(steps, 1) * 1e3}
+    g.set_engine(eng)
+    g.set_launch(*((tuned["rows_per_strip"], tuned["members_per_cta"]) if tuned else (0, 0)))
+    per_device = {}
+    for n in (1, 2, 4, 8, 16, 32, 64, 96):
+        with capi.Grid(terr.z, terr.n) as e:
+            e.ensemble_init(n, rm[:n], sc[:n], hy, h0=np.full(terr.z.shape, 0.05, np.float32),
+                            stream=stream)
+            e.advance_to(10.0, stream=stream)          # warm-up
+            e.profile(True)
+            s0 = e.members()["steps"].sum()
+            e.advance_to(70.0, stream=stream)
+            kms, kn = e.profile(False)
+            steps = float(e.members()["steps"].sum() - s0)
+            per_device[str(n)] = {"ms_per_step": kms / max(kn, 1),
+                                  "eta_bar_us_per_member_step": kms / max(steps, 1) * 1e3}
+    best = min(per_cta, key=lambda k: per_cta[k]["eta_bar_us_per_member_step"])
+    return {"config": "eta-bar = step-kernel time / member-steps (Eq. 13 per step); members per "
+                      "CTA on the live 96-member ensemble; members on the device from a 5 cm wet "
+                      "start", "members_per_cta": per_cta, "members_per_device": per_device,
+            "best_members_per_cta": int(best),
+            "per_cta_gain_best_over_1": per_cta["1"]["eta_bar_us_per_member_step"]
+                                        / per_cta[best]["eta_bar_us_per_member_step"] - 1.0}
+
+
+def products_only(capi):
+    """The product maps alone (profiling): an ensemble of the benchmark's
+    shape with its running maxima tracked over 60 s from a 5 cm wet start,
+    then the exceedance and 10/50/90 % maps three times with equal weights
+    and three times with unequal ones, maps kept on the device."""
+    import torch
+    from paper_2302_08341_gb300 import synth
+    device = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(device)
+    terr = synth.make_terrain(NY, NX, seed=SEED)
+    hy = synth.hyetograph_triangular(60.0, 1200.0, 3600.0)
+    rm, sc = synth.ensemble_prior(SEED, M)
+    maps = (torch.empty((NY, NX), dtype=torch.float32, device=device),
+            torch.empty((3, NY, NX), dtype=torch.float32, device=device))
+    res = {}
+    with capi.Grid(terr.z, terr.n) as g:
+        g.ensemble_init(M, rm, sc, hy, h0=np.full((NY, NX), 0.05, np.float32), stream=stream)
+        g.track_max_depth(True, stream=stream)
+        g.advance_to(60.0, stream=stream)
+        for name, w in (("equal_weights", np.full(M, 1.0 / M)),
+                        ("unequal_weights", np.linspace(1.0, 3.0, M) / np.linspace(1.0, 3.0, M).sum())):
+            g.set_members(weights=w)
+            ts = []
+            for _ in range(3):
+                e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.ensemble_products(0.2, (0.1, 0.5, 0.9), stream=stream, out=maps)
+                e1.record(stream)
+                torch.cuda.synchronize(device)
+                ts.append(e0.elapsed_time(e1))
+            res[name + "_ms"] = ts
+    return res
+
+
+def assimilation_overhead(g, stream, device, cells, obs):
+    """Fig. 12c's analogue: one assimilation round (gauge sample, weights,
+    N_eff, and -- when resampling -- the systematic resampling, the member
+    copies and the perturbation) on the 96-member 4.0 M-cell ensemble, timed
+    by CUDA events with and without resampling (5 rounds each)."""
+    import torch
+    from paper_2302_08341_gb300 import synth
+    M_ = g.M
+    out = {}
+    for name, force, thr in (("no_resampling", False, 0.0), ("resampling", True, 0.8)):
+        ts = []
+        for r in range(5):
+            u, beta = synth.pf_draws(SEED, 100 + r, M_)
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(device)
+            e0.record(stream)
+            g.gauge_sample(cells, stream=stream)
+            pf = g.pf_assimilate(obs, 0.05, u, beta, stream=stream, force=force, n_thr_frac=thr)
+            e1.record(stream)
+            torch.cuda.synchronize(device)
+            ts.append(e0.elapsed_time(e1))
+            assert bool(pf["resampled"]) == force
+        out[name + "_ms"] = float(np.median(ts))
+    out["resampling_over_no_resampling"] = out["resampling_ms"] / out["no_resampling_ms"]
+    out["config"] = ("gauge sample + particle-filter update of 96 members x 4.0 M cells, median "
+                     "of 5 rounds; the call includes the host reading the filter's outputs")
+    return out
+
+
 def land_cover_measure(capi):
     """Land cover (Section 4.1) on the benchmark ensemble: 2000 x 2000 cells,
     96 members with their own class roughness (Table 1 ranges) and drainage
@@ -516,9 +648,11 @@ def land_cover_measure(capi):
             torch.cuda.synchronize()
             kms, kn = g.profile(False)
             ms = e0.elapsed_time(e1)
-            units = float(g.members()["steps"].sum() - s0) * NY * NX
+            # only the cells of the domain count as work (the outside ones carry none)
+            active = float((cls != 3).sum()) if land else float(NY * NX)
+            units = float(g.members()["steps"].sum() - s0) * active
             res[name] = {"value": units / (ms * 1e-3), "ms_per_window": ms,
-                         "step_kernel_ms": kms / max(kn, 1)}
+                         "step_kernel_ms": kms / max(kn, 1), "active_cells": active}
             if land:
                 vol = g.volumes()
                 drained = g.drained()
@@ -546,6 +680,60 @@ def land_cover_measure(capi):
             "adjoint": adj}
 
 
+def masked_domain_measure(capi):
+    """Land cover over an irregular domain shaped like the paper's study area
+    (Section 4.1: 4,002,457 active cells of 3 m in an 8.2 x 7.6 km box):
+    2533 x 2733 cells, 57.8 % active (4.0 M), 96 members.  The step launches
+    only the tiles that hold a cell of the domain; beside it, the same box
+    with every cell active.  Member-cell-steps count active cells only; the
+    second 300 s window is timed."""
+    import torch
+    from paper_2302_08341_gb300 import synth
+    ny, nx = 2533, 2733
+    terr = synth.make_terrain(ny, nx, seed=SEED)
+    dom = synth.irregular_domain(ny, nx, 0.578, seed=SEED)
+    hy = synth.hyetograph_triangular(60.0, 1200.0, 3600.0)
+    rm, sc = synth.ensemble_prior(SEED, M)
+    n_m, d_m = synth.land_prior(SEED, M)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, domain in (("masked", dom), ("whole_box", np.ones_like(dom))):
+        cls = synth.land_cover(terr, seed=SEED, domain=domain)
+        active = float(domain.sum())
+        with capi.Grid(terr.z, terr.n) as g:
+            g.set_land_cover(cls, synth.LAND_CLASSES)
+            g.ensemble_init(M, rm, sc, hy, stream=stream)
+            g.set_land_params(n_m, d_m)
+            g.advance_to(WINDOW, stream=stream)
+            rows, _ = g.get_launch()
+            g.profile(True)
+            s0 = g.members()["steps"].sum()
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            g.advance_to(2 * WINDOW, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            kms, kn = g.profile(False)
+            ms = e0.elapsed_time(e1)
+            steps = float(g.members()["steps"].sum() - s0)
+        tiles = sum(bool(domain[a:a + rows, b:b + 128].any())
+                    for a in range(0, ny, rows) for b in range(0, nx, 128))
+        tiles_all = ((ny + rows - 1) // rows) * ((nx + 127) // 128)
+        step_ms = kms / max(kn, 1)
+        # algorithmic bytes: 26 B per active member-cell-step (26.25 B with the class byte)
+        res[name] = {"value": steps * active / (ms * 1e-3), "unit": "member-cell-steps/s",
+                     "active_cells": active, "active_frac": active / (ny * nx),
+                     "tiles_launched_frac": tiles / tiles_all, "rows_per_strip": rows,
+                     "ms_per_window": ms, "step_kernel_ms": step_ms,
+                     "hbm_frac_active": steps / max(kn, 1) * active * 26.25 / (step_ms * 1e-3)
+                                        / 1e9 / peaks()[0]}
+    res["config"] = (f"{ny}x{nx} box, {M} members, land cover, irregular domain "
+                     f"{100 * dom.mean():.1f} % active ({int(dom.sum())} cells), second 300 s window")
+    res["step_time_ratio"] = res["masked"]["step_kernel_ms"] / res["whole_box"]["step_kernel_ms"]
+    return res
+
+
 def products_measure(g, stream, device, ncell, fused_value):
     """Section 4.4's products on the benchmark ensemble: one 300 s window with
     every member's running maximum depth kept by the step kernel (8 more
@@ -555,24 +743,49 @@ def products_measure(g, stream, device, ncell, fused_value):
     t = float(g.members()["t"].max())
     g.track_max_depth(True, stream=stream)
     s0 = g.members()["steps"].sum()
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     torch.cuda.synchronize(device)
     e[0].record(stream)
     g.advance_to(t + WINDOW, stream=stream)
     e[1].record(stream)
     torch.cuda.synchronize(device)
     units = float(g.members()["steps"].sum() - s0) * ncell
-    e[2].record(stream)
-    exceed, pct = g.ensemble_products(0.2, (0.1, 0.5, 0.9), stream=stream)
-    e[3].record(stream)
-    torch.cuda.synchronize(device)
+    w0 = g.members()["weights"]
+
+    maps = (torch.empty((NY, NX), dtype=torch.float32, device=device),
+            torch.empty((3, NY, NX), dtype=torch.float32, device=device))
+
+    def timed_products():
+        # the call is synchronous; the events bracket it on the same stream,
+        # the maps stay on the device
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        ex, _ = g.ensemble_products(0.2, (0.1, 0.5, 0.9), stream=stream, out=maps)
+        ev[1].record(stream)
+        torch.cuda.synchronize(device)
+        return ev[0].elapsed_time(ev[1]), ex.cpu().numpy()
+
+    g.set_members(weights=np.full(len(w0), 1.0 / len(w0)))
+    timed_products()                                  # first call: allocator, attributes
+    eq_ms, exceed = timed_products()
+    wu = np.linspace(1.0, 3.0, len(w0)); wu /= wu.sum()
+    g.set_members(weights=wu)
+    uneq_ms, _ = timed_products()
+    g.set_members(weights=w0)
+    cur_ms, _ = timed_products()
     g.track_max_depth(False, stream=stream)
     v = units / (e[0].elapsed_time(e[1]) * 1e-3)
+    maxima_bytes = float(len(w0)) * ncell * 4.0 + 4.0 * ncell * 4.0   # maxima in, 4 maps out
     return {"config": "one 300 s window with the running maxima tracked, then P(hmax >= 0.2 m) "
                       "and the 10/50/90 % maps over 96 members (4.0 M cells each)",
             "tracked_value": v, "unit": "member-cell-steps/s",
             "tracking_cost": fused_value / v - 1.0,
-            "products_ms": e[2].elapsed_time(e[3]),
+            "products_ms": cur_ms,
+            "weights_equal_after_filter": bool(np.all(w0 == w0[0])),
+            "products_ms_equal_weights": eq_ms,
+            "products_ms_unequal_weights": uneq_ms,
+            "products_hbm_frac_equal_weights": maxima_bytes / (eq_ms * 1e-3) / 1e9 / peaks()[0],
+            "products_hbm_frac_unequal_weights": maxima_bytes / (uneq_ms * 1e-3) / 1e9 / peaks()[0],
             "cells_with_p_above_half": int((exceed > 0.5).sum())}
 
 
@@ -730,16 +943,12 @@ def run_gb300(args):
     if not args.no_extensions and world == 1:
         plain = plain_vs_fused(g, tuned, stream, device, ncell, hbm_peak)
         products = products_measure(g, stream, device, ncell, plain["fused"]["value"])
+        eta = guarded(eta_sweeps, capi, g, tuned, stream, device, terr, hy, rm, sc)
+        da = guarded(assimilation_overhead, g, stream, device, cells, obs[0])
     g.close()
     extensions = {}
     if not args.no_extensions and world == 1:
         # a failing extension is reported on the line instead of losing it
-        def guarded(fn, *a, **kw):
-            try:
-                return fn(*a, **kw)
-            except Exception as e:  # noqa: BLE001
-                return {"error": f"{type(e).__name__}: {e}"}
-
         extensions["adjoint"] = guarded(adjoint_measure, capi)
         extensions["batched"] = guarded(batch_measure, capi, tune=True)
         pers = guarded(batch_measure, capi, engine=2,
@@ -751,12 +960,21 @@ def run_gb300(args):
                 **{k: pers[k] for k in ("value", "unit", "ms", "all_finished", "gpu_launches",
                                         "engine", "rows_per_strip")},
                 "hbm_frac_whole_window": pers["value"] * BYTES_SINGLE / 1e9 / hbm_peak}
+        bm = guarded(batch_measure, capi, engine=extensions["batched"].get("engine_id"),
+                     rows=extensions["batched"].get("rows_per_strip"), members=4)
+        if "error" not in bm:
+            # 24 B of state per member-cell-step, the bed and roughness once per tile of 4
+            bm["hbm_frac_whole_window"] = bm["value"] * (BYTES_STATE + BYTES_STATIC / 4) / 1e9 / hbm_peak
+        extensions["batched"]["four_members"] = bm
         extensions["calibration"] = guarded(calibration_measure, capi,
                                             windows=args.calibration_windows)
         extensions["land_cover"] = guarded(land_cover_measure, capi)
+        extensions["masked_domain"] = guarded(masked_domain_measure, capi)
         extensions["autotune"] = tuned
         extensions["plain_vs_fused"] = plain
         extensions["products"] = products
+        extensions["eta_bar"] = eta
+        extensions["assimilation_overhead"] = da
 
     if rank != 0:
         if world > 1:
@@ -798,6 +1016,10 @@ def run_only(args):
         res = batch_measure(capi, engine=args.engine, tune=args.engine is None and not ROWS)
     elif args.only == "land_cover":
         res = land_cover_measure(capi)
+    elif args.only == "masked_domain":
+        res = masked_domain_measure(capi)
+    elif args.only == "products":
+        res = products_only(capi)
     else:
         res = calibration_measure(capi, windows=args.calibration_windows)
     print(json.dumps({"only": args.only, "members": M, "cells": NY * NX, **res}))
