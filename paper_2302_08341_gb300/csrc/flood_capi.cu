@@ -192,9 +192,8 @@ int launch_steps(flood_grid* g, int64_t count, double t_end, cudaStream_t s)
         if (g->engine == 1 && g->maps_ok) {
             flood::TmaArgs t;
             t.state_map = g->state_map;
-            t.static_map = g->static_map;
+            t.static_map = a.lc_on ? g->static_map_lc : g->static_map;
             if (a.hmax_field) t.hm_map = g->hm_map;
-            if (a.lc_on) t.cls_map = g->cls_map;
             // the ordinary step leaves out the tiles wholly outside the domain
             if (a.lc_on && g->lc_out_mask && !a.ckpt && a.wait_budget == kTmaWaitBudgetDefault) {
                 if (g->tiles_rows != g->rows_per_strip) {
@@ -379,6 +378,8 @@ int flood_destroy(flood_grid* g)
     dfree(g->n0); dfree(g->fac); dfree(g->fgrad);
     dfree(g->inflow);
     dfree(g->tiles);
+    dfree(g->prod_u);
+    dfree(g->zc);
     delete g;
     return FLOOD_OK;
 }

@@ -22,7 +22,9 @@ struct flood_grid {
     CUtensorMap static_map{};
     CUtensorMap state_map{};
     CUtensorMap hm_map;          // running maxima, for the TMA step (tracking)
-    CUtensorMap cls_map;         // land classes as bytes, for the TMA step (land cover)
+    CUtensorMap static_map_lc;   // land cover: the bed and each cell's class code (zc), the
+                                 // TMA step's static planes (the roughness comes from the class)
+    float* zc = nullptr;         // [2][ny][ld] land cover: bed, then class codes (uint32 bits)
     bool maps_ok = false;
     // ensemble
     int M = 0, nb = 0;
@@ -112,6 +114,7 @@ struct flood_grid {
     double* inflow_acc = nullptr; // [M] inflow volume
     // ensemble products (products.cu)
     float* hmax_field = nullptr;  // [M][plane] running maximum depth of each member
+    long long* prod_u = nullptr;  // [384] the products' weights in units of 2^-60
     bool track_max = false;
     // gradient calibration (calibrate.cu)
     float* n0 = nullptr;          // [ny][ld] base roughness, kept once a factor field is set

@@ -78,6 +78,7 @@ struct ProdArgs {
     long long u_eq;                // equal weights: the common weight
     float* exceed;        // [ny][nx] (or null)
     float* pct;           // [n_levels][ny][nx] of this pass (or null)
+    int* err;             // the grid's error word (bit 1: a bounded wait gave up)
 };
 
 __device__ __forceinline__ float exceed_value(long long units)
@@ -91,130 +92,219 @@ __device__ __forceinline__ float exceed_value(long long units)
 // network sorts MT slots.  The merge levels (P, K) are template parameters,
 // so every slot index is a compile-time constant and the slots stay in
 // registers.
-template <bool PAIRS, int MT>
-__device__ __forceinline__ void compare_exchange(float (&v)[MT], int (&id)[PAIRS ? MT : 1], int i,
-                                                 int k)
+// One comparator: the smaller value to slot i, the larger to slot k.  With
+// PAIRS the slots' member indices travel with their values; they are kept
+// as bytes, four to a register (id of slot i = byte i % 4 of word i / 4),
+// and exchanged by byte permutes, which halves the registers the indices
+// take next to 32-bit ones.
+__host__ __device__ constexpr unsigned swap_nibbles(int a, int b)
 {
+    unsigned s = 0x3210u;
+    s &= ~(0xFu << (4 * a));
+    s &= ~(0xFu << (4 * b));
+    return s | ((unsigned)b << (4 * a)) | ((unsigned)a << (4 * b));
+}
+__host__ __device__ constexpr unsigned take_nibble(int dst, int src)  // byte dst <- byte src of y
+{
+    return (0x3210u & ~(0xFu << (4 * dst))) | ((unsigned)(4 + src) << (4 * dst));
+}
+
+template <bool PAIRS, int MT, int NW>
+__device__ __forceinline__ void compare_exchange(float (&v)[MT], uint32_t (&id)[NW], int i, int k)
+{
+    const bool sw = v[i] > v[k];
+    const float lo = fminf(v[i], v[k]);
+    v[k] = fmaxf(v[i], v[k]);
+    v[i] = lo;
     if (PAIRS) {
-        const bool sw = v[i] > v[k];
-        const float vi = v[i], vk = v[k];
-        const int ii = id[PAIRS ? i : 0], ik = id[PAIRS ? k : 0];
-        v[i] = sw ? vk : vi;
-        v[k] = sw ? vi : vk;
-        id[PAIRS ? i : 0] = sw ? ik : ii;
-        id[PAIRS ? k : 0] = sw ? ii : ik;
-    } else {
-        const float lo = fminf(v[i], v[k]);
-        v[k] = fmaxf(v[i], v[k]);
-        v[i] = lo;
+        const int wi = i >> 2, bi = i & 3, wk = k >> 2, bk = k & 3;
+        if (wi == wk) {
+            const uint32_t x = __byte_perm(id[wi], 0u, swap_nibbles(bi, bk));
+            id[wi] = sw ? x : id[wi];
+        } else {
+            const uint32_t xi = __byte_perm(id[wi], id[wk], take_nibble(bi, bk));
+            const uint32_t xk = __byte_perm(id[wk], id[wi], take_nibble(bk, bi));
+            id[wi] = sw ? xi : id[wi];
+            id[wk] = sw ? xk : id[wk];
+        }
     }
 }
 
-template <bool PAIRS, int N, int MT, int P, int K>
-__device__ __forceinline__ void merge_level(float (&v)[MT], int (&id)[PAIRS ? MT : 1])
+template <bool PAIRS, int N, int MT, int P, int K, int NW>
+__device__ __forceinline__ void merge_level(float (&v)[MT], uint32_t (&id)[NW])
 {
 #pragma unroll
     for (int j = K % P; j + K < N; j += 2 * K) {
 #pragma unroll
         for (int i = 0; i < K; ++i) {
             if (i + j + K < MT && (i + j) / (2 * P) == (i + j + K) / (2 * P))
-                compare_exchange<PAIRS, MT>(v, id, i + j, i + j + K);
+                compare_exchange<PAIRS, MT, NW>(v, id, i + j, i + j + K);
         }
     }
-    if constexpr (K > 1) merge_level<PAIRS, N, MT, P, K / 2>(v, id);
+    if constexpr (K > 1) merge_level<PAIRS, N, MT, P, K / 2, NW>(v, id);
 }
 
-template <bool PAIRS, int N, int MT, int P = 1>
-__device__ __forceinline__ void odd_even_merge_sort(float (&v)[MT], int (&id)[PAIRS ? MT : 1])
+// Batcher's odd-even merge sort on N (a power of two) slots, every
+// comparator ascending (min to the lower slot).  Slots MT..N-1 would hold
+// +inf and never move, so every comparator reaching them is left out: the
+// network sorts MT slots.  The merge levels (P, K) are template parameters,
+// so every slot index is a compile-time constant and the slots stay in
+// registers.
+template <bool PAIRS, int N, int MT, int NW, int P = 1>
+__device__ __forceinline__ void odd_even_merge_sort(float (&v)[MT], uint32_t (&id)[NW])
 {
     if constexpr (P < N) {
-        merge_level<PAIRS, N, MT, P, P>(v, id);
-        odd_even_merge_sort<PAIRS, N, MT, 2 * P>(v, id);
+        merge_level<PAIRS, N, MT, P, P, NW>(v, id);
+        odd_even_merge_sort<PAIRS, N, MT, NW, 2 * P>(v, id);
     }
 }
 
-// v[k] for a run-time k < MT by a tournament on the bits of k (a select per
-// pair and level), so that v stays in registers (an indexed read would move
-// the whole array to local memory).
+// v[k] for a run-time k (k >= MT: 0) by a select per slot, written in PTX
+// so that the compiler keeps v in registers (read as v[k] it would move the
+// whole array to local memory); only the answer is live beside v.
 template <int MT>
 __device__ __forceinline__ float select_slot(const float (&v)[MT], int k)
 {
-    constexpr int L = MT <= 32 ? 5 : MT <= 64 ? 6 : 7;
-    float t[MT];
+    float ans = 0.0f;
 #pragma unroll
-    for (int i = 0; i < MT; ++i) t[i] = v[i];
-#pragma unroll
-    for (int b = 0; b < L; ++b) {
-        const bool hi = (k >> b) & 1;
-#pragma unroll
-        for (int i = 0; i < ((MT + (1 << b) - 1) >> b); i += 2)
-            t[i >> 1] = (((i + 1) << b) < MT && hi) ? t[i + 1] : t[i];
-    }
-    return t[0];
+    for (int i = 0; i < MT; ++i)
+        asm("{\n\t.reg .pred p;\n\tsetp.eq.s32 p, %2, %3;\n\tselp.f32 %0, %1, %0, p;\n\t}"
+            : "+f"(ans)
+            : "f"(v[i]), "r"(k), "r"(i));
+    return ans;
 }
 
-// One thread per cell.  The cell's MT slots (members, then +inf padding)
-// are sorted in registers; with equal weights the a-percentile is the
-// value of the rank that first reaches a (ranks from the host), otherwise
-// the members travel with their values through the sort and one prefix pass
-// over their weights finds, per level, the first sorted position whose
-// cumulative weight reaches it.  Tied values may come out in any order: the
-// first position to reach a level then still holds the tied value.
+// Arguments of the staged kernel: the running maxima as a 3-D tensor map
+// (nx, ny, M) whose box is 32 cells x 1 row x M members (one warp's group),
+// and the cell groups (32 consecutive cells of one row) to cover.
+struct ProdTma {
+    CUtensorMap map;
+    ProdArgs a;
+    int n_groups, groups_per_row;
+};
+
+constexpr int kProdWarps = 4;  // warps per CTA of the staged kernel
+
+template <int MT>
+__host__ __device__ constexpr int prod_stage_bytes() { return (MT * 32 * 4 + 127) / 128 * 128; }
+
+// One thread per cell, warps persistent over groups of 32 cells.  A group's
+// maxima (every member of 32 cells) arrive by one tensor copy into the
+// warp's stage; the lanes read them into registers and the copy of the
+// warp's next group starts at once, so it lands while this group is
+// sorted.  The cell's MT slots (members, then +inf padding) are sorted in
+// registers; with equal weights the a-percentile is the value of the rank
+// that first reaches a (ranks from the host), otherwise the members travel
+// with their values through the sort and one prefix pass over their weights
+// finds, per level, the first sorted position whose cumulative weight
+// reaches it.  Tied values may come out in any order: the first position to
+// reach a level then still holds the tied value.  Every wait is bounded: one
+// that gives up records FLOOD_ERR_TIMEOUT in the error word, waits for the
+// warp's copy in flight and returns.
 template <int MT, bool EQUAL>
-__global__ void __launch_bounds__(128) sorted_products_kernel(const ProdArgs a)
+__global__ void __launch_bounds__(32 * kProdWarps, MT <= 96 ? (EQUAL ? 4 : 3) : 2)
+    tma_products_kernel(const __grid_constant__ ProdTma t)
 {
+    extern __shared__ unsigned char smem_raw[];
+    const ProdArgs& a = t.a;
+    constexpr int NW = EQUAL ? 1 : (MT + 3) / 4;
+    constexpr int kStage = prod_stage_bytes<MT>();
+    constexpr long long kBudget = flood::kTmaWaitBudgetDefault;
     __shared__ long long us[EQUAL ? 1 : MT];
     if (!EQUAL) {
         for (int j = threadIdx.x; j < MT; j += blockDim.x) us[j] = j < a.M ? a.u[j] : 0;
         __syncthreads();
     }
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const int r = blockIdx.y;
-    if (c >= a.nx) return;
-    const float* f = a.field + (size_t)r * a.ld + c;
-    float v[MT];
-    int id[EQUAL ? 1 : MT];
-    if (EQUAL) id[0] = 0;
-    long long ex = 0;
-    int cnt = 0;
-    float top = -__int_as_float(0x7f800000);
-#pragma unroll
-    for (int j = 0; j < MT; ++j) {
-        const bool live = j < a.M;
-        const float x = live ? __ldcs(f + (size_t)j * a.plane) : __int_as_float(0x7f800000);
-        v[j] = x;
-        if (!EQUAL) id[EQUAL ? 0 : j] = j;
-        if (live) {
-            top = fmaxf(top, x);
-            if (EQUAL) cnt += x >= a.threshold;
-            else if (x >= a.threshold) ex += us[j];
-        }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+    const uint32_t bar = flood::smem_u32(base) + 8u * w;
+    const float* stage = reinterpret_cast<const float*>(base + 128 + kStage * w);
+    const uint32_t stage_s = flood::smem_u32(stage);
+    const uint32_t tx = 32u * 4u * (uint32_t)a.M;
+    const int gw = blockIdx.x * kProdWarps + w, nwarps = gridDim.x * kProdWarps;
+    if (lane == 0) {
+        flood::mbar_init(bar, 1);
+        flood::fence_mbar_init();
     }
+    __syncwarp();
+    auto issue = [&](int g) {
+        const int r = g / t.groups_per_row, c0 = (g % t.groups_per_row) * 32;
+        flood::mbar_arrive_expect_tx(bar, tx);
+        flood::tma_load_3d(stage_s, &t.map, c0, r, 0, bar);
+    };
+    if (gw < t.n_groups && lane == 0) issue(gw);
+    uint32_t phase = 0;
     constexpr int N = MT <= 32 ? 32 : MT <= 64 ? 64 : 128;   // the network's power of two
-    odd_even_merge_sort<!EQUAL, N, MT>(v, id);
-    const size_t out = (size_t)r * a.nx + c;
-    if (a.exceed) a.exceed[out] = exceed_value(EQUAL ? (long long)cnt * a.u_eq : ex);
-    if (!a.pct) return;
-    int pos[kLevelsPerPass];   // 0-based sorted position holding each level's value (>= M: none)
-    if (EQUAL) {
-#pragma unroll
-        for (int q = 0; q < kLevelsPerPass; ++q) pos[q] = a.rank[q] - 1;
-    } else {
-#pragma unroll
-        for (int q = 0; q < kLevelsPerPass; ++q) pos[q] = 0;
-        long long P = 0;
-#pragma unroll
-        for (int k = 0; k < MT; ++k) {
-            P += us[id[EQUAL ? 0 : k]];
-#pragma unroll
-            for (int q = 0; q < kLevelsPerPass; ++q) pos[q] += P < a.A[q];
+    for (int g = gw; g < t.n_groups; g += nwarps) {
+        if (!flood::mbar_wait_bounded(bar, phase, kBudget)) {
+            if (lane == 0) atomicOr(a.err, 2);
+            flood::mbar_wait_bounded(bar, phase, kBudget);  // the copy in flight lands first
+            return;
         }
-    }
+        phase ^= 1u;
+        float v[MT];
+        uint32_t id[NW];
+        long long ex = 0;
+        int cnt = 0;
 #pragma unroll
-    for (int q = 0; q < kLevelsPerPass; ++q) {
-        if (q >= a.n_levels) break;
-        const float sel = select_slot<MT>(v, pos[q]);
-        a.pct[(size_t)q * a.ny * a.nx + out] = pos[q] < a.M ? sel : top;
+        for (int j = 0; j < MT; ++j) {
+            const bool live = j < a.M;
+            const float x = live ? stage[j * 32 + lane] : __int_as_float(0x7f800000);
+            v[j] = x;
+        }
+        if (!EQUAL) {
+#pragma unroll
+            for (int q = 0; q < NW; ++q) id[q] = 0x03020100u + 0x04040404u * (uint32_t)q;
+        }
+        __syncwarp();  // every lane has read the stage: the next copy may overwrite it
+        const int gn = g + nwarps;
+        if (gn < t.n_groups && lane == 0) {
+            flood::fence_proxy_async_smem();
+            issue(gn);
+        }
+        odd_even_merge_sort<!EQUAL, N, MT, NW>(v, id);
+        if (EQUAL) {
+            // members at or above the threshold, counted on the sorted slots
+            // (the +inf padding slots above M count too and are taken off);
+            // counted while loading, the comparisons would keep the unsorted
+            // values live through the sort
+#pragma unroll
+            for (int k = 0; k < MT; ++k) cnt += v[k] >= a.threshold;
+            cnt -= MT - a.M;
+        }
+        const int r = g / t.groups_per_row, c = (g % t.groups_per_row) * 32 + lane;
+        if (c >= a.nx) continue;
+        const size_t out = (size_t)r * a.nx + c;
+        int pos[kLevelsPerPass];   // 0-based sorted position holding each level's value (>= M: none)
+        if (EQUAL) {
+#pragma unroll
+            for (int q = 0; q < kLevelsPerPass; ++q) pos[q] = a.rank[q] - 1;
+        } else {
+            // one pass over the sorted slots: the weight at or above the
+            // threshold, and per level the slots whose cumulative weight
+            // stays below it (the padding slots weigh nothing)
+#pragma unroll
+            for (int q = 0; q < kLevelsPerPass; ++q) pos[q] = 0;
+            long long P = 0;
+#pragma unroll
+            for (int k = 0; k < MT; ++k) {
+                const long long uk = us[(id[EQUAL ? 0 : k >> 2] >> (8 * (k & 3))) & 0xffu];
+                P += uk;
+                if (v[k] >= a.threshold) ex += uk;
+#pragma unroll
+                for (int q = 0; q < kLevelsPerPass; ++q) pos[q] += P < a.A[q];
+            }
+        }
+        if (a.exceed) a.exceed[out] = exceed_value(EQUAL ? (long long)cnt * a.u_eq : ex);
+        if (!a.pct) continue;
+        const float top = a.M == MT ? v[MT - 1] : select_slot<MT>(v, a.M - 1);
+#pragma unroll
+        for (int q = 0; q < kLevelsPerPass; ++q) {
+            if (q >= a.n_levels) break;
+            const float sel = select_slot<MT>(v, pos[q]);
+            a.pct[(size_t)q * a.ny * a.nx + out] = pos[q] < a.M ? sel : top;
+        }
     }
 }
 
@@ -263,26 +353,40 @@ __global__ void __launch_bounds__(kCells) staged_products_kernel(const ProdArgs 
 size_t products_smem(int M) { return sizeof(long long) * M + sizeof(float) * (size_t)M * kCells; }
 
 template <int MT, bool EQUAL>
-void launch_sorted(const ProdArgs& a, cudaStream_t s)
+void launch_tma_products(ProdTma& t, int n_sm, cudaStream_t s)
 {
-    dim3 grid((a.nx + 127) / 128, a.ny);
-    sorted_products_kernel<MT, EQUAL><<<grid, 128, 0, s>>>(a);
+    constexpr size_t shm = 128 + (size_t)prod_stage_bytes<MT>() * kProdWarps + 128;
+    static int per_sm = 0;
+    if (!per_sm) {
+        cudaFuncSetAttribute(tma_products_kernel<MT, EQUAL>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tma_products_kernel<MT, EQUAL>,
+                                                      32 * kProdWarps, shm);
+        per_sm = std::max(per_sm, 1);
+    }
+    const int need = (t.n_groups + kProdWarps - 1) / kProdWarps;
+    const int blocks = std::max(1, std::min(need, n_sm * per_sm));
+    tma_products_kernel<MT, EQUAL><<<blocks, 32 * kProdWarps, shm, s>>>(t);
 }
 
-// The fastest kernel for the member count and weights: sorted slots in
-// registers up to 96 members (128 with equal weights), staged otherwise.
-void launch_products(const ProdArgs& a, bool equal, cudaStream_t s)
+// The staged kernel up to 128 members (its copy box holds every member of
+// 32 cells), the shared-memory kernel beyond or without a tensor map.
+void launch_products(ProdTma& t, bool have_map, bool equal, int n_sm, cudaStream_t s)
 {
-    if (equal && a.M <= 32) launch_sorted<32, true>(a, s);
-    else if (equal && a.M <= 64) launch_sorted<64, true>(a, s);
-    else if (equal && a.M <= 96) launch_sorted<96, true>(a, s);
-    else if (equal && a.M <= 128) launch_sorted<128, true>(a, s);
-    else if (!equal && a.M <= 32) launch_sorted<32, false>(a, s);
-    else if (!equal && a.M <= 64) launch_sorted<64, false>(a, s);
-    else if (!equal && a.M <= 96) launch_sorted<96, false>(a, s);
-    else {
-        dim3 grid((a.nx + kCells - 1) / kCells, a.ny);
-        staged_products_kernel<<<grid, kCells, products_smem(a.M), s>>>(a);
+    const int M = t.a.M;
+    if (!have_map || M > 128) {
+        dim3 grid((t.a.nx + kCells - 1) / kCells, t.a.ny);
+        staged_products_kernel<<<grid, kCells, products_smem(M), s>>>(t.a);
+    } else if (equal) {
+        if (M <= 32) launch_tma_products<32, true>(t, n_sm, s);
+        else if (M <= 64) launch_tma_products<64, true>(t, n_sm, s);
+        else if (M <= 96) launch_tma_products<96, true>(t, n_sm, s);
+        else launch_tma_products<128, true>(t, n_sm, s);
+    } else {
+        if (M <= 32) launch_tma_products<32, false>(t, n_sm, s);
+        else if (M <= 64) launch_tma_products<64, false>(t, n_sm, s);
+        else if (M <= 96) launch_tma_products<96, false>(t, n_sm, s);
+        else launch_tma_products<128, false>(t, n_sm, s);
     }
 }
 
@@ -371,15 +475,34 @@ extern "C" int flood_ensemble_products(flood_grid* g, double threshold, int n_le
         return flood::fail(g, FLOOD_ERR_STATE, "particle weights do not sum to one");
     const bool equal = std::all_of(u.begin(), u.end(), [&](long long x) { return x == u[0]; });
     const size_t cells = (size_t)g->ny * g->nx;
-    const size_t need_f = (exceed ? cells : 0) + (size_t)n_levels * cells;
+    // outputs in device memory are written in place; others go through a
+    // device buffer and a copy
+    auto on_device = [](const void* p) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    };
+    const bool ex_dev = exceed && on_device(exceed);
+    const bool pct_dev_ok = n_levels > 0 && on_device(pct);
+    const size_t need_f = (exceed && !ex_dev ? cells : 0) + (pct_dev_ok ? 0 : (size_t)n_levels * cells);
     char* buf = nullptr;
-    const size_t bytes = sizeof(long long) * M + sizeof(float) * need_f;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&buf), bytes, s);
-    if (e != cudaSuccess)
-        return flood::fail(g, e == cudaErrorMemoryAllocation ? FLOOD_ERR_OOM : FLOOD_ERR_CUDA,
-                           std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
-    long long* du = reinterpret_cast<long long*>(buf);
-    float* dout = reinterpret_cast<float*>(du + M);
+    if (need_f) {
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&buf), sizeof(float) * need_f, s);
+        if (e != cudaSuccess)
+            return flood::fail(g, e == cudaErrorMemoryAllocation ? FLOOD_ERR_OOM : FLOOD_ERR_CUDA,
+                               std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+    }
+    float* dtmp = reinterpret_cast<float*>(buf);
+    float* dex = ex_dev ? exceed : (exceed ? dtmp : nullptr);
+    float* dpct = pct_dev_ok ? pct : (n_levels ? dtmp + (exceed && !ex_dev ? cells : 0) : nullptr);
+    if (!g->prod_u) {
+        const int rc = flood::dalloc(g, &g->prod_u, kMaxMembers);
+        if (rc) return rc;
+    }
+    long long* du = g->prod_u;
     CK(g, cudaMemcpyAsync(du, u.data(), sizeof(long long) * M, cudaMemcpyHostToDevice, s));
     static bool attr = false;
     if (!attr) {
@@ -387,7 +510,16 @@ extern "C" int flood_ensemble_products(flood_grid* g, double threshold, int n_le
                                    (int)products_smem(kMaxMembers)));
         attr = true;
     }
-    ProdArgs a{};
+    // the maxima as (nx, ny, M) with a box of 32 cells x 1 row x M members
+    ProdTma tm{};
+    const bool have_map =
+        M <= 128 && flood::encode_map_3d(&tm.map, g->hmax_field, g->nx, g->ny, (uint64_t)M,
+                                         sizeof(float) * g->ld, sizeof(float) * g->plane, 32, 1,
+                                         (uint32_t)M) == 0;
+    tm.groups_per_row = (g->nx + 31) / 32;
+    tm.n_groups = tm.groups_per_row * g->ny;
+    ProdArgs& a = tm.a;
+    a.err = g->err;
     a.field = g->hmax_field;
     a.u = du;
     a.M = M;
@@ -395,7 +527,6 @@ extern "C" int flood_ensemble_products(flood_grid* g, double threshold, int n_le
     a.plane = g->plane;
     a.threshold = (float)threshold;
     a.u_eq = u[0];
-    float* pct_dev = dout + (exceed ? cells : 0);
     // one pass per kLevelsPerPass levels (at least one: the exceedance map)
     for (int q0 = 0; q0 == 0 || q0 < n_levels; q0 += kLevelsPerPass) {
         a.n_levels = std::min(kLevelsPerPass, n_levels - q0);
@@ -407,16 +538,19 @@ extern "C" int flood_ensemble_products(flood_grid* g, double threshold, int n_le
             if (on && u[0] > 0) k = std::min<long long>(M + 1, (A[q0 + q] + u[0] - 1) / u[0]);
             a.rank[q] = (int)std::max<long long>(k, 1);
         }
-        a.exceed = (exceed && q0 == 0) ? dout : nullptr;
-        a.pct = a.n_levels > 0 ? pct_dev + (size_t)q0 * cells : nullptr;
-        launch_products(a, equal, s);
+        a.exceed = q0 == 0 ? dex : nullptr;
+        a.pct = a.n_levels > 0 ? dpct + (size_t)q0 * cells : nullptr;
+        launch_products(tm, have_map, equal, g->n_sm, s);
         g->launches++;
         CK(g, cudaGetLastError());
     }
-    if (exceed) CK(g, cudaMemcpyAsync(exceed, dout, sizeof(float) * cells, cudaMemcpyDefault, s));
-    if (n_levels)
-        CK(g, cudaMemcpyAsync(pct, pct_dev, sizeof(float) * cells * n_levels, cudaMemcpyDefault, s));
-    CK(g, cudaFreeAsync(buf, s));
+    if (exceed && !ex_dev) CK(g, cudaMemcpyAsync(exceed, dex, sizeof(float) * cells, cudaMemcpyDefault, s));
+    if (n_levels && !pct_dev_ok)
+        CK(g, cudaMemcpyAsync(pct, dpct, sizeof(float) * cells * n_levels, cudaMemcpyDefault, s));
+    if (buf) CK(g, cudaFreeAsync(buf, s));
     CK(g, cudaStreamSynchronize(s));
+    int err = 0;
+    CK(g, cudaMemcpy(&err, g->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err & 2) return flood::fail(g, FLOOD_ERR_TIMEOUT, "a bounded wait for staged maxima gave up");
     return FLOOD_OK;
 }
