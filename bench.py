@@ -960,8 +960,7 @@ def run_gb300(args):
                 **{k: pers[k] for k in ("value", "unit", "ms", "all_finished", "gpu_launches",
                                         "engine", "rows_per_strip")},
                 "hbm_frac_whole_window": pers["value"] * BYTES_SINGLE / 1e9 / hbm_peak}
-        bm = guarded(batch_measure, capi, engine=extensions["batched"].get("engine_id"),
-                     rows=extensions["batched"].get("rows_per_strip"), members=4)
+        bm = guarded(batch_measure, capi, tune=True, members=4)
         if "error" not in bm:
             # 24 B of state per member-cell-step, the bed and roughness once per tile of 4
             bm["hbm_frac_whole_window"] = bm["value"] * (BYTES_STATE + BYTES_STATIC / 4) / 1e9 / hbm_peak

@@ -271,8 +271,7 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
         flood::TmaArgs rt;
         if (tma_replay) {
             rt.state_map = tma.seg_map;
-            rt.static_map = g->static_map;
-            if (g->lc_on) rt.cls_map = g->cls_map;
+            rt.static_map = g->lc_on ? g->static_map_lc : g->static_map;
         }
         for (int i = 0; i < len; ++i) {
             a.replay_i = i;

@@ -88,12 +88,12 @@ struct StepArgs {
 
 // Arguments of the TMA-staged step kernel: tensor maps of the two state
 // buffers ([2 M 3] planes of [ny][ld]) and of the static fields ([z, n]
-// planes), 3-D tiles of 136 columns x 1 row x (3 or 2) planes.
+// planes; with land cover [z, class code]), 3-D tiles of 136 columns x 1 row
+// x (3 or 2) planes.
 struct TmaArgs {
     CUtensorMap state_map;
     CUtensorMap static_map;
     CUtensorMap hm_map;     // running maxima (ld, ny, M), box 128 x 1 x 1 (tracking only)
-    CUtensorMap cls_map;    // land classes (ld, ny, 1) as bytes, box 160 x 1 x 1 (land cover only)
     StepArgs a;
 };
 
@@ -303,7 +303,10 @@ __device__ __forceinline__ uint32_t cls_word(const uint8_t* cls, size_t o)
     return *reinterpret_cast<const uint32_t*>(cls + o);
 }
 
-__device__ __forceinline__ uint32_t cls_at(uint32_t w, int j) { return (w >> (8 * j)) & 0xffu; }
+// Source lane of cell j's class-table entry, for land_get: the shuffle reads
+// only the five low bits of its source lane, and class codes (< 4) fill the
+// two low bits of their byte, so the byte needs no masking.
+__device__ __forceinline__ uint32_t cls_at(uint32_t w, int j) { return w >> (8 * j); }
 
 __device__ __forceinline__ void land_n4(float (&nv)[4], uint32_t w, const LandK& lk)
 {

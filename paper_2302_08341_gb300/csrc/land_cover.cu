@@ -14,6 +14,7 @@
 
 #include "grid.cuh"
 #include "pf_kernels.cuh"
+#include "tma.cuh"
 
 #define CK FLOOD_CK
 
@@ -317,10 +318,21 @@ extern "C" int flood_set_land_cover(flood_grid* g, const uint8_t* cls, int n_cla
     }
     int rc = flood::dalloc(g, &g->cls8, pad.size());
     if (rc) return rc;
+    // the TMA step's static planes with land cover: the bed (raised outside
+    // the domain) and each cell's class code, where the roughness plane
+    // would be (the roughness comes from the class)
+    if ((rc = flood::dalloc(g, &g->zc, 2 * g->plane))) return rc;
+    CK(g, cudaMemcpy(g->zc, g->z, sizeof(float) * g->plane, cudaMemcpyDeviceToDevice));
+    {
+        std::vector<uint32_t> codes(g->plane, 0u);
+        for (size_t i = 0; i < g->plane; ++i) codes[i] = pad[i];
+        CK(g, cudaMemcpy(g->zc + g->plane, codes.data(), sizeof(uint32_t) * g->plane,
+                         cudaMemcpyHostToDevice));
+    }
+    if (flood::encode_map_3d(&g->static_map_lc, g->zc, g->ld, g->ny, 2, sizeof(float) * g->ld,
+                             sizeof(float) * g->plane, flood::tma_box_cols(), 1, 2) != 0)
+        return flood::fail(g, FLOOD_ERR_CUDA, "tensor map of the bed and class codes");
     CK(g, cudaMemcpy(g->cls8, pad.data(), pad.size(), cudaMemcpyHostToDevice));
-    if (flood::encode_map_3d_u8(&g->cls_map, g->cls8, g->ld, g->ny, 1, g->ld, (uint64_t)g->ld * g->ny,
-                                160, 1, 1) != 0)
-        return flood::fail(g, FLOOD_ERR_CUDA, "tensor map of the land classes");
     for (int q = 0; q < kMaxClasses; ++q) {
         g->lc_runoff[q] = runoff[q];
         g->lc_drains[q] = drains[q];

@@ -17,7 +17,7 @@ constexpr int kSpan = kTmaSpan;
 // CK: the step may write checkpoints (the adjoint's logged forward); the
 // ordinary step is compiled without that path.
 template <int WM, bool TRACK_MAX, bool LC, int LIM, bool CK, bool HOOK = false>
-__global__ void __launch_bounds__(32 * WM, (LC || TRACK_MAX ? 16 : 20) / WM) step_tma_kernel(const __grid_constant__ TmaArgs t)
+__global__ void __launch_bounds__(32 * WM, (TRACK_MAX ? 16 : 20) / WM) step_tma_kernel(const __grid_constant__ TmaArgs t)
 {
     extern __shared__ unsigned char smem_raw[];
     const StepArgs& a = t.a;
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(32 * WM, (LC || TRACK_MAX ? 16 : 20) / WM) ste
     if (!tma_march<TRACK_MAX, LC, LIM, HOOK>(&t.state_map, &t.static_map, (pl.cur * a.M + m) * 3, bar0,
                                   my_stages, dst, ck, hm, a.err, a.plane, a.ny, a.nx, a.ld, c0, r0,
                                   r1, lane, k, pl.dt_dx, a.scale[m], pl.dr, a.east_out, a.south_out,
-                                  mo, &lk, a.wait_budget, &t.hm_map, m, &t.cls_map))
+                                  mo, &lk, a.wait_budget, &t.hm_map, m))
         return;
 
     if (mo.bad) atomicOr(a.err, 1);
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(32 * WM, (LC || TRACK_MAX ? 16 : 20) / WM) ste
 // replay_i + 1, with the member's plan taken from the step log.  LC: with
 // land cover (the class bytes ride in the stage, as in the step).
 template <int WM, int LIM, bool LC = false>
-__global__ void __launch_bounds__(32 * WM, (LC ? 16 : 20) / WM) replay_tma_kernel(const __grid_constant__ TmaArgs t)
+__global__ void __launch_bounds__(32 * WM, 20 / WM) replay_tma_kernel(const __grid_constant__ TmaArgs t)
 {
     extern __shared__ unsigned char smem_raw[];
     const StepArgs& a = t.a;
@@ -134,8 +134,7 @@ __global__ void __launch_bounds__(32 * WM, (LC ? 16 : 20) / WM) replay_tma_kerne
     if (!tma_march<false, LC, LIM>(&t.state_map, &t.static_map, (a.replay_i * a.M + m) * 3, bar0,
                                    my_stages, dst, nullptr, nullptr, a.err, a.plane, a.ny, a.nx,
                                    a.ld, c0, r0, r1, lane, k, pl.dt_dx, a.scale[m], pl.dr,
-                                   a.east_out, a.south_out, mo, &lk, kTmaWaitBudget, nullptr, 0,
-                                   &t.cls_map))
+                                   a.east_out, a.south_out, mo, &lk, kTmaWaitBudget, nullptr, 0))
         return;
     if (mo.bad) atomicOr(a.err, 1);
 }

@@ -34,11 +34,11 @@ __host__ __device__ constexpr size_t tma_march_smem_bytes(int warps, int stage_b
     return 128 + 128 * ((8 * kTmaNS * warps + 127) / 128) + (size_t)kTmaNS * stage_bytes * warps;
 }
 constexpr int kTmaHmOff = kTmaStageBytes;              // running maxima: 128 floats after z, n
-// land classes: 160 bytes (columns c0 - 16 .. c0 + 143) after the maxima, if any
-__host__ __device__ constexpr int tma_cls_off(bool track) { return kTmaStageBytes + (track ? 512 : 0); }
+// With land cover the static planes are the bed and each cell's class code
+// (a uint32 where the roughness would be): the stage keeps its size.
 __host__ __device__ constexpr int tma_stage_bytes(bool track, bool lc)
 {
-    return tma_cls_off(track) + (lc ? 256 : 0);
+    return kTmaStageBytes + (track ? 512 : 0) + (lc ? 0 : 0);
 }
 
 // This warp's barriers and stages inside the CTA's dynamic shared memory.
@@ -69,8 +69,9 @@ __device__ __forceinline__ void tma_store4(float* p, const float (&v)[4])
 // running maximum depth at hm, whose old values arrive with each row through
 // hm_map (member plane hm_plane, 128 columns from c0; a 3.3 KB stage, so four
 // CTAs of four warps per SM); LC: land cover (roughness by class from lk,
-// the class's share of the rain and its drainage; the class bytes of each
-// row, columns c0 - 16 .. c0 + 143, arrive with the row through cls_map).  Each is a separate
+// the class's share of the rain and its drainage; static_map then holds the
+// bed and each cell's class code, so the codes arrive with the row where
+// the roughness would, halo included).  Each is a separate
 // instantiation, so the plain step carries no trace of them.  Returns false
 // if a wait gave up.  WAIT_HOOK: each row wait may take wait_budget clock
 // cycles instead of kTmaWaitBudget (a failure-detection hook; the copies
@@ -85,15 +86,13 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
                                           int east_out, int south_out, MarchOut& out,
                                           const LandK* lk = nullptr,
                                           long long wait_budget = kTmaWaitBudget,
-                                          const CUtensorMap* hm_map = nullptr, int hm_plane = 0,
-                                          const CUtensorMap* cls_map = nullptr)
+                                          const CUtensorMap* hm_map = nullptr, int hm_plane = 0)
 {
     constexpr int kNS = kTmaNS;
     constexpr int kBox = kTmaBox;
     constexpr int kStaticOff = kTmaStaticOff;
     constexpr int kStageBytes = tma_stage_bytes(TRACK_MAX, LC);
-    constexpr int kClsOff = tma_cls_off(TRACK_MAX);
-    constexpr uint32_t kTx = kTmaTx + (TRACK_MAX ? 512u : 0u) + (LC ? 160u : 0u);
+    constexpr uint32_t kTx = kTmaTx + (TRACK_MAX ? 512u : 0u);
     constexpr int kZ = kStaticOff / 4;
     constexpr int kN = kZ + kBox;
     constexpr long long kWaitBudget = kTmaWaitBudget;
@@ -121,19 +120,19 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
         tma_load_3d(dsts, state_map, c0 - 4, row, plane0, bar);
         tma_load_3d(dsts + kStaticOff, static_map, c0 - 4, row, 0, bar);
         if (TRACK_MAX) tma_load_3d(dsts + kTmaHmOff, hm_map, c0, row, hm_plane, bar);
-        if (LC) tma_load_3d(dsts + kClsOff, cls_map, c0 - 16, row, 0, bar);
     };
-    // land classes of a staged row: the lane's four cells, and the cells just
-    // east and west of the span
+    // land classes of a staged row (LC: the class-code plane): the lane's
+    // four cells as one byte each of a word, and the cells just east and
+    // west of the span
     auto cls_of = [&](const float* P) -> uint32_t {
-        return *reinterpret_cast<const uint32_t*>(reinterpret_cast<const unsigned char*>(P) +
-                                                  kClsOff + 16 + 4 * lane);
+        const uint4 q = *reinterpret_cast<const uint4*>(P + kN + 4 + 4 * lane);
+        return __byte_perm(__byte_perm(q.x, q.y, 0x0040u), __byte_perm(q.z, q.w, 0x0040u), 0x5410u);
     };
     auto cls_e = [&](const float* P) -> uint32_t {
-        return reinterpret_cast<const unsigned char*>(P)[kClsOff + 16 + kTmaSpan];
+        return __float_as_uint(P[kN + 4 + kTmaSpan]);
     };
     auto cls_w = [&](const float* P) -> uint32_t {
-        return reinterpret_cast<const unsigned char*>(P)[kClsOff + 15];
+        return __float_as_uint(P[kN + 3]);
     };
     for (; issued < rb && issued < ra + kNS; ++issued)
         if (lane == 0) issue(issued);
