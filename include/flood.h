@@ -482,7 +482,8 @@ int flood_set_engine(flood_grid* g, int engine);
 int flood_set_wait_budget(flood_grid* g, int64_t cycles);
 
 /* Autotuner: time every step-kernel configuration (engine x rows per strip
- * {32, 64, 128} x members per CTA {4, 1}) for steps_per_trial steps on the
+ * {32, 64, 128} x members per CTA {8, 4, 2, 1}; 8 and 2 with the plain TMA
+ * step only) for steps_per_trial steps on the
  * live ensemble, keep the fastest, and restore the ensemble (state, clocks,
  * volume counters) to where it was.  Writes the choice and its time per step
  * (ms); any output may be NULL.  Synchronous. */

@@ -862,10 +862,18 @@ extern "C" int flood_autotune(flood_grid* g, int steps_per_trial, int* best_rows
     g->track_max = false;
     struct Cand { int rows, mpc, engine; };
     std::vector<Cand> cands;
+    // members per CTA: the TMA engine's plain step also has 2 and 8 (the
+    // land-cover and tracking forms run 2 as 1 and 8 as 4, so those are not
+    // timed twice)
+    const bool plain_tma = !g->lc_on && !g->track_max;
     for (int e : {1, 0})
         for (int r : {32, 64, 128})
-            for (int mp : {4, 1})
-                if ((e == 0 || g->maps_ok) && (mp == 1 || M >= 4)) cands.push_back({r, mp, e});
+            for (int mp : {8, 4, 2, 1}) {
+                if (e == 1 && !g->maps_ok) continue;
+                if ((mp == 2 || mp == 8) && !(e == 1 && plain_tma)) continue;
+                if (mp > M) continue;
+                cands.push_back({r, mp, e});
+            }
     cudaEvent_t e0, e1;
     CK(g, cudaEventCreate(&e0));
     CK(g, cudaEventCreate(&e1));
