@@ -228,3 +228,34 @@ def test_full_size_adjoint_against_central_differences(capi):
             ("factor", "fac_f", (Gf.astype(np.float64) * f).sum())):
         dL = (run(**{kw: 1 + eps}) - run(**{kw: 1 - eps})).sum() / (2 * eps)
         assert want != 0.0 and abs(dL - want) <= 0.03 * abs(dL), (key, dL, want)
+
+
+def test_full_size_adjoint_matches_the_fp64_adjoint_on_one_member(capi):
+    """The calibration's gradients at their full size against the FP64
+    oracle's reverse mode: 2000 x 2000 cells, one member of the calibration
+    ensemble from 5 cm of water under the storm, 6 gauges observed at 30 s and
+    60 s (the oracle keeps the whole trajectory, about 6 GB for these 60 s).
+    Loss 1e-4, rain-multiplier and Manning-scale gradients 2e-3 relative, the
+    per-cell Manning gradient 2e-3 of its largest magnitude; the factor-field
+    gradient follows from it by the chain rule (pinned on the CPU)."""
+    ny = nx = 2000
+    terr = synth.make_terrain(ny, nx, seed=4)
+    hy = synth.hyetograph_triangular(60.0, 1200.0, 3600.0)
+    rm, sc = synth.ensemble_prior(4, 1)
+    cells = synth.gauge_cells(terr, 6, seed=4)
+    h0 = np.full((ny, nx), 0.05, np.float32)
+    d = np.array([[0.06] * 6, [0.07] * 6])
+    p = capi.Params.default()
+    with capi.Grid(terr.z, terr.n, p) as g:
+        g.ensemble_init(1, rm, sc, hy, h0=h0)
+        out = g.adjoint(cells, d, 30.0, grad_h0=False)
+    ref = oracle.loss_and_grad(oracle_params(p, ny, nx), terr.z, terr.n, float(sc[0]), float(rm[0]),
+                               hy, h0, 30.0, d, cells)
+    assert abs(out["loss"][0] - ref["loss"]) <= 1e-4 * ref["loss"]
+    for key in ("grad_rain", "grad_scale"):
+        assert abs(out[key][0] - ref[key]) <= 2e-3 * abs(ref[key]), (key, out[key][0], ref[key])
+    err = np.max(np.abs(out["grad_n"] - ref["grad_n"])) / np.max(np.abs(ref["grad_n"]))
+    print(f"2000x2000 adjoint, 60 s: grad_n max err {err:.2e}, grad_rain "
+          f"{abs(out['grad_rain'][0] - ref['grad_rain']) / abs(ref['grad_rain']):.2e}, "
+          f"grad_scale {abs(out['grad_scale'][0] - ref['grad_scale']) / abs(ref['grad_scale']):.2e}")
+    assert err <= 2e-3, err
