@@ -7,7 +7,8 @@ The oracle cannot carry 96 full-size members through the hour in a test, so
 it follows particles: every particle alive at the end descends, window by
 window, from one of the initial particles (a resampling copies a state
 exactly), so its whole ancestry can be evolved by the oracle from the dry
-start at t = 0 with no restart.  The resampling decisions the oracle takes
+start at t = 0 with no restart; six final particles are followed, one host
+thread each.  The resampling decisions the oracle takes
 are its own -- Eq. 9-12 and systematic resampling on the GPU's gauge outputs
 (the only outputs that exist for all 96 members), which must give the GPU's
 indices bit for bit -- and the rain multipliers it carries are its own FP64
@@ -27,7 +28,7 @@ pytestmark = pytest.mark.gpu
 
 NY = NX = 2000
 M, G, SEED, WINDOWS, WINDOW = 96, 6, 1, 12, 300.0
-FOLLOW = (0, 47, 95)          # final slots whose ancestry the oracle evolves
+FOLLOW = (0, 19, 38, 57, 76, 95)   # final slots whose ancestry the oracle evolves
 
 
 @pytest.fixture(scope="module")
@@ -124,7 +125,8 @@ def test_headline_ensemble_follows_the_oracle_for_the_whole_hour(capi):
     for f in FOLLOW:    # the GPU run repeats itself bit for bit
         assert np.array_equal(run2["final"][f], run1["final"][f])
 
-    # the oracle evolves the followed ancestries from the dry start
+    # the oracle evolves the followed ancestries from the dry start, one host
+    # thread each
     op = oracle_params(capi.Params.default(), NY, NX)
     ens = oracle.Ensemble(op, len(FOLLOW))
     z = terr.z.astype(np.float64); n = terr.n.astype(np.float64)
@@ -151,6 +153,7 @@ def test_headline_ensemble_follows_the_oracle_for_the_whole_hour(capi):
         assert np.max(np.abs(run1["final"][f] - ens.h[k])) <= 1e-3
         v_o = oracle.storage(ens.h[k], op.dx)
         assert abs(run1["vol"]["storage"][f] - v_o) <= 1e-5 * v_o
+    starts = sorted({during[f][1] for f in FOLLOW})
     print(f"full-run parity: {n_resampled} resamplings, max |dh| {worst_h:.3e} m, "
-          f"max storage rel err {worst_v:.3e}, ancestries "
+          f"max storage rel err {worst_v:.3e}, initial particles {starts}, ancestries "
           f"{ {f: during[f][1:] for f in FOLLOW} }")
