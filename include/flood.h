@@ -350,8 +350,10 @@ int flood_get_max_depth(flood_grid* g, int member, float* out, void* stream);
 /* The products above with the current particle weights.  exceed: [ny][nx]
  * FP32 or NULL; levels: n_levels (0..16) values in (0, 1]; pct:
  * [n_levels][ny][nx] FP32.  Host or device outputs.  One thread per cell
- * sorts the cell's maxima in registers (up to 96 members, 128 with equal
- * weights; more members are staged in shared memory).  Synchronous.  Errors:
+ * sorts the cell's maxima in registers (up to 128 members; with unequal
+ * weights as 32-bit keys carrying the member index; more members are
+ * staged in shared memory).  A percentile of a value that ties -0 with +0
+ * may come out as either zero.  Maxima must not be NaN.  Synchronous.  Errors:
  * FLOOD_ERR_STATE (not tracking, or weights outside [0, 1] or summing far
  * above one), FLOOD_ERR_ARG (levels, more than 384 members or 65535 rows),
  * FLOOD_ERR_OOM. */

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "grid.cuh"
@@ -72,6 +73,7 @@ struct ProdArgs {
     int M, ny, nx, ld;
     size_t plane;
     float threshold;
+    uint32_t th_ord;      // ord of the threshold (of -0 for a zero threshold): x >= it iff ord(x) >= th_ord
     int n_levels;                  // levels of this pass (<= kLevelsPerPass)
     long long A[kLevelsPerPass];   // level thresholds in units of 2^-60
     int rank[kLevelsPerPass];      // equal weights: 1-based rank reaching the level (M + 1: none)
@@ -88,74 +90,44 @@ __device__ __forceinline__ float exceed_value(long long units)
 
 // Batcher's odd-even merge sort on N (a power of two) slots, every
 // comparator ascending (min to the lower slot).  Slots MT..N-1 would hold
-// +inf and never move, so every comparator reaching them is left out: the
-// network sorts MT slots.  The merge levels (P, K) are template parameters,
-// so every slot index is a compile-time constant and the slots stay in
-// registers.
-// One comparator: the smaller value to slot i, the larger to slot k.  With
-// PAIRS the slots' member indices travel with their values; they are kept
-// as bytes, four to a register (id of slot i = byte i % 4 of word i / 4),
-// and exchanged by byte permutes, which halves the registers the indices
-// take next to 32-bit ones.
-__host__ __device__ constexpr unsigned swap_nibbles(int a, int b)
+// the largest value and never move, so every comparator reaching them is
+// left out: the network sorts MT slots.  The merge levels (P, K) are
+// template parameters, so every slot index is a compile-time constant and
+// the slots stay in registers.  The slots are FP32 values (equal weights)
+// or 32-bit keys (below).
+__device__ __forceinline__ void order2(float& x, float& y)
 {
-    unsigned s = 0x3210u;
-    s &= ~(0xFu << (4 * a));
-    s &= ~(0xFu << (4 * b));
-    return s | ((unsigned)b << (4 * a)) | ((unsigned)a << (4 * b));
+    const float lo = fminf(x, y);
+    y = fmaxf(x, y);
+    x = lo;
 }
-__host__ __device__ constexpr unsigned take_nibble(int dst, int src)  // byte dst <- byte src of y
+__device__ __forceinline__ void order2(uint32_t& x, uint32_t& y)
 {
-    return (0x3210u & ~(0xFu << (4 * dst))) | ((unsigned)(4 + src) << (4 * dst));
+    const uint32_t lo = min(x, y);
+    y = max(x, y);
+    x = lo;
 }
 
-template <bool PAIRS, int MT, int NW>
-__device__ __forceinline__ void compare_exchange(float (&v)[MT], uint32_t (&id)[NW], int i, int k)
-{
-    const bool sw = v[i] > v[k];
-    const float lo = fminf(v[i], v[k]);
-    v[k] = fmaxf(v[i], v[k]);
-    v[i] = lo;
-    if (PAIRS) {
-        const int wi = i >> 2, bi = i & 3, wk = k >> 2, bk = k & 3;
-        if (wi == wk) {
-            const uint32_t x = __byte_perm(id[wi], 0u, swap_nibbles(bi, bk));
-            id[wi] = sw ? x : id[wi];
-        } else {
-            const uint32_t xi = __byte_perm(id[wi], id[wk], take_nibble(bi, bk));
-            const uint32_t xk = __byte_perm(id[wk], id[wi], take_nibble(bk, bi));
-            id[wi] = sw ? xi : id[wi];
-            id[wk] = sw ? xk : id[wk];
-        }
-    }
-}
-
-template <bool PAIRS, int N, int MT, int P, int K, int NW>
-__device__ __forceinline__ void merge_level(float (&v)[MT], uint32_t (&id)[NW])
+template <typename T, int N, int MT, int P, int K>
+__device__ __forceinline__ void merge_level(T (&v)[MT])
 {
 #pragma unroll
     for (int j = K % P; j + K < N; j += 2 * K) {
 #pragma unroll
         for (int i = 0; i < K; ++i) {
             if (i + j + K < MT && (i + j) / (2 * P) == (i + j + K) / (2 * P))
-                compare_exchange<PAIRS, MT, NW>(v, id, i + j, i + j + K);
+                order2(v[i + j], v[i + j + K]);
         }
     }
-    if constexpr (K > 1) merge_level<PAIRS, N, MT, P, K / 2, NW>(v, id);
+    if constexpr (K > 1) merge_level<T, N, MT, P, K / 2>(v);
 }
 
-// Batcher's odd-even merge sort on N (a power of two) slots, every
-// comparator ascending (min to the lower slot).  Slots MT..N-1 would hold
-// +inf and never move, so every comparator reaching them is left out: the
-// network sorts MT slots.  The merge levels (P, K) are template parameters,
-// so every slot index is a compile-time constant and the slots stay in
-// registers.
-template <bool PAIRS, int N, int MT, int NW, int P = 1>
-__device__ __forceinline__ void odd_even_merge_sort(float (&v)[MT], uint32_t (&id)[NW])
+template <typename T, int N, int MT, int P = 1>
+__device__ __forceinline__ void odd_even_merge_sort(T (&v)[MT])
 {
     if constexpr (P < N) {
-        merge_level<PAIRS, N, MT, P, P, NW>(v, id);
-        odd_even_merge_sort<PAIRS, N, MT, NW, 2 * P>(v, id);
+        merge_level<T, N, MT, P, P>(v);
+        odd_even_merge_sort<T, N, MT, 2 * P>(v);
     }
 }
 
@@ -172,6 +144,20 @@ __device__ __forceinline__ float select_slot(const float (&v)[MT], int k)
             : "+f"(ans)
             : "f"(v[i]), "r"(k), "r"(i));
     return ans;
+}
+
+// An order-preserving map of FP32 bit patterns onto unsigned integers
+// (negative values reversed below the positive ones): for non-NaN x, y
+// other than the pair -0, +0, x < y iff ord(x) < ord(y); ord(-0) is one
+// below ord(+0).
+__device__ __forceinline__ uint32_t ord_of(float x)
+{
+    const uint32_t b = __float_as_uint(x);
+    return b ^ ((uint32_t)((int32_t)b >> 31) | 0x80000000u);
+}
+__device__ __forceinline__ float from_ord(uint32_t o)
+{
+    return __uint_as_float(o ^ ((uint32_t)((int32_t)~o >> 31) | 0x80000000u));
 }
 
 // Arguments of the staged kernel: the running maxima as a 3-D tensor map
@@ -192,27 +178,46 @@ __host__ __device__ constexpr int prod_stage_bytes() { return (MT * 32 * 4 + 127
 // maxima (every member of 32 cells) arrive by one tensor copy into the
 // warp's stage; the lanes read them into registers and the copy of the
 // warp's next group starts at once, so it lands while this group is
-// sorted.  The cell's MT slots (members, then +inf padding) are sorted in
-// registers; with equal weights the a-percentile is the value of the rank
-// that first reaches a (ranks from the host), otherwise the members travel
-// with their values through the sort and one prefix pass over their weights
-// finds, per level, the first sorted position whose cumulative weight
-// reaches it.  Tied values may come out in any order: the first position to
-// reach a level then still holds the tied value.  Every wait is bounded: one
-// that gives up records FLOOD_ERR_TIMEOUT in the error word, waits for the
-// warp's copy in flight and returns.
+// sorted.
+//
+// Equal weights: the cell's MT slots (members, then +inf padding) are
+// sorted as FP32 values and the a-percentile is the value of the rank that
+// first reaches a (ranks from the host).  Tied values may come out in any
+// order: the first position to reach a level then still holds the tied
+// value.
+//
+// Unequal weights: each member becomes one 32-bit key, its value's place
+// above the cell's smallest value in the high 25 bits and its index in the
+// low 7, so sorting the keys as integers orders the members and carries
+// their indices at the cost of a value sort.  The place is ord(x) - ord(min),
+// exact while the cell's values span fewer than 2^25 - 1 representable
+// FP32 numbers (about four binades); beyond that it is shifted right by the
+// fewest bits that fit, so values closer than 2^shift representable numbers
+// may share a place and come out in index order.  One pass over the sorted
+// keys sums the weights (exact integers) and keeps, per level, the key at
+// the first position whose cumulative weight reaches it, and the weight of
+// the members at or above the threshold.  A warp with a shifted lane keeps
+// its stage until that lane has settled each level exactly: the answer lies
+// among the members sharing the found key's place (every place below
+// holds smaller values, every place above larger ones), which a pass over
+// the staged values bounds; if they differ, candidates are tried in
+// increasing order against the exact weighted distribution function.  The
+// same lane sums the exceedance weight from the staged values.
+//
+// Every wait is bounded: one that gives up records FLOOD_ERR_TIMEOUT in the
+// error word, waits for the warp's copy in flight and returns.
 template <int MT, bool EQUAL>
-__global__ void __launch_bounds__(32 * kProdWarps, MT <= 96 ? (EQUAL ? 4 : 3) : 2)
+__global__ void __launch_bounds__(32 * kProdWarps, MT <= 96 ? 4 : 2)
     tma_products_kernel(const __grid_constant__ ProdTma t)
 {
     extern __shared__ unsigned char smem_raw[];
     const ProdArgs& a = t.a;
-    constexpr int NW = EQUAL ? 1 : (MT + 3) / 4;
     constexpr int kStage = prod_stage_bytes<MT>();
     constexpr long long kBudget = flood::kTmaWaitBudgetDefault;
-    __shared__ long long us[EQUAL ? 1 : MT];
+    constexpr uint32_t kPad = 0xFFFFFFFFu;   // key of a padding slot: index 127, no weight
+    __shared__ long long us[EQUAL ? 1 : 128];
     if (!EQUAL) {
-        for (int j = threadIdx.x; j < MT; j += blockDim.x) us[j] = j < a.M ? a.u[j] : 0;
+        for (int j = threadIdx.x; j < 128; j += blockDim.x) us[j] = j < a.M ? a.u[j] : 0;
         __syncthreads();
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -233,6 +238,15 @@ __global__ void __launch_bounds__(32 * kProdWarps, MT <= 96 ? (EQUAL ? 4 : 3) : 
         flood::mbar_arrive_expect_tx(bar, tx);
         flood::tma_load_3d(stage_s, &t.map, c0, r, 0, bar);
     };
+    // the next group's copy, once every lane has read the stage
+    auto release = [&](int g) {
+        __syncwarp();
+        const int gn = g + nwarps;
+        if (gn < t.n_groups && lane == 0) {
+            flood::fence_proxy_async_smem();
+            issue(gn);
+        }
+    };
     if (gw < t.n_groups && lane == 0) issue(gw);
     uint32_t phase = 0;
     constexpr int N = MT <= 32 ? 32 : MT <= 64 ? 64 : 128;   // the network's power of two
@@ -243,67 +257,125 @@ __global__ void __launch_bounds__(32 * kProdWarps, MT <= 96 ? (EQUAL ? 4 : 3) : 
             return;
         }
         phase ^= 1u;
-        float v[MT];
-        uint32_t id[NW];
-        long long ex = 0;
-        int cnt = 0;
+        const int r = g / t.groups_per_row, c = (g % t.groups_per_row) * 32 + lane;
+        const size_t out = (size_t)r * a.nx + c;
+        if constexpr (EQUAL) {
+            float v[MT];
 #pragma unroll
-        for (int j = 0; j < MT; ++j) {
-            const bool live = j < a.M;
-            const float x = live ? stage[j * 32 + lane] : __int_as_float(0x7f800000);
-            v[j] = x;
-        }
-        if (!EQUAL) {
-#pragma unroll
-            for (int q = 0; q < NW; ++q) id[q] = 0x03020100u + 0x04040404u * (uint32_t)q;
-        }
-        __syncwarp();  // every lane has read the stage: the next copy may overwrite it
-        const int gn = g + nwarps;
-        if (gn < t.n_groups && lane == 0) {
-            flood::fence_proxy_async_smem();
-            issue(gn);
-        }
-        odd_even_merge_sort<!EQUAL, N, MT, NW>(v, id);
-        if (EQUAL) {
+            for (int j = 0; j < MT; ++j)
+                v[j] = j < a.M ? stage[j * 32 + lane] : __int_as_float(0x7f800000);
+            release(g);
+            odd_even_merge_sort<float, N, MT>(v);
             // members at or above the threshold, counted on the sorted slots
             // (the +inf padding slots above M count too and are taken off);
             // counted while loading, the comparisons would keep the unsorted
             // values live through the sort
+            int cnt = 0;
 #pragma unroll
             for (int k = 0; k < MT; ++k) cnt += v[k] >= a.threshold;
             cnt -= MT - a.M;
-        }
-        const int r = g / t.groups_per_row, c = (g % t.groups_per_row) * 32 + lane;
-        if (c >= a.nx) continue;
-        const size_t out = (size_t)r * a.nx + c;
-        int pos[kLevelsPerPass];   // 0-based sorted position holding each level's value (>= M: none)
-        if (EQUAL) {
+            if (c >= a.nx) continue;
+            if (a.exceed) a.exceed[out] = exceed_value((long long)cnt * a.u_eq);
+            if (!a.pct) continue;
+            const float top = a.M == MT ? v[MT - 1] : select_slot<MT>(v, a.M - 1);
 #pragma unroll
-            for (int q = 0; q < kLevelsPerPass; ++q) pos[q] = a.rank[q] - 1;
+            for (int q = 0; q < kLevelsPerPass; ++q) {
+                if (q >= a.n_levels) break;
+                const int pos = a.rank[q] - 1;   // 0-based sorted position (>= M: none)
+                const float sel = select_slot<MT>(v, pos);
+                a.pct[(size_t)q * a.ny * a.nx + out] = pos < a.M ? sel : top;
+            }
         } else {
-            // one pass over the sorted slots: the weight at or above the
-            // threshold, and per level the slots whose cumulative weight
-            // stays below it (the padding slots weigh nothing)
+            uint32_t key[MT];
+            uint32_t omin = kPad, omax = 0u;
 #pragma unroll
-            for (int q = 0; q < kLevelsPerPass; ++q) pos[q] = 0;
-            long long P = 0;
+            for (int j = 0; j < MT; ++j) {
+                if (j < a.M) {
+                    const uint32_t o = ord_of(stage[j * 32 + lane]);
+                    key[j] = o;
+                    omin = min(omin, o);
+                    omax = max(omax, o);
+                } else {
+                    key[j] = kPad;
+                }
+            }
+            const uint32_t d = omax - omin;
+            int sh = max(0, 7 - __clz(d));              // bits of d above 25
+            if ((d >> sh) == 0x1FFFFFFu) ++sh;          // keeps real keys below kPad
+            const bool exact = sh == 0;
+            const bool early = __all_sync(0xffffffffu, exact);
+            if (early) release(g);
+#pragma unroll
+            for (int j = 0; j < MT; ++j)
+                if (j < a.M) key[j] = (((key[j] - omin) >> sh) << 7) | (uint32_t)j;
+            odd_even_merge_sort<uint32_t, N, MT>(key);
+            // the threshold as a key (exact places)
+            const uint32_t kth = a.th_ord <= omin ? 0u : a.th_ord > omax ? kPad : (a.th_ord - omin) << 7;
+            long long P = 0, ex = 0;
+            uint32_t kc[kLevelsPerPass];
+#pragma unroll
+            for (int q = 0; q < kLevelsPerPass; ++q) kc[q] = kPad;
 #pragma unroll
             for (int k = 0; k < MT; ++k) {
-                const long long uk = us[(id[EQUAL ? 0 : k >> 2] >> (8 * (k & 3))) & 0xffu];
+                const long long uk = us[key[k] & 0x7Fu];
+#pragma unroll
+                for (int q = 0; q < kLevelsPerPass; ++q) kc[q] = P < a.A[q] ? key[k] : kc[q];
                 P += uk;
-                if (v[k] >= a.threshold) ex += uk;
-#pragma unroll
-                for (int q = 0; q < kLevelsPerPass; ++q) pos[q] += P < a.A[q];
+                ex += key[k] >= kth ? uk : 0;
             }
-        }
-        if (a.exceed) a.exceed[out] = exceed_value(EQUAL ? (long long)cnt * a.u_eq : ex);
-        if (!a.pct) continue;
-        const float top = a.M == MT ? v[MT - 1] : select_slot<MT>(v, a.M - 1);
+            // per level the ord of the answer (none reached: the largest value)
+            uint32_t oq[kLevelsPerPass];
 #pragma unroll
-        for (int q = 0; q < kLevelsPerPass; ++q) {
-            if (q >= a.n_levels) break;
-            const float sel = select_slot<MT>(v, pos[q]);
-            a.pct[(size_t)q * a.ny * a.nx + out] = pos[q] < a.M ? sel : top;
+            for (int q = 0; q < kLevelsPerPass; ++q) oq[q] = P < a.A[q] ? omax : (kc[q] >> 7) + omin;
+            if (!early) {
+                if (!exact) {
+                    uint32_t lo[kLevelsPerPass], hi[kLevelsPerPass];
+#pragma unroll
+                    for (int q = 0; q < kLevelsPerPass; ++q) {
+                        lo[q] = kPad;
+                        hi[q] = 0u;
+                    }
+                    ex = 0;
+                    for (int j = 0; j < a.M; ++j) {
+                        const uint32_t o = ord_of(stage[j * 32 + lane]);
+                        const uint32_t place = (o - omin) >> sh;
+                        if (o >= a.th_ord) ex += us[j];
+#pragma unroll
+                        for (int q = 0; q < kLevelsPerPass; ++q) {
+                            if (place == kc[q] >> 7) {
+                                lo[q] = min(lo[q], o);
+                                hi[q] = max(hi[q], o);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < kLevelsPerPass; ++q) {
+                        if (q >= a.n_levels || P < a.A[q]) continue;
+                        uint32_t v = lo[q];
+                        for (int it = 0; it < a.M && v != hi[q]; ++it) {
+                            long long W = 0;
+                            uint32_t nxt = hi[q];
+                            for (int j = 0; j < a.M; ++j) {
+                                const uint32_t o = ord_of(stage[j * 32 + lane]);
+                                if (o <= v) W += us[j];
+                                else nxt = min(nxt, o);
+                            }
+                            if (W >= a.A[q]) break;
+                            v = nxt;
+                        }
+                        oq[q] = v;
+                    }
+                }
+                release(g);
+            }
+            if (c >= a.nx) continue;
+            if (a.exceed) a.exceed[out] = exceed_value(ex);
+            if (!a.pct) continue;
+#pragma unroll
+            for (int q = 0; q < kLevelsPerPass; ++q) {
+                if (q >= a.n_levels) break;
+                a.pct[(size_t)q * a.ny * a.nx + out] = from_ord(oq[q]);
+            }
         }
     }
 }
@@ -526,6 +598,13 @@ extern "C" int flood_ensemble_products(flood_grid* g, double threshold, int n_le
     a.ny = g->ny; a.nx = g->nx; a.ld = g->ld;
     a.plane = g->plane;
     a.threshold = (float)threshold;
+    {
+        // the order-preserving map of the kernels' keys; a zero threshold
+        // takes ord(-0), so that -0 and +0 both reach it
+        uint32_t b = 0;
+        std::memcpy(&b, &a.threshold, 4);
+        a.th_ord = a.threshold == 0.0f ? 0x7FFFFFFFu : b ^ ((uint32_t)((int32_t)b >> 31) | 0x80000000u);
+    }
     a.u_eq = u[0];
     // one pass per kLevelsPerPass levels (at least one: the exceedance map)
     for (int q0 = 0; q0 == 0 || q0 < n_levels; q0 += kLevelsPerPass) {

@@ -163,3 +163,55 @@ def test_products_every_kernel_path_bit_for_bit(capi, M, equal):
     assert np.array_equal(exceed, prod.exceedance(hm, w, 0.003))
     assert np.array_equal(pct, prod.percentiles(hm, w, levels))
     assert 0 < exceed.max() <= 1.0
+
+
+@pytest.mark.parametrize("M", [96, 100, 128])
+def test_weighted_keys_on_crafted_maxima(capi, M):
+    """Maxima set directly (the tracked maximum starts at the members'
+    depths) to the cases the unequal-weights kernel treats apart: cells
+    whose values span many binades (shifted keys: values one FP32 step
+    apart share a place, in index order against the value order), cells
+    within one binade (exact keys), exact ties, -0 beside +0, negative
+    values, a threshold equal to members' values, and dyadic weights whose
+    prefix sums hit the levels exactly.  The maps equal the oracle's, bit
+    for bit, with unequal and with equal weights."""
+    ny, nx = 4, 70
+    rng = np.random.default_rng(M)
+    hm = np.zeros((M, ny, nx), np.float32)
+    mags = np.array([0.0, 1e-30, 1e-6, 1e-3, 0.2, 0.5, 3.0], np.float32)
+    hm[:, 0] = rng.choice(mags, (M, nx)) * rng.uniform(1, 1.01, (M, nx)).astype(np.float32)
+    hm[:, 1] = rng.uniform(0.2, 0.3, (M, nx)).astype(np.float32)
+    hm[:, 2] = rng.choice(np.array([-0.5, -0.0, 0.0, 1e-30, 0.2], np.float32), (M, nx))
+    hm[:, 3] = np.float32(0.25)
+    hm[:, 3, ::3] = 0.0
+    hm[: M // 2, 3, 1::3] = np.float32(0.2)
+    # near ties: in rows 0 and 1 the higher index of a pair holds the smaller value
+    for i in range(0, M - 1, 5):
+        for r in (0, 1):
+            v = hm[i + 1, r]
+            hm[i, r] = np.nextafter(v, np.float32(np.inf))
+    hm[1::7, 1, ::2] = np.float32(0.2)         # the threshold itself
+    k = rng.integers(1, 40, M)
+    k[::11] = 0                                 # weightless members
+    k = k * 8192 // k.sum()
+    k[np.flatnonzero(k)[: 8192 - k.sum()]] += 1
+    w = k / 8192.0                              # dyadic: the prefix sums are exact
+    levels = (0.05, 0.1, 0.5, 0.77, 0.9, 1.0, float(np.cumsum(w)[M // 3]), float(np.cumsum(w)[M // 2]))
+    hy = synth.hyetograph_constant(0.0, 60.0)
+    terr = synth.make_terrain(ny, nx, seed=56)
+    with capi.Grid(terr.z, terr.n) as g:
+        g.ensemble_init(M, np.ones(M, np.float32), np.ones(M, np.float32), hy)
+        for m in range(M):
+            g.set_state(m, h=hm[m])
+        g.track_max_depth(True)
+        got_hm = np.array([g.max_depth(m) for m in range(M)])
+        g.set_members(weights=w)
+        res = {th: g.ensemble_products(th, levels) for th in (0.2, 0.0)}
+        g.set_members(weights=np.full(M, 1.0 / M))
+        eq = g.ensemble_products(0.2, levels)
+    assert np.array_equal(got_hm.view(np.uint32), hm.view(np.uint32))
+    for th, (exceed, pct) in res.items():
+        assert np.array_equal(exceed, prod.exceedance(hm, w, th)), th
+        assert np.array_equal(pct, prod.percentiles(hm, w, levels)), th
+    assert np.array_equal(eq[0], prod.exceedance(hm, np.full(M, 1.0 / M), 0.2))
+    assert np.array_equal(eq[1], prod.percentiles(hm, np.full(M, 1.0 / M), levels))
