@@ -66,8 +66,8 @@ def parse():
                     help="skip the adjoint and uneven-batch measurements")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch configuration (profiling runs)")
-    ap.add_argument("--only", choices=["adjoint", "batch", "calibration", "land_cover",
-                                       "masked_domain", "products"],
+    ap.add_argument("--only", choices=["adjoint", "batch", "batch_land_cover", "calibration",
+                                       "land_cover", "masked_domain", "products"],
                     help="run one extension measurement alone and print it (profiling runs)")
     ap.add_argument("--calibration-windows", type=int, default=3)
     ap.add_argument("--rows-per-strip", type=int, default=None,
@@ -324,17 +324,21 @@ def adjoint_measure(capi):
             "adj_over_fwd": res["reverse_ms"] / res["forward_ms"]}
 
 
-def batch_measure(capi, engine=None, rows=None, tune=False, members=1):
+def batch_measure(capi, engine=None, rows=None, tune=False, members=1, land_cover=False):
     """Uneven batch: 64 scenarios, square sides U{512..2048}, own DEM seeds,
     rain U[20, 100] mm/h, durations U[900, 3600] s, advanced in 300 s windows
     by graph-replayed batched launches; member-cell-steps/s over the batch.
     members > 1: that many members per scenario (rain multiplier LN(0, 0.3),
     Manning scale U[0.6, 1.4] each), sharing the scenario's bed and
-    roughness tile by tile."""
+    roughness tile by tile.  land_cover: every scenario with its own land
+    cover (Section 4.1: roads and buildings hardened and drained, ponds,
+    green land, two corners outside the domain) and each member with its
+    own class roughness and drainage rate."""
     import torch
     from paper_2302_08341_gb300 import synth
     scen = synth.uneven_batch(64)
     terrs = [synth.make_terrain(s.ny, s.nx, seed=s.seed) for s in scen]
+    clss = [synth.land_cover(t, seed=s.seed) for t, s in zip(terrs, scen)] if land_cover else None
     hys = [synth.hyetograph_constant(s.rain_mm_h, s.duration_s) for s in scen]
     dur = np.array([s.duration_s for s in scen])
     counts = np.full(len(scen), members, np.int32)
@@ -344,9 +348,24 @@ def batch_measure(capi, engine=None, rows=None, tune=False, members=1):
         rm = sc = np.ones(len(scen), np.float32)
     mkw = {"members": counts} if members > 1 else {}
     cells = np.repeat(np.array([s.ny * s.nx for s in scen], np.float64), counts)
+    first = np.concatenate([[0], np.cumsum(counts)])
+    if land_cover:
+        outside = np.array([c[3] for c in synth.LAND_CLASSES], bool)
+        active = np.repeat(np.array([float((~outside[c]).sum()) for c in clss]), counts)
+        n_m, d_m = synth.land_prior(SEED + 65, int(counts.sum()))
     dur_m = np.repeat(dur, counts)
     tuned = None
+
+    def init(b):
+        b.init(hys, rm, sc, dur, **mkw)
+        if land_cover:
+            for i in range(len(scen)):
+                b.set_land_params(i, n_m[first[i]:first[i + 1]], d_m[first[i]:first[i + 1]])
+
     with capi.Batch([t.z for t in terrs], [t.n for t in terrs]) as b:
+        if land_cover:
+            for i, c in enumerate(clss):
+                b.set_land_cover(i, c, synth.LAND_CLASSES)
         if engine is not None:
             b.set_engine(engine)
         else:
@@ -354,13 +373,13 @@ def batch_measure(capi, engine=None, rows=None, tune=False, members=1):
         rows = rows or ROWS
         if rows:
             b.set_launch(rows, 4)
-        b.init(hys, rm, sc, dur, **mkw)
+        init(b)
         b.step(300.0)                      # warm-up window (graph capture)
         if tune:                           # on the live batch after the first window
             r, w, e, t = b.autotune(30.0)
             tuned = {"rows_per_strip": r, "warps_per_cta": w, "engine": e, "trial_ms": t}
             engine, rows = e, r
-        b.init(hys, rm, sc, dur, **mkw)
+        init(b)
         stream = torch.cuda.current_stream()
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
         l0 = b.launch_count
@@ -374,6 +393,11 @@ def batch_measure(capi, engine=None, rows=None, tune=False, members=1):
         mem = b.members()
         launches = b.launch_count - l0
     units = float((mem["steps"] * cells).sum())
+    extra = {}
+    if land_cover:
+        extra = {"land_cover": "4 classes per scenario, per-member class roughness and drainage",
+                 "active_value": float((mem["steps"] * active).sum()) / (ms * 1e-3),
+                 "active_frac": float(active.sum() / cells.sum())}
     form = {0: "direct loads, CUDA-graph replayed per-step launches",
             1: "TMA-staged rows, CUDA-graph replayed per-step launches",
             2: "TMA-staged rows, one persistent cooperative launch per window"}[engine]
@@ -386,7 +410,7 @@ def batch_measure(capi, engine=None, rows=None, tune=False, members=1):
             "all_finished": bool(np.all(mem["t"] == dur_m)), "gpu_launches": launches,
             "engine": {0: "direct loads", 1: "tma", 2: "tma persistent"}[engine],
             "engine_id": engine,
-            "rows_per_strip": rows or 64, "autotune": tuned}
+            "rows_per_strip": rows or 64, "autotune": tuned, **extra}
 
 
 def calibration_measure(capi, windows=3):
@@ -1008,6 +1032,11 @@ def run_gb300(args):
             # 24 B of state per member-cell-step, the bed and roughness once per tile of 4
             bm["hbm_frac_whole_window"] = bm["value"] * (BYTES_STATE + BYTES_STATIC / 4) / 1e9 / hbm_peak
         extensions["batched"]["four_members"] = bm
+        bl = guarded(batch_measure, capi, tune=True, members=4, land_cover=True)
+        if "error" not in bl:
+            bl["hbm_frac_whole_window"] = (bl["active_value"] * (BYTES_STATE + BYTES_STATIC / 4)
+                                           / 1e9 / hbm_peak)
+        extensions["batched"]["land_cover"] = bl
         extensions["calibration"] = guarded(calibration_measure, capi,
                                             windows=args.calibration_windows)
         extensions["land_cover"] = guarded(land_cover_measure, capi)
@@ -1057,6 +1086,9 @@ def run_only(args):
         res = adjoint_measure(capi)
     elif args.only == "batch":
         res = batch_measure(capi, engine=args.engine, tune=args.engine is None and not ROWS)
+    elif args.only == "batch_land_cover":
+        res = batch_measure(capi, engine=args.engine, tune=args.engine is None and not ROWS,
+                            members=4, land_cover=True)
     elif args.only == "land_cover":
         res = land_cover_measure(capi)
     elif args.only == "masked_domain":

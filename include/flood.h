@@ -279,8 +279,8 @@ int flood_flow_sample(flood_grid* g, int n_sections, const flood_section* sectio
  * multiplier's gradient weighs each cell by its runoff coefficient, and a
  * cell that drainage emptied (h* > 0 and h' = 0) passes no sensitivity, like
  * a clamped one; the drainage rate's gradient comes from flood_adjoint_land_grad.
- * Not covered: the batched
- * API, a roughness factor field (refused either way). */
+ * Not covered: a roughness factor field (refused either way).  Batches of
+ * scenarios take land cover through flood_batch_set_land_cover. */
 typedef struct {
     float n;        /* Manning n of the class (s m^-1/3), > 0 */
     float runoff;   /* share of the rain that stays on the surface, [0, 1] */
@@ -598,6 +598,31 @@ int64_t flood_batch_launch_count(const flood_batch* b);
  * flood_batch_step. */
 int flood_batch_autotune(flood_batch* b, double trial_s, int* best_rows, int* best_warps,
                          int* best_engine, double* best_ms, void* stream);
+
+/* Land cover of scenario `scen` (Section 4.1; the same classes, rules and
+ * arithmetic as flood_set_land_cover on a grid): cls [ny][nx] uint8
+ * (< n_classes <= 4), host or device.  Set before flood_batch_init, for
+ * every scenario of the batch or for none (flood_batch_init refuses a mix).
+ * The bed of cells outside the domain is raised out of reach and they get
+ * no rain; the tiles (128 columns x the strip height) that hold no cell of
+ * the domain are not scheduled.  Each member starts with the classes' n and
+ * no drainage at every flood_batch_init.  Synchronous.  Errors:
+ * FLOOD_ERR_ARG, FLOOD_ERR_STATE (after flood_batch_init, or set twice),
+ * FLOOD_ERR_OOM. */
+int flood_batch_set_land_cover(flood_batch* b, int scen, const uint8_t* cls, int n_classes,
+                               const flood_land_class* classes);
+
+/* Land-cover parameters of the members of scenario `scen`: n_class
+ * [members][n_classes] (> 0) and drain_rate [members] (m/s, >= 0), host or
+ * device; either may be NULL (kept).  Synchronous.  Errors: FLOOD_ERR_STATE
+ * (no land cover, or before flood_batch_init), FLOOD_ERR_ARG. */
+int flood_batch_set_land_params(flood_batch* b, int scen, const float* n_class,
+                                const float* drain_rate);
+
+/* Volume removed by drainage so far, per member [sum of the members] FP64
+ * (m^3; zeros without land cover); storage = rain - outflow + clamp -
+ * drained.  Synchronous. */
+int flood_batch_drained_volume(flood_batch* b, double* drained);
 
 /* ==== Allocation-free volume reduction ======================================
  * The paper has no counterpart: this is a service for callers that cannot

@@ -36,7 +36,8 @@ EXPORTED = ["flood_default_params", "flood_last_error", "flood_create_grid", "fl
             "flood_ensemble_products", "flood_set_land_cover", "flood_set_land_params",
             "flood_get_land_params", "flood_drained_volume", "flood_flow_sample", "flood_set_inflow",
             "flood_inflow_volume", "flood_batch_autotune", "flood_batch_set_wait_budget",
-            "flood_adjoint_land_grad", "flood_batch_init_members", "flood_batch_get_member_state"]
+            "flood_adjoint_land_grad", "flood_batch_init_members", "flood_batch_get_member_state",
+            "flood_batch_set_land_cover", "flood_batch_set_land_params", "flood_batch_drained_volume"]
 
 
 class LandClass(C.Structure):
@@ -157,6 +158,9 @@ def lib(path: str = LIB_PATH):
     L.flood_batch_get_member_state.argtypes = [_VP, C.c_int, C.c_int, _VP, _VP, _VP, _VP]
     L.flood_batch_init_members.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]
     L.flood_batch_members.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _VP]
+    L.flood_batch_set_land_cover.argtypes = [_VP, C.c_int, _VP, C.c_int, C.POINTER(LandClass)]
+    L.flood_batch_set_land_params.argtypes = [_VP, C.c_int, _VP, _VP]
+    L.flood_batch_drained_volume.argtypes = [_VP, _VP]
     L.flood_batch_launch_count.argtypes = [_VP]
     L.flood_batch_launch_count.restype = C.c_int64
     for name in EXPORTED:
@@ -657,6 +661,31 @@ class Batch:
         _bcheck(lib().flood_batch_members(self.h, *(out[k].ctypes.data for k in
                                                      ("t", "steps", "storage", "rain", "outflow",
                                                       "clamp"))), self.h)
+        return out
+
+    def set_land_cover(self, i, cls, classes):
+        """Land cover of scenario i (flood_batch_set_land_cover): cls [ny][nx]
+        uint8; classes: list of (n, runoff, drains, outside) tuples.  Before
+        init, for every scenario or none."""
+        cls = np.ascontiguousarray(cls, dtype=np.uint8)
+        tab = (LandClass * len(classes))(*[LandClass(float(n), float(r), int(d), int(o))
+                                           for n, r, d, o in classes])
+        _bcheck(lib().flood_batch_set_land_cover(self.h, int(i), cls.ctypes.data, len(classes), tab),
+                self.h)
+
+    def set_land_params(self, i, n_class=None, drain_rate=None):
+        """Per-member class roughness [members][n_classes] and drainage rates
+        [members] of scenario i (flood_batch_set_land_params)."""
+        nc = None if n_class is None else np.ascontiguousarray(n_class, np.float32)
+        dr = None if drain_rate is None else np.ascontiguousarray(drain_rate, np.float32)
+        _bcheck(lib().flood_batch_set_land_params(self.h, int(i), None if nc is None else nc.ctypes.data,
+                                                  None if dr is None else dr.ctypes.data), self.h)
+
+    def drained(self):
+        """Drained volume per member, scenario by scenario (FP64, m^3)."""
+        S = int(np.sum(getattr(self, "members_per", np.ones(self.S))))
+        out = np.zeros(S)
+        _bcheck(lib().flood_batch_drained_volume(self.h, out.ctypes.data), self.h)
         return out
 
     @property

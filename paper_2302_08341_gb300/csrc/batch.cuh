@@ -16,8 +16,32 @@ struct ScenDesc {
     int ny, nx, ld, nb;
     float rain_mult, scale;
     double t_end;          // the scenario's own end time
-    double ncell;
+    double ncell;          // cells the rain falls on (with land cover: the sum of runoff shares)
+    // land cover (Section 4.1; lc = 0: none): the scenario's class of every
+    // cell and per-class runoff share and drainage flag, the member's
+    // Manning n of every class and drainage rate
+    const uint8_t* cls;    // [ny][ld]
+    float lc_n[4];
+    float lc_runoff[4];
+    float lc_drains[4];
+    float lc_drain;        // m/s
+    int lc;
 };
+
+// The land-cover tables of a member for one step, as for the ensemble's
+// members (land_k): lane q of every group of four holds class q's entries,
+// read from the descriptor in global memory (indexed by lane, a copy in
+// registers would move to local memory).
+__device__ __forceinline__ LandK batch_land_k(const ScenDesc* sd, float dr, double dt, int lane)
+{
+    LandK lk;
+    lk.cls = sd->cls;
+    const int q = lane & 3;
+    lk.n = sd->lc_n[q];
+    lk.dr = __fmul_rn(dr, sd->lc_runoff[q]);
+    lk.dd = __fmul_rn(__fmul_rn(sd->lc_drain, sd->lc_drains[q]), (float)dt);
+    return lk;
+}
 
 // One warp's work: a 128-column span of rows [r0, r1) of one scenario.
 struct WarpTask {
@@ -36,12 +60,15 @@ struct BatchArgs {
     const double* t_stop;      // window end (device scalar, so captured graphs are reusable)
     MemberPlan* plan;          // [S] this step's plans
     double* vacc;              // [nslot_total][2]
+    double* dacc;              // [nslot_total] drained volume partials (land cover)
+    int lc;                    // every scenario has land cover (0: none has)
     double* rain_acc;          // [S]
     int* err;
     double alpha_dx, g, dt_cap, dt_fixed, h_floor, rain_block, dxd, cell_area;
     float h_eps, edge_drop;
     int limiter, east_out, south_out;
-    const CUtensorMap* maps;   // [S][2] per scenario: state (ld, ny, 6 planes), z and n (ld, ny, 2)
+    const CUtensorMap* maps;   // [S][2] per entry: state (ld, ny, 6 planes); z and n, or with
+                               // land cover z and the class codes (ld, ny, 2)
 };
 
 // The persistent form: one cooperative launch loops plan phase -> grid

@@ -2,6 +2,7 @@
 // the flat warp-task table, and the step driver that replays a CUDA graph of
 // kGraphSteps step launches until every scenario has reached the window end.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -67,6 +68,17 @@ struct flood_batch {
     int64_t k = 0, launches = 0;
     cudaGraphExec_t graph = nullptr;
     cudaStream_t cap_stream = nullptr;
+    // land cover per scenario (Section 4.1), set before flood_batch_init for
+    // every scenario or for none
+    std::vector<int> lc;                        // 1: the scenario has land cover
+    std::vector<uint8_t*> cls8;                 // class of every cell [ny][ld]
+    std::vector<float*> zc;                     // bed and class codes [2][ny][ld] (TMA engines)
+    std::vector<int> lc_K;                      // classes
+    std::vector<std::array<float, 4>> lc_runoff, lc_drains, lc_n0;
+    std::vector<double> lc_rain_cells;          // sum of the runoff shares over the cells
+    std::vector<std::vector<uint8_t>> span_out; // [ny][spans]: 1 where a row's span lies outside
+    double* dacc = nullptr;                     // [nslot] drained volume partials
+    bool lc_all = false;                        // every scenario has land cover
     std::string msg;
 };
 
@@ -108,8 +120,17 @@ int build_tasks(flood_batch* b)
     for (int sc = 0; sc < b->n_scen; ++sc) {
         const int e0 = b->first[sc], e1 = b->first[sc + 1];
         const int spans = (b->nx[e0] + kSpan - 1) / kSpan;
+        const bool skip = b->lc[sc] && !b->span_out[sc].empty();
         for (int r0 = 0; r0 < b->ny[e0]; r0 += b->rows_per_strip)
-            for (int sp = 0; sp < spans; ++sp)
+            for (int sp = 0; sp < spans; ++sp) {
+                // land cover: a tile wholly outside the domain stays dry and
+                // at rest, so it is not scheduled (the same results)
+                if (skip) {
+                    bool out = true;
+                    const int r1 = std::min(r0 + b->rows_per_strip, b->ny[e0]);
+                    for (int r = r0; out && r < r1; ++r) out = b->span_out[sc][(size_t)r * spans + sp] != 0;
+                    if (out) continue;
+                }
                 for (int e = e0; e < e1; ++e) {
                     flood::WarpTask t;
                     t.scen = e;
@@ -121,11 +142,12 @@ int build_tasks(flood_batch* b)
                     slots[e].push_back((int)b->tasks.size());
                     b->tasks.push_back(t);
                 }
+            }
     }
     // volume slots: each entry's tasks own consecutive slots
     int slot = 0;
     for (int e = 0; e < b->S; ++e) {
-        b->slot0[e] = slot;
+        b->slot0[e] = slots[e].empty() ? -1 : slot;  // -1: no tile of the entry is scheduled
         for (int ti : slots[e]) b->tasks[ti].slot = slot++;
     }
     if (b->d_tasks) cudaFree(b->d_tasks);
@@ -139,6 +161,10 @@ int build_tasks(flood_batch* b)
     b->vacc = nullptr;
     BCK(b, cudaMalloc(&b->vacc, sizeof(double) * nw.size()));
     BCK(b, cudaMemcpy(b->vacc, nw.data(), sizeof(double) * nw.size(), cudaMemcpyHostToDevice));
+    if (b->dacc) cudaFree(b->dacc);
+    b->dacc = nullptr;
+    BCK(b, cudaMalloc(&b->dacc, sizeof(double) * std::max(slot, 1)));
+    BCK(b, cudaMemset(b->dacc, 0, sizeof(double) * std::max(slot, 1)));
     b->nslot = slot;
     drop_graph(b);
     return FLOOD_OK;
@@ -172,6 +198,8 @@ flood::BatchArgs batch_args(const flood_batch* b, int64_t k)
     a.east_out = b->p.east_outflow;
     a.south_out = b->p.south_outflow;
     a.maps = b->d_maps;
+    a.dacc = b->dacc;
+    a.lc = b->lc_all ? 1 : 0;
     return a;
 }
 
@@ -255,7 +283,15 @@ int set_entries(flood_batch* b, const std::vector<int>& counts)
             d.rain_mult = 1.0f;
             d.scale = 1.0f;
             d.t_end = 0.0;
-            d.ncell = (double)b->sny[sc] * b->snx[sc];
+            d.ncell = b->lc[sc] ? b->lc_rain_cells[sc] : (double)b->sny[sc] * b->snx[sc];
+            d.lc = b->lc[sc];
+            d.cls = b->lc[sc] ? b->cls8[sc] : nullptr;
+            for (int q = 0; q < 4; ++q) {
+                d.lc_n[q] = b->lc[sc] ? b->lc_n0[sc][q] : 0.0f;
+                d.lc_runoff[q] = b->lc[sc] ? b->lc_runoff[sc][q] : 1.0f;
+                d.lc_drains[q] = b->lc[sc] ? b->lc_drains[sc][q] : 0.0f;
+            }
+            d.lc_drain = 0.0f;
         }
     BCK(b, cudaMalloc(&b->ms, sizeof(MemberClock) * 3 * S));
     BCK(b, cudaMemset(b->ms, 0, sizeof(MemberClock) * 3 * S));
@@ -266,7 +302,8 @@ int set_entries(flood_batch* b, const std::vector<int>& counts)
     BCK(b, cudaMalloc(&b->d_desc, sizeof(flood::ScenDesc) * S));
     BCK(b, cudaMemcpy(b->d_desc, b->desc.data(), sizeof(flood::ScenDesc) * S, cudaMemcpyHostToDevice));
     // tensor maps of every entry for the TMA-staged step (direct loads if the
-    // encoder is unavailable): its own state, its scenario's bed and roughness
+    // encoder is unavailable): its own state, its scenario's bed and
+    // roughness (with land cover: the bed and the class codes)
     std::vector<CUtensorMap> maps((size_t)2 * S);
     bool ok = b->tma_ok;
     for (int e = 0; ok && e < S; ++e) {
@@ -274,8 +311,8 @@ int set_entries(flood_batch* b, const std::vector<int>& counts)
         const uint64_t s1 = sizeof(float) * b->ld[e], s2 = sizeof(float) * b->desc[e].plane;
         ok = flood::encode_map_3d(&maps[2 * e], b->state[e], b->ld[e], b->ny[e], 6, s1, s2,
                                   flood::tma_box_cols(), 1, 3) == 0 &&
-             flood::encode_map_3d(&maps[2 * e + 1], b->zn[sc], b->ld[e], b->ny[e], 2, s1, s2,
-                                  flood::tma_box_cols(), 1, 2) == 0;
+             flood::encode_map_3d(&maps[2 * e + 1], b->lc[sc] ? b->zc[sc] : b->zn[sc], b->ld[e],
+                                  b->ny[e], 2, s1, s2, flood::tma_box_cols(), 1, 2) == 0;
     }
     if (ok) {
         BCK(b, cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * maps.size()));
@@ -285,6 +322,22 @@ int set_entries(flood_batch* b, const std::vector<int>& counts)
         b->engine = 0;
     }
     return build_tasks(b);
+}
+
+// Each entry's volume sums (outflow, clamp; drained) into the first slot of
+// its tasks, the other slots zeroed (after the task table changed).
+int put_entry_sums(flood_batch* b, const std::vector<double>& per, const std::vector<double>& dper)
+{
+    std::vector<double> v((size_t)b->nslot * 2, 0.0), dv(std::max(b->nslot, 1), 0.0);
+    for (int i = 0; i < b->S; ++i) {
+        if (b->slot0[i] < 0) continue;  // no task: nothing was summed
+        v[(size_t)b->slot0[i] * 2] = per[(size_t)i * 2];
+        v[(size_t)b->slot0[i] * 2 + 1] = per[(size_t)i * 2 + 1];
+        dv[b->slot0[i]] = dper[i];
+    }
+    BCK(b, cudaMemcpy(b->vacc, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice));
+    BCK(b, cudaMemcpy(b->dacc, dv.data(), sizeof(double) * dv.size(), cudaMemcpyHostToDevice));
+    return FLOOD_OK;
 }
 
 }  // namespace
@@ -317,6 +370,15 @@ int flood_batch_create(flood_batch** out, int n, const int32_t* ny, const int32_
     b->sld.resize(n);
     b->zn.assign(n, nullptr);
     b->hyeto.assign(n, nullptr);
+    b->lc.assign(n, 0);
+    b->cls8.assign(n, nullptr);
+    b->zc.assign(n, nullptr);
+    b->lc_K.assign(n, 0);
+    b->lc_runoff.assign(n, {1.0f, 1.0f, 1.0f, 1.0f});
+    b->lc_drains.assign(n, {0.0f, 0.0f, 0.0f, 0.0f});
+    b->lc_n0.assign(n, {0.05f, 0.05f, 0.05f, 0.05f});
+    b->lc_rain_cells.assign(n, 0.0);
+    b->span_out.assign(n, {});
     auto bad = [&](cudaError_t e) {
         g_batch_msg = std::string("flood_batch_create: ") + cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? FLOOD_ERR_OOM : FLOOD_ERR_CUDA;
@@ -369,8 +431,11 @@ int flood_batch_destroy(flood_batch* b)
     for (float* p : b->zn) if (p) cudaFree(p);
     for (float* p : b->state) if (p) cudaFree(p);
     for (float* p : b->hyeto) if (p) cudaFree(p);
+    for (float* p : b->zc) if (p) cudaFree(p);
+    for (uint8_t* p : b->cls8) if (p) cudaFree(p);
     void* bufs[] = {b->d_desc, b->d_tasks, b->ms, b->vacc, b->rain_acc, b->storage, b->part,
-                    b->err, b->t_stop, b->plan, b->d_maps, b->pbar, b->pact, b->pdone, b->pdiag};
+                    b->err, b->t_stop, b->plan, b->d_maps, b->pbar, b->pact, b->pdone, b->pdiag,
+                    b->dacc};
     for (void* p : bufs) if (p) cudaFree(p);
     delete b;
     return FLOOD_OK;
@@ -397,6 +462,10 @@ int flood_batch_init_members(flood_batch* b, const float* const* hyetographs,
         total += n_members[i];
     }
     if (total > (1 << 20)) return bfail(b, FLOOD_ERR_ARG, "more than 2^20 members in all");
+    const int n_lc = (int)std::count(b->lc.begin(), b->lc.end(), 1);
+    if (n_lc != 0 && n_lc != b->n_scen)
+        return bfail(b, FLOOD_ERR_STATE, "land cover must be set for every scenario or for none");
+    b->lc_all = n_lc == b->n_scen;
     bool same = (int)total == b->S;
     for (int i = 0; same && i < b->n_scen; ++i) same = b->first[i + 1] - b->first[i] == counts[i];
     int rc;
@@ -419,6 +488,8 @@ int flood_batch_init_members(flood_batch* b, const float* const* hyetographs,
         d.rain_mult = rm[e];
         d.scale = sc[e];
         d.t_end = t_end[i];
+        for (int q = 0; q < 4; ++q) d.lc_n[q] = b->lc[i] ? b->lc_n0[i][q] : 0.0f;
+        d.lc_drain = 0.0f;
         BCK(b, cudaMemsetAsync(b->state[e], 0, sizeof(float) * 6 * d.plane, s));
     }
     BCK(b, cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(flood::ScenDesc) * b->S,
@@ -428,10 +499,12 @@ int flood_batch_init_members(flood_batch* b, const float* const* hyetographs,
     BCK(b, cudaMemcpyAsync(b->ms, ms.data(), sizeof(MemberClock) * 3 * b->S, cudaMemcpyHostToDevice, s));
     BCK(b, cudaMemsetAsync(b->rain_acc, 0, sizeof(double) * b->S, s));
     BCK(b, cudaMemsetAsync(b->vacc, 0, sizeof(double) * b->nslot * 2, s));
+    BCK(b, cudaMemsetAsync(b->dacc, 0, sizeof(double) * std::max(b->nslot, 1), s));
     BCK(b, cudaMemsetAsync(b->err, 0, sizeof(int), s));
     BCK(b, cudaStreamSynchronize(s));
     b->k = 0;
     b->initialised = true;
+    drop_graph(b);  // the launches depend on land cover being on
     return FLOOD_OK;
 }
 
@@ -480,26 +553,22 @@ int flood_batch_set_launch(flood_batch* b, int rows_per_strip, int warps_per_cta
         return bfail(b, FLOOD_ERR_ARG, "rows_per_strip in [1, 4096], warps_per_cta 4 or 8");
     BCK(b, cudaDeviceSynchronize());
     // fold the volume slots of each scenario before the table changes
-    std::vector<double> per((size_t)b->S * 2, 0.0);
+    std::vector<double> per((size_t)b->S * 2, 0.0), dper(b->S, 0.0);
     if (b->vacc && b->nslot) {
-        std::vector<double> v((size_t)b->nslot * 2);
+        std::vector<double> v((size_t)b->nslot * 2), dv(b->nslot);
         BCK(b, cudaMemcpy(v.data(), b->vacc, sizeof(double) * v.size(), cudaMemcpyDeviceToHost));
+        BCK(b, cudaMemcpy(dv.data(), b->dacc, sizeof(double) * dv.size(), cudaMemcpyDeviceToHost));
         for (const auto& t : b->tasks) {
             per[(size_t)t.scen * 2] += v[(size_t)t.slot * 2];
             per[(size_t)t.scen * 2 + 1] += v[(size_t)t.slot * 2 + 1];
+            dper[t.scen] += dv[t.slot];
         }
     }
     b->rows_per_strip = rows_per_strip;
     b->warps_per_cta = warps_per_cta;
     int rc = build_tasks(b);
     if (rc) return rc;
-    std::vector<double> v((size_t)b->nslot * 2, 0.0);
-    for (int i = 0; i < b->S; ++i) {
-        v[(size_t)b->slot0[i] * 2] = per[(size_t)i * 2];
-        v[(size_t)b->slot0[i] * 2 + 1] = per[(size_t)i * 2 + 1];
-    }
-    BCK(b, cudaMemcpy(b->vacc, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice));
-    return FLOOD_OK;
+    return put_entry_sums(b, per, dper);
 }
 
 int flood_batch_step(flood_batch* b, double t_stop, void* stream)
@@ -665,12 +734,15 @@ int flood_batch_autotune(flood_batch* b, double trial_s, int* best_rows, int* be
     std::vector<MemberClock> ms0((size_t)3 * S);
     BCK(b, cudaMemcpy(ms0.data(), b->ms, sizeof(MemberClock) * ms0.size(), cudaMemcpyDeviceToHost));
     const MemberClock* c0 = ms0.data() + (b->k % 3) * S;
-    std::vector<double> rain0(S), per((size_t)S * 2, 0.0), v((size_t)b->nslot * 2);
+    std::vector<double> rain0(S), per((size_t)S * 2, 0.0), dper(S, 0.0), v((size_t)b->nslot * 2),
+        dv(std::max(b->nslot, 1));
     BCK(b, cudaMemcpy(rain0.data(), b->rain_acc, sizeof(double) * S, cudaMemcpyDeviceToHost));
     BCK(b, cudaMemcpy(v.data(), b->vacc, sizeof(double) * v.size(), cudaMemcpyDeviceToHost));
+    BCK(b, cudaMemcpy(dv.data(), b->dacc, sizeof(double) * dv.size(), cudaMemcpyDeviceToHost));
     for (const auto& t : b->tasks) {
         per[(size_t)t.scen * 2] += v[(size_t)t.slot * 2];
         per[(size_t)t.scen * 2 + 1] += v[(size_t)t.slot * 2 + 1];
+        dper[t.scen] += dv[t.slot];
     }
     size_t total = 0;
     for (int i = 0; i < S; ++i) total += 3 * b->desc[i].plane;
@@ -695,12 +767,9 @@ int flood_batch_autotune(flood_batch* b, double trial_s, int* best_rows, int* be
         BCK(b, cudaMemcpyAsync(b->ms, ms0.data(), sizeof(MemberClock) * ms0.size(),
                                cudaMemcpyHostToDevice, s));
         BCK(b, cudaMemcpyAsync(b->rain_acc, rain0.data(), sizeof(double) * S, cudaMemcpyHostToDevice, s));
-        std::vector<double> nv((size_t)b->nslot * 2, 0.0);
-        for (int i = 0; i < S; ++i) {
-            nv[(size_t)b->slot0[i] * 2] = per[(size_t)i * 2];
-            nv[(size_t)b->slot0[i] * 2 + 1] = per[(size_t)i * 2 + 1];
-        }
-        BCK(b, cudaMemcpyAsync(b->vacc, nv.data(), sizeof(double) * nv.size(), cudaMemcpyHostToDevice, s));
+        BCK(b, cudaStreamSynchronize(s));
+        const int rc_sums = put_entry_sums(b, per, dper);
+        if (rc_sums) return rc_sums;
         BCK(b, cudaMemsetAsync(b->err, 0, sizeof(int), s));
         BCK(b, cudaStreamSynchronize(s));
         b->k = k0;
@@ -767,6 +836,124 @@ int flood_batch_autotune(flood_batch* b, double trial_s, int* best_rows, int* be
     if (best_warps) *best_warps = bc.warps;
     if (best_engine) *best_engine = bc.engine;
     if (best_ms) *best_ms = best;
+    return FLOOD_OK;
+}
+
+// ---- land cover (Section 4.1) --------------------------------------------
+
+int flood_batch_set_land_cover(flood_batch* b, int scen, const uint8_t* cls, int n_classes,
+                               const flood_land_class* classes)
+{
+    constexpr float kWallZ = 1.0e6f;  // m: the bed of cells outside the domain
+    if (!b) return bfail(nullptr, FLOOD_ERR_ARG, "batch is NULL");
+    if (scen < 0 || scen >= b->n_scen) return bfail(b, FLOOD_ERR_ARG, "scenario out of range");
+    if (b->initialised) return bfail(b, FLOOD_ERR_STATE, "land cover is set before flood_batch_init");
+    if (b->lc[scen]) return bfail(b, FLOOD_ERR_STATE, "land cover is already set for the scenario");
+    if (!cls || !classes || n_classes < 1 || n_classes > 4)
+        return bfail(b, FLOOD_ERR_ARG, "need cls, 1..4 classes and their table");
+    for (int q = 0; q < n_classes; ++q) {
+        const flood_land_class& k = classes[q];
+        if (!(k.n > 0.0f) || !(k.runoff >= 0.0f && k.runoff <= 1.0f) ||
+            (k.drains != 0 && k.drains != 1) || (k.outside != 0 && k.outside != 1))
+            return bfail(b, FLOOD_ERR_ARG, "class needs n > 0, runoff in [0, 1], flags 0/1");
+    }
+    const int ny = b->sny[scen], nx = b->snx[scen], ld = b->sld[scen];
+    const size_t plane = (size_t)ny * ld;
+    std::vector<uint8_t> hc((size_t)ny * nx);
+    BCK(b, cudaMemcpy(hc.data(), cls, hc.size(), cudaMemcpyDefault));
+    std::array<float, 4> runoff{1.0f, 1.0f, 1.0f, 1.0f}, drains{0.0f, 0.0f, 0.0f, 0.0f},
+        n0{0.05f, 0.05f, 0.05f, 0.05f};
+    for (int q = 0; q < n_classes; ++q) {
+        runoff[q] = classes[q].outside ? 0.0f : classes[q].runoff;
+        drains[q] = classes[q].outside ? 0.0f : (float)classes[q].drains;
+        n0[q] = classes[q].n;
+    }
+    const int spans = (nx + kSpan - 1) / kSpan;
+    std::vector<uint8_t> pad(plane, 0), span_out((size_t)ny * spans, 1);
+    std::vector<float> z(plane);
+    BCK(b, cudaMemcpy(z.data(), b->zn[scen], sizeof(float) * plane, cudaMemcpyDeviceToHost));
+    double rain_cells = 0.0;
+    for (int r = 0; r < ny; ++r)
+        for (int c = 0; c < nx; ++c) {
+            const uint8_t k = hc[(size_t)r * nx + c];
+            if (k >= n_classes) return bfail(b, FLOOD_ERR_ARG, "class index out of range");
+            pad[(size_t)r * ld + c] = k;
+            rain_cells += runoff[k];
+            if (classes[k].outside)
+                z[(size_t)r * ld + c] = kWallZ;  // no link into the cell carries flow (Eq. 3)
+            else
+                span_out[(size_t)r * spans + c / kSpan] = 0;
+        }
+    uint8_t* d_cls = nullptr;
+    float* d_zc = nullptr;
+    BCK(b, cudaMalloc(&d_cls, plane));
+    cudaError_t e = cudaMalloc(&d_zc, sizeof(float) * 2 * plane);
+    if (e != cudaSuccess) {
+        cudaFree(d_cls);
+        BCK(b, e);
+    }
+    b->cls8[scen] = d_cls;
+    b->zc[scen] = d_zc;
+    BCK(b, cudaMemcpy(d_cls, pad.data(), plane, cudaMemcpyHostToDevice));
+    BCK(b, cudaMemcpy(b->zn[scen], z.data(), sizeof(float) * plane, cudaMemcpyHostToDevice));
+    // the TMA engines' static planes: the bed and each cell's class code
+    // where the roughness plane would be
+    std::vector<uint32_t> codes(plane);
+    for (size_t i = 0; i < plane; ++i) codes[i] = pad[i];
+    BCK(b, cudaMemcpy(d_zc, z.data(), sizeof(float) * plane, cudaMemcpyHostToDevice));
+    BCK(b, cudaMemcpy(d_zc + plane, codes.data(), sizeof(uint32_t) * plane, cudaMemcpyHostToDevice));
+    b->lc_K[scen] = n_classes;
+    b->lc_runoff[scen] = runoff;
+    b->lc_drains[scen] = drains;
+    b->lc_n0[scen] = n0;
+    b->lc_rain_cells[scen] = rain_cells;
+    b->span_out[scen] = std::move(span_out);
+    b->lc[scen] = 1;
+    std::vector<int> counts(b->n_scen);
+    for (int i = 0; i < b->n_scen; ++i) counts[i] = b->first[i + 1] - b->first[i];
+    return set_entries(b, counts);
+}
+
+int flood_batch_set_land_params(flood_batch* b, int scen, const float* n_class,
+                                const float* drain_rate)
+{
+    if (!b) return bfail(nullptr, FLOOD_ERR_ARG, "batch is NULL");
+    if (scen < 0 || scen >= b->n_scen) return bfail(b, FLOOD_ERR_ARG, "scenario out of range");
+    if (!b->initialised || !b->lc[scen])
+        return bfail(b, FLOOD_ERR_STATE, "needs land cover and flood_batch_init");
+    const int e0 = b->first[scen], N = b->first[scen + 1] - e0, K = b->lc_K[scen];
+    BCK(b, cudaDeviceSynchronize());
+    if (n_class) {
+        std::vector<float> in((size_t)N * K);
+        BCK(b, cudaMemcpy(in.data(), n_class, sizeof(float) * in.size(), cudaMemcpyDefault));
+        for (float v : in)
+            if (!(v > 0.0f) || !std::isfinite(v))
+                return bfail(b, FLOOD_ERR_ARG, "class roughness must be positive");
+        for (int m = 0; m < N; ++m)
+            for (int q = 0; q < K; ++q) b->desc[e0 + m].lc_n[q] = in[(size_t)m * K + q];
+    }
+    if (drain_rate) {
+        std::vector<float> d(N);
+        BCK(b, cudaMemcpy(d.data(), drain_rate, sizeof(float) * N, cudaMemcpyDefault));
+        for (float v : d)
+            if (!(v >= 0.0f) || !std::isfinite(v))
+                return bfail(b, FLOOD_ERR_ARG, "drainage rates must be >= 0");
+        for (int m = 0; m < N; ++m) b->desc[e0 + m].lc_drain = d[m];
+    }
+    BCK(b, cudaMemcpy(b->d_desc + e0, b->desc.data() + e0, sizeof(flood::ScenDesc) * N,
+                      cudaMemcpyHostToDevice));
+    return FLOOD_OK;
+}
+
+int flood_batch_drained_volume(flood_batch* b, double* drained)
+{
+    if (!b) return bfail(nullptr, FLOOD_ERR_ARG, "batch is NULL");
+    if (!drained) return bfail(b, FLOOD_ERR_ARG, "drained is NULL");
+    BCK(b, cudaDeviceSynchronize());
+    std::vector<double> dv(std::max(b->nslot, 1)), out(b->S, 0.0);
+    BCK(b, cudaMemcpy(dv.data(), b->dacc, sizeof(double) * dv.size(), cudaMemcpyDeviceToHost));
+    for (const auto& t : b->tasks) out[t.scen] += dv[t.slot];
+    std::copy(out.begin(), out.end(), drained);
     return FLOOD_OK;
 }
 

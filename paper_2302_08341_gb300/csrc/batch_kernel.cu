@@ -41,7 +41,46 @@ __global__ void batch_plan_kernel(const BatchArgs a, int n_scen)
     a.plan[i] = p;
 }
 
-template <int W>
+// A task's reductions: the scenario's maximum depth (atomicMax into its next
+// clock), the non-finite flag, and the task's outflow, clamp and (land
+// cover) drained volume partials in its own slot.  ATOMIC: the slot may be
+// updated from another SM in the same launch (persistent form).
+template <bool LC, bool ATOMIC>
+__device__ __forceinline__ void finish_task(const BatchArgs& a, MemberClock* ms_out, const WarpTask& tk,
+                                            const MemberPlan& p, const MarchOut& mo, int lane)
+{
+    if (mo.bad) atomicOr(a.err, 1);
+    const unsigned hb = __reduce_max_sync(0xffffffffu, mo.bad ? 0u : __float_as_uint(mo.hmax) & 0x7fffffffu);
+    double out_acc = (double)mo.out_s - (double)mo.out_c, clamp_acc = (double)mo.clamp;
+    double drn_acc = LC ? (double)mo.drn_s - (double)mo.drn_c : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        out_acc += __shfl_xor_sync(0xffffffffu, out_acc, off);
+        clamp_acc += __shfl_xor_sync(0xffffffffu, clamp_acc, off);
+        if (LC) drn_acc += __shfl_xor_sync(0xffffffffu, drn_acc, off);
+    }
+    if (lane == 0) {
+        atomicMax(&ms_out[tk.scen].hmax_bits, hb);
+        if (out_acc != 0.0 || clamp_acc != 0.0) {
+            double* v = a.vacc + (size_t)tk.slot * 2;
+            if (ATOMIC) {
+                atomicAdd(v, out_acc * p.dt * a.dxd);
+                atomicAdd(v + 1, clamp_acc * a.cell_area);
+            } else {
+                v[0] += out_acc * p.dt * a.dxd;
+                v[1] += clamp_acc * a.cell_area;
+            }
+        }
+        if (LC && drn_acc != 0.0) {
+            if (ATOMIC)
+                atomicAdd(a.dacc + tk.slot, drn_acc * a.cell_area);
+            else
+                a.dacc[tk.slot] += drn_acc * a.cell_area;
+        }
+    }
+}
+
+template <int W, bool LC>
 __global__ void __launch_bounds__(32 * W) batch_step_kernel(const BatchArgs a)
 {
     const int lane = threadIdx.x;
@@ -64,30 +103,17 @@ __global__ void __launch_bounds__(32 * W) batch_step_kernel(const BatchArgs a)
     const size_t ms = 3 * sd.plane;
     const float* src = sd.state + (size_t)p.cur * ms;
     float* dst = sd.state + (size_t)(1 - p.cur) * ms;
-    const MarchOut mo = march_rows(src, dst, nullptr, nullptr, sd.z, sd.n, sd.plane, sd.ny, sd.nx, sd.ld, tk.c0,
-                                   tk.r0, tk.r1, lane, k, p.dt_dx, sd.scale, p.dr, a.east_out,
-                                   a.south_out);
-    if (mo.bad) atomicOr(a.err, 1);
-    const unsigned hb = __reduce_max_sync(0xffffffffu, mo.bad ? 0u : __float_as_uint(mo.hmax) & 0x7fffffffu);
-    double out_acc = (double)mo.out_s - (double)mo.out_c, clamp_acc = (double)mo.clamp;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        out_acc += __shfl_xor_sync(0xffffffffu, out_acc, off);
-        clamp_acc += __shfl_xor_sync(0xffffffffu, clamp_acc, off);
-    }
-    if (lane == 0) {
-        atomicMax(&a.ms_out[i].hmax_bits, hb);
-        if (out_acc != 0.0 || clamp_acc != 0.0) {
-            double* v = a.vacc + (size_t)tk.slot * 2;
-            v[0] += out_acc * p.dt * a.dxd;
-            v[1] += clamp_acc * a.cell_area;
-        }
-    }
+    LandK lk;
+    if (LC) lk = batch_land_k(a.scen + i, p.dr, p.dt, lane);
+    const MarchOut mo = march_rows<LC>(src, dst, nullptr, nullptr, sd.z, sd.n, sd.plane, sd.ny, sd.nx,
+                                       sd.ld, tk.c0, tk.r0, tk.r1, lane, k, p.dt_dx, sd.scale, p.dr,
+                                       a.east_out, a.south_out, &lk);
+    finish_task<LC, false>(a, a.ms_out, tk, p, mo, lane);
 }
 
 // TMA-staged form of batch_step_kernel (same results, bit for bit): the
 // task's rows stream through shared memory by the scenario's own tensor maps.
-template <int W, int LIM>
+template <int W, int LIM, bool LC>
 __global__ void __launch_bounds__(32 * W, 20 / W) batch_tma_kernel(const BatchArgs a)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -114,27 +140,15 @@ __global__ void __launch_bounds__(32 * W, 20 / W) batch_tma_kernel(const BatchAr
     unsigned char* my_stages;
     tma_march_smem(smem_raw, W, w, bar0, my_stages);
     float* dst = sd.state + (size_t)(1 - p.cur) * 3 * sd.plane;
+    LandK lk;
+    if (LC) lk = batch_land_k(a.scen + i, p.dr, p.dt, lane);
     MarchOut mo;
-    if (!tma_march<false, false, LIM>(a.maps + 2 * i, a.maps + 2 * i + 1, p.cur * 3, bar0, my_stages, dst, nullptr,
-                   nullptr, a.err, sd.plane, sd.ny, sd.nx, sd.ld, tk.c0, tk.r0, tk.r1, lane, k, p.dt_dx,
-                   sd.scale, p.dr, a.east_out, a.south_out, mo))
+    if (!tma_march<false, LC, LIM>(a.maps + 2 * i, a.maps + 2 * i + 1, p.cur * 3, bar0, my_stages,
+                                   dst, nullptr, nullptr, a.err, sd.plane, sd.ny, sd.nx, sd.ld, tk.c0,
+                                   tk.r0, tk.r1, lane, k, p.dt_dx, sd.scale, p.dr, a.east_out,
+                                   a.south_out, mo, &lk))
         return;
-    if (mo.bad) atomicOr(a.err, 1);
-    const unsigned hb = __reduce_max_sync(0xffffffffu, mo.bad ? 0u : __float_as_uint(mo.hmax) & 0x7fffffffu);
-    double out_acc = (double)mo.out_s - (double)mo.out_c, clamp_acc = (double)mo.clamp;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        out_acc += __shfl_xor_sync(0xffffffffu, out_acc, off);
-        clamp_acc += __shfl_xor_sync(0xffffffffu, clamp_acc, off);
-    }
-    if (lane == 0) {
-        atomicMax(&a.ms_out[i].hmax_bits, hb);
-        if (out_acc != 0.0 || clamp_acc != 0.0) {
-            double* v = a.vacc + (size_t)tk.slot * 2;
-            v[0] += out_acc * p.dt * a.dxd;
-            v[1] += clamp_acc * a.cell_area;
-        }
-    }
+    finish_task<LC, false>(a, a.ms_out, tk, p, mo, lane);
 }
 
 // ---- persistent form ------------------------------------------------------
@@ -276,7 +290,7 @@ __device__ __forceinline__ bool grid_barrier_plan(const PersistArgs& q, int j, d
 // different SM each step).
 // Returns false if a wait of the march gave up (the warp then takes no
 // further task: its barriers may still have a copy in flight).
-template <int LIM>
+template <int LIM, bool LC>
 __device__ __forceinline__ bool persistent_task(const PersistArgs& q, int j, int t, MemberClock* ms_out,
                                                 int lane, uint32_t bar0, unsigned char* my_stages)
 {
@@ -296,11 +310,14 @@ __device__ __forceinline__ bool persistent_task(const PersistArgs& q, int j, int
     k.q_in = 0.0f;  // no inflow boundary here
     k.in_r0 = k.in_r1 = 0;
     float* dst = sd.state + (size_t)(1 - p.cur) * 3 * sd.plane;
+    LandK lk;
+    if (LC) lk = batch_land_k(a.scen + i, p.dr, p.dt, lane);
     MarchOut mo;
-    const bool ok = tma_march<false, false, LIM>(a.maps + 2 * i, a.maps + 2 * i + 1, p.cur * 3, bar0,
-                                                 my_stages, dst, nullptr, nullptr, a.err, sd.plane,
-                                                 sd.ny, sd.nx, sd.ld, tk.c0, tk.r0, tk.r1, lane, k,
-                                                 p.dt_dx, sd.scale, p.dr, a.east_out, a.south_out, mo);
+    const bool ok = tma_march<false, LC, LIM>(a.maps + 2 * i, a.maps + 2 * i + 1, p.cur * 3, bar0,
+                                              my_stages, dst, nullptr, nullptr, a.err, sd.plane,
+                                              sd.ny, sd.nx, sd.ld, tk.c0, tk.r0, tk.r1, lane, k,
+                                              p.dt_dx, sd.scale, p.dr, a.east_out, a.south_out, mo,
+                                              &lk);
     if (!ok) {
         if (lane == 0) record_wait(q, 2, j, t, i);
         return false;
@@ -314,26 +331,11 @@ __device__ __forceinline__ bool persistent_task(const PersistArgs& q, int j, int
         for (int s = 0; s < kTmaNS; ++s) mbar_inval(bar0 + 8u * s);
     }
     __syncwarp();
-    if (mo.bad) atomicOr(a.err, 1);
-    const unsigned hb = __reduce_max_sync(0xffffffffu, mo.bad ? 0u : __float_as_uint(mo.hmax) & 0x7fffffffu);
-    double out_acc = (double)mo.out_s - (double)mo.out_c, clamp_acc = (double)mo.clamp;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        out_acc += __shfl_xor_sync(0xffffffffu, out_acc, off);
-        clamp_acc += __shfl_xor_sync(0xffffffffu, clamp_acc, off);
-    }
-    if (lane == 0) {
-        atomicMax(&ms_out[i].hmax_bits, hb);
-        if (out_acc != 0.0 || clamp_acc != 0.0) {
-            double* v = a.vacc + (size_t)tk.slot * 2;
-            atomicAdd(v, out_acc * p.dt * a.dxd);
-            atomicAdd(v + 1, clamp_acc * a.cell_area);
-        }
-    }
+    finish_task<LC, true>(a, ms_out, tk, p, mo, lane);
     return true;
 }
 
-template <int W, int LIM>
+template <int W, int LIM, bool LC>
 __global__ void __launch_bounds__(32 * W, 20 / W) batch_persistent_kernel(const __grid_constant__ PersistArgs q)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -361,7 +363,7 @@ __global__ void __launch_bounds__(32 * W, 20 / W) batch_persistent_kernel(const 
             const unsigned nw = gridDim.x * W;
             unsigned t = blockIdx.x * W + w;
             while (t < (unsigned)a.ntasks) {
-                if (!persistent_task<LIM>(q, j, (int)t, ms_out, lane, bar0, my_stages)) break;
+                if (!persistent_task<LIM, LC>(q, j, (int)t, ms_out, lane, bar0, my_stages)) break;
                 if (nw >= (unsigned)a.ntasks) break;
                 unsigned d = 0;
                 if (lane == 0) d = atomicAdd(q.task_next + (j & 1), 1u);
@@ -381,39 +383,49 @@ __global__ void __launch_bounds__(32 * W, 20 / W) batch_persistent_kernel(const 
 int batch_tma_prepare()
 {
     cudaError_t e = cudaSuccess;
-    for (auto f : {batch_tma_kernel<4, 0>, batch_tma_kernel<4, 1>})
+    for (auto f : {batch_tma_kernel<4, 0, false>, batch_tma_kernel<4, 1, false>,
+                   batch_tma_kernel<4, 0, true>, batch_tma_kernel<4, 1, true>})
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)tma_march_smem_bytes(4));
-    for (auto f : {batch_tma_kernel<8, 0>, batch_tma_kernel<8, 1>})
+    for (auto f : {batch_tma_kernel<8, 0, false>, batch_tma_kernel<8, 1, false>,
+                   batch_tma_kernel<8, 0, true>, batch_tma_kernel<8, 1, true>})
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)tma_march_smem_bytes(8));
     return e == cudaSuccess ? 0 : -1;
 }
 
-// the limiter is fixed at compile time (one instantiation per setting)
+namespace {
+
+template <int W, bool LC>
+void launch_tma_w(const BatchArgs& a, cudaStream_t s)
+{
+    const unsigned g = (a.ntasks + W - 1) / W;
+    if (a.limiter)
+        batch_tma_kernel<W, 1, LC><<<g, dim3(32, W), tma_march_smem_bytes(W), s>>>(a);
+    else
+        batch_tma_kernel<W, 0, LC><<<g, dim3(32, W), tma_march_smem_bytes(W), s>>>(a);
+}
+
+}  // namespace
+
+// the limiter and land cover are fixed at compile time (one instantiation
+// per setting)
 void launch_batch_step_tma(const BatchArgs& a, int warps_per_cta, cudaStream_t s)
 {
-    const unsigned g8 = (a.ntasks + 7) / 8, g4 = (a.ntasks + 3) / 4;
-    if (warps_per_cta >= 8) {
-        if (a.limiter)
-            batch_tma_kernel<8, 1><<<g8, dim3(32, 8), tma_march_smem_bytes(8), s>>>(a);
-        else
-            batch_tma_kernel<8, 0><<<g8, dim3(32, 8), tma_march_smem_bytes(8), s>>>(a);
-    } else {
-        if (a.limiter)
-            batch_tma_kernel<4, 1><<<g4, dim3(32, 4), tma_march_smem_bytes(4), s>>>(a);
-        else
-            batch_tma_kernel<4, 0><<<g4, dim3(32, 4), tma_march_smem_bytes(4), s>>>(a);
-    }
+    if (warps_per_cta >= 8)
+        a.lc ? launch_tma_w<8, true>(a, s) : launch_tma_w<8, false>(a, s);
+    else
+        a.lc ? launch_tma_w<4, true>(a, s) : launch_tma_w<4, false>(a, s);
 }
 
 // One cooperative launch (its CTAs are resident together, which the grid
 // barrier needs): as many CTAs of four warps as fit on the GPU.
 cudaError_t launch_batch_persistent(const PersistArgs& q, cudaStream_t s)
 {
-    auto f = q.a.limiter ? batch_persistent_kernel<4, 1> : batch_persistent_kernel<4, 0>;
+    auto f = q.a.lc ? (q.a.limiter ? batch_persistent_kernel<4, 1, true> : batch_persistent_kernel<4, 0, true>)
+                    : (q.a.limiter ? batch_persistent_kernel<4, 1, false> : batch_persistent_kernel<4, 0, false>);
     const size_t shm = tma_march_smem_bytes(4);
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
     int dev = 0, nsm = 0, per_sm = 0;
@@ -435,9 +447,15 @@ void launch_batch_plan(const BatchArgs& a, int n_scen, cudaStream_t s)
 void launch_batch_step(const BatchArgs& a, int warps_per_cta, cudaStream_t s)
 {
     if (warps_per_cta >= 8) {
-        batch_step_kernel<8><<<(a.ntasks + 7) / 8, dim3(32, 8), 0, s>>>(a);
+        if (a.lc)
+            batch_step_kernel<8, true><<<(a.ntasks + 7) / 8, dim3(32, 8), 0, s>>>(a);
+        else
+            batch_step_kernel<8, false><<<(a.ntasks + 7) / 8, dim3(32, 8), 0, s>>>(a);
     } else {
-        batch_step_kernel<4><<<(a.ntasks + 3) / 4, dim3(32, 4), 0, s>>>(a);
+        if (a.lc)
+            batch_step_kernel<4, true><<<(a.ntasks + 3) / 4, dim3(32, 4), 0, s>>>(a);
+        else
+            batch_step_kernel<4, false><<<(a.ntasks + 3) / 4, dim3(32, 4), 0, s>>>(a);
     }
 }
 

@@ -259,3 +259,111 @@ def test_batch_with_several_members_per_scenario(capi, engine):
     oracle.advance(oracle_params(p, ny, nx), terrs[i].z, terrs[i].n, float(sc[first[i] + m]),
                    float(rm[first[i] + m]), hys[i], mo, t_end=float(dur[i]))
     compare(got[(i, m)][0], mo.h, 1e-3)
+
+
+@pytest.mark.parametrize("engine", [0, 1, 2])
+def test_batch_with_land_cover(capi, engine):
+    """Land cover in the batch (Section 4.1): three scenarios of uneven sizes
+    with per-class roughness, runoff and drainage, cells outside the domain
+    (two western quarter discs, and an irregular domain whose outside tiles
+    are not scheduled), two or three members each with their own class
+    roughness and drainage rate.  Every member equals, bit for bit, the same
+    member of a single-grid land-cover ensemble of its scenario (same step
+    counts; drained volumes to the rounding of per-strip partials); the balance closes with
+    the drained volume; one member follows the FP64 oracle."""
+    shapes = [(70, 150), (45, 260), (150, 300)]
+    terrs = [synth.make_terrain(ny, nx, seed=120 + k) for k, (ny, nx) in enumerate(shapes)]
+    clss = [synth.land_cover(terrs[0], seed=121, pond_side=(6, 14)),
+            synth.land_cover(terrs[1], seed=122, pond_side=(5, 12)),
+            synth.land_cover(terrs[2], seed=123, pond_side=(6, 14),
+                             domain=synth.irregular_domain(150, 300, 0.55, seed=123))]
+    counts = np.array([2, 3, 2], np.int32)
+    first = np.concatenate([[0], np.cumsum(counts)])
+    rng = np.random.default_rng(124)
+    rm = rng.uniform(0.8, 1.5, counts.sum()).astype(np.float32)
+    sc = rng.uniform(0.8, 1.2, counts.sum()).astype(np.float32)
+    n_cls = [(np.array([c[0] for c in synth.LAND_CLASSES], np.float32)
+              * rng.uniform(0.7, 1.4, (counts[i], 4))).astype(np.float32) for i in range(3)]
+    drain = [rng.uniform(5.0, 20.0, counts[i]).astype(np.float32) / 3.6e6 for i in range(3)]
+    dur = np.array([600.0, 450.0, 540.0])
+    hys = [synth.hyetograph_constant(r, t) for r, t in zip((120.0, 80.0, 150.0), dur)]
+    with capi.Batch([t.z for t in terrs], [t.n for t in terrs]) as b:
+        for i in range(3):
+            b.set_land_cover(i, clss[i], synth.LAND_CLASSES)
+        b.set_engine(engine)
+        b.init(hys, rm, sc, dur, members=counts)
+        for i in range(3):
+            b.set_land_params(i, n_cls[i], drain[i])
+        for w in (300.0, 600.0):
+            b.step(w)
+        got = {(i, m): b.get_state(i, member=m) for i in range(3) for m in range(counts[i])}
+        mem = b.members()
+        drained = b.drained()
+    assert np.array_equal(mem["t"], np.repeat(dur, counts))
+    assert np.all(drained > 0)
+    bal = mem["storage"] - (mem["rain"] - mem["outflow"] + mem["clamp"] - drained)
+    assert np.all(np.abs(bal) <= 1e-5 * mem["rain"])
+    p = capi.Params.default()
+    for i, t in enumerate(terrs):
+        sl = slice(first[i], first[i + 1])
+        with capi.Grid(t.z, t.n, p) as g:
+            g.set_land_cover(clss[i], synth.LAND_CLASSES)
+            g.ensemble_init(int(counts[i]), rm[sl], sc[sl], hys[i])
+            g.set_land_params(n_cls[i], drain[i])
+            g.advance_to(float(dur[i]))
+            members = g.members()
+            vols = g.volumes()
+            for m in range(counts[i]):
+                alone = g.get_state(m)
+                for k in range(3):
+                    assert np.array_equal(got[(i, m)][k], alone[k]), (i, m, k)
+            grid_drained = g.drained()
+        assert np.array_equal(mem["steps"][sl], members["steps"])
+        # per-warp FP32 partials over the rows of each strip: the launch shapes differ
+        assert np.allclose(drained[sl], grid_drained, rtol=1e-8, atol=0)
+        assert np.allclose(mem["rain"][sl], vols["rain"], rtol=1e-12, atol=0)
+    # the irregular domain: cells outside it stay dry and at rest
+    out = ~synth.irregular_domain(150, 300, 0.55, seed=123)
+    for m in range(counts[2]):
+        assert np.all(got[(2, m)][0][out] == 0) and np.all(got[(2, m)][1][out] == 0)
+    # one member against the oracle
+    i, m = 0, 1
+    tab = synth.LAND_CLASSES
+    outside = np.array([c[3] for c in tab], bool)
+    runoff = np.where(outside, 0.0, np.array([c[1] for c in tab], np.float32)).astype(np.float64)
+    drains = np.where(outside, 0, np.array([c[2] for c in tab])).astype(np.float64)
+    cls = clss[i]
+    z = np.where(outside[cls], np.float32(1.0e6), terrs[i].z).astype(np.float32)
+    n = n_cls[i][m][cls].astype(np.float64)
+    ny, nx = z.shape
+    op = oracle_params(p, ny, nx)
+    op.rc = np.ascontiguousarray(runoff[cls])
+    op.drain = np.ascontiguousarray(float(np.float32(drain[i][m])) * drains[cls])
+    mo = oracle.Member.dry(ny, nx)
+    oracle.advance(op, z, n, float(sc[first[i] + m]), float(rm[first[i] + m]), hys[i], mo,
+                   t_end=float(dur[i]))
+    compare(got[(i, m)][0], mo.h, 1e-3)
+    assert mo.drained > 0 and abs(drained[first[i] + m] - mo.drained) <= 1e-3 * mo.drained
+
+
+def test_batch_land_cover_refusals(capi):
+    terrs = [synth.make_terrain(20, 30, seed=130 + k) for k in range(2)]
+    cls = synth.land_cover(terrs[0], seed=130, pond_side=(3, 5))
+    hy = synth.hyetograph_constant(50.0, 300.0)
+    with capi.Batch([t.z for t in terrs], [t.n for t in terrs]) as b:
+        with pytest.raises(capi.FloodError):
+            b.set_land_cover(2, cls, synth.LAND_CLASSES)          # no such scenario
+        with pytest.raises(capi.FloodError):
+            b.set_land_cover(0, cls + 4, synth.LAND_CLASSES)      # class out of range
+        b.set_land_cover(0, cls, synth.LAND_CLASSES)
+        with pytest.raises(capi.FloodError):
+            b.set_land_cover(0, cls, synth.LAND_CLASSES)          # set twice
+        with pytest.raises(capi.FloodError):                      # one scenario of two
+            b.init([hy, hy], np.ones(2, np.float32), np.ones(2, np.float32), [300.0, 300.0])
+        b.set_land_cover(1, synth.land_cover(terrs[1], seed=131, pond_side=(3, 5)),
+                         synth.LAND_CLASSES)
+        b.init([hy, hy], np.ones(2, np.float32), np.ones(2, np.float32), [300.0, 300.0])
+        with pytest.raises(capi.FloodError):
+            b.set_land_cover(0, cls, synth.LAND_CLASSES)          # after init
+        with pytest.raises(capi.FloodError):
+            b.set_land_params(0, -np.ones((1, 4), np.float32))    # roughness must be positive
