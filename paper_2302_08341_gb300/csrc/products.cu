@@ -131,21 +131,6 @@ __device__ __forceinline__ void odd_even_merge_sort(T (&v)[MT])
     }
 }
 
-// v[k] for a run-time k (k >= MT: 0) by a select per slot, written in PTX
-// so that the compiler keeps v in registers (read as v[k] it would move the
-// whole array to local memory); only the answer is live beside v.
-template <int MT>
-__device__ __forceinline__ float select_slot(const float (&v)[MT], int k)
-{
-    float ans = 0.0f;
-#pragma unroll
-    for (int i = 0; i < MT; ++i)
-        asm("{\n\t.reg .pred p;\n\tsetp.eq.s32 p, %2, %3;\n\tselp.f32 %0, %1, %0, p;\n\t}"
-            : "+f"(ans)
-            : "f"(v[i]), "r"(k), "r"(i));
-    return ans;
-}
-
 // An order-preserving map of FP32 bit patterns onto unsigned integers
 // (negative values reversed below the positive ones): for non-NaN x, y
 // other than the pair -0, +0, x < y iff ord(x) < ord(y); ord(-0) is one
@@ -176,9 +161,10 @@ __host__ __device__ constexpr int prod_stage_bytes() { return (MT * 32 * 4 + 127
 
 // One thread per cell, warps persistent over groups of 32 cells.  A group's
 // maxima (every member of 32 cells) arrive by one tensor copy into the
-// warp's stage; the lanes read them into registers and the copy of the
-// warp's next group starts at once, so it lands while this group is
-// sorted.
+// warp's stage; the lanes read them into registers, sort them there, and
+// write the sorted slots back into their own columns of the stage, from
+// which the levels are read; then the copy of the warp's next group starts
+// (the other warps of the SM cover its latency).
 //
 // Equal weights: the cell's MT slots (members, then +inf padding) are
 // sorted as FP32 values and the a-percentile is the value of the rank that
@@ -196,13 +182,13 @@ __host__ __device__ constexpr int prod_stage_bytes() { return (MT * 32 * 4 + 127
 // may share a place and come out in index order.  One pass over the sorted
 // keys sums the weights (exact integers) and keeps, per level, the key at
 // the first position whose cumulative weight reaches it, and the weight of
-// the members at or above the threshold.  A warp with a shifted lane keeps
-// its stage until that lane has settled each level exactly: the answer lies
-// among the members sharing the found key's place (every place below
+// the members at or above the threshold.  A lane with shifted places then
+// settles each level exactly from its maxima in global memory: the answer
+// lies among the members sharing the found key's place (every place below
 // holds smaller values, every place above larger ones), which a pass over
-// the staged values bounds; if they differ, candidates are tried in
-// increasing order against the exact weighted distribution function.  The
-// same lane sums the exceedance weight from the staged values.
+// the maxima bounds; if they differ, candidates are tried in increasing
+// order against the exact weighted distribution function.  The same lane
+// sums the exceedance weight from the maxima.
 //
 // Every wait is bounded: one that gives up records FLOOD_ERR_TIMEOUT in the
 // error word, waits for the warp's copy in flight and returns.
@@ -224,7 +210,7 @@ __global__ void __launch_bounds__(32 * kProdWarps, MT <= 96 ? 4 : 2)
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
     const uint32_t bar = flood::smem_u32(base) + 8u * w;
-    const float* stage = reinterpret_cast<const float*>(base + 128 + kStage * w);
+    float* const stage = reinterpret_cast<float*>(base + 128 + kStage * w);
     const uint32_t stage_s = flood::smem_u32(stage);
     const uint32_t tx = 32u * 4u * (uint32_t)a.M;
     const int gw = blockIdx.x * kProdWarps + w, nwarps = gridDim.x * kProdWarps;
@@ -264,26 +250,33 @@ __global__ void __launch_bounds__(32 * kProdWarps, MT <= 96 ? 4 : 2)
 #pragma unroll
             for (int j = 0; j < MT; ++j)
                 v[j] = j < a.M ? stage[j * 32 + lane] : __int_as_float(0x7f800000);
-            release(g);
             odd_even_merge_sort<float, N, MT>(v);
-            // members at or above the threshold, counted on the sorted slots
-            // (the +inf padding slots above M count too and are taken off);
-            // counted while loading, the comparisons would keep the unsorted
-            // values live through the sort
-            int cnt = 0;
+            // the sorted slots go back into this lane's column of the stage
+            // (the lane alone reads and writes it): a level then reads one
+            // word, and the members below the threshold are a binary search
+            // on the column (the +inf padding is never below it), where
+            // reading v[k] for a run-time k would take a select per slot
+            float* const col = stage + lane;
 #pragma unroll
-            for (int k = 0; k < MT; ++k) cnt += v[k] >= a.threshold;
-            cnt -= MT - a.M;
+            for (int k = 0; k < MT; ++k) col[k * 32] = v[k];
+            constexpr int kStep = MT >= 128 ? 128 : MT >= 64 ? 64 : 32;  // largest power of two <= MT
+            int below = 0;  // the sorted slots below the threshold, a prefix of the column
+#pragma unroll
+            for (int st = kStep; st > 0; st >>= 1)
+                if (below + st <= MT && col[(below + st - 1) * 32] < a.threshold) below += st;
+            const int cnt = a.M - below;
+            float pv[kLevelsPerPass];
+#pragma unroll
+            for (int q = 0; q < kLevelsPerPass; ++q)  // rank past M: none reaches the level, the top
+                pv[q] = col[min(a.rank[q] - 1, a.M - 1) * 32];
+            release(g);
             if (c >= a.nx) continue;
             if (a.exceed) a.exceed[out] = exceed_value((long long)cnt * a.u_eq);
             if (!a.pct) continue;
-            const float top = a.M == MT ? v[MT - 1] : select_slot<MT>(v, a.M - 1);
 #pragma unroll
             for (int q = 0; q < kLevelsPerPass; ++q) {
                 if (q >= a.n_levels) break;
-                const int pos = a.rank[q] - 1;   // 0-based sorted position (>= M: none)
-                const float sel = select_slot<MT>(v, pos);
-                a.pct[(size_t)q * a.ny * a.nx + out] = pos < a.M ? sel : top;
+                a.pct[(size_t)q * a.ny * a.nx + out] = pv[q];
             }
         } else {
             uint32_t key[MT];
@@ -303,70 +296,78 @@ __global__ void __launch_bounds__(32 * kProdWarps, MT <= 96 ? 4 : 2)
             int sh = max(0, 7 - __clz(d));              // bits of d above 25
             if ((d >> sh) == 0x1FFFFFFu) ++sh;          // keeps real keys below kPad
             const bool exact = sh == 0;
-            const bool early = __all_sync(0xffffffffu, exact);
-            if (early) release(g);
 #pragma unroll
             for (int j = 0; j < MT; ++j)
                 if (j < a.M) key[j] = (((key[j] - omin) >> sh) << 7) | (uint32_t)j;
             odd_even_merge_sort<uint32_t, N, MT>(key);
+            // the sorted keys go into this lane's column of the stage (its
+            // values are in registers now), and the pass over them is a short
+            // loop: unrolled over the registers it doubled the code and the
+            // warps waited on instruction fetch
+            uint32_t* const kcol = reinterpret_cast<uint32_t*>(stage) + lane;
+#pragma unroll
+            for (int k = 0; k < MT; ++k) kcol[k * 32] = key[k];
             // the threshold as a key (exact places)
             const uint32_t kth = a.th_ord <= omin ? 0u : a.th_ord > omax ? kPad : (a.th_ord - omin) << 7;
             long long P = 0, ex = 0;
             uint32_t kc[kLevelsPerPass];
 #pragma unroll
             for (int q = 0; q < kLevelsPerPass; ++q) kc[q] = kPad;
-#pragma unroll
+#pragma unroll 4
             for (int k = 0; k < MT; ++k) {
-                const long long uk = us[key[k] & 0x7Fu];
+                const uint32_t kk = kcol[k * 32];
+                const long long uk = us[kk & 0x7Fu];
 #pragma unroll
-                for (int q = 0; q < kLevelsPerPass; ++q) kc[q] = P < a.A[q] ? key[k] : kc[q];
+                for (int q = 0; q < kLevelsPerPass; ++q) kc[q] = P < a.A[q] ? kk : kc[q];
                 P += uk;
-                ex += key[k] >= kth ? uk : 0;
+                ex += kk >= kth ? uk : 0;
             }
+            release(g);
             // per level the ord of the answer (none reached: the largest value)
             uint32_t oq[kLevelsPerPass];
 #pragma unroll
             for (int q = 0; q < kLevelsPerPass; ++q) oq[q] = P < a.A[q] ? omax : (kc[q] >> 7) + omin;
-            if (!early) {
-                if (!exact) {
-                    uint32_t lo[kLevelsPerPass], hi[kLevelsPerPass];
+            if (!exact) {
+                // a lane with shifted places settles each level and the
+                // exceedance exactly from its maxima in global memory (the
+                // stage has moved on; the group's lines are still in L2)
+                const float* fc = a.field + (size_t)r * a.ld + c;
+                uint32_t lo[kLevelsPerPass], hi[kLevelsPerPass];
+#pragma unroll
+                for (int q = 0; q < kLevelsPerPass; ++q) {
+                    lo[q] = kPad;
+                    hi[q] = 0u;
+                }
+                ex = 0;
+                for (int j = 0; j < a.M; ++j) {
+                    const uint32_t o = ord_of(fc[(size_t)j * a.plane]);
+                    const uint32_t place = (o - omin) >> sh;
+                    if (o >= a.th_ord) ex += us[j];
 #pragma unroll
                     for (int q = 0; q < kLevelsPerPass; ++q) {
-                        lo[q] = kPad;
-                        hi[q] = 0u;
-                    }
-                    ex = 0;
-                    for (int j = 0; j < a.M; ++j) {
-                        const uint32_t o = ord_of(stage[j * 32 + lane]);
-                        const uint32_t place = (o - omin) >> sh;
-                        if (o >= a.th_ord) ex += us[j];
-#pragma unroll
-                        for (int q = 0; q < kLevelsPerPass; ++q) {
-                            if (place == kc[q] >> 7) {
-                                lo[q] = min(lo[q], o);
-                                hi[q] = max(hi[q], o);
-                            }
+                        if (place == kc[q] >> 7) {
+                            lo[q] = min(lo[q], o);
+                            hi[q] = max(hi[q], o);
                         }
-                    }
-#pragma unroll
-                    for (int q = 0; q < kLevelsPerPass; ++q) {
-                        if (q >= a.n_levels || P < a.A[q]) continue;
-                        uint32_t v = lo[q];
-                        for (int it = 0; it < a.M && v != hi[q]; ++it) {
-                            long long W = 0;
-                            uint32_t nxt = hi[q];
-                            for (int j = 0; j < a.M; ++j) {
-                                const uint32_t o = ord_of(stage[j * 32 + lane]);
-                                if (o <= v) W += us[j];
-                                else nxt = min(nxt, o);
-                            }
-                            if (W >= a.A[q]) break;
-                            v = nxt;
-                        }
-                        oq[q] = v;
                     }
                 }
-                release(g);
+#pragma unroll
+                for (int q = 0; q < kLevelsPerPass; ++q) {
+                    if (q >= a.n_levels || P < a.A[q]) continue;
+                    uint32_t v = lo[q];
+                    for (int it = 0; it < a.M && v != hi[q]; ++it) {
+                        long long W = 0;
+                        uint32_t nxt = hi[q];
+                        for (int j = 0; j < a.M; ++j) {
+                            const uint32_t o = ord_of(fc[(size_t)j * a.plane]);
+                            if (o <= v) W += us[j];
+                            else nxt = min(nxt, o);
+                        }
+                        if (W >= a.A[q]) break;
+                        v = nxt;
+                    }
+                    oq[q] = v;
+                }
             }
             if (c >= a.nx) continue;
             if (a.exceed) a.exceed[out] = exceed_value(ex);
