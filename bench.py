@@ -800,6 +800,43 @@ def masked_domain_measure(capi):
     return res
 
 
+def network_minmax(M):
+    """Min/max operations per cell of the products kernels' register sort:
+    Batcher's odd-even merge sort on N (a power of two) slots with every
+    comparator that reaches a padding slot above MT left out (MT = the
+    member count rounded up to 32, 64, 96 or 128), the same pruning rule as
+    the kernels, two operations per comparator (1056 comparators at 96)."""
+    MT = 32 if M <= 32 else 64 if M <= 64 else 96 if M <= 96 else 128
+    N = 32 if MT <= 32 else 64 if MT <= 64 else 128
+    n, P = 0, 1
+    while P < N:
+        K = P
+        while K >= 1:
+            j = K % P
+            while j + K < N:
+                n += sum(1 for i in range(K)
+                         if i + j + K < MT and (i + j) // (2 * P) == (i + j + K) // (2 * P))
+                j += 2 * K
+            K //= 2
+        P *= 2
+    return 2 * n
+
+
+# Minimum / maximum results per clock per SM (the ALU pipe: 16 lanes per
+# scheduler, 4 schedulers), and the GB300's SM count.
+ALU_MINMAX_PER_CLK_SM = 64
+N_SM = 152
+
+
+def alu_roofline(ops, ms, sm_mhz):
+    """The sort network's min/max operations per second against the ALU
+    pipe's peak at the sampled SM clock."""
+    peak = ALU_MINMAX_PER_CLK_SM * N_SM * sm_mhz * 1e6
+    achieved = ops / (ms * 1e-3)
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+            "unit": "T min/max per s", "frac": achieved / peak, "ops_per_cell": ops / (NY * NX)}
+
+
 def products_measure(g, stream, device, ncell, fused_value):
     """Section 4.4's products on the benchmark ensemble: one 300 s window with
     every member's running maximum depth kept by the step kernel (8 more
@@ -852,6 +889,8 @@ def products_measure(g, stream, device, ncell, fused_value):
             "products_ms_unequal_weights": uneq_ms,
             "products_hbm_frac_equal_weights": maxima_bytes / (eq_ms * 1e-3) / 1e9 / peaks()[0],
             "products_hbm_frac_unequal_weights": maxima_bytes / (uneq_ms * 1e-3) / 1e9 / peaks()[0],
+            "network_ops": float(network_minmax(len(w0))) * ncell,
+            "network_ms": {"equal_weights": eq_ms, "unequal_weights": uneq_ms},
             "cells_with_p_above_half": int((exceed > 0.5).sum())}
 
 
@@ -1057,6 +1096,15 @@ def run_gb300(args):
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(terr, hy, rm, sc)
         cpu["all_cores"] = cpu_all_cores(terr, hy, rm, sc)
+    clocks = clk.summary()
+    prod = extensions.get("products")
+    if prod and "network_ops" in prod:
+        # the product maps are bound by the ALU pipe (the sort network's
+        # min/max), at the SM clock sampled during the timed windows
+        mhz = (clocks or {}).get("sm_mhz") or 2070.0
+        ops = prod.pop("network_ops")
+        tms = prod.pop("network_ms")
+        prod["alu_roofline"] = {k: alu_roofline(ops, v, mhz) for k, v in tms.items()}
     line = {
         "metric": "member-cell-steps/s", "value": value, "unit": "member-cell-steps/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -1066,7 +1114,7 @@ def run_gb300(args):
                    "parallelism": f"replicas{world}",
                    "l2": "state 9.2 GB >> 129 MB L2 (no flush needed)"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
-        "clocks": clk.summary(),
+        "clocks": clocks,
     }
     line.update(extensions)
     print(json.dumps(line))
