@@ -215,3 +215,32 @@ def test_weighted_keys_on_crafted_maxima(capi, M):
         assert np.array_equal(pct, prod.percentiles(hm, w, levels)), th
     assert np.array_equal(eq[0], prod.exceedance(hm, np.full(M, 1.0 / M), 0.2))
     assert np.array_equal(eq[1], prod.percentiles(hm, np.full(M, 1.0 / M), levels))
+
+
+@pytest.mark.parametrize("M", [1, 7, 96])
+def test_products_exceedance_only_and_sixteen_levels(capi, M):
+    """The call's extremes: no percentile level (the exceedance map alone,
+    one pass) and the largest number of levels, sixteen (four passes of
+    four), with unequal weights (equal for one member): bit for bit the
+    oracle's maps."""
+    ny, nx = 9, 70
+    terr = synth.make_terrain(ny, nx, seed=57)
+    hy = synth.hyetograph_constant(90.0, 600.0)
+    rm, sc = synth.ensemble_prior(57, M)
+    rng = np.random.default_rng(57 + M)
+    w = rng.random(M) + 0.1
+    w = w / w.sum()
+    levels = tuple(np.sort(rng.uniform(0.01, 1.0, 16)))
+    with capi.Grid(terr.z, terr.n) as g:
+        g.ensemble_init(M, rm, sc, hy)
+        g.track_max_depth(True)
+        g.advance_to(90.0)
+        g.set_members(weights=w)
+        w_dev = g.members()["weights"]
+        ex0, pct0 = g.ensemble_products(0.004, ())
+        ex16, pct16 = g.ensemble_products(0.004, levels)
+        hm = np.array([g.max_depth(m) for m in range(M)])
+    want = prod.exceedance(hm, w_dev, 0.004)
+    assert np.array_equal(ex0, want) and np.array_equal(ex16, want)
+    assert pct0.shape[0] == 0
+    assert np.array_equal(pct16, prod.percentiles(hm, w_dev, levels))
