@@ -122,17 +122,10 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
         if (TRACK_MAX) tma_load_3d(dsts + kTmaHmOff, hm_map, c0, row, hm_plane, bar);
     };
     // land classes of a staged row (LC: the class-code plane): the lane's
-    // four cells as one byte each of a word, and the cells just east and
-    // west of the span
+    // four cells as one byte each of a word
     auto cls_of = [&](const float* P) -> uint32_t {
         const uint4 q = *reinterpret_cast<const uint4*>(P + kN + 4 + 4 * lane);
         return __byte_perm(__byte_perm(q.x, q.y, 0x0040u), __byte_perm(q.z, q.w, 0x0040u), 0x5410u);
-    };
-    auto cls_e = [&](const float* P) -> uint32_t {
-        return __float_as_uint(P[kN + 4 + kTmaSpan]);
-    };
-    auto cls_w = [&](const float* P) -> uint32_t {
-        return __float_as_uint(P[kN + 3]);
     };
     for (; issued < rb && issued < ra + kNS; ++issued)
         if (lane == 0) issue(issued);
@@ -185,14 +178,10 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
     }
     // land classes (LC): they come with each staged row (zeros past the
     // grid's edges, where no link uses them)
-    uint32_t clsC = 0, eC = 0, wC = 0, eN = 0, wN = 0;
+    uint32_t clsC = 0;
     {
         const float* P = row_ptr(r0);
-        if (LC) {
-            clsC = cls_of(P);
-            eC = cls_e(P);
-            wC = cls_w(P);
-        }
+        if (LC) clsC = cls_of(P);
         tma_lds4(hC, P + x0);
         tma_lds4(zC, P + kZ + x0);
         if (LC)
@@ -241,29 +230,28 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
         tma_lds4(qxo, P + kBox + x0);
         tma_lds4(qyo, P + 2 * kBox + x0);
         uint32_t clsS = 0;
+        if (LC) {
+            // the whole warp, outside any branch (the lookups are shuffles);
+            // past the grid's last row the stage holds an earlier row, whose
+            // classes go unused
+            clsS = cls_of(row_ptr(r + 1));
+            land_n4(nS, clsS, *lk);
+        }
         if (has_s) {
             const float* Q = row_ptr(r + 1);
-            if (LC) {
-                clsS = cls_of(Q);
-                eN = cls_e(Q);
-                wN = cls_w(Q);
-            }
             tma_lds4(hS, Q + x0);
             tma_lds4(zS, Q + kZ + x0);
-            if (LC)
-                land_n4(nS, clsS, *lk);
-            else
-                tma_lds4(nS, Q + kN + x0);
+            if (!LC) tma_lds4(nS, Q + kN + x0);
         }
         // east neighbour of the lane's last cell, straight from the tile
         const float hE = P[x0 + 4], zE = P[kZ + x0 + 4];
         float nE;
         float nWl = 0.0f, drv[4], ddv[4];
         if (LC) {
-            nE = __shfl_down_sync(0xffffffffu, nC[0], 1);
-            const float nEl = land_get(lk->n, eC);
-            if (lane == 31) nE = nEl;  // unused past the grid's east edge
-            nWl = land_get(lk->n, wC);
+            // the east neighbour's and the west halo cell's classes come
+            // with the tile (the codes sit where the roughness would)
+            nE = land_get(lk->n, __float_as_uint(P[kN + x0 + 4]));
+            nWl = land_get(lk->n, __float_as_uint(P[kN + 3]));
             land_src4(drv, ddv, clsC, *lk);
         } else {
             nE = P[kN + x0 + 4];
@@ -324,8 +312,6 @@ __device__ __forceinline__ bool tma_march(const CUtensorMap* state_map, const CU
             nC[j] = nS[j];
         }
         clsC = clsS;
-        eC = eN;
-        wC = wN;
         release(r);
     }
 
