@@ -16,6 +16,12 @@ struct AdjArgs {
     size_t n_mstride;        // 0 (one field for all members) or plane (land cover)
     const float* rw;         // [ny][ld] fraction of the rain that stays (land cover), or null
     const float* dflag;      // [ny][ld] 1 where the member's drainage applies (land cover)
+    // land cover, TMA form: the member's Manning n of every class [M][4] and
+    // the classes' runoff shares and drainage flags (the cells' classes come
+    // with the staged rows)
+    const float* lc_n;
+    float lc_runoff[4];
+    float lc_drains[4];
     double* gdpart;          // [M][nslot] per-warp partials of dL/d(drainage rate) (land cover)
     const float* scale;      // [M]
     const MemberPlan* log;   // [M][dt_log_cap] plans of the recorded steps
@@ -38,7 +44,7 @@ struct AdjTmaArgs {
     CUtensorMap seg1_map;    // the same memory, box of 1 plane (the depth after a step)
     CUtensorMap lam_map;     // lam as (ld, ny, 2 * M * 3), box of 3 planes
     CUtensorMap static_map;  // z, n as (ld, ny, 2), box of 2 planes; land cover: z and the
-                             // members' n fields as (ld, ny, 1 + M), box of 1 plane
+                             // class codes (one uint32 per cell), the same layout
     CUtensorMap gn_map;      // per-member Manning gradients as (ld, ny, M), box of 1 plane
     AdjArgs a;
 };

@@ -237,11 +237,8 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
                                  1, 3) == 0 &&
             (!grad_n || flood::encode_map_3d(&tma.gn_map, g->gnm, g->ld, g->ny, (uint64_t)M, s1, s2,
                                              bc, 1, 1) == 0);
-        if (g->lc_on)
-            use_tma = use_tma && flood::encode_map_3d(&tma.static_map, g->lc_adj, g->ld, g->ny,
-                                                      (uint64_t)M + 1, s1, s2, bc, 1, 1) == 0;
-        else
-            tma.static_map = g->static_map;
+        // with land cover the bed and the class codes, as the forward stages them
+        tma.static_map = g->lc_on ? g->static_map_lc : g->static_map;
     }
     const bool tma_replay = use_tma;
     const bool tma_reverse = use_tma && g->rows_per_strip >= 16;
@@ -294,6 +291,13 @@ extern "C" int flood_adjoint(flood_grid* g, const flood_loss_spec* L, int ckpt_e
         b.rw = g->lc_on ? g->lc_adj + (size_t)(M + 1) * plane : nullptr;
         b.dflag = g->lc_on ? g->lc_adj + (size_t)(M + 2) * plane : nullptr;
         b.gdpart = g->lc_on ? g->gdpart : nullptr;
+        if (g->lc_on) {
+            b.lc_n = g->lc_n;
+            for (int q = 0; q < 4; ++q) {
+                b.lc_runoff[q] = g->lc_runoff[q];
+                b.lc_drains[q] = g->lc_drains[q];
+            }
+        }
         b.scale = g->scale;
         b.log = g->log;
         b.seg_end = g->seg_end;

@@ -7,9 +7,9 @@
 // warp streams its rows through a ring of shared-memory stages filled by the
 // tensor memory accelerator, one row of all ten planes it reads per stage:
 // the state before the step (h, qx, qy), the depth after it, the
-// sensitivities lambda (h, qx, qy), the bed and roughness, and the member's
-// Manning gradient, each 136 columns wide (the warp's 128 plus a 4-column
-// halo on each side).  Lane 0 keeps kNS - 1 rows in flight ahead of the row
+// sensitivities lambda (h, qx, qy), the bed and roughness (with land cover
+// the bed and the class codes), and the member's Manning gradient, each 136
+// columns wide (the warp's 128 plus a 4-column halo on each side).  Lane 0 keeps kNS - 1 rows in flight ahead of the row
 // being computed.  Every mbarrier wait is bounded: on timeout the kernel
 // records FLOOD_ERR_TIMEOUT, waits (bounded) for its own copies in flight,
 // and returns.
@@ -40,15 +40,8 @@ static_assert(kLam * 4 >= (kHa + kBox) * 4 && kLam % 32 == 0, "stage layout");
 static_assert(kZ * 4 >= (kLam + 3 * kBox) * 4 && kZ % 32 == 0, "stage layout");
 static_assert(kGn * 4 >= (kN + kBox) * 4 && kGn % 32 == 0, "stage layout");
 static_assert(kStageBytes >= (kGn + kBox) * 4 && kStageBytes % 128 == 0, "stage layout");
-// Land cover: the roughness is the member's own plane, a copy of its own that
-// must start on a 128-byte boundary like every other part, so the roughness
-// and the Manning gradient move up and the stage grows by one 128-byte line.
-constexpr int kNLc = 1152;
-constexpr int kGnLc = 1312;
-constexpr int kStageBytesLc = 5888;
-static_assert(kNLc * 4 >= (kZ + kBox) * 4 && kNLc % 32 == 0, "stage layout");
-static_assert(kGnLc * 4 >= (kNLc + kBox) * 4 && kGnLc % 32 == 0, "stage layout");
-static_assert(kStageBytesLc >= (kGnLc + kBox) * 4 && kStageBytesLc % 128 == 0, "stage layout");
+// Land cover: the roughness plane's place holds each cell's class code (a
+// uint32), staged with the bed as in the forward step.
 
 __device__ __forceinline__ void lds4(float (&v)[4], const float* p)
 {
@@ -61,15 +54,15 @@ __device__ __forceinline__ void store4(float* p, const float (&v)[4])
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
-// LC: land cover (the member's own roughness plane, rain weighed by the
-// runoff coefficient, read directly: one plane shared by all members).
+// LC: land cover: the roughness, runoff share and drainage flag of every
+// cell from its class (the codes come with the staged rows, the member's
+// class table lives in lanes 0..3 and is read by shuffle, so every lane takes
+// part in each lookup, outside lane-dependent branches).
 template <int WM, int LIM, bool LC = false>
 __global__ void __launch_bounds__(32 * WM, WM == 4 ? 3 : 12) adjoint_tma_kernel(
     const __grid_constant__ AdjTmaArgs t)
 {
-    constexpr int kN = LC ? kNLc : kZ + kBox;
-    constexpr int kGn = LC ? kGnLc : flood::kGn;
-    constexpr int kStageBytes = LC ? kStageBytesLc : flood::kStageBytes;
+
     extern __shared__ unsigned char smem_raw[];
     const AdjArgs& a = t.a;
     const int lane = threadIdx.x;
@@ -144,12 +137,7 @@ __global__ void __launch_bounds__(32 * WM, WM == 4 ? 3 : 12) adjoint_tma_kernel(
         tma_load_3d(dsts + 4 * kSt, &t.seg_map, c0 - 4, row, p_before, bar);
         tma_load_3d(dsts + 4 * kHa, &t.seg1_map, c0 - 4, row, p_after, bar);
         tma_load_3d(dsts + 4 * kLam, &t.lam_map, c0 - 4, row, p_lam, bar);
-        if (LC) {
-            tma_load_3d(dsts + 4 * kZ, &t.static_map, c0 - 4, row, 0, bar);
-            tma_load_3d(dsts + 4 * kN, &t.static_map, c0 - 4, row, 1 + m, bar);
-        } else {
-            tma_load_3d(dsts + 4 * kZ, &t.static_map, c0 - 4, row, 0, bar);
-        }
+        tma_load_3d(dsts + 4 * kZ, &t.static_map, c0 - 4, row, 0, bar);
         if (gn) tma_load_3d(dsts + 4 * kGn, &t.gn_map, c0 - 4, row, m, bar);
     };
     for (; issued < rb && issued < ra + kNS; ++issued)
@@ -179,6 +167,35 @@ __global__ void __launch_bounds__(32 * WM, WM == 4 ? 3 : 12) adjoint_tma_kernel(
     };
 
     const int x0 = 4 + 4 * lane;  // this lane's first cell in a tile row
+    // land cover: lane q of every group of four holds class q's roughness,
+    // runoff share and drainage flag for this member
+    float ln = 0.0f, lro = 0.0f, ldr = 0.0f;
+    if (LC) {
+        const int q = lane & 3;
+        ln = a.lc_n[(size_t)m * 4 + q];
+        lro = a.lc_runoff[q];
+        ldr = a.lc_drains[q];
+    }
+    // the classes of the lane's four cells in a staged row, one byte each
+    auto cls4 = [&](const float* R) -> uint32_t {
+        const uint4 q = *reinterpret_cast<const uint4*>(R + kN + x0);
+        return __byte_perm(__byte_perm(q.x, q.y, 0x0040u), __byte_perm(q.z, q.w, 0x0040u), 0x5410u);
+    };
+    // roughness of the lane's four cells / of one cell of a staged row (with
+    // land cover by shuffle: every lane calls these; the shuffle reads the
+    // five low bits of its source lane, where a class byte sits alone)
+    auto n4 = [&](float (&nv)[4], const float* R) {
+        if (LC) {
+            const uint32_t wc = cls4(R);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) nv[q] = __shfl_sync(0xffffffffu, ln, (int)(wc >> (8 * q)));
+        } else {
+            lds4(nv, R + kN + x0);
+        }
+    };
+    auto n1 = [&](const float* R, int x) -> float {
+        return LC ? __shfl_sync(0xffffffffu, ln, (int)__float_as_uint(R[kN + x])) : R[kN + x];
+    };
     float hC[4], zC[4], nC[4], lC[4];
     float carH[4] = {0, 0, 0, 0}, carN[4] = {0, 0, 0, 0};  // north link: mu*dh2, mu*dnl
     bool ok = true;
@@ -199,7 +216,7 @@ __global__ void __launch_bounds__(32 * WM, WM == 4 ? 3 : 12) adjoint_tma_kernel(
         float ha[4], la[4];
         lds4(hC, P + kSt + x0);
         lds4(zC, P + kZ + x0);
-        lds4(nC, P + kN + x0);
+        n4(nC, P);
         lds4(ha, P + kHa + x0);
         lds4(la, P + kLam + x0);
 #pragma unroll
@@ -209,7 +226,7 @@ __global__ void __launch_bounds__(32 * WM, WM == 4 ? 3 : 12) adjoint_tma_kernel(
             float hU[4], zU[4], nU[4], qU[4], lqU[4], haU[4], lhU[4], lU[4];
             lds4(hU, U + kSt + x0);
             lds4(zU, U + kZ + x0);
-            lds4(nU, U + kN + x0);
+            n4(nU, U);
             lds4(qU, U + kSt + 2 * kBox + x0);
             lds4(lqU, U + kLam + 2 * kBox + x0);
             lds4(haU, U + kHa + x0);
@@ -249,7 +266,7 @@ __global__ void __launch_bounds__(32 * WM, WM == 4 ? 3 : 12) adjoint_tma_kernel(
             float ha[4], la[4];
             lds4(hS, Q + kSt + x0);
             lds4(zS, Q + kZ + x0);
-            lds4(nS, Q + kN + x0);
+            n4(nS, Q);
             lds4(ha, Q + kHa + x0);
             lds4(la, Q + kLam + x0);
 #pragma unroll
@@ -257,11 +274,12 @@ __global__ void __launch_bounds__(32 * WM, WM == 4 ? 3 : 12) adjoint_tma_kernel(
         }
         // east neighbour of the lane's last cell and the span's west
         // neighbour, straight from the tile's halo
-        const float hE = P[kSt + x0 + 4], zE = P[kZ + x0 + 4], nE = P[kN + x0 + 4];
+        const float hE = P[kSt + x0 + 4], zE = P[kZ + x0 + 4], nE = n1(P, x0 + 4);
         const float lE = masked(P[kHa + x0 + 4], P[kLam + x0 + 4]);
+        const float nW = n1(P, 3);
         WestIn wi{0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
         if (lane == 0 && c0 > 0) {
-            wi.h = P[kSt + 3]; wi.z = P[kZ + 3]; wi.n = P[kN + 3];
+            wi.h = P[kSt + 3]; wi.z = P[kZ + 3]; wi.n = nW;
             wi.qx = P[kSt + kBox + 3]; wi.lqx = P[kLam + kBox + 3];
             wi.l = masked(P[kHa + 3], P[kLam + 3]);
         }
@@ -269,12 +287,14 @@ __global__ void __launch_bounds__(32 * WM, WM == 4 ? 3 : 12) adjoint_tma_kernel(
         float gr_row = 0.0f, gs_row = 0.0f;
         float rwv[4] = {0, 0, 0, 0};
         if (LC) {
-            float dfv[4] = {0, 0, 0, 0}, haC[4];
-            if (act) {
-                const float4 v = ldg4(a.rw + o);
-                rwv[0] = v.x; rwv[1] = v.y; rwv[2] = v.z; rwv[3] = v.w;
-                const float4 f = ldg4(a.dflag + o);
-                dfv[0] = f.x; dfv[1] = f.y; dfv[2] = f.z; dfv[3] = f.w;
+            float dfv[4], haC[4];
+            const uint32_t wc = cls4(P);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {  // the cells' runoff shares and drainage flags
+                const float rv = __shfl_sync(0xffffffffu, lro, (int)(wc >> (8 * q)));
+                const float dv = __shfl_sync(0xffffffffu, ldr, (int)(wc >> (8 * q)));
+                rwv[q] = act ? rv : 0.0f;
+                dfv[q] = act ? dv : 0.0f;
             }
             lds4(haC, P + kHa + x0);
             kahan_add(gd_s, gd_c, drain_row(lC, haC, dfv));
@@ -318,8 +338,8 @@ __global__ void __launch_bounds__(32 * WM, WM == 4 ? 3 : 12) adjoint_tma_kernel(
 template <int WM, bool LC>
 size_t adj_smem_bytes()
 {
-    return 128 + 128 * ((8 * kNS * WM + 127) / 128) +
-           (size_t)kNS * (LC ? kStageBytesLc : kStageBytes) * WM;
+    (void)LC;  // the land-cover stage has the plain layout
+    return 128 + 128 * ((8 * kNS * WM + 127) / 128) + (size_t)kNS * kStageBytes * WM;
 }
 
 template <int LIM, bool LC>
