@@ -183,12 +183,12 @@ __host__ __device__ constexpr int prod_stage_bytes() { return (MT * 32 * 4 + 127
 // keys sums the weights (exact integers) and keeps, per level, the key at
 // the first position whose cumulative weight reaches it, and the weight of
 // the members at or above the threshold.  A lane with shifted places then
-// settles each level exactly from its maxima in global memory: the answer
-// lies among the members sharing the found key's place (every place below
-// holds smaller values, every place above larger ones), which a pass over
-// the maxima bounds; if they differ, candidates are tried in increasing
-// order against the exact weighted distribution function.  The same lane
-// sums the exceedance weight from the maxima.
+// checks its sorted keys: a level whose key is alone in its place takes that
+// member's value from its maxima in global memory; where members share it,
+// the answer lies among them (every place below holds smaller values, every
+// place above larger ones), and candidates are tried in increasing order
+// against the exact weighted distribution function.  The members in the
+// threshold's place, counted as reaching it, are checked against it.
 //
 // Every wait is bounded: one that gives up records FLOOD_ERR_TIMEOUT in the
 // error word, waits for the warp's copy in flight and returns.
@@ -236,6 +236,7 @@ __global__ void __launch_bounds__(32 * kProdWarps, MT <= 96 ? 4 : 2)
     if (gw < t.n_groups && lane == 0) issue(gw);
     uint32_t phase = 0;
     constexpr int N = MT <= 32 ? 32 : MT <= 64 ? 64 : 128;   // the network's power of two
+    constexpr int kStep = MT >= 128 ? 128 : MT >= 64 ? 64 : 32;  // largest power of two <= MT
     for (int g = gw; g < t.n_groups; g += nwarps) {
         if (!flood::mbar_wait_bounded(bar, phase, kBudget)) {
             if (lane == 0) atomicOr(a.err, 2);
@@ -259,7 +260,6 @@ __global__ void __launch_bounds__(32 * kProdWarps, MT <= 96 ? 4 : 2)
             float* const col = stage + lane;
 #pragma unroll
             for (int k = 0; k < MT; ++k) col[k * 32] = v[k];
-            constexpr int kStep = MT >= 128 ? 128 : MT >= 64 ? 64 : 32;  // largest power of two <= MT
             int below = 0;  // the sorted slots below the threshold, a prefix of the column
 #pragma unroll
             for (int st = kStep; st > 0; st >>= 1)
@@ -307,8 +307,10 @@ __global__ void __launch_bounds__(32 * kProdWarps, MT <= 96 ? 4 : 2)
             uint32_t* const kcol = reinterpret_cast<uint32_t*>(stage) + lane;
 #pragma unroll
             for (int k = 0; k < MT; ++k) kcol[k * 32] = key[k];
-            // the threshold as a key (exact places)
-            const uint32_t kth = a.th_ord <= omin ? 0u : a.th_ord > omax ? kPad : (a.th_ord - omin) << 7;
+            // the threshold as a key: the first key of its place (shifted
+            // lanes settle the members of that place below)
+            const uint32_t kth =
+                a.th_ord <= omin ? 0u : a.th_ord > omax ? kPad : ((a.th_ord - omin) >> sh) << 7;
             long long P = 0, ex = 0;
             uint32_t kc[kLevelsPerPass];
 #pragma unroll
@@ -322,42 +324,58 @@ __global__ void __launch_bounds__(32 * kProdWarps, MT <= 96 ? 4 : 2)
                 P += uk;
                 ex += kk >= kth ? uk : 0;
             }
-            release(g);
             // per level the ord of the answer (none reached: the largest value)
             uint32_t oq[kLevelsPerPass];
 #pragma unroll
             for (int q = 0; q < kLevelsPerPass; ++q) oq[q] = P < a.A[q] ? omax : (kc[q] >> 7) + omin;
             if (!exact) {
-                // a lane with shifted places settles each level and the
-                // exceedance exactly from its maxima in global memory (the
-                // stage has moved on; the group's lines are still in L2)
+                // a lane with shifted places: its keys order the members up
+                // to values that share a place.  The exceedance counted every
+                // member in the threshold's place as reaching it, and a level
+                // whose key shares its place with other members needs their
+                // values: both are settled from the maxima in global memory
+                // (the stage holds the keys now; the group's lines are still
+                // in L2)
                 const float* fc = a.field + (size_t)r * a.ld + c;
-                uint32_t lo[kLevelsPerPass], hi[kLevelsPerPass];
+                auto below_key = [&](uint32_t kq) -> int {  // sorted keys below kq
+                    int n = 0;
 #pragma unroll
-                for (int q = 0; q < kLevelsPerPass; ++q) {
-                    lo[q] = kPad;
-                    hi[q] = 0u;
-                }
-                ex = 0;
-                for (int j = 0; j < a.M; ++j) {
-                    const uint32_t o = ord_of(fc[(size_t)j * a.plane]);
-                    const uint32_t place = (o - omin) >> sh;
-                    if (o >= a.th_ord) ex += us[j];
-#pragma unroll
-                    for (int q = 0; q < kLevelsPerPass; ++q) {
-                        if (place == kc[q] >> 7) {
-                            lo[q] = min(lo[q], o);
-                            hi[q] = max(hi[q], o);
-                        }
+                    for (int st = kStep; st > 0; st >>= 1)
+                        if (n + st <= MT && kcol[(n + st - 1) * 32] < kq) n += st;
+                    return n;
+                };
+                if (a.th_ord > omin && a.th_ord <= omax) {
+                    const uint32_t pth = (a.th_ord - omin) >> sh;
+                    const int end = below_key((pth + 1) << 7);
+                    for (int p = below_key(pth << 7); p < end; ++p) {
+                        const uint32_t id = kcol[p * 32] & 0x7Fu;  // a real member: < M
+                        if (id < (uint32_t)a.M && ord_of(fc[(size_t)id * a.plane]) < a.th_ord) ex -= us[id];
                     }
                 }
 #pragma unroll
                 for (int q = 0; q < kLevelsPerPass; ++q) {
                     if (q >= a.n_levels || P < a.A[q]) continue;
-                    uint32_t v = lo[q];
-                    for (int it = 0; it < a.M && v != hi[q]; ++it) {
+                    const uint32_t pl = kc[q] >> 7;
+                    const int plo = below_key(pl << 7), phi = below_key((pl + 1) << 7);
+                    if (phi - plo == 1) {  // the key's member is alone in its place
+                        oq[q] = ord_of(fc[(size_t)min(kc[q] & 0x7Fu, (uint32_t)a.M - 1u) * a.plane]);
+                        continue;
+                    }
+                    // members that share the place: their range, then
+                    // candidates in increasing order against the exact
+                    // weighted distribution function (lower places hold
+                    // smaller values, higher places larger ones)
+                    uint32_t lo = kPad, hi = 0u;
+                    for (int p = plo; p < phi; ++p) {
+                        const uint32_t id = min(kcol[p * 32] & 0x7Fu, (uint32_t)a.M - 1u);
+                        const uint32_t o = ord_of(fc[(size_t)id * a.plane]);
+                        lo = min(lo, o);
+                        hi = max(hi, o);
+                    }
+                    uint32_t v = lo;
+                    for (int it = 0; it < a.M && v != hi; ++it) {
                         long long W = 0;
-                        uint32_t nxt = hi[q];
+                        uint32_t nxt = hi;
                         for (int j = 0; j < a.M; ++j) {
                             const uint32_t o = ord_of(fc[(size_t)j * a.plane]);
                             if (o <= v) W += us[j];
@@ -369,6 +387,8 @@ __global__ void __launch_bounds__(32 * kProdWarps, MT <= 96 ? 4 : 2)
                     oq[q] = v;
                 }
             }
+            // the shifted lanes have read the keys: the next copy may overwrite them
+            release(g);
             if (c >= a.nx) continue;
             if (a.exceed) a.exceed[out] = exceed_value(ex);
             if (!a.pct) continue;

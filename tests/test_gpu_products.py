@@ -124,10 +124,18 @@ def test_full_size_products_on_sampled_rows(capi):
         levels = (0.1, 0.5, 0.9)
         exceed, pct = g.ensemble_products(0.01, levels)
         w = g.members()["weights"]
+        # unequal weights over the same maxima (roof cells whose members
+        # range from nearly dry to wet take the shifted keys)
+        wu = np.linspace(1.0, 3.0, M)
+        g.set_members(weights=wu / wu.sum())
+        exceed_u, pct_u = g.ensemble_products(0.01, levels)
+        w_u = g.members()["weights"]
         rows = np.random.default_rng(1).choice(ny, 5, replace=False)
         hm = np.array([g.max_depth(m)[rows] for m in range(M)])
     assert np.array_equal(exceed[rows], prod.exceedance(hm, w, 0.01))
     assert np.array_equal(pct[:, rows], prod.percentiles(hm, w, levels))
+    assert np.array_equal(exceed_u[rows], prod.exceedance(hm, w_u, 0.01))
+    assert np.array_equal(pct_u[:, rows], prod.percentiles(hm, w_u, levels))
     assert exceed.max() > 0
 
 
@@ -244,3 +252,37 @@ def test_products_exceedance_only_and_sixteen_levels(capi, M):
     assert np.array_equal(ex0, want) and np.array_equal(ex16, want)
     assert pct0.shape[0] == 0
     assert np.array_equal(pct16, prod.percentiles(hm, w_dev, levels))
+
+
+def test_weighted_keys_with_several_groups_per_warp(capi):
+    """Crafted maxima (as above: values over many binades, neighbours one
+    FP32 step apart, exact ties, the threshold itself) on a grid of more
+    32-cell groups than the kernel has warps, so every warp sorts several
+    groups while the copy of its next one lands in the same stage: the
+    maps of sampled rows equal the oracle's, bit for bit."""
+    ny, nx, M = 330, 300, 96
+    rng = np.random.default_rng(58)
+    mags = np.array([0.0, 1e-30, 1e-6, 1e-3, 0.2, 0.5, 3.0], np.float32)
+    hm = rng.choice(mags, (M, ny, nx)) * rng.uniform(1, 1.01, (M, ny, nx)).astype(np.float32)
+    hm[:, 1::3] = rng.uniform(0.2, 0.3, (M, ny, nx))[:, 1::3].astype(np.float32)
+    for i in range(0, M - 1, 5):
+        hm[i] = np.nextafter(hm[i + 1], np.float32(np.inf))
+    hm[1::7, :, ::2] = np.float32(0.2)
+    hm = hm.astype(np.float32)
+    w = rng.random(M) ** 2 + 0.01
+    w = w / w.sum()
+    levels = (0.1, 0.5, 0.9)
+    terr = synth.make_terrain(ny, nx, seed=58)
+    with capi.Grid(terr.z, terr.n) as g:
+        g.ensemble_init(M, np.ones(M, np.float32), np.ones(M, np.float32),
+                        synth.hyetograph_constant(0.0, 60.0))
+        for m in range(M):
+            g.set_state(m, h=hm[m])
+        g.track_max_depth(True)
+        g.set_members(weights=w)
+        w_dev = g.members()["weights"]
+        exceed, pct = g.ensemble_products(0.2, levels)
+    rows = np.random.default_rng(59).choice(ny, 12, replace=False)
+    sub = hm[:, rows]
+    assert np.array_equal(exceed[rows], prod.exceedance(sub, w_dev, 0.2))
+    assert np.array_equal(pct[:, rows], prod.percentiles(sub, w_dev, levels))
