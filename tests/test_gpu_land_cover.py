@@ -276,3 +276,41 @@ def test_irregular_domain_skips_outside_tiles_and_follows_the_oracle(capi):
         assert np.all(mo.h[out] == 0.0)
         V = oracle.storage(mo.h, p.dx)
         assert abs(vol1["storage"][m] - V) <= 1e-5 * V
+
+
+def test_water_body_warmup_follows_the_oracle(capi):
+    """§4.1's start: the water bodies filled to a 3.0 m water level, then a
+    warm-up with no rain (shortened here to 600 s), through the initial depth
+    field of the ensemble: against the oracle from the same field, the volume
+    balance closing with the drainage and the outflow."""
+    ny, nx, M = 64, 100, 2
+    terr = synth.make_terrain(ny, nx, seed=64)
+    cls = synth.land_cover(terr, seed=64, pond_side=(6, 14))
+    water = cls == 1
+    assert water.any()
+    h0 = np.where(water, np.maximum(np.float32(3.0) - terr.z, 0.0), 0.0).astype(np.float32)
+    assert h0.max() > 0
+    hy = synth.hyetograph_constant(0.0, 600.0)
+    rm, sc = synth.ensemble_prior(64, M)
+    n_m, d_m = synth.land_prior(64, M)
+    p = capi.Params.default()
+    with capi.Grid(terr.z, terr.n, p) as g:
+        g.set_land_cover(cls, synth.LAND_CLASSES)
+        g.ensemble_init(M, rm, sc, hy, h0=h0)
+        g.set_land_params(n_m, d_m)
+        V0 = g.volumes()["storage"]
+        g.advance_to(600.0)
+        states = [g.get_state(m) for m in range(M)]
+        vol = g.volumes()
+        drained = g.drained()
+    for m in range(M):
+        z, n, rc, dr, out = _oracle_fields(terr, cls, n_m[m], d_m[m])
+        op = oracle_params(p, ny, nx)
+        op.rc, op.drain = rc, dr
+        mo = oracle.Member.dry(ny, nx)
+        mo.h[:] = np.where(out, 0.0, h0)
+        oracle.advance(op, z, n, float(sc[m]), float(rm[m]), hy, mo, t_end=600.0)
+        compare(states[m][0], mo.h, 1e-3)
+        assert vol["rain"][m] == 0.0
+        bal = vol["storage"][m] - (V0[m] - vol["outflow"][m] + vol["clamp"][m] - drained[m])
+        assert abs(bal) <= 1e-5 * V0[m]
