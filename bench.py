@@ -823,18 +823,20 @@ def network_minmax(M):
 
 
 # Minimum / maximum results per clock per SM (the ALU pipe: 16 lanes per
-# scheduler, 4 schedulers), and the GB300's SM count.
+# scheduler, 4 schedulers).
 ALU_MINMAX_PER_CLK_SM = 64
-N_SM = 152
 
 
 def alu_roofline(ops, ms, sm_mhz):
     """The sort network's min/max operations per second against the ALU
-    pipe's peak at the sampled SM clock."""
-    peak = ALU_MINMAX_PER_CLK_SM * N_SM * sm_mhz * 1e6
+    pipe's peak at the sampled SM clock, over the device's SMs."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = ALU_MINMAX_PER_CLK_SM * n_sm * sm_mhz * 1e6
     achieved = ops / (ms * 1e-3)
     return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-            "unit": "T min/max per s", "frac": achieved / peak, "ops_per_cell": ops / (NY * NX)}
+            "unit": "T min/max per s", "frac": achieved / peak, "ops_per_cell": ops / (NY * NX),
+            "sms": n_sm}
 
 
 def products_measure(g, stream, device, ncell, fused_value):
