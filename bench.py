@@ -240,17 +240,19 @@ def make_inputs():
 
 def truth_observations(capi, terr, hy, cells, n_windows):
     """Hidden truth member (own prior draw) run on the GPU; noisy depths at
-    the gauges at every window end (inputs of the benchmark, not timed)."""
+    the gauges at every window end (inputs of the benchmark, not timed), and
+    the truth's own depths there."""
     from paper_2302_08341_gb300 import synth
     trm, tsc = synth.ensemble_prior(SEED + 1000, 1)
-    obs = []
+    obs, truth = [], []
     with capi.Grid(terr.z, terr.n) as g:
         g.ensemble_init(1, trm, tsc, hy)
         for w in range(1, n_windows + 1):
             g.advance_to(WINDOW * w)
             y = g.gauge_sample(cells)
             obs.append(synth.observe(y[0], seed=SEED, window=w))
-    return obs
+            truth.append(y[0].astype(np.float64))
+    return obs, np.array(truth)
 
 
 def cpu_baseline(terr, hy, rm, sc, target_s=15.0):
@@ -949,7 +951,7 @@ def run_gb300(args):
 
     terr, hy, rm, sc, cells = make_inputs()
     n_win = args.warmup + args.steps
-    obs = truth_observations(capi, terr, hy, cells, max(n_win, args.steps))
+    obs, truth = truth_observations(capi, terr, hy, cells, max(n_win, args.steps))
     stream = torch.cuda.current_stream(device)
     ncell = NY * NX
 
@@ -1019,7 +1021,7 @@ def run_gb300(args):
 
     # end to end through the public API with host buffers (pinned), copies
     # inside the timed region
-    e2e = None
+    e2e = da_skill = None
     if not args.no_e2e:
         h_d = [torch.tensor(o, dtype=torch.float64).pin_memory() for o in obs]
         h_beta = [torch.tensor(b).pin_memory() for _, b in draws]
@@ -1033,11 +1035,17 @@ def run_gb300(args):
         barrier(world)
         torch.cuda.synchronize(device)
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        w_prior = np.full(M, 1.0 / M)   # the weights the members carry into a window
+        est = []                        # per window: prior and posterior estimates at the gauges
         e0.record(stream)
         for w in range(1, args.steps + 1):
             window(g, w, h_d[w - 1], h_beta[w - 1], draws[w - 1][0], h_outs)
             stream.synchronize()   # the host reads the window's result
             _ = float(h_outs["neff"][0])
+            y = h_outs["y"].numpy().astype(np.float64)
+            w_post = h_outs["weights"].numpy().copy()
+            est.append((w_prior @ y, w_post @ y))
+            w_prior = np.full(M, 1.0 / M) if int(h_outs["resampled"][0]) else w_post
         e1.record(stream)
         torch.cuda.synchronize(device)
         barrier(world)
@@ -1046,6 +1054,16 @@ def run_gb300(args):
         e2e = {"value": e_units / (e_ms * 1e-3), "unit": "member-cell-steps/s",
                "h2d_bytes_per_step": G * 8 + M * 4,
                "d2h_bytes_per_step": M * 8 + M * 4 + 8 + 4 + M * G * 4}
+        # what the filter does with the ensemble (§4.4): the weighted mean
+        # depth at the gauges before and after each window's update, against
+        # the hidden truth's own depths there
+        pri = np.array([e[0] for e in est]); post = np.array([e[1] for e in est])
+        tr = truth[:len(est)]
+        da_skill = {"rmse_prior_m": float(np.sqrt(np.mean((pri - tr) ** 2))),
+                    "rmse_posterior_m": float(np.sqrt(np.mean((post - tr) ** 2))),
+                    "windows": len(est), "gauges": G,
+                    "config": "weighted ensemble mean of the gauge depths before and after each "
+                              "window's particle-filter update, against the hidden truth"}
     plain = products = eta = da = cfl = None
     if not args.no_extensions and world == 1:
         plain = plain_vs_fused(g, tuned, stream, device, ncell, hbm_peak)
@@ -1088,6 +1106,7 @@ def run_gb300(args):
         extensions["eta_bar"] = eta
         extensions["cfl_bound"] = cfl
         extensions["assimilation_overhead"] = da
+        extensions["da_skill"] = da_skill
 
     if rank != 0:
         if world > 1:
