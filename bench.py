@@ -802,26 +802,33 @@ def masked_domain_measure(capi):
     return res
 
 
-def network_minmax(M):
-    """Min/max operations per cell of the products kernels' register sort:
-    Batcher's odd-even merge sort on N (a power of two) slots with every
-    comparator that reaches a padding slot above MT left out (MT = the
-    member count rounded up to 32, 64, 96 or 128), the same pruning rule as
-    the kernels, two operations per comparator (1056 comparators at 96)."""
+def sort_network(M):
+    """The comparators (lo, hi) of the products kernels' register sort, in
+    order: Batcher's odd-even merge sort on N (a power of two) slots with
+    every comparator that reaches a padding slot at or above MT left out
+    (MT = the member count rounded up to 32, 64, 96 or 128; N = MT rounded up
+    to a power of two), the same pruning rule as the kernels.  The padding
+    slots hold +inf, so the comparators left out never move a value."""
     MT = 32 if M <= 32 else 64 if M <= 64 else 96 if M <= 96 else 128
     N = 32 if MT <= 32 else 64 if MT <= 64 else 128
-    n, P = 0, 1
+    pairs, P = [], 1
     while P < N:
         K = P
         while K >= 1:
             j = K % P
             while j + K < N:
-                n += sum(1 for i in range(K)
-                         if i + j + K < MT and (i + j) // (2 * P) == (i + j + K) // (2 * P))
+                pairs += [(i + j, i + j + K) for i in range(K)
+                          if i + j + K < MT and (i + j) // (2 * P) == (i + j + K) // (2 * P)]
                 j += 2 * K
             K //= 2
         P *= 2
-    return 2 * n
+    return pairs
+
+
+def network_minmax(M):
+    """Min/max operations per cell of the products kernels' register sort:
+    two per comparator of `sort_network` (1056 comparators at 96 members)."""
+    return 2 * len(sort_network(M))
 
 
 # Minimum / maximum results per clock per SM (the ALU pipe: 16 lanes per
