@@ -59,3 +59,27 @@ def test_argument_errors_are_reported_before_any_device_work(capi):
     assert L.flood_step(None, 1, -1.0, None) == -1
     assert L.flood_destroy(None) == 0
     assert L.flood_launch_count(None) == 0
+
+
+def test_every_handle_call_refuses_a_null_handle(capi):
+    """Each entry point that takes a grid or batch handle returns
+    FLOOD_ERR_ARG for a NULL one (no device work); the destroy calls accept
+    NULL and the launch counters read 0."""
+    L = capi.lib()
+    no_handle = {"flood_default_params", "flood_create_grid", "flood_batch_create",
+                 "pf_resample_systematic", "flood_storage_static", "flood_storage_static_error"}
+    want = {"flood_destroy": 0, "flood_batch_destroy": 0, "flood_launch_count": 0,
+            "flood_batch_launch_count": 0}
+    text = {"flood_last_error", "flood_batch_last_error"}
+    checked = 0
+    for name in capi.EXPORTED:
+        if name in no_handle or name in text:
+            continue
+        f = getattr(L, name)
+        args = [0 if t in (C.c_int, C.c_int64) else 0.0 if t is C.c_double else None
+                for t in f.argtypes]
+        assert f(*args) == want.get(name, -1), name
+        checked += 1
+    assert checked == len(capi.EXPORTED) - len(no_handle) - len(text)
+    assert L.flood_last_error(None) == b"grid is NULL"
+    assert L.flood_batch_last_error(None) == b"batch is NULL"
