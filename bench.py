@@ -89,6 +89,62 @@ def guarded(fn, *a, **kw):
         return {"error": f"{type(e).__name__}: {e}"}
 
 
+def rounded(o, digits=4):
+    """Floats of a nested result to `digits` significant digits (the
+    extension figures; the timing keys keep full precision)."""
+    if isinstance(o, float):
+        return float(f"{o:.{digits}g}")
+    if isinstance(o, dict):
+        return {k: rounded(v, digits) for k, v in o.items()}
+    if isinstance(o, list):
+        return [rounded(v, digits) for v in o]
+    return o
+
+
+# (summary key, path into the extensions) of the figures repeated, compact,
+# at the end of the line
+SUMMARY_PATHS = [
+    ("adj_over_fwd_1024x1024x1_1800s", ("adjoint", "adj_over_fwd")),
+    ("adj_over_fwd_2000x2000x96_calibration", ("calibration", "adj_over_fwd")),
+    ("adj_over_fwd_2000x2000x96_land_cover", ("land_cover", "adjoint", "adj_over_fwd")),
+    ("calibration_ms_per_window", ("calibration", "ms_per_window")),
+    ("batched_value", ("batched", "value")),
+    ("batched_hbm_frac", ("batched", "hbm_frac_whole_window")),
+    ("batched_persistent_value", ("batched", "persistent", "value")),
+    ("batched_four_members_value", ("batched", "four_members", "value")),
+    ("batched_four_members_hbm_frac", ("batched", "four_members", "hbm_frac_whole_window")),
+    ("batched_land_cover_active_value", ("batched", "land_cover", "active_value")),
+    ("land_cover_step_ms", ("land_cover", "step_kernel_ms")),
+    ("land_cover_step_ms_without", ("land_cover", "without", "step_kernel_ms")),
+    ("masked_domain_step_time_ratio", ("masked_domain", "step_time_ratio")),
+    ("masked_domain_tiles_launched_frac", ("masked_domain", "masked", "tiles_launched_frac")),
+    ("fused_over_plain_per_member", ("plain_vs_fused", "fused_over_plain")),
+    ("cfl_bound_value", ("cfl_bound", "value")),
+    ("cfl_bound_hbm_frac", ("cfl_bound", "hbm_frac_step_kernel")),
+    ("products_ms_equal_weights", ("products", "products_ms_equal_weights")),
+    ("products_ms_unequal_weights", ("products", "products_ms_unequal_weights")),
+    ("products_alu_frac_equal", ("products", "alu_roofline", "equal_weights", "frac")),
+    ("products_alu_frac_unequal", ("products", "alu_roofline", "unequal_weights", "frac")),
+    ("eta_bar_us_96_members", ("eta_bar", "members_per_device", "96", "eta_bar_us_per_member_step")),
+    ("pf_update_ms_resampling", ("assimilation_overhead", "resampling_ms")),
+    ("gauge_rmse_prior_m", ("da_skill", "rmse_prior_m")),
+    ("gauge_rmse_posterior_m", ("da_skill", "rmse_posterior_m")),
+]
+
+
+def extension_summary(ext):
+    """The headline figure of each extension, in one short object (a long
+    line's readers may keep only its end); missing ones are left out."""
+    out = {}
+    for name, path in SUMMARY_PATHS:
+        v = ext
+        for k in path:
+            v = v.get(k) if isinstance(v, dict) else None
+        if isinstance(v, (int, float)) and not isinstance(v, bool):
+            out[name] = rounded(float(v))
+    return out
+
+
 def kernel_hash():
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
@@ -1144,7 +1200,9 @@ def run_gb300(args):
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
         "clocks": clocks,
     }
-    line.update(extensions)
+    line.update(rounded(extensions))
+    if extensions:
+        line["summary"] = extension_summary(extensions)
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -53,3 +53,16 @@ def test_unsorted_input_is_caught():
     x = rng.integers(0, 2, size=(4000, 32)).astype(np.float64)
     out = apply_network(pairs, x)
     assert not np.array_equal(out, np.sort(x, axis=1))
+
+
+def test_summary_repeats_the_extension_figures_at_the_end():
+    ext = {"adjoint": {"adj_over_fwd": 1.72900268, "config": "x"},
+           "land_cover": {"step_kernel_ms": 1.8107496, "without": {"step_kernel_ms": 1.628},
+                          "adjoint": {"adj_over_fwd": 2.62}},
+           "batched": {"error": "RuntimeError: no device"},
+           "products": {"alu_roofline": {"equal_weights": {"frac": True}}}}
+    s = bench.extension_summary(ext)
+    assert s == {"adj_over_fwd_1024x1024x1_1800s": 1.729,
+                 "adj_over_fwd_2000x2000x96_land_cover": 2.62,
+                 "land_cover_step_ms": 1.811, "land_cover_step_ms_without": 1.628}
+    assert bench.rounded({"a": [0.123456, 2], "b": "c"}) == {"a": [0.1235, 2], "b": "c"}
