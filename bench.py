@@ -126,6 +126,8 @@ SUMMARY_PATHS = [
     ("products_alu_frac_equal", ("products", "alu_roofline", "equal_weights", "frac")),
     ("products_alu_frac_unequal", ("products", "alu_roofline", "unequal_weights", "frac")),
     ("eta_bar_us_96_members", ("eta_bar", "members_per_device", "96", "eta_bar_us_per_member_step")),
+    ("graphs_speedup_256x256x1", ("graphs", "small", "speedup")),
+    ("graphs_speedup_2000x2000x96", ("graphs", "ensemble", "speedup")),
     ("pf_update_ms_resampling", ("assimilation_overhead", "resampling_ms")),
     ("gauge_rmse_prior_m", ("da_skill", "rmse_prior_m")),
     ("gauge_rmse_posterior_m", ("da_skill", "rmse_posterior_m")),
@@ -625,6 +627,53 @@ def cfl_bound_measure(capi, terr, hy, rm, sc, tuned):
                                     / (kms * 1e-3) / 1e9 / peaks()[0]}
 
 
+def graphs_measure(capi, terr, hy, rm, sc, tuned):
+    """The ensemble's steps launched one by one against runs of 24 steps
+    replayed from a CUDA graph (flood_set_graphs), both timed with CUDA
+    events around one flood_step call: a small single-member grid whose
+    kernels last microseconds (256 x 256 cells, 50 mm/h, 600 s of steps: the
+    launches bound it), and one 300 s window of the benchmark ensemble (the
+    step kernel bounds it).  The capture of each call's run is inside the
+    timed region."""
+    import torch
+    from paper_2302_08341_gb300 import synth
+    stream = torch.cuda.current_stream()
+    small = synth.make_terrain(256, 256, seed=0)
+    cases = {"small": (small, synth.hyetograph_constant(50.0, 900.0),
+                       np.ones(1, np.float32), np.ones(1, np.float32), 30.0, 630.0, None),
+             "ensemble": (terr, hy, rm, sc, 60.0, 60.0 + WINDOW, tuned)}
+    res = {}
+    for name, (tr, hyc, rmc, scc, t0, t1, tun) in cases.items():
+        out = {}
+        for graphs in (False, True):
+            with capi.Grid(tr.z, tr.n) as g:
+                g.ensemble_init(len(rmc), rmc, scc, hyc, stream=stream)
+                if tun:
+                    g.set_engine(tun["engine"])
+                    g.set_launch(tun["rows_per_strip"], tun["members_per_cta"])
+                g.set_graphs(graphs)
+                g.advance_to(t0, stream=stream)
+                s0 = g.members()["steps"].sum()
+                e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                h0 = time.perf_counter()
+                e0.record(stream)
+                g.advance_to(t1, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                wall = (time.perf_counter() - h0) * 1e3
+                steps = float(g.members()["steps"].sum() - s0)
+                out["graphs" if graphs else "plain"] = {
+                    "ms": e0.elapsed_time(e1), "host_ms": wall,
+                    "member_cell_steps_per_s": steps * tr.z.size / (e0.elapsed_time(e1) * 1e-3),
+                    "captures_replays": list(g.graph_stats())}
+        out["speedup"] = out["plain"]["ms"] / out["graphs"]["ms"]
+        out["config"] = (f"{tr.z.shape[0]}x{tr.z.shape[1]} cells, {len(rmc)} member(s), "
+                         f"flood_step from t = {t0:g} s to {t1:g} s")
+        res[name] = out
+    return res
+
+
 def eta_sweeps(capi, g, tuned, stream, device, terr, hy, rm, sc):
     """Section 4.4's eta-bar (Eq. 13: the run time of one member, the
     ensemble's time divided by the members sharing the device) on this GPU,
@@ -1094,6 +1143,7 @@ def run_gb300(args):
                       resampled=torch.zeros(1, dtype=torch.int32).pin_memory(),
                       y=torch.zeros((M, G), dtype=torch.float32).pin_memory())
         g.ensemble_init(M, rm, sc, hy, stream=stream)
+        g.set_graphs(True)   # runs of steps replayed from CUDA graphs (bit for bit the same)
         s0 = g.members()["steps"].sum()
         barrier(world)
         torch.cuda.synchronize(device)
@@ -1112,6 +1162,7 @@ def run_gb300(args):
         e1.record(stream)
         torch.cuda.synchronize(device)
         barrier(world)
+        g.set_graphs(False)
         e_ms = max_over_ranks(e0.elapsed_time(e1), world, device)
         e_units = sum_over_ranks(float(g.members()["steps"].sum() - s0) * ncell, world, device)
         e2e = {"value": e_units / (e_ms * 1e-3), "unit": "member-cell-steps/s",
@@ -1127,12 +1178,13 @@ def run_gb300(args):
                     "windows": len(est), "gauges": G,
                     "config": "weighted ensemble mean of the gauge depths before and after each "
                               "window's particle-filter update, against the hidden truth"}
-    plain = products = eta = da = cfl = None
+    plain = products = eta = da = cfl = graphs = None
     if not args.no_extensions and world == 1:
         plain = plain_vs_fused(g, tuned, stream, device, ncell, hbm_peak)
         products = products_measure(g, stream, device, ncell, plain["fused"]["value"])
         eta = guarded(eta_sweeps, capi, g, tuned, stream, device, terr, hy, rm, sc)
         cfl = guarded(cfl_bound_measure, capi, terr, hy, rm, sc, tuned)
+        graphs = guarded(graphs_measure, capi, terr, hy, rm, sc, tuned)
         da = guarded(assimilation_overhead, g, stream, device, cells, obs[0])
     g.close()
     extensions = {}
@@ -1168,6 +1220,7 @@ def run_gb300(args):
         extensions["products"] = products
         extensions["eta_bar"] = eta
         extensions["cfl_bound"] = cfl
+        extensions["graphs"] = graphs
         extensions["assimilation_overhead"] = da
         extensions["da_skill"] = da_skill
 

@@ -483,6 +483,23 @@ int flood_set_engine(flood_grid* g, int engine);
  * ordinary step keeps its limit as a constant.  Errors: FLOOD_ERR_ARG. */
 int flood_set_wait_budget(flood_grid* g, int64_t cycles);
 
+/* CUDA-graph replay of flood_step (extension; the paper launches its kernels
+ * one by one).  With on != 0, flood_step captures a run of 24 steps (the plan
+ * and step kernels of each, in order) once, on a stream of the grid's own, and
+ * replays that graph on the caller's stream for every further run of 24 steps
+ * while every launch argument stays the same: t_end, the engine and launch
+ * shape, land cover, the running maximum, inflow and the device buffers.  A
+ * change captures again.  The steps before the member-clock ring returns to
+ * its first slot and the remainder launch one by one.  Results are bit for bit
+ * those of plain launches.  Steps timed by flood_profile and the adjoint's
+ * logged forward launch plainly.  Off by default.  Errors: FLOOD_ERR_ARG;
+ * flood_step reports a failed capture as FLOOD_ERR_CUDA. */
+int flood_set_graphs(flood_grid* g, int on);
+
+/* How many runs flood_step has captured into a graph and how many it has
+ * replayed (either pointer may be NULL).  Errors: FLOOD_ERR_ARG. */
+int flood_graph_stats(flood_grid* g, int64_t* captures, int64_t* replays);
+
 /* Autotuner: time every step-kernel configuration (engine x rows per strip
  * {32, 64, 128} x members per CTA {8, 4, 2, 1}; 8 and 2 with the plain TMA
  * step only) for steps_per_trial steps on the

@@ -37,7 +37,8 @@ EXPORTED = ["flood_default_params", "flood_last_error", "flood_create_grid", "fl
             "flood_get_land_params", "flood_drained_volume", "flood_flow_sample", "flood_set_inflow",
             "flood_inflow_volume", "flood_batch_autotune", "flood_batch_set_wait_budget",
             "flood_adjoint_land_grad", "flood_batch_init_members", "flood_batch_get_member_state",
-            "flood_batch_set_land_cover", "flood_batch_set_land_params", "flood_batch_drained_volume"]
+            "flood_batch_set_land_cover", "flood_batch_set_land_params", "flood_batch_drained_volume",
+            "flood_set_graphs", "flood_graph_stats"]
 
 
 class LandClass(C.Structure):
@@ -124,6 +125,8 @@ def lib(path: str = LIB_PATH):
     L.flood_adjoint.argtypes = [_VP, C.POINTER(LossSpec), C.c_int, _VP, _VP, _VP, _VP, _VP, _VP]
     L.flood_adjoint_timing.argtypes = [_VP, _VP, _VP]
     L.flood_set_wait_budget.argtypes = [_VP, C.c_int64]
+    L.flood_set_graphs.argtypes = [_VP, C.c_int]
+    L.flood_graph_stats.argtypes = [_VP, _VP, _VP]
     L.flood_batch_autotune.argtypes = [_VP, C.c_double, _VP, _VP, _VP, _VP, _VP]
     L.flood_batch_set_wait_budget.argtypes = [_VP, C.c_int64]
     L.flood_autotune.argtypes = [_VP, C.c_int, _VP, _VP, _VP, _VP, _VP]
@@ -380,6 +383,17 @@ class Grid:
         """Clock-cycle limit of the TMA step kernel's row waits (< 0: the
         default); a failure-detection hook (flood_set_wait_budget)."""
         _check(lib().flood_set_wait_budget(self.h, int(cycles)), self.h)
+
+    def set_graphs(self, on=True):
+        """CUDA-graph replay of runs of 24 steps in advance_to / step
+        (flood_set_graphs); identical results."""
+        _check(lib().flood_set_graphs(self.h, int(bool(on))), self.h)
+
+    def graph_stats(self):
+        """(runs captured, runs replayed) so far (flood_graph_stats)."""
+        c = C.c_int64(); r = C.c_int64()
+        _check(lib().flood_graph_stats(self.h, C.byref(c), C.byref(r)), self.h)
+        return c.value, r.value
 
     def get_launch(self):
         r = C.c_int(); m = C.c_int()

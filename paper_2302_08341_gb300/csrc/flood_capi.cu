@@ -171,53 +171,160 @@ void collect_profile(flood_grid* g)
     g->ev_pending.clear();
 }
 
+// Whether the TMA step leaves out the tiles wholly outside the domain (land
+// cover with classes outside it; the ordinary step only).
+static bool skips_tiles(const flood_grid* g, const StepArgs& a)
+{
+    return g->engine == 1 && g->maps_ok && a.lc_on && g->lc_out_mask && !a.ckpt &&
+           a.wait_budget == kTmaWaitBudgetDefault;
+}
+
+// One step of every member: the plan kernel (Eq. 4, the events), then the
+// step kernel of the chosen engine.
+static int launch_one(flood_grid* g, double t_end, cudaStream_t s)
+{
+    flood::StepArgs a = step_args(g, t_end);
+    flood::launch_plan(a, s);
+    g->launches++;
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (g->profile) {
+        if (g->ev_free.empty()) {
+            CK(g, cudaEventCreate(&ev.first));
+            CK(g, cudaEventCreate(&ev.second));
+        } else {
+            ev = g->ev_free.back();
+            g->ev_free.pop_back();
+        }
+        CK(g, cudaEventRecord(ev.first, s));
+    }
+    if (g->engine == 1 && g->maps_ok) {
+        flood::TmaArgs t;
+        t.state_map = g->state_map;
+        t.static_map = a.lc_on ? g->static_map_lc : g->static_map;
+        if (a.hmax_field) t.hm_map = g->hm_map;
+        if (skips_tiles(g, a)) {
+            if (g->tiles_rows != g->rows_per_strip) {
+                const int rc = land_tiles(g);
+                if (rc) return rc;
+            }
+            a.tiles = g->tiles;
+            a.n_tiles = g->n_tiles;
+        }
+        t.a = a;
+        if (flood::launch_step_tma(t, g->members_per_cta, s))
+            return fail(g, FLOOD_ERR_STATE, "a changed wait budget covers the plain step only");
+    } else if (g->engine == 2 && !g->lc_on) {
+        flood::launch_step_per_member(a, s);
+        g->launches += g->M - 1;
+    } else {
+        flood::launch_step(a, g->members_per_cta, s);
+    }
+    if (g->profile) {
+        CK(g, cudaEventRecord(ev.second, s));
+        g->ev_pending.push_back(ev);
+    }
+    g->k++;
+    g->launches++;
+    return FLOOD_OK;
+}
+
+// Steps per captured run: a multiple of the member-clock ring's period (3),
+// so that a run captured at ring phase 0 replays at every later phase 0.
+static constexpr int kGraphSteps = 24;
+
+// Everything the launches of a step take from the host, at ring phase 0: the
+// step arguments (t_end included), the engine and its launch shape, the
+// tensor maps and the tile list.  A captured run replays while this holds.
+static std::vector<unsigned char> graph_key(const flood_grid* g, double t_end)
+{
+    const flood::StepArgs a = step_args(g, t_end);
+    std::vector<unsigned char> key;
+    auto put = [&key](const void* p, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(p);
+        key.insert(key.end(), b, b + n);
+    };
+    put(&a, sizeof a);
+    const int v[4] = {g->engine, g->members_per_cta, g->maps_ok ? 1 : 0, g->n_tiles};
+    put(v, sizeof v);
+    put(&g->tiles, sizeof g->tiles);
+    if (g->engine == 1 && g->maps_ok) {
+        put(&g->state_map, sizeof g->state_map);
+        put(a.lc_on ? &g->static_map_lc : &g->static_map, sizeof(CUtensorMap));
+        if (a.hmax_field) put(&g->hm_map, sizeof g->hm_map);
+    }
+    return key;
+}
+
+// Capture kGraphSteps steps from ring phase 0 on the grid's own stream
+// (nothing runs; the steps' kernels become the graph's nodes in order),
+// unless the graph in hand was captured from the same launch arguments.
+static int ensure_graph(flood_grid* g, double t_end)
+{
+    CK(g, cudaGetLastError());  // the plain launches before this one
+    if (skips_tiles(g, step_args(g, t_end)) && g->tiles_rows != g->rows_per_strip) {
+        const int rc = land_tiles(g);  // allocates: not while capturing
+        if (rc) return rc;
+    }
+    std::vector<unsigned char> key = graph_key(g, t_end);
+    if (g->gexec && key == g->graph_key) return FLOOD_OK;
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    g->gexec = nullptr;
+    g->graph = nullptr;
+    g->graph_key.clear();
+    if (!g->cap_stream) CK(g, cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+    const int64_t k0 = g->k, l0 = g->launches;
+    CK(g, cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeRelaxed));
+    int rc = FLOOD_OK;
+    for (int i = 0; i < kGraphSteps && rc == FLOOD_OK; ++i) rc = launch_one(g, t_end, g->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(g->cap_stream, &graph);
+    g->graph_launch_delta = g->launches - l0;
+    g->k = k0;
+    g->launches = l0;
+    cudaGetLastError();  // a failed capture is reported below, not by the next check
+    if (rc != FLOOD_OK || ec != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc != FLOOD_OK ? rc
+                              : fail(g, FLOOD_ERR_CUDA,
+                                     std::string("capturing the steps: ") + cudaGetErrorString(ec));
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&g->gexec, graph, 0);
+    if (ei != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        g->gexec = nullptr;
+        return fail(g, FLOOD_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei));
+    }
+    g->graph = graph;
+    g->graph_key = std::move(key);
+    g->graph_captures++;
+    return FLOOD_OK;
+}
+
 int launch_steps(flood_grid* g, int64_t count, double t_end, cudaStream_t s)
 {
     g->epoch++;
-    for (int64_t i = 0; i < count; ++i) {
-        flood::StepArgs a = step_args(g, t_end);
-        flood::launch_plan(a, s);
-        g->launches++;
-        std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
-        if (g->profile) {
-            if (g->ev_free.empty()) {
-                CK(g, cudaEventCreate(&ev.first));
-                CK(g, cudaEventCreate(&ev.second));
-            } else {
-                ev = g->ev_free.back();
-                g->ev_free.pop_back();
-            }
-            CK(g, cudaEventRecord(ev.first, s));
+    int64_t i = 0;
+    // runs of kGraphSteps steps from a captured graph (steps timed one by one
+    // and the adjoint's logged steps launch plainly); the steps before ring
+    // phase 0 and the remainder launch plainly
+    if (g->graphs && !g->profile && !g->logging && count >= kGraphSteps + 2) {
+        for (; g->k % 3 != 0; ++i) {
+            const int rc = launch_one(g, t_end, s);
+            if (rc) return rc;
         }
-        if (g->engine == 1 && g->maps_ok) {
-            flood::TmaArgs t;
-            t.state_map = g->state_map;
-            t.static_map = a.lc_on ? g->static_map_lc : g->static_map;
-            if (a.hmax_field) t.hm_map = g->hm_map;
-            // the ordinary step leaves out the tiles wholly outside the domain
-            if (a.lc_on && g->lc_out_mask && !a.ckpt && a.wait_budget == kTmaWaitBudgetDefault) {
-                if (g->tiles_rows != g->rows_per_strip) {
-                    const int rc = land_tiles(g);
-                    if (rc) return rc;
-                }
-                a.tiles = g->tiles;
-                a.n_tiles = g->n_tiles;
-            }
-            t.a = a;
-            if (flood::launch_step_tma(t, g->members_per_cta, s))
-                return fail(g, FLOOD_ERR_STATE, "a changed wait budget covers the plain step only");
-        } else if (g->engine == 2 && !g->lc_on) {
-            flood::launch_step_per_member(a, s);
-            g->launches += g->M - 1;
-        } else {
-            flood::launch_step(a, g->members_per_cta, s);
+        const int rc = ensure_graph(g, t_end);
+        if (rc) return rc;
+        for (; count - i >= kGraphSteps; i += kGraphSteps) {
+            CK(g, cudaGraphLaunch(g->gexec, s));
+            g->k += kGraphSteps;
+            g->launches += g->graph_launch_delta;
+            g->graph_replays++;
         }
-        if (g->profile) {
-            CK(g, cudaEventRecord(ev.second, s));
-            g->ev_pending.push_back(ev);
-        }
-        g->k++;
-        g->launches++;
+    }
+    for (; i < count; ++i) {
+        const int rc = launch_one(g, t_end, s);
+        if (rc) return rc;
     }
     CK(g, cudaGetLastError());
     return FLOOD_OK;
@@ -372,6 +479,9 @@ int flood_destroy(flood_grid* g)
         cudaEventDestroy(p.first);
         cudaEventDestroy(p.second);
     }
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     free_ensemble(g);
     dfree(g->zn);
     dfree(g->err);
@@ -801,6 +911,21 @@ int flood_set_wait_budget(flood_grid* g, int64_t cycles)
 {
     if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
     g->wait_budget = cycles < 0 ? -1 : (long long)cycles;
+    return FLOOD_OK;
+}
+
+int flood_set_graphs(flood_grid* g, int on)
+{
+    if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    g->graphs = on != 0;
+    return FLOOD_OK;
+}
+
+int flood_graph_stats(flood_grid* g, int64_t* captures, int64_t* replays)
+{
+    if (!g) return fail(nullptr, FLOOD_ERR_ARG, "grid is NULL");
+    if (captures) *captures = g->graph_captures;
+    if (replays) *replays = g->graph_replays;
     return FLOOD_OK;
 }
 

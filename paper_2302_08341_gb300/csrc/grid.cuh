@@ -65,6 +65,16 @@ struct flood_grid {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free;
     double prof_ms = 0.0;
     int64_t prof_launches = 0;
+    // CUDA-graph replay of flood_step's launches (flood_set_graphs): a run of
+    // kGraphSteps steps captured on cap_stream and replayed on the caller's
+    // stream while the launch arguments stay those of graph_key
+    bool graphs = false;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<unsigned char> graph_key;
+    int64_t graph_launch_delta = 0;  // kernel launches of one replay
+    int64_t graph_captures = 0, graph_replays = 0;
     // adjoint (flood_adjoint): step log, checkpoints, segment replay buffers
     flood::MemberPlan* plan = nullptr;  // [M] the current step's plans
     flood::MemberPlan* log = nullptr;   // [M][log_cap] plans of the logged steps
