@@ -122,6 +122,8 @@ int flood_ensemble_init(flood_grid* g, int n_members, const float* h0, int h0_pe
  *   t_end >= 0  advance every member to t_end (members already there stay
  *               put).  n_steps <= 0: no limit on steps, > 0: at most n_steps
  *               steps.  Synchronises `stream` to follow the members' clocks.
+ * Each step is a plan kernel then a step kernel on `stream`; with
+ * flood_set_graphs, runs of 24 steps are replayed from a CUDA graph instead.
  * Errors: FLOOD_ERR_STATE before flood_ensemble_init, FLOOD_ERR_NAN if a
  * depth became non-finite (detected at the synchronisation points),
  * FLOOD_ERR_CUDA.
